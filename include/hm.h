@@ -1,0 +1,225 @@
+/*
+ * hm.h -- C-ABI of libhm.so: GB300 (sm_103a) H-matrix build and H-matrix-vector
+ * product for kernel matrices A_{phi,Y x Y} (optionally + sigma^2 I), after
+ * P. Zaspel, "Algorithmic patterns for H-matrices on many-core processors"
+ * (arXiv 1708.09707).
+ *
+ * Conventions for every entry point:
+ *  - Pointers may be host (pageable or pinned) or device memory of the current
+ *    CUDA device; the library tells them apart with cudaPointerGetAttributes.
+ *    Host inputs are copied in, host outputs copied out before return.
+ *  - Functions returning int give HM_OK (0) or a negative HM_E* code and never
+ *    abort the process; hm_last_error() describes the last failure of the
+ *    calling thread. No kernel traps: device-side failures (loop limits) set a
+ *    status word that the host turns into HM_ETIMEOUT.
+ *  - The caller keeps ownership of every pointer it passes; the library keeps
+ *    no reference to caller memory after a call returns. The handle owns all
+ *    device memory it allocates until hm_free.
+ *  - Work is enqueued on the handle's stream (hm_options.stream, default the
+ *    legacy default stream). Functions that return data to host memory, or
+ *    read sizes back, synchronise that stream.
+ *  - All floating-point inputs are IEEE double; the arithmetic used inside is
+ *    set by hm_options.precision.
+ */
+#ifndef HM_H
+#define HM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Kernel functions phi(y, y') of r = |y - y'|, params[0] = length scale l > 0:
+ *   HM_GAUSSIAN:  exp(-r^2 / l^2)           (Sec. 6.2 uses l = 1)
+ *   HM_MATERN32:  (1 + sqrt3 r / l) exp(-sqrt3 r / l)
+ * params[1] = sigma^2 >= 0 is added on the diagonal by the product (Sec. 1,
+ * the GPR / kernel ridge regression system A + sigma^2 I). */
+enum { HM_GAUSSIAN = 0, HM_MATERN32 = 1 };
+
+enum {
+    HM_OK = 0,
+    HM_EINVAL = -1,     /* bad argument (sizes, parameters, non-finite input) */
+    HM_ENOMEM = -2,     /* device allocation failed */
+    HM_EOVERFLOW = -3,  /* an internal bound was exceeded and could not grow */
+    HM_ECUDA = -4,      /* a CUDA runtime call failed */
+    HM_ETIMEOUT = -5,   /* a device loop hit its iteration limit */
+    HM_ENOTSUP = -6     /* option combination not supported */
+};
+
+/* Arithmetic of the build and the product. */
+enum {
+    HM_PREC_FP64 = 0,   /* everything in double precision */
+    HM_PREC_MIXED = 1   /* FP32 kernel evaluation, ACA and factors; FP64 ACA
+                           stopping test; near field per near_format; FP32
+                           products with compensated accumulation */
+};
+
+/* Storage of the near-field (inadmissible) leaf blocks. */
+enum {
+    HM_NEAR_AUTO = 0,   /* FP64 for HM_PREC_FP64, BF16X2 for HM_PREC_MIXED */
+    HM_NEAR_FP64 = 1,
+    HM_NEAR_FP32 = 2,
+    HM_NEAR_BF16X2 = 3, /* hi + lo bfloat16 pair per entry (about 16 bits) */
+    HM_NEAR_BF16 = 4    /* single bfloat16 (8 bits; about 1e-3 per entry) */
+};
+
+typedef struct hm_options {
+    int precision;        /* HM_PREC_*, default HM_PREC_FP64 */
+    int near_format;      /* HM_NEAR_*, default HM_NEAR_AUTO */
+    int adm_max;          /* 0: min{diam} <= eta dist (paper), 1: max{diam} */
+    int k_cap;            /* ACA rank cap, default 64; fixed rank when aca_eps<=0 */
+    double aca_eta;       /* eta of the ACA stopping rule, default 0 */
+    double eps0;          /* column rejection threshold, <=0: 1e-14 (FP64) / 1e-6 */
+    int accumulate;       /* hm_matvec: 0 overwrite y, 1 y += H x */
+    int rank_model;       /* 1: size factor storage by the learned rank model */
+    const float* rank_model_theta; /* 4801 FP32 weights (host or device), or NULL */
+    double scratch_gb;    /* bound on ACA scratch per pass, <=0: automatic */
+    void* stream;         /* cudaStream_t, NULL = legacy default stream */
+} hm_options;
+
+typedef struct hm_handle_s* hm_handle;
+
+/* Fill *opt with the defaults above. */
+void hm_options_default(hm_options* opt);
+
+/* Build the H-matrix of A_{phi, Y x Y} (Sec. 5: Morton codes and sort, cluster
+ * tree, block cluster tree by level-synchronous traversal (Alg. 1, Alg. 4),
+ * batched ACA of the admissible leaves (Alg. 2, Sec. 5.4.1), batched
+ * evaluation of the dense leaves (Sec. 5.4.2)).
+ *   points    (N, d) row-major doubles, host or device; copied, may be freed
+ *             on return
+ *   N >= 1, d in {1, 2, 3}, kernel HM_GAUSSIAN | HM_MATERN32
+ *   params    [l, sigma^2] (host)
+ *   leaf_size C_leaf >= 1; eta >= 0 admissibility parameter
+ *   aca_eps   relative Frobenius accuracy of each ACA block; <= 0 selects the
+ *             paper's fixed-rank mode with k = k_cap
+ * Returns NULL on failure (hm_last_error() says why). */
+hm_handle hm_build(const double* points, int64_t N, int d, int kernel,
+                   const double* params, int leaf_size, double eta,
+                   double aca_eps);
+
+/* As hm_build with options; *status (may be NULL) receives the HM_* code. */
+hm_handle hm_build_ex(const double* points, int64_t N, int d, int kernel,
+                      const double* params, int leaf_size, double eta,
+                      double aca_eps, const hm_options* opt, int* status);
+
+/* y = H x + sigma^2 x (Alg. 3, batched: Sec. 5.4), x and y of length N in the
+ * caller's point order, host or device doubles. y is overwritten unless the
+ * handle was built with accumulate = 1. */
+int hm_matvec(hm_handle h, const double* x, double* y);
+
+/* nrhs right-hand sides stored one after another (x[r*N + i]); stream
+ * overrides the handle's stream when not NULL. */
+int hm_matvec_ex(hm_handle h, const double* x, double* y, int nrhs, void* stream);
+
+/* Release everything the handle owns. NULL-safe. */
+void hm_free(hm_handle h);
+
+/* Thread-local description of the last failure ("" if none). */
+const char* hm_last_error(void);
+
+/* Counts, ranks and bytes of a built handle. */
+typedef struct hm_stats {
+    int64_t n_points, n_nodes, n_adm, n_dense, n_tiles;
+    int depth, d;
+    int64_t sum_rank;           /* sum of ACA ranks */
+    int max_rank;
+    int64_t rank_cap_hits;      /* blocks that stopped at the rank cap */
+    int64_t n_rejected;         /* rejected ACA columns, all blocks */
+    int64_t n_mispredicted;     /* rank model: blocks re-run with k_cap */
+    int64_t factor_entries;     /* sum_b k_b (m_b + n_b) */
+    int64_t near_entries;       /* sum over dense leaves m_b n_b */
+    int64_t factor_bytes, near_bytes;
+    int64_t mvp_bytes;          /* algorithmic bytes moved by one product */
+    int64_t reserved_factor_entries; /* storage reserved for the factors */
+    double t_structure_ms, t_aca_ms, t_dense_ms, t_total_ms; /* last build */
+    int aca_passes;             /* scratch passes of the plain ACA */
+    int precision, near_format;
+} hm_stats;
+
+int hm_get_stats(hm_handle h, hm_stats* out);
+
+/* Structure for parity checks (all host arrays, caller-allocated):
+ *   codes[N] (uint64, input order), perm[N] (int64: Morton position ->
+ *   input index), adm[2*n_adm] and dense[2*n_dense] (int64 node-id pairs in
+ *   canonical (tau.lo, sigma.lo) order), ranks[n_adm] (int32). Any may be NULL. */
+int hm_export_structure(hm_handle h, uint64_t* codes, int64_t* perm,
+                        int64_t* adm, int64_t* dense, int32_t* ranks);
+
+/* Cluster-tree node ranges and bounding boxes (host arrays of n_nodes and
+ * n_nodes*d entries; absent nodes have lo = hi = -1). */
+int hm_export_tree(hm_handle h, int64_t* lo, int64_t* hi, double* bbmin,
+                   double* bbmax);
+
+/* Factors of admissible leaf b (canonical index): U (m, k) and V (n, k)
+ * column-major doubles into host arrays of m*k_cap and n*k_cap entries;
+ * *rank receives k. Converted to double in mixed precision. */
+int hm_export_factors(hm_handle h, int64_t b, double* U, double* V, int* rank);
+
+/* Conjugate gradients on (H + sigma^2 I) x = b (Sec. 1, with the H-MVP as
+ * the operator): FP64 inner products and vector updates on the device. x
+ * holds the start vector on entry (host or device). Stops when
+ * ||r_k|| / ||b|| <= rtol or after maxit iterations. */
+int hm_cg(hm_handle h, const double* b, double* x, double rtol, int maxit,
+          int* iters, double* relres);
+
+/* ------------------------------------------------------------------------
+ * Batched form: many independent point sets built and multiplied together
+ * (Sec. 4.2 batching applied across problems). points_all holds the sets one
+ * after another ((sum N_s), d_s per set, row-major), x_all / y_all likewise.
+ * ------------------------------------------------------------------------ */
+typedef struct hm_batch_s* hm_batch;
+
+hm_batch hm_build_batch(int nsets, const double* points_all, const int64_t* N,
+                        const int* d, int kernel, const double* params,
+                        int leaf_size, double eta, double aca_eps,
+                        const hm_options* opt, int* status);
+int hm_matvec_batch(hm_batch b, const double* x_all, double* y_all);
+int hm_batch_stats(hm_batch b, hm_stats* out);
+void hm_free_batch(hm_batch b);
+
+/* ------------------------------------------------------------------------
+ * Learned rank model (not in the paper): MLP 8 -> 64 -> 64 -> 1 with ReLU,
+ * FP32. theta = [W1 (64x8 row-major), b1 (64), W2 (64x64), b2 (64),
+ * W3 (1x64), b3 (1)] = 4801 floats. Features per admissible block:
+ *   f = [d/3, log2|tau|/16, log2|sigma|/16, log2(1+diam_tau/l),
+ *        log2(1+diam_sigma/l), log2(1+dist/l), -log10(eps)/8, kernel]
+ * and the target is log2(1 + ACA rank).
+ * ------------------------------------------------------------------------ */
+#define HM_MLP_NPARAM 4801
+
+/* Features (n_adm x 8 floats) and ranks of a built handle (device or host). */
+int hm_block_features(hm_handle h, float* feats, float* target);
+
+/* out[n] = MLP(F[n x 8]) (device or host pointers). */
+int hm_mlp_forward(const float* theta, const float* F, int64_t n, float* out,
+                   void* stream);
+
+/* Mean squared error of MLP(F) against target and its gradient grad[4801]
+ * (device pointers). *loss may be NULL. */
+int hm_mlp_loss_grad(const float* theta, const float* F, const float* target,
+                     int64_t n, float* grad, float* loss, void* stream);
+
+/* One Adam step (device pointers), step count t >= 1. */
+int hm_mlp_adam(float* theta, const float* grad, float* m, float* v, int64_t t,
+                float lr, float b1, float b2, float eps, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Device helpers exposed for parity tests of the individual build steps.
+ * ------------------------------------------------------------------------ */
+
+/* Morton codes of N points (device in/out). bits per dimension is
+ * min(32, 64/d); the box is the points' global min/max. */
+int hm_morton_codes(const double* points, int64_t N, int d, uint64_t* codes,
+                    void* stream);
+
+/* Stable LSD radix sort of (key, value) pairs on the device, in place,
+ * sorting on the low key_bits bits of the keys. */
+int hm_radix_sort_pairs(uint64_t* keys, uint32_t* values, int64_t n,
+                        int key_bits, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HM_H */

@@ -1,0 +1,288 @@
+// hm_api.cu -- the C-ABI of libhm.so (include/hm.h): handle life cycle, the
+// build pipeline, the product, statistics, exports and conjugate gradients.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "hm_build.cuh"
+#include "hm_handle.cuh"
+
+namespace hm {
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string g_last_error;
+
+void check_cuda(cudaError_t e, const char* what, const char* file, int line)
+{
+    if (e == cudaSuccess) return;
+    std::string msg = std::string(what) + ": " + cudaGetErrorString(e) + " (" + file + ":" +
+                      std::to_string(line) + ")";
+    throw Error(e == cudaErrorMemoryAllocation ? HM_ENOMEM : HM_ECUDA, msg);
+}
+
+void fail(int code, const std::string& msg) { throw Error(code, msg); }
+
+void set_error(const std::string& s) { g_last_error = s; }
+
+int to_status(const std::exception& e)
+{
+    if (auto* he = dynamic_cast<const Error*>(&e)) {
+        set_error(he->what());
+        return he->code;
+    }
+    if (dynamic_cast<const std::bad_alloc*>(&e)) {
+        set_error("host allocation failed");
+        return HM_ENOMEM;
+    }
+    set_error(e.what());
+    return HM_ECUDA;
+}
+
+// ------------------------------------------------------------------ memory
+static bool g_pool_ready = false;
+
+void* dev_alloc(size_t bytes, cudaStream_t s)
+{
+    if (!g_pool_ready) {
+        int dev = 0;
+        HM_CUDA(cudaGetDevice(&dev));
+        cudaMemPool_t pool;
+        HM_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+        uint64_t thr = UINT64_MAX;  // keep freed blocks cached in this process
+        HM_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+        g_pool_ready = true;
+    }
+    void* p = nullptr;
+    cudaError_t e = cudaMallocAsync(&p, bytes, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        fail(HM_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed: " +
+                            cudaGetErrorString(e));
+    }
+    return p;
+}
+
+void dev_free(void* p, cudaStream_t s)
+{
+    if (p) cudaFreeAsync(p, s);
+}
+
+bool is_device_ptr(const void* p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void copy_in(void* dst, const void* src, size_t bytes, cudaStream_t s)
+{
+    if (bytes) HM_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s));
+}
+
+void copy_out(void* dst, const void* src, size_t bytes, cudaStream_t s)
+{
+    if (bytes) HM_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s));
+}
+
+int num_sms()
+{
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        HM_CUDA(cudaGetDevice(&dev));
+        HM_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+    }
+    return n;
+}
+
+KernelParams make_kernel_params(int kernel, double ell)
+{
+    KernelParams k;
+    k.kernel = kernel;
+    k.c64 = (kernel == HM_GAUSSIAN) ? 1.0 / (ell * ell) : std::sqrt(3.0) / ell;
+    k.c32 = (float)k.c64;
+    return k;
+}
+
+}  // namespace hm
+
+using namespace hm;
+
+// ------------------------------------------------------------------ C ABI
+extern "C" {
+
+void hm_options_default(hm_options* o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = HM_PREC_FP64;
+    o->near_format = HM_NEAR_AUTO;
+    o->adm_max = 0;
+    o->k_cap = 64;
+    o->aca_eta = 0.0;
+    o->eps0 = 0.0;
+    o->accumulate = 0;
+    o->rank_model = 0;
+    o->rank_model_theta = nullptr;
+    o->scratch_gb = 0.0;
+    o->stream = nullptr;
+}
+
+const char* hm_last_error(void) { return g_last_error.c_str(); }
+
+hm_handle hm_build_ex(const double* points, int64_t N, int d, int kernel, const double* params,
+                      int leaf_size, double eta, double aca_eps, const hm_options* opt,
+                      int* status)
+{
+    set_error("");
+    try {
+        hm_options o;
+        hm_options_default(&o);
+        if (opt) o = *opt;
+        std::unique_ptr<hm_handle_s> h(new hm_handle_s());
+        int64_t Ns[1] = {N};
+        int ds[1] = {d};
+        build_sets(*h, 1, points, Ns, ds, kernel, params, leaf_size, eta, aca_eps, o);
+        if (status) *status = HM_OK;
+        return h.release();
+    } catch (const std::exception& e) {
+        int st = to_status(e);
+        if (status) *status = st;
+        return nullptr;
+    }
+}
+
+hm_handle hm_build(const double* points, int64_t N, int d, int kernel, const double* params,
+                   int leaf_size, double eta, double aca_eps)
+{
+    return hm_build_ex(points, N, d, kernel, params, leaf_size, eta, aca_eps, nullptr, nullptr);
+}
+
+int hm_matvec_ex(hm_handle h, const double* x, double* y, int nrhs, void* stream)
+{
+    set_error("");
+    try {
+        if (!h) fail(HM_EINVAL, "null handle");
+        if (!x || !y || nrhs < 1) fail(HM_EINVAL, "bad matvec arguments");
+        matvec(*h, x, y, nrhs, stream ? (cudaStream_t)stream : h->stream);
+        return HM_OK;
+    } catch (const std::exception& e) {
+        return to_status(e);
+    }
+}
+
+int hm_matvec(hm_handle h, const double* x, double* y)
+{
+    return hm_matvec_ex(h, x, y, 1, nullptr);
+}
+
+void hm_free(hm_handle h)
+{
+    if (!h) return;
+    try {
+        cudaStream_t s = h->stream;
+        delete h;
+        cudaStreamSynchronize(s);
+    } catch (...) {
+    }
+}
+
+int hm_get_stats(hm_handle h, hm_stats* out)
+{
+    set_error("");
+    if (!h || !out) {
+        set_error("null argument");
+        return HM_EINVAL;
+    }
+    *out = h->stats;
+    return HM_OK;
+}
+
+int hm_export_structure(hm_handle h, uint64_t* codes, int64_t* perm, int64_t* adm,
+                        int64_t* dense, int32_t* ranks)
+{
+    set_error("");
+    try {
+        if (!h) fail(HM_EINVAL, "null handle");
+        export_structure(*h, codes, perm, adm, dense, ranks);
+        return HM_OK;
+    } catch (const std::exception& e) {
+        return to_status(e);
+    }
+}
+
+int hm_export_tree(hm_handle h, int64_t* lo, int64_t* hi, double* bbmin, double* bbmax)
+{
+    set_error("");
+    try {
+        if (!h) fail(HM_EINVAL, "null handle");
+        export_tree(*h, lo, hi, bbmin, bbmax);
+        return HM_OK;
+    } catch (const std::exception& e) {
+        return to_status(e);
+    }
+}
+
+int hm_export_factors(hm_handle h, int64_t b, double* U, double* V, int* rank)
+{
+    set_error("");
+    try {
+        if (!h) fail(HM_EINVAL, "null handle");
+        export_factors(*h, b, U, V, rank);
+        return HM_OK;
+    } catch (const std::exception& e) {
+        return to_status(e);
+    }
+}
+
+int hm_cg(hm_handle h, const double* b, double* x, double rtol, int maxit, int* iters,
+          double* relres)
+{
+    set_error("");
+    try {
+        if (!h || !b || !x) fail(HM_EINVAL, "null argument");
+        if (maxit < 0) fail(HM_EINVAL, "maxit < 0");
+        cg_solve(*h, b, x, rtol, maxit, iters, relres);
+        return HM_OK;
+    } catch (const std::exception& e) {
+        return to_status(e);
+    }
+}
+
+int hm_morton_codes(const double* points, int64_t N, int d, uint64_t* codes, void* stream)
+{
+    set_error("");
+    try {
+        if (!points || !codes || N < 1 || d < 1 || d > 3) fail(HM_EINVAL, "bad arguments");
+        cudaStream_t s = (cudaStream_t)stream;
+        DevBuf<double> box(9, s);
+        morton_codes(points, N, d, codes, nullptr, box.p, s);
+        return HM_OK;
+    } catch (const std::exception& e) {
+        return to_status(e);
+    }
+}
+
+int hm_radix_sort_pairs(uint64_t* keys, uint32_t* values, int64_t n, int key_bits, void* stream)
+{
+    set_error("");
+    try {
+        if (!keys || !values || n < 0 || key_bits < 0 || key_bits > 64)
+            fail(HM_EINVAL, "bad arguments");
+        radix_sort_u64_u32(keys, values, n, key_bits, (cudaStream_t)stream);
+        return HM_OK;
+    } catch (const std::exception& e) {
+        return to_status(e);
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,139 @@
+// hm_build.cuh -- structure builder and the kernels of the compression and
+// product phases (declarations shared by the translation units).
+#pragma once
+
+#include "hm_internal.cuh"
+
+namespace hm {
+
+// Morton-ordered coordinates of all sets: x64[i][row] (double, zero-padded to
+// three dimensions) and, for mixed precision, a hi/lo float split stored as
+// six planes x32[(2i + {0,1}) * stride32 + row].
+struct DeviceCoords {
+    double* x64[3] = {nullptr, nullptr, nullptr};
+    float* x32 = nullptr;
+    int64_t stride32 = 0;
+};
+
+int tree_depth(int64_t N, int C);
+int morton_bits(int d);
+
+// Morton codes (input order) of N points; idx (may be null) receives 0..N-1;
+// box receives lo[3], hi[3], scale[3].
+void morton_codes(const double* pts, int64_t N, int d, uint64_t* codes, uint32_t* idx,
+                  double* box, cudaStream_t s);
+
+// Morton sort, coordinates, cluster tree, boxes, traversal and canonical leaf
+// lists of one point set. pts: device (N, d) row-major. adm / dense receive
+// (tau, sigma) node ids local to the set.
+void build_structure(const double* pts, SetStructure& S, double eta, int adm_max,
+                     const DeviceCoords& X, int64_t* perm_out, uint64_t* codes_out,
+                     int32_t* node_lo, int32_t* node_hi, double* bmin, double* bmax,
+                     DevBuf<int2>& adm, DevBuf<int2>& dense, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Batched ACA (hm_aca.cu)
+// ---------------------------------------------------------------------------
+struct AcaArgs {
+    const Blk* blk;          // per admissible block (absolute Morton rows/cols)
+    const int32_t* kres;     // reserved columns per block
+    const uint64_t* Uptr;    // per block: address of U (m x kres, column-major)
+    const uint64_t* Vptr;    // per block: address of V (n x kres)
+    int32_t* rank;           // out: rank
+    int32_t* nrej;           // out: rejected columns
+    int32_t* flags;          // out: bit0 hit the reserved cap without converging
+    int* status;             // out: device status word (nonzero = loop limit)
+    double eps;              // aca_eps (<= 0: fixed rank)
+    double aca_eta;
+    double eps0;
+    int k_cap;
+};
+
+// Run ACA on the blocks listed in order[0..n) (indices into the block arrays).
+void aca_run(int precision, const KernelParams& kp, const DeviceCoords& X,
+             const AcaArgs& a, const uint32_t* order, int64_t n, int64_t max_dim,
+             cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Near field (hm_near.cu)
+// ---------------------------------------------------------------------------
+// Evaluate the dense leaf blocks into the near-field store in the given format
+// (column-major m x n per block at off[b]; BF16X2 stores hi then lo planes).
+void near_assemble(int near_format, const KernelParams& kp, const DeviceCoords& X,
+                   const Blk* blk, const int64_t* off, int64_t n, void* store,
+                   cudaStream_t s);
+size_t near_entry_bytes(int near_format);
+
+// ---------------------------------------------------------------------------
+// Product (hm_mvp.cu)
+// ---------------------------------------------------------------------------
+struct MvpPlan {
+    int precision = 0, near_format = 0;
+    int64_t Ntot = 0;
+    // admissible blocks
+    int64_t n_adm = 0;
+    const Blk* ablk = nullptr;
+    const int32_t* rank = nullptr;
+    const uint64_t* Uptr = nullptr;
+    const uint64_t* Vptr = nullptr;
+    const int64_t* toff = nullptr;     // offset of t_b in the t buffer
+    int64_t t_len = 0;
+    // V^T x work items: (block, column chunk)
+    int64_t n_vitems = 0;
+    const int2* vitems = nullptr;       // (block, chunk start)
+    const int64_t* tpart_off = nullptr; // per work item: partial-sum slot
+    int64_t tpart_len = 0;
+    const int32_t* tsum_first = nullptr;  // per block: first work item
+    const int32_t* tsum_count = nullptr;  // per block: work items
+    int64_t n_multi = 0;                   // blocks with more than one item
+    const int32_t* multi = nullptr;        // their ids
+    // dense blocks
+    int64_t n_dense = 0;
+    const Blk* dblk = nullptr;
+    const int64_t* doff = nullptr;
+    const void* near = nullptr;
+    int64_t near_entries = 0;
+    // row tiles and their gather lists
+    int64_t n_tiles = 0;
+    const int64_t* tile_row0 = nullptr;
+    const int32_t* tile_m = nullptr;
+    const int64_t* lr_ptr = nullptr;    // CSR over tiles
+    const int2* lr_ent = nullptr;       // (block, row offset)
+    const int64_t* dn_ptr = nullptr;
+    const int2* dn_ent = nullptr;
+    int max_tile = 0;
+    // permutation and diagonal shift
+    const int64_t* perm = nullptr;      // Morton row -> caller index (absolute)
+    double sigma2 = 0.0;
+    const double* sig_row = nullptr;    // optional per-row sigma^2 (batched sets)
+};
+
+// Work buffers of the product (xm, t, partial sums).
+struct MvpWork {
+    DevBuf<double> xm64, ym64;
+    DevBuf<float> xm32;
+    DevBuf<double> t64, tp64;
+    DevBuf<float> t32, tp32;
+};
+
+void mvp_alloc_work(const MvpPlan& P, MvpWork& W, cudaStream_t s);
+// y = H x (+ sigma^2 x) for device x, y in the caller's order.
+void mvp_run(const MvpPlan& P, MvpWork& W, const double* x, double* y, int accumulate,
+             cudaStream_t s);
+// Build the gather lists of the plan (CSR by tile).
+struct MvpLists {
+    DevBuf<int64_t> tile_row0;
+    DevBuf<int32_t> tile_m;
+    DevBuf<int64_t> lr_ptr, dn_ptr;
+    DevBuf<int2> lr_ent, dn_ent;
+    DevBuf<int2> vitems;
+    DevBuf<int64_t> tpart_off, toff;
+    DevBuf<int32_t> tsum_first, tsum_count, multi;
+    int64_t n_tiles = 0, n_vitems = 0, tpart_len = 0, t_len = 0, n_multi = 0;
+    int max_tile = 0;
+};
+void mvp_build_lists(const Blk* ablk, const int32_t* rank, int64_t n_adm, const Blk* dblk,
+                     int64_t n_dense, const int64_t* leaf_row0, const int32_t* leaf_m,
+                     int64_t n_tiles, MvpLists& L, cudaStream_t s);
+
+}  // namespace hm

@@ -1,0 +1,86 @@
+// hm_handle.cuh -- the handle behind hm_handle / hm_batch and the pipeline
+// functions that the C-ABI entry points call.
+#pragma once
+
+#include <memory>
+#include <vector>
+
+#include "hm_build.cuh"
+
+namespace hm {
+
+struct FactorSegment {
+    DevBuf<char> mem;
+};
+
+}  // namespace hm
+
+struct hm_handle_s {
+    hm_options opt{};
+    int kernel = 0, leaf = 0, precision = 0, near_format = 0;
+    double ell = 1.0, sigma2 = 0.0, eta = 0.0, aca_eps = 0.0;
+    cudaStream_t stream = 0;
+    hm::KernelParams kp{};
+    std::vector<hm::SetStructure> sets;
+    int64_t Ntot = 0, n_nodes_tot = 0, n_adm = 0, n_dense = 0, n_tiles = 0;
+    int64_t max_set_n = 0;
+    // points and structure
+    hm::DevBuf<double> X64;
+    hm::DevBuf<float> X32;
+    hm::DeviceCoords X;
+    hm::DevBuf<int64_t> perm;
+    hm::DevBuf<uint64_t> codes;
+    hm::DevBuf<int32_t> node_lo, node_hi;
+    hm::DevBuf<double> bmin, bmax;
+    hm::DevBuf<int2> adm_pairs, dense_pairs;   // set-local node ids, canonical order
+    hm::DevBuf<int32_t> adm_set, dense_set;     // owning set of each leaf
+    hm::DevBuf<hm::Blk> ablk, dblk;
+    hm::DevBuf<int64_t> tile_row0;
+    hm::DevBuf<int32_t> tile_m;
+    // factors
+    hm::DevBuf<int32_t> kres, rank, nrej, flags;
+    hm::DevBuf<uint64_t> Uptr, Vptr;
+    std::vector<std::unique_ptr<hm::FactorSegment>> segments;
+    // near field
+    hm::DevBuf<int64_t> doff;
+    hm::DevBuf<char> near;
+    // product
+    hm::MvpLists lists;
+    hm::MvpPlan plan;
+    hm::MvpWork work;
+    hm::DevBuf<double> xbuf, ybuf;
+    hm::DevBuf<int> status;
+    hm_stats stats{};
+    ~hm_handle_s();
+};
+
+struct hm_batch_s {
+    hm_handle_s h;
+    std::vector<int64_t> set_n;
+    std::vector<int> set_d;
+};
+
+namespace hm {
+
+void set_error(const std::string& s);
+int to_status(const std::exception& e);
+
+void build_sets(hm_handle_s& h, int nsets, const double* points_all, const int64_t* N,
+                const int* d, int kernel, const double* params, int leaf, double eta,
+                double aca_eps, const hm_options& opt);
+void matvec(hm_handle_s& h, const double* x, double* y, int nrhs, cudaStream_t s);
+void export_structure(hm_handle_s& h, uint64_t* codes, int64_t* perm, int64_t* adm,
+                      int64_t* dense, int32_t* ranks);
+void export_tree(hm_handle_s& h, int64_t* lo, int64_t* hi, double* bbmin, double* bbmax);
+void export_factors(hm_handle_s& h, int64_t b, double* U, double* V, int* rank);
+void add_perm_offsets(hm_handle_s& h);
+void fill_block_sets(hm_handle_s& h);
+void alloc_factor_meta(hm_handle_s& h);
+void compress(hm_handle_s& h, const uint32_t* ids, int64_t n, const int32_t* kpred);
+// learned rank model (hm_mlp.cu)
+void predict_ranks(hm_handle_s& h, int32_t* kpred);
+void rerun_mispredicted(hm_handle_s& h);
+void cg_solve(hm_handle_s& h, const double* b, double* x, double rtol, int maxit, int* iters,
+              double* relres);
+
+}  // namespace hm

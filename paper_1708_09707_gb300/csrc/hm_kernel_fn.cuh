@@ -1,0 +1,143 @@
+// hm_kernel_fn.cuh -- kernel functions phi(y, y') on Morton-ordered points.
+//   Gaussian:    exp(-D2 * c),        c = 1 / l^2
+//   Matern-3/2:  (1 + s) exp(-s),     s = sqrt(D2) * c,  c = sqrt(3) / l
+// (Sec. 6.2 model problem; l and the Matern order are the workloads' choice.)
+// The double path loads double coordinates. The float path loads a hi/lo
+// float split of every coordinate and forms each difference as
+// (hi_a - hi_b) + (lo_a - lo_b), which keeps the difference accurate to about
+// float precision relative to itself even when the points are far from the
+// origin of the unit cube.
+#pragma once
+
+#include "hm_build.cuh"
+
+namespace hm {
+
+template <class R>
+struct Pt;
+
+template <>
+struct Pt<double> {
+    double x[3];
+};
+
+template <>
+struct Pt<float> {
+    float h[3], l[3];
+};
+
+__device__ __forceinline__ Pt<double> load_pt64(const DeviceCoords& X, int64_t row)
+{
+    Pt<double> p;
+    p.x[0] = X.x64[0][row];
+    p.x[1] = X.x64[1][row];
+    p.x[2] = X.x64[2][row];
+    return p;
+}
+
+__device__ __forceinline__ Pt<float> load_pt32(const DeviceCoords& X, int64_t row)
+{
+    Pt<float> p;
+    const float* F = X.x32;
+    const int64_t st = X.stride32;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        p.h[i] = F[(2 * i) * st + row];
+        p.l[i] = F[(2 * i + 1) * st + row];
+    }
+    return p;
+}
+
+template <class R>
+__device__ __forceinline__ Pt<R> load_pt(const DeviceCoords& X, int64_t row);
+
+template <>
+__device__ __forceinline__ Pt<double> load_pt<double>(const DeviceCoords& X, int64_t row)
+{
+    return load_pt64(X, row);
+}
+
+template <>
+__device__ __forceinline__ Pt<float> load_pt<float>(const DeviceCoords& X, int64_t row)
+{
+    return load_pt32(X, row);
+}
+
+__device__ __forceinline__ double dist2(const Pt<double>& a, const Pt<double>& b)
+{
+    double t0 = a.x[0] - b.x[0], t1 = a.x[1] - b.x[1], t2 = a.x[2] - b.x[2];
+    return fma(t2, t2, fma(t1, t1, t0 * t0));
+}
+
+__device__ __forceinline__ float dist2(const Pt<float>& a, const Pt<float>& b)
+{
+    float t0 = (a.h[0] - b.h[0]) + (a.l[0] - b.l[0]);
+    float t1 = (a.h[1] - b.h[1]) + (a.l[1] - b.l[1]);
+    float t2 = (a.h[2] - b.h[2]) + (a.l[2] - b.l[2]);
+    return fmaf(t2, t2, fmaf(t1, t1, t0 * t0));
+}
+
+template <int KERN>
+__device__ __forceinline__ double phi(double D2, double c)
+{
+    if (KERN == HM_GAUSSIAN) return exp(-(D2 * c));
+    double s = sqrt(D2) * c;
+    return (1.0 + s) * exp(-s);
+}
+
+template <int KERN>
+__device__ __forceinline__ float phi(float D2, float c)
+{
+    if (KERN == HM_GAUSSIAN) return expf(-(D2 * c));
+    float s = sqrtf(D2) * c;
+    return (1.0f + s) * expf(-s);
+}
+
+template <class R>
+__host__ __device__ __forceinline__ R kconst(const KernelParams& kp);
+
+template <>
+__host__ __device__ __forceinline__ double kconst<double>(const KernelParams& kp)
+{
+    return kp.c64;
+}
+
+template <>
+__host__ __device__ __forceinline__ float kconst<float>(const KernelParams& kp)
+{
+    return kp.c32;
+}
+
+// Warp-wide helpers.
+template <class T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <class T>
+__device__ __forceinline__ T warp_max(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// argmax of (val, idx) with ties to the lower index.
+template <class T>
+__device__ __forceinline__ void warp_argmax(T& val, int& idx)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        T ov = __shfl_xor_sync(0xffffffffu, val, o);
+        int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+        if (ov > val || (ov == val && oi < idx)) {
+            val = ov;
+            idx = oi;
+        }
+    }
+}
+
+}  // namespace hm

@@ -1,0 +1,687 @@
+// hm_pipeline.cu -- the build pipeline behind hm_build / hm_build_batch, the
+// product driver, exports and conjugate gradients.
+//
+// Build (Sec. 5): per point set, Morton sort + cluster tree + traversal
+// (hm_build.cu); then, over the leaves of all sets at once, block descriptors,
+// batched ACA of the admissible leaves (hm_aca.cu), batched evaluation of the
+// dense leaves (hm_near.cu) and the gather lists of the product (hm_mvp.cu).
+//
+// Factor storage. The plain method does not know the ranks before ACA runs,
+// so blocks are compressed in passes: each pass reserves min(k_cap, m, n)
+// columns per block in a bounded scratch area, runs ACA, then copies the
+// rank-k columns into an exactly sized segment. With the learned rank model,
+// every block reserves its predicted rank directly in the final store (one
+// pass, no copy) and only blocks whose prediction was too small are re-run
+// with the full cap.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "hm_handle.cuh"
+#include "hm_mlp.cuh"
+
+hm_handle_s::~hm_handle_s()
+{
+    if (stream) cudaStreamSynchronize(stream);
+}
+
+namespace hm {
+
+namespace {
+
+constexpr int NT = 256;
+inline unsigned grid_for(int64_t n) { return (unsigned)ceil_div(n, NT); }
+
+int bits_for(int64_t n)
+{
+    int b = 0;
+    while ((1ll << b) < n) ++b;
+    return b;
+}
+
+__global__ void k_make_blk(const int2* __restrict__ pairs, int64_t n,
+                           const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
+                           int64_t row0, Blk* __restrict__ out)
+{
+    int64_t b = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (b >= n) return;
+    int2 p = pairs[b];
+    Blk B;
+    B.row0 = row0 + lo[p.x];
+    B.col0 = row0 + lo[p.y];
+    B.m = hi[p.x] - lo[p.x];
+    B.n = hi[p.y] - lo[p.y];
+    out[b] = B;
+}
+
+__global__ void k_leaf_flags(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
+                             int64_t nn, int C, int64_t* __restrict__ flag)
+{
+    int64_t v = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (v >= nn) return;
+    flag[v] = (lo[v] >= 0 && hi[v] - lo[v] <= C) ? 1 : 0;
+}
+
+__global__ void k_leaf_emit(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
+                            int64_t nn, const int64_t* __restrict__ flag,
+                            const int64_t* __restrict__ off, uint64_t* __restrict__ key,
+                            uint32_t* __restrict__ val, int32_t* __restrict__ vid)
+{
+    int64_t v = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (v >= nn || !flag[v]) return;
+    int64_t o = off[v];
+    key[o] = (uint64_t)lo[v];
+    val[o] = (uint32_t)o;
+    vid[o] = (int32_t)v;
+}
+
+__global__ void k_leaf_tiles(const uint32_t* __restrict__ val, const int32_t* __restrict__ vid,
+                             int64_t nt, const int32_t* __restrict__ lo,
+                             const int32_t* __restrict__ hi, int64_t row0,
+                             int64_t* __restrict__ trow, int32_t* __restrict__ tm)
+{
+    int64_t q = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (q >= nt) return;
+    int v = vid[val[q]];
+    trow[q] = row0 + lo[v];
+    tm[q] = hi[v] - lo[v];
+}
+
+// size class of an admissible block: 0..3 warp kernels, 4 CTA kernel
+__device__ __forceinline__ int size_class(int m, int n)
+{
+    int d = max(m, n);
+    return d <= 64 ? 0 : d <= 128 ? 1 : d <= 256 ? 2 : d <= 512 ? 3 : 4;
+}
+
+__global__ void k_classes(const Blk* __restrict__ blk, const uint32_t* __restrict__ ids,
+                          int64_t n, int kcap, const int32_t* __restrict__ kpred,
+                          uint64_t* __restrict__ key, uint32_t* __restrict__ val,
+                          int32_t* __restrict__ kres, int64_t* __restrict__ cls_count)
+{
+    int64_t q = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (q >= n) return;
+    const uint32_t b = ids ? ids[q] : (uint32_t)q;
+    Blk B = blk[b];
+    int c = size_class(B.m, B.n);
+    key[q] = (uint64_t)(4 - c);   // largest class first
+    val[q] = b;
+    int full = min(kcap, min(B.m, B.n));
+    kres[b] = kpred ? max(1, min(kpred[b], full)) : full;
+    atomicAdd((unsigned long long*)&cls_count[c], 1ull);
+}
+
+__global__ void k_reserve(const Blk* __restrict__ blk, const uint32_t* __restrict__ order,
+                          int64_t n, const int32_t* __restrict__ kres, int64_t* __restrict__ res)
+{
+    int64_t q = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (q >= n) return;
+    uint32_t b = order[q];
+    res[q] = (int64_t)kres[b] * (blk[b].m + blk[b].n);
+}
+
+__global__ void k_set_ptrs(const Blk* __restrict__ blk, const uint32_t* __restrict__ order,
+                           int64_t q0, int64_t q1, const int64_t* __restrict__ pre,
+                           const int32_t* __restrict__ kres, char* base, int esz,
+                           uint64_t* __restrict__ Uptr, uint64_t* __restrict__ Vptr)
+{
+    int64_t q = q0 + (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (q >= q1) return;
+    uint32_t b = order[q];
+    char* u = base + (pre[q] - pre[q0]) * esz;
+    Uptr[b] = (uint64_t)u;
+    Vptr[b] = (uint64_t)(u + (int64_t)kres[b] * blk[b].m * esz);
+}
+
+__global__ void k_final_size(const Blk* __restrict__ blk, const uint32_t* __restrict__ order,
+                             int64_t q0, int64_t q1, const int32_t* __restrict__ rank,
+                             int64_t* __restrict__ fs)
+{
+    int64_t q = q0 + (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (q >= q1) return;
+    uint32_t b = order[q];
+    fs[q - q0] = (int64_t)rank[b] * (blk[b].m + blk[b].n);
+}
+
+// Copy the rank-k columns of U and V (contiguous prefixes of the column-major
+// scratch) into the final segment; one warp per block.
+__global__ void k_copy_factors(const Blk* __restrict__ blk, const uint32_t* __restrict__ order,
+                               int64_t q0, int64_t q1, const int32_t* __restrict__ rank,
+                               const int64_t* __restrict__ foff, char* base, int esz,
+                               uint64_t* __restrict__ Uptr, uint64_t* __restrict__ Vptr)
+{
+    int64_t w = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    int64_t q = q0 + w;
+    if (q >= q1) return;
+    uint32_t b = order[q];
+    const Blk B = blk[b];
+    const int r = rank[b];
+    char* dst = base + foff[w] * esz;
+    const int64_t nu = (int64_t)r * B.m * esz, nv = (int64_t)r * B.n * esz;
+    const char* su = reinterpret_cast<const char*>(Uptr[b]);
+    const char* sv = reinterpret_cast<const char*>(Vptr[b]);
+    // element-size words (4 or 8 bytes): both sources and dst are aligned
+    if (esz == 8) {
+        const double* a = reinterpret_cast<const double*>(su);
+        const double* c = reinterpret_cast<const double*>(sv);
+        double* o = reinterpret_cast<double*>(dst);
+        for (int64_t e = lane; e < nu / 8; e += 32) o[e] = a[e];
+        for (int64_t e = lane; e < nv / 8; e += 32) o[nu / 8 + e] = c[e];
+    } else {
+        const float* a = reinterpret_cast<const float*>(su);
+        const float* c = reinterpret_cast<const float*>(sv);
+        float* o = reinterpret_cast<float*>(dst);
+        for (int64_t e = lane; e < nu / 4; e += 32) o[e] = a[e];
+        for (int64_t e = lane; e < nv / 4; e += 32) o[nu / 4 + e] = c[e];
+    }
+    __syncwarp();
+    if (lane == 0) {
+        Uptr[b] = (uint64_t)dst;
+        Vptr[b] = (uint64_t)(dst + nu);
+    }
+}
+
+__global__ void k_near_size(const Blk* __restrict__ blk, int64_t n, int64_t* __restrict__ sz)
+{
+    int64_t b = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (b < n) sz[b] = (int64_t)blk[b].m * blk[b].n;
+}
+
+// Statistics of the factors: [sum rank, max rank, cap hits, mispredicted,
+// rejected, factor entries, reserved entries]
+__global__ void k_rank_stats(const Blk* __restrict__ blk, const int32_t* __restrict__ rank,
+                             const int32_t* __restrict__ nrej, const int32_t* __restrict__ flags,
+                             const int32_t* __restrict__ kres, int64_t n,
+                             unsigned long long* __restrict__ out)
+{
+    int64_t b = (int64_t)blockIdx.x * NT + threadIdx.x;
+    unsigned long long s[7] = {0, 0, 0, 0, 0, 0, 0};
+    if (b < n) {
+        int r = rank[b];
+        s[0] = r;
+        s[1] = r;
+        s[2] = (flags[b] & 2) ? 1 : 0;
+        s[3] = (flags[b] & 1) ? 1 : 0;
+        s[4] = nrej[b];
+        s[5] = (unsigned long long)r * (blk[b].m + blk[b].n);
+        s[6] = (unsigned long long)kres[b] * (blk[b].m + blk[b].n);
+    }
+    for (int o = 16; o > 0; o >>= 1)
+        for (int k = 0; k < 7; ++k) {
+            unsigned long long v = __shfl_xor_sync(0xffffffffu, s[k], o);
+            s[k] = (k == 1) ? max(s[k], v) : s[k] + v;
+        }
+    if ((threadIdx.x & 31) == 0) {
+        for (int k = 0; k < 7; ++k)
+            if (k == 1) atomicMax(&out[1], s[1]);
+            else atomicAdd(&out[k], s[k]);
+    }
+}
+
+struct Timer {
+    cudaEvent_t a, b;
+    cudaStream_t s;
+    explicit Timer(cudaStream_t st) : s(st)
+    {
+        HM_CUDA(cudaEventCreate(&a));
+        HM_CUDA(cudaEventCreate(&b));
+        HM_CUDA(cudaEventRecord(a, s));
+    }
+    double stop_ms()
+    {
+        HM_CUDA(cudaEventRecord(b, s));
+        HM_CUDA(cudaEventSynchronize(b));
+        float ms = 0.f;
+        HM_CUDA(cudaEventElapsedTime(&ms, a, b));
+        return ms;
+    }
+    ~Timer()
+    {
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+    }
+};
+
+void check_status(hm_handle_s& h)
+{
+    int st = 0;
+    HM_CUDA(cudaMemcpyAsync(&st, h.status.p, sizeof(int), cudaMemcpyDeviceToHost, h.stream));
+    HM_CUDA(cudaStreamSynchronize(h.stream));
+    if (st) fail(HM_ETIMEOUT, "a device loop reached its iteration limit");
+}
+
+}  // namespace
+
+void alloc_factor_meta(hm_handle_s& h)
+{
+    cudaStream_t s = h.stream;
+    const int64_t n = std::max<int64_t>(h.n_adm, 1);
+    h.kres.alloc(n, s);
+    h.rank.alloc(n, s);
+    h.nrej.alloc(n, s);
+    h.flags.alloc(n, s);
+    h.Uptr.alloc(n, s);
+    h.Vptr.alloc(n, s);
+    HM_CUDA(cudaMemsetAsync(h.flags.p, 0, n * sizeof(int32_t), s));
+    HM_CUDA(cudaMemsetAsync(h.rank.p, 0, n * sizeof(int32_t), s));
+    HM_CUDA(cudaMemsetAsync(h.nrej.p, 0, n * sizeof(int32_t), s));
+}
+
+// ACA of the admissible blocks ids[0..n) (all blocks when ids is null); see
+// the file comment for the two storage modes (kpred != null: learned sizing,
+// one arena; else bounded scratch passes with exact final segments).
+void compress(hm_handle_s& h, const uint32_t* ids, int64_t n, const int32_t* kpred)
+{
+    cudaStream_t s = h.stream;
+    const int esz = h.precision == HM_PREC_FP64 ? 8 : 4;
+    if (n == 0) return;
+
+    DevBuf<uint64_t> key(n, s);
+    DevBuf<uint32_t> order(n, s);
+    DevBuf<int64_t> ccount(5, s);
+    HM_CUDA(cudaMemsetAsync(ccount.p, 0, 5 * sizeof(int64_t), s));
+    k_classes<<<grid_for(n), NT, 0, s>>>(h.ablk.p, ids, n, h.opt.k_cap, kpred, key.p, order.p,
+                                         h.kres.p, ccount.p);
+    HM_LAUNCH("classes");
+    radix_sort_u64_u32(key.p, order.p, n, 3, s);
+    int64_t cc[5];
+    HM_CUDA(cudaMemcpyAsync(cc, ccount.p, sizeof(cc), cudaMemcpyDeviceToHost, s));
+    DevBuf<int64_t> res(n, s), pre(n + 1, s);
+    k_reserve<<<grid_for(n), NT, 0, s>>>(h.ablk.p, order.p, n, h.kres.p, res.p);
+    scan_exclusive_i64(res.p, pre.p, n, pre.p + n, s);
+    std::vector<int64_t> hpre(n + 1);
+    HM_CUDA(cudaMemcpyAsync(hpre.data(), pre.p, (n + 1) * sizeof(int64_t),
+                            cudaMemcpyDeviceToHost, s));
+    HM_CUDA(cudaStreamSynchronize(s));
+    // class ranges in the sorted order: class 4 first
+    int64_t cstart[5], cend[5];
+    {
+        int64_t q = 0;
+        for (int c = 4; c >= 0; --c) {
+            cstart[c] = q;
+            q += cc[c];
+            cend[c] = q;
+        }
+    }
+    const int64_t cls_dim[5] = {64, 128, 256, 512, h.max_set_n};
+    AcaArgs a;
+    a.blk = h.ablk.p;
+    a.kres = h.kres.p;
+    a.Uptr = h.Uptr.p;
+    a.Vptr = h.Vptr.p;
+    a.rank = h.rank.p;
+    a.nrej = h.nrej.p;
+    a.flags = h.flags.p;
+    a.status = h.status.p;
+    a.eps = h.aca_eps;
+    a.aca_eta = h.opt.aca_eta;
+    a.eps0 = h.opt.eps0 > 0 ? h.opt.eps0 : (h.precision == HM_PREC_FP64 ? 1e-14 : 1e-6);
+    a.k_cap = h.opt.k_cap;
+
+    auto run_range = [&](int64_t q0, int64_t q1) {
+        for (int c = 4; c >= 0; --c) {
+            int64_t lo = std::max(q0, cstart[c]), hi = std::min(q1, cend[c]);
+            if (hi > lo) aca_run(h.precision, h.kp, h.X, a, order.p + lo, hi - lo, cls_dim[c], s);
+        }
+    };
+
+    if (kpred) {
+        // learned sizing: reserve the predicted ranks directly in the final store
+        auto seg = std::make_unique<FactorSegment>();
+        seg->mem.alloc((size_t)hpre[n] * esz, s);
+        k_set_ptrs<<<grid_for(n), NT, 0, s>>>(h.ablk.p, order.p, 0, n, pre.p, h.kres.p,
+                                               seg->mem.p, esz, h.Uptr.p, h.Vptr.p);
+        HM_LAUNCH("set ptrs");
+        h.segments.push_back(std::move(seg));
+        run_range(0, n);
+        h.stats.aca_passes += 1;
+        return;
+    }
+
+    size_t freeb = 0, totb = 0;
+    HM_CUDA(cudaMemGetInfo(&freeb, &totb));
+    int64_t cap = h.opt.scratch_gb > 0 ? (int64_t)(h.opt.scratch_gb * 1e9 / esz)
+                                       : (int64_t)(0.30 * (double)freeb / esz);
+    cap = std::max<int64_t>(cap, 1);
+    int64_t maxres = 0;
+    for (int64_t q = 0; q < n; ++q) maxres = std::max(maxres, hpre[q + 1] - hpre[q]);
+    cap = std::max(cap, maxres);
+    cap = std::min(cap, hpre[n]);
+    DevBuf<char> scratch((size_t)cap * esz, s);
+    int passes = 0;
+    for (int64_t q0 = 0; q0 < n;) {
+        // largest q1 with hpre[q1] - hpre[q0] <= cap
+        int64_t q1 = std::upper_bound(hpre.begin() + q0 + 1, hpre.end(), hpre[q0] + cap) -
+                     hpre.begin() - 1;
+        q1 = std::max(q1, q0 + 1);
+        k_set_ptrs<<<grid_for(q1 - q0), NT, 0, s>>>(h.ablk.p, order.p, q0, q1, pre.p, h.kres.p,
+                                                     scratch.p, esz, h.Uptr.p, h.Vptr.p);
+        HM_LAUNCH("set ptrs");
+        run_range(q0, q1);
+        DevBuf<int64_t> fs(q1 - q0, s), foff(q1 - q0 + 1, s);
+        k_final_size<<<grid_for(q1 - q0), NT, 0, s>>>(h.ablk.p, order.p, q0, q1, h.rank.p, fs.p);
+        scan_exclusive_i64(fs.p, foff.p, q1 - q0, foff.p + (q1 - q0), s);
+        int64_t tot = 0;
+        HM_CUDA(cudaMemcpyAsync(&tot, foff.p + (q1 - q0), sizeof(int64_t),
+                                cudaMemcpyDeviceToHost, s));
+        HM_CUDA(cudaStreamSynchronize(s));
+        auto seg = std::make_unique<FactorSegment>();
+        seg->mem.alloc((size_t)std::max<int64_t>(tot, 1) * esz, s);
+        k_copy_factors<<<(unsigned)ceil_div((q1 - q0) * 32, NT), NT, 0, s>>>(
+            h.ablk.p, order.p, q0, q1, h.rank.p, foff.p, seg->mem.p, esz, h.Uptr.p, h.Vptr.p);
+        HM_LAUNCH("copy factors");
+        h.segments.push_back(std::move(seg));
+        ++passes;
+        q0 = q1;
+    }
+    h.stats.aca_passes += passes;
+}
+
+namespace {
+
+void rank_stats(hm_handle_s& h)
+{
+    cudaStream_t s = h.stream;
+    DevBuf<unsigned long long> out(7, s);
+    HM_CUDA(cudaMemsetAsync(out.p, 0, 7 * sizeof(unsigned long long), s));
+    if (h.n_adm > 0)
+        k_rank_stats<<<grid_for(h.n_adm), NT, 0, s>>>(h.ablk.p, h.rank.p, h.nrej.p, h.flags.p,
+                                                     h.kres.p, h.n_adm, out.p);
+    unsigned long long o[7];
+    HM_CUDA(cudaMemcpyAsync(o, out.p, sizeof(o), cudaMemcpyDeviceToHost, s));
+    HM_CUDA(cudaStreamSynchronize(s));
+    h.stats.sum_rank = (int64_t)o[0];
+    h.stats.max_rank = (int)o[1];
+    h.stats.rank_cap_hits = (int64_t)o[2];
+    h.stats.n_rejected = (int64_t)o[4];
+    h.stats.factor_entries = (int64_t)o[5];
+    h.stats.reserved_factor_entries = (int64_t)o[6];
+}
+
+void validate(int nsets, const int64_t* N, const int* d, int kernel, const double* params,
+              int leaf, double eta, const hm_options& o)
+{
+    if (nsets < 1) fail(HM_EINVAL, "no point sets");
+    if (!params) fail(HM_EINVAL, "params is NULL");
+    if (kernel != HM_GAUSSIAN && kernel != HM_MATERN32) fail(HM_EINVAL, "unknown kernel");
+    if (!(params[0] > 0.0) || !std::isfinite(params[0])) fail(HM_EINVAL, "length scale must be > 0");
+    if (!(params[1] >= 0.0) || !std::isfinite(params[1])) fail(HM_EINVAL, "sigma^2 must be >= 0");
+    if (leaf < 1) fail(HM_EINVAL, "leaf_size must be >= 1");
+    if (!(eta >= 0.0) || !std::isfinite(eta)) fail(HM_EINVAL, "eta must be >= 0");
+    if (o.k_cap < 1 || o.k_cap > 128) fail(HM_EINVAL, "k_cap must be in [1, 128]");
+    if (o.precision != HM_PREC_FP64 && o.precision != HM_PREC_MIXED)
+        fail(HM_EINVAL, "unknown precision");
+    if (o.near_format < 0 || o.near_format > HM_NEAR_BF16) fail(HM_EINVAL, "unknown near format");
+    if (o.precision == HM_PREC_FP64 && o.near_format != HM_NEAR_AUTO &&
+        o.near_format != HM_NEAR_FP64)
+        fail(HM_ENOTSUP, "the FP64 path stores the near field in FP64");
+    int64_t tot = 0;
+    for (int q = 0; q < nsets; ++q) {
+        if (N[q] < 1) fail(HM_EINVAL, "N must be >= 1");
+        if (d[q] < 1 || d[q] > 3) fail(HM_EINVAL, "d must be 1, 2 or 3");
+        tot += N[q];
+    }
+    if (tot >= (1ll << 31)) fail(HM_EINVAL, "more than 2^31 points");
+}
+
+}  // namespace
+
+void build_sets(hm_handle_s& h, int nsets, const double* points_all, const int64_t* N,
+                const int* d, int kernel, const double* params, int leaf, double eta,
+                double aca_eps, const hm_options& opt)
+{
+    validate(nsets, N, d, kernel, params, leaf, eta, opt);
+    if (!points_all) fail(HM_EINVAL, "points is NULL");
+    auto t0 = std::chrono::steady_clock::now();
+    h.opt = opt;
+    h.kernel = kernel;
+    h.ell = params[0];
+    h.sigma2 = params[1];
+    h.leaf = leaf;
+    h.eta = eta;
+    h.aca_eps = aca_eps;
+    h.precision = opt.precision;
+    h.near_format = opt.near_format == HM_NEAR_AUTO
+                        ? (opt.precision == HM_PREC_FP64 ? HM_NEAR_FP64 : HM_NEAR_BF16X2)
+                        : opt.near_format;
+    h.stream = (cudaStream_t)opt.stream;
+    h.kp = make_kernel_params(kernel, h.ell);
+    cudaStream_t s = h.stream;
+    h.status.alloc(1, s);
+    HM_CUDA(cudaMemsetAsync(h.status.p, 0, sizeof(int), s));
+
+    // sets, offsets, sizes
+    int64_t Ntot = 0, nn = 0, nval = 0;
+    h.sets.resize(nsets);
+    for (int q = 0; q < nsets; ++q) {
+        SetStructure& S = h.sets[q];
+        S.N = N[q];
+        S.d = d[q];
+        S.C = leaf;
+        S.depth = tree_depth(S.N, leaf);
+        S.n_nodes = (2ll << S.depth) - 1;
+        S.row0 = Ntot;
+        S.node0 = nn;
+        Ntot += S.N;
+        nn += S.n_nodes;
+        nval += S.N * S.d;
+        h.max_set_n = std::max(h.max_set_n, S.N);
+    }
+    h.Ntot = Ntot;
+    h.n_nodes_tot = nn;
+
+    Timer tstruct(s);
+    // points on the device
+    DevBuf<double> pts_dev;
+    const double* pts = points_all;
+    if (!is_device_ptr(points_all)) {
+        pts_dev.alloc(nval, s);
+        copy_in(pts_dev.p, points_all, nval * sizeof(double), s);
+        pts = pts_dev.p;
+    }
+    h.X64.alloc(3 * Ntot, s);
+    h.X.x64[0] = h.X64.p;
+    h.X.x64[1] = h.X64.p + Ntot;
+    h.X.x64[2] = h.X64.p + 2 * Ntot;
+    if (h.precision == HM_PREC_MIXED) {
+        h.X32.alloc(6 * Ntot, s);
+        h.X.x32 = h.X32.p;
+        h.X.stride32 = Ntot;
+    }
+    h.perm.alloc(Ntot, s);
+    h.codes.alloc(Ntot, s);
+    h.node_lo.alloc(nn, s);
+    h.node_hi.alloc(nn, s);
+    h.bmin.alloc(3 * nn, s);
+    h.bmax.alloc(3 * nn, s);
+
+    std::vector<DevBuf<int2>> adm(nsets), dense(nsets);
+    const double* p = pts;
+    for (int q = 0; q < nsets; ++q) {
+        SetStructure& S = h.sets[q];
+        build_structure(p, S, eta, opt.adm_max, h.X, h.perm.p, h.codes.p + S.row0, h.node_lo.p,
+                        h.node_hi.p, h.bmin.p, h.bmax.p, adm[q], dense[q], s);
+        p += S.N * S.d;
+        h.n_adm += S.n_adm;
+        h.n_dense += S.n_dense;
+    }
+    // perm holds set-local indices; make them absolute for the product
+    // (the offsets are applied below by a small kernel per set)
+    h.adm_pairs.alloc(std::max<int64_t>(h.n_adm, 1), s);
+    h.dense_pairs.alloc(std::max<int64_t>(h.n_dense, 1), s);
+    h.ablk.alloc(std::max<int64_t>(h.n_adm, 1), s);
+    h.dblk.alloc(std::max<int64_t>(h.n_dense, 1), s);
+    std::vector<DevBuf<int64_t>> trow(nsets);
+    std::vector<DevBuf<int32_t>> tm(nsets);
+    std::vector<int64_t> ntile(nsets);
+    {
+        int64_t ao = 0, dof = 0;
+        for (int q = 0; q < nsets; ++q) {
+            SetStructure& S = h.sets[q];
+            const int32_t* lo = h.node_lo.p + S.node0;
+            const int32_t* hi = h.node_hi.p + S.node0;
+            if (S.n_adm) {
+                HM_CUDA(cudaMemcpyAsync(h.adm_pairs.p + ao, adm[q].p, S.n_adm * sizeof(int2),
+                                        cudaMemcpyDeviceToDevice, s));
+                k_make_blk<<<grid_for(S.n_adm), NT, 0, s>>>(adm[q].p, S.n_adm, lo, hi, S.row0,
+                                                            h.ablk.p + ao);
+            }
+            if (S.n_dense) {
+                HM_CUDA(cudaMemcpyAsync(h.dense_pairs.p + dof, dense[q].p,
+                                        S.n_dense * sizeof(int2), cudaMemcpyDeviceToDevice, s));
+                k_make_blk<<<grid_for(S.n_dense), NT, 0, s>>>(dense[q].p, S.n_dense, lo, hi,
+                                                              S.row0, h.dblk.p + dof);
+            }
+            HM_LAUNCH("blocks");
+            ao += S.n_adm;
+            dof += S.n_dense;
+            // leaf tiles of this set, in row order
+            DevBuf<int64_t> flag(S.n_nodes, s), off(S.n_nodes + 1, s);
+            k_leaf_flags<<<grid_for(S.n_nodes), NT, 0, s>>>(lo, hi, S.n_nodes, leaf, flag.p);
+            scan_exclusive_i64(flag.p, off.p, S.n_nodes, off.p + S.n_nodes, s);
+            int64_t nt = 0;
+            HM_CUDA(cudaMemcpyAsync(&nt, off.p + S.n_nodes, sizeof(int64_t),
+                                    cudaMemcpyDeviceToHost, s));
+            HM_CUDA(cudaStreamSynchronize(s));
+            DevBuf<uint64_t> k(nt, s);
+            DevBuf<uint32_t> v(nt, s);
+            DevBuf<int32_t> vid(nt, s);
+            k_leaf_emit<<<grid_for(S.n_nodes), NT, 0, s>>>(lo, hi, S.n_nodes, flag.p, off.p, k.p,
+                                                           v.p, vid.p);
+            radix_sort_u64_u32(k.p, v.p, nt, bits_for(S.N + 1), s);
+            trow[q].alloc(nt, s);
+            tm[q].alloc(nt, s);
+            k_leaf_tiles<<<grid_for(nt), NT, 0, s>>>(v.p, vid.p, nt, lo, hi, S.row0, trow[q].p,
+                                                     tm[q].p);
+            HM_LAUNCH("tiles");
+            ntile[q] = nt;
+            h.n_tiles += nt;
+        }
+    }
+    h.tile_row0.alloc(std::max<int64_t>(h.n_tiles, 1), s);
+    h.tile_m.alloc(std::max<int64_t>(h.n_tiles, 1), s);
+    {
+        int64_t o = 0;
+        for (int q = 0; q < nsets; ++q) {
+            HM_CUDA(cudaMemcpyAsync(h.tile_row0.p + o, trow[q].p, ntile[q] * sizeof(int64_t),
+                                    cudaMemcpyDeviceToDevice, s));
+            HM_CUDA(cudaMemcpyAsync(h.tile_m.p + o, tm[q].p, ntile[q] * sizeof(int32_t),
+                                    cudaMemcpyDeviceToDevice, s));
+            o += ntile[q];
+        }
+    }
+    fill_block_sets(h);
+    add_perm_offsets(h);
+    h.stats.t_structure_ms = tstruct.stop_ms();
+    adm.clear();
+    dense.clear();
+    if (pts_dev.p) pts_dev.release();
+
+    // batched ACA of the admissible leaves
+    {
+        Timer ta(s);
+        alloc_factor_meta(h);
+        DevBuf<int32_t> kpred;
+        if (opt.rank_model) {
+            kpred.alloc(std::max<int64_t>(h.n_adm, 1), s);
+            predict_ranks(h, kpred.p);
+        }
+        compress(h, nullptr, h.n_adm, opt.rank_model ? kpred.p : nullptr);
+        if (opt.rank_model) rerun_mispredicted(h);
+        check_status(h);
+        h.stats.t_aca_ms = ta.stop_ms();
+    }
+    rank_stats(h);
+
+    // near field
+    {
+        Timer td(s);
+        const int64_t nd = h.n_dense;
+        h.doff.alloc(std::max<int64_t>(nd, 1), s);
+        int64_t tot = 0;
+        if (nd > 0) {
+            DevBuf<int64_t> sz(nd, s), t(1, s);
+            k_near_size<<<grid_for(nd), NT, 0, s>>>(h.dblk.p, nd, sz.p);
+            scan_exclusive_i64(sz.p, h.doff.p, nd, t.p, s);
+            HM_CUDA(cudaMemcpyAsync(&tot, t.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            HM_CUDA(cudaStreamSynchronize(s));
+        }
+        h.near.alloc(std::max<int64_t>(tot, 1) * near_entry_bytes(h.near_format), s);
+        near_assemble(h.near_format, h.kp, h.X, h.dblk.p, h.doff.p, nd, h.near.p, s);
+        h.stats.near_entries = tot;
+        h.stats.t_dense_ms = td.stop_ms();
+    }
+
+    // product lists and plan
+    mvp_build_lists(h.ablk.p, h.rank.p, h.n_adm, h.dblk.p, h.n_dense, h.tile_row0.p, h.tile_m.p,
+                    h.n_tiles, h.lists, s);
+    MvpPlan& P = h.plan;
+    P.precision = h.precision;
+    P.near_format = h.near_format;
+    P.Ntot = Ntot;
+    P.n_adm = h.n_adm;
+    P.ablk = h.ablk.p;
+    P.rank = h.rank.p;
+    P.Uptr = h.Uptr.p;
+    P.Vptr = h.Vptr.p;
+    P.toff = h.lists.toff.p;
+    P.t_len = h.lists.t_len;
+    P.n_vitems = h.lists.n_vitems;
+    P.vitems = h.lists.vitems.p;
+    P.tpart_off = h.lists.tpart_off.p;
+    P.tpart_len = h.lists.tpart_len;
+    P.tsum_first = h.lists.tsum_first.p;
+    P.tsum_count = h.lists.tsum_count.p;
+    P.n_multi = h.lists.n_multi;
+    P.multi = h.lists.multi.p;
+    P.n_dense = h.n_dense;
+    P.dblk = h.dblk.p;
+    P.doff = h.doff.p;
+    P.near = h.near.p;
+    P.near_entries = h.stats.near_entries;
+    P.n_tiles = h.n_tiles;
+    P.tile_row0 = h.tile_row0.p;
+    P.tile_m = h.tile_m.p;
+    P.lr_ptr = h.lists.lr_ptr.p;
+    P.lr_ent = h.lists.lr_ent.p;
+    P.dn_ptr = h.lists.dn_ptr.p;
+    P.dn_ent = h.lists.dn_ent.p;
+    P.perm = h.perm.p;
+    P.sigma2 = h.sigma2;
+    mvp_alloc_work(P, h.work, s);
+    HM_CUDA(cudaStreamSynchronize(s));
+
+    // statistics
+    hm_stats& st = h.stats;
+    st.n_points = Ntot;
+    st.n_nodes = nn;
+    st.n_adm = h.n_adm;
+    st.n_dense = h.n_dense;
+    st.n_tiles = h.n_tiles;
+    st.depth = h.sets[0].depth;
+    st.d = h.sets[0].d;
+    st.precision = h.precision;
+    st.near_format = h.near_format;
+    const int64_t fsz = h.precision == HM_PREC_FP64 ? 8 : 4;
+    st.factor_bytes = st.factor_entries * fsz;
+    st.near_bytes = st.near_entries * (int64_t)near_entry_bytes(h.near_format);
+    int64_t n_ent = 0;
+    {
+        int64_t a = 0, b = 0;
+        HM_CUDA(cudaMemcpy(&a, h.lists.lr_ptr.p + h.n_tiles, sizeof(int64_t), cudaMemcpyDeviceToHost));
+        HM_CUDA(cudaMemcpy(&b, h.lists.dn_ptr.p + h.n_tiles, sizeof(int64_t), cudaMemcpyDeviceToHost));
+        n_ent = a + b;
+    }
+    // algorithmic bytes of one product: factors + near field + x (read once
+    // through the permutation) + perm + y written + gather entries
+    st.mvp_bytes = st.factor_bytes + st.near_bytes + Ntot * (8 + 8 + 8) + n_ent * 8;
+    st.t_total_ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+}  // namespace hm

@@ -1,0 +1,322 @@
+"""ctypes binding of libhm.so (include/hm.h): argument marshalling only.
+
+Every step of the build and the product runs in the CUDA library; this module
+converts numpy arrays / torch tensors into pointers, fills the option struct
+and turns negative status codes into exceptions. There is no CPU fallback:
+if the library is missing, ``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+GAUSSIAN, MATERN32 = 0, 1
+PREC_FP64, PREC_MIXED = 0, 1
+NEAR_AUTO, NEAR_FP64, NEAR_FP32, NEAR_BF16X2, NEAR_BF16 = range(5)
+MLP_NPARAM = 4801
+
+_STATUS = {0: "HM_OK", -1: "HM_EINVAL", -2: "HM_ENOMEM", -3: "HM_EOVERFLOW",
+           -4: "HM_ECUDA", -5: "HM_ETIMEOUT", -6: "HM_ENOTSUP"}
+
+
+class HMError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s: %s" % (_STATUS.get(code, code), msg))
+        self.code = code
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("near_format", C.c_int),
+                ("adm_max", C.c_int), ("k_cap", C.c_int),
+                ("aca_eta", C.c_double), ("eps0", C.c_double),
+                ("accumulate", C.c_int), ("rank_model", C.c_int),
+                ("rank_model_theta", C.c_void_p), ("scratch_gb", C.c_double),
+                ("stream", C.c_void_p)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("n_points", C.c_int64), ("n_nodes", C.c_int64),
+                ("n_adm", C.c_int64), ("n_dense", C.c_int64),
+                ("n_tiles", C.c_int64), ("depth", C.c_int), ("d", C.c_int),
+                ("sum_rank", C.c_int64), ("max_rank", C.c_int),
+                ("rank_cap_hits", C.c_int64), ("n_rejected", C.c_int64),
+                ("n_mispredicted", C.c_int64), ("factor_entries", C.c_int64),
+                ("near_entries", C.c_int64), ("factor_bytes", C.c_int64),
+                ("near_bytes", C.c_int64), ("mvp_bytes", C.c_int64),
+                ("reserved_factor_entries", C.c_int64),
+                ("t_structure_ms", C.c_double), ("t_aca_ms", C.c_double),
+                ("t_dense_ms", C.c_double), ("t_total_ms", C.c_double),
+                ("aca_passes", C.c_int), ("precision", C.c_int),
+                ("near_format", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+_vp = C.c_void_p
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libhm.so (built by __graft_entry__.build()); raise if absent."""
+    global _lib
+    if _lib is None:
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError("libhm.so not built: run python -m paper_1708_09707_gb300.build")
+        L = C.CDLL(path)
+        _declare(L)
+        _lib = L
+    return _lib
+
+
+def _declare(L):
+    i64, pi = C.c_int64, C.POINTER(C.c_int)
+    L.hm_options_default.argtypes = [C.POINTER(Options)]
+    L.hm_last_error.restype = C.c_char_p
+    L.hm_build_ex.restype = _vp
+    L.hm_build_ex.argtypes = [_vp, i64, C.c_int, C.c_int, _vp, C.c_int, C.c_double,
+                              C.c_double, C.POINTER(Options), pi]
+    L.hm_build.restype = _vp
+    L.hm_build.argtypes = [_vp, i64, C.c_int, C.c_int, _vp, C.c_int, C.c_double, C.c_double]
+    L.hm_matvec.argtypes = [_vp, _vp, _vp]
+    L.hm_matvec_ex.argtypes = [_vp, _vp, _vp, C.c_int, _vp]
+    L.hm_free.argtypes = [_vp]
+    L.hm_get_stats.argtypes = [_vp, C.POINTER(Stats)]
+    L.hm_export_structure.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
+    L.hm_export_tree.argtypes = [_vp, _vp, _vp, _vp, _vp]
+    L.hm_export_factors.argtypes = [_vp, i64, _vp, _vp, pi]
+    L.hm_cg.argtypes = [_vp, _vp, _vp, C.c_double, C.c_int, pi, C.POINTER(C.c_double)]
+    L.hm_build_batch.restype = _vp
+    L.hm_build_batch.argtypes = [C.c_int, _vp, _vp, _vp, C.c_int, _vp, C.c_int, C.c_double,
+                                 C.c_double, C.POINTER(Options), pi]
+    L.hm_matvec_batch.argtypes = [_vp, _vp, _vp]
+    L.hm_batch_stats.argtypes = [_vp, C.POINTER(Stats)]
+    L.hm_free_batch.argtypes = [_vp]
+    L.hm_block_features.argtypes = [_vp, _vp, _vp]
+    L.hm_mlp_forward.argtypes = [_vp, _vp, i64, _vp, _vp]
+    L.hm_mlp_loss_grad.argtypes = [_vp, _vp, _vp, i64, _vp, _vp, _vp]
+    L.hm_mlp_adam.argtypes = [_vp, _vp, _vp, _vp, i64, C.c_float, C.c_float, C.c_float,
+                              C.c_float, _vp]
+    L.hm_morton_codes.argtypes = [_vp, i64, C.c_int, _vp, _vp]
+    L.hm_radix_sort_pairs.argtypes = [_vp, _vp, i64, C.c_int, _vp]
+
+
+def _check(code: int):
+    if code != 0:
+        raise HMError(code, lib().hm_last_error().decode())
+
+
+def _ptr(a):
+    """Address of a numpy array or torch tensor (must be contiguous)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags.c_contiguous
+        return a.ctypes.data
+    if not a.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return a.data_ptr()
+
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+def options(precision=PREC_FP64, near_format=NEAR_AUTO, adm_max=False, k_cap=64,
+            aca_eta=0.0, eps0=0.0, accumulate=False, rank_model_theta=None,
+            scratch_gb=0.0, stream=None) -> Options:
+    o = Options()
+    lib().hm_options_default(C.byref(o))
+    o.precision = precision
+    o.near_format = near_format
+    o.adm_max = int(adm_max)
+    o.k_cap = k_cap
+    o.aca_eta = aca_eta
+    o.eps0 = eps0
+    o.accumulate = int(accumulate)
+    o.rank_model = int(rank_model_theta is not None)
+    o.rank_model_theta = _ptr(rank_model_theta)
+    o.scratch_gb = scratch_gb
+    o.stream = _stream_ptr(stream)
+    return o
+
+
+class HMatrix:
+    """H-matrix of A_{phi, Y x Y} (+ sigma^2 I) built on the GPU (hm_build_ex).
+
+    points: (N, d) float64 numpy array (host) or torch tensor (host or cuda).
+    """
+
+    def __init__(self, points, kernel: int, ell: float, leaf: int, eta: float,
+                 aca_eps: float, sigma2: float = 0.0, **opts):
+        L = lib()
+        if isinstance(points, np.ndarray):
+            points = np.ascontiguousarray(points, dtype=np.float64)
+        self.n, self.d = int(points.shape[0]), int(points.shape[1])
+        self._theta = opts.get("rank_model_theta")
+        self.opt = options(**opts)
+        prm = np.array([ell, sigma2], dtype=np.float64)
+        st = C.c_int(0)
+        self._h = L.hm_build_ex(_ptr(points), self.n, self.d, kernel, prm.ctypes.data, leaf,
+                                eta, aca_eps, C.byref(self.opt), C.byref(st))
+        if not self._h:
+            raise HMError(st.value, L.hm_last_error().decode())
+        self.kernel, self.ell, self.leaf, self.eta = kernel, ell, leaf, eta
+        self.aca_eps, self.sigma2 = aca_eps, sigma2
+
+    def free(self):
+        if getattr(self, "_h", None):
+            lib().hm_free(self._h)
+            self._h = None
+
+    __del__ = free
+
+    def matvec(self, x, y=None, stream=None):
+        """y = H x + sigma^2 x; numpy in -> numpy out, torch in -> torch out."""
+        if _is_torch(x):
+            import torch
+            nrhs = 1 if x.dim() == 1 else x.shape[0]
+            if y is None:
+                y = torch.empty_like(x)
+        else:
+            x = np.ascontiguousarray(x, dtype=np.float64)
+            nrhs = 1 if x.ndim == 1 else x.shape[0]
+            if y is None:
+                y = np.empty_like(x)
+        _check(lib().hm_matvec_ex(self._h, _ptr(x), _ptr(y), nrhs, _stream_ptr(stream)))
+        return y
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(lib().hm_get_stats(self._h, C.byref(s)))
+        return s.as_dict()
+
+    def structure(self):
+        st = self.stats()
+        codes = np.zeros(self.n, np.uint64)
+        perm = np.zeros(self.n, np.int64)
+        adm = np.zeros((max(st["n_adm"], 1), 2), np.int64)
+        dense = np.zeros((max(st["n_dense"], 1), 2), np.int64)
+        ranks = np.zeros(max(st["n_adm"], 1), np.int32)
+        _check(lib().hm_export_structure(self._h, _ptr(codes), _ptr(perm), _ptr(adm),
+                                         _ptr(dense), _ptr(ranks)))
+        return dict(codes=codes, perm=perm, adm=adm[: st["n_adm"]],
+                    dense=dense[: st["n_dense"]], ranks=ranks[: st["n_adm"]])
+
+    def tree(self):
+        nn = self.stats()["n_nodes"]
+        lo = np.zeros(nn, np.int64)
+        hi = np.zeros(nn, np.int64)
+        bmin = np.zeros((nn, self.d))
+        bmax = np.zeros((nn, self.d))
+        _check(lib().hm_export_tree(self._h, _ptr(lo), _ptr(hi), _ptr(bmin), _ptr(bmax)))
+        return lo, hi, bmin, bmax
+
+    def factors(self, b: int, m: int, n: int):
+        k = self.opt.k_cap
+        U = np.zeros((k, m))
+        V = np.zeros((k, n))
+        r = C.c_int(0)
+        _check(lib().hm_export_factors(self._h, b, _ptr(U), _ptr(V), C.byref(r)))
+        r = r.value
+        return (U.reshape(-1)[: r * m].reshape(r, m).T.copy(),
+                V.reshape(-1)[: r * n].reshape(r, n).T.copy())
+
+    def cg(self, b, rtol=1e-6, maxit=1000, x0=None):
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x = np.zeros(self.n) if x0 is None else np.array(x0, dtype=np.float64)
+        it = C.c_int(0)
+        rr = C.c_double(0)
+        _check(lib().hm_cg(self._h, _ptr(b), _ptr(x), rtol, maxit, C.byref(it), C.byref(rr)))
+        return x, it.value, rr.value
+
+    def features(self):
+        na = self.stats()["n_adm"]
+        F = np.zeros((max(na, 1), 8), np.float32)
+        T = np.zeros(max(na, 1), np.float32)
+        _check(lib().hm_block_features(self._h, _ptr(F), _ptr(T)))
+        return F[:na], T[:na]
+
+
+class HBatch:
+    """Many independent point sets built and multiplied together."""
+
+    def __init__(self, point_sets, kernel: int, ell: float, leaf: int, eta: float,
+                 aca_eps: float, sigma2: float = 0.0, **opts):
+        L = lib()
+        self.sizes = np.array([p.shape[0] for p in point_sets], np.int64)
+        self.dims = np.array([p.shape[1] for p in point_sets], np.int32)
+        allp = np.ascontiguousarray(np.concatenate([np.asarray(p, np.float64).ravel()
+                                                    for p in point_sets]))
+        self.opt = options(**opts)
+        prm = np.array([ell, sigma2], dtype=np.float64)
+        st = C.c_int(0)
+        self._b = L.hm_build_batch(len(point_sets), _ptr(allp), _ptr(self.sizes),
+                                   _ptr(self.dims), kernel, prm.ctypes.data, leaf, eta,
+                                   aca_eps, C.byref(self.opt), C.byref(st))
+        if not self._b:
+            raise HMError(st.value, L.hm_last_error().decode())
+        self.n = int(self.sizes.sum())
+
+    def free(self):
+        if getattr(self, "_b", None):
+            lib().hm_free_batch(self._b)
+            self._b = None
+
+    __del__ = free
+
+    def matvec(self, x, y=None):
+        if _is_torch(x):
+            import torch
+            y = torch.empty_like(x) if y is None else y
+        else:
+            x = np.ascontiguousarray(x, dtype=np.float64)
+            y = np.empty_like(x) if y is None else y
+        _check(lib().hm_matvec_batch(self._b, _ptr(x), _ptr(y)))
+        return y
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(lib().hm_batch_stats(self._b, C.byref(s)))
+        return s.as_dict()
+
+
+# ------------------------------------------------------------- step helpers
+def morton_codes(points_dev, codes_dev, stream=None):
+    n, d = points_dev.shape
+    _check(lib().hm_morton_codes(_ptr(points_dev), n, d, _ptr(codes_dev), _stream_ptr(stream)))
+
+
+def radix_sort_pairs(keys_dev, vals_dev, key_bits: int, stream=None):
+    _check(lib().hm_radix_sort_pairs(_ptr(keys_dev), _ptr(vals_dev), keys_dev.numel(),
+                                     key_bits, _stream_ptr(stream)))
+
+
+def mlp_forward(theta, F, out, stream=None):
+    _check(lib().hm_mlp_forward(_ptr(theta), _ptr(F), F.shape[0], _ptr(out),
+                                _stream_ptr(stream)))
+
+
+def mlp_loss_grad(theta, F, target, grad, loss=None, stream=None):
+    _check(lib().hm_mlp_loss_grad(_ptr(theta), _ptr(F), _ptr(target), F.shape[0], _ptr(grad),
+                                  _ptr(loss), _stream_ptr(stream)))
+
+
+def mlp_adam(theta, grad, m, v, t: int, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, stream=None):
+    _check(lib().hm_mlp_adam(_ptr(theta), _ptr(grad), _ptr(m), _ptr(v), t, lr, b1, b2, eps,
+                             _stream_ptr(stream)))
