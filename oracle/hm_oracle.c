@@ -206,9 +206,12 @@ int or_admissible(const double* amin, const double* amax, const double* bmin,
 /*  - first column j_1 = 0; later columns: argmax over unused columns of     */
 /*    |v_{r-1}|, lowest index on ties;                                       */
 /*  - row pivot i_r = argmax |u^_r| (lowest index on ties);                  */
-/*  - the paper asks for a column with ||u^|| > eps0: a column whose largest */
-/*    residual entry is <= eps0 * max_i |A(i,j)| is rejected, the lowest     */
-/*    unused column is tried next and r does not advance;                    */
+/*  - the paper asks for a column with ||u^|| > eps0, eps0 near machine     */
+/*    precision, and leaves the search open: a column whose largest residual */
+/*    entry is <= eps0 * max_i |A(i,j)| is rejected, the lowest unused       */
+/*    column is tried next and r does not advance; after OR_REJ_RUN          */
+/*    rejections in a row the block is taken as fully approximated (the      */
+/*    search is bounded instead of scanning every column);                   */
 /*  - the eta in the stopping rule is a separate aca_eta (the admissibility  */
 /*    eta = 1 of the workloads would make the rule never fire);              */
 /*  - ||sum_l u_l v_l^T||_F^2 is updated by the textbook recursion           */
@@ -218,6 +221,8 @@ int or_admissible(const double* amin, const double* amax, const double* bmin,
 /*    mode (no test, k = k_cap);                                             */
 /*  - the rank never exceeds min(k_cap, m, n).                               */
 /* ------------------------------------------------------------------------ */
+#define OR_REJ_RUN 4
+
 int or_aca(or_entry_fn f, const void* ctx, int64_t m, int64_t n, double eps,
            int k_cap, double aca_eta, double eps0, double* U, double* V,
            int64_t* piv_i, int64_t* piv_j, int64_t* n_rej)
@@ -231,7 +236,7 @@ int or_aca(or_entry_fn f, const void* ctx, int64_t m, int64_t n, double eps,
     double thr = (eps > 0.0) ? eps * (1.0 - aca_eta) / (1.0 + eps) : -1.0;
     double S2 = 0.0;
     int r = 0;
-    int64_t j = 0, rej = 0;
+    int64_t j = 0, rej = 0, run = 0;
 
     while (r < kmax) {
         /* residual column u^_r = A(:, j) - sum_{l<r} u_l (v_l)_j */
@@ -255,6 +260,7 @@ int or_aca(or_entry_fn f, const void* ctx, int64_t m, int64_t n, double eps,
         if (!(best > eps0 * amax)) {
             /* column already represented: try the lowest unused one */
             rej++;
+            if (++run >= OR_REJ_RUN) break;
             int64_t jn = -1;
             for (int64_t c = 0; c < n; ++c)
                 if (!used[c]) {
@@ -265,6 +271,7 @@ int or_aca(or_entry_fn f, const void* ctx, int64_t m, int64_t n, double eps,
             j = jn;
             continue;
         }
+        run = 0;
         /* u_r = u^_r / u^_{i_r} */
         double piv = uh[is];
         double* u = U + (int64_t)r * m;
