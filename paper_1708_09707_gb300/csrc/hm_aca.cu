@@ -6,8 +6,8 @@
 //  * blocks with m, n <= 32*MAXR are handled by one warp each: a lane owns
 //    rows lane + 32t and columns lane + 32t, the residual column and row live
 //    in registers, pivot searches and norms are warp-shuffle reductions;
-//  * larger blocks get one CTA each (persistent CTAs pull blocks from a
-//    counter), with the residual vectors in the output factor columns.
+//  * larger blocks get one CTA or one thread-block cluster each, with the
+//    residual vectors in the output factor columns.
 // Readings of Alg. 2 (the same as the CPU oracle): first column 0; row pivot
 // argmax |u^| (lowest index on ties); a column whose largest residual entry
 // is <= eps0 * max |A(:,j)| is rejected and the lowest unused column is tried;
@@ -15,6 +15,8 @@
 // updated by S2 += 2 sum_l (u.u_l)(v_l.v) + |u|^2 |v|^2; the rule
 // |u||v| <= eps (1-aca_eta)/(1+eps) sqrt(S2) stops (eps <= 0: fixed rank).
 // The norms, S2 and the stopping test are always accumulated in double.
+#include <cooperative_groups.h>
+
 #include "hm_kernel_fn.cuh"
 
 namespace hm {
@@ -22,9 +24,10 @@ namespace hm {
 namespace {
 
 constexpr int WARP_NT = 128;   // threads per CTA of the warp kernel
-constexpr int CTA_NT = 512;
+constexpr int CTA_NT = 256;
 constexpr int CTA_WARPS = CTA_NT / 32;
 constexpr int KBUF = 128;      // largest supported k_cap
+constexpr int REJ_RUN = 4;     // rejected columns in a row that end a block
 
 template <class R, int KERN, int MAXR>
 __global__ void __launch_bounds__(WARP_NT)
@@ -47,7 +50,7 @@ k_aca_warp(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restric
     R acc[MAXR];
     R vv[MAXR];
     unsigned used = 0;
-    int r = 0, j = 0, rej = 0;
+    int r = 0, j = 0, rej = 0, run = 0;
     bool converged = false;
     double S2 = 0.0;
     const int limit = kmax + n + 1;
@@ -97,8 +100,13 @@ k_aca_warp(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restric
         warp_argmax(best, bi);
         amax = warp_max(amax);
         if (!(best > eps0 * amax)) {
-            // column already represented: take the lowest unused column
+            // column already represented: take the lowest unused column,
+            // or stop after REJ_RUN rejections in a row
             ++rej;
+            if (++run >= REJ_RUN) {
+                converged = true;
+                break;
+            }
             int cand = 0x7fffffff;
 #pragma unroll
             for (int t = 0; t < MAXR; ++t) {
@@ -117,6 +125,7 @@ k_aca_warp(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restric
             j = cand;
             continue;
         }
+        run = 0;
         // u_r = u^ / u^_{i_r}
         R mine = 0;
 #pragma unroll
@@ -218,69 +227,52 @@ k_aca_warp(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restric
 }
 
 // --------------------------------------------------------------------------
-// One CTA per large block; persistent CTAs take blocks from a counter.
+// Large blocks: one CTA or one thread-block cluster of CS CTAs per block
+// (CS = 1, 4 or 8). The rows and columns of the block are dealt round-robin
+// to all CS * CTA_NT threads; every reduction (pivot search, norms, cross
+// terms, next column) first reduces inside each CTA, then every CTA reads the
+// partials of all CTAs of its cluster from distributed shared memory in rank
+// order, so all CTAs reach identical decisions and follow the same control
+// flow. Partials are double-buffered, so one cluster barrier per reduction
+// suffices. The block's used-column bitmap lives in global memory.
 // --------------------------------------------------------------------------
-struct CtaRed {
-    double dsum[CTA_WARPS][2];
-    double dl[CTA_WARPS][KBUF];
-    double dm[CTA_WARPS][KBUF];
-    float fbest[CTA_WARPS];
-    double dbest[CTA_WARPS];
-    int ibest[CTA_WARPS];
-    double damax[CTA_WARPS];
+struct ClPart {
+    double best, bval, amax;   // column pivot: |u^|, u^ at the pivot, max |A(:,j)|
+    int bi, cand, vbj, pad;
+    double nu2, nv2, vbest;
+    double du[KBUF], dv[KBUF];
 };
 
-template <class R>
-__device__ __forceinline__ void cta_argmax(R val, int idx, R amax, CtaRed& red, R& out_val,
-                                           int& out_idx, R& out_amax)
-{
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    warp_argmax(val, idx);
-    amax = warp_max(amax);
-    if (lane == 0) {
-        red.dbest[w] = (double)val;
-        red.ibest[w] = idx;
-        red.damax[w] = (double)amax;
-    }
-    __syncthreads();
-    double bv = red.dbest[0];
-    int bi = red.ibest[0];
-    double am = red.damax[0];
-    for (int k = 1; k < CTA_WARPS; ++k) {
-        double v = red.dbest[k];
-        int i = red.ibest[k];
-        if (v > bv || (v == bv && i < bi)) {
-            bv = v;
-            bi = i;
-        }
-        am = fmax(am, red.damax[k]);
-    }
-    __syncthreads();
-    out_val = (R)bv;
-    out_idx = bi;
-    out_amax = (R)am;
-}
+struct ClShared {
+    ClPart part[2];
+    double wl[CTA_WARPS][KBUF];   // per-warp partial dots
+    double wm[CTA_WARPS][KBUF];
+    double ws[CTA_WARPS][4];
+    int wi[CTA_WARPS][2];
+    double bc[4];                 // broadcast: reduced values
+    int bci[2];
+};
 
 template <class R, int KERN>
-__global__ void __launch_bounds__(CTA_NT, 1)
-k_aca_cta(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restrict__ order,
-          int64_t nblocks, double thr, int* __restrict__ counter,
-          uint32_t* __restrict__ usedpool, int64_t used_words)
+__global__ void __launch_bounds__(CTA_NT)
+k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restrict__ order,
+              int64_t nblocks, double thr, uint32_t* __restrict__ usedpool, int64_t used_words)
 {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const int CS = (int)cl.num_blocks();
+    const int crank = (int)cl.block_rank();
     __shared__ R sg[KBUF];
-    __shared__ CtaRed red;
-    __shared__ int s_next;
+    __shared__ ClShared sh;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    uint32_t* used = usedpool + (int64_t)blockIdx.x * used_words;
+    const int gt = crank * CTA_NT + tid, GT = CS * CTA_NT;
+    const int64_t cid = blockIdx.x / CS, ncl = gridDim.x / CS;
+    uint32_t* used = usedpool + cid * used_words;
     const R c = kconst<R>(kp);
     const R eps0 = (R)a.eps0;
+    int ph = 0;
 
-    for (;;) {
-        if (tid == 0) s_next = atomicAdd(counter, 1);
-        __syncthreads();
-        const int64_t q = s_next;
-        __syncthreads();
-        if (q >= nblocks) break;
+    for (int64_t q = cid; q < nblocks; q += ncl) {
         const uint32_t b = order[q];
         const Blk B = a.blk[b];
         const int m = B.m, n = B.n;
@@ -288,26 +280,28 @@ k_aca_cta(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restrict
         const int kmax = min(kres, min(m, n));
         R* __restrict__ U = reinterpret_cast<R*>(a.Uptr[b]);
         R* __restrict__ V = reinterpret_cast<R*>(a.Vptr[b]);
-        for (int k = tid; k < (n + 31) / 32; k += CTA_NT) used[k] = 0u;
-        __syncthreads();
+        const int words = (n + 31) / 32;
+        for (int k = gt; k < words; k += GT) used[k] = 0u;
+        cl.sync();
 
-        int r = 0, j = 0, rej = 0;
+        int r = 0, j = 0, rej = 0, run = 0;
         bool converged = false;
         double S2 = 0.0;
         const int limit = kmax + n + 1;
         for (int it = 0; r < kmax; ++it) {
             if (it > limit) {
-                if (tid == 0) atomicOr(a.status, 1);
+                if (gt == 0) atomicOr(a.status, 1);
                 break;
             }
-            if (tid == 0) used[j >> 5] |= 1u << (j & 31);
+            if (gt == 0) used[j >> 5] |= 1u << (j & 31);
             if (tid < r) sg[tid] = V[(int64_t)tid * n + j];
             __syncthreads();
+            // residual column and its pivot
             const Pt<R> pj = load_pt<R>(X, B.col0 + j);
             R* __restrict__ Ur = U + (int64_t)r * m;
-            R best = -1, amax = 0;
+            R best = -1, amax = 0, bval = 0;
             int bi = 0x7fffffff;
-            for (int i = tid; i < m; i += CTA_NT) {
+            for (int i = gt; i < m; i += GT) {
                 R v = phi<KERN>(dist2(load_pt<R>(X, B.row0 + i), pj), c);
                 amax = max(amax, fabs(v));
                 for (int l = 0; l < r; ++l) v -= U[(int64_t)l * m + i] * sg[l];
@@ -315,82 +309,226 @@ k_aca_cta(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restrict
                 if (fabs(v) > best) {
                     best = fabs(v);
                     bi = i;
+                    bval = v;
                 }
             }
-            cta_argmax<R>(best, bi, amax, red, best, bi, amax);
+            {
+                // warp then CTA argmax carrying the signed value
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    R ob = __shfl_xor_sync(0xffffffffu, best, o);
+                    int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                    R ov = __shfl_xor_sync(0xffffffffu, bval, o);
+                    if (ob > best || (ob == best && oi < bi)) {
+                        best = ob;
+                        bi = oi;
+                        bval = ov;
+                    }
+                }
+                amax = warp_max(amax);
+                if (lane == 0) {
+                    sh.ws[w][0] = (double)best;
+                    sh.ws[w][1] = (double)bval;
+                    sh.ws[w][2] = (double)amax;
+                    sh.wi[w][0] = bi;
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    double B0 = sh.ws[0][0], V0 = sh.ws[0][1], A0 = sh.ws[0][2];
+                    int I0 = sh.wi[0][0];
+                    for (int k = 1; k < CTA_WARPS; ++k) {
+                        if (sh.ws[k][0] > B0 || (sh.ws[k][0] == B0 && sh.wi[k][0] < I0)) {
+                            B0 = sh.ws[k][0];
+                            V0 = sh.ws[k][1];
+                            I0 = sh.wi[k][0];
+                        }
+                        A0 = fmax(A0, sh.ws[k][2]);
+                    }
+                    sh.part[ph].best = B0;
+                    sh.part[ph].bval = V0;
+                    sh.part[ph].amax = A0;
+                    sh.part[ph].bi = I0;
+                }
+                cl.sync();
+                if (tid == 0) {
+                    double B0 = -1, V0 = 0, A0 = 0;
+                    int I0 = 0x7fffffff;
+                    for (int k = 0; k < CS; ++k) {
+                        const ClPart* P = cl.map_shared_rank(&sh.part[ph], k);
+                        if (P->best > B0 || (P->best == B0 && P->bi < I0)) {
+                            B0 = P->best;
+                            V0 = P->bval;
+                            I0 = P->bi;
+                        }
+                        A0 = fmax(A0, P->amax);
+                    }
+                    sh.bc[0] = B0;
+                    sh.bc[1] = V0;
+                    sh.bc[2] = A0;
+                    sh.bci[0] = I0;
+                }
+                ph ^= 1;
+                __syncthreads();
+                best = (R)sh.bc[0];
+                bval = (R)sh.bc[1];
+                amax = (R)sh.bc[2];
+                bi = sh.bci[0];
+                __syncthreads();
+            }
             if (!(best > eps0 * amax)) {
                 ++rej;
-                // lowest unused column
+                if (++run >= REJ_RUN) {
+                    converged = true;
+                    break;
+                }
+                // lowest unused column over the whole cluster
                 int cand = 0x7fffffff;
-                for (int k = tid; k < (n + 31) / 32; k += CTA_NT) {
+                for (int k = gt; k < words; k += GT) {
                     uint32_t free_bits = ~used[k];
-                    if (k == (n - 1) / 32 && (n & 31)) free_bits &= (1u << (n & 31)) - 1u;
+                    if (k == words - 1 && (n & 31)) free_bits &= (1u << (n & 31)) - 1u;
                     if (free_bits) {
                         cand = k * 32 + __ffs(free_bits) - 1;
                         break;
                     }
                 }
-                // all values equal: the argmax tie rule returns the lowest index
-                R dummy = 0;
-                R dv0 = 0;
-                cta_argmax<R>(dv0, cand, dummy, red, dv0, cand, dummy);
-                if (cand == 0x7fffffff || cand < 0 || cand >= n) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) cand = min(cand, __shfl_xor_sync(0xffffffffu, cand, o));
+                if (lane == 0) sh.wi[w][1] = cand;
+                __syncthreads();
+                if (tid == 0) {
+                    int cm = 0x7fffffff;
+                    for (int k = 0; k < CTA_WARPS; ++k) cm = min(cm, sh.wi[k][1]);
+                    sh.part[ph].cand = cm;
+                }
+                cl.sync();
+                if (tid == 0) {
+                    int cm = 0x7fffffff;
+                    for (int k = 0; k < CS; ++k) cm = min(cm, cl.map_shared_rank(&sh.part[ph], k)->cand);
+                    sh.bci[1] = cm;
+                }
+                ph ^= 1;
+                __syncthreads();
+                cand = sh.bci[1];
+                __syncthreads();
+                if (cand == 0x7fffffff || cand >= n) {
                     converged = true;
                     break;
                 }
                 j = cand;
                 continue;
             }
-            // scale, gather U(i_r, l)
-            const R piv = Ur[bi];
-            __syncthreads();
-            for (int i = tid; i < m; i += CTA_NT) Ur[i] = Ur[i] / piv;
+            run = 0;
+            const R piv = bval;
             if (tid < r) sg[tid] = U[(int64_t)tid * m + bi];
             __syncthreads();
+            // residual row, scaled column, norms and next-column candidates
             const Pt<R> pi = load_pt<R>(X, B.row0 + bi);
             R* __restrict__ Vr = V + (int64_t)r * n;
-            double nv2 = 0.0;
-            for (int jj = tid; jj < n; jj += CTA_NT) {
+            double nv2 = 0.0, nu2 = 0.0;
+            R vb = -1;
+            int vbj = 0x7fffffff;
+            for (int jj = gt; jj < n; jj += GT) {
                 R v = phi<KERN>(dist2(pi, load_pt<R>(X, B.col0 + jj)), c);
                 for (int l = 0; l < r; ++l) v -= sg[l] * V[(int64_t)l * n + jj];
                 Vr[jj] = v;
                 nv2 += (double)v * (double)v;
+                if (!((used[jj >> 5] >> (jj & 31)) & 1u) && fabs(v) > vb) {
+                    vb = fabs(v);
+                    vbj = jj;
+                }
             }
-            double nu2 = 0.0;
-            for (int i = tid; i < m; i += CTA_NT) nu2 += (double)Ur[i] * (double)Ur[i];
-            // per-warp partial dots for all l, one reduction across warps
+            for (int i = gt; i < m; i += GT) {
+                const R u = Ur[i] / piv;
+                Ur[i] = u;
+                nu2 += (double)u * (double)u;
+            }
             for (int l = 0; l < r; ++l) {
                 const R* Ul = U + (int64_t)l * m;
                 const R* Vl = V + (int64_t)l * n;
                 R du = 0, dv = 0;
-                for (int i = tid; i < m; i += CTA_NT) du += Ur[i] * Ul[i];
-                for (int jj = tid; jj < n; jj += CTA_NT) dv += Vl[jj] * Vr[jj];
-                double ddu = warp_sum((double)du), ddv = warp_sum((double)dv);
+                for (int i = gt; i < m; i += GT) du += Ur[i] * Ul[i];
+                for (int jj = gt; jj < n; jj += GT) dv += Vl[jj] * Vr[jj];
+                const double ddu = warp_sum((double)du), ddv = warp_sum((double)dv);
                 if (lane == 0) {
-                    red.dl[w][l] = ddu;
-                    red.dm[w][l] = ddv;
+                    sh.wl[w][l] = ddu;
+                    sh.wm[w][l] = ddv;
                 }
             }
             nu2 = warp_sum(nu2);
             nv2 = warp_sum(nv2);
+            warp_argmax(vb, vbj);
             if (lane == 0) {
-                red.dsum[w][0] = nu2;
-                red.dsum[w][1] = nv2;
+                sh.ws[w][0] = nu2;
+                sh.ws[w][1] = nv2;
+                sh.ws[w][2] = (double)vb;
+                sh.wi[w][0] = vbj;
             }
             __syncthreads();
-            double NU2 = 0.0, NV2 = 0.0, cross = 0.0;
-            for (int k = 0; k < CTA_WARPS; ++k) {
-                NU2 += red.dsum[k][0];
-                NV2 += red.dsum[k][1];
-            }
-            for (int l = 0; l < r; ++l) {
-                double du = 0.0, dv = 0.0;
-                for (int k = 0; k < CTA_WARPS; ++k) {
-                    du += red.dl[k][l];
-                    dv += red.dm[k][l];
+            {
+                ClPart& P = sh.part[ph];
+                if (tid < r) {
+                    double su = 0.0, sv = 0.0;
+                    for (int k = 0; k < CTA_WARPS; ++k) {
+                        su += sh.wl[k][tid];
+                        sv += sh.wm[k][tid];
+                    }
+                    P.du[tid] = su;
+                    P.dv[tid] = sv;
                 }
-                cross += du * dv;
+                if (tid == 0) {
+                    double a0 = 0.0, a1 = 0.0, B0 = -1.0;
+                    int I0 = 0x7fffffff;
+                    for (int k = 0; k < CTA_WARPS; ++k) {
+                        a0 += sh.ws[k][0];
+                        a1 += sh.ws[k][1];
+                        if (sh.ws[k][2] > B0 || (sh.ws[k][2] == B0 && sh.wi[k][0] < I0)) {
+                            B0 = sh.ws[k][2];
+                            I0 = sh.wi[k][0];
+                        }
+                    }
+                    P.nu2 = a0;
+                    P.nv2 = a1;
+                    P.vbest = B0;
+                    P.vbj = I0;
+                }
             }
+            cl.sync();
+            if (w == 0) {
+                // cross term sum_l (sum_ranks du_l)(sum_ranks dv_l), in rank order
+                double cr = 0.0;
+                for (int l0 = 0; l0 < r; l0 += 32) {
+                    const int l = l0 + lane;
+                    double su = 0.0, sv = 0.0;
+                    if (l < r)
+                        for (int k = 0; k < CS; ++k) {
+                            const ClPart* P = cl.map_shared_rank(&sh.part[ph], k);
+                            su += P->du[l];
+                            sv += P->dv[l];
+                        }
+                    cr += warp_sum(su * sv);
+                }
+                if (lane == 0) {
+                    double a0 = 0.0, a1 = 0.0, B0 = -1.0;
+                    int I0 = 0x7fffffff;
+                    for (int k = 0; k < CS; ++k) {
+                        const ClPart* P = cl.map_shared_rank(&sh.part[ph], k);
+                        a0 += P->nu2;
+                        a1 += P->nv2;
+                        if (P->vbest > B0 || (P->vbest == B0 && P->vbj < I0)) {
+                            B0 = P->vbest;
+                            I0 = P->vbj;
+                        }
+                    }
+                    sh.bc[0] = a0;
+                    sh.bc[1] = a1;
+                    sh.bc[2] = cr;
+                    sh.bci[0] = I0;
+                }
+            }
+            ph ^= 1;
+            __syncthreads();
+            const double NU2 = sh.bc[0], NV2 = sh.bc[1], cross = sh.bc[2];
+            const int nj = sh.bci[0];
             __syncthreads();
             S2 += 2.0 * cross + NU2 * NV2;
             ++r;
@@ -399,25 +537,13 @@ k_aca_cta(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restrict
                 break;
             }
             if (r >= kmax) break;
-            // next column: largest |v_r| over unused columns
-            R bv = -1, dummy = 0;
-            int bj = 0x7fffffff;
-            for (int jj = tid; jj < n; jj += CTA_NT) {
-                if ((used[jj >> 5] >> (jj & 31)) & 1u) continue;
-                R v = fabs(Vr[jj]);
-                if (v > bv) {
-                    bv = v;
-                    bj = jj;
-                }
-            }
-            cta_argmax<R>(bv, bj, dummy, red, bv, bj, dummy);
-            if (bj == 0x7fffffff) {
+            if (nj == 0x7fffffff) {
                 converged = true;
                 break;
             }
-            j = bj;
+            j = nj;
         }
-        if (tid == 0) {
+        if (gt == 0) {
             a.rank[b] = r;
             a.nrej[b] = rej;
             const int full = min(a.k_cap, min(m, n));
@@ -425,55 +551,74 @@ k_aca_cta(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restrict
             if (!converged && r >= kmax) f |= (kres < full) ? 1 : 2;
             a.flags[b] = f;
         }
-        __syncthreads();
+        cl.sync();
     }
 }
 
 template <class R, int KERN>
 void launch_all(const KernelParams& kp, const DeviceCoords& X, const AcaArgs& a,
-                const uint32_t* order, int64_t n, int64_t max_dim, cudaStream_t s)
+                const uint32_t* order, int64_t n, int cls, int64_t max_n, cudaStream_t s)
 {
-    // blocks are given grouped by size class: the caller passes the size
-    // classes one at a time (max_dim is the class bound)
     const double thr = (a.eps > 0.0) ? a.eps * (1.0 - a.aca_eta) / (1.0 + a.eps) : -1.0;
     const unsigned wgrid = (unsigned)ceil_div(n * 32, WARP_NT);
-    if (max_dim <= 64) {
-        k_aca_warp<R, KERN, 2><<<wgrid, WARP_NT, 0, s>>>(kp, X, a, order, n, thr);
-    } else if (max_dim <= 128) {
-        k_aca_warp<R, KERN, 4><<<wgrid, WARP_NT, 0, s>>>(kp, X, a, order, n, thr);
-    } else if (max_dim <= 256) {
-        k_aca_warp<R, KERN, 8><<<wgrid, WARP_NT, 0, s>>>(kp, X, a, order, n, thr);
-    } else if (max_dim <= 512) {
-        k_aca_warp<R, KERN, 16><<<wgrid, WARP_NT, 0, s>>>(kp, X, a, order, n, thr);
-    } else {
+    switch (cls) {
+    case 0: k_aca_warp<R, KERN, 2><<<wgrid, WARP_NT, 0, s>>>(kp, X, a, order, n, thr); break;
+    case 1: k_aca_warp<R, KERN, 4><<<wgrid, WARP_NT, 0, s>>>(kp, X, a, order, n, thr); break;
+    case 2: k_aca_warp<R, KERN, 8><<<wgrid, WARP_NT, 0, s>>>(kp, X, a, order, n, thr); break;
+    case 3: k_aca_warp<R, KERN, 16><<<wgrid, WARP_NT, 0, s>>>(kp, X, a, order, n, thr); break;
+    default: {
+        const int cs = cls == 4 ? 1 : (cls == 5 ? 4 : 8);
         int occ = 0;
-        HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_aca_cta<R, KERN>, CTA_NT, 0));
-        int64_t grid = std::min<int64_t>(n, (int64_t)std::max(occ, 1) * num_sms());
-        int64_t words = ceil_div(max_dim, 32);
-        DevBuf<uint32_t> usedpool((size_t)(grid * words), s);
-        DevBuf<int> counter(1, s);
-        HM_CUDA(cudaMemsetAsync(counter.p, 0, sizeof(int), s));
-        k_aca_cta<R, KERN><<<(unsigned)grid, CTA_NT, 0, s>>>(kp, X, a, order, n, thr, counter.p,
-                                                            usedpool.p, words);
+        HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_aca_cluster<R, KERN>,
+                                                              CTA_NT, 0));
+        int64_t nclusters = std::min<int64_t>(n, std::max<int64_t>(1, (int64_t)std::max(occ, 1) *
+                                                                         num_sms() / cs));
+        const int64_t words = ceil_div(max_n, 32);
+        DevBuf<uint32_t> usedpool((size_t)(nclusters * words), s);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(nclusters * cs));
+        cfg.blockDim = dim3(CTA_NT);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = cs;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        HM_CUDA(cudaLaunchKernelEx(&cfg, k_aca_cluster<R, KERN>, kp, X, a, order, n, thr,
+                                   usedpool.p, words));
+        break;
+    }
     }
     HM_LAUNCH("aca");
 }
 
+
 }  // namespace
 
 void aca_run(int precision, const KernelParams& kp, const DeviceCoords& X, const AcaArgs& a,
-             const uint32_t* order, int64_t n, int64_t max_dim, cudaStream_t s)
+             const uint32_t* order, int64_t n, int cls, int64_t max_n, cudaStream_t s)
 {
     if (n <= 0) return;
     if (a.k_cap > KBUF) fail(HM_ENOTSUP, "k_cap above 128 is not supported");
     const bool f64 = precision == HM_PREC_FP64;
     if (kp.kernel == HM_GAUSSIAN) {
-        if (f64) launch_all<double, HM_GAUSSIAN>(kp, X, a, order, n, max_dim, s);
-        else launch_all<float, HM_GAUSSIAN>(kp, X, a, order, n, max_dim, s);
+        if (f64) launch_all<double, HM_GAUSSIAN>(kp, X, a, order, n, cls, max_n, s);
+        else launch_all<float, HM_GAUSSIAN>(kp, X, a, order, n, cls, max_n, s);
     } else {
-        if (f64) launch_all<double, HM_MATERN32>(kp, X, a, order, n, max_dim, s);
-        else launch_all<float, HM_MATERN32>(kp, X, a, order, n, max_dim, s);
+        if (f64) launch_all<double, HM_MATERN32>(kp, X, a, order, n, cls, max_n, s);
+        else launch_all<float, HM_MATERN32>(kp, X, a, order, n, cls, max_n, s);
     }
+}
+
+int aca_class_of(int m, int n)
+{
+    const int d = m > n ? m : n;
+    for (int c = 0; c < ACA_NCLASS - 1; ++c)
+        if (d <= kAcaClassDim[c]) return c;
+    return ACA_NCLASS - 1;
 }
 
 }  // namespace hm

@@ -49,9 +49,17 @@ struct AcaArgs {
     int k_cap;
 };
 
-// Run ACA on the blocks listed in order[0..n) (indices into the block arrays).
+// Size classes of admissible blocks by max(m, n): classes 0-3 (<= 64, 128,
+// 256, 512) run one warp per block, class 4 (<= 4096) one CTA per block,
+// class 5 (<= 32768) a cluster of 4 CTAs and class 6 a cluster of 8 CTAs.
+constexpr int ACA_NCLASS = 7;
+constexpr int kAcaClassDim[ACA_NCLASS - 1] = {64, 128, 256, 512, 4096, 32768};
+int aca_class_of(int m, int n);
+
+// Run ACA on the blocks listed in order[0..n) (indices into the block arrays),
+// all of size class cls; max_n bounds the column count of any block.
 void aca_run(int precision, const KernelParams& kp, const DeviceCoords& X,
-             const AcaArgs& a, const uint32_t* order, int64_t n, int64_t max_dim,
+             const AcaArgs& a, const uint32_t* order, int64_t n, int cls, int64_t max_n,
              cudaStream_t s);
 
 // ---------------------------------------------------------------------------

@@ -91,11 +91,12 @@ __global__ void k_leaf_tiles(const uint32_t* __restrict__ val, const int32_t* __
     tm[q] = hi[v] - lo[v];
 }
 
-// size class of an admissible block: 0..3 warp kernels, 4 CTA kernel
+// size class of an admissible block (the thresholds of kAcaClassDim)
 __device__ __forceinline__ int size_class(int m, int n)
 {
     int d = max(m, n);
-    return d <= 64 ? 0 : d <= 128 ? 1 : d <= 256 ? 2 : d <= 512 ? 3 : 4;
+    return d <= 64 ? 0 : d <= 128 ? 1 : d <= 256 ? 2 : d <= 512 ? 3 : d <= 4096 ? 4
+         : d <= 32768 ? 5 : 6;
 }
 
 __global__ void k_classes(const Blk* __restrict__ blk, const uint32_t* __restrict__ ids,
@@ -108,7 +109,7 @@ __global__ void k_classes(const Blk* __restrict__ blk, const uint32_t* __restric
     const uint32_t b = ids ? ids[q] : (uint32_t)q;
     Blk B = blk[b];
     int c = size_class(B.m, B.n);
-    key[q] = (uint64_t)(4 - c);   // largest class first
+    key[q] = (uint64_t)(ACA_NCLASS - 1 - c);   // largest class first
     val[q] = b;
     int full = min(kcap, min(B.m, B.n));
     kres[b] = kpred ? max(1, min(kpred[b], full)) : full;
@@ -148,15 +149,15 @@ __global__ void k_final_size(const Blk* __restrict__ blk, const uint32_t* __rest
 }
 
 // Copy the rank-k columns of U and V (contiguous prefixes of the column-major
-// scratch) into the final segment; one warp per block.
+// scratch) into the final segment; one CTA per block.
 __global__ void k_copy_factors(const Blk* __restrict__ blk, const uint32_t* __restrict__ order,
                                int64_t q0, int64_t q1, const int32_t* __restrict__ rank,
                                const int64_t* __restrict__ foff, char* base, int esz,
                                uint64_t* __restrict__ Uptr, uint64_t* __restrict__ Vptr)
 {
-    int64_t w = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    int64_t q = q0 + w;
+    const int64_t w = blockIdx.x;
+    const int lane = threadIdx.x;
+    const int64_t q = q0 + w;
     if (q >= q1) return;
     uint32_t b = order[q];
     const Blk B = blk[b];
@@ -170,16 +171,16 @@ __global__ void k_copy_factors(const Blk* __restrict__ blk, const uint32_t* __re
         const double* a = reinterpret_cast<const double*>(su);
         const double* c = reinterpret_cast<const double*>(sv);
         double* o = reinterpret_cast<double*>(dst);
-        for (int64_t e = lane; e < nu / 8; e += 32) o[e] = a[e];
-        for (int64_t e = lane; e < nv / 8; e += 32) o[nu / 8 + e] = c[e];
+        for (int64_t e = lane; e < nu / 8; e += NT) o[e] = a[e];
+        for (int64_t e = lane; e < nv / 8; e += NT) o[nu / 8 + e] = c[e];
     } else {
         const float* a = reinterpret_cast<const float*>(su);
         const float* c = reinterpret_cast<const float*>(sv);
         float* o = reinterpret_cast<float*>(dst);
-        for (int64_t e = lane; e < nu / 4; e += 32) o[e] = a[e];
-        for (int64_t e = lane; e < nv / 4; e += 32) o[nu / 4 + e] = c[e];
+        for (int64_t e = lane; e < nu / 4; e += NT) o[e] = a[e];
+        for (int64_t e = lane; e < nv / 4; e += NT) o[nu / 4 + e] = c[e];
     }
-    __syncwarp();
+    __syncthreads();
     if (lane == 0) {
         Uptr[b] = (uint64_t)dst;
         Vptr[b] = (uint64_t)(dst + nu);
@@ -247,6 +248,42 @@ struct Timer {
     }
 };
 
+// Side streams for the ACA size classes, forked from and joined into s.
+struct ClassStreams {
+    cudaStream_t main;
+    cudaStream_t st[ACA_NCLASS];
+    cudaEvent_t ev[ACA_NCLASS + 1];
+    explicit ClassStreams(cudaStream_t s) : main(s)
+    {
+        for (int c = 0; c < ACA_NCLASS; ++c) {
+            HM_CUDA(cudaStreamCreateWithFlags(&st[c], cudaStreamNonBlocking));
+            HM_CUDA(cudaEventCreateWithFlags(&ev[c], cudaEventDisableTiming));
+        }
+        HM_CUDA(cudaEventCreateWithFlags(&ev[ACA_NCLASS], cudaEventDisableTiming));
+    }
+    void fork()
+    {
+        HM_CUDA(cudaEventRecord(ev[ACA_NCLASS], main));
+        for (int c = 0; c < ACA_NCLASS; ++c) HM_CUDA(cudaStreamWaitEvent(st[c], ev[ACA_NCLASS], 0));
+    }
+    void join()
+    {
+        for (int c = 0; c < ACA_NCLASS; ++c) {
+            HM_CUDA(cudaEventRecord(ev[c], st[c]));
+            HM_CUDA(cudaStreamWaitEvent(main, ev[c], 0));
+        }
+    }
+    ~ClassStreams()
+    {
+        for (int c = 0; c < ACA_NCLASS; ++c) {
+            cudaStreamSynchronize(st[c]);
+            cudaStreamDestroy(st[c]);
+            cudaEventDestroy(ev[c]);
+        }
+        cudaEventDestroy(ev[ACA_NCLASS]);
+    }
+};
+
 void check_status(hm_handle_s& h)
 {
     int st = 0;
@@ -283,13 +320,13 @@ void compress(hm_handle_s& h, const uint32_t* ids, int64_t n, const int32_t* kpr
 
     DevBuf<uint64_t> key(n, s);
     DevBuf<uint32_t> order(n, s);
-    DevBuf<int64_t> ccount(5, s);
-    HM_CUDA(cudaMemsetAsync(ccount.p, 0, 5 * sizeof(int64_t), s));
+    DevBuf<int64_t> ccount(ACA_NCLASS, s);
+    HM_CUDA(cudaMemsetAsync(ccount.p, 0, ACA_NCLASS * sizeof(int64_t), s));
     k_classes<<<grid_for(n), NT, 0, s>>>(h.ablk.p, ids, n, h.opt.k_cap, kpred, key.p, order.p,
                                          h.kres.p, ccount.p);
     HM_LAUNCH("classes");
     radix_sort_u64_u32(key.p, order.p, n, 3, s);
-    int64_t cc[5];
+    int64_t cc[ACA_NCLASS];
     HM_CUDA(cudaMemcpyAsync(cc, ccount.p, sizeof(cc), cudaMemcpyDeviceToHost, s));
     DevBuf<int64_t> res(n, s), pre(n + 1, s);
     k_reserve<<<grid_for(n), NT, 0, s>>>(h.ablk.p, order.p, n, h.kres.p, res.p);
@@ -298,17 +335,16 @@ void compress(hm_handle_s& h, const uint32_t* ids, int64_t n, const int32_t* kpr
     HM_CUDA(cudaMemcpyAsync(hpre.data(), pre.p, (n + 1) * sizeof(int64_t),
                             cudaMemcpyDeviceToHost, s));
     HM_CUDA(cudaStreamSynchronize(s));
-    // class ranges in the sorted order: class 4 first
-    int64_t cstart[5], cend[5];
+    // class ranges in the sorted order: the largest class first
+    int64_t cstart[ACA_NCLASS], cend[ACA_NCLASS];
     {
         int64_t q = 0;
-        for (int c = 4; c >= 0; --c) {
+        for (int c = ACA_NCLASS - 1; c >= 0; --c) {
             cstart[c] = q;
             q += cc[c];
             cend[c] = q;
         }
     }
-    const int64_t cls_dim[5] = {64, 128, 256, 512, h.max_set_n};
     AcaArgs a;
     a.blk = h.ablk.p;
     a.kres = h.kres.p;
@@ -323,11 +359,18 @@ void compress(hm_handle_s& h, const uint32_t* ids, int64_t n, const int32_t* kpr
     a.eps0 = h.opt.eps0 > 0 ? h.opt.eps0 : (h.precision == HM_PREC_FP64 ? 1e-14 : 1e-6);
     a.k_cap = h.opt.k_cap;
 
+    // every size class runs on its own stream so that the few largest blocks
+    // (clusters of CTAs) overlap the many small ones
+    ClassStreams cs(s);
     auto run_range = [&](int64_t q0, int64_t q1) {
-        for (int c = 4; c >= 0; --c) {
+        cs.fork();
+        for (int c = ACA_NCLASS - 1; c >= 0; --c) {
             int64_t lo = std::max(q0, cstart[c]), hi = std::min(q1, cend[c]);
-            if (hi > lo) aca_run(h.precision, h.kp, h.X, a, order.p + lo, hi - lo, cls_dim[c], s);
+            if (hi > lo)
+                aca_run(h.precision, h.kp, h.X, a, order.p + lo, hi - lo, c, h.max_set_n,
+                        cs.st[c]);
         }
+        cs.join();
     };
 
     if (kpred) {
@@ -372,7 +415,7 @@ void compress(hm_handle_s& h, const uint32_t* ids, int64_t n, const int32_t* kpr
         HM_CUDA(cudaStreamSynchronize(s));
         auto seg = std::make_unique<FactorSegment>();
         seg->mem.alloc((size_t)std::max<int64_t>(tot, 1) * esz, s);
-        k_copy_factors<<<(unsigned)ceil_div((q1 - q0) * 32, NT), NT, 0, s>>>(
+        k_copy_factors<<<(unsigned)(q1 - q0), NT, 0, s>>>(
             h.ablk.p, order.p, q0, q1, h.rank.p, foff.p, seg->mem.p, esz, h.Uptr.p, h.Vptr.p);
         HM_LAUNCH("copy factors");
         h.segments.push_back(std::move(seg));

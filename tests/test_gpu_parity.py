@@ -114,12 +114,14 @@ def test_factors_match_oracle(hm, orc):
         t, s = A[b]
         U, V = H.factors(b, hi[t] - lo[t], hi[s] - lo[s])
         Uo, Vo = O.factors(b)
-        # same rank and pivots give the same cross approximation; the factors
-        # differ only by rounding (exp and fused multiply-adds differ)
+        # same rank and pivots give the same cross approximation U V^T; single
+        # late columns are normalised residuals of size ~eps and carry
+        # relative rounding differences of that order, so only the product
+        # of the factors is compared
         assert U.shape == Uo.shape
         R, Ro = U @ V.T, Uo @ Vo.T
         assert np.linalg.norm(R - Ro) <= 1e-12 * np.linalg.norm(Ro)
-        assert np.allclose(U, Uo, rtol=0, atol=1e-9 * np.abs(Uo).max())
+        assert np.array_equal(U.argmax(0), Uo.argmax(0))
 
 
 @pytest.mark.parametrize("near", ["bf16x2", "fp32"])
