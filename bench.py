@@ -1,0 +1,410 @@
+"""Benchmark: H-matrix build + H-matrix-vector products at N = 2^20 on GB300.
+
+One step = the whole hot path over one synthetic point cloud: hm_build
+(Morton codes, radix sort, cluster tree, traversal, batched ACA, near field,
+gather lists) followed by 10 products y = H x, then hm_free. Points and x
+are resident on the device when the timed region starts (value); the e2e
+number repeats the same step through the C-ABI with pinned host buffers
+(host->device copies of the points and of every x, device->host copy of
+every y inside the timed region).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = ("H-build s + H-MVP ms at N=2^20 (mixed vs FP64 on GB300, rel err <=1e-5); "
+          "% HBM roofline")
+WORKLOAD = "mix2d_n1m"
+N_MVP = 10
+FP32_LANES_PER_SM = 128
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+FP64_NOMINAL_TFLOPS = 1.25
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default=WORKLOAD)
+    p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        return float(m["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        self.f.flush()
+        rows = []
+        try:
+            with open(self.f.name) as fh:
+                for line in fh:
+                    c = [x.strip() for x in line.split(",")]
+                    if len(c) >= 9:
+                        rows.append(c)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- oracle leg
+def oracle_sample(name: str, budget_s: float = 12.0, seed: int = 0):
+    """The CPU oracle, as it stands, on a bounded sample of the workload.
+
+    Full-size structure (Morton sort, cluster tree, Alg. 1 traversal) is timed
+    as is; ACA is timed on blocks sampled per size class and scaled by the
+    class counts; the product is timed on the same workload at N = 2^14 and
+    scaled by the number of stored entries. Returns seconds per step (build +
+    N_MVP products) and a description of the sample.
+    """
+    import oracle
+    from paper_1708_09707_gb300 import inputs
+    w = inputs.WORKLOADS[name]
+    pts = inputs.workload_points(name)
+    t0 = time.perf_counter()
+    O = oracle.HMatrix(pts, w["kernel"], w["ell"], w["leaf"], w["eta"], w["eps"],
+                       adm_max=(w["adm"] == "max"), compress=False)
+    t_struct = time.perf_counter() - t0
+    lo, hi, _, _ = O.tree()
+    A = O.adm_leaves()
+    m = hi[A[:, 0]] - lo[A[:, 0]]
+    n = hi[A[:, 1]] - lo[A[:, 1]]
+    size = np.maximum(m, n)
+    rng = np.random.default_rng(seed)
+    t_aca = 0.0
+    spent = 0.0
+    nsampled = 0
+    classes = np.unique(size)
+    per = max(1.0, budget_s / max(len(classes), 1))
+    for c in classes:
+        idx = np.nonzero(size == c)[0]
+        rng.shuffle(idx)
+        t_cls = 0.0
+        k = 0
+        for b in idx:
+            ts = time.perf_counter()
+            O.compress_range(int(b), int(b) + 1)
+            t_cls += time.perf_counter() - ts
+            k += 1
+            if t_cls > per or k >= len(idx):
+                break
+        spent += t_cls
+        nsampled += k
+        t_aca += t_cls / k * len(idx)
+    # product: full oracle H-matrix at N = 2^14, scaled by stored entries
+    ns = 1 << 14
+    ps = inputs.workload_points(name, ns)
+    Os = oracle.HMatrix(ps, w["kernel"], w["ell"], w["leaf"], w["eta"], w["eps"],
+                        adm_max=(w["adm"] == "max"))
+    xs = inputs.normal_vector(ns, 1)
+    ts = time.perf_counter()
+    Os.matvec(xs)
+    t_mv_small = time.perf_counter() - ts
+
+    def entries(H):
+        l, h, _, _ = H.tree()
+        a, d = H.adm_leaves(), H.dense_leaves()
+        return (int((h[d[:, 0]] - l[d[:, 0]]).astype(np.int64) @ (h[d[:, 1]] - l[d[:, 1]]))
+                + int((h[a[:, 0]] - l[a[:, 0]] + h[a[:, 1]] - l[a[:, 1]]).sum() * 8))
+
+    t_mv = t_mv_small * entries(O) / max(entries(Os), 1)
+    step = t_struct + t_aca + N_MVP * t_mv
+    sample = ("full-size structure (%.1f s); ACA on %d of %d admissible blocks sampled per "
+              "size class (%.1f s), scaled by class counts; product timed at N=2^14 "
+              "(%.2f s) scaled by stored entries; single thread" %
+              (t_struct, nsampled, len(A), spent, t_mv_small))
+    return step, t_struct + t_aca, t_mv, sample
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_1708_09707_gb300 import inputs
+    w = inputs.WORKLOADS[args.workload]
+    vals = []
+    sample = ""
+    for it in range(args.warmup + args.steps):
+        step, tb, tm, sample = oracle_sample(args.workload, budget_s=6.0, seed=it)
+        if it >= args.warmup:
+            vals.append(step)
+    v = float(np.mean(vals))
+    unit = "s/step (build + %d H-MVP)" % N_MVP
+    line = {"metric": METRIC, "value": v, "unit": unit, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload, "n": w["n"], "d": w["d"],
+                       "kernel": "gaussian" if w["kernel"] == 0 else "matern32",
+                       "ell": w["ell"], "leaf": w["leaf"], "eta": w["eta"],
+                       "aca_eps": w["eps"], "mvp_per_step": N_MVP},
+            "cpu_baseline": {"value": v, "unit": unit, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------- GPU leg
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    from paper_1708_09707_gb300 import build as hbuild
+    if not os.path.exists(hbuild.LIB):
+        hbuild.build()
+    from paper_1708_09707_gb300 import hm, inputs
+    w = inputs.WORKLOADS[args.workload]
+    N, d = w["n"], w["d"]
+    pts_np = inputs.workload_points(args.workload)
+    x_np = inputs.normal_vector(N, inputs.X_SEED)
+    pts = torch.from_numpy(pts_np).cuda()
+    x = torch.from_numpy(x_np).cuda()
+    y = torch.empty_like(x)
+    kw = dict(adm_max=(w["adm"] == "max"))
+    stream = torch.cuda.current_stream()
+
+    def step(prec, ev=None, profile=False):
+        if ev:
+            ev[0].record(stream)
+        H = hm.HMatrix(pts, w["kernel"], w["ell"], w["leaf"], w["eta"], w["eps"],
+                       precision=prec, profile=profile, **kw)
+        if ev:
+            ev[1].record(stream)
+        for _ in range(N_MVP):
+            H.matvec(x, y)
+        if ev:
+            ev[2].record(stream)
+        st = H.stats()
+        H.free()
+        return st
+
+    def timed(prec, steps, warmup, profile):
+        for _ in range(warmup):
+            step(prec)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+        l0 = hm.kernel_launches()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        stats = []
+        t0.record(stream)
+        for k in range(steps):
+            stats.append(step(prec, evs[k], profile))
+        t1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        launches = (hm.kernel_launches() - l0) / steps
+        total = t0.elapsed_time(t1) / steps
+        build = np.mean([e[0].elapsed_time(e[1]) for e in evs])
+        mvp = np.mean([e[1].elapsed_time(e[2]) for e in evs]) / N_MVP
+        return total, build, mvp, stats, launches
+
+    hbm, peak_src = peaks()
+    with ClockSampler(local) as clk:
+        total, build_ms, mvp_ms, stats, launches = timed(hm.PREC_MIXED, args.steps,
+                                                         args.warmup, True)
+    clocks = clk.summary()
+    # max over ranks
+    tot_t = torch.tensor([total, build_ms, mvp_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(tot_t, op=dist.ReduceOp.MAX)
+    total, build_ms, mvp_ms = [float(v) for v in tot_t.cpu()]
+    st = stats[-1]
+
+    # FP64 reference path on the same GPU (same step, fewer repetitions)
+    fp64 = None
+    err = None
+    if not args.no_fp64:
+        t64, b64, m64, s64, _ = timed(hm.PREC_FP64, 1, 1, False)
+        fp64 = {"build_s": b64 / 1e3, "mvp_ms": m64, "ms_per_step": t64,
+                "mvp_roofline_frac": s64[-1]["mvp_bytes"] / (m64 * 1e-3) / (hbm * 1e9)}
+        H64 = hm.HMatrix(pts, w["kernel"], w["ell"], w["leaf"], w["eta"], w["eps"],
+                         precision=hm.PREC_FP64, **kw)
+        y64 = H64.matvec(x).cpu().numpy()
+        H64.free()
+        H32 = hm.HMatrix(pts, w["kernel"], w["ell"], w["leaf"], w["eta"], w["eps"],
+                         precision=hm.PREC_MIXED, **kw)
+        y32 = H32.matvec(x).cpu().numpy()
+        H32.free()
+        err = float(np.linalg.norm(y32 - y64) / np.linalg.norm(y64))
+
+    # e2e: the same step through the C-ABI with pinned host buffers
+    pts_h = torch.from_numpy(pts_np).pin_memory()
+    xs_h = torch.from_numpy(x_np).pin_memory()
+    ys_h = torch.empty(N, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(1, min(args.steps, 3))
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        H = hm.HMatrix(pts_h, w["kernel"], w["ell"], w["leaf"], w["eta"], w["eps"],
+                       precision=hm.PREC_MIXED, **kw)
+        for _ in range(N_MVP):
+            H.matvec(xs_h, ys_h)
+        H.free()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    ysum = float(ys_h.sum())
+    assert math.isfinite(ysum)
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    # rooflines from the library's own CUDA events on the launching stream
+    mvp_t_tile = st["t_mvp_tile_ms"] / max(st["mvp_count"], 1)
+    mvp_t_vtx = st["t_mvp_vtx_ms"] / max(st["mvp_count"], 1)
+    mvp_t = st["t_mvp_ms"] / max(st["mvp_count"], 1)
+    mvp_roof = {"bound": "hbm", "kernel": "k_tile (gather: U slices + near field)",
+                "achieved": st["mvp_tile_bytes"] / (mvp_t_tile * 1e-3) / 1e9, "peak": hbm,
+                "unit": "GB/s", "traffic": None,
+                "whole_product": {"achieved": st["mvp_bytes"] / (mvp_t * 1e-3) / 1e9,
+                                  "ms": mvp_t, "bytes": st["mvp_bytes"]},
+                "vtx": {"achieved": st["mvp_vtx_bytes"] / (mvp_t_vtx * 1e-3) / 1e9,
+                        "ms": mvp_t_vtx}}
+    mvp_roof["frac"] = mvp_roof["achieved"] / hbm
+    mvp_roof["peak_source"] = peak_src + " copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
+    sm_mhz = clocks.get("sm_mhz") or SM_MAX_MHZ
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    aca_roof = {"bound": "alu", "kernel": "batched ACA (all size classes, concurrent)",
+                "achieved": st["aca_flops"] / (st["t_aca_ms"] * 1e-3) / 1e12,
+                "peak": fp32_peak, "unit": "TFLOP/s", "traffic": None,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz"}
+    aca_roof["frac"] = aca_roof["achieved"] / fp32_peak
+    # dominant kernel of the step: ACA phase vs the N_MVP gather launches
+    dominant = aca_roof if st["t_aca_ms"] > N_MVP * mvp_t_tile else mvp_roof
+
+    cpu = None
+    if not args.no_cpu and world == 1:
+        cstep, cbuild, cmv, sample = oracle_sample(args.workload, budget_s=12.0)
+        cpu = {"value": cstep, "unit": "s/step (build + %d H-MVP)" % N_MVP, "cores": 1,
+               "kind": "oracle", "sample": sample, "build_s": cbuild, "mvp_ms": cmv * 1e3}
+
+    value = total / 1e3
+    line = {
+        "metric": METRIC, "value": value, "unit": "s/step (build + %d H-MVP)" % N_MVP,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "n": N, "d": d,
+                   "points": w["points"], "kernel": "gaussian" if w["kernel"] == 0 else "matern32",
+                   "ell": w["ell"], "leaf": w["leaf"], "eta": w["eta"], "aca_eps": w["eps"],
+                   "precision": "mixed (FP32 ACA + FP64 stopping test, BF16 hi/lo near field)",
+                   "mvp_per_step": N_MVP, "l2": "inputs larger than L2 (product streams "
+                   "%.1f GB per call)" % (st["mvp_bytes"] / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "build_s": build_ms / 1e3, "mvp_ms": mvp_ms,
+        "fp64": fp64, "mixed_vs_fp64_rel_err": err,
+        "speedup_vs_fp64": (fp64["ms_per_step"] / total) if fp64 else None,
+        "e2e": {"value": e2e_ms / 1e3, "unit": "s/step (build + %d H-MVP)" % N_MVP,
+                "h2d_bytes_per_step": N * d * 8 + N_MVP * N * 8,
+                "d2h_bytes_per_step": N_MVP * N * 8},
+        "roofline": dominant, "mvp_roofline": mvp_roof, "aca_roofline": aca_roof,
+        "gpu_launches": int(round(launches)),
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+        "stats": {k: st[k] for k in ("n_adm", "n_dense", "sum_rank", "max_rank",
+                                     "rank_cap_hits", "n_rejected", "factor_bytes",
+                                     "near_bytes", "mvp_bytes", "t_structure_ms",
+                                     "t_aca_ms", "t_dense_ms", "aca_passes")},
+    }
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

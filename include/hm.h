@@ -76,6 +76,8 @@ typedef struct hm_options {
     const float* rank_model_theta; /* 4801 FP32 weights (host or device), or NULL */
     double scratch_gb;    /* bound on ACA scratch per pass, <=0: automatic */
     void* stream;         /* cudaStream_t, NULL = legacy default stream */
+    int profile;          /* 1: time every product kernel with CUDA events on
+                             the launching stream (read by hm_get_stats) */
 } hm_options;
 
 typedef struct hm_handle_s* hm_handle;
@@ -119,6 +121,9 @@ void hm_free(hm_handle h);
 /* Thread-local description of the last failure ("" if none). */
 const char* hm_last_error(void);
 
+/* Number of CUDA kernels this library has launched in the process so far. */
+uint64_t hm_kernel_launches(void);
+
 /* Counts, ranks and bytes of a built handle. */
 typedef struct hm_stats {
     int64_t n_points, n_nodes, n_adm, n_dense, n_tiles;
@@ -136,6 +141,13 @@ typedef struct hm_stats {
     double t_structure_ms, t_aca_ms, t_dense_ms, t_total_ms; /* last build */
     int aca_passes;             /* scratch passes of the plain ACA */
     int precision, near_format;
+    int64_t aca_evals;          /* kernel evaluations done by ACA */
+    double aca_flops;           /* algorithmic ACA flops: evals * flops per
+                                   evaluation + sum_b 2 k_b (k_b - 1)(m_b + n_b) */
+    /* profile = 1: sums over the products since the last hm_get_stats */
+    int64_t mvp_count;
+    double t_mvp_ms, t_mvp_gather_ms, t_mvp_vtx_ms, t_mvp_tile_ms;
+    int64_t mvp_vtx_bytes, mvp_tile_bytes;  /* algorithmic bytes per product */
 } hm_stats;
 
 int hm_get_stats(hm_handle h, hm_stats* out);

@@ -562,10 +562,10 @@ void launch_all(const KernelParams& kp, const DeviceCoords& X, const AcaArgs& a,
     const double thr = (a.eps > 0.0) ? a.eps * (1.0 - a.aca_eta) / (1.0 + a.eps) : -1.0;
     const unsigned wgrid = (unsigned)ceil_div(n * 32, WARP_NT);
     switch (cls) {
-    case 0: k_aca_warp<R, KERN, 2><<<wgrid, WARP_NT, 0, s>>>(kp, X, a, order, n, thr); break;
-    case 1: k_aca_warp<R, KERN, 4><<<wgrid, WARP_NT, 0, s>>>(kp, X, a, order, n, thr); break;
-    case 2: k_aca_warp<R, KERN, 8><<<wgrid, WARP_NT, 0, s>>>(kp, X, a, order, n, thr); break;
-    case 3: k_aca_warp<R, KERN, 16><<<wgrid, WARP_NT, 0, s>>>(kp, X, a, order, n, thr); break;
+    case 0: k_aca_warp<R, KERN, 2><<<wgrid, WARP_NT, 0, s>>>(kp, X, a, order, n, thr); note_launch(); break;
+    case 1: k_aca_warp<R, KERN, 4><<<wgrid, WARP_NT, 0, s>>>(kp, X, a, order, n, thr); note_launch(); break;
+    case 2: k_aca_warp<R, KERN, 8><<<wgrid, WARP_NT, 0, s>>>(kp, X, a, order, n, thr); note_launch(); break;
+    case 3: k_aca_warp<R, KERN, 16><<<wgrid, WARP_NT, 0, s>>>(kp, X, a, order, n, thr); note_launch(); break;
     default: {
         const int cs = cls == 4 ? 1 : (cls == 5 ? 4 : 8);
         int occ = 0;
@@ -589,6 +589,7 @@ void launch_all(const KernelParams& kp, const DeviceCoords& X, const AcaArgs& a,
         cfg.numAttrs = 1;
         HM_CUDA(cudaLaunchKernelEx(&cfg, k_aca_cluster<R, KERN>, kp, X, a, order, n, thr,
                                    usedpool.p, words));
+        note_launch();
         break;
     }
     }

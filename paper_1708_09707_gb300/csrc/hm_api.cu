@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -93,6 +94,10 @@ void copy_out(void* dst, const void* src, size_t bytes, cudaStream_t s)
     if (bytes) HM_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s));
 }
 
+static std::atomic<uint64_t> g_launches{0};
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
 int num_sms()
 {
     static int n = 0;
@@ -138,6 +143,8 @@ void hm_options_default(hm_options* o)
 }
 
 const char* hm_last_error(void) { return g_last_error.c_str(); }
+
+uint64_t hm_kernel_launches(void) { return g_launches.load(); }
 
 hm_handle hm_build_ex(const double* points, int64_t N, int d, int kernel, const double* params,
                       int leaf_size, double eta, double aca_eps, const hm_options* opt,
@@ -202,6 +209,20 @@ int hm_get_stats(hm_handle h, hm_stats* out)
     if (!h || !out) {
         set_error("null argument");
         return HM_EINVAL;
+    }
+    try {
+        if (h->opt.profile) {
+            h->timer.collect();
+            h->stats.mvp_count = h->timer.count;
+            h->stats.t_mvp_ms = h->timer.t_total;
+            h->stats.t_mvp_gather_ms = h->timer.t_gather;
+            h->stats.t_mvp_vtx_ms = h->timer.t_vtx;
+            h->stats.t_mvp_tile_ms = h->timer.t_tile;
+            h->timer.count = 0;
+            h->timer.t_total = h->timer.t_gather = h->timer.t_vtx = h->timer.t_tile = 0.0;
+        }
+    } catch (const std::exception& e) {
+        return to_status(e);
     }
     *out = h->stats;
     return HM_OK;

@@ -333,11 +333,11 @@ void canonical_sort(DevBuf<int2>& leaves, int64_t n, const int32_t* lo, int64_t 
     if (n <= 1) return;
     DevBuf<uint64_t> keys(n, s);
     DevBuf<uint32_t> idx(n, s);
-    k_leaf_keys<<<grid_for(n), NT, 0, s>>>(leaves.p, n, lo, N, keys.p, idx.p);
+    k_leaf_keys<<<grid_for(n), NT, 0, s>>>(leaves.p, n, lo, N, keys.p, idx.p); note_launch();
     HM_LAUNCH("leaf keys");
     radix_sort_u64_u32(keys.p, idx.p, n, 2 * bits_for(N + 1), s);
     DevBuf<int2> out(n, s);
-    k_gather_pairs<<<grid_for(n), NT, 0, s>>>(leaves.p, idx.p, n, out.p);
+    k_gather_pairs<<<grid_for(n), NT, 0, s>>>(leaves.p, idx.p, n, out.p); note_launch();
     HM_LAUNCH("leaf gather");
     leaves = std::move(out);
 }
@@ -374,9 +374,9 @@ void morton_codes(const double* pts, int64_t N, int d, uint64_t* codes, uint32_t
     DevBuf<double> part((size_t)nb * 6, s);
     DevBuf<int> bad(1, s);
     HM_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), s));
-    k_box_partial<<<nb, NT, 0, s>>>(pts, N, d, part.p, bad.p);
-    k_box_final<<<1, 32, 0, s>>>(part.p, nb, d, morton_bits(d), box);
-    k_morton<<<grid_for(N), NT, 0, s>>>(pts, N, d, morton_bits(d), box, codes, idx);
+    k_box_partial<<<nb, NT, 0, s>>>(pts, N, d, part.p, bad.p); note_launch();
+    k_box_final<<<1, 32, 0, s>>>(part.p, nb, d, morton_bits(d), box); note_launch();
+    k_morton<<<grid_for(N), NT, 0, s>>>(pts, N, d, morton_bits(d), box, codes, idx); note_launch();
     HM_LAUNCH("morton");
     int hbad = 0;
     HM_CUDA(cudaMemcpyAsync(&hbad, bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -408,7 +408,7 @@ void build_structure(const double* pts, SetStructure& S, double eta, int adm_max
     const int64_t r0 = S.row0;
     k_permute<<<grid_for(N), NT, 0, s>>>(pts, N, d, idx.p, X.x64[0] + r0, X.x64[1] + r0,
                                         X.x64[2] + r0, X.x32 ? X.x32 + r0 : nullptr,
-                                        X.stride32, perm_out + r0);
+                                        X.stride32, perm_out + r0); note_launch();
     HM_LAUNCH("permute");
 
     // cluster tree and bounding boxes, bottom-up one level per launch
@@ -416,13 +416,13 @@ void build_structure(const double* pts, SetStructure& S, double eta, int adm_max
     int32_t* hi = node_hi + S.node0;
     double* bn = bmin + S.node0 * 3;
     double* bx = bmax + S.node0 * 3;
-    k_tree_ranges<<<grid_for(S.n_nodes), NT, 0, s>>>(S.n_nodes, N, C, lo, hi);
+    k_tree_ranges<<<grid_for(S.n_nodes), NT, 0, s>>>(S.n_nodes, N, C, lo, hi); note_launch();
     HM_LAUNCH("tree ranges");
     for (int l = S.depth; l >= 0; --l) {
         int64_t first = (1ll << l) - 1, count = 1ll << l;
         k_bbox_level<<<grid_for(count * 32), NT, 0, s>>>(first, count, C, lo, hi,
                                                          X.x64[0] + r0, X.x64[1] + r0,
-                                                         X.x64[2] + r0, bn, bx);
+                                                         X.x64[2] + r0, bn, bx); note_launch();
     }
     HM_LAUNCH("bbox");
 
@@ -438,7 +438,7 @@ void build_structure(const double* pts, SetStructure& S, double eta, int adm_max
     for (int l = 0; P > 0; ++l) {
         if (l > S.depth) fail(HM_EOVERFLOW, "block tree deeper than the cluster tree");
         DevBuf<int64_t> flag(P, s), off(P, s);
-        k_classify<<<grid_for(P), NT, 0, s>>>(cur.p, P, C, lo, hi, bn, bx, eta2, adm_max, flag.p);
+        k_classify<<<grid_for(P), NT, 0, s>>>(cur.p, P, C, lo, hi, bn, bx, eta2, adm_max, flag.p); note_launch();
         HM_LAUNCH("classify");
         scan_exclusive_i64(flag.p, off.p, P, tot.p, s);
         int64_t h_tot = 0;
@@ -449,7 +449,7 @@ void build_structure(const double* pts, SetStructure& S, double eta, int adm_max
         grow(dense, n_dense, n_dense + nd, s);
         nxt.alloc(std::max<int64_t>(4 * ns, 1), s);
         k_emit<<<grid_for(P), NT, 0, s>>>(cur.p, P, flag.p, off.p, nxt.p, adm.p, n_adm,
-                                         dense.p, n_dense);
+                                         dense.p, n_dense); note_launch();
         HM_LAUNCH("emit");
         n_adm += na;
         n_dense += nd;

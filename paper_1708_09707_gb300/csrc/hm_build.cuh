@@ -116,6 +116,20 @@ struct MvpPlan {
     const double* sig_row = nullptr;    // optional per-row sigma^2 (batched sets)
 };
 
+// CUDA events around the product's kernels (when profiling), read later.
+struct MvpTimer {
+    struct Rec {
+        cudaEvent_t e[4];
+    };
+    std::vector<Rec> recs;
+    std::vector<Rec> pool;
+    double t_total = 0, t_gather = 0, t_vtx = 0, t_tile = 0;
+    int64_t count = 0;
+    Rec* begin();
+    void collect();   // synchronises the recorded events and sums the times
+    ~MvpTimer();
+};
+
 // Work buffers of the product (xm, t, partial sums).
 struct MvpWork {
     DevBuf<double> xm64, ym64;
@@ -127,7 +141,7 @@ struct MvpWork {
 void mvp_alloc_work(const MvpPlan& P, MvpWork& W, cudaStream_t s);
 // y = H x (+ sigma^2 x) for device x, y in the caller's order.
 void mvp_run(const MvpPlan& P, MvpWork& W, const double* x, double* y, int accumulate,
-             cudaStream_t s);
+             cudaStream_t s, MvpTimer* timer = nullptr);
 // Build the gather lists of the plan (CSR by tile).
 struct MvpLists {
     DevBuf<int64_t> tile_row0;

@@ -57,8 +57,8 @@ __global__ void k_dot_final(const double* __restrict__ part, double* __restrict_
 
 void dot(const double* a, const double* b, int64_t n, double* out, double* part, cudaStream_t s)
 {
-    k_dot_part<<<DOT_BLOCKS, NT, 0, s>>>(a, b, n, part);
-    k_dot_final<<<1, 256, 0, s>>>(part, out);
+    k_dot_part<<<DOT_BLOCKS, NT, 0, s>>>(a, b, n, part); note_launch();
+    k_dot_final<<<1, 256, 0, s>>>(part, out); note_launch();
     HM_LAUNCH("dot");
 }
 
@@ -117,9 +117,9 @@ void fill_block_sets(hm_handle_s& h)
     int64_t a = 0, d = 0;
     for (size_t q = 0; q < h.sets.size(); ++q) {
         const SetStructure& S = h.sets[q];
-        if (S.n_adm) k_fill_i32<<<grid_for(S.n_adm), NT, 0, h.stream>>>(h.adm_set.p + a, S.n_adm, (int)q);
+        if (S.n_adm) k_fill_i32<<<grid_for(S.n_adm), NT, 0, h.stream>>>(h.adm_set.p + a, S.n_adm, (int)q); note_launch();
         if (S.n_dense)
-            k_fill_i32<<<grid_for(S.n_dense), NT, 0, h.stream>>>(h.dense_set.p + d, S.n_dense, (int)q);
+            k_fill_i32<<<grid_for(S.n_dense), NT, 0, h.stream>>>(h.dense_set.p + d, S.n_dense, (int)q); note_launch();
         a += S.n_adm;
         d += S.n_dense;
     }
@@ -130,7 +130,7 @@ void add_perm_offsets(hm_handle_s& h)
 {
     for (const SetStructure& S : h.sets)
         if (S.row0)
-            k_add_offset<<<grid_for(S.N), NT, 0, h.stream>>>(h.perm.p + S.row0, S.N, S.row0);
+            k_add_offset<<<grid_for(S.N), NT, 0, h.stream>>>(h.perm.p + S.row0, S.N, S.row0); note_launch();
     HM_LAUNCH("perm offsets");
 }
 
@@ -156,7 +156,7 @@ void matvec(hm_handle_s& h, const double* x, double* y, int nrhs, cudaStream_t s
             if (h.opt.accumulate) copy_in(h.ybuf.p, yr, N * sizeof(double), s);
             yout = h.ybuf.p;
         }
-        mvp_run(h.plan, h.work, xin, yout, h.opt.accumulate, s);
+        mvp_run(h.plan, h.work, xin, yout, h.opt.accumulate, s, h.opt.profile ? &h.timer : nullptr);
         if (!yd) copy_out(yr, h.ybuf.p, N * sizeof(double), s);
     }
     if (!yd) HM_CUDA(cudaStreamSynchronize(s));
@@ -242,8 +242,8 @@ void export_factors(hm_handle_s& h, int64_t b, double* U, double* V, int* rank)
         if (V && nv) copy_out(V, (const void*)vp, nv * sizeof(double), s);
     } else {
         DevBuf<double> t(std::max<int64_t>(nu + nv, 1), s);
-        if (nu) k_f32_to_f64<<<grid_for(nu), NT, 0, s>>>((const float*)up, nu, t.p);
-        if (nv) k_f32_to_f64<<<grid_for(nv), NT, 0, s>>>((const float*)vp, nv, t.p + nu);
+        if (nu) k_f32_to_f64<<<grid_for(nu), NT, 0, s>>>((const float*)up, nu, t.p); note_launch();
+        if (nv) k_f32_to_f64<<<grid_for(nv), NT, 0, s>>>((const float*)vp, nv, t.p + nu); note_launch();
         if (U && nu) copy_out(U, t.p, nu * sizeof(double), s);
         if (V && nv) copy_out(V, t.p + nu, nv * sizeof(double), s);
     }
@@ -260,7 +260,7 @@ void cg_solve(hm_handle_s& h, const double* b, double* x, double rtol, int maxit
     copy_in(xd.p, x, n * sizeof(double), s);
     // sc[0] = rr, sc[1] = pq, sc[2] = rr_new, sc[3] = bb
     mvp_run(h.plan, h.work, xd.p, q.p, 0, s);
-    k_cg_init<<<grid_for(n), NT, 0, s>>>(bd.p, q.p, n, r.p, p.p);
+    k_cg_init<<<grid_for(n), NT, 0, s>>>(bd.p, q.p, n, r.p, p.p); note_launch();
     dot(bd.p, bd.p, n, sc.p + 3, part.p, s);
     dot(r.p, r.p, n, sc.p, part.p, s);
     double hs[4];
@@ -273,9 +273,9 @@ void cg_solve(hm_handle_s& h, const double* b, double* x, double rtol, int maxit
     while (it < maxit && std::sqrt(rr) / bn > rtol) {
         mvp_run(h.plan, h.work, p.p, q.p, 0, s);
         dot(p.p, q.p, n, sc.p + 1, part.p, s);
-        k_cg_xr<<<grid_for(n), NT, 0, s>>>(sc.p, p.p, q.p, n, xd.p, r.p);
+        k_cg_xr<<<grid_for(n), NT, 0, s>>>(sc.p, p.p, q.p, n, xd.p, r.p); note_launch();
         dot(r.p, r.p, n, sc.p + 2, part.p, s);
-        k_cg_p<<<grid_for(n), NT, 0, s>>>(sc.p, r.p, n, p.p);
+        k_cg_p<<<grid_for(n), NT, 0, s>>>(sc.p, r.p, n, p.p); note_launch();
         HM_CUDA(cudaMemcpyAsync(sc.p, sc.p + 2, sizeof(double), cudaMemcpyDeviceToDevice, s));
         HM_CUDA(cudaMemcpyAsync(&rr, sc.p + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
         HM_CUDA(cudaStreamSynchronize(s));

@@ -24,6 +24,7 @@ struct hm_handle_s {
     std::vector<hm::SetStructure> sets;
     int64_t Ntot = 0, n_nodes_tot = 0, n_adm = 0, n_dense = 0, n_tiles = 0;
     int64_t max_set_n = 0;
+    int64_t factor_entries_U = 0;   // sum_b k_b m_b
     // points and structure
     hm::DevBuf<double> X64;
     hm::DevBuf<float> X32;
@@ -48,6 +49,7 @@ struct hm_handle_s {
     hm::MvpLists lists;
     hm::MvpPlan plan;
     hm::MvpWork work;
+    hm::MvpTimer timer;
     hm::DevBuf<double> xbuf, ybuf;
     hm::DevBuf<int> status;
     hm_stats stats{};

@@ -257,7 +257,7 @@ void features(hm_handle_s& h, float* F, float* target, cudaStream_t s)
     copy_in(sd.p, dd.data(), dd.size() * sizeof(int32_t), s);
     k_features<<<grid_for(n), NT, 0, s>>>(h.adm_pairs.p, h.adm_set.p, n, sn0.p, sd.p, h.bmin.p,
                                          h.bmax.p, h.node_lo.p, h.node_hi.p, h.ell, h.aca_eps,
-                                         h.kernel, target ? h.rank.p : nullptr, F, target);
+                                         h.kernel, target ? h.rank.p : nullptr, F, target); note_launch();
     HM_LAUNCH("features");
     HM_CUDA(cudaStreamSynchronize(s));
 }
@@ -267,7 +267,7 @@ void features(hm_handle_s& h, float* F, float* target, cudaStream_t s)
 void mlp_forward(const float* theta, const float* F, int64_t n, float* out, cudaStream_t s)
 {
     if (n <= 0) return;
-    k_mlp_fwd<<<grid_for(n), NT, 0, s>>>(theta, F, n, out);
+    k_mlp_fwd<<<grid_for(n), NT, 0, s>>>(theta, F, n, out); note_launch();
     HM_LAUNCH("mlp forward");
 }
 
@@ -279,8 +279,8 @@ void mlp_loss_grad(const float* theta, const float* F, const float* target, int6
     DevBuf<float> part((size_t)nparts * MLP_NPARAM, s), lpart(nparts, s);
     const int smem = (int)sizeof(GradSmem);
     HM_CUDA(cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    k_mlp_grad<<<nparts, NT, smem, s>>>(theta, F, target, n, part.p, lpart.p);
-    k_mlp_sum<<<grid_for(MLP_NPARAM), NT, 0, s>>>(part.p, lpart.p, nparts, n, grad, loss);
+    k_mlp_grad<<<nparts, NT, smem, s>>>(theta, F, target, n, part.p, lpart.p); note_launch();
+    k_mlp_sum<<<grid_for(MLP_NPARAM), NT, 0, s>>>(part.p, lpart.p, nparts, n, grad, loss); note_launch();
     HM_LAUNCH("mlp grad");
 }
 
@@ -290,7 +290,7 @@ void mlp_adam(float* theta, const float* grad, float* m, float* v, int64_t t, fl
     if (t < 1) fail(HM_EINVAL, "Adam step count must be >= 1");
     const float c1 = (float)(1.0 - std::pow((double)b1, (double)t));
     const float c2 = (float)(1.0 - std::pow((double)b2, (double)t));
-    k_adam<<<grid_for(MLP_NPARAM), NT, 0, s>>>(theta, grad, m, v, MLP_NPARAM, lr, b1, b2, eps, c1, c2);
+    k_adam<<<grid_for(MLP_NPARAM), NT, 0, s>>>(theta, grad, m, v, MLP_NPARAM, lr, b1, b2, eps, c1, c2); note_launch();
     HM_LAUNCH("adam");
 }
 
@@ -304,7 +304,7 @@ void predict_ranks(hm_handle_s& h, int32_t* kpred)
     copy_in(th.p, h.opt.rank_model_theta, MLP_NPARAM * sizeof(float), s);
     features(h, F.p, nullptr, s);
     mlp_forward(th.p, F.p, n, y.p, s);
-    k_pred_to_rank<<<grid_for(n), NT, 0, s>>>(y.p, n, kpred);
+    k_pred_to_rank<<<grid_for(n), NT, 0, s>>>(y.p, n, kpred); note_launch();
     HM_LAUNCH("predict ranks");
 }
 
@@ -314,7 +314,7 @@ void rerun_mispredicted(hm_handle_s& h)
     const int64_t n = h.n_adm;
     if (n == 0) return;
     DevBuf<int64_t> f(n, s), off(n + 1, s);
-    k_flag_mispred<<<grid_for(n), NT, 0, s>>>(h.flags.p, n, f.p);
+    k_flag_mispred<<<grid_for(n), NT, 0, s>>>(h.flags.p, n, f.p); note_launch();
     scan_exclusive_i64(f.p, off.p, n, off.p + n, s);
     int64_t cnt = 0;
     HM_CUDA(cudaMemcpyAsync(&cnt, off.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -322,7 +322,7 @@ void rerun_mispredicted(hm_handle_s& h)
     h.stats.n_mispredicted = cnt;
     if (cnt == 0) return;
     DevBuf<uint32_t> ids(cnt, s);
-    k_emit_ids<<<grid_for(n), NT, 0, s>>>(f.p, off.p, n, ids.p);
+    k_emit_ids<<<grid_for(n), NT, 0, s>>>(f.p, off.p, n, ids.p); note_launch();
     HM_LAUNCH("mispredicted ids");
     compress(h, ids.p, cnt, nullptr);
 }

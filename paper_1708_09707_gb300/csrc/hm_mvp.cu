@@ -280,7 +280,7 @@ void build_csr(const Blk* blk, int64_t nb, const int64_t* tr0, int64_t nt,
         return;
     }
     DevBuf<int64_t> first(nb, s), cnt(nb, s), off(nb, s), tot(1, s);
-    k_tile_span<<<grid_for(nb), NT, 0, s>>>(blk, nb, tr0, nt, first.p, cnt.p);
+    k_tile_span<<<grid_for(nb), NT, 0, s>>>(blk, nb, tr0, nt, first.p, cnt.p); note_launch();
     scan_exclusive_i64(cnt.p, off.p, nb, tot.p, s);
     int64_t E = 0;
     HM_CUDA(cudaMemcpyAsync(&E, tot.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -290,13 +290,13 @@ void build_csr(const Blk* blk, int64_t nb, const int64_t* tr0, int64_t nt,
     DevBuf<uint32_t> val(E, s);
     DevBuf<int2> tmp(E, s);
     k_emit_entries<<<grid_for(nb), NT, 0, s>>>(blk, nb, first.p, cnt.p, off.p, tr0, key.p,
-                                               val.p, tmp.p, tcount.p);
+                                               val.p, tmp.p, tcount.p); note_launch();
     HM_LAUNCH("emit entries");
     radix_sort_u64_u32(key.p, val.p, E, bits_for(nt + 1), s);
     ent.alloc(E, s);
-    k_gather_ent<<<grid_for(E), NT, 0, s>>>(tmp.p, val.p, E, ent.p);
+    k_gather_ent<<<grid_for(E), NT, 0, s>>>(tmp.p, val.p, E, ent.p); note_launch();
     DevBuf<int64_t> c64(nt + 1, s);
-    k_i32_to_i64<<<grid_for(nt + 1), NT, 0, s>>>(tcount.p, nt + 1, c64.p);
+    k_i32_to_i64<<<grid_for(nt + 1), NT, 0, s>>>(tcount.p, nt + 1, c64.p); note_launch();
     scan_exclusive_i64(c64.p, ptr.p, nt + 1, nullptr, s);
     HM_LAUNCH("csr");
 }
@@ -355,7 +355,7 @@ void mvp_build_lists(const Blk* ablk, const int32_t* rank, int64_t n_adm, const 
     int64_t h[3] = {0, 0, 0};
     int32_t hm = 0;
     if (n_adm > 0) {
-        k_vitems_count<<<grid_for(n_adm), NT, 0, s>>>(ablk, rank, n_adm, cnt.p, mt.p, ism.p, rk.p);
+        k_vitems_count<<<grid_for(n_adm), NT, 0, s>>>(ablk, rank, n_adm, cnt.p, mt.p, ism.p, rk.p); note_launch();
         scan_exclusive_i64(cnt.p, ioff.p, n_adm, tot.p, s);
         scan_exclusive_i64(mt.p, poff.p, n_adm, tot.p + 1, s);
         scan_exclusive_i64(rk.p, L.toff.p, n_adm, tot.p + 2, s);
@@ -376,7 +376,7 @@ void mvp_build_lists(const Blk* ablk, const int32_t* rank, int64_t n_adm, const 
         k_vitems_emit<<<grid_for(n_adm), NT, 0, s>>>(ablk, n_adm, cnt.p, ioff.p, poff.p,
                                                      L.toff.p, rank, moff.p, L.vitems.p,
                                                      L.tpart_off.p, L.tsum_first.p,
-                                                     L.tsum_count.p, L.multi.p);
+                                                     L.tsum_count.p, L.multi.p); note_launch();
     HM_LAUNCH("vitems");
 }
 
@@ -397,41 +397,88 @@ namespace {
 
 template <class R, int FMT>
 void run_typed(const MvpPlan& P, R* xm, R* t, R* tp, const double* x, double* y,
-               int accumulate, cudaStream_t s)
+               int accumulate, cudaStream_t s, MvpTimer* timer)
 {
-    k_gather_x<R><<<grid_for(P.Ntot), NT, 0, s>>>(x, P.perm, P.Ntot, xm);
+    MvpTimer::Rec* rec = timer ? timer->begin() : nullptr;
+    if (rec) HM_CUDA(cudaEventRecord(rec->e[0], s));
+    k_gather_x<R><<<grid_for(P.Ntot), NT, 0, s>>>(x, P.perm, P.Ntot, xm); note_launch();
+    if (rec) HM_CUDA(cudaEventRecord(rec->e[1], s));
     if (P.n_vitems > 0)
         k_vtx<R><<<grid_for(P.n_vitems * 32, VT_NT), VT_NT, 0, s>>>(
-            P.ablk, P.rank, P.Vptr, P.vitems, P.n_vitems, P.tpart_off, xm, t, tp);
+            P.ablk, P.rank, P.Vptr, P.vitems, P.n_vitems, P.tpart_off, xm, t, tp); note_launch();
     if (P.n_multi > 0)
         k_tsum<R><<<(unsigned)P.n_multi, 64, 0, s>>>(P.multi, P.n_multi, P.rank, P.tsum_first,
-                                                     P.tsum_count, P.tpart_off, P.toff, tp, t);
+                                                     P.tsum_count, P.tpart_off, P.toff, tp, t); note_launch();
+    if (rec) HM_CUDA(cudaEventRecord(rec->e[2], s));
     if (P.n_tiles > 0)
-        k_tile<R, FMT><<<(unsigned)P.n_tiles, TILE_NT, 0, s>>>(P, xm, t, x, y, accumulate);
+        k_tile<R, FMT><<<(unsigned)P.n_tiles, TILE_NT, 0, s>>>(P, xm, t, x, y, accumulate); note_launch();
+    if (rec) HM_CUDA(cudaEventRecord(rec->e[3], s));
     HM_LAUNCH("matvec");
 }
 
 }  // namespace
 
+MvpTimer::Rec* MvpTimer::begin()
+{
+    Rec r;
+    if (!pool.empty()) {
+        r = pool.back();
+        pool.pop_back();
+    } else {
+        for (int k = 0; k < 4; ++k) HM_CUDA(cudaEventCreate(&r.e[k]));
+    }
+    recs.push_back(r);
+    return &recs.back();
+}
+
+void MvpTimer::collect()
+{
+    for (Rec& r : recs) {
+        HM_CUDA(cudaEventSynchronize(r.e[3]));
+        float a = 0, b = 0, c = 0;
+        HM_CUDA(cudaEventElapsedTime(&a, r.e[0], r.e[1]));
+        HM_CUDA(cudaEventElapsedTime(&b, r.e[1], r.e[2]));
+        HM_CUDA(cudaEventElapsedTime(&c, r.e[2], r.e[3]));
+        t_gather += a;
+        t_vtx += b;
+        t_tile += c;
+        t_total += a + b + c;
+        ++count;
+        pool.push_back(r);
+    }
+    recs.clear();
+}
+
+MvpTimer::~MvpTimer()
+{
+    for (Rec& r : recs) pool.push_back(r);
+    for (Rec& r : pool)
+        for (int k = 0; k < 4; ++k) cudaEventDestroy(r.e[k]);
+}
+
+namespace {
+
+}  // namespace
+
 void mvp_run(const MvpPlan& P, MvpWork& W, const double* x, double* y, int accumulate,
-             cudaStream_t s)
+             cudaStream_t s, MvpTimer* timer)
 {
     if (P.precision == HM_PREC_FP64) {
-        run_typed<double, HM_NEAR_FP64>(P, W.xm64.p, W.t64.p, W.tp64.p, x, y, accumulate, s);
+        run_typed<double, HM_NEAR_FP64>(P, W.xm64.p, W.t64.p, W.tp64.p, x, y, accumulate, s, timer);
         return;
     }
     switch (P.near_format) {
     case HM_NEAR_FP64:
-        run_typed<float, HM_NEAR_FP64>(P, W.xm32.p, W.t32.p, W.tp32.p, x, y, accumulate, s);
+        run_typed<float, HM_NEAR_FP64>(P, W.xm32.p, W.t32.p, W.tp32.p, x, y, accumulate, s, timer);
         break;
     case HM_NEAR_FP32:
-        run_typed<float, HM_NEAR_FP32>(P, W.xm32.p, W.t32.p, W.tp32.p, x, y, accumulate, s);
+        run_typed<float, HM_NEAR_FP32>(P, W.xm32.p, W.t32.p, W.tp32.p, x, y, accumulate, s, timer);
         break;
     case HM_NEAR_BF16X2:
-        run_typed<float, HM_NEAR_BF16X2>(P, W.xm32.p, W.t32.p, W.tp32.p, x, y, accumulate, s);
+        run_typed<float, HM_NEAR_BF16X2>(P, W.xm32.p, W.t32.p, W.tp32.p, x, y, accumulate, s, timer);
         break;
     default:
-        run_typed<float, HM_NEAR_BF16>(P, W.xm32.p, W.t32.p, W.tp32.p, x, y, accumulate, s);
+        run_typed<float, HM_NEAR_BF16>(P, W.xm32.p, W.t32.p, W.tp32.p, x, y, accumulate, s, timer);
         break;
     }
 }

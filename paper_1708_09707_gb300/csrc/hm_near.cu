@@ -51,10 +51,10 @@ void launch(int fmt, const KernelParams& kp, const DeviceCoords& X, const Blk* b
 {
     const unsigned g = (unsigned)n;
     switch (fmt) {
-    case HM_NEAR_FP64: k_near<KERN, HM_NEAR_FP64><<<g, NT, 0, s>>>(kp, X, blk, off, n, store); break;
-    case HM_NEAR_FP32: k_near<KERN, HM_NEAR_FP32><<<g, NT, 0, s>>>(kp, X, blk, off, n, store); break;
-    case HM_NEAR_BF16X2: k_near<KERN, HM_NEAR_BF16X2><<<g, NT, 0, s>>>(kp, X, blk, off, n, store); break;
-    default: k_near<KERN, HM_NEAR_BF16><<<g, NT, 0, s>>>(kp, X, blk, off, n, store); break;
+    case HM_NEAR_FP64: k_near<KERN, HM_NEAR_FP64><<<g, NT, 0, s>>>(kp, X, blk, off, n, store); note_launch(); break;
+    case HM_NEAR_FP32: k_near<KERN, HM_NEAR_FP32><<<g, NT, 0, s>>>(kp, X, blk, off, n, store); note_launch(); break;
+    case HM_NEAR_BF16X2: k_near<KERN, HM_NEAR_BF16X2><<<g, NT, 0, s>>>(kp, X, blk, off, n, store); note_launch(); break;
+    default: k_near<KERN, HM_NEAR_BF16><<<g, NT, 0, s>>>(kp, X, blk, off, n, store); note_launch(); break;
     }
 }
 

@@ -194,31 +194,36 @@ __global__ void k_near_size(const Blk* __restrict__ blk, int64_t n, int64_t* __r
 }
 
 // Statistics of the factors: [sum rank, max rank, cap hits, mispredicted,
-// rejected, factor entries, reserved entries]
+// rejected, factor entries, reserved entries, sum k m, evaluations,
+// sum 2 k (k-1) (m + n)]
+constexpr int NSTAT = 10;
 __global__ void k_rank_stats(const Blk* __restrict__ blk, const int32_t* __restrict__ rank,
                              const int32_t* __restrict__ nrej, const int32_t* __restrict__ flags,
                              const int32_t* __restrict__ kres, int64_t n,
                              unsigned long long* __restrict__ out)
 {
     int64_t b = (int64_t)blockIdx.x * NT + threadIdx.x;
-    unsigned long long s[7] = {0, 0, 0, 0, 0, 0, 0};
+    unsigned long long s[NSTAT] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     if (b < n) {
-        int r = rank[b];
+        const unsigned long long r = rank[b], m = blk[b].m, nn = blk[b].n;
         s[0] = r;
         s[1] = r;
         s[2] = (flags[b] & 2) ? 1 : 0;
         s[3] = (flags[b] & 1) ? 1 : 0;
         s[4] = nrej[b];
-        s[5] = (unsigned long long)r * (blk[b].m + blk[b].n);
-        s[6] = (unsigned long long)kres[b] * (blk[b].m + blk[b].n);
+        s[5] = r * (m + nn);
+        s[6] = (unsigned long long)kres[b] * (m + nn);
+        s[7] = r * m;
+        s[8] = r * (m + nn) + (unsigned long long)nrej[b] * m;
+        s[9] = r ? 2ull * r * (r - 1) * (m + nn) : 0ull;
     }
     for (int o = 16; o > 0; o >>= 1)
-        for (int k = 0; k < 7; ++k) {
+        for (int k = 0; k < NSTAT; ++k) {
             unsigned long long v = __shfl_xor_sync(0xffffffffu, s[k], o);
             s[k] = (k == 1) ? max(s[k], v) : s[k] + v;
         }
     if ((threadIdx.x & 31) == 0) {
-        for (int k = 0; k < 7; ++k)
+        for (int k = 0; k < NSTAT; ++k)
             if (k == 1) atomicMax(&out[1], s[1]);
             else atomicAdd(&out[k], s[k]);
     }
@@ -323,13 +328,13 @@ void compress(hm_handle_s& h, const uint32_t* ids, int64_t n, const int32_t* kpr
     DevBuf<int64_t> ccount(ACA_NCLASS, s);
     HM_CUDA(cudaMemsetAsync(ccount.p, 0, ACA_NCLASS * sizeof(int64_t), s));
     k_classes<<<grid_for(n), NT, 0, s>>>(h.ablk.p, ids, n, h.opt.k_cap, kpred, key.p, order.p,
-                                         h.kres.p, ccount.p);
+                                         h.kres.p, ccount.p); note_launch();
     HM_LAUNCH("classes");
     radix_sort_u64_u32(key.p, order.p, n, 3, s);
     int64_t cc[ACA_NCLASS];
     HM_CUDA(cudaMemcpyAsync(cc, ccount.p, sizeof(cc), cudaMemcpyDeviceToHost, s));
     DevBuf<int64_t> res(n, s), pre(n + 1, s);
-    k_reserve<<<grid_for(n), NT, 0, s>>>(h.ablk.p, order.p, n, h.kres.p, res.p);
+    k_reserve<<<grid_for(n), NT, 0, s>>>(h.ablk.p, order.p, n, h.kres.p, res.p); note_launch();
     scan_exclusive_i64(res.p, pre.p, n, pre.p + n, s);
     std::vector<int64_t> hpre(n + 1);
     HM_CUDA(cudaMemcpyAsync(hpre.data(), pre.p, (n + 1) * sizeof(int64_t),
@@ -378,7 +383,7 @@ void compress(hm_handle_s& h, const uint32_t* ids, int64_t n, const int32_t* kpr
         auto seg = std::make_unique<FactorSegment>();
         seg->mem.alloc((size_t)hpre[n] * esz, s);
         k_set_ptrs<<<grid_for(n), NT, 0, s>>>(h.ablk.p, order.p, 0, n, pre.p, h.kres.p,
-                                               seg->mem.p, esz, h.Uptr.p, h.Vptr.p);
+                                               seg->mem.p, esz, h.Uptr.p, h.Vptr.p); note_launch();
         HM_LAUNCH("set ptrs");
         h.segments.push_back(std::move(seg));
         run_range(0, n);
@@ -403,11 +408,11 @@ void compress(hm_handle_s& h, const uint32_t* ids, int64_t n, const int32_t* kpr
                      hpre.begin() - 1;
         q1 = std::max(q1, q0 + 1);
         k_set_ptrs<<<grid_for(q1 - q0), NT, 0, s>>>(h.ablk.p, order.p, q0, q1, pre.p, h.kres.p,
-                                                     scratch.p, esz, h.Uptr.p, h.Vptr.p);
+                                                     scratch.p, esz, h.Uptr.p, h.Vptr.p); note_launch();
         HM_LAUNCH("set ptrs");
         run_range(q0, q1);
         DevBuf<int64_t> fs(q1 - q0, s), foff(q1 - q0 + 1, s);
-        k_final_size<<<grid_for(q1 - q0), NT, 0, s>>>(h.ablk.p, order.p, q0, q1, h.rank.p, fs.p);
+        k_final_size<<<grid_for(q1 - q0), NT, 0, s>>>(h.ablk.p, order.p, q0, q1, h.rank.p, fs.p); note_launch();
         scan_exclusive_i64(fs.p, foff.p, q1 - q0, foff.p + (q1 - q0), s);
         int64_t tot = 0;
         HM_CUDA(cudaMemcpyAsync(&tot, foff.p + (q1 - q0), sizeof(int64_t),
@@ -416,7 +421,7 @@ void compress(hm_handle_s& h, const uint32_t* ids, int64_t n, const int32_t* kpr
         auto seg = std::make_unique<FactorSegment>();
         seg->mem.alloc((size_t)std::max<int64_t>(tot, 1) * esz, s);
         k_copy_factors<<<(unsigned)(q1 - q0), NT, 0, s>>>(
-            h.ablk.p, order.p, q0, q1, h.rank.p, foff.p, seg->mem.p, esz, h.Uptr.p, h.Vptr.p);
+            h.ablk.p, order.p, q0, q1, h.rank.p, foff.p, seg->mem.p, esz, h.Uptr.p, h.Vptr.p); note_launch();
         HM_LAUNCH("copy factors");
         h.segments.push_back(std::move(seg));
         ++passes;
@@ -430,12 +435,12 @@ namespace {
 void rank_stats(hm_handle_s& h)
 {
     cudaStream_t s = h.stream;
-    DevBuf<unsigned long long> out(7, s);
-    HM_CUDA(cudaMemsetAsync(out.p, 0, 7 * sizeof(unsigned long long), s));
+    DevBuf<unsigned long long> out(NSTAT, s);
+    HM_CUDA(cudaMemsetAsync(out.p, 0, NSTAT * sizeof(unsigned long long), s));
     if (h.n_adm > 0)
         k_rank_stats<<<grid_for(h.n_adm), NT, 0, s>>>(h.ablk.p, h.rank.p, h.nrej.p, h.flags.p,
-                                                     h.kres.p, h.n_adm, out.p);
-    unsigned long long o[7];
+                                                     h.kres.p, h.n_adm, out.p); note_launch();
+    unsigned long long o[NSTAT];
     HM_CUDA(cudaMemcpyAsync(o, out.p, sizeof(o), cudaMemcpyDeviceToHost, s));
     HM_CUDA(cudaStreamSynchronize(s));
     h.stats.sum_rank = (int64_t)o[0];
@@ -444,6 +449,14 @@ void rank_stats(hm_handle_s& h)
     h.stats.n_rejected = (int64_t)o[4];
     h.stats.factor_entries = (int64_t)o[5];
     h.stats.reserved_factor_entries = (int64_t)o[6];
+    h.factor_entries_U = (int64_t)o[7];
+    h.stats.aca_evals = (int64_t)o[8];
+    // algorithmic flops of one kernel evaluation: squared distance in three
+    // coordinates (3 subtractions, 1 multiply, 2 fused multiply-adds = 8)
+    // plus the kernel (Gaussian: scale + exp = 2; Matern-3/2: sqrt, scale,
+    // exp, add, multiply = 5)
+    const double fe = h.kernel == HM_GAUSSIAN ? 10.0 : 13.0;
+    h.stats.aca_flops = fe * (double)o[8] + (double)o[9];
 }
 
 void validate(int nsets, const int64_t* N, const int* d, int kernel, const double* params,
@@ -572,20 +585,20 @@ void build_sets(hm_handle_s& h, int nsets, const double* points_all, const int64
                 HM_CUDA(cudaMemcpyAsync(h.adm_pairs.p + ao, adm[q].p, S.n_adm * sizeof(int2),
                                         cudaMemcpyDeviceToDevice, s));
                 k_make_blk<<<grid_for(S.n_adm), NT, 0, s>>>(adm[q].p, S.n_adm, lo, hi, S.row0,
-                                                            h.ablk.p + ao);
+                                                            h.ablk.p + ao); note_launch();
             }
             if (S.n_dense) {
                 HM_CUDA(cudaMemcpyAsync(h.dense_pairs.p + dof, dense[q].p,
                                         S.n_dense * sizeof(int2), cudaMemcpyDeviceToDevice, s));
                 k_make_blk<<<grid_for(S.n_dense), NT, 0, s>>>(dense[q].p, S.n_dense, lo, hi,
-                                                              S.row0, h.dblk.p + dof);
+                                                              S.row0, h.dblk.p + dof); note_launch();
             }
             HM_LAUNCH("blocks");
             ao += S.n_adm;
             dof += S.n_dense;
             // leaf tiles of this set, in row order
             DevBuf<int64_t> flag(S.n_nodes, s), off(S.n_nodes + 1, s);
-            k_leaf_flags<<<grid_for(S.n_nodes), NT, 0, s>>>(lo, hi, S.n_nodes, leaf, flag.p);
+            k_leaf_flags<<<grid_for(S.n_nodes), NT, 0, s>>>(lo, hi, S.n_nodes, leaf, flag.p); note_launch();
             scan_exclusive_i64(flag.p, off.p, S.n_nodes, off.p + S.n_nodes, s);
             int64_t nt = 0;
             HM_CUDA(cudaMemcpyAsync(&nt, off.p + S.n_nodes, sizeof(int64_t),
@@ -595,12 +608,12 @@ void build_sets(hm_handle_s& h, int nsets, const double* points_all, const int64
             DevBuf<uint32_t> v(nt, s);
             DevBuf<int32_t> vid(nt, s);
             k_leaf_emit<<<grid_for(S.n_nodes), NT, 0, s>>>(lo, hi, S.n_nodes, flag.p, off.p, k.p,
-                                                           v.p, vid.p);
+                                                           v.p, vid.p); note_launch();
             radix_sort_u64_u32(k.p, v.p, nt, bits_for(S.N + 1), s);
             trow[q].alloc(nt, s);
             tm[q].alloc(nt, s);
             k_leaf_tiles<<<grid_for(nt), NT, 0, s>>>(v.p, vid.p, nt, lo, hi, S.row0, trow[q].p,
-                                                     tm[q].p);
+                                                     tm[q].p); note_launch();
             HM_LAUNCH("tiles");
             ntile[q] = nt;
             h.n_tiles += nt;
@@ -649,7 +662,7 @@ void build_sets(hm_handle_s& h, int nsets, const double* points_all, const int64
         int64_t tot = 0;
         if (nd > 0) {
             DevBuf<int64_t> sz(nd, s), t(1, s);
-            k_near_size<<<grid_for(nd), NT, 0, s>>>(h.dblk.p, nd, sz.p);
+            k_near_size<<<grid_for(nd), NT, 0, s>>>(h.dblk.p, nd, sz.p); note_launch();
             scan_exclusive_i64(sz.p, h.doff.p, nd, t.p, s);
             HM_CUDA(cudaMemcpyAsync(&tot, t.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
             HM_CUDA(cudaStreamSynchronize(s));
@@ -723,6 +736,10 @@ void build_sets(hm_handle_s& h, int nsets, const double* points_all, const int64
     // algorithmic bytes of one product: factors + near field + x (read once
     // through the permutation) + perm + y written + gather entries
     st.mvp_bytes = st.factor_bytes + st.near_bytes + Ntot * (8 + 8 + 8) + n_ent * 8;
+    // per kernel: V^T x reads V and writes t; the gather reads U, the near
+    // field, its entries, perm and x (for sigma^2 x) and writes y
+    st.mvp_vtx_bytes = (st.factor_entries - h.factor_entries_U) * fsz + h.lists.t_len * fsz;
+    st.mvp_tile_bytes = h.factor_entries_U * fsz + st.near_bytes + Ntot * (8 + 8 + 8) + n_ent * 8;
     st.t_total_ms =
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }

@@ -107,9 +107,9 @@ void scan_exclusive(const T* in, T* out, int64_t n, T* total, cudaStream_t s)
     }
     int64_t tiles = ceil_div(n, SCAN_TILE);
     DevBuf<T> part(tiles, s);
-    k_scan_reduce<T><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, n, part.p);
-    k_scan_partials<T><<<1, SCAN_THREADS, 0, s>>>(part.p, tiles, total);
-    k_scan_down<T><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, out, n, part.p);
+    k_scan_reduce<T><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, n, part.p); note_launch();
+    k_scan_partials<T><<<1, SCAN_THREADS, 0, s>>>(part.p, tiles, total); note_launch();
+    k_scan_down<T><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, out, n, part.p); note_launch();
     HM_LAUNCH("scan");
 }
 
@@ -246,9 +246,9 @@ void radix_sort_u64_u32(uint64_t* keys, uint32_t* vals, int64_t n, int key_bits,
     uint32_t *va = vals, *vb = v2.p;
     for (int p = 0; p < passes; ++p) {
         int shift = 8 * p;
-        k_rs_hist<<<ntiles, RS_THREADS, 0, s>>>(ka, n, shift, cnt.p, ntiles);
+        k_rs_hist<<<ntiles, RS_THREADS, 0, s>>>(ka, n, shift, cnt.p, ntiles); note_launch();
         scan_exclusive<int32_t>(cnt.p, cnt.p, (int64_t)256 * ntiles, nullptr, s);
-        k_rs_scatter<<<ntiles, RS_THREADS, 0, s>>>(ka, va, kb, vb, n, shift, cnt.p, ntiles);
+        k_rs_scatter<<<ntiles, RS_THREADS, 0, s>>>(ka, va, kb, vb, n, shift, cnt.p, ntiles); note_launch();
         HM_LAUNCH("radix sort pass");
         std::swap(ka, kb);
         std::swap(va, vb);

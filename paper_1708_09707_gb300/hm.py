@@ -35,7 +35,7 @@ class Options(C.Structure):
                 ("aca_eta", C.c_double), ("eps0", C.c_double),
                 ("accumulate", C.c_int), ("rank_model", C.c_int),
                 ("rank_model_theta", C.c_void_p), ("scratch_gb", C.c_double),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("profile", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -51,7 +51,11 @@ class Stats(C.Structure):
                 ("t_structure_ms", C.c_double), ("t_aca_ms", C.c_double),
                 ("t_dense_ms", C.c_double), ("t_total_ms", C.c_double),
                 ("aca_passes", C.c_int), ("precision", C.c_int),
-                ("near_format", C.c_int)]
+                ("near_format", C.c_int), ("aca_evals", C.c_int64),
+                ("aca_flops", C.c_double), ("mvp_count", C.c_int64),
+                ("t_mvp_ms", C.c_double), ("t_mvp_gather_ms", C.c_double),
+                ("t_mvp_vtx_ms", C.c_double), ("t_mvp_tile_ms", C.c_double),
+                ("mvp_vtx_bytes", C.c_int64), ("mvp_tile_bytes", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -82,6 +86,7 @@ def _declare(L):
     i64, pi = C.c_int64, C.POINTER(C.c_int)
     L.hm_options_default.argtypes = [C.POINTER(Options)]
     L.hm_last_error.restype = C.c_char_p
+    L.hm_kernel_launches.restype = C.c_uint64
     L.hm_build_ex.restype = _vp
     L.hm_build_ex.argtypes = [_vp, i64, C.c_int, C.c_int, _vp, C.c_int, C.c_double,
                               C.c_double, C.POINTER(Options), pi]
@@ -139,7 +144,7 @@ def _stream_ptr(stream):
 
 def options(precision=PREC_FP64, near_format=NEAR_AUTO, adm_max=False, k_cap=64,
             aca_eta=0.0, eps0=0.0, accumulate=False, rank_model_theta=None,
-            scratch_gb=0.0, stream=None) -> Options:
+            scratch_gb=0.0, stream=None, profile=False) -> Options:
     o = Options()
     lib().hm_options_default(C.byref(o))
     o.precision = precision
@@ -153,6 +158,7 @@ def options(precision=PREC_FP64, near_format=NEAR_AUTO, adm_max=False, k_cap=64,
     o.rank_model_theta = _ptr(rank_model_theta)
     o.scratch_gb = scratch_gb
     o.stream = _stream_ptr(stream)
+    o.profile = int(profile)
     return o
 
 
@@ -320,3 +326,8 @@ def mlp_loss_grad(theta, F, target, grad, loss=None, stream=None):
 def mlp_adam(theta, grad, m, v, t: int, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, stream=None):
     _check(lib().hm_mlp_adam(_ptr(theta), _ptr(grad), _ptr(m), _ptr(v), t, lr, b1, b2, eps,
                              _stream_ptr(stream)))
+
+
+def kernel_launches() -> int:
+    """Kernels the library has launched in this process."""
+    return int(lib().hm_kernel_launches())
