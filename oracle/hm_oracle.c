@@ -203,8 +203,14 @@ int or_admissible(const double* amin, const double* amax, const double* bmin,
 /* ------------------------------------------------------------------------ */
 /* Alg. 2: ACA with partial pivoting.                                        */
 /* Readings of the paper (Sec. 2.4 leaves them open):                        */
-/*  - first column j_1 = 0; later columns: argmax over unused columns of     */
-/*    |v_{r-1}|, lowest index on ties;                                       */
+/*  - first column j_1 = 0; later columns: argmax over unused columns of the */
+/*    residual of a reference row, lowest index on ties. The reference row  */
+/*    starts at row 0; once its residual is resolved (max <= tol times the   */
+/*    row's own max, tol = eps, or eps0 in fixed-rank mode) it moves to the  */
+/*    lowest row not yet used as pivot or reference (at most once per step). */
+/*    The residual row v_r of the pivot row is not used for the choice: next */
+/*    to the current column j_r it is nearly maximal at the columns of close */
+/*    or duplicate points, which adds nearly redundant crosses;              */
 /*  - row pivot i_r = argmax |u^_r| (lowest index on ties);                  */
 /*  - the paper asks for a column with ||u^|| > eps0, eps0 near machine     */
 /*    precision, and leaves the search open: a column whose largest residual */
@@ -217,8 +223,8 @@ int or_admissible(const double* amin, const double* amax, const double* bmin,
 /*  - ||sum_l u_l v_l^T||_F^2 is updated by the textbook recursion           */
 /*    S2 += 2 sum_{l<r} (u_r.u_l)(v_l.v_r) + |u_r|^2 |v_r|^2;                */
 /*  - stop when |u_r| |v_r| <= eps (1-aca_eta)/(1+eps) sqrt(S2) (eps relative */
-/*    to the approximation's own norm); eps <= 0 is the paper's fixed-rank   */
-/*    mode (no test, k = k_cap);                                             */
+/*    to the approximation's own norm) and the reference row is resolved;    */
+/*    eps <= 0 is the paper's fixed-rank mode (no test, k = k_cap);          */
 /*  - the rank never exceeds min(k_cap, m, n).                               */
 /* ------------------------------------------------------------------------ */
 #define OR_REJ_RUN 4
@@ -232,11 +238,21 @@ int or_aca(or_entry_fn f, const void* ctx, int64_t m, int64_t n, double eps,
     if (kmax > n) kmax = n;
     if (eps0 <= 0.0) eps0 = 1e-14;
     unsigned char* used = (unsigned char*)calloc((size_t)n, 1);
+    unsigned char* seen = (unsigned char*)calloc((size_t)m, 1); /* pivot/reference rows */
     double* uh = (double*)malloc((size_t)m * sizeof(double));
+    double* rr = (double*)malloc((size_t)n * sizeof(double));   /* reference row residual */
     double thr = (eps > 0.0) ? eps * (1.0 - aca_eta) / (1.0 + eps) : -1.0;
+    double rtol = (eps > 0.0) ? eps : eps0;
     double S2 = 0.0;
     int r = 0;
     int64_t j = 0, rej = 0, run = 0;
+    int64_t iref = 0;
+    double rs = 0.0;
+    seen[0] = 1;
+    for (int64_t c = 0; c < n; ++c) {
+        rr[c] = f(ctx, 0, c);
+        if (fabs(rr[c]) > rs) rs = fabs(rr[c]);
+    }
 
     while (r < kmax) {
         /* residual column u^_r = A(:, j) - sum_{l<r} u_l (v_l)_j */
@@ -297,23 +313,55 @@ int or_aca(or_entry_fn f, const void* ctx, int64_t m, int64_t n, double eps,
         }
         S2 = S2 + (2.0 * cross + nu2 * nv2);
         r++;
-        /* stopping criterion of Alg. 2 */
-        if (thr >= 0.0 && sqrt(nu2) * sqrt(nv2) <= thr * sqrt(S2 > 0.0 ? S2 : 0.0))
+        seen[is] = 1;
+        /* reference row residual, moved on once resolved */
+        double ui = u[iref], rmax = 0.0;
+        for (int64_t c = 0; c < n; ++c) {
+            rr[c] = rr[c] - ui * v[c];
+            if (fabs(rr[c]) > rmax) rmax = fabs(rr[c]);
+        }
+        if (!(rmax > rtol * rs)) {
+            int64_t in = -1;
+            for (int64_t i = 0; i < m; ++i)
+                if (!seen[i]) {
+                    in = i;
+                    break;
+                }
+            if (in >= 0) {
+                iref = in;
+                seen[in] = 1;
+                rs = 0.0;
+                rmax = 0.0;
+                for (int64_t c = 0; c < n; ++c) {
+                    double a = f(ctx, iref, c);
+                    if (fabs(a) > rs) rs = fabs(a);
+                    double s = a;
+                    for (int l = 0; l < r; ++l) s = s - U[l * m + iref] * V[l * n + c];
+                    rr[c] = s;
+                    if (fabs(s) > rmax) rmax = fabs(s);
+                }
+            }
+        }
+        /* stopping criterion of Alg. 2, with the reference row resolved */
+        if (thr >= 0.0 && sqrt(nu2) * sqrt(nv2) <= thr * sqrt(S2 > 0.0 ? S2 : 0.0) &&
+            !(rmax > rtol * rs))
             break;
         if (r >= kmax) break;
-        /* next column: largest |v_r| among unused columns */
+        /* next column: largest reference-row residual among unused columns */
         int64_t jn = -1;
         double bv = -1.0;
         for (int64_t c = 0; c < n; ++c)
-            if (!used[c] && fabs(v[c]) > bv) {
-                bv = fabs(v[c]);
+            if (!used[c] && fabs(rr[c]) > bv) {
+                bv = fabs(rr[c]);
                 jn = c;
             }
         if (jn < 0) break;
         j = jn;
     }
     free(used);
+    free(seen);
     free(uh);
+    free(rr);
     if (n_rej) *n_rej = rej;
     return r;
 }

@@ -45,8 +45,25 @@ def test_aca_first_column_and_pivot_rule(orc):
     assert np.allclose(U[:, 0], [0.25, 1.0, 0.5])
     assert np.allclose(V[:, 0], [4.0, -8.0, 6.0])
     U, V, pi, pj, _ = orc.aca_dense(A, 0.0, k_cap=2)
-    # second column: argmax of |v_1| over unused columns {1,2} -> column 1
+    # second column: argmax over unused columns {1,2} of the reference row's
+    # residual: row 0 minus u_1[0] v_1 = [1,2,3] - 0.25 [4,-8,6] = [0, 4, 1.5]
     assert pj[1] == 1
+    B = np.array([[1.0, 2.0, 9.0], [4.0, -8.0, 6.0], [2.0, 1.0, 0.5]])
+    U, V, pi, pj, _ = orc.aca_dense(B, 0.0, k_cap=2)
+    # [1,2,9] - 0.25 [4,-8,6] = [0, 4, 7.5] -> column 2, although |v_1| is
+    # largest at column 1
+    assert pi[0] == 1 and pj[1] == 2
+
+
+def test_aca_near_duplicate_columns(orc):
+    # points on a line with a tight pair next to the first column: the
+    # reference-row choice keeps the cross approximation accurate
+    rng = np.random.default_rng(5)
+    X = np.sort(rng.uniform(0, 1, 300))
+    Y = np.concatenate([[2.0, 2.0 + 1e-9, 2.0 + 2e-9], rng.uniform(2.0, 4.0, 200)])
+    A = np.exp(-(X[:, None] - Y[None, :]) ** 2 / 0.5)
+    U, V, *_ = orc.aca_dense(A, 1e-8, k_cap=64)
+    assert np.linalg.norm(A - U @ V.T) <= 10 * 1e-8 * np.linalg.norm(A)
 
 
 def test_aca_rejects_zero_columns(orc):
