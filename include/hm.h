@@ -78,6 +78,8 @@ typedef struct hm_options {
     void* stream;         /* cudaStream_t, NULL = legacy default stream */
     int profile;          /* 1: time every product kernel with CUDA events on
                              the launching stream (read by hm_get_stats) */
+    int structure_only;   /* 1: stop after the cluster tree and the leaf lists
+                             (no ACA, no near field; hm_matvec is refused) */
 } hm_options;
 
 typedef struct hm_handle_s* hm_handle;

@@ -206,8 +206,9 @@ int or_admissible(const double* amin, const double* amax, const double* bmin,
 /*  - first column j_1 = 0; later columns: argmax over unused columns of the */
 /*    residual of a reference row, lowest index on ties. The reference row  */
 /*    starts at row 0; once its residual is resolved (max <= tol times the   */
-/*    row's own max, tol = eps, or eps0 in fixed-rank mode) it moves to the  */
-/*    lowest row not yet used as pivot or reference (at most once per step). */
+/*    RMS row norm sqrt(S2/m) of the approximation, tol = eps, or eps0 in    */
+/*    fixed-rank mode) it moves to the lowest row not yet used as pivot or   */
+/*    reference (at most once per step).                                     */
 /*    The residual row v_r of the pivot row is not used for the choice: next */
 /*    to the current column j_r it is nearly maximal at the columns of close */
 /*    or duplicate points, which adds nearly redundant crosses;              */
@@ -247,12 +248,8 @@ int or_aca(or_entry_fn f, const void* ctx, int64_t m, int64_t n, double eps,
     int r = 0;
     int64_t j = 0, rej = 0, run = 0;
     int64_t iref = 0;
-    double rs = 0.0;
     seen[0] = 1;
-    for (int64_t c = 0; c < n; ++c) {
-        rr[c] = f(ctx, 0, c);
-        if (fabs(rr[c]) > rs) rs = fabs(rr[c]);
-    }
+    for (int64_t c = 0; c < n; ++c) rr[c] = f(ctx, 0, c);
 
     while (r < kmax) {
         /* residual column u^_r = A(:, j) - sum_{l<r} u_l (v_l)_j */
@@ -320,7 +317,8 @@ int or_aca(or_entry_fn f, const void* ctx, int64_t m, int64_t n, double eps,
             rr[c] = rr[c] - ui * v[c];
             if (fabs(rr[c]) > rmax) rmax = fabs(rr[c]);
         }
-        if (!(rmax > rtol * rs)) {
+        double rlim = rtol * sqrt((S2 > 0.0 ? S2 : 0.0) / (double)m);
+        if (!(rmax > rlim)) {
             int64_t in = -1;
             for (int64_t i = 0; i < m; ++i)
                 if (!seen[i]) {
@@ -330,12 +328,9 @@ int or_aca(or_entry_fn f, const void* ctx, int64_t m, int64_t n, double eps,
             if (in >= 0) {
                 iref = in;
                 seen[in] = 1;
-                rs = 0.0;
                 rmax = 0.0;
                 for (int64_t c = 0; c < n; ++c) {
-                    double a = f(ctx, iref, c);
-                    if (fabs(a) > rs) rs = fabs(a);
-                    double s = a;
+                    double s = f(ctx, iref, c);
                     for (int l = 0; l < r; ++l) s = s - U[l * m + iref] * V[l * n + c];
                     rr[c] = s;
                     if (fabs(s) > rmax) rmax = fabs(s);
@@ -344,7 +339,7 @@ int or_aca(or_entry_fn f, const void* ctx, int64_t m, int64_t n, double eps,
         }
         /* stopping criterion of Alg. 2, with the reference row resolved */
         if (thr >= 0.0 && sqrt(nu2) * sqrt(nv2) <= thr * sqrt(S2 > 0.0 ? S2 : 0.0) &&
-            !(rmax > rtol * rs))
+            !(rmax > rlim))
             break;
         if (r >= kmax) break;
         /* next column: largest reference-row residual among unused columns */

@@ -10,10 +10,14 @@
 //    residual vectors in the output factor columns.
 // Readings of Alg. 2 (the same as the CPU oracle): first column 0; row pivot
 // argmax |u^| (lowest index on ties); a column whose largest residual entry
-// is <= eps0 * max |A(:,j)| is rejected and the lowest unused column is tried;
-// the next column is argmax over unused columns of |v_r|; ||S_r||_F^2 is
-// updated by S2 += 2 sum_l (u.u_l)(v_l.v) + |u|^2 |v|^2; the rule
-// |u||v| <= eps (1-aca_eta)/(1+eps) sqrt(S2) stops (eps <= 0: fixed rank).
+// is <= eps0 * max |A(:,j)| is rejected and the lowest unused column is tried
+// (four rejections in a row end the block); the next column is the argmax
+// over unused columns of the residual of a reference row (row 0, moved to the
+// lowest row not yet used as pivot or reference once its residual is below
+// tol sqrt(S2 / m), tol = eps, or eps0 in fixed-rank mode);
+// ||S_r||_F^2 is updated by S2 += 2 sum_l (u.u_l)(v_l.v) + |u|^2 |v|^2; the
+// rule |u||v| <= eps (1-aca_eta)/(1+eps) sqrt(S2) with the reference row
+// resolved stops (eps <= 0: fixed rank).
 // The norms, S2 and the stopping test are always accumulated in double.
 #include <cooperative_groups.h>
 
@@ -29,6 +33,12 @@ constexpr int CTA_WARPS = CTA_NT / 32;
 constexpr int KBUF = 128;      // largest supported k_cap
 constexpr int REJ_RUN = 4;     // rejected columns in a row that end a block
 
+// --------------------------------------------------------------------------
+// One warp per block (m, n <= 32 MAXR). Lane l owns rows and columns
+// l + 32 t, t < MAXR: the residual column, the residual row and the
+// reference-row residual live in registers; used columns and seen rows are
+// bit masks per lane.
+// --------------------------------------------------------------------------
 template <class R, int KERN, int MAXR>
 __global__ void __launch_bounds__(WARP_NT)
 k_aca_warp(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restrict__ order,
@@ -41,19 +51,30 @@ k_aca_warp(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restric
     const Blk B = a.blk[b];
     const int m = B.m, n = B.n;
     const int kres = a.kres[b];
-    int kmax = min(kres, min(m, n));
+    const int kmax = min(kres, min(m, n));
     R* __restrict__ U = reinterpret_cast<R*>(a.Uptr[b]);
     R* __restrict__ V = reinterpret_cast<R*>(a.Vptr[b]);
     const R c = kconst<R>(kp);
     const R eps0 = (R)a.eps0;
+    const double rtol = a.eps > 0.0 ? a.eps : a.eps0;
 
-    R acc[MAXR];
-    R vv[MAXR];
-    unsigned used = 0;
-    int r = 0, j = 0, rej = 0, run = 0;
+    R acc[MAXR], vv[MAXR];
+    Resid<R> res[MAXR], rr[MAXR];   // rr: reference-row residual (compensated)
+    unsigned used = 0, seen = (lane == 0) ? 1u : 0u;
+    int r = 0, j = 0, rej = 0, run = 0, iref = 0;
     bool converged = false;
     double S2 = 0.0;
     const int limit = kmax + n + 1;
+
+    // reference row 0
+    {
+        const Pt<R> p0 = load_pt<R>(X, B.row0);
+#pragma unroll
+        for (int t = 0; t < MAXR; ++t) {
+            const int jj = lane + 32 * t;
+            rr[t].init((jj < n) ? phi<KERN>(dist2(p0, load_pt<R>(X, B.col0 + jj)), c) : R(0));
+        }
+    }
 
     for (int it = 0; r < kmax; ++it) {
         if (it > limit) {
@@ -72,7 +93,7 @@ k_aca_warp(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restric
                 v = phi<KERN>(dist2(load_pt<R>(X, B.row0 + i), pj), c);
                 amax = max(amax, fabs(v));
             }
-            acc[t] = v;
+            res[t].init(v);
         }
         for (int l0 = 0; l0 < r; l0 += 32) {
             const R vjc = (l0 + lane < r) ? V[(int64_t)(l0 + lane) * n + j] : R(0);
@@ -83,7 +104,7 @@ k_aca_warp(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restric
 #pragma unroll
                 for (int t = 0; t < MAXR; ++t) {
                     const int i = lane + 32 * t;
-                    if (i < m) acc[t] -= Ul[i] * vjl;
+                    if (i < m) res[t].sub(Ul[i], vjl);
                 }
             }
         }
@@ -91,6 +112,7 @@ k_aca_warp(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restric
         int bi = 0x7fffffff;
 #pragma unroll
         for (int t = 0; t < MAXR; ++t) {
+            acc[t] = res[t].value();
             const int i = lane + 32 * t;
             if (i < m && fabs(acc[t]) > best) {
                 best = fabs(acc[t]);
@@ -132,7 +154,9 @@ k_aca_warp(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restric
         for (int t = 0; t < MAXR; ++t)
             if (t == (bi >> 5)) mine = acc[t];
         const R piv = __shfl_sync(0xffffffffu, mine, bi & 31);
+        if ((bi & 31) == lane) seen |= 1u << (bi >> 5);
         R* __restrict__ Ur = U + (int64_t)r * m;
+        R uiref = 0;
 #pragma unroll
         for (int t = 0; t < MAXR; ++t) {
             const int i = lane + 32 * t;
@@ -140,13 +164,15 @@ k_aca_warp(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restric
                 acc[t] = acc[t] / piv;
                 Ur[i] = acc[t];
             }
+            if (t == (iref >> 5)) uiref = acc[t];
         }
+        uiref = __shfl_sync(0xffffffffu, uiref, iref & 31);
         // residual row v = A(i_r, :)^T - sum_{l<r} (u_l)_{i_r} v_l
         const Pt<R> pi = load_pt<R>(X, B.row0 + bi);
 #pragma unroll
         for (int t = 0; t < MAXR; ++t) {
             const int jj = lane + 32 * t;
-            vv[t] = (jj < n) ? phi<KERN>(dist2(pi, load_pt<R>(X, B.col0 + jj)), c) : R(0);
+            res[t].init((jj < n) ? phi<KERN>(dist2(pi, load_pt<R>(X, B.col0 + jj)), c) : R(0));
         }
         for (int l0 = 0; l0 < r; l0 += 32) {
             const R uic = (l0 + lane < r) ? U[(int64_t)(l0 + lane) * m + bi] : R(0);
@@ -157,21 +183,28 @@ k_aca_warp(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restric
 #pragma unroll
                 for (int t = 0; t < MAXR; ++t) {
                     const int jj = lane + 32 * t;
-                    if (jj < n) vv[t] -= uil * Vl[jj];
+                    if (jj < n) res[t].sub(uil, Vl[jj]);
                 }
             }
         }
         R* __restrict__ Vr = V + (int64_t)r * n;
         double nu2 = 0.0, nv2 = 0.0;
+        R rmax = 0;
 #pragma unroll
         for (int t = 0; t < MAXR; ++t) {
+            vv[t] = res[t].value();
             const int i = lane + 32 * t;
-            if (i < n) Vr[i] = vv[t];
+            if (i < n) {
+                Vr[i] = vv[t];
+                nv2 += (double)vv[t] * (double)vv[t];
+                rr[t].sub(uiref, vv[t]);
+                rmax = max(rmax, fabs(rr[t].value()));
+            }
             if (i < m) nu2 += (double)acc[t] * (double)acc[t];
-            if (i < n) nv2 += (double)vv[t] * (double)vv[t];
         }
         nu2 = warp_sum(nu2);
         nv2 = warp_sum(nv2);
+        rmax = warp_max(rmax);
         // cross terms (u_r . u_l)(v_l . v_r)
         double cross = 0.0;
         for (int l = 0; l < r; ++l) {
@@ -190,19 +223,65 @@ k_aca_warp(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restric
         }
         S2 += 2.0 * cross + nu2 * nv2;
         ++r;
-        if (thr >= 0.0 && sqrt(nu2) * sqrt(nv2) <= thr * sqrt(fmax(S2, 0.0))) {
+        // a resolved reference row moves to the lowest row not seen yet
+        const double rlim = rtol * sqrt(fmax(S2, 0.0) / (double)m);
+        if (!((double)rmax > rlim)) {
+            int cand = 0x7fffffff;
+#pragma unroll
+            for (int t = 0; t < MAXR; ++t) {
+                const int i = lane + 32 * t;
+                if (i < m && !((seen >> t) & 1u)) {
+                    cand = i;
+                    break;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) cand = min(cand, __shfl_xor_sync(0xffffffffu, cand, o));
+            if (cand != 0x7fffffff) {
+                iref = cand;
+                if ((iref & 31) == lane) seen |= 1u << (iref >> 5);
+                const Pt<R> pr = load_pt<R>(X, B.row0 + iref);
+#pragma unroll
+                for (int t = 0; t < MAXR; ++t) {
+                    const int jj = lane + 32 * t;
+                    res[t].init((jj < n) ? phi<KERN>(dist2(pr, load_pt<R>(X, B.col0 + jj)), c) : R(0));
+                }
+                for (int l0 = 0; l0 < r; l0 += 32) {
+                    const R uic = (l0 + lane < r) ? U[(int64_t)(l0 + lane) * m + iref] : R(0);
+                    const int lend = min(r - l0, 32);
+                    for (int l = 0; l < lend; ++l) {
+                        const R uil = __shfl_sync(0xffffffffu, uic, l);
+                        const R* Vl = V + (int64_t)(l0 + l) * n;
+#pragma unroll
+                        for (int t = 0; t < MAXR; ++t) {
+                            const int jj = lane + 32 * t;
+                            if (jj < n) res[t].sub(uil, Vl[jj]);
+                        }
+                    }
+                }
+                rmax = 0;
+#pragma unroll
+                for (int t = 0; t < MAXR; ++t) {
+                    rr[t] = res[t];
+                    if (lane + 32 * t < n) rmax = max(rmax, fabs(rr[t].value()));
+                }
+                rmax = warp_max(rmax);
+            }
+        }
+        if (thr >= 0.0 && sqrt(nu2) * sqrt(nv2) <= thr * sqrt(fmax(S2, 0.0)) &&
+            !((double)rmax > rlim)) {
             converged = true;
             break;
         }
         if (r >= kmax) break;
-        // next column: largest |v_r| over unused columns
+        // next column: largest reference-row residual over unused columns
         R bv = -1;
         int bj = 0x7fffffff;
 #pragma unroll
         for (int t = 0; t < MAXR; ++t) {
             const int jj = lane + 32 * t;
-            if (jj < n && !((used >> t) & 1u) && fabs(vv[t]) > bv) {
-                bv = fabs(vv[t]);
+            if (jj < n && !((used >> t) & 1u) && fabs(rr[t].value()) > bv) {
+                bv = fabs(rr[t].value());
                 bj = jj;
             }
         }
@@ -229,34 +308,135 @@ k_aca_warp(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restric
 // --------------------------------------------------------------------------
 // Large blocks: one CTA or one thread-block cluster of CS CTAs per block
 // (CS = 1, 4 or 8). The rows and columns of the block are dealt round-robin
-// to all CS * CTA_NT threads; every reduction (pivot search, norms, cross
-// terms, next column) first reduces inside each CTA, then every CTA reads the
-// partials of all CTAs of its cluster from distributed shared memory in rank
-// order, so all CTAs reach identical decisions and follow the same control
-// flow. Partials are double-buffered, so one cluster barrier per reduction
-// suffices. The block's used-column bitmap lives in global memory.
+// to all CS * CTA_NT threads, so every thread owns the same rows and columns
+// in every pass. A reduction first combines inside each CTA, then every CTA
+// reads the partials of all CTAs of its cluster from distributed shared
+// memory in rank order, so all CTAs reach identical values and follow the
+// same control flow. Partials are double-buffered, so one cluster barrier per
+// reduction suffices. Used columns, seen rows and the reference-row residual
+// live in global scratch owned by the cluster.
 // --------------------------------------------------------------------------
+struct Red {
+    double s0, s1;        // sums
+    double x0, x1;        // maxima
+    double av, aval;      // argmax value (|.|) and the signed value there
+    int ai, mn;           // argmax index (ties: lowest), minimum
+};
+
+__device__ __forceinline__ void red_init(Red& q)
+{
+    q.s0 = q.s1 = 0.0;
+    q.x0 = q.x1 = 0.0;
+    q.av = -1.0;
+    q.aval = 0.0;
+    q.ai = 0x7fffffff;
+    q.mn = 0x7fffffff;
+}
+
+__device__ __forceinline__ void red_join(Red& q, const Red& o)
+{
+    q.s0 += o.s0;
+    q.s1 += o.s1;
+    q.x0 = fmax(q.x0, o.x0);
+    q.x1 = fmax(q.x1, o.x1);
+    if (o.av > q.av || (o.av == q.av && o.ai < q.ai)) {
+        q.av = o.av;
+        q.ai = o.ai;
+        q.aval = o.aval;
+    }
+    q.mn = min(q.mn, o.mn);
+}
+
+__device__ __forceinline__ void red_warp(Red& q)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        Red p;
+        p.s0 = __shfl_xor_sync(0xffffffffu, q.s0, o);
+        p.s1 = __shfl_xor_sync(0xffffffffu, q.s1, o);
+        p.x0 = __shfl_xor_sync(0xffffffffu, q.x0, o);
+        p.x1 = __shfl_xor_sync(0xffffffffu, q.x1, o);
+        p.av = __shfl_xor_sync(0xffffffffu, q.av, o);
+        p.aval = __shfl_xor_sync(0xffffffffu, q.aval, o);
+        p.ai = __shfl_xor_sync(0xffffffffu, q.ai, o);
+        p.mn = __shfl_xor_sync(0xffffffffu, q.mn, o);
+        red_join(q, p);
+    }
+}
+
 struct ClPart {
-    double best, bval, amax;   // column pivot: |u^|, u^ at the pivot, max |A(:,j)|
-    int bi, cand, vbj, pad;
-    double nu2, nv2, vbest;
+    Red q;
     double du[KBUF], dv[KBUF];
 };
 
 struct ClShared {
     ClPart part[2];
+    Red wq[CTA_WARPS];
     double wl[CTA_WARPS][KBUF];   // per-warp partial dots
     double wm[CTA_WARPS][KBUF];
-    double ws[CTA_WARPS][4];
-    int wi[CTA_WARPS][2];
-    double bc[4];                 // broadcast: reduced values
-    int bci[2];
+    Red out;                      // broadcast: the cluster-wide result
+    double cross;
 };
+
+// Cluster-wide reduction of q (and, with ndots > 0, of the per-warp dot
+// partials in sh.wl / sh.wm); every thread of every CTA receives the result.
+template <class CL>
+__device__ Red cl_reduce(CL& cl, ClShared& sh, int& ph, Red q, int ndots)
+{
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int CS = (int)cl.num_blocks();
+    red_warp(q);
+    if (lane == 0) sh.wq[w] = q;
+    __syncthreads();
+    ClPart& P = sh.part[ph];
+    if (tid == 0) {
+        Red t = sh.wq[0];
+        for (int k = 1; k < CTA_WARPS; ++k) red_join(t, sh.wq[k]);
+        P.q = t;
+    }
+    if (tid < ndots) {
+        double su = 0.0, sv = 0.0;
+        for (int k = 0; k < CTA_WARPS; ++k) {
+            su += sh.wl[k][tid];
+            sv += sh.wm[k][tid];
+        }
+        P.du[tid] = su;
+        P.dv[tid] = sv;
+    }
+    cl.sync();
+    if (w == 0) {
+        double cr = 0.0;
+        for (int l0 = 0; l0 < ndots; l0 += 32) {
+            const int l = l0 + lane;
+            double su = 0.0, sv = 0.0;
+            if (l < ndots)
+                for (int k = 0; k < CS; ++k) {
+                    const ClPart* Q = cl.map_shared_rank(&sh.part[ph], k);
+                    su += Q->du[l];
+                    sv += Q->dv[l];
+                }
+            cr += warp_sum(su * sv);
+        }
+        if (lane == 0) {
+            Red t = cl.map_shared_rank(&sh.part[ph], 0)->q;
+            for (int k = 1; k < CS; ++k) red_join(t, cl.map_shared_rank(&sh.part[ph], k)->q);
+            sh.out = t;
+            sh.cross = cr;
+        }
+    }
+    ph ^= 1;
+    __syncthreads();
+    Red res = sh.out;
+    __syncthreads();
+    return res;
+}
 
 template <class R, int KERN>
 __global__ void __launch_bounds__(CTA_NT)
 k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restrict__ order,
-              int64_t nblocks, double thr, uint32_t* __restrict__ usedpool, int64_t used_words)
+              int64_t nblocks, double thr, uint32_t* __restrict__ usedpool,
+              uint32_t* __restrict__ seenpool, R* __restrict__ rrpool, int64_t words,
+              int64_t maxdim)
 {
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
@@ -267,9 +447,13 @@ k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __rest
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int gt = crank * CTA_NT + tid, GT = CS * CTA_NT;
     const int64_t cid = blockIdx.x / CS, ncl = gridDim.x / CS;
-    uint32_t* used = usedpool + cid * used_words;
+    uint32_t* used = usedpool + cid * words;
+    uint32_t* seen = seenpool + cid * words;
+    R* rr = rrpool + cid * 2 * maxdim;   // reference-row residual: value
+    R* rc = rr + maxdim;                  // and its rounding compensation
     const R c = kconst<R>(kp);
     const R eps0 = (R)a.eps0;
+    const double rtol = a.eps > 0.0 ? a.eps : a.eps0;
     int ph = 0;
 
     for (int64_t q = cid; q < nblocks; q += ncl) {
@@ -280,11 +464,21 @@ k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __rest
         const int kmax = min(kres, min(m, n));
         R* __restrict__ U = reinterpret_cast<R*>(a.Uptr[b]);
         R* __restrict__ V = reinterpret_cast<R*>(a.Vptr[b]);
-        const int words = (n + 31) / 32;
-        for (int k = gt; k < words; k += GT) used[k] = 0u;
+        const int wn = (n + 31) / 32, wm = (m + 31) / 32;
+        for (int k = gt; k < wn; k += GT) used[k] = 0u;
+        for (int k = gt; k < wm; k += GT) seen[k] = 0u;
         cl.sync();
-
-        int r = 0, j = 0, rej = 0, run = 0;
+        if (gt == 0) seen[0] = 1u;
+        // reference row 0
+        double rmax = 0.0;
+        {
+            const Pt<R> p0 = load_pt<R>(X, B.row0);
+            for (int jj = gt; jj < n; jj += GT) {
+                rr[jj] = phi<KERN>(dist2(p0, load_pt<R>(X, B.col0 + jj)), c);
+                rc[jj] = 0;
+            }
+        }
+        int r = 0, j = 0, rej = 0, run = 0, iref = 0;
         bool converged = false;
         double S2 = 0.0;
         const int limit = kmax + n + 1;
@@ -296,85 +490,29 @@ k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __rest
             if (gt == 0) used[j >> 5] |= 1u << (j & 31);
             if (tid < r) sg[tid] = V[(int64_t)tid * n + j];
             __syncthreads();
-            // residual column and its pivot
+            // residual column, its pivot and u^ at the reference row
             const Pt<R> pj = load_pt<R>(X, B.col0 + j);
             R* __restrict__ Ur = U + (int64_t)r * m;
-            R best = -1, amax = 0, bval = 0;
-            int bi = 0x7fffffff;
+            Red qc;
+            red_init(qc);
             for (int i = gt; i < m; i += GT) {
-                R v = phi<KERN>(dist2(load_pt<R>(X, B.row0 + i), pj), c);
-                amax = max(amax, fabs(v));
-                for (int l = 0; l < r; ++l) v -= U[(int64_t)l * m + i] * sg[l];
+                const R a0 = phi<KERN>(dist2(load_pt<R>(X, B.row0 + i), pj), c);
+                qc.x0 = fmax(qc.x0, (double)fabs(a0));
+                Resid<R> rs_;
+                rs_.init(a0);
+                for (int l = 0; l < r; ++l) rs_.sub(U[(int64_t)l * m + i], sg[l]);
+                const R v = rs_.value();
                 Ur[i] = v;
-                if (fabs(v) > best) {
-                    best = fabs(v);
-                    bi = i;
-                    bval = v;
+                if ((double)fabs(v) > qc.av) {
+                    qc.av = fabs(v);
+                    qc.ai = i;
+                    qc.aval = v;
                 }
+                if (i == iref) qc.s0 = v;
             }
-            {
-                // warp then CTA argmax carrying the signed value
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    R ob = __shfl_xor_sync(0xffffffffu, best, o);
-                    int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                    R ov = __shfl_xor_sync(0xffffffffu, bval, o);
-                    if (ob > best || (ob == best && oi < bi)) {
-                        best = ob;
-                        bi = oi;
-                        bval = ov;
-                    }
-                }
-                amax = warp_max(amax);
-                if (lane == 0) {
-                    sh.ws[w][0] = (double)best;
-                    sh.ws[w][1] = (double)bval;
-                    sh.ws[w][2] = (double)amax;
-                    sh.wi[w][0] = bi;
-                }
-                __syncthreads();
-                if (tid == 0) {
-                    double B0 = sh.ws[0][0], V0 = sh.ws[0][1], A0 = sh.ws[0][2];
-                    int I0 = sh.wi[0][0];
-                    for (int k = 1; k < CTA_WARPS; ++k) {
-                        if (sh.ws[k][0] > B0 || (sh.ws[k][0] == B0 && sh.wi[k][0] < I0)) {
-                            B0 = sh.ws[k][0];
-                            V0 = sh.ws[k][1];
-                            I0 = sh.wi[k][0];
-                        }
-                        A0 = fmax(A0, sh.ws[k][2]);
-                    }
-                    sh.part[ph].best = B0;
-                    sh.part[ph].bval = V0;
-                    sh.part[ph].amax = A0;
-                    sh.part[ph].bi = I0;
-                }
-                cl.sync();
-                if (tid == 0) {
-                    double B0 = -1, V0 = 0, A0 = 0;
-                    int I0 = 0x7fffffff;
-                    for (int k = 0; k < CS; ++k) {
-                        const ClPart* P = cl.map_shared_rank(&sh.part[ph], k);
-                        if (P->best > B0 || (P->best == B0 && P->bi < I0)) {
-                            B0 = P->best;
-                            V0 = P->bval;
-                            I0 = P->bi;
-                        }
-                        A0 = fmax(A0, P->amax);
-                    }
-                    sh.bc[0] = B0;
-                    sh.bc[1] = V0;
-                    sh.bc[2] = A0;
-                    sh.bci[0] = I0;
-                }
-                ph ^= 1;
-                __syncthreads();
-                best = (R)sh.bc[0];
-                bval = (R)sh.bc[1];
-                amax = (R)sh.bc[2];
-                bi = sh.bci[0];
-                __syncthreads();
-            }
+            const Red oc = cl_reduce(cl, sh, ph, qc, 0);
+            const R best = (R)oc.av, amax = (R)oc.x0;
+            const int bi = oc.ai;
             if (!(best > eps0 * amax)) {
                 ++rej;
                 if (++run >= REJ_RUN) {
@@ -382,34 +520,17 @@ k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __rest
                     break;
                 }
                 // lowest unused column over the whole cluster
-                int cand = 0x7fffffff;
-                for (int k = gt; k < words; k += GT) {
+                Red qn;
+                red_init(qn);
+                for (int k = gt; k < wn; k += GT) {
                     uint32_t free_bits = ~used[k];
-                    if (k == words - 1 && (n & 31)) free_bits &= (1u << (n & 31)) - 1u;
+                    if (k == wn - 1 && (n & 31)) free_bits &= (1u << (n & 31)) - 1u;
                     if (free_bits) {
-                        cand = k * 32 + __ffs(free_bits) - 1;
+                        qn.mn = k * 32 + __ffs(free_bits) - 1;
                         break;
                     }
                 }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) cand = min(cand, __shfl_xor_sync(0xffffffffu, cand, o));
-                if (lane == 0) sh.wi[w][1] = cand;
-                __syncthreads();
-                if (tid == 0) {
-                    int cm = 0x7fffffff;
-                    for (int k = 0; k < CTA_WARPS; ++k) cm = min(cm, sh.wi[k][1]);
-                    sh.part[ph].cand = cm;
-                }
-                cl.sync();
-                if (tid == 0) {
-                    int cm = 0x7fffffff;
-                    for (int k = 0; k < CS; ++k) cm = min(cm, cl.map_shared_rank(&sh.part[ph], k)->cand);
-                    sh.bci[1] = cm;
-                }
-                ph ^= 1;
-                __syncthreads();
-                cand = sh.bci[1];
-                __syncthreads();
+                const int cand = cl_reduce(cl, sh, ph, qn, 0).mn;
                 if (cand == 0x7fffffff || cand >= n) {
                     converged = true;
                     break;
@@ -418,29 +539,40 @@ k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __rest
                 continue;
             }
             run = 0;
-            const R piv = bval;
+            const R piv = (R)oc.aval;
+            const R uiref = (R)oc.s0 / piv;
+            if (gt == 0) seen[bi >> 5] |= 1u << (bi & 31);
             if (tid < r) sg[tid] = U[(int64_t)tid * m + bi];
             __syncthreads();
-            // residual row, scaled column, norms and next-column candidates
+            // residual row, scaled column, reference row, norms, next column
             const Pt<R> pi = load_pt<R>(X, B.row0 + bi);
             R* __restrict__ Vr = V + (int64_t)r * n;
-            double nv2 = 0.0, nu2 = 0.0;
-            R vb = -1;
-            int vbj = 0x7fffffff;
+            Red qr;
+            red_init(qr);
             for (int jj = gt; jj < n; jj += GT) {
-                R v = phi<KERN>(dist2(pi, load_pt<R>(X, B.col0 + jj)), c);
-                for (int l = 0; l < r; ++l) v -= sg[l] * V[(int64_t)l * n + jj];
+                Resid<R> rs_;
+                rs_.init(phi<KERN>(dist2(pi, load_pt<R>(X, B.col0 + jj)), c));
+                for (int l = 0; l < r; ++l) rs_.sub(sg[l], V[(int64_t)l * n + jj]);
+                const R v = rs_.value();
                 Vr[jj] = v;
-                nv2 += (double)v * (double)v;
-                if (!((used[jj >> 5] >> (jj & 31)) & 1u) && fabs(v) > vb) {
-                    vb = fabs(v);
-                    vbj = jj;
+                qr.s1 += (double)v * (double)v;
+                Resid<R> rx;
+                rx.s = rr[jj];
+                rx.setc(rc[jj]);
+                rx.sub(uiref, v);
+                rr[jj] = rx.s;
+                rc[jj] = rx.getc();
+                const R x = rx.value();
+                qr.x1 = fmax(qr.x1, (double)fabs(x));
+                if (!((used[jj >> 5] >> (jj & 31)) & 1u) && (double)fabs(x) > qr.av) {
+                    qr.av = fabs(x);
+                    qr.ai = jj;
                 }
             }
             for (int i = gt; i < m; i += GT) {
                 const R u = Ur[i] / piv;
                 Ur[i] = u;
-                nu2 += (double)u * (double)u;
+                qr.s0 += (double)u * (double)u;
             }
             for (int l = 0; l < r; ++l) {
                 const R* Ul = U + (int64_t)l * m;
@@ -454,85 +586,54 @@ k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __rest
                     sh.wm[w][l] = ddv;
                 }
             }
-            nu2 = warp_sum(nu2);
-            nv2 = warp_sum(nv2);
-            warp_argmax(vb, vbj);
-            if (lane == 0) {
-                sh.ws[w][0] = nu2;
-                sh.ws[w][1] = nv2;
-                sh.ws[w][2] = (double)vb;
-                sh.wi[w][0] = vbj;
-            }
-            __syncthreads();
-            {
-                ClPart& P = sh.part[ph];
-                if (tid < r) {
-                    double su = 0.0, sv = 0.0;
-                    for (int k = 0; k < CTA_WARPS; ++k) {
-                        su += sh.wl[k][tid];
-                        sv += sh.wm[k][tid];
-                    }
-                    P.du[tid] = su;
-                    P.dv[tid] = sv;
-                }
-                if (tid == 0) {
-                    double a0 = 0.0, a1 = 0.0, B0 = -1.0;
-                    int I0 = 0x7fffffff;
-                    for (int k = 0; k < CTA_WARPS; ++k) {
-                        a0 += sh.ws[k][0];
-                        a1 += sh.ws[k][1];
-                        if (sh.ws[k][2] > B0 || (sh.ws[k][2] == B0 && sh.wi[k][0] < I0)) {
-                            B0 = sh.ws[k][2];
-                            I0 = sh.wi[k][0];
-                        }
-                    }
-                    P.nu2 = a0;
-                    P.nv2 = a1;
-                    P.vbest = B0;
-                    P.vbj = I0;
-                }
-            }
-            cl.sync();
-            if (w == 0) {
-                // cross term sum_l (sum_ranks du_l)(sum_ranks dv_l), in rank order
-                double cr = 0.0;
-                for (int l0 = 0; l0 < r; l0 += 32) {
-                    const int l = l0 + lane;
-                    double su = 0.0, sv = 0.0;
-                    if (l < r)
-                        for (int k = 0; k < CS; ++k) {
-                            const ClPart* P = cl.map_shared_rank(&sh.part[ph], k);
-                            su += P->du[l];
-                            sv += P->dv[l];
-                        }
-                    cr += warp_sum(su * sv);
-                }
-                if (lane == 0) {
-                    double a0 = 0.0, a1 = 0.0, B0 = -1.0;
-                    int I0 = 0x7fffffff;
-                    for (int k = 0; k < CS; ++k) {
-                        const ClPart* P = cl.map_shared_rank(&sh.part[ph], k);
-                        a0 += P->nu2;
-                        a1 += P->nv2;
-                        if (P->vbest > B0 || (P->vbest == B0 && P->vbj < I0)) {
-                            B0 = P->vbest;
-                            I0 = P->vbj;
-                        }
-                    }
-                    sh.bc[0] = a0;
-                    sh.bc[1] = a1;
-                    sh.bc[2] = cr;
-                    sh.bci[0] = I0;
-                }
-            }
-            ph ^= 1;
-            __syncthreads();
-            const double NU2 = sh.bc[0], NV2 = sh.bc[1], cross = sh.bc[2];
-            const int nj = sh.bci[0];
-            __syncthreads();
+            const Red orr = cl_reduce(cl, sh, ph, qr, r);
+            const double NU2 = orr.s0, NV2 = orr.s1, cross = sh.cross;
+            rmax = orr.x1;
+            int nj = orr.ai;
             S2 += 2.0 * cross + NU2 * NV2;
             ++r;
-            if (thr >= 0.0 && sqrt(NU2) * sqrt(NV2) <= thr * sqrt(fmax(S2, 0.0))) {
+            // a resolved reference row moves to the lowest row not seen yet
+            const double rlim = rtol * sqrt(fmax(S2, 0.0) / (double)m);
+            if (!(rmax > rlim)) {
+                Red qs;
+                red_init(qs);
+                for (int k = gt; k < wm; k += GT) {
+                    uint32_t free_bits = ~seen[k];
+                    if (k == wm - 1 && (m & 31)) free_bits &= (1u << (m & 31)) - 1u;
+                    if (free_bits) {
+                        qs.mn = k * 32 + __ffs(free_bits) - 1;
+                        break;
+                    }
+                }
+                const int cand = cl_reduce(cl, sh, ph, qs, 0).mn;
+                if (cand != 0x7fffffff && cand < m) {
+                    iref = cand;
+                    if (gt == 0) seen[iref >> 5] |= 1u << (iref & 31);
+                    if (tid < r) sg[tid] = U[(int64_t)tid * m + iref];
+                    __syncthreads();
+                    const Pt<R> pr = load_pt<R>(X, B.row0 + iref);
+                    Red qf;
+                    red_init(qf);
+                    for (int jj = gt; jj < n; jj += GT) {
+                        Resid<R> rs_;
+                        rs_.init(phi<KERN>(dist2(pr, load_pt<R>(X, B.col0 + jj)), c));
+                        for (int l = 0; l < r; ++l) rs_.sub(sg[l], V[(int64_t)l * n + jj]);
+                        const R x = rs_.value();
+                        rr[jj] = rs_.s;
+                        rc[jj] = rs_.getc();
+                        qf.x1 = fmax(qf.x1, (double)fabs(x));
+                        if (!((used[jj >> 5] >> (jj & 31)) & 1u) && (double)fabs(x) > qf.av) {
+                            qf.av = fabs(x);
+                            qf.ai = jj;
+                        }
+                    }
+                    const Red of = cl_reduce(cl, sh, ph, qf, 0);
+                    rmax = of.x1;
+                    nj = of.ai;
+                }
+            }
+            if (thr >= 0.0 && sqrt(NU2) * sqrt(NV2) <= thr * sqrt(fmax(S2, 0.0)) &&
+                !(rmax > rlim)) {
                 converged = true;
                 break;
             }
@@ -568,13 +669,16 @@ void launch_all(const KernelParams& kp, const DeviceCoords& X, const AcaArgs& a,
     case 3: k_aca_warp<R, KERN, 16><<<wgrid, WARP_NT, 0, s>>>(kp, X, a, order, n, thr); note_launch(); break;
     default: {
         const int cs = cls == 4 ? 1 : (cls == 5 ? 4 : 8);
+        const int64_t dim = std::min<int64_t>(cls == 6 ? max_n : kAcaClassDim[cls], max_n);
         int occ = 0;
         HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_aca_cluster<R, KERN>,
                                                               CTA_NT, 0));
         int64_t nclusters = std::min<int64_t>(n, std::max<int64_t>(1, (int64_t)std::max(occ, 1) *
                                                                          num_sms() / cs));
-        const int64_t words = ceil_div(max_n, 32);
+        const int64_t words = ceil_div(dim, 32);
         DevBuf<uint32_t> usedpool((size_t)(nclusters * words), s);
+        DevBuf<uint32_t> seenpool((size_t)(nclusters * words), s);
+        DevBuf<R> rrpool((size_t)(nclusters * 2 * dim), s);
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)(nclusters * cs));
         cfg.blockDim = dim3(CTA_NT);
@@ -588,14 +692,13 @@ void launch_all(const KernelParams& kp, const DeviceCoords& X, const AcaArgs& a,
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         HM_CUDA(cudaLaunchKernelEx(&cfg, k_aca_cluster<R, KERN>, kp, X, a, order, n, thr,
-                                   usedpool.p, words));
+                                   usedpool.p, seenpool.p, rrpool.p, words, dim));
         note_launch();
         break;
     }
     }
     HM_LAUNCH("aca");
 }
-
 
 }  // namespace
 

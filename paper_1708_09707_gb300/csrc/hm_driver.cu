@@ -136,6 +136,7 @@ void add_perm_offsets(hm_handle_s& h)
 
 void matvec(hm_handle_s& h, const double* x, double* y, int nrhs, cudaStream_t s)
 {
+    if (h.opt.structure_only) fail(HM_EINVAL, "the handle was built with structure_only");
     const int64_t N = h.Ntot;
     const bool xd = is_device_ptr(x), yd = is_device_ptr(y);
     if ((!xd || !yd) && !h.xbuf.p) {

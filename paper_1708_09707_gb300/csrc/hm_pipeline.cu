@@ -638,6 +638,22 @@ void build_sets(hm_handle_s& h, int nsets, const double* points_all, const int64
     dense.clear();
     if (pts_dev.p) pts_dev.release();
 
+    if (opt.structure_only) {
+        alloc_factor_meta(h);
+        hm_stats& st = h.stats;
+        st.n_points = Ntot;
+        st.n_nodes = nn;
+        st.n_adm = h.n_adm;
+        st.n_dense = h.n_dense;
+        st.n_tiles = h.n_tiles;
+        st.depth = h.sets[0].depth;
+        st.d = h.sets[0].d;
+        st.precision = h.precision;
+        st.near_format = h.near_format;
+        HM_CUDA(cudaStreamSynchronize(s));
+        return;
+    }
+
     // batched ACA of the admissible leaves
     {
         Timer ta(s);

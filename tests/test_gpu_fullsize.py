@@ -56,13 +56,11 @@ def test_fullsize_structure_bit_exact(hm, orc, name):
     w = inputs.WORKLOADS[name]
     pts = inputs.workload_points(name)
     O = orc.HMatrix(pts, w["kernel"], w["ell"], w["leaf"], w["eta"], w["eps"], compress=False)
-    # the structure of the handle does not depend on the precision
-    from paper_1708_09707_gb300 import hm as H
-    import ctypes
-    L = H.lib()
-    # build structure + compression in mixed precision (fits for both workloads)
+    # the integer structure does not depend on the compression that follows
     Hm = hm.HMatrix(pts, w["kernel"], w["ell"], w["leaf"], w["eta"], w["eps"],
-                    precision=hm.PREC_MIXED, near_format=hm.NEAR_BF16X2)
+                    structure_only=True)
+    with pytest.raises(hm.HMError):
+        Hm.matvec(np.zeros(w["n"]))
     s = Hm.structure()
     assert np.array_equal(s["codes"], O.codes())
     assert np.array_equal(s["perm"], O.perm())
