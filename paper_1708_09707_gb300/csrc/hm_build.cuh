@@ -63,12 +63,36 @@ void aca_run(int precision, const KernelParams& kp, const DeviceCoords& X,
              cudaStream_t s);
 
 // ---------------------------------------------------------------------------
+// Product layout. The product gathers, for every row tile (a leaf of the
+// cluster tree), slices of the low-rank factors U_b and of the dense blocks
+// A_b restricted to the tile's rows. Both are stored tile-major: the slices a
+// tile reads are contiguous and in its gather order, each slice column-major
+// with the tile's row count as leading dimension.
+// ---------------------------------------------------------------------------
+struct LrDesc {        // one (tile, admissible block) pair
+    int64_t uoff;      // element offset of the slice in the tile-major U store
+    int64_t toff;      // offset of t_b = V_b^T x in the t buffer
+    int32_t k;         // rank (columns of the slice)
+    int32_t pad;
+};
+
+struct DnDesc {        // one (tile, dense block) pair
+    int64_t noff;      // element offset of the slice in the near-field store
+    int64_t col0;      // first Morton column of the block
+    int32_t n;         // columns of the slice
+    int32_t pad;
+};
+
+// ---------------------------------------------------------------------------
 // Near field (hm_near.cu)
 // ---------------------------------------------------------------------------
-// Evaluate the dense leaf blocks into the near-field store in the given format
-// (column-major m x n per block at off[b]; BF16X2 stores hi then lo planes).
+// Evaluate the dense leaf blocks directly into their tile slices: entry e of
+// the dense gather list is block ent[e].x restricted to the rows of tile
+// etile[e] (offset ent[e].y in the block). BF16X2 slices hold the hi plane
+// followed by the lo plane.
 void near_assemble(int near_format, const KernelParams& kp, const DeviceCoords& X,
-                   const Blk* blk, const int64_t* off, int64_t n, void* store,
+                   const Blk* blk, const int2* ent, const int32_t* etile,
+                   const int32_t* tile_m, const DnDesc* desc, int64_t n_ent, void* store,
                    cudaStream_t s);
 size_t near_entry_bytes(int near_format);
 
@@ -95,21 +119,18 @@ struct MvpPlan {
     const int32_t* tsum_count = nullptr;  // per block: work items
     int64_t n_multi = 0;                   // blocks with more than one item
     const int32_t* multi = nullptr;        // their ids
-    // dense blocks
-    int64_t n_dense = 0;
-    const Blk* dblk = nullptr;
-    const int64_t* doff = nullptr;
+    // tile-major stores of the U slices and of the near field
+    const void* ustore = nullptr;
     const void* near = nullptr;
     int64_t near_entries = 0;
-    // row tiles and their gather lists
+    // row tiles and their gather lists (CSR over tiles)
     int64_t n_tiles = 0;
     const int64_t* tile_row0 = nullptr;
     const int32_t* tile_m = nullptr;
-    const int64_t* lr_ptr = nullptr;    // CSR over tiles
-    const int2* lr_ent = nullptr;       // (block, row offset)
+    const int64_t* lr_ptr = nullptr;
+    const LrDesc* lr_desc = nullptr;
     const int64_t* dn_ptr = nullptr;
-    const int2* dn_ent = nullptr;
-    int max_tile = 0;
+    const DnDesc* dn_desc = nullptr;
     // permutation and diagonal shift
     const int64_t* perm = nullptr;      // Morton row -> caller index (absolute)
     double sigma2 = 0.0;
@@ -144,18 +165,22 @@ void mvp_run(const MvpPlan& P, MvpWork& W, const double* x, double* y, int accum
              cudaStream_t s, MvpTimer* timer = nullptr);
 // Build the gather lists of the plan (CSR by tile).
 struct MvpLists {
-    DevBuf<int64_t> tile_row0;
-    DevBuf<int32_t> tile_m;
     DevBuf<int64_t> lr_ptr, dn_ptr;
-    DevBuf<int2> lr_ent, dn_ent;
+    DevBuf<int2> lr_ent, dn_ent;          // (block, row offset of the tile)
+    DevBuf<int32_t> lr_tile, dn_tile;     // tile of every entry
+    DevBuf<LrDesc> lr_desc;
+    DevBuf<DnDesc> dn_desc;
     DevBuf<int2> vitems;
     DevBuf<int64_t> tpart_off, toff;
     DevBuf<int32_t> tsum_first, tsum_count, multi;
     int64_t n_tiles = 0, n_vitems = 0, tpart_len = 0, t_len = 0, n_multi = 0;
-    int max_tile = 0;
+    int64_t n_lr = 0, n_dn = 0, u_elems = 0, near_elems = 0;
 };
 void mvp_build_lists(const Blk* ablk, const int32_t* rank, int64_t n_adm, const Blk* dblk,
                      int64_t n_dense, const int64_t* leaf_row0, const int32_t* leaf_m,
                      int64_t n_tiles, MvpLists& L, cudaStream_t s);
+// Copy every block's U rows of every tile it covers into the tile-major store.
+void mvp_relayout_u(int precision, const MvpLists& L, const Blk* ablk, const uint64_t* Uptr,
+                    const int32_t* tile_m, void* ustore, cudaStream_t s);
 
 }  // namespace hm

@@ -96,11 +96,6 @@ __global__ void k_cg_p(const double* __restrict__ sc, const double* __restrict__
     p[i] = r[i] + beta * p[i];
 }
 
-__global__ void k_f32_to_f64(const float* __restrict__ a, int64_t n, double* __restrict__ b)
-{
-    int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x;
-    if (i < n) b[i] = a[i];
-}
 
 __global__ void k_fill_i32(int32_t* __restrict__ p, int64_t n, int32_t v)
 {
@@ -227,26 +222,58 @@ void export_tree(hm_handle_s& h, int64_t* lo, int64_t* hi, double* bbmin, double
 void export_factors(hm_handle_s& h, int64_t b, double* U, double* V, int* rank)
 {
     if (b < 0 || b >= h.n_adm) fail(HM_EINVAL, "block index out of range");
+    if (h.opt.structure_only) fail(HM_EINVAL, "the handle was built with structure_only");
     cudaStream_t s = h.stream;
     Blk B;
     int r = 0;
-    uint64_t up = 0, vp = 0;
+    uint64_t vp = 0;
     HM_CUDA(cudaMemcpyAsync(&B, h.ablk.p + b, sizeof(Blk), cudaMemcpyDeviceToHost, s));
     HM_CUDA(cudaMemcpyAsync(&r, h.rank.p + b, sizeof(int), cudaMemcpyDeviceToHost, s));
-    HM_CUDA(cudaMemcpyAsync(&up, h.Uptr.p + b, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
     HM_CUDA(cudaMemcpyAsync(&vp, h.Vptr.p + b, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
     HM_CUDA(cudaStreamSynchronize(s));
     if (rank) *rank = r;
-    const int64_t nu = (int64_t)r * B.m, nv = (int64_t)r * B.n;
-    if (h.precision == HM_PREC_FP64) {
-        if (U && nu) copy_out(U, (const void*)up, nu * sizeof(double), s);
-        if (V && nv) copy_out(V, (const void*)vp, nv * sizeof(double), s);
-    } else {
-        DevBuf<double> t(std::max<int64_t>(nu + nv, 1), s);
-        if (nu) k_f32_to_f64<<<grid_for(nu), NT, 0, s>>>((const float*)up, nu, t.p); note_launch();
-        if (nv) k_f32_to_f64<<<grid_for(nv), NT, 0, s>>>((const float*)vp, nv, t.p + nu); note_launch();
-        if (U && nu) copy_out(U, t.p, nu * sizeof(double), s);
-        if (V && nv) copy_out(V, t.p + nu, nv * sizeof(double), s);
+    const bool f64 = h.precision == HM_PREC_FP64;
+    const size_t esz = f64 ? 8 : 4;
+    auto to_double = [&](const std::vector<char>& raw, size_t cnt, double* out) {
+        for (size_t e = 0; e < cnt; ++e)
+            out[e] = f64 ? reinterpret_cast<const double*>(raw.data())[e]
+                         : (double)reinterpret_cast<const float*>(raw.data())[e];
+    };
+    const int64_t nv = (int64_t)r * B.n;
+    if (V && nv) {
+        std::vector<char> raw(nv * esz);
+        HM_CUDA(cudaMemcpy(raw.data(), (const void*)vp, nv * esz, cudaMemcpyDeviceToHost));
+        std::vector<double> tmp(nv);
+        to_double(raw, nv, tmp.data());
+        copy_out(V, tmp.data(), nv * sizeof(double), s);
+    }
+    if (U && r) {
+        const MvpLists& L = h.lists;
+        if (h.h_lr_ent.empty() && L.n_lr > 0) {
+            h.h_lr_ent.resize(L.n_lr);
+            h.h_lr_desc.resize(L.n_lr);
+            h.h_lr_tile.resize(L.n_lr);
+            h.h_tile_m.resize(h.n_tiles);
+            HM_CUDA(cudaMemcpy(h.h_lr_ent.data(), L.lr_ent.p, L.n_lr * sizeof(int2), cudaMemcpyDeviceToHost));
+            HM_CUDA(cudaMemcpy(h.h_lr_desc.data(), L.lr_desc.p, L.n_lr * sizeof(LrDesc), cudaMemcpyDeviceToHost));
+            HM_CUDA(cudaMemcpy(h.h_lr_tile.data(), L.lr_tile.p, L.n_lr * sizeof(int32_t), cudaMemcpyDeviceToHost));
+            HM_CUDA(cudaMemcpy(h.h_tile_m.data(), h.tile_m.p, h.n_tiles * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        }
+        std::vector<double> tmp((size_t)r * B.m, 0.0);
+        for (int64_t e = 0; e < L.n_lr; ++e) {
+            if (h.h_lr_ent[e].x != b) continue;
+            const int rows = h.h_tile_m[h.h_lr_tile[e]];
+            const int rowoff = h.h_lr_ent[e].y;
+            std::vector<char> raw((size_t)r * rows * esz);
+            HM_CUDA(cudaMemcpy(raw.data(), h.ustore.p + h.h_lr_desc[e].uoff * esz, raw.size(),
+                               cudaMemcpyDeviceToHost));
+            std::vector<double> sl((size_t)r * rows);
+            to_double(raw, sl.size(), sl.data());
+            for (int l = 0; l < r; ++l)
+                for (int i = 0; i < rows; ++i)
+                    tmp[(size_t)l * B.m + rowoff + i] = sl[(size_t)l * rows + i];
+        }
+        copy_out(U, tmp.data(), tmp.size() * sizeof(double), s);
     }
     HM_CUDA(cudaStreamSynchronize(s));
 }

@@ -40,11 +40,15 @@ struct hm_handle_s {
     hm::DevBuf<int32_t> tile_m;
     // factors
     hm::DevBuf<int32_t> kres, rank, nrej, flags;
-    hm::DevBuf<uint64_t> Uptr, Vptr;
-    std::vector<std::unique_ptr<hm::FactorSegment>> segments;
-    // near field
-    hm::DevBuf<int64_t> doff;
+    hm::DevBuf<uint64_t> Uptr, Vptr;   // per block (U: valid until the relayout)
+    std::vector<std::unique_ptr<hm::FactorSegment>> usegments, vsegments;
+    hm::DevBuf<char> ustore;            // tile-major U slices
+    // near field (tile-major slices)
     hm::DevBuf<char> near;
+    // host copies of the gather lists for factor export (filled on demand)
+    std::vector<int2> h_lr_ent;
+    std::vector<hm::LrDesc> h_lr_desc;
+    std::vector<int32_t> h_lr_tile, h_tile_m;
     // product
     hm::MvpLists lists;
     hm::MvpPlan plan;

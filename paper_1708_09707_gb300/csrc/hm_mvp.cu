@@ -8,7 +8,10 @@
 // writes y in the caller's order.
 //
 // Traffic per product: every factor entry and every near-field entry is read
-// exactly once; x is gathered once (L2-resident reuse), y written once.
+// exactly once; x is gathered once (L2-resident reuse), y written once. The
+// U slices and near-field slices a tile reads are contiguous (tile-major
+// stores), and each gather entry carries its own descriptor, so the gather
+// streams its data without dependent metadata loads.
 #include "hm_kernel_fn.cuh"
 
 namespace hm {
@@ -18,7 +21,7 @@ namespace {
 constexpr int NT = 256;
 constexpr int VT_NT = 256;        // threads per CTA of the V^T x kernel
 constexpr int VCH = 256;          // columns per V^T x work item (8 per lane)
-constexpr int TILE_NT = 128;      // threads per CTA of the gather kernel
+constexpr int TILE_NT = 256;      // threads per CTA of the gather kernel
 constexpr int TILE_WARPS = TILE_NT / 32;
 constexpr int TROWS = 64;         // rows handled per pass of a tile
 
@@ -124,75 +127,199 @@ struct Acc<float> {
     __device__ double value() const { return (double)s + (double)c; }
 };
 
+// Slices use an even leading dimension (the tile's rows rounded up), so every
+// column starts on an 8-byte boundary for float pairs, 16 for double pairs.
+__host__ __device__ __forceinline__ int slice_ld(int rows) { return rows + (rows & 1); }
+
+// Rows 2i and 2i+1 of column c of a U slice.
+__device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
+__device__ __forceinline__ double2 ld2(const double* p) { return *reinterpret_cast<const double2*>(p); }
+
+template <class R>
+struct V2;
+template <>
+struct V2<float> {
+    using T = float2;
+};
+template <>
+struct V2<double> {
+    using T = double2;
+};
+
+// Rows 2i and 2i+1 of column c of a near-field slice starting at element o
+// (BF16X2 slices are a hi plane followed by a lo plane of `plane` entries).
 template <class R, int FMT>
-__device__ __forceinline__ R near_at(const void* store, int64_t o, int64_t mn, int64_t e)
+__device__ __forceinline__ typename V2<R>::T near2(const void* store, int64_t o, int64_t plane,
+                                                   int64_t e)
 {
-    if (FMT == HM_NEAR_FP64) return (R) static_cast<const double*>(store)[o + e];
-    if (FMT == HM_NEAR_FP32) return (R) static_cast<const float*>(store)[o + e];
-    if (FMT == HM_NEAR_BF16X2) {
+    typename V2<R>::T v;
+    if (FMT == HM_NEAR_FP64) {
+        const double2 a = *reinterpret_cast<const double2*>(static_cast<const double*>(store) + o + e);
+        v.x = (R)a.x;
+        v.y = (R)a.y;
+    } else if (FMT == HM_NEAR_FP32) {
+        const float2 a = *reinterpret_cast<const float2*>(static_cast<const float*>(store) + o + e);
+        v.x = (R)a.x;
+        v.y = (R)a.y;
+    } else if (FMT == HM_NEAR_BF16X2) {
         const __nv_bfloat16* S = static_cast<const __nv_bfloat16*>(store) + 2 * o;
-        return (R)(__bfloat162float(S[e]) + __bfloat162float(S[mn + e]));
+        const float2 h = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(S + e));
+        const float2 l = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(S + plane + e));
+        v.x = (R)(h.x + l.x);
+        v.y = (R)(h.y + l.y);
+    } else {
+        const __nv_bfloat16* S = static_cast<const __nv_bfloat16*>(store) + o;
+        const float2 h = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(S + e));
+        v.x = (R)h.x;
+        v.y = (R)h.y;
     }
-    return (R)__bfloat162float(static_cast<const __nv_bfloat16*>(store)[o + e]);
+    return v;
 }
 
-// One CTA per row tile; warps take the tile's gather entries round-robin and
-// lanes own rows lane and lane + 32 of the current 64-row pass.
+constexpr int DESC_CHUNK = 128;   // gather descriptors staged in shared memory
+
+// One CTA per row tile. Lane l owns rows 2l and 2l+1 of the current 64-row
+// pass and reads both with one vector load per column; warps take the tile's
+// gather entries round-robin, four columns at a time, and prefetch the next
+// entry's multipliers (t_b or x) while the current entry streams.
 template <class R, int FMT>
 __global__ void __launch_bounds__(TILE_NT)
 k_tile(MvpPlan P, const R* __restrict__ xm, const R* __restrict__ t, const double* __restrict__ x,
        double* __restrict__ y, int accumulate)
 {
+    using R2 = typename V2<R>::T;
     __shared__ double part[TILE_WARPS][TROWS];
+    __shared__ LrDesc lds[DESC_CHUNK];
+    __shared__ DnDesc dds[DESC_CHUNK];
     const int64_t tile = blockIdx.x;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t r0 = P.tile_row0[tile];
     const int mt = P.tile_m[tile];
+    const int ld = slice_ld(mt);
     const int64_t l0 = P.lr_ptr[tile], l1 = P.lr_ptr[tile + 1];
     const int64_t d0 = P.dn_ptr[tile], d1 = P.dn_ptr[tile + 1];
+    const R* __restrict__ US = static_cast<const R*>(P.ustore);
     for (int rp = 0; rp < mt; rp += TROWS) {
         const int rows = min(TROWS, mt - rp);
+        const int ir = rp + 2 * lane;           // first of the lane's two rows
+        const bool act = 2 * lane < rows;
         Acc<R> acc0, acc1;
-        const int i0 = lane, i1 = lane + 32;
         // low-rank contributions U_b(rows, :) t_b
-        for (int64_t e = l0 + w; e < l1; e += TILE_WARPS) {
-            const int2 en = P.lr_ent[e];
-            const int b = en.x;
-            const int k = P.rank[b];
-            const int m = P.ablk[b].m;
-            const R* __restrict__ U = reinterpret_cast<const R*>(P.Uptr[b]) + en.y + rp;
-            const R* __restrict__ tb = t + P.toff[b];
-            R s0 = 0, s1 = 0;
-            for (int l = 0; l < k; ++l) {
-                const R tl = tb[l];
-                const R* Ul = U + (int64_t)l * m;
-                if (i0 < rows) s0 += Ul[i0] * tl;
-                if (i1 < rows) s1 += Ul[i1] * tl;
+        for (int64_t c0 = l0; c0 < l1; c0 += DESC_CHUNK) {
+            const int nc = (l1 - c0) < DESC_CHUNK ? (int)(l1 - c0) : DESC_CHUNK;
+            __syncthreads();
+            for (int q = threadIdx.x; q < nc; q += TILE_NT) lds[q] = P.lr_desc[c0 + q];
+            __syncthreads();
+            int q = w;
+            LrDesc dn;
+            R tn = 0;
+            if (q < nc) {
+                dn = lds[q];
+                tn = (lane < dn.k) ? t[dn.toff + lane] : R(0);
             }
-            acc0.add(s0);
-            acc1.add(s1);
+            for (; q < nc; q += TILE_WARPS) {
+                const LrDesc d = dn;
+                R tv = tn;
+                if (q + TILE_WARPS < nc) {
+                    dn = lds[q + TILE_WARPS];
+                    tn = (lane < dn.k) ? t[dn.toff + lane] : R(0);
+                }
+                const R* __restrict__ Us = US + d.uoff + ir;
+                const int k = d.k;
+                R s0 = 0, s1 = 0;
+                for (int lb = 0; lb < k; lb += 32) {
+                    if (lb > 0) tv = (lb + lane < k) ? t[d.toff + lb + lane] : R(0);
+                    const int kn = min(32, k - lb);
+                    int l = 0;
+                    for (; l + 4 <= kn; l += 4) {
+                        const R* Uc = Us + (int64_t)(lb + l) * ld;
+                        R2 a0 = {0, 0}, a1 = {0, 0}, a2 = {0, 0}, a3 = {0, 0};
+                        if (act) {
+                            a0 = ld2(Uc);
+                            a1 = ld2(Uc + ld);
+                            a2 = ld2(Uc + 2 * ld);
+                            a3 = ld2(Uc + 3 * ld);
+                        }
+                        const R t0 = __shfl_sync(0xffffffffu, tv, l);
+                        const R t1 = __shfl_sync(0xffffffffu, tv, l + 1);
+                        const R t2 = __shfl_sync(0xffffffffu, tv, l + 2);
+                        const R t3 = __shfl_sync(0xffffffffu, tv, l + 3);
+                        s0 += a0.x * t0 + a1.x * t1 + a2.x * t2 + a3.x * t3;
+                        s1 += a0.y * t0 + a1.y * t1 + a2.y * t2 + a3.y * t3;
+                    }
+                    for (; l < kn; ++l) {
+                        const R* Uc = Us + (int64_t)(lb + l) * ld;
+                        const R tl = __shfl_sync(0xffffffffu, tv, l);
+                        if (act) {
+                            const R2 a = ld2(Uc);
+                            s0 += a.x * tl;
+                            s1 += a.y * tl;
+                        }
+                    }
+                }
+                acc0.add(s0);
+                acc1.add(s1);
+            }
         }
         // dense contributions A_b(rows, :) x|sigma
-        for (int64_t e = d0 + w; e < d1; e += TILE_WARPS) {
-            const int2 en = P.dn_ent[e];
-            const int b = en.x;
-            const Blk B = P.dblk[b];
-            const int64_t o = P.doff[b];
-            const int64_t mn = (int64_t)B.m * B.n;
-            const R* __restrict__ xs = xm + B.col0;
-            R s0 = 0, s1 = 0;
-            const int ra = en.y + rp + i0, rb = en.y + rp + i1;
-            for (int j = 0; j < B.n; ++j) {
-                const R xj = xs[j];
-                const int64_t cj = (int64_t)j * B.m;
-                if (i0 < rows) s0 += near_at<R, FMT>(P.near, o, mn, cj + ra) * xj;
-                if (i1 < rows) s1 += near_at<R, FMT>(P.near, o, mn, cj + rb) * xj;
+        for (int64_t c0 = d0; c0 < d1; c0 += DESC_CHUNK) {
+            const int nc = (d1 - c0) < DESC_CHUNK ? (int)(d1 - c0) : DESC_CHUNK;
+            __syncthreads();
+            for (int q = threadIdx.x; q < nc; q += TILE_NT) dds[q] = P.dn_desc[c0 + q];
+            __syncthreads();
+            int q = w;
+            DnDesc dn;
+            R xn = 0;
+            if (q < nc) {
+                dn = dds[q];
+                xn = (lane < dn.n) ? xm[dn.col0 + lane] : R(0);
             }
-            acc0.add(s0);
-            acc1.add(s1);
+            for (; q < nc; q += TILE_WARPS) {
+                const DnDesc d = dn;
+                R xv = xn;
+                if (q + TILE_WARPS < nc) {
+                    dn = dds[q + TILE_WARPS];
+                    xn = (lane < dn.n) ? xm[dn.col0 + lane] : R(0);
+                }
+                const int n = d.n;
+                const int64_t plane = (int64_t)ld * n;
+                R s0 = 0, s1 = 0;
+                for (int jb = 0; jb < n; jb += 32) {
+                    if (jb > 0) xv = (jb + lane < n) ? xm[d.col0 + jb + lane] : R(0);
+                    const int jn = min(32, n - jb);
+                    int j = 0;
+                    for (; j + 4 <= jn; j += 4) {
+                        const int64_t c = (int64_t)(jb + j) * ld + ir;
+                        R2 a0 = {0, 0}, a1 = {0, 0}, a2 = {0, 0}, a3 = {0, 0};
+                        if (act) {
+                            a0 = near2<R, FMT>(P.near, d.noff, plane, c);
+                            a1 = near2<R, FMT>(P.near, d.noff, plane, c + ld);
+                            a2 = near2<R, FMT>(P.near, d.noff, plane, c + 2 * ld);
+                            a3 = near2<R, FMT>(P.near, d.noff, plane, c + 3 * ld);
+                        }
+                        const R x0 = __shfl_sync(0xffffffffu, xv, j);
+                        const R x1 = __shfl_sync(0xffffffffu, xv, j + 1);
+                        const R x2 = __shfl_sync(0xffffffffu, xv, j + 2);
+                        const R x3 = __shfl_sync(0xffffffffu, xv, j + 3);
+                        s0 += a0.x * x0 + a1.x * x1 + a2.x * x2 + a3.x * x3;
+                        s1 += a0.y * x0 + a1.y * x1 + a2.y * x2 + a3.y * x3;
+                    }
+                    for (; j < jn; ++j) {
+                        const int64_t c = (int64_t)(jb + j) * ld + ir;
+                        const R xj = __shfl_sync(0xffffffffu, xv, j);
+                        if (act) {
+                            const R2 a = near2<R, FMT>(P.near, d.noff, plane, c);
+                            s0 += a.x * xj;
+                            s1 += a.y * xj;
+                        }
+                    }
+                }
+                acc0.add(s0);
+                acc1.add(s1);
+            }
         }
-        part[w][i0] = acc0.value();
-        part[w][i1] = acc1.value();
+        part[w][2 * lane] = acc0.value();
+        part[w][2 * lane + 1] = acc1.value();
         __syncthreads();
         if ((int)threadIdx.x < rows) {
             double s = 0.0;
@@ -301,6 +428,82 @@ void build_csr(const Blk* blk, int64_t nb, const int64_t* tr0, int64_t nt,
     HM_LAUNCH("csr");
 }
 
+// tile index of every CSR entry
+__global__ void k_entry_tiles(const int64_t* __restrict__ ptr, int64_t nt, int32_t* __restrict__ et)
+{
+    const int64_t tl = blockIdx.x;
+    if (tl >= nt) return;
+    for (int64_t e = ptr[tl] + threadIdx.x; e < ptr[tl + 1]; e += blockDim.x) et[e] = (int32_t)tl;
+}
+
+__global__ void k_lr_sizes(const int2* __restrict__ ent, const int32_t* __restrict__ et,
+                           int64_t ne, const int32_t* __restrict__ rank,
+                           const int32_t* __restrict__ tile_m, int64_t* __restrict__ sz)
+{
+    int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (e < ne) sz[e] = (int64_t)rank[ent[e].x] * slice_ld(tile_m[et[e]]);
+}
+
+__global__ void k_lr_desc(const int2* __restrict__ ent, int64_t ne,
+                          const int32_t* __restrict__ rank, const int64_t* __restrict__ off,
+                          const int64_t* __restrict__ toff, LrDesc* __restrict__ d)
+{
+    int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (e >= ne) return;
+    const int b = ent[e].x;
+    LrDesc q;
+    q.uoff = off[e];
+    q.toff = toff[b];
+    q.k = rank[b];
+    q.pad = 0;
+    d[e] = q;
+}
+
+__global__ void k_dn_sizes(const int2* __restrict__ ent, const int32_t* __restrict__ et,
+                           int64_t ne, const Blk* __restrict__ dblk,
+                           const int32_t* __restrict__ tile_m, int64_t* __restrict__ sz)
+{
+    int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (e < ne) sz[e] = (int64_t)dblk[ent[e].x].n * slice_ld(tile_m[et[e]]);
+}
+
+__global__ void k_dn_desc(const int2* __restrict__ ent, int64_t ne, const Blk* __restrict__ dblk,
+                          const int64_t* __restrict__ off, DnDesc* __restrict__ d)
+{
+    int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (e >= ne) return;
+    const Blk B = dblk[ent[e].x];
+    DnDesc q;
+    q.noff = off[e];
+    q.col0 = B.col0;
+    q.n = B.n;
+    q.pad = 0;
+    d[e] = q;
+}
+
+// One warp per low-rank entry: copy U_b(rowoff + 0..rows, 0..k) (leading
+// dimension m_b) into the entry's slice (leading dimension rows).
+template <class R>
+__global__ void k_relayout_u(const int2* __restrict__ ent, const int32_t* __restrict__ et,
+                             const LrDesc* __restrict__ desc, int64_t ne,
+                             const Blk* __restrict__ ablk, const uint64_t* __restrict__ Uptr,
+                             const int32_t* __restrict__ tile_m, R* __restrict__ dst)
+{
+    const int64_t w = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= ne) return;
+    const int2 en = ent[w];
+    const int rows = tile_m[et[w]];
+    const int ld = slice_ld(rows);
+    const int m = ablk[en.x].m;
+    const LrDesc d = desc[w];
+    const R* src = reinterpret_cast<const R*>(Uptr[en.x]) + en.y;
+    R* out = dst + d.uoff;
+    for (int l = 0; l < d.k; ++l)
+        for (int i = lane; i < ld; i += 32)
+            out[(int64_t)l * ld + i] = i < rows ? src[(int64_t)l * m + i] : R(0);
+}
+
 __global__ void k_vitems_count(const Blk* __restrict__ blk, const int32_t* __restrict__ rank,
                                int64_t nb, int64_t* __restrict__ cnt,
                                int64_t* __restrict__ multi_t, int32_t* __restrict__ ismulti,
@@ -345,6 +548,30 @@ void mvp_build_lists(const Blk* ablk, const int32_t* rank, int64_t n_adm, const 
     L.n_tiles = n_tiles;
     build_csr(ablk, n_adm, leaf_row0, n_tiles, L.lr_ptr, L.lr_ent, s);
     build_csr(dblk, n_dense, leaf_row0, n_tiles, L.dn_ptr, L.dn_ent, s);
+    {
+        int64_t h[2] = {0, 0};
+        HM_CUDA(cudaMemcpyAsync(&h[0], L.lr_ptr.p + n_tiles, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        HM_CUDA(cudaMemcpyAsync(&h[1], L.dn_ptr.p + n_tiles, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        HM_CUDA(cudaStreamSynchronize(s));
+        L.n_lr = h[0];
+        L.n_dn = h[1];
+    }
+    L.lr_tile.alloc(std::max<int64_t>(L.n_lr, 1), s);
+    L.dn_tile.alloc(std::max<int64_t>(L.n_dn, 1), s);
+    if (n_tiles > 0) {
+        k_entry_tiles<<<(unsigned)n_tiles, 64, 0, s>>>(L.lr_ptr.p, n_tiles, L.lr_tile.p); note_launch();
+        k_entry_tiles<<<(unsigned)n_tiles, 64, 0, s>>>(L.dn_ptr.p, n_tiles, L.dn_tile.p); note_launch();
+    }
+    // dense slices: offsets and descriptors
+    L.dn_desc.alloc(std::max<int64_t>(L.n_dn, 1), s);
+    if (L.n_dn > 0) {
+        DevBuf<int64_t> sz(L.n_dn, s), off(L.n_dn + 1, s);
+        k_dn_sizes<<<grid_for(L.n_dn), NT, 0, s>>>(L.dn_ent.p, L.dn_tile.p, L.n_dn, dblk, leaf_m, sz.p); note_launch();
+        scan_exclusive_i64(sz.p, off.p, L.n_dn, off.p + L.n_dn, s);
+        k_dn_desc<<<grid_for(L.n_dn), NT, 0, s>>>(L.dn_ent.p, L.n_dn, dblk, off.p, L.dn_desc.p); note_launch();
+        HM_CUDA(cudaMemcpyAsync(&L.near_elems, off.p + L.n_dn, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        HM_CUDA(cudaStreamSynchronize(s));
+    }
     // t offsets and V^T x work items
     const int64_t nb = std::max<int64_t>(n_adm, 1);
     DevBuf<int64_t> cnt(nb, s), ioff(nb, s), mt(nb, s), poff(nb, s), rk(nb, s), tot(3, s);
@@ -378,6 +605,32 @@ void mvp_build_lists(const Blk* ablk, const int32_t* rank, int64_t n_adm, const 
                                                      L.tpart_off.p, L.tsum_first.p,
                                                      L.tsum_count.p, L.multi.p); note_launch();
     HM_LAUNCH("vitems");
+    // low-rank slices: offsets and descriptors (t offsets are known now)
+    L.lr_desc.alloc(std::max<int64_t>(L.n_lr, 1), s);
+    if (L.n_lr > 0) {
+        DevBuf<int64_t> sz(L.n_lr, s), off(L.n_lr + 1, s);
+        k_lr_sizes<<<grid_for(L.n_lr), NT, 0, s>>>(L.lr_ent.p, L.lr_tile.p, L.n_lr, rank, leaf_m, sz.p); note_launch();
+        scan_exclusive_i64(sz.p, off.p, L.n_lr, off.p + L.n_lr, s);
+        k_lr_desc<<<grid_for(L.n_lr), NT, 0, s>>>(L.lr_ent.p, L.n_lr, rank, off.p, L.toff.p, L.lr_desc.p); note_launch();
+        HM_CUDA(cudaMemcpyAsync(&L.u_elems, off.p + L.n_lr, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        HM_CUDA(cudaStreamSynchronize(s));
+    }
+    HM_LAUNCH("descriptors");
+}
+
+void mvp_relayout_u(int precision, const MvpLists& L, const Blk* ablk, const uint64_t* Uptr,
+                    const int32_t* tile_m, void* ustore, cudaStream_t s)
+{
+    if (L.n_lr <= 0) return;
+    const unsigned g = (unsigned)ceil_div(L.n_lr * 32, NT);
+    if (precision == HM_PREC_FP64)
+        k_relayout_u<double><<<g, NT, 0, s>>>(L.lr_ent.p, L.lr_tile.p, L.lr_desc.p, L.n_lr, ablk, Uptr,
+                                              tile_m, static_cast<double*>(ustore));
+    else
+        k_relayout_u<float><<<g, NT, 0, s>>>(L.lr_ent.p, L.lr_tile.p, L.lr_desc.p, L.n_lr, ablk, Uptr,
+                                             tile_m, static_cast<float*>(ustore));
+    note_launch();
+    HM_LAUNCH("relayout U");
 }
 
 void mvp_alloc_work(const MvpPlan& P, MvpWork& W, cudaStream_t s)

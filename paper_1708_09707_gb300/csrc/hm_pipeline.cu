@@ -116,44 +116,51 @@ __global__ void k_classes(const Blk* __restrict__ blk, const uint32_t* __restric
     atomicAdd((unsigned long long*)&cls_count[c], 1ull);
 }
 
+// Reserved entries of block order[q]: total kres (m + n) and the U part kres m.
 __global__ void k_reserve(const Blk* __restrict__ blk, const uint32_t* __restrict__ order,
-                          int64_t n, const int32_t* __restrict__ kres, int64_t* __restrict__ res)
+                          int64_t n, const int32_t* __restrict__ kres, int64_t* __restrict__ res,
+                          int64_t* __restrict__ resu)
 {
     int64_t q = (int64_t)blockIdx.x * NT + threadIdx.x;
     if (q >= n) return;
     uint32_t b = order[q];
     res[q] = (int64_t)kres[b] * (blk[b].m + blk[b].n);
+    resu[q] = (int64_t)kres[b] * blk[b].m;
 }
 
-__global__ void k_set_ptrs(const Blk* __restrict__ blk, const uint32_t* __restrict__ order,
-                           int64_t q0, int64_t q1, const int64_t* __restrict__ pre,
-                           const int32_t* __restrict__ kres, char* base, int esz,
-                           uint64_t* __restrict__ Uptr, uint64_t* __restrict__ Vptr)
+// U of order[q] at ubase + (preu[q] - preu[q0]), V at vbase + (prev[q] - prev[q0])
+// where prev = pre - preu.
+__global__ void k_set_ptrs(const uint32_t* __restrict__ order, int64_t q0, int64_t q1,
+                           const int64_t* __restrict__ pre, const int64_t* __restrict__ preu,
+                           char* ubase, char* vbase, int esz, uint64_t* __restrict__ Uptr,
+                           uint64_t* __restrict__ Vptr)
 {
     int64_t q = q0 + (int64_t)blockIdx.x * NT + threadIdx.x;
     if (q >= q1) return;
     uint32_t b = order[q];
-    char* u = base + (pre[q] - pre[q0]) * esz;
-    Uptr[b] = (uint64_t)u;
-    Vptr[b] = (uint64_t)(u + (int64_t)kres[b] * blk[b].m * esz);
+    const int64_t u0 = preu[q0], v0 = pre[q0] - preu[q0];
+    Uptr[b] = (uint64_t)(ubase + (preu[q] - u0) * esz);
+    Vptr[b] = (uint64_t)(vbase + (pre[q] - preu[q] - v0) * esz);
 }
 
 __global__ void k_final_size(const Blk* __restrict__ blk, const uint32_t* __restrict__ order,
                              int64_t q0, int64_t q1, const int32_t* __restrict__ rank,
-                             int64_t* __restrict__ fs)
+                             int64_t* __restrict__ fsu, int64_t* __restrict__ fsv)
 {
     int64_t q = q0 + (int64_t)blockIdx.x * NT + threadIdx.x;
     if (q >= q1) return;
     uint32_t b = order[q];
-    fs[q - q0] = (int64_t)rank[b] * (blk[b].m + blk[b].n);
+    fsu[q - q0] = (int64_t)rank[b] * blk[b].m;
+    fsv[q - q0] = (int64_t)rank[b] * blk[b].n;
 }
 
 // Copy the rank-k columns of U and V (contiguous prefixes of the column-major
-// scratch) into the final segment; one CTA per block.
+// scratch) into exactly sized U and V segments; one CTA per block.
 __global__ void k_copy_factors(const Blk* __restrict__ blk, const uint32_t* __restrict__ order,
                                int64_t q0, int64_t q1, const int32_t* __restrict__ rank,
-                               const int64_t* __restrict__ foff, char* base, int esz,
-                               uint64_t* __restrict__ Uptr, uint64_t* __restrict__ Vptr)
+                               const int64_t* __restrict__ foffu, const int64_t* __restrict__ foffv,
+                               char* ubase, char* vbase, int esz, uint64_t* __restrict__ Uptr,
+                               uint64_t* __restrict__ Vptr)
 {
     const int64_t w = blockIdx.x;
     const int lane = threadIdx.x;
@@ -162,36 +169,27 @@ __global__ void k_copy_factors(const Blk* __restrict__ blk, const uint32_t* __re
     uint32_t b = order[q];
     const Blk B = blk[b];
     const int r = rank[b];
-    char* dst = base + foff[w] * esz;
-    const int64_t nu = (int64_t)r * B.m * esz, nv = (int64_t)r * B.n * esz;
-    const char* su = reinterpret_cast<const char*>(Uptr[b]);
-    const char* sv = reinterpret_cast<const char*>(Vptr[b]);
-    // element-size words (4 or 8 bytes): both sources and dst are aligned
+    char* du = ubase + foffu[w] * esz;
+    char* dv = vbase + foffv[w] * esz;
+    const int64_t nu = (int64_t)r * B.m, nv = (int64_t)r * B.n;
     if (esz == 8) {
-        const double* a = reinterpret_cast<const double*>(su);
-        const double* c = reinterpret_cast<const double*>(sv);
-        double* o = reinterpret_cast<double*>(dst);
-        for (int64_t e = lane; e < nu / 8; e += NT) o[e] = a[e];
-        for (int64_t e = lane; e < nv / 8; e += NT) o[nu / 8 + e] = c[e];
+        const double* a = reinterpret_cast<const double*>(Uptr[b]);
+        const double* c = reinterpret_cast<const double*>(Vptr[b]);
+        for (int64_t e = lane; e < nu; e += NT) reinterpret_cast<double*>(du)[e] = a[e];
+        for (int64_t e = lane; e < nv; e += NT) reinterpret_cast<double*>(dv)[e] = c[e];
     } else {
-        const float* a = reinterpret_cast<const float*>(su);
-        const float* c = reinterpret_cast<const float*>(sv);
-        float* o = reinterpret_cast<float*>(dst);
-        for (int64_t e = lane; e < nu / 4; e += NT) o[e] = a[e];
-        for (int64_t e = lane; e < nv / 4; e += NT) o[nu / 4 + e] = c[e];
+        const float* a = reinterpret_cast<const float*>(Uptr[b]);
+        const float* c = reinterpret_cast<const float*>(Vptr[b]);
+        for (int64_t e = lane; e < nu; e += NT) reinterpret_cast<float*>(du)[e] = a[e];
+        for (int64_t e = lane; e < nv; e += NT) reinterpret_cast<float*>(dv)[e] = c[e];
     }
     __syncthreads();
     if (lane == 0) {
-        Uptr[b] = (uint64_t)dst;
-        Vptr[b] = (uint64_t)(dst + nu);
+        Uptr[b] = (uint64_t)du;
+        Vptr[b] = (uint64_t)dv;
     }
 }
 
-__global__ void k_near_size(const Blk* __restrict__ blk, int64_t n, int64_t* __restrict__ sz)
-{
-    int64_t b = (int64_t)blockIdx.x * NT + threadIdx.x;
-    if (b < n) sz[b] = (int64_t)blk[b].m * blk[b].n;
-}
 
 // Statistics of the factors: [sum rank, max rank, cap hits, mispredicted,
 // rejected, factor entries, reserved entries, sum k m, evaluations,
@@ -333,11 +331,14 @@ void compress(hm_handle_s& h, const uint32_t* ids, int64_t n, const int32_t* kpr
     radix_sort_u64_u32(key.p, order.p, n, 3, s);
     int64_t cc[ACA_NCLASS];
     HM_CUDA(cudaMemcpyAsync(cc, ccount.p, sizeof(cc), cudaMemcpyDeviceToHost, s));
-    DevBuf<int64_t> res(n, s), pre(n + 1, s);
-    k_reserve<<<grid_for(n), NT, 0, s>>>(h.ablk.p, order.p, n, h.kres.p, res.p); note_launch();
+    DevBuf<int64_t> res(n, s), pre(n + 1, s), resu(n, s), preu(n + 1, s);
+    k_reserve<<<grid_for(n), NT, 0, s>>>(h.ablk.p, order.p, n, h.kres.p, res.p, resu.p); note_launch();
     scan_exclusive_i64(res.p, pre.p, n, pre.p + n, s);
-    std::vector<int64_t> hpre(n + 1);
+    scan_exclusive_i64(resu.p, preu.p, n, preu.p + n, s);
+    std::vector<int64_t> hpre(n + 1), hpreu(n + 1);
     HM_CUDA(cudaMemcpyAsync(hpre.data(), pre.p, (n + 1) * sizeof(int64_t),
+                            cudaMemcpyDeviceToHost, s));
+    HM_CUDA(cudaMemcpyAsync(hpreu.data(), preu.p, (n + 1) * sizeof(int64_t),
                             cudaMemcpyDeviceToHost, s));
     HM_CUDA(cudaStreamSynchronize(s));
     // class ranges in the sorted order: the largest class first
@@ -379,13 +380,16 @@ void compress(hm_handle_s& h, const uint32_t* ids, int64_t n, const int32_t* kpr
     };
 
     if (kpred) {
-        // learned sizing: reserve the predicted ranks directly in the final store
-        auto seg = std::make_unique<FactorSegment>();
-        seg->mem.alloc((size_t)hpre[n] * esz, s);
-        k_set_ptrs<<<grid_for(n), NT, 0, s>>>(h.ablk.p, order.p, 0, n, pre.p, h.kres.p,
-                                               seg->mem.p, esz, h.Uptr.p, h.Vptr.p); note_launch();
+        // learned sizing: reserve the predicted ranks directly (no copy)
+        auto useg = std::make_unique<FactorSegment>();
+        auto vseg = std::make_unique<FactorSegment>();
+        useg->mem.alloc((size_t)std::max<int64_t>(hpreu[n], 1) * esz, s);
+        vseg->mem.alloc((size_t)std::max<int64_t>(hpre[n] - hpreu[n], 1) * esz, s);
+        k_set_ptrs<<<grid_for(n), NT, 0, s>>>(order.p, 0, n, pre.p, preu.p, useg->mem.p,
+                                               vseg->mem.p, esz, h.Uptr.p, h.Vptr.p); note_launch();
         HM_LAUNCH("set ptrs");
-        h.segments.push_back(std::move(seg));
+        h.usegments.push_back(std::move(useg));
+        h.vsegments.push_back(std::move(vseg));
         run_range(0, n);
         h.stats.aca_passes += 1;
         return;
@@ -407,23 +411,31 @@ void compress(hm_handle_s& h, const uint32_t* ids, int64_t n, const int32_t* kpr
         int64_t q1 = std::upper_bound(hpre.begin() + q0 + 1, hpre.end(), hpre[q0] + cap) -
                      hpre.begin() - 1;
         q1 = std::max(q1, q0 + 1);
-        k_set_ptrs<<<grid_for(q1 - q0), NT, 0, s>>>(h.ablk.p, order.p, q0, q1, pre.p, h.kres.p,
-                                                     scratch.p, esz, h.Uptr.p, h.Vptr.p); note_launch();
+        // the chunk's U reservations first, then its V reservations
+        char* vbase = scratch.p + (hpreu[q1] - hpreu[q0]) * esz;
+        k_set_ptrs<<<grid_for(q1 - q0), NT, 0, s>>>(order.p, q0, q1, pre.p, preu.p, scratch.p,
+                                                     vbase, esz, h.Uptr.p, h.Vptr.p); note_launch();
         HM_LAUNCH("set ptrs");
         run_range(q0, q1);
-        DevBuf<int64_t> fs(q1 - q0, s), foff(q1 - q0 + 1, s);
-        k_final_size<<<grid_for(q1 - q0), NT, 0, s>>>(h.ablk.p, order.p, q0, q1, h.rank.p, fs.p); note_launch();
-        scan_exclusive_i64(fs.p, foff.p, q1 - q0, foff.p + (q1 - q0), s);
-        int64_t tot = 0;
-        HM_CUDA(cudaMemcpyAsync(&tot, foff.p + (q1 - q0), sizeof(int64_t),
-                                cudaMemcpyDeviceToHost, s));
+        const int64_t nq = q1 - q0;
+        DevBuf<int64_t> fsu(nq, s), fsv(nq, s), foffu(nq + 1, s), foffv(nq + 1, s);
+        k_final_size<<<grid_for(nq), NT, 0, s>>>(h.ablk.p, order.p, q0, q1, h.rank.p, fsu.p, fsv.p); note_launch();
+        scan_exclusive_i64(fsu.p, foffu.p, nq, foffu.p + nq, s);
+        scan_exclusive_i64(fsv.p, foffv.p, nq, foffv.p + nq, s);
+        int64_t tot[2] = {0, 0};
+        HM_CUDA(cudaMemcpyAsync(&tot[0], foffu.p + nq, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        HM_CUDA(cudaMemcpyAsync(&tot[1], foffv.p + nq, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         HM_CUDA(cudaStreamSynchronize(s));
-        auto seg = std::make_unique<FactorSegment>();
-        seg->mem.alloc((size_t)std::max<int64_t>(tot, 1) * esz, s);
-        k_copy_factors<<<(unsigned)(q1 - q0), NT, 0, s>>>(
-            h.ablk.p, order.p, q0, q1, h.rank.p, foff.p, seg->mem.p, esz, h.Uptr.p, h.Vptr.p); note_launch();
+        auto useg = std::make_unique<FactorSegment>();
+        auto vseg = std::make_unique<FactorSegment>();
+        useg->mem.alloc((size_t)std::max<int64_t>(tot[0], 1) * esz, s);
+        vseg->mem.alloc((size_t)std::max<int64_t>(tot[1], 1) * esz, s);
+        k_copy_factors<<<(unsigned)nq, NT, 0, s>>>(h.ablk.p, order.p, q0, q1, h.rank.p, foffu.p,
+                                                   foffv.p, useg->mem.p, vseg->mem.p, esz,
+                                                   h.Uptr.p, h.Vptr.p); note_launch();
         HM_LAUNCH("copy factors");
-        h.segments.push_back(std::move(seg));
+        h.usegments.push_back(std::move(useg));
+        h.vsegments.push_back(std::move(vseg));
         ++passes;
         q0 = q1;
     }
@@ -670,28 +682,24 @@ void build_sets(hm_handle_s& h, int nsets, const double* points_all, const int64
     }
     rank_stats(h);
 
-    // near field
+    // product lists, near field in tile slices, U in tile slices
     {
         Timer td(s);
-        const int64_t nd = h.n_dense;
-        h.doff.alloc(std::max<int64_t>(nd, 1), s);
-        int64_t tot = 0;
-        if (nd > 0) {
-            DevBuf<int64_t> sz(nd, s), t(1, s);
-            k_near_size<<<grid_for(nd), NT, 0, s>>>(h.dblk.p, nd, sz.p); note_launch();
-            scan_exclusive_i64(sz.p, h.doff.p, nd, t.p, s);
-            HM_CUDA(cudaMemcpyAsync(&tot, t.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-            HM_CUDA(cudaStreamSynchronize(s));
-        }
-        h.near.alloc(std::max<int64_t>(tot, 1) * near_entry_bytes(h.near_format), s);
-        near_assemble(h.near_format, h.kp, h.X, h.dblk.p, h.doff.p, nd, h.near.p, s);
-        h.stats.near_entries = tot;
+        mvp_build_lists(h.ablk.p, h.rank.p, h.n_adm, h.dblk.p, h.n_dense, h.tile_row0.p,
+                        h.tile_m.p, h.n_tiles, h.lists, s);
+        const MvpLists& L = h.lists;
+        h.near.alloc((size_t)std::max<int64_t>(L.near_elems, 1) * near_entry_bytes(h.near_format), s);
+        near_assemble(h.near_format, h.kp, h.X, h.dblk.p, L.dn_ent.p,
+                      L.dn_tile.p, h.tile_m.p, L.dn_desc.p, L.n_dn, h.near.p, s);
+        const int esz = h.precision == HM_PREC_FP64 ? 8 : 4;
+        h.ustore.alloc((size_t)std::max<int64_t>(L.u_elems, 1) * esz, s);
+        mvp_relayout_u(h.precision, L, h.ablk.p, h.Uptr.p, h.tile_m.p, h.ustore.p, s);
+        HM_CUDA(cudaStreamSynchronize(s));
+        h.usegments.clear();   // the per-block U copies are no longer needed
+        h.stats.near_entries = L.near_elems;
         h.stats.t_dense_ms = td.stop_ms();
     }
 
-    // product lists and plan
-    mvp_build_lists(h.ablk.p, h.rank.p, h.n_adm, h.dblk.p, h.n_dense, h.tile_row0.p, h.tile_m.p,
-                    h.n_tiles, h.lists, s);
     MvpPlan& P = h.plan;
     P.precision = h.precision;
     P.near_format = h.near_format;
@@ -711,18 +719,16 @@ void build_sets(hm_handle_s& h, int nsets, const double* points_all, const int64
     P.tsum_count = h.lists.tsum_count.p;
     P.n_multi = h.lists.n_multi;
     P.multi = h.lists.multi.p;
-    P.n_dense = h.n_dense;
-    P.dblk = h.dblk.p;
-    P.doff = h.doff.p;
+    P.ustore = h.ustore.p;
     P.near = h.near.p;
     P.near_entries = h.stats.near_entries;
     P.n_tiles = h.n_tiles;
     P.tile_row0 = h.tile_row0.p;
     P.tile_m = h.tile_m.p;
     P.lr_ptr = h.lists.lr_ptr.p;
-    P.lr_ent = h.lists.lr_ent.p;
+    P.lr_desc = h.lists.lr_desc.p;
     P.dn_ptr = h.lists.dn_ptr.p;
-    P.dn_ent = h.lists.dn_ent.p;
+    P.dn_desc = h.lists.dn_desc.p;
     P.perm = h.perm.p;
     P.sigma2 = h.sigma2;
     mvp_alloc_work(P, h.work, s);
