@@ -18,6 +18,13 @@
 // ||S_r||_F^2 is updated by S2 += 2 sum_l (u.u_l)(v_l.v) + |u|^2 |v|^2; the
 // rule |u||v| <= eps (1-aca_eta)/(1+eps) sqrt(S2) with the reference row
 // resolved stops (eps <= 0: fixed rank).
+//
+// Mixed precision adds a global floor to both tests: S2 is replaced by
+// max(S2, m n / N). Since ||A||_F >= sqrt(N) phi(0) with phi(0) = 1, blocks
+// that meet the floored tests keep ||A - H||_F <= eps ||A||_F overall, while
+// far blocks whose entries are far below float resolution (exp(-x) with
+// x ~ 100 is subnormal in float) stop at rank 1 instead of fitting rounding
+// noise up to the rank cap.
 // The norms, S2 and the stopping test are always accumulated in double.
 #include <cooperative_groups.h>
 
@@ -32,6 +39,7 @@ constexpr int CTA_NT = 256;
 constexpr int CTA_WARPS = CTA_NT / 32;
 constexpr int KBUF = 128;      // largest supported k_cap
 constexpr int REJ_RUN = 4;     // rejected columns in a row that end a block
+constexpr int UNR = 8;         // rows (columns) per thread whose loads are issued together
 
 // --------------------------------------------------------------------------
 // One warp per block (m, n <= 32 MAXR). Lane l owns rows and columns
@@ -57,6 +65,7 @@ k_aca_warp(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restric
     const R c = kconst<R>(kp);
     const R eps0 = (R)a.eps0;
     const double rtol = a.eps > 0.0 ? a.eps : a.eps0;
+    const double floor2 = a.bset ? (double)m * (double)n / (double)a.set_n[a.bset[b]] : 0.0;
 
     R acc[MAXR], vv[MAXR];
     Resid<R> res[MAXR], rr[MAXR];   // rr: reference-row residual (compensated)
@@ -224,7 +233,8 @@ k_aca_warp(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restric
         S2 += 2.0 * cross + nu2 * nv2;
         ++r;
         // a resolved reference row moves to the lowest row not seen yet
-        const double rlim = rtol * sqrt(fmax(S2, 0.0) / (double)m);
+        const double S2f = fmax(S2, floor2);
+        const double rlim = rtol * sqrt(S2f / (double)m);
         if (!((double)rmax > rlim)) {
             int cand = 0x7fffffff;
 #pragma unroll
@@ -268,8 +278,7 @@ k_aca_warp(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restric
                 rmax = warp_max(rmax);
             }
         }
-        if (thr >= 0.0 && sqrt(nu2) * sqrt(nv2) <= thr * sqrt(fmax(S2, 0.0)) &&
-            !((double)rmax > rlim)) {
+        if (thr >= 0.0 && sqrt(nu2) * sqrt(nv2) <= thr * sqrt(S2f) && !((double)rmax > rlim)) {
             converged = true;
             break;
         }
@@ -465,6 +474,7 @@ k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __rest
         R* __restrict__ U = reinterpret_cast<R*>(a.Uptr[b]);
         R* __restrict__ V = reinterpret_cast<R*>(a.Vptr[b]);
         const int wn = (n + 31) / 32, wm = (m + 31) / 32;
+        const double floor2 = a.bset ? (double)m * (double)n / (double)a.set_n[a.bset[b]] : 0.0;
         for (int k = gt; k < wn; k += GT) used[k] = 0u;
         for (int k = gt; k < wm; k += GT) seen[k] = 0u;
         cl.sync();
@@ -495,20 +505,41 @@ k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __rest
             R* __restrict__ Ur = U + (int64_t)r * m;
             Red qc;
             red_init(qc);
-            for (int i = gt; i < m; i += GT) {
-                const R a0 = phi<KERN>(dist2(load_pt<R>(X, B.row0 + i), pj), c);
-                qc.x0 = fmax(qc.x0, (double)fabs(a0));
-                Resid<R> rs_;
-                rs_.init(a0);
-                for (int l = 0; l < r; ++l) rs_.sub(U[(int64_t)l * m + i], sg[l]);
-                const R v = rs_.value();
-                Ur[i] = v;
-                if ((double)fabs(v) > qc.av) {
-                    qc.av = fabs(v);
-                    qc.ai = i;
-                    qc.aval = v;
+            // rows in chunks of UNR per thread so that UNR loads are in flight
+            for (int i0 = gt; i0 < m; i0 += UNR * GT) {
+                Resid<R> rs_[UNR];
+#pragma unroll
+                for (int q = 0; q < UNR; ++q) {
+                    const int i = i0 + q * GT;
+                    R a0 = 0;
+                    if (i < m) {
+                        a0 = phi<KERN>(dist2(load_pt<R>(X, B.row0 + i), pj), c);
+                        qc.x0 = fmax(qc.x0, (double)fabs(a0));
+                    }
+                    rs_[q].init(a0);
                 }
-                if (i == iref) qc.s0 = v;
+                for (int l = 0; l < r; ++l) {
+                    const R vl = sg[l];
+                    const R* Ul = U + (int64_t)l * m;
+                    R uv[UNR];
+#pragma unroll
+                    for (int q = 0; q < UNR; ++q) uv[q] = (i0 + q * GT < m) ? Ul[i0 + q * GT] : R(0);
+#pragma unroll
+                    for (int q = 0; q < UNR; ++q) rs_[q].sub(uv[q], vl);
+                }
+#pragma unroll
+                for (int q = 0; q < UNR; ++q) {
+                    const int i = i0 + q * GT;
+                    if (i >= m) continue;
+                    const R v = rs_[q].value();
+                    Ur[i] = v;
+                    if ((double)fabs(v) > qc.av) {
+                        qc.av = fabs(v);
+                        qc.ai = i;
+                        qc.aval = v;
+                    }
+                    if (i == iref) qc.s0 = v;
+                }
             }
             const Red oc = cl_reduce(cl, sh, ph, qc, 0);
             const R best = (R)oc.av, amax = (R)oc.x0;
@@ -549,26 +580,44 @@ k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __rest
             R* __restrict__ Vr = V + (int64_t)r * n;
             Red qr;
             red_init(qr);
-            for (int jj = gt; jj < n; jj += GT) {
-                Resid<R> rs_;
-                rs_.init(phi<KERN>(dist2(pi, load_pt<R>(X, B.col0 + jj)), c));
-                for (int l = 0; l < r; ++l) rs_.sub(sg[l], V[(int64_t)l * n + jj]);
-                const R v = rs_.value();
-                Vr[jj] = v;
-                qr.s1 += (double)v * (double)v;
-                Resid<R> rx;
-                rx.s = rr[jj];
-                rx.setc(rc[jj]);
-                rx.sub(uiref, v);
-                rr[jj] = rx.s;
-                rc[jj] = rx.getc();
-                const R x = rx.value();
-                qr.x1 = fmax(qr.x1, (double)fabs(x));
-                if (!((used[jj >> 5] >> (jj & 31)) & 1u) && (double)fabs(x) > qr.av) {
-                    qr.av = fabs(x);
-                    qr.ai = jj;
+            for (int j0 = gt; j0 < n; j0 += UNR * GT) {
+                Resid<R> rs_[UNR];
+#pragma unroll
+                for (int q = 0; q < UNR; ++q) {
+                    const int jj = j0 + q * GT;
+                    rs_[q].init(jj < n ? phi<KERN>(dist2(pi, load_pt<R>(X, B.col0 + jj)), c) : R(0));
+                }
+                for (int l = 0; l < r; ++l) {
+                    const R ul = sg[l];
+                    const R* Vl = V + (int64_t)l * n;
+                    R vv[UNR];
+#pragma unroll
+                    for (int q = 0; q < UNR; ++q) vv[q] = (j0 + q * GT < n) ? Vl[j0 + q * GT] : R(0);
+#pragma unroll
+                    for (int q = 0; q < UNR; ++q) rs_[q].sub(ul, vv[q]);
+                }
+#pragma unroll
+                for (int q = 0; q < UNR; ++q) {
+                    const int jj = j0 + q * GT;
+                    if (jj >= n) continue;
+                    const R v = rs_[q].value();
+                    Vr[jj] = v;
+                    qr.s1 += (double)v * (double)v;
+                    Resid<R> rx;
+                    rx.s = rr[jj];
+                    rx.setc(rc[jj]);
+                    rx.sub(uiref, v);
+                    rr[jj] = rx.s;
+                    rc[jj] = rx.getc();
+                    const R x = rx.value();
+                    qr.x1 = fmax(qr.x1, (double)fabs(x));
+                    if (!((used[jj >> 5] >> (jj & 31)) & 1u) && (double)fabs(x) > qr.av) {
+                        qr.av = fabs(x);
+                        qr.ai = jj;
+                    }
                 }
             }
+#pragma unroll 4
             for (int i = gt; i < m; i += GT) {
                 const R u = Ur[i] / piv;
                 Ur[i] = u;
@@ -578,8 +627,28 @@ k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __rest
                 const R* Ul = U + (int64_t)l * m;
                 const R* Vl = V + (int64_t)l * n;
                 R du = 0, dv = 0;
-                for (int i = gt; i < m; i += GT) du += Ur[i] * Ul[i];
-                for (int jj = gt; jj < n; jj += GT) dv += Vl[jj] * Vr[jj];
+                for (int i0 = gt; i0 < m; i0 += UNR * GT) {
+                    R a[UNR], b[UNR];
+#pragma unroll
+                    for (int q = 0; q < UNR; ++q) {
+                        const int i = i0 + q * GT;
+                        a[q] = i < m ? Ur[i] : R(0);
+                        b[q] = i < m ? Ul[i] : R(0);
+                    }
+#pragma unroll
+                    for (int q = 0; q < UNR; ++q) du += a[q] * b[q];
+                }
+                for (int j0 = gt; j0 < n; j0 += UNR * GT) {
+                    R a[UNR], b[UNR];
+#pragma unroll
+                    for (int q = 0; q < UNR; ++q) {
+                        const int jj = j0 + q * GT;
+                        a[q] = jj < n ? Vl[jj] : R(0);
+                        b[q] = jj < n ? Vr[jj] : R(0);
+                    }
+#pragma unroll
+                    for (int q = 0; q < UNR; ++q) dv += a[q] * b[q];
+                }
                 const double ddu = warp_sum((double)du), ddv = warp_sum((double)dv);
                 if (lane == 0) {
                     sh.wl[w][l] = ddu;
@@ -593,7 +662,8 @@ k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __rest
             S2 += 2.0 * cross + NU2 * NV2;
             ++r;
             // a resolved reference row moves to the lowest row not seen yet
-            const double rlim = rtol * sqrt(fmax(S2, 0.0) / (double)m);
+            const double S2f = fmax(S2, floor2);
+            const double rlim = rtol * sqrt(S2f / (double)m);
             if (!(rmax > rlim)) {
                 Red qs;
                 red_init(qs);
@@ -614,17 +684,34 @@ k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __rest
                     const Pt<R> pr = load_pt<R>(X, B.row0 + iref);
                     Red qf;
                     red_init(qf);
-                    for (int jj = gt; jj < n; jj += GT) {
-                        Resid<R> rs_;
-                        rs_.init(phi<KERN>(dist2(pr, load_pt<R>(X, B.col0 + jj)), c));
-                        for (int l = 0; l < r; ++l) rs_.sub(sg[l], V[(int64_t)l * n + jj]);
-                        const R x = rs_.value();
-                        rr[jj] = rs_.s;
-                        rc[jj] = rs_.getc();
-                        qf.x1 = fmax(qf.x1, (double)fabs(x));
-                        if (!((used[jj >> 5] >> (jj & 31)) & 1u) && (double)fabs(x) > qf.av) {
-                            qf.av = fabs(x);
-                            qf.ai = jj;
+                    for (int j0 = gt; j0 < n; j0 += UNR * GT) {
+                        Resid<R> rs_[UNR];
+#pragma unroll
+                        for (int q = 0; q < UNR; ++q) {
+                            const int jj = j0 + q * GT;
+                            rs_[q].init(jj < n ? phi<KERN>(dist2(pr, load_pt<R>(X, B.col0 + jj)), c) : R(0));
+                        }
+                        for (int l = 0; l < r; ++l) {
+                            const R ul = sg[l];
+                            const R* Vl = V + (int64_t)l * n;
+                            R vv[UNR];
+#pragma unroll
+                            for (int q = 0; q < UNR; ++q) vv[q] = (j0 + q * GT < n) ? Vl[j0 + q * GT] : R(0);
+#pragma unroll
+                            for (int q = 0; q < UNR; ++q) rs_[q].sub(ul, vv[q]);
+                        }
+#pragma unroll
+                        for (int q = 0; q < UNR; ++q) {
+                            const int jj = j0 + q * GT;
+                            if (jj >= n) continue;
+                            const R x = rs_[q].value();
+                            rr[jj] = rs_[q].s;
+                            rc[jj] = rs_[q].getc();
+                            qf.x1 = fmax(qf.x1, (double)fabs(x));
+                            if (!((used[jj >> 5] >> (jj & 31)) & 1u) && (double)fabs(x) > qf.av) {
+                                qf.av = fabs(x);
+                                qf.ai = jj;
+                            }
                         }
                     }
                     const Red of = cl_reduce(cl, sh, ph, qf, 0);
@@ -632,8 +719,7 @@ k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __rest
                     nj = of.ai;
                 }
             }
-            if (thr >= 0.0 && sqrt(NU2) * sqrt(NV2) <= thr * sqrt(fmax(S2, 0.0)) &&
-                !(rmax > rlim)) {
+            if (thr >= 0.0 && sqrt(NU2) * sqrt(NV2) <= thr * sqrt(S2f) && !(rmax > rlim)) {
                 converged = true;
                 break;
             }

@@ -47,6 +47,11 @@ struct AcaArgs {
     double aca_eta;
     double eps0;
     int k_cap;
+    // Global error floor (mixed precision): the stopping tests compare with
+    // max(||S_r||_F^2, m n / N_set) instead of ||S_r||_F^2, N_set the size of
+    // the block's point set; null = the paper's blockwise relative test.
+    const int32_t* bset;     // per block: its point set
+    const int64_t* set_n;    // per set: number of points
 };
 
 // Size classes of admissible blocks by max(m, n): classes 0-3 (<= 64, 128,

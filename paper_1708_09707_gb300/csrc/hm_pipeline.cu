@@ -364,6 +364,17 @@ void compress(hm_handle_s& h, const uint32_t* ids, int64_t n, const int32_t* kpr
     a.aca_eta = h.opt.aca_eta;
     a.eps0 = h.opt.eps0 > 0 ? h.opt.eps0 : (h.precision == HM_PREC_FP64 ? 1e-14 : 1e-6);
     a.k_cap = h.opt.k_cap;
+    a.bset = nullptr;
+    a.set_n = nullptr;
+    DevBuf<int64_t> setn;
+    if (h.precision == HM_PREC_MIXED) {
+        std::vector<int64_t> sn(h.sets.size());
+        for (size_t q = 0; q < h.sets.size(); ++q) sn[q] = h.sets[q].N;
+        setn.alloc(sn.size(), s);
+        copy_in(setn.p, sn.data(), sn.size() * sizeof(int64_t), s);
+        a.bset = h.adm_set.p;
+        a.set_n = setn.p;
+    }
 
     // every size class runs on its own stream so that the few largest blocks
     // (clusters of CTAs) overlap the many small ones
