@@ -233,6 +233,27 @@ int hm_morton_codes(const double* points, int64_t N, int d, uint64_t* codes,
 int hm_radix_sort_pairs(uint64_t* keys, uint32_t* values, int64_t n,
                         int key_bits, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free sort. The paper has no counterpart: this entry point is
+ * for callers that cannot allocate device memory while they run, such as a
+ * program that has handed all free device memory to its own pool or caching
+ * allocator, or a latency-critical loop that must not block on an
+ * allocation. It sorts like hm_radix_sort_pairs (stable LSD radix sort of
+ * (key, value) pairs on the low key_bits bits, in place) but allocates
+ * nothing: no cudaMalloc, cudaFree or allocating library call.
+ *   keys, values  device pointers, n entries each (sorted in place)
+ *   n             at most HM_NOALLOC_SORT_MAX; larger n returns HM_EINVAL
+ *                 and leaves the arrays untouched
+ * Its scratch is one fixed array of about 3.3 MB in the library's device
+ * memory, held by every GPU that loads the library until the process ends.
+ * The first call on each device looks up that array's address (with that
+ * device current); make that first call before any stream capture. All calls
+ * on a device share the array, so calls that overlap on the GPU (on streams
+ * without an order between them) race and give wrong results. */
+#define HM_NOALLOC_SORT_MAX 262144
+int hm_radix_sort_pairs_noalloc(uint64_t* keys, uint32_t* values, int64_t n, int key_bits,
+                                void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -306,4 +306,23 @@ int hm_radix_sort_pairs(uint64_t* keys, uint32_t* values, int64_t n, int key_bit
     }
 }
 
+int hm_radix_sort_pairs_noalloc(uint64_t* keys, uint32_t* values, int64_t n, int key_bits,
+                                void* stream)
+{
+    set_error("");
+    try {
+        if (!keys || !values || n < 0 || key_bits < 0 || key_bits > 64)
+            fail(HM_EINVAL, "bad arguments");
+        if (n > HM_NOALLOC_SORT_MAX)
+            fail(HM_EINVAL, "n = " + std::to_string(n) + " exceeds HM_NOALLOC_SORT_MAX (" +
+                                std::to_string((long long)HM_NOALLOC_SORT_MAX) + ")");
+        if (n > 1 && (!is_device_ptr(keys) || !is_device_ptr(values)))
+            fail(HM_EINVAL, "keys and values must be device pointers");
+        radix_sort_noalloc(keys, values, n, key_bits, (cudaStream_t)stream);
+        return HM_OK;
+    } catch (const std::exception& e) {
+        return to_status(e);
+    }
+}
+
 }  // extern "C"

@@ -98,6 +98,9 @@ void scan_exclusive_i32(const int32_t* in, int32_t* out, int64_t n,
 // Stable LSD radix sort of (key, value) on the low key_bits bits.
 void radix_sort_u64_u32(uint64_t* keys, uint32_t* vals, int64_t n, int key_bits,
                         cudaStream_t s);
+// The same sort with all scratch in a fixed device array (no allocation).
+void radix_sort_noalloc(uint64_t* keys, uint32_t* vals, int64_t n, int key_bits,
+                        cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Kernel function parameters

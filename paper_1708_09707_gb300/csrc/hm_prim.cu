@@ -5,6 +5,9 @@
 // inter-block spin waits: the scan is reduce -> scan partials -> downsweep and
 // each radix pass is histogram -> scan -> scatter, so no launch can hang on
 // another block's progress.
+#include <mutex>
+#include <string>
+
 #include "hm_internal.cuh"
 
 namespace hm {
@@ -250,6 +253,97 @@ void radix_sort_u64_u32(uint64_t* keys, uint32_t* vals, int64_t n, int key_bits,
         scan_exclusive<int32_t>(cnt.p, cnt.p, (int64_t)256 * ntiles, nullptr, s);
         k_rs_scatter<<<ntiles, RS_THREADS, 0, s>>>(ka, va, kb, vb, n, shift, cnt.p, ntiles); note_launch();
         HM_LAUNCH("radix sort pass");
+        std::swap(ka, kb);
+        std::swap(va, vb);
+    }
+    if (ka != keys) {
+        HM_CUDA(cudaMemcpyAsync(keys, ka, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+        HM_CUDA(cudaMemcpyAsync(vals, va, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the radix sort (hm_radix_sort_pairs_noalloc).
+//
+// Some callers cannot allocate device memory while they run: a program that
+// has handed all free device memory to its own pool or caching allocator
+// must not have memory taken from under it, and a latency-critical loop
+// cannot afford an allocation that may block on the driver. For them the
+// sort below takes all of its scratch (ping-pong key and value buffers,
+// digit counts, scan partials) from one fixed array in the library's device
+// memory instead of allocating. The array holds NOALLOC_BYTES (about 3.3 MB)
+// on every GPU that loads the library, for the life of the process.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int64_t NOALLOC_MAX_N = HM_NOALLOC_SORT_MAX;
+constexpr int64_t NOALLOC_TILES = (NOALLOC_MAX_N + RS_TILE - 1) / RS_TILE;
+constexpr int64_t NOALLOC_COUNTS = 256 * NOALLOC_TILES;
+constexpr int64_t NOALLOC_PARTS = (NOALLOC_COUNTS + SCAN_TILE - 1) / SCAN_TILE;
+// byte offsets of the sub-buffers (each 256-byte aligned)
+constexpr size_t NA_KEYS = 0;
+constexpr size_t NA_VALS = NA_KEYS + ((NOALLOC_MAX_N * 8 + 255) / 256) * 256;
+constexpr size_t NA_CNT = NA_VALS + ((NOALLOC_MAX_N * 4 + 255) / 256) * 256;
+constexpr size_t NA_PART = NA_CNT + ((NOALLOC_COUNTS * 4 + 255) / 256) * 256;
+constexpr size_t NOALLOC_BYTES = NA_PART + ((NOALLOC_PARTS * 4 + 255) / 256) * 256;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[256] = {};
+
+// Device address of the scratch array on the current device. The first call
+// on a device looks it up with cudaGetSymbolAddress (with that device
+// current); later calls reuse it.
+char* noalloc_scratch()
+{
+    int dev = 0;
+    HM_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) fail(HM_EINVAL, "device ordinal out of range");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            fail(HM_ECUDA, std::string("cudaGetSymbolAddress of the sort scratch failed: ") +
+                               cudaGetErrorString(e));
+        }
+        g_noalloc_addr[dev] = p;
+    }
+    return static_cast<char*>(g_noalloc_addr[dev]);
+}
+
+}  // namespace
+
+void radix_sort_noalloc(uint64_t* keys, uint32_t* vals, int64_t n, int key_bits, cudaStream_t s)
+{
+    if (n > NOALLOC_MAX_N)
+        fail(HM_EINVAL, "hm_radix_sort_pairs_noalloc: n = " + std::to_string(n) +
+                            " exceeds the fixed scratch limit of " + std::to_string(NOALLOC_MAX_N) +
+                            " pairs");
+    if (n <= 1 || key_bits <= 0) return;
+    char* base = noalloc_scratch();
+    uint64_t* k2 = reinterpret_cast<uint64_t*>(base + NA_KEYS);
+    uint32_t* v2 = reinterpret_cast<uint32_t*>(base + NA_VALS);
+    int32_t* cnt = reinterpret_cast<int32_t*>(base + NA_CNT);
+    int32_t* part = reinterpret_cast<int32_t*>(base + NA_PART);
+    // every word of cnt and part that a pass reads is written earlier in the
+    // same pass (histogram, then reduce), so nothing needs clearing
+    const int passes = (key_bits + 7) / 8;
+    const int ntiles = (int)ceil_div(n, RS_TILE);
+    const int64_t ncnt = (int64_t)256 * ntiles;
+    const int64_t sparts = ceil_div(ncnt, SCAN_TILE);
+    uint64_t *ka = keys, *kb = k2;
+    uint32_t *va = vals, *vb = v2;
+    for (int p = 0; p < passes; ++p) {
+        const int shift = 8 * p;
+        k_rs_hist<<<ntiles, RS_THREADS, 0, s>>>(ka, n, shift, cnt, ntiles); note_launch();
+        k_scan_reduce<int32_t><<<(unsigned)sparts, SCAN_THREADS, 0, s>>>(cnt, ncnt, part); note_launch();
+        k_scan_partials<int32_t><<<1, SCAN_THREADS, 0, s>>>(part, sparts, nullptr); note_launch();
+        k_scan_down<int32_t><<<(unsigned)sparts, SCAN_THREADS, 0, s>>>(cnt, cnt, ncnt, part); note_launch();
+        k_rs_scatter<<<ntiles, RS_THREADS, 0, s>>>(ka, va, kb, vb, n, shift, cnt, ntiles); note_launch();
+        HM_LAUNCH("radix sort pass (no allocation)");
         std::swap(ka, kb);
         std::swap(va, vb);
     }

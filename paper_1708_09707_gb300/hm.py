@@ -114,6 +114,7 @@ def _declare(L):
                               C.c_float, _vp]
     L.hm_morton_codes.argtypes = [_vp, i64, C.c_int, _vp, _vp]
     L.hm_radix_sort_pairs.argtypes = [_vp, _vp, i64, C.c_int, _vp]
+    L.hm_radix_sort_pairs_noalloc.argtypes = [_vp, _vp, i64, C.c_int, _vp]
 
 
 def _check(code: int):
@@ -314,6 +315,12 @@ def morton_codes(points_dev, codes_dev, stream=None):
 def radix_sort_pairs(keys_dev, vals_dev, key_bits: int, stream=None):
     _check(lib().hm_radix_sort_pairs(_ptr(keys_dev), _ptr(vals_dev), keys_dev.numel(),
                                      key_bits, _stream_ptr(stream)))
+
+
+def radix_sort_pairs_noalloc(keys_dev, vals_dev, key_bits: int, stream=None):
+    """hm_radix_sort_pairs_noalloc: the sort without any device allocation."""
+    _check(lib().hm_radix_sort_pairs_noalloc(_ptr(keys_dev), _ptr(vals_dev), keys_dev.numel(),
+                                             key_bits, _stream_ptr(stream)))
 
 
 def mlp_forward(theta, F, out, stream=None):
