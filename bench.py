@@ -47,6 +47,9 @@ def parse():
     p.add_argument("--workload", default=WORKLOAD)
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--rank-model", default="on", choices=["on", "off"],
+                   help="size the ACA factor arena with the learned rank model "
+                        "(trained before the timed region on other point sets)")
     return p.parse_args()
 
 
@@ -250,11 +253,27 @@ def main():
     kw = dict(adm_max=(w["adm"] == "max"))
     stream = torch.cuda.current_stream()
 
-    def step(prec, ev=None, profile=False):
+    # learned rank model: trained untimed, on point sets other than the
+    # benchmark's (other seeds and sizes), with the library's MLP kernels
+    theta = None
+    model_info = None
+    if args.rank_model == "on":
+        from paper_1708_09707_gb300 import rank_model
+        t_m = time.time()
+        F, T = rank_model.training_data()
+        theta, hist = rank_model.train(F, T)
+        model_info = {"train_s": time.time() - t_m, "samples": int(F.shape[0]),
+                      "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1],
+                      "train_sets": [dict(s) for s in rank_model.TRAIN_SETS]}
+
+    def step(prec, ev=None, profile=False, model=True):
         if ev:
             ev[0].record(stream)
+        mk = dict(kw)
+        if model and theta is not None:
+            mk["rank_model_theta"] = theta
         H = hm.HMatrix(pts, w["kernel"], w["ell"], w["leaf"], w["eta"], w["eps"],
-                       precision=prec, profile=profile, **kw)
+                       precision=prec, profile=profile, **mk)
         if ev:
             ev[1].record(stream)
         for _ in range(N_MVP):
@@ -265,9 +284,9 @@ def main():
         H.free()
         return st
 
-    def timed(prec, steps, warmup, profile):
+    def timed(prec, steps, warmup, profile, model=True):
         for _ in range(warmup):
-            step(prec)
+            step(prec, model=model)
         torch.cuda.synchronize()
         barrier()
         torch.cuda.synchronize()
@@ -278,7 +297,7 @@ def main():
         stats = []
         t0.record(stream)
         for k in range(steps):
-            stats.append(step(prec, evs[k], profile))
+            stats.append(step(prec, evs[k], profile, model))
         t1.record(stream)
         torch.cuda.synchronize()
         barrier()
@@ -305,18 +324,29 @@ def main():
     fp64 = None
     err = None
     if not args.no_fp64:
-        t64, b64, m64, s64, _ = timed(hm.PREC_FP64, 1, 1, False)
+        t64, b64, m64, s64, _ = timed(hm.PREC_FP64, 1, 1, False, model=False)
         fp64 = {"build_s": b64 / 1e3, "mvp_ms": m64, "ms_per_step": t64,
                 "mvp_roofline_frac": s64[-1]["mvp_bytes"] / (m64 * 1e-3) / (hbm * 1e9)}
         H64 = hm.HMatrix(pts, w["kernel"], w["ell"], w["leaf"], w["eta"], w["eps"],
                          precision=hm.PREC_FP64, **kw)
         y64 = H64.matvec(x).cpu().numpy()
         H64.free()
+        mk = dict(kw)
+        if theta is not None:
+            mk["rank_model_theta"] = theta
         H32 = hm.HMatrix(pts, w["kernel"], w["ell"], w["leaf"], w["eta"], w["eps"],
-                         precision=hm.PREC_MIXED, **kw)
+                         precision=hm.PREC_MIXED, **mk)
         y32 = H32.matvec(x).cpu().numpy()
         H32.free()
         err = float(np.linalg.norm(y32 - y64) / np.linalg.norm(y64))
+
+    # the same mixed step without the rank model (chunked ACA passes)
+    plain = None
+    if theta is not None:
+        tp, bp, mp, sp, _ = timed(hm.PREC_MIXED, 1, 1, False, model=False)
+        plain = {"build_s": bp / 1e3, "mvp_ms": mp, "ms_per_step": tp,
+                 "aca_ms": sp[-1]["t_aca_ms"], "aca_passes": sp[-1]["aca_passes"],
+                 "reserved_factor_entries": sp[-1]["reserved_factor_entries"]}
 
     # e2e: the same step through the C-ABI with pinned host buffers
     pts_h = torch.from_numpy(pts_np).pin_memory()
@@ -327,9 +357,12 @@ def main():
     e1 = torch.cuda.Event(enable_timing=True)
     e2e_steps = max(1, min(args.steps, 3))
     e0.record(stream)
+    mk = dict(kw)
+    if theta is not None:
+        mk["rank_model_theta"] = theta
     for _ in range(e2e_steps):
         H = hm.HMatrix(pts_h, w["kernel"], w["ell"], w["leaf"], w["eta"], w["eps"],
-                       precision=hm.PREC_MIXED, **kw)
+                       precision=hm.PREC_MIXED, **mk)
         for _ in range(N_MVP):
             H.matvec(xs_h, ys_h)
         H.free()
@@ -383,11 +416,13 @@ def main():
                    "points": w["points"], "kernel": "gaussian" if w["kernel"] == 0 else "matern32",
                    "ell": w["ell"], "leaf": w["leaf"], "eta": w["eta"], "aca_eps": w["eps"],
                    "precision": "mixed (FP32 ACA + FP64 stopping test, BF16 hi/lo near field)",
+                   "rank_model": args.rank_model,
                    "mvp_per_step": N_MVP, "l2": "inputs larger than L2 (product streams "
                    "%.1f GB per call)" % (st["mvp_bytes"] / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
         "build_s": build_ms / 1e3, "mvp_ms": mvp_ms,
         "fp64": fp64, "mixed_vs_fp64_rel_err": err,
+        "mixed_without_rank_model": plain, "rank_model": model_info,
         "speedup_vs_fp64": (fp64["ms_per_step"] / total) if fp64 else None,
         "e2e": {"value": e2e_ms / 1e3, "unit": "s/step (build + %d H-MVP)" % N_MVP,
                 "h2d_bytes_per_step": N * d * 8 + N_MVP * N * 8,
@@ -399,7 +434,8 @@ def main():
         "stats": {k: st[k] for k in ("n_adm", "n_dense", "sum_rank", "max_rank",
                                      "rank_cap_hits", "n_rejected", "factor_bytes",
                                      "near_bytes", "mvp_bytes", "t_structure_ms",
-                                     "t_aca_ms", "t_dense_ms", "aca_passes")},
+                                     "t_aca_ms", "t_dense_ms", "aca_passes",
+                                     "n_mispredicted", "reserved_factor_entries")},
     }
     print(json.dumps(line))
     if world > 1:
