@@ -25,7 +25,10 @@
 // far blocks whose entries are far below float resolution (exp(-x) with
 // x ~ 100 is subnormal in float) stop at rank 1 instead of fitting rounding
 // noise up to the rank cap.
-// The norms, S2 and the stopping test are always accumulated in double.
+// The norms, S2 and the stopping test are accumulated in double across
+// threads; inside a thread the float kernels keep their partials in float
+// (compensated sums, exact maxima), since this GPU's double pipe runs at a
+// small fraction of its float rate.
 #include <cooperative_groups.h>
 
 #include "hm_kernel_fn.cuh"
@@ -66,6 +69,8 @@ k_aca_warp(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restric
     const R eps0 = (R)a.eps0;
     const double rtol = a.eps > 0.0 ? a.eps : a.eps0;
     const double floor2 = a.bset ? (double)m * (double)n / (double)a.set_n[a.bset[b]] : 0.0;
+    // both tests in squared form (no division or square root per step)
+    const double rtol2_m = rtol * rtol / (double)m, thr2 = thr * thr;
 
     R acc[MAXR], vv[MAXR];
     Resid<R> res[MAXR], rr[MAXR];   // rr: reference-row residual (compensated)
@@ -197,7 +202,9 @@ k_aca_warp(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restric
             }
         }
         R* __restrict__ Vr = V + (int64_t)r * n;
-        double nu2 = 0.0, nv2 = 0.0;
+        TSum<R> tu, tv;
+        tu.init();
+        tv.init();
         R rmax = 0;
 #pragma unroll
         for (int t = 0; t < MAXR; ++t) {
@@ -205,17 +212,22 @@ k_aca_warp(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restric
             const int i = lane + 32 * t;
             if (i < n) {
                 Vr[i] = vv[t];
-                nv2 += (double)vv[t] * (double)vv[t];
+                tv.add(vv[t] * vv[t]);
                 rr[t].sub(uiref, vv[t]);
                 rmax = max(rmax, fabs(rr[t].value()));
             }
-            if (i < m) nu2 += (double)acc[t] * (double)acc[t];
+            if (i < m) tu.add(acc[t] * acc[t]);
         }
-        nu2 = warp_sum(nu2);
-        nv2 = warp_sum(nv2);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            tu.shfl_join(o);
+            tv.shfl_join(o);
+        }
+        const double nu2 = tu.value(), nv2 = tv.value();
         rmax = warp_max(rmax);
-        // cross terms (u_r . u_l)(v_l . v_r)
-        double cross = 0.0;
+        // cross terms (u_r . u_l)(v_l . v_r), reduced and summed in R
+        TSum<R> tc;
+        tc.init();
         for (int l = 0; l < r; ++l) {
             const R* Ul = U + (int64_t)l * m;
             const R* Vl = V + (int64_t)l * n;
@@ -226,16 +238,17 @@ k_aca_warp(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restric
                 if (i < m) du += acc[t] * Ul[i];
                 if (i < n) dv += Vl[i] * vv[t];
             }
-            double ddu = warp_sum((double)du);
-            double ddv = warp_sum((double)dv);
-            cross += ddu * ddv;
+            const R ddu = warp_sum(du);
+            const R ddv = warp_sum(dv);
+            tc.add(ddu * ddv);
         }
-        S2 += 2.0 * cross + nu2 * nv2;
+        S2 += 2.0 * tc.value() + nu2 * nv2;
         ++r;
-        // a resolved reference row moves to the lowest row not seen yet
+        // a resolved reference row (max |residual| <= tol sqrt(S2 / m)) moves
+        // to the lowest row not seen yet
         const double S2f = fmax(S2, floor2);
-        const double rlim = rtol * sqrt(S2f / (double)m);
-        if (!((double)rmax > rlim)) {
+        const double rlim2 = rtol2_m * S2f;
+        if (!((double)rmax * (double)rmax > rlim2)) {
             int cand = 0x7fffffff;
 #pragma unroll
             for (int t = 0; t < MAXR; ++t) {
@@ -278,7 +291,7 @@ k_aca_warp(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restric
                 rmax = warp_max(rmax);
             }
         }
-        if (thr >= 0.0 && sqrt(nu2) * sqrt(nv2) <= thr * sqrt(S2f) && !((double)rmax > rlim)) {
+        if (thr >= 0.0 && nu2 * nv2 <= thr2 * S2f && !((double)rmax * (double)rmax > rlim2)) {
             converged = true;
             break;
         }
@@ -325,92 +338,138 @@ k_aca_warp(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restric
 // reduction suffices. Used columns, seen rows and the reference-row residual
 // live in global scratch owned by the cluster.
 // --------------------------------------------------------------------------
+// The reduced values of one step: sums, maxima, an argmax with its signed
+// value (ties to the lowest index) and a minimum index. Each thread keeps one
+// in its own type R (compensated sums, exact maxima); warps, CTAs and the
+// cluster combine them in R, in a fixed order, and only the cluster result is
+// widened to double (Red).
 struct Red {
-    double s0, s1;        // sums
-    double x0, x1;        // maxima
-    double av, aval;      // argmax value (|.|) and the signed value there
-    int ai, mn;           // argmax index (ties: lowest), minimum
+    double s0, s1;
+    double x0, x1;
+    double av, aval;
+    int ai, mn;
 };
 
-__device__ __forceinline__ void red_init(Red& q)
-{
-    q.s0 = q.s1 = 0.0;
-    q.x0 = q.x1 = 0.0;
-    q.av = -1.0;
-    q.aval = 0.0;
-    q.ai = 0x7fffffff;
-    q.mn = 0x7fffffff;
-}
-
-__device__ __forceinline__ void red_join(Red& q, const Red& o)
-{
-    q.s0 += o.s0;
-    q.s1 += o.s1;
-    q.x0 = fmax(q.x0, o.x0);
-    q.x1 = fmax(q.x1, o.x1);
-    if (o.av > q.av || (o.av == q.av && o.ai < q.ai)) {
-        q.av = o.av;
-        q.ai = o.ai;
-        q.aval = o.aval;
+template <class R>
+struct LRed {
+    TSum<R> s0, s1;
+    R x0, x1, av, aval;
+    int ai, mn;
+    __device__ __forceinline__ void init()
+    {
+        s0.init();
+        s1.init();
+        x0 = x1 = R(0);
+        av = R(-1);
+        aval = R(0);
+        ai = mn = 0x7fffffff;
     }
-    q.mn = min(q.mn, o.mn);
-}
-
-__device__ __forceinline__ void red_warp(Red& q)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        Red p;
-        p.s0 = __shfl_xor_sync(0xffffffffu, q.s0, o);
-        p.s1 = __shfl_xor_sync(0xffffffffu, q.s1, o);
-        p.x0 = __shfl_xor_sync(0xffffffffu, q.x0, o);
-        p.x1 = __shfl_xor_sync(0xffffffffu, q.x1, o);
-        p.av = __shfl_xor_sync(0xffffffffu, q.av, o);
-        p.aval = __shfl_xor_sync(0xffffffffu, q.aval, o);
-        p.ai = __shfl_xor_sync(0xffffffffu, q.ai, o);
-        p.mn = __shfl_xor_sync(0xffffffffu, q.mn, o);
-        red_join(q, p);
+    __device__ __forceinline__ void join(const LRed& o)
+    {
+        s0.join(o.s0);
+        s1.join(o.s1);
+        x0 = max(x0, o.x0);
+        x1 = max(x1, o.x1);
+        if (o.av > av || (o.av == av && o.ai < ai)) {
+            av = o.av;
+            ai = o.ai;
+            aval = o.aval;
+        }
+        mn = min(mn, o.mn);
     }
-}
+    // butterfly step: every lane ends with the same values
+    __device__ __forceinline__ void shfl_join(int o)
+    {
+        s0.shfl_join(o);
+        s1.shfl_join(o);
+        x0 = max(x0, __shfl_xor_sync(0xffffffffu, x0, o));
+        x1 = max(x1, __shfl_xor_sync(0xffffffffu, x1, o));
+        const R oav = __shfl_xor_sync(0xffffffffu, av, o);
+        const R oaval = __shfl_xor_sync(0xffffffffu, aval, o);
+        const int oai = __shfl_xor_sync(0xffffffffu, ai, o);
+        if (oav > av || (oav == av && oai < ai)) {
+            av = oav;
+            ai = oai;
+            aval = oaval;
+        }
+        mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    }
+    __device__ __forceinline__ Red widen() const
+    {
+        Red t;
+        t.s0 = s0.value();
+        t.s1 = s1.value();
+        t.x0 = (double)x0;
+        t.x1 = (double)x1;
+        t.av = (double)av;
+        t.aval = (double)aval;
+        t.ai = ai;
+        t.mn = mn;
+        return t;
+    }
+};
 
+template <class R>
 struct ClPart {
-    Red q;
+    LRed<R> q;
     double du[KBUF], dv[KBUF];
 };
 
+// Decisions of one step, taken once per CTA by the thread that forms the
+// cluster result (every CTA of a cluster takes the same ones).
+struct Ctl {
+    double rlim2;    // tol^2 S2 / m: squared limit of a resolved reference row
+    int resolved;    // reference-row residual within the limit
+    int stop_ok;     // |u||v| <= thr sqrt(S2)
+};
+
+template <class R>
 struct ClShared {
-    ClPart part[2];
-    Red wq[CTA_WARPS];
-    double wl[CTA_WARPS][KBUF];   // per-warp partial dots
-    double wm[CTA_WARPS][KBUF];
-    Red out;                      // broadcast: the cluster-wide result
-    double cross;
+    ClPart<R> part[2];
+    LRed<R> wq[CTA_WARPS];
+    R wl[CTA_WARPS][KBUF];   // per-warp partial dots
+    R wm[CTA_WARPS][KBUF];
+    Red out;                 // broadcast: the cluster-wide result
+    Ctl ctl;
+};
+
+struct NoFin {
+    __device__ __forceinline__ void operator()(const Red&, double) const {}
 };
 
 // Cluster-wide reduction of q (and, with ndots > 0, of the per-warp dot
-// partials in sh.wl / sh.wm); every thread of every CTA receives the result.
-template <class CL>
-__device__ Red cl_reduce(CL& cl, ClShared& sh, int& ph, Red q, int ndots)
+// partials in sh.wl / sh.wm, whose cross sum is handed to fin); thread 0 of
+// every CTA runs fin on the result, which may write sh.ctl; every thread of
+// every CTA receives the result. No barrier is needed after the broadcast is
+// read: the next reduction's first barrier orders those reads before sh.out
+// and sh.ctl are written again.
+template <class CL, class R, class FIN>
+__device__ Red cl_reduce(CL& cl, ClShared<R>& sh, int& ph, const LRed<R>& lq, int ndots,
+                         const FIN& fin)
 {
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int CS = (int)cl.num_blocks();
-    red_warp(q);
+    LRed<R> q = lq;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) q.shfl_join(o);
     if (lane == 0) sh.wq[w] = q;
     __syncthreads();
-    ClPart& P = sh.part[ph];
+    ClPart<R>& P = sh.part[ph];
     if (tid == 0) {
-        Red t = sh.wq[0];
-        for (int k = 1; k < CTA_WARPS; ++k) red_join(t, sh.wq[k]);
+        LRed<R> t = sh.wq[0];
+        for (int k = 1; k < CTA_WARPS; ++k) t.join(sh.wq[k]);
         P.q = t;
     }
     if (tid < ndots) {
-        double su = 0.0, sv = 0.0;
+        TSum<R> su, sv;
+        su.init();
+        sv.init();
         for (int k = 0; k < CTA_WARPS; ++k) {
-            su += sh.wl[k][tid];
-            sv += sh.wm[k][tid];
+            su.add(sh.wl[k][tid]);
+            sv.add(sh.wm[k][tid]);
         }
-        P.du[tid] = su;
-        P.dv[tid] = sv;
+        P.du[tid] = su.value();
+        P.dv[tid] = sv.value();
     }
     cl.sync();
     if (w == 0) {
@@ -420,24 +479,23 @@ __device__ Red cl_reduce(CL& cl, ClShared& sh, int& ph, Red q, int ndots)
             double su = 0.0, sv = 0.0;
             if (l < ndots)
                 for (int k = 0; k < CS; ++k) {
-                    const ClPart* Q = cl.map_shared_rank(&sh.part[ph], k);
+                    const ClPart<R>* Q = cl.map_shared_rank(&sh.part[ph], k);
                     su += Q->du[l];
                     sv += Q->dv[l];
                 }
             cr += warp_sum(su * sv);
         }
         if (lane == 0) {
-            Red t = cl.map_shared_rank(&sh.part[ph], 0)->q;
-            for (int k = 1; k < CS; ++k) red_join(t, cl.map_shared_rank(&sh.part[ph], k)->q);
-            sh.out = t;
-            sh.cross = cr;
+            LRed<R> t = cl.map_shared_rank(&sh.part[ph], 0)->q;
+            for (int k = 1; k < CS; ++k) t.join(cl.map_shared_rank(&sh.part[ph], k)->q);
+            const Red o = t.widen();
+            fin(o, cr);
+            sh.out = o;
         }
     }
     ph ^= 1;
     __syncthreads();
-    Red res = sh.out;
-    __syncthreads();
-    return res;
+    return sh.out;
 }
 
 template <class R, int KERN>
@@ -452,7 +510,7 @@ k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __rest
     const int CS = (int)cl.num_blocks();
     const int crank = (int)cl.block_rank();
     __shared__ R sg[KBUF];
-    __shared__ ClShared sh;
+    __shared__ ClShared<R> sh;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int gt = crank * CTA_NT + tid, GT = CS * CTA_NT;
     const int64_t cid = blockIdx.x / CS, ncl = gridDim.x / CS;
@@ -463,6 +521,8 @@ k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __rest
     const R c = kconst<R>(kp);
     const R eps0 = (R)a.eps0;
     const double rtol = a.eps > 0.0 ? a.eps : a.eps0;
+    const double thr2 = thr * thr;
+    const NoFin nofin;
     int ph = 0;
 
     for (int64_t q = cid; q < nblocks; q += ncl) {
@@ -475,12 +535,26 @@ k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __rest
         R* __restrict__ V = reinterpret_cast<R*>(a.Vptr[b]);
         const int wn = (n + 31) / 32, wm = (m + 31) / 32;
         const double floor2 = a.bset ? (double)m * (double)n / (double)a.set_n[a.bset[b]] : 0.0;
+        const double rtol2_m = rtol * rtol / (double)m;
+        double S2 = 0.0;   // ||S_r||_F^2, kept by thread 0 of each CTA
+        // the step's decisions from the row reduction: S2, the reference-row
+        // limit and both tests in squared form
+        auto fin_row = [&](const Red& o, double cross) {
+            S2 += 2.0 * cross + o.s0 * o.s1;
+            const double S2f = fmax(S2, floor2);
+            const double rlim2 = rtol2_m * S2f;
+            sh.ctl.rlim2 = rlim2;
+            sh.ctl.resolved = !(o.x1 * o.x1 > rlim2);
+            sh.ctl.stop_ok = thr >= 0.0 && o.s0 * o.s1 <= thr2 * S2f;
+        };
+        auto fin_ref = [&](const Red& o, double) {
+            sh.ctl.resolved = !(o.x1 * o.x1 > sh.ctl.rlim2);
+        };
         for (int k = gt; k < wn; k += GT) used[k] = 0u;
         for (int k = gt; k < wm; k += GT) seen[k] = 0u;
         cl.sync();
         if (gt == 0) seen[0] = 1u;
         // reference row 0
-        double rmax = 0.0;
         {
             const Pt<R> p0 = load_pt<R>(X, B.row0);
             for (int jj = gt; jj < n; jj += GT) {
@@ -490,7 +564,6 @@ k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __rest
         }
         int r = 0, j = 0, rej = 0, run = 0, iref = 0;
         bool converged = false;
-        double S2 = 0.0;
         const int limit = kmax + n + 1;
         for (int it = 0; r < kmax; ++it) {
             if (it > limit) {
@@ -503,8 +576,8 @@ k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __rest
             // residual column, its pivot and u^ at the reference row
             const Pt<R> pj = load_pt<R>(X, B.col0 + j);
             R* __restrict__ Ur = U + (int64_t)r * m;
-            Red qc;
-            red_init(qc);
+            LRed<R> qc;
+            qc.init();
             // rows in chunks of UNR per thread so that UNR loads are in flight
             for (int i0 = gt; i0 < m; i0 += UNR * GT) {
                 Resid<R> rs_[UNR];
@@ -514,7 +587,7 @@ k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __rest
                     R a0 = 0;
                     if (i < m) {
                         a0 = phi<KERN>(dist2(load_pt<R>(X, B.row0 + i), pj), c);
-                        qc.x0 = fmax(qc.x0, (double)fabs(a0));
+                        qc.x0 = max(qc.x0, fabs(a0));
                     }
                     rs_[q].init(a0);
                 }
@@ -533,15 +606,15 @@ k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __rest
                     if (i >= m) continue;
                     const R v = rs_[q].value();
                     Ur[i] = v;
-                    if ((double)fabs(v) > qc.av) {
+                    if (fabs(v) > qc.av) {
                         qc.av = fabs(v);
                         qc.ai = i;
                         qc.aval = v;
                     }
-                    if (i == iref) qc.s0 = v;
+                    if (i == iref) qc.s0.set(v);
                 }
             }
-            const Red oc = cl_reduce(cl, sh, ph, qc, 0);
+            const Red oc = cl_reduce(cl, sh, ph, qc, 0, nofin);
             const R best = (R)oc.av, amax = (R)oc.x0;
             const int bi = oc.ai;
             if (!(best > eps0 * amax)) {
@@ -551,8 +624,8 @@ k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __rest
                     break;
                 }
                 // lowest unused column over the whole cluster
-                Red qn;
-                red_init(qn);
+                LRed<R> qn;
+                qn.init();
                 for (int k = gt; k < wn; k += GT) {
                     uint32_t free_bits = ~used[k];
                     if (k == wn - 1 && (n & 31)) free_bits &= (1u << (n & 31)) - 1u;
@@ -561,7 +634,7 @@ k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __rest
                         break;
                     }
                 }
-                const int cand = cl_reduce(cl, sh, ph, qn, 0).mn;
+                const int cand = cl_reduce(cl, sh, ph, qn, 0, nofin).mn;
                 if (cand == 0x7fffffff || cand >= n) {
                     converged = true;
                     break;
@@ -578,8 +651,8 @@ k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __rest
             // residual row, scaled column, reference row, norms, next column
             const Pt<R> pi = load_pt<R>(X, B.row0 + bi);
             R* __restrict__ Vr = V + (int64_t)r * n;
-            Red qr;
-            red_init(qr);
+            LRed<R> qr;
+            qr.init();
             for (int j0 = gt; j0 < n; j0 += UNR * GT) {
                 Resid<R> rs_[UNR];
 #pragma unroll
@@ -602,7 +675,7 @@ k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __rest
                     if (jj >= n) continue;
                     const R v = rs_[q].value();
                     Vr[jj] = v;
-                    qr.s1 += (double)v * (double)v;
+                    qr.s1.add(v * v);
                     Resid<R> rx;
                     rx.s = rr[jj];
                     rx.setc(rc[jj]);
@@ -610,8 +683,8 @@ k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __rest
                     rr[jj] = rx.s;
                     rc[jj] = rx.getc();
                     const R x = rx.value();
-                    qr.x1 = fmax(qr.x1, (double)fabs(x));
-                    if (!((used[jj >> 5] >> (jj & 31)) & 1u) && (double)fabs(x) > qr.av) {
+                    qr.x1 = max(qr.x1, fabs(x));
+                    if (!((used[jj >> 5] >> (jj & 31)) & 1u) && fabs(x) > qr.av) {
                         qr.av = fabs(x);
                         qr.ai = jj;
                     }
@@ -621,7 +694,7 @@ k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __rest
             for (int i = gt; i < m; i += GT) {
                 const R u = Ur[i] / piv;
                 Ur[i] = u;
-                qr.s0 += (double)u * (double)u;
+                qr.s0.add(u * u);
             }
             for (int l = 0; l < r; ++l) {
                 const R* Ul = U + (int64_t)l * m;
@@ -649,24 +722,21 @@ k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __rest
 #pragma unroll
                     for (int q = 0; q < UNR; ++q) dv += a[q] * b[q];
                 }
-                const double ddu = warp_sum((double)du), ddv = warp_sum((double)dv);
+                const R ddu = warp_sum(du), ddv = warp_sum(dv);
                 if (lane == 0) {
                     sh.wl[w][l] = ddu;
                     sh.wm[w][l] = ddv;
                 }
             }
-            const Red orr = cl_reduce(cl, sh, ph, qr, r);
-            const double NU2 = orr.s0, NV2 = orr.s1, cross = sh.cross;
-            rmax = orr.x1;
+            const Red orr = cl_reduce(cl, sh, ph, qr, r, fin_row);
             int nj = orr.ai;
-            S2 += 2.0 * cross + NU2 * NV2;
             ++r;
+            bool resolved = sh.ctl.resolved;
+            const bool stop_ok = sh.ctl.stop_ok;
             // a resolved reference row moves to the lowest row not seen yet
-            const double S2f = fmax(S2, floor2);
-            const double rlim = rtol * sqrt(S2f / (double)m);
-            if (!(rmax > rlim)) {
-                Red qs;
-                red_init(qs);
+            if (resolved) {
+                LRed<R> qs;
+                qs.init();
                 for (int k = gt; k < wm; k += GT) {
                     uint32_t free_bits = ~seen[k];
                     if (k == wm - 1 && (m & 31)) free_bits &= (1u << (m & 31)) - 1u;
@@ -675,15 +745,15 @@ k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __rest
                         break;
                     }
                 }
-                const int cand = cl_reduce(cl, sh, ph, qs, 0).mn;
+                const int cand = cl_reduce(cl, sh, ph, qs, 0, nofin).mn;
                 if (cand != 0x7fffffff && cand < m) {
                     iref = cand;
                     if (gt == 0) seen[iref >> 5] |= 1u << (iref & 31);
                     if (tid < r) sg[tid] = U[(int64_t)tid * m + iref];
                     __syncthreads();
                     const Pt<R> pr = load_pt<R>(X, B.row0 + iref);
-                    Red qf;
-                    red_init(qf);
+                    LRed<R> qf;
+                    qf.init();
                     for (int j0 = gt; j0 < n; j0 += UNR * GT) {
                         Resid<R> rs_[UNR];
 #pragma unroll
@@ -707,19 +777,19 @@ k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __rest
                             const R x = rs_[q].value();
                             rr[jj] = rs_[q].s;
                             rc[jj] = rs_[q].getc();
-                            qf.x1 = fmax(qf.x1, (double)fabs(x));
-                            if (!((used[jj >> 5] >> (jj & 31)) & 1u) && (double)fabs(x) > qf.av) {
+                            qf.x1 = max(qf.x1, fabs(x));
+                            if (!((used[jj >> 5] >> (jj & 31)) & 1u) && fabs(x) > qf.av) {
                                 qf.av = fabs(x);
                                 qf.ai = jj;
                             }
                         }
                     }
-                    const Red of = cl_reduce(cl, sh, ph, qf, 0);
-                    rmax = of.x1;
+                    const Red of = cl_reduce(cl, sh, ph, qf, 0, fin_ref);
+                    resolved = sh.ctl.resolved;
                     nj = of.ai;
                 }
             }
-            if (thr >= 0.0 && sqrt(NU2) * sqrt(NV2) <= thr * sqrt(S2f) && !(rmax > rlim)) {
+            if (stop_ok && resolved) {
                 converged = true;
                 break;
             }

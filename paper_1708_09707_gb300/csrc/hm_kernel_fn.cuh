@@ -155,6 +155,60 @@ struct Resid<float> {
     __device__ __forceinline__ float value() const { return __fadd_rn(s, c); }
 };
 
+// Sum kept by one thread (or combined over a warp). In double a plain sum.
+// In float a compensated pair s + c: every addition is Knuth's TwoSum, whose
+// exact rounding error is added to c, so the pair is accurate to about 2^-24
+// of the sum of magnitudes however many terms it takes, and the float kernels
+// do no double arithmetic per entry (this GPU's double pipe runs at a small
+// fraction of its float rate).
+template <class R>
+struct TSum;
+
+template <>
+struct TSum<double> {
+    double s;
+    __device__ __forceinline__ void init() { s = 0.0; }
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ void set(double x) { s = x; }
+    __device__ __forceinline__ void join(const TSum& o) { s += o.s; }
+    __device__ __forceinline__ void shfl_join(int o) { s += __shfl_xor_sync(0xffffffffu, s, o); }
+    __device__ __forceinline__ double value() const { return s; }
+};
+
+template <>
+struct TSum<float> {
+    float s, c;
+    __device__ __forceinline__ void init()
+    {
+        s = 0.f;
+        c = 0.f;
+    }
+    __device__ __forceinline__ void add2(float x, float xc)
+    {
+        const float t = __fadd_rn(s, x);
+        const float z = __fsub_rn(t, s);
+        const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(x, z));
+        s = t;
+        // (c + xc) + e: symmetric in the two operands, so a butterfly over a
+        // warp leaves the same pair in every lane
+        c = __fadd_rn(__fadd_rn(c, xc), e);
+    }
+    __device__ __forceinline__ void add(float x) { add2(x, 0.f); }
+    __device__ __forceinline__ void set(float x)
+    {
+        s = x;
+        c = 0.f;
+    }
+    __device__ __forceinline__ void join(const TSum& o) { add2(o.s, o.c); }
+    __device__ __forceinline__ void shfl_join(int o)
+    {
+        const float os = __shfl_xor_sync(0xffffffffu, s, o);
+        const float oc = __shfl_xor_sync(0xffffffffu, c, o);
+        add2(os, oc);
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
 // Warp-wide helpers.
 template <class T>
 __device__ __forceinline__ T warp_sum(T v)
