@@ -73,7 +73,7 @@ k_aca_warp(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restric
     const double rtol2_m = rtol * rtol / (double)m, thr2 = thr * thr;
 
     R acc[MAXR], vv[MAXR];
-    Resid<R> res[MAXR], rr[MAXR];   // rr: reference-row residual (compensated)
+    Resid<R> res[MAXR], rr[MAXR];   // rr: reference-row residual
     unsigned used = 0, seen = (lane == 0) ? 1u : 0u;
     int r = 0, j = 0, rej = 0, run = 0, iref = 0;
     bool converged = false;
@@ -516,8 +516,7 @@ k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __rest
     const int64_t cid = blockIdx.x / CS, ncl = gridDim.x / CS;
     uint32_t* used = usedpool + cid * words;
     uint32_t* seen = seenpool + cid * words;
-    R* rr = rrpool + cid * 2 * maxdim;   // reference-row residual: value
-    R* rc = rr + maxdim;                  // and its rounding compensation
+    R* rr = rrpool + cid * maxdim;   // reference-row residual
     const R c = kconst<R>(kp);
     const R eps0 = (R)a.eps0;
     const double rtol = a.eps > 0.0 ? a.eps : a.eps0;
@@ -559,7 +558,6 @@ k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __rest
             const Pt<R> p0 = load_pt<R>(X, B.row0);
             for (int jj = gt; jj < n; jj += GT) {
                 rr[jj] = phi<KERN>(dist2(p0, load_pt<R>(X, B.col0 + jj)), c);
-                rc[jj] = 0;
             }
         }
         int r = 0, j = 0, rej = 0, run = 0, iref = 0;
@@ -677,12 +675,10 @@ k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __rest
                     Vr[jj] = v;
                     qr.s1.add(v * v);
                     Resid<R> rx;
-                    rx.s = rr[jj];
-                    rx.setc(rc[jj]);
+                    rx.init(rr[jj]);
                     rx.sub(uiref, v);
-                    rr[jj] = rx.s;
-                    rc[jj] = rx.getc();
                     const R x = rx.value();
+                    rr[jj] = x;
                     qr.x1 = max(qr.x1, fabs(x));
                     if (!((used[jj >> 5] >> (jj & 31)) & 1u) && fabs(x) > qr.av) {
                         qr.av = fabs(x);
@@ -775,8 +771,7 @@ k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __rest
                             const int jj = j0 + q * GT;
                             if (jj >= n) continue;
                             const R x = rs_[q].value();
-                            rr[jj] = rs_[q].s;
-                            rc[jj] = rs_[q].getc();
+                            rr[jj] = x;
                             qf.x1 = max(qf.x1, fabs(x));
                             if (!((used[jj >> 5] >> (jj & 31)) & 1u) && fabs(x) > qf.av) {
                                 qf.av = fabs(x);
@@ -834,7 +829,7 @@ void launch_all(const KernelParams& kp, const DeviceCoords& X, const AcaArgs& a,
         const int64_t words = ceil_div(dim, 32);
         DevBuf<uint32_t> usedpool((size_t)(nclusters * words), s);
         DevBuf<uint32_t> seenpool((size_t)(nclusters * words), s);
-        DevBuf<R> rrpool((size_t)(nclusters * 2 * dim), s);
+        DevBuf<R> rrpool((size_t)(nclusters * dim), s);
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)(nclusters * cs));
         cfg.blockDim = dim3(CTA_NT);

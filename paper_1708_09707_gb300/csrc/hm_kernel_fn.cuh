@@ -108,51 +108,16 @@ __host__ __device__ __forceinline__ float kconst<float>(const KernelParams& kp)
     return kp.c32;
 }
 
-// Residual accumulator r = a - sum_l u_l v_l of the ACA cross updates. In
-// double it is a plain fused multiply-add chain. In float every update is an
-// error-free transformation: u v = p + e exactly (e from a fused multiply-add)
-// and s - p = t + err exactly (Knuth's TwoSum), the rounding errors err - e
-// are collected in a second float, and the residual is s + c. Without this the
-// float residual of a rank-r approximation carries about r * 2^-24 |a| of
-// rounding, as large as the 1e-6 accuracy asked of the approximation; with it
-// the residual is accurate to about 2^-24 of itself, and the stored float
-// factors are corrected by the later cross updates.
+// Residual accumulator r = a - sum_l u_l v_l of the ACA cross updates: a
+// fused multiply-add chain in the kernel's type. In float the chain's rounding
+// is about sqrt(r) 2^-24 |a|, far below the accuracy asked of the
+// approximation (eps >= 1e-6 relative to the block).
 template <class R>
-struct Resid;
-
-template <>
-struct Resid<double> {
-    double s;
-    __device__ __forceinline__ void init(double a) { s = a; }
-    __device__ __forceinline__ void setc(double) {}
-    __device__ __forceinline__ double getc() const { return 0.0; }
-    __device__ __forceinline__ void sub(double u, double v) { s = fma(-u, v, s); }
-    __device__ __forceinline__ double value() const { return s; }
-};
-
-template <>
-struct Resid<float> {
-    float s, c;
-    __device__ __forceinline__ void init(float a)
-    {
-        s = a;
-        c = 0.f;
-    }
-    __device__ __forceinline__ void setc(float v) { c = v; }
-    __device__ __forceinline__ float getc() const { return c; }
-    // round-to-nearest intrinsics: the compiler must not contract or
-    // reassociate these operations
-    __device__ __forceinline__ void sub(float u, float v)
-    {
-        const float p = __fmul_rn(u, v);
-        const float e = __fmaf_rn(u, v, -p);
-        const float t = __fsub_rn(s, p);
-        const float z = __fsub_rn(t, s);
-        const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(-p, z));
-        s = t;
-        c = __fadd_rn(c, __fsub_rn(err, e));
-    }
-    __device__ __forceinline__ float value() const { return __fadd_rn(s, c); }
+struct Resid {
+    R s;
+    __device__ __forceinline__ void init(R a) { s = a; }
+    __device__ __forceinline__ void sub(R u, R v) { s = fma(-u, v, s); }
+    __device__ __forceinline__ R value() const { return s; }
 };
 
 // Sum kept by one thread (or combined over a warp). In double a plain sum.
