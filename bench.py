@@ -400,12 +400,13 @@ def main():
                         "ms": mvp_t_vtx}}
     mvp_roof["frac"] = mvp_roof["achieved"] / hbm
     mvp_roof["peak_source"] = peak_src + " copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
-    sm_mhz = clocks.get("sm_mhz") or SM_MAX_MHZ
-    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    fp32_peak = hm.alu_peak(hm.PREC_MIXED) / 1e12
     aca_roof = {"bound": "alu", "kernel": "batched ACA (all size classes, concurrent)",
                 "achieved": st["aca_flops"] / (st["t_aca_ms"] * 1e-3) / 1e12,
                 "peak": fp32_peak, "unit": "TFLOP/s", "traffic": None,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz"}
+                "peak_source": "measured: FP32 FMA chains on every SM (hm_alu_peak); "
+                               "nominal 152 SMs x 128 lanes x 2 x 2070 MHz = %.1f"
+                               % (SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12)}
     aca_roof["frac"] = aca_roof["achieved"] / fp32_peak
     # dominant kernel of the step: ACA phase vs the N_MVP gather launches
     dominant = aca_roof if st["t_aca_ms"] > N_MVP * mvp_t_tile else mvp_roof

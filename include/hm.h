@@ -254,6 +254,18 @@ int hm_radix_sort_pairs(uint64_t* keys, uint32_t* values, int64_t n,
 int hm_radix_sort_pairs_noalloc(uint64_t* keys, uint32_t* values, int64_t n, int key_bits,
                                 void* stream);
 
+/* ------------------------------------------------------------------------
+ * Measured arithmetic peak. Not part of the paper's method: it gives the
+ * denominator of the roofline fractions of the ALU-bound kernels (ACA, dense
+ * evaluation). A kernel of independent fused multiply-add chains fills every
+ * SM of the current device; the best of three launches, timed with CUDA
+ * events, gives *flops in FLOP/s (one FMA counts 2).
+ *   precision  HM_PREC_MIXED: FP32 FMA;  HM_PREC_FP64: FP64 FMA
+ *   flops      host pointer, written on success
+ * Synchronises the device. Returns HM_EINVAL for a NULL pointer or an unknown
+ * precision, HM_ECUDA if a CUDA call fails. */
+int hm_alu_peak(int precision, double* flops);
+
 #ifdef __cplusplus
 }
 #endif

@@ -42,7 +42,7 @@ constexpr int CTA_NT = 256;
 constexpr int CTA_WARPS = CTA_NT / 32;
 constexpr int KBUF = 128;      // largest supported k_cap
 constexpr int REJ_RUN = 4;     // rejected columns in a row that end a block
-constexpr int UNR = 8;         // rows (columns) per thread whose loads are issued together
+constexpr int UNR = 4;         // rows (columns) per thread whose loads are issued together
 
 // --------------------------------------------------------------------------
 // One warp per block (m, n <= 32 MAXR). Lane l owns rows and columns
@@ -499,7 +499,7 @@ __device__ Red cl_reduce(CL& cl, ClShared<R>& sh, int& ph, const LRed<R>& lq, in
 }
 
 template <class R, int KERN>
-__global__ void __launch_bounds__(CTA_NT)
+__global__ void __launch_bounds__(CTA_NT, 3)
 k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restrict__ order,
               int64_t nblocks, double thr, uint32_t* __restrict__ usedpool,
               uint32_t* __restrict__ seenpool, R* __restrict__ rrpool, int64_t words,

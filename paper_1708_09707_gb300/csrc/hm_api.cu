@@ -325,4 +325,18 @@ int hm_radix_sort_pairs_noalloc(uint64_t* keys, uint32_t* values, int64_t n, int
     }
 }
 
+int hm_alu_peak(int precision, double* flops)
+{
+    set_error("");
+    try {
+        if (!flops) fail(HM_EINVAL, "flops is NULL");
+        if (precision != HM_PREC_FP64 && precision != HM_PREC_MIXED)
+            fail(HM_EINVAL, "unknown precision");
+        *flops = alu_peak(precision);
+        return HM_OK;
+    } catch (const std::exception& e) {
+        return to_status(e);
+    }
+}
+
 }  // extern "C"

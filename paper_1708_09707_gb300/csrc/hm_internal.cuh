@@ -82,6 +82,7 @@ void copy_out(void* dst, const void* src_dev, size_t bytes, cudaStream_t s);
 
 __host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 int num_sms();
+double alu_peak(int precision);   // FLOP/s of FMA chains on the current device
 
 // Count of kernels this library has launched in the process (hm_kernel_launches).
 void note_launch();

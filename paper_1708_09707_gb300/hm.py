@@ -88,6 +88,7 @@ def _declare(L):
     L.hm_options_default.argtypes = [C.POINTER(Options)]
     L.hm_last_error.restype = C.c_char_p
     L.hm_kernel_launches.restype = C.c_uint64
+    L.hm_alu_peak.argtypes = [C.c_int, C.POINTER(C.c_double)]
     L.hm_build_ex.restype = _vp
     L.hm_build_ex.argtypes = [_vp, i64, C.c_int, C.c_int, _vp, C.c_int, C.c_double,
                               C.c_double, C.POINTER(Options), pi]
@@ -341,3 +342,10 @@ def mlp_adam(theta, grad, m, v, t: int, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, str
 def kernel_launches() -> int:
     """Kernels the library has launched in this process."""
     return int(lib().hm_kernel_launches())
+
+
+def alu_peak(precision: int = PREC_MIXED) -> float:
+    """Measured FMA throughput (FLOP/s) of the current device (hm_alu_peak)."""
+    v = C.c_double(0.0)
+    _check(lib().hm_alu_peak(precision, C.byref(v)))
+    return v.value

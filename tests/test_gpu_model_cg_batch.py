@@ -159,3 +159,14 @@ def test_batch_equals_separate_builds(hm, prec):
         o += p.shape[0]
     st = B.stats()
     assert st["n_points"] == int(sizes.sum())
+
+
+def test_alu_peak_is_plausible(hm):
+    """The measured FMA peaks used as roofline denominators: FP32 near the
+    CUDA-core rate, FP64 far below it on this part."""
+    f32 = hm.alu_peak(hm.PREC_MIXED)
+    f64 = hm.alu_peak(hm.PREC_FP64)
+    assert 10e12 < f32 < 200e12, f32
+    assert 0.1e12 < f64 < f32, f64
+    with pytest.raises(hm.HMError):
+        hm.alu_peak(7)
