@@ -429,7 +429,7 @@ struct ClShared {
     LRed<R> wq[CTA_WARPS];
     R wl[CTA_WARPS][KBUF];   // per-warp partial dots
     R wm[CTA_WARPS][KBUF];
-    Red out;                 // broadcast: the cluster-wide result
+    LRed<R> out;             // broadcast: the cluster-wide result
     Ctl ctl;
 };
 
@@ -439,13 +439,13 @@ struct NoFin {
 
 // Cluster-wide reduction of q (and, with ndots > 0, of the per-warp dot
 // partials in sh.wl / sh.wm, whose cross sum is handed to fin); thread 0 of
-// every CTA runs fin on the result, which may write sh.ctl; every thread of
-// every CTA receives the result. No barrier is needed after the broadcast is
-// read: the next reduction's first barrier orders those reads before sh.out
-// and sh.ctl are written again.
+// every CTA runs fin on the result widened to double, which may write
+// sh.ctl; every thread of every CTA receives the result in R. No barrier is
+// needed after the broadcast is read: the next reduction's first barrier
+// orders those reads before sh.out and sh.ctl are written again.
 template <class CL, class R, class FIN>
-__device__ Red cl_reduce(CL& cl, ClShared<R>& sh, int& ph, const LRed<R>& lq, int ndots,
-                         const FIN& fin)
+__device__ LRed<R> cl_reduce(CL& cl, ClShared<R>& sh, int& ph, const LRed<R>& lq, int ndots,
+                             const FIN& fin)
 {
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int CS = (int)cl.num_blocks();
@@ -488,9 +488,8 @@ __device__ Red cl_reduce(CL& cl, ClShared<R>& sh, int& ph, const LRed<R>& lq, in
         if (lane == 0) {
             LRed<R> t = cl.map_shared_rank(&sh.part[ph], 0)->q;
             for (int k = 1; k < CS; ++k) t.join(cl.map_shared_rank(&sh.part[ph], k)->q);
-            const Red o = t.widen();
-            fin(o, cr);
-            sh.out = o;
+            fin(t.widen(), cr);
+            sh.out = t;
         }
     }
     ph ^= 1;
@@ -533,9 +532,13 @@ k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __rest
         R* __restrict__ U = reinterpret_cast<R*>(a.Uptr[b]);
         R* __restrict__ V = reinterpret_cast<R*>(a.Vptr[b]);
         const int wn = (n + 31) / 32, wm = (m + 31) / 32;
-        const double floor2 = a.bset ? (double)m * (double)n / (double)a.set_n[a.bset[b]] : 0.0;
-        const double rtol2_m = rtol * rtol / (double)m;
-        double S2 = 0.0;   // ||S_r||_F^2, kept by thread 0 of each CTA
+        // ||S_r||_F^2, the floor and tol^2 / m: kept and used by thread 0 of
+        // each CTA only (the other threads do no double arithmetic)
+        double S2 = 0.0, floor2 = 0.0, rtol2_m = 0.0;
+        if (tid == 0) {
+            floor2 = a.bset ? (double)m * (double)n / (double)a.set_n[a.bset[b]] : 0.0;
+            rtol2_m = rtol * rtol / (double)m;
+        }
         // the step's decisions from the row reduction: S2, the reference-row
         // limit and both tests in squared form
         auto fin_row = [&](const Red& o, double cross) {
@@ -612,8 +615,8 @@ k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __rest
                     if (i == iref) qc.s0.set(v);
                 }
             }
-            const Red oc = cl_reduce(cl, sh, ph, qc, 0, nofin);
-            const R best = (R)oc.av, amax = (R)oc.x0;
+            const LRed<R> oc = cl_reduce(cl, sh, ph, qc, 0, nofin);
+            const R best = oc.av, amax = oc.x0;
             const int bi = oc.ai;
             if (!(best > eps0 * amax)) {
                 ++rej;
@@ -641,8 +644,8 @@ k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __rest
                 continue;
             }
             run = 0;
-            const R piv = (R)oc.aval;
-            const R uiref = (R)oc.s0 / piv;
+            const R piv = oc.aval;
+            const R uiref = oc.s0.s / piv;
             if (gt == 0) seen[bi >> 5] |= 1u << (bi & 31);
             if (tid < r) sg[tid] = U[(int64_t)tid * m + bi];
             __syncthreads();
@@ -724,7 +727,7 @@ k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __rest
                     sh.wm[w][l] = ddv;
                 }
             }
-            const Red orr = cl_reduce(cl, sh, ph, qr, r, fin_row);
+            const LRed<R> orr = cl_reduce(cl, sh, ph, qr, r, fin_row);
             int nj = orr.ai;
             ++r;
             bool resolved = sh.ctl.resolved;
@@ -779,7 +782,7 @@ k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __rest
                             }
                         }
                     }
-                    const Red of = cl_reduce(cl, sh, ph, qf, 0, fin_ref);
+                    const LRed<R> of = cl_reduce(cl, sh, ph, qf, 0, fin_ref);
                     resolved = sh.ctl.resolved;
                     nj = of.ai;
                 }

@@ -120,11 +120,12 @@ struct Resid {
     __device__ __forceinline__ R value() const { return s; }
 };
 
-// Sum kept by one thread (or combined over a warp). In double a plain sum.
-// In float a compensated pair s + c: every addition is Knuth's TwoSum, whose
-// exact rounding error is added to c, so the pair is accurate to about 2^-24
-// of the sum of magnitudes however many terms it takes, and the float kernels
-// do no double arithmetic per entry (this GPU's double pipe runs at a small
+// Sum kept by one thread and combined over threads. In double a plain sum.
+// In float a pair s + c: a thread adds its own terms plainly (it holds at
+// most a few dozen, so its partial is accurate to about 1e-6 of itself),
+// and the joins of partials across lanes, warps and CTAs are Knuth's TwoSum,
+// whose exact rounding error is carried in c. The float kernels thus do no
+// double arithmetic per entry (this GPU's double pipe runs at a small
 // fraction of its float rate).
 template <class R>
 struct TSum;
@@ -158,7 +159,7 @@ struct TSum<float> {
         // warp leaves the same pair in every lane
         c = __fadd_rn(__fadd_rn(c, xc), e);
     }
-    __device__ __forceinline__ void add(float x) { add2(x, 0.f); }
+    __device__ __forceinline__ void add(float x) { s += x; }
     __device__ __forceinline__ void set(float x)
     {
         s = x;
