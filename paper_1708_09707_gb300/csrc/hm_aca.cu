@@ -810,46 +810,599 @@ k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __rest
     }
 }
 
+// --------------------------------------------------------------------------
+// Blocks with 512 < max(m, n) <= 65536: one CTA or one thread-block cluster
+// of CS CTAs per block, persistent over the blocks of a size class. Thread g
+// of the cluster (g = rank * NT + tid, G = CS * NT) owns the rows g + qG and
+// the columns g + qG, q < R, and keeps in registers the residual column at
+// its rows, the reference-row residual at its columns and bit masks of its
+// used columns and seen rows, so a step touches global memory only for the
+// block's earlier factor columns, and loads LC ranks of R rows at once.
+//
+// The cross terms of ||S_r||_F^2 come out of the same passes. The column
+// pass subtracts the ranks in batches [l0, l0 + LC); before batch l0 the
+// residual is w = A(:, j) - sum_{l' < l0} u_l' (v_l')_j, and for l in the
+// batch
+//     u^ . u_l = w . u_l - sum_{l' >= l0} (u_l' . u_l) (v_l')_j,
+// so the pass accumulates w . u_l beside the residual, and the Gram matrix
+// of u_0 .. u_{r-1} (shared memory) corrects the sums afterwards; likewise on
+// the row side with the Gram matrix of the v's. A step therefore has two
+// reductions (three when the reference row moves).
+// --------------------------------------------------------------------------
+constexpr int KG = 64;                       // largest rank of k_aca_big
+constexpr int KGP = KG * (KG + 1) / 2;       // packed lower triangle
+constexpr int LC = 8;                        // ranks per batch of loads
+
+__device__ __forceinline__ int pk(int a, int b)   // a >= b
+{
+    return a * (a + 1) / 2 + b;
+}
+
+// Values reduced over the threads of a cluster in one step.
+template <class T>
+struct BRed {
+    TSum<T> s0, s1;   // sums
+    T x0;             // maximum
+    T av, aval;       // argmax: |value|, signed value
+    int ai;           // argmax index (ties: lowest index)
+    int mn;           // minimum index
+    T pick;           // a value contributed by a single thread (others 0)
+    __device__ __forceinline__ void init()
+    {
+        s0.init();
+        s1.init();
+        x0 = T(0);
+        av = T(-1);
+        aval = T(0);
+        ai = mn = 0x7fffffff;
+        pick = T(0);
+    }
+    __device__ __forceinline__ void take(T oav, T oaval, int oai)
+    {
+        if (oav > av || (oav == av && oai < ai)) {
+            av = oav;
+            ai = oai;
+            aval = oaval;
+        }
+    }
+    __device__ __forceinline__ void join(const BRed& o)
+    {
+        s0.join(o.s0);
+        s1.join(o.s1);
+        x0 = max(x0, o.x0);
+        take(o.av, o.aval, o.ai);
+        mn = min(mn, o.mn);
+        pick += o.pick;
+    }
+    __device__ __forceinline__ void shfl_join(int o)
+    {
+        s0.shfl_join(o);
+        s1.shfl_join(o);
+        x0 = max(x0, __shfl_xor_sync(0xffffffffu, x0, o));
+        const T oav = __shfl_xor_sync(0xffffffffu, av, o);
+        const T oaval = __shfl_xor_sync(0xffffffffu, aval, o);
+        const int oai = __shfl_xor_sync(0xffffffffu, ai, o);
+        take(oav, oaval, oai);
+        mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        pick += __shfl_xor_sync(0xffffffffu, pick, o);
+    }
+    __device__ __forceinline__ void bcast(int src)
+    {
+        s0.s = __shfl_sync(0xffffffffu, s0.s, src);
+        s1.s = __shfl_sync(0xffffffffu, s1.s, src);
+        if constexpr (sizeof(TSum<T>) > sizeof(T)) {
+            s0.c = __shfl_sync(0xffffffffu, s0.c, src);
+            s1.c = __shfl_sync(0xffffffffu, s1.c, src);
+        }
+        x0 = __shfl_sync(0xffffffffu, x0, src);
+        av = __shfl_sync(0xffffffffu, av, src);
+        aval = __shfl_sync(0xffffffffu, aval, src);
+        ai = __shfl_sync(0xffffffffu, ai, src);
+        mn = __shfl_sync(0xffffffffu, mn, src);
+        pick = __shfl_sync(0xffffffffu, pick, src);
+    }
+};
+
+template <class T, int NW>
+struct BigShared {
+    T Gu[KGP], Gv[KGP];          // Gram matrices of the u's and of the v's
+    T sgv[KG], sgu[KG];          // (v_l)_j and (u_l)_{i*} of the current step
+    T wvec[NW][KG];              // per-warp partial dot products
+    BRed<T> wq[NW];
+    struct Part {
+        BRed<T> q;
+        T vec[KG];
+    } part[2];                   // per-CTA partials, read by the whole cluster
+    double rlim2;                // decisions of thread 0
+    int resolved, stop_ok;
+};
+
+// Warp sums of eight per-lane values: lanes 4e .. 4e+3 receive the total of
+// value e (a reduce-scatter butterfly, nine shuffles in all).
+template <class T>
+__device__ __forceinline__ T warp_scatter8(const T (&p)[LC])
+{
+    const int lane = threadIdx.x & 31;
+    const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+    T a4[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const T send = h16 ? p[e] : p[e + 4];
+        const T keep = h16 ? p[e + 4] : p[e];
+        a4[e] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+    T a2[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const T send = h8 ? a4[e] : a4[e + 2];
+        const T keep = h8 ? a4[e + 2] : a4[e];
+        a2[e] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    T a1 = (h4 ? a2[1] : a2[0]) + __shfl_xor_sync(0xffffffffu, h4 ? a2[0] : a2[1], 4);
+    a1 += __shfl_xor_sync(0xffffffffu, a1, 2);
+    a1 += __shfl_xor_sync(0xffffffffu, a1, 1);
+    return a1;
+}
+
+// Cluster-wide reduction of q and of the first nvec entries of the per-warp
+// vectors sh.wvec. Every thread receives the scalar result; lane L of every
+// warp receives the vector entries L and L + 32 in vout. Partials are double
+// buffered (ph), so two barriers per reduction suffice: a later reduction
+// writes the other buffer, and the one after that only once every CTA has
+// passed the cluster barrier in between.
+template <class T, int NT, class CL>
+__device__ __forceinline__ BRed<T> big_reduce(CL& cl, int CS, BigShared<T, NT / 32>& sh, int& ph,
+                                              BRed<T> q, int nvec, T (&vout)[KG / 32])
+{
+    constexpr int NW = NT / 32;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) q.shfl_join(o);
+    if (lane == 0) sh.wq[w] = q;
+    __syncthreads();
+    auto& P = sh.part[ph];
+    if (tid == 0) {
+        BRed<T> t = sh.wq[0];
+        for (int k = 1; k < NW; ++k) t.join(sh.wq[k]);
+        P.q = t;
+    }
+    for (int l = tid; l < nvec; l += NT) {
+        T s = T(0);
+        for (int k = 0; k < NW; ++k) s += sh.wvec[k][l];
+        P.vec[l] = s;
+    }
+    cl.sync();
+    BRed<T> t;
+    if (CS == 1) {
+        t = P.q;
+    } else {
+        if (lane < CS) t = cl.map_shared_rank(&sh.part[ph], lane)->q;
+        else t.init();
+        for (int o = 1; o < CS; o <<= 1) t.shfl_join(o);
+        t.bcast(0);
+    }
+#pragma unroll
+    for (int s = 0; s < KG / 32; ++s) {
+        const int l = lane + 32 * s;
+        T v = T(0);
+        if (l < nvec)
+            for (int k = 0; k < CS; ++k) v += cl.map_shared_rank(&sh.part[ph], k)->vec[l];
+        vout[s] = v;
+    }
+    ph ^= 1;
+    return t;
+}
+
+template <class T, int KERN, int R, int NT>
+__global__ void __launch_bounds__(NT, 512 / NT)
+k_aca_big(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restrict__ order,
+          int64_t nblocks, double thr)
+{
+    namespace cg = cooperative_groups;
+    constexpr int NW = NT / 32;
+    static_assert(R <= 32, "bit masks hold 32 rows per thread");
+    cg::cluster_group cl = cg::this_cluster();
+    const int CS = (int)cl.num_blocks();
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int g = (int)cl.block_rank() * NT + tid, G = CS * NT;
+    const int64_t cid = blockIdx.x / CS, ncl = gridDim.x / CS;
+    __shared__ BigShared<T, NW> sh;
+    const T c = kconst<T>(kp);
+    const T eps0 = (T)a.eps0;
+    const double rtol = a.eps > 0.0 ? a.eps : a.eps0;
+    const double thr2 = thr * thr;
+    int ph = 0;
+
+    for (int64_t qb = cid; qb < nblocks; qb += ncl) {
+        const uint32_t b = order[qb];
+        const Blk B = a.blk[b];
+        const int m = B.m, n = B.n;
+        const int kres = a.kres[b];
+        const int kmax = min(min(kres, KG), min(m, n));
+        if (max(m, n) > R * G) {   // the host routes no such block here
+            if (g == 0) atomicOr(a.status, 2);
+            continue;
+        }
+        T* __restrict__ U = reinterpret_cast<T*>(a.Uptr[b]);
+        T* __restrict__ V = reinterpret_cast<T*>(a.Vptr[b]);
+        // ||S_r||_F^2, the floor and tol^2 / m: thread 0 of each CTA only
+        double S2 = 0.0, floor2 = 0.0, rtol2_m = 0.0;
+        if (tid == 0) {
+            floor2 = a.bset ? (double)m * (double)n / (double)a.set_n[a.bset[b]] : 0.0;
+            rtol2_m = rtol * rtol / (double)m;
+        }
+        T uh[R], rr[R];
+        unsigned used = 0u, seen = (g == 0) ? 1u : 0u;
+        {
+            const Pt<T> p0 = load_pt<T>(X, B.row0);
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                const int jj = g + q * G;
+                rr[q] = jj < n ? phi<KERN>(dist2(p0, load_pt<T>(X, B.col0 + jj)), c) : T(0);
+            }
+        }
+        int r = 0, j = 0, rej = 0, run = 0, iref = 0;
+        bool converged = false;
+        const int limit = kmax + n + 1;
+        T du[KG / 32];
+        for (int it = 0; r < kmax; ++it) {
+            if (it > limit) {
+                if (g == 0) atomicOr(a.status, 1);
+                break;
+            }
+            if (j % G == g) used |= 1u << (j / G);
+            if (w == 0)
+                for (int l = lane; l < r; l += 32) sh.sgv[l] = __ldcg(V + (int64_t)l * n + j);
+            // ---- column pass: u^ = a - sum_l u_l (v_l)_j and a . u_l
+            BRed<T> qc;
+            qc.init();
+            {
+                const Pt<T> pj = load_pt<T>(X, B.col0 + j);
+#pragma unroll
+                for (int q = 0; q < R; ++q) {
+                    const int i = g + q * G;
+                    T v = T(0);
+                    if (i < m) v = phi<KERN>(dist2(load_pt<T>(X, B.row0 + i), pj), c);
+                    qc.x0 = max(qc.x0, fabs(v));
+                    uh[q] = v;
+                }
+            }
+            for (int l0 = 0; l0 < r; l0 += LC) {
+                T sv[LC], p[LC];
+#pragma unroll
+                for (int e = 0; e < LC; ++e) {
+                    sv[e] = (l0 + e < r) ? __ldcg(V + (int64_t)(l0 + e) * n + j) : T(0);
+                    p[e] = T(0);
+                }
+#pragma unroll
+                for (int q = 0; q < R; ++q) {
+                    const int i = g + q * G;
+                    T u[LC];
+#pragma unroll
+                    for (int e = 0; e < LC; ++e)
+                        u[e] = (i < m && l0 + e < r) ? __ldcg(U + (int64_t)(l0 + e) * m + i) : T(0);
+#pragma unroll
+                    for (int e = 0; e < LC; ++e) p[e] = fma(uh[q], u[e], p[e]);
+#pragma unroll
+                    for (int e = 0; e < LC; ++e) uh[q] = fma(-u[e], sv[e], uh[q]);
+                }
+                const T ps = warp_scatter8(p);
+                const int e = (lane >> 2) & 7;
+                if ((lane & 3) == 0 && l0 + e < r) sh.wvec[w][l0 + e] = ps;
+            }
+            bool have_mn = false;
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                const int i = g + q * G;
+                if (i < m) {
+                    qc.take(fabs(uh[q]), uh[q], i);
+                    if (i == iref) qc.pick = uh[q];
+                }
+                const int jj = g + q * G;
+                if (!have_mn && jj < n && !((used >> q) & 1u)) {
+                    qc.mn = jj;
+                    have_mn = true;
+                }
+            }
+            T Pv[KG / 32];
+            const BRed<T> oc = big_reduce<T, NT>(cl, CS, sh, ph, qc, r, Pv);
+            if (!(oc.av > eps0 * oc.x0)) {
+                // column already represented: take the lowest unused column,
+                // or stop after REJ_RUN rejections in a row
+                ++rej;
+                if (++run >= REJ_RUN || oc.mn >= n) {
+                    converged = true;
+                    break;
+                }
+                j = oc.mn;
+                continue;
+            }
+            run = 0;
+            const T piv = oc.aval;
+            const int bi = oc.ai;
+            const T uiref = oc.pick / piv;
+            if (bi % G == g) seen |= 1u << (bi / G);
+            // u_r . u_l = (a . u_l - sum_l' Gu(l, l') (v_l')_j) / piv
+#pragma unroll
+            for (int s = 0; s < KG / 32; ++s) {
+                const int l = lane + 32 * s;
+                T x = T(0);
+                if (l < r) {
+                    x = Pv[s];
+                    for (int l2 = l - l % LC; l2 < r; ++l2)
+                        x = fma(-sh.Gu[l >= l2 ? pk(l, l2) : pk(l2, l)], sh.sgv[l2], x);
+                    x = x / piv;
+                }
+                du[s] = x;
+            }
+            if (w == 0)
+                for (int l = lane; l < r; l += 32) sh.sgu[l] = __ldcg(U + (int64_t)l * m + bi);
+            // ---- u_r = u^ / piv, then the row pass: v = A(i*, :) - sum_l (u_l)_i* v_l
+            BRed<T> qr;
+            qr.init();
+            T* __restrict__ Ur = U + (int64_t)r * m;
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                const int i = g + q * G;
+                if (i < m) {
+                    const T u = uh[q] / piv;
+                    Ur[i] = u;
+                    qr.s0.add(u * u);
+                }
+            }
+            {
+                const Pt<T> pi = load_pt<T>(X, B.row0 + bi);
+#pragma unroll
+                for (int q = 0; q < R; ++q) {
+                    const int jj = g + q * G;
+                    uh[q] = jj < n ? phi<KERN>(dist2(pi, load_pt<T>(X, B.col0 + jj)), c) : T(0);
+                }
+            }
+            for (int l0 = 0; l0 < r; l0 += LC) {
+                T su[LC], p[LC];
+#pragma unroll
+                for (int e = 0; e < LC; ++e) {
+                    su[e] = (l0 + e < r) ? __ldcg(U + (int64_t)(l0 + e) * m + bi) : T(0);
+                    p[e] = T(0);
+                }
+#pragma unroll
+                for (int q = 0; q < R; ++q) {
+                    const int jj = g + q * G;
+                    T v[LC];
+#pragma unroll
+                    for (int e = 0; e < LC; ++e)
+                        v[e] = (jj < n && l0 + e < r) ? __ldcg(V + (int64_t)(l0 + e) * n + jj) : T(0);
+#pragma unroll
+                    for (int e = 0; e < LC; ++e) p[e] = fma(uh[q], v[e], p[e]);
+#pragma unroll
+                    for (int e = 0; e < LC; ++e) uh[q] = fma(-su[e], v[e], uh[q]);
+                }
+                const T ps = warp_scatter8(p);
+                const int e = (lane >> 2) & 7;
+                if ((lane & 3) == 0 && l0 + e < r) sh.wvec[w][l0 + e] = ps;
+            }
+            T* __restrict__ Vr = V + (int64_t)r * n;
+            bool have_mn2 = false;
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                const int jj = g + q * G;
+                if (jj < n) {
+                    const T v = uh[q];
+                    Vr[jj] = v;
+                    qr.s1.add(v * v);
+                    rr[q] = fma(-uiref, v, rr[q]);
+                    const T x = fabs(rr[q]);
+                    qr.x0 = max(qr.x0, x);
+                    if (!((used >> q) & 1u)) qr.take(x, rr[q], jj);
+                }
+                const int i = g + q * G;
+                if (!have_mn2 && i < m && !((seen >> q) & 1u)) {
+                    qr.mn = i;
+                    have_mn2 = true;
+                }
+            }
+            T Qv[KG / 32];
+            const BRed<T> orr = big_reduce<T, NT>(cl, CS, sh, ph, qr, r, Qv);
+            // v_l . v_r = a' . v_l - sum_l' Gv(l, l') (u_l')_i*; cross terms of S2
+            T cr = T(0), dv[KG / 32];
+#pragma unroll
+            for (int s = 0; s < KG / 32; ++s) {
+                const int l = lane + 32 * s;
+                T x = T(0);
+                if (l < r) {
+                    x = Qv[s];
+                    for (int l2 = l - l % LC; l2 < r; ++l2)
+                        x = fma(-sh.Gv[l >= l2 ? pk(l, l2) : pk(l2, l)], sh.sgu[l2], x);
+                }
+                dv[s] = x;
+                cr = fma(du[s], x, cr);
+            }
+            cr = warp_sum(cr);
+            const double nu2 = orr.s0.value(), nv2 = orr.s1.value();
+            if (w == 0) {
+#pragma unroll
+                for (int s = 0; s < KG / 32; ++s) {
+                    const int l = lane + 32 * s;
+                    if (l < r) {
+                        sh.Gu[pk(r, l)] = du[s];
+                        sh.Gv[pk(r, l)] = dv[s];
+                    }
+                }
+                if (lane == 0) {
+                    sh.Gu[pk(r, r)] = (T)nu2;
+                    sh.Gv[pk(r, r)] = (T)nv2;
+                    S2 += 2.0 * (double)cr + nu2 * nv2;
+                    const double S2f = fmax(S2, floor2);
+                    const double rlim2 = rtol2_m * S2f;
+                    sh.rlim2 = rlim2;
+                    sh.resolved = !((double)orr.x0 * (double)orr.x0 > rlim2);
+                    sh.stop_ok = thr >= 0.0 && nu2 * nv2 <= thr2 * S2f;
+                }
+            }
+            __syncthreads();
+            ++r;
+            bool resolved = sh.resolved;
+            const bool stop_ok = sh.stop_ok;
+            int nj = orr.ai;
+            // a resolved reference row moves to the lowest row not seen yet
+            if (resolved && orr.mn < m) {
+                iref = orr.mn;
+                if (iref % G == g) seen |= 1u << (iref / G);
+                const Pt<T> pr = load_pt<T>(X, B.row0 + iref);
+#pragma unroll
+                for (int q = 0; q < R; ++q) {
+                    const int jj = g + q * G;
+                    uh[q] = jj < n ? phi<KERN>(dist2(pr, load_pt<T>(X, B.col0 + jj)), c) : T(0);
+                }
+                for (int l0 = 0; l0 < r; l0 += LC) {
+                    T su[LC];
+#pragma unroll
+                    for (int e = 0; e < LC; ++e)
+                        su[e] = (l0 + e < r) ? __ldcg(U + (int64_t)(l0 + e) * m + iref) : T(0);
+#pragma unroll
+                    for (int q = 0; q < R; ++q) {
+                        const int jj = g + q * G;
+                        T v[LC];
+#pragma unroll
+                        for (int e = 0; e < LC; ++e)
+                            v[e] = (jj < n && l0 + e < r) ? __ldcg(V + (int64_t)(l0 + e) * n + jj) : T(0);
+#pragma unroll
+                        for (int e = 0; e < LC; ++e) uh[q] = fma(-su[e], v[e], uh[q]);
+                    }
+                }
+                BRed<T> qf;
+                qf.init();
+#pragma unroll
+                for (int q = 0; q < R; ++q) {
+                    const int jj = g + q * G;
+                    if (jj < n) {
+                        rr[q] = uh[q];
+                        const T x = fabs(rr[q]);
+                        qf.x0 = max(qf.x0, x);
+                        if (!((used >> q) & 1u)) qf.take(x, rr[q], jj);
+                    }
+                }
+                T dummy[KG / 32];
+                const BRed<T> of = big_reduce<T, NT>(cl, CS, sh, ph, qf, 0, dummy);
+                if (tid == 0) sh.resolved = !((double)of.x0 * (double)of.x0 > sh.rlim2);
+                __syncthreads();
+                resolved = sh.resolved;
+                nj = of.ai;
+            }
+            if (stop_ok && resolved) {
+                converged = true;
+                break;
+            }
+            if (r >= kmax) break;
+            if (nj >= n) {
+                converged = true;
+                break;
+            }
+            j = nj;
+        }
+        if (g == 0) {
+            a.rank[b] = r;
+            a.nrej[b] = rej;
+            const int full = min(a.k_cap, min(m, n));
+            int f = 0;
+            if (!converged && r >= kmax) f |= (kres < full) ? 1 : 2;
+            a.flags[b] = f;
+        }
+        cl.sync();
+    }
+}
+
+template <class R, int KERN>
+void launch_cluster(const KernelParams& kp, const DeviceCoords& X, const AcaArgs& a,
+                    const uint32_t* order, int64_t n, int cs, int64_t dim, double thr,
+                    cudaStream_t s)
+{
+    int occ = 0;
+    HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_aca_cluster<R, KERN>, CTA_NT, 0));
+    int64_t nclusters = std::min<int64_t>(n, std::max<int64_t>(1, (int64_t)std::max(occ, 1) *
+                                                                     num_sms() / cs));
+    const int64_t words = ceil_div(dim, 32);
+    DevBuf<uint32_t> usedpool((size_t)(nclusters * words), s);
+    DevBuf<uint32_t> seenpool((size_t)(nclusters * words), s);
+    DevBuf<R> rrpool((size_t)(nclusters * dim), s);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(nclusters * cs));
+    cfg.blockDim = dim3(CTA_NT);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    HM_CUDA(cudaLaunchKernelEx(&cfg, k_aca_cluster<R, KERN>, kp, X, a, order, n, thr, usedpool.p,
+                               seenpool.p, rrpool.p, words, dim));
+    note_launch();
+}
+
+// One CTA (cs = 1) or one cluster of cs CTAs per block, as many as fit at once.
+template <class R, int KERN, int RR, int NT>
+void launch_big(const KernelParams& kp, const DeviceCoords& X, const AcaArgs& a,
+                const uint32_t* order, int64_t n, int cs, double thr, cudaStream_t s)
+{
+    auto kern = k_aca_big<R, KERN, RR, NT>;
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int64_t fit = 0;
+    if (cs == 1) {
+        int occ = 0;
+        HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, 0));
+        fit = (int64_t)std::max(occ, 1) * num_sms();
+    } else {
+        cfg.gridDim = dim3((unsigned)cs);
+        int ncl = 0;
+        HM_CUDA(cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg));
+        fit = std::max(ncl, 1);
+    }
+    const int64_t nclusters = std::min<int64_t>(n, fit);
+    cfg.gridDim = dim3((unsigned)(nclusters * cs));
+    HM_CUDA(cudaLaunchKernelEx(&cfg, kern, kp, X, a, order, n, thr));
+    note_launch();
+}
+
 template <class R, int KERN>
 void launch_all(const KernelParams& kp, const DeviceCoords& X, const AcaArgs& a,
                 const uint32_t* order, int64_t n, int cls, int64_t max_n, cudaStream_t s)
 {
     const double thr = (a.eps > 0.0) ? a.eps * (1.0 - a.aca_eta) / (1.0 + a.eps) : -1.0;
     const unsigned wgrid = (unsigned)ceil_div(n * 32, WARP_NT);
+    const int64_t dim = std::min<int64_t>(cls == ACA_NCLASS - 1 ? max_n : aca_class_dim(cls), max_n);
+    if (cls >= 4 && cls < ACA_NCLASS - 1 && a.k_cap > KG) {
+        // ranks above the Gram matrices' size: residuals in global scratch
+        launch_cluster<R, KERN>(kp, X, a, order, n, dim <= 4096 ? 1 : dim <= 32768 ? 4 : 8, dim,
+                                thr, s);
+        HM_LAUNCH("aca");
+        return;
+    }
     switch (cls) {
     case 0: k_aca_warp<R, KERN, 2><<<wgrid, WARP_NT, 0, s>>>(kp, X, a, order, n, thr); note_launch(); break;
     case 1: k_aca_warp<R, KERN, 4><<<wgrid, WARP_NT, 0, s>>>(kp, X, a, order, n, thr); note_launch(); break;
     case 2: k_aca_warp<R, KERN, 8><<<wgrid, WARP_NT, 0, s>>>(kp, X, a, order, n, thr); note_launch(); break;
     case 3: k_aca_warp<R, KERN, 16><<<wgrid, WARP_NT, 0, s>>>(kp, X, a, order, n, thr); note_launch(); break;
-    default: {
-        const int cs = cls == 4 ? 1 : (cls == 5 ? 4 : 8);
-        const int64_t dim = std::min<int64_t>(cls == 6 ? max_n : kAcaClassDim[cls], max_n);
-        int occ = 0;
-        HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_aca_cluster<R, KERN>,
-                                                              CTA_NT, 0));
-        int64_t nclusters = std::min<int64_t>(n, std::max<int64_t>(1, (int64_t)std::max(occ, 1) *
-                                                                         num_sms() / cs));
-        const int64_t words = ceil_div(dim, 32);
-        DevBuf<uint32_t> usedpool((size_t)(nclusters * words), s);
-        DevBuf<uint32_t> seenpool((size_t)(nclusters * words), s);
-        DevBuf<R> rrpool((size_t)(nclusters * dim), s);
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)(nclusters * cs));
-        cfg.blockDim = dim3(CTA_NT);
-        cfg.dynamicSmemBytes = 0;
-        cfg.stream = s;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = cs;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        HM_CUDA(cudaLaunchKernelEx(&cfg, k_aca_cluster<R, KERN>, kp, X, a, order, n, thr,
-                                   usedpool.p, seenpool.p, rrpool.p, words, dim));
-        note_launch();
-        break;
-    }
+    case 4: launch_big<R, KERN, 8, 128>(kp, X, a, order, n, 1, thr, s); break;     // <= 1024
+    case 5: launch_big<R, KERN, 8, 256>(kp, X, a, order, n, 1, thr, s); break;     // <= 2048
+    case 6: launch_big<R, KERN, 8, 512>(kp, X, a, order, n, 1, thr, s); break;     // <= 4096
+    case 7: launch_big<R, KERN, 8, 512>(kp, X, a, order, n, 2, thr, s); break;     // <= 8192
+    case 8: launch_big<R, KERN, 8, 512>(kp, X, a, order, n, 4, thr, s); break;     // <= 16384
+    case 9: launch_big<R, KERN, 8, 512>(kp, X, a, order, n, 8, thr, s); break;     // <= 32768
+    case 10: launch_big<R, KERN, 16, 512>(kp, X, a, order, n, 8, thr, s); break;   // <= 65536
+    default: launch_cluster<R, KERN>(kp, X, a, order, n, 8, dim, thr, s); break;
     }
     HM_LAUNCH("aca");
 }
@@ -871,12 +1424,5 @@ void aca_run(int precision, const KernelParams& kp, const DeviceCoords& X, const
     }
 }
 
-int aca_class_of(int m, int n)
-{
-    const int d = m > n ? m : n;
-    for (int c = 0; c < ACA_NCLASS - 1; ++c)
-        if (d <= kAcaClassDim[c]) return c;
-    return ACA_NCLASS - 1;
-}
 
 }  // namespace hm

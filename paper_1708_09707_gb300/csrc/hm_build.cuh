@@ -54,12 +54,21 @@ struct AcaArgs {
     const int64_t* set_n;    // per set: number of points
 };
 
-// Size classes of admissible blocks by max(m, n): classes 0-3 (<= 64, 128,
-// 256, 512) run one warp per block, class 4 (<= 4096) one CTA per block,
-// class 5 (<= 32768) a cluster of 4 CTAs and class 6 a cluster of 8 CTAs.
-constexpr int ACA_NCLASS = 7;
-constexpr int kAcaClassDim[ACA_NCLASS - 1] = {64, 128, 256, 512, 4096, 32768};
-int aca_class_of(int m, int n);
+// Size classes of admissible blocks by d = max(m, n): class c holds the
+// blocks with 2^(c+5) < d <= 2^(c+6) (class 0: d <= 64, the last class: all
+// larger blocks). Classes 0-3 (d <= 512) run one warp per block, classes 4-10
+// (d <= 65536) one CTA or one thread-block cluster per block with the block's
+// residuals in registers, class 11 a cluster of 8 CTAs with its residuals in
+// global scratch.
+constexpr int ACA_NCLASS = 12;
+__host__ __device__ __forceinline__ int aca_class_dim(int c) { return 64 << c; }
+__host__ __device__ __forceinline__ int aca_class_of(int m, int n)
+{
+    const int d = m > n ? m : n;
+    int c = 0;
+    while (c < ACA_NCLASS - 1 && d > aca_class_dim(c)) ++c;
+    return c;
+}
 
 // Run ACA on the blocks listed in order[0..n) (indices into the block arrays),
 // all of size class cls; max_n bounds the column count of any block.

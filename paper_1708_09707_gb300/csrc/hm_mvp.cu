@@ -82,7 +82,6 @@ k_vtx(const Blk* __restrict__ blk, const int32_t* __restrict__ rank,
         if (lane == 0) out[l] = s;
     }
 }
-
 // Sum the partials of blocks that span several column chunks (fixed order).
 template <class R>
 __global__ void k_tsum(const int32_t* __restrict__ multi, int64_t nmulti,
@@ -499,9 +498,25 @@ __global__ void k_relayout_u(const int2* __restrict__ ent, const int32_t* __rest
     const LrDesc d = desc[w];
     const R* src = reinterpret_cast<const R*>(Uptr[en.x]) + en.y;
     R* out = dst + d.uoff;
-    for (int l = 0; l < d.k; ++l)
-        for (int i = lane; i < ld; i += 32)
-            out[(int64_t)l * ld + i] = i < rows ? src[(int64_t)l * m + i] : R(0);
+    // 64 rows x 4 columns per round: eight loads in flight per lane
+    for (int i0 = 0; i0 < ld; i0 += 64)
+        for (int l0 = 0; l0 < d.k; l0 += 4) {
+            R v[4][2];
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int i = i0 + lane + 32 * h, l = l0 + e;
+                    v[e][h] = (l < d.k && i < rows) ? src[(int64_t)l * m + i] : R(0);
+                }
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int i = i0 + lane + 32 * h, l = l0 + e;
+                    if (l < d.k && i < ld) out[(int64_t)l * ld + i] = v[e][h];
+                }
+        }
 }
 
 __global__ void k_vitems_count(const Blk* __restrict__ blk, const int32_t* __restrict__ rank,

@@ -13,6 +13,11 @@ namespace {
 
 constexpr int NT = 128;
 
+// One CTA per slice. Thread t owns the row pair (2p, 2p + 1), p = t mod
+// (ld / 2), keeps both row points in registers and walks the columns
+// t / (ld / 2), stepping by NT / (ld / 2); a warp thus covers consecutive row
+// pairs of one column and stores them as one contiguous vector line. Slices
+// taller than 2 NT rows are done in row passes of 2 NT.
 template <int KERN, int FMT>
 __global__ void __launch_bounds__(NT)
 k_near(KernelParams kp, DeviceCoords X, const Blk* __restrict__ blk, const int2* __restrict__ ent,
@@ -26,26 +31,53 @@ k_near(KernelParams kp, DeviceCoords X, const Blk* __restrict__ blk, const int2*
     const int rows = tile_m[etile[e]];
     const int ld = rows + (rows & 1);   // even leading dimension (zero pad row)
     const int64_t r0 = B.row0 + en.y;
-    const int64_t mn = (int64_t)ld * B.n;
+    const int n = B.n;
+    const int64_t mn = (int64_t)ld * n;
     const int64_t o = desc[e].noff;
-    for (int64_t q = threadIdx.x; q < mn; q += NT) {
-        const int i = (int)(q % ld), j = (int)(q / ld);
-        const bool pad = i >= rows;
+    for (int pr0 = 0; pr0 < ld / 2; pr0 += NT) {
+        const int npair = min(NT, ld / 2 - pr0);
+        const int cstep = NT / npair;
+        const int t = threadIdx.x;
+        if (t >= cstep * npair) continue;
+        const int i = 2 * (pr0 + t % npair);      // first row of the pair
+        const bool v0 = i < rows, v1 = i + 1 < rows;
+        // the pair's points (a padding row repeats the last real row)
+        const int64_t ra = r0 + i, rb = r0 + (v1 ? i + 1 : i);
+        Pt<double> pa64, pb64;
+        Pt<float> pa32, pb32;
         if (FMT == HM_NEAR_FP64) {
-            double v = pad ? 0.0 : phi<KERN>(dist2(load_pt64(X, r0 + i), load_pt64(X, B.col0 + j)), kp.c64);
-            static_cast<double*>(store)[o + q] = v;
+            pa64 = load_pt64(X, ra);
+            pb64 = load_pt64(X, rb);
         } else {
-            // float kernel evaluation from the hi/lo coordinate split
-            float v = pad ? 0.f : phi<KERN>(dist2(load_pt32(X, r0 + i), load_pt32(X, B.col0 + j)), kp.c32);
-            if (FMT == HM_NEAR_FP32) {
-                static_cast<float*>(store)[o + q] = v;
-            } else if (FMT == HM_NEAR_BF16X2) {
-                __nv_bfloat16* S = static_cast<__nv_bfloat16*>(store) + 2 * o;
-                __nv_bfloat16 h = __float2bfloat16_rn(v);
-                S[q] = h;
-                S[mn + q] = __float2bfloat16_rn(v - __bfloat162float(h));
+            pa32 = load_pt32(X, ra);
+            pb32 = load_pt32(X, rb);
+        }
+        for (int j = t / npair; j < n; j += cstep) {
+            const int64_t q = (int64_t)j * ld + i;
+            if (FMT == HM_NEAR_FP64) {
+                const Pt<double> pc = load_pt64(X, B.col0 + j);
+                double2 v;
+                v.x = v0 ? phi<KERN>(dist2(pa64, pc), kp.c64) : 0.0;
+                v.y = v1 ? phi<KERN>(dist2(pb64, pc), kp.c64) : 0.0;
+                *reinterpret_cast<double2*>(static_cast<double*>(store) + o + q) = v;
             } else {
-                static_cast<__nv_bfloat16*>(store)[o + q] = __float2bfloat16_rn(v);
+                // float kernel evaluation from the hi/lo coordinate split
+                const Pt<float> pc = load_pt32(X, B.col0 + j);
+                const float a = v0 ? phi<KERN>(dist2(pa32, pc), kp.c32) : 0.f;
+                const float b = v1 ? phi<KERN>(dist2(pb32, pc), kp.c32) : 0.f;
+                if (FMT == HM_NEAR_FP32) {
+                    *reinterpret_cast<float2*>(static_cast<float*>(store) + o + q) = make_float2(a, b);
+                } else if (FMT == HM_NEAR_BF16X2) {
+                    __nv_bfloat16* S = static_cast<__nv_bfloat16*>(store) + 2 * o;
+                    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+                    const float2 hf = __bfloat1622float2(h);
+                    *reinterpret_cast<__nv_bfloat162*>(S + q) = h;
+                    *reinterpret_cast<__nv_bfloat162*>(S + mn + q) =
+                        __floats2bfloat162_rn(a - hf.x, b - hf.y);
+                } else {
+                    *reinterpret_cast<__nv_bfloat162*>(static_cast<__nv_bfloat16*>(store) + o + q) =
+                        __floats2bfloat162_rn(a, b);
+                }
             }
         }
     }

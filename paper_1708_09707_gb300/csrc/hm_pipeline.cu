@@ -91,14 +91,6 @@ __global__ void k_leaf_tiles(const uint32_t* __restrict__ val, const int32_t* __
     tm[q] = hi[v] - lo[v];
 }
 
-// size class of an admissible block (the thresholds of kAcaClassDim)
-__device__ __forceinline__ int size_class(int m, int n)
-{
-    int d = max(m, n);
-    return d <= 64 ? 0 : d <= 128 ? 1 : d <= 256 ? 2 : d <= 512 ? 3 : d <= 4096 ? 4
-         : d <= 32768 ? 5 : 6;
-}
-
 __global__ void k_classes(const Blk* __restrict__ blk, const uint32_t* __restrict__ ids,
                           int64_t n, int kcap, const int32_t* __restrict__ kpred,
                           uint64_t* __restrict__ key, uint32_t* __restrict__ val,
@@ -108,7 +100,7 @@ __global__ void k_classes(const Blk* __restrict__ blk, const uint32_t* __restric
     if (q >= n) return;
     const uint32_t b = ids ? ids[q] : (uint32_t)q;
     Blk B = blk[b];
-    int c = size_class(B.m, B.n);
+    int c = aca_class_of(B.m, B.n);
     key[q] = (uint64_t)(ACA_NCLASS - 1 - c);   // largest class first
     val[q] = b;
     int full = min(kcap, min(B.m, B.n));
@@ -328,7 +320,7 @@ void compress(hm_handle_s& h, const uint32_t* ids, int64_t n, const int32_t* kpr
     k_classes<<<grid_for(n), NT, 0, s>>>(h.ablk.p, ids, n, h.opt.k_cap, kpred, key.p, order.p,
                                          h.kres.p, ccount.p); note_launch();
     HM_LAUNCH("classes");
-    radix_sort_u64_u32(key.p, order.p, n, 3, s);
+    radix_sort_u64_u32(key.p, order.p, n, bits_for(ACA_NCLASS), s);
     int64_t cc[ACA_NCLASS];
     HM_CUDA(cudaMemcpyAsync(cc, ccount.p, sizeof(cc), cudaMemcpyDeviceToHost, s));
     DevBuf<int64_t> res(n, s), pre(n + 1, s), resu(n, s), preu(n + 1, s);
