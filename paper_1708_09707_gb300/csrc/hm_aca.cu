@@ -43,6 +43,77 @@ constexpr int CTA_WARPS = CTA_NT / 32;
 constexpr int KBUF = 128;      // largest supported k_cap
 constexpr int REJ_RUN = 4;     // rejected columns in a row that end a block
 constexpr int UNR = 4;         // rows (columns) per thread whose loads are issued together
+constexpr int LC = 4;          // ranks per batch of loads and dot products
+
+// Warp sums of LC per-lane values (a reduce-scatter butterfly): afterwards
+// the lanes L with scatter_elem(L) == e hold the total of value e, and lane
+// scatter_writer(e) is the first of them.
+template <class T>
+__device__ __forceinline__ T warp_scatter(const T (&p)[LC])
+{
+    static_assert(LC == 4, "reduce-scatter of four values");
+    const int lane = threadIdx.x & 31;
+    const bool h16 = lane & 16, h8 = lane & 8;
+    T a2[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const T send = h16 ? p[e] : p[e + 2];
+        const T keep = h16 ? p[e + 2] : p[e];
+        a2[e] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+    T a1 = (h8 ? a2[1] : a2[0]) + __shfl_xor_sync(0xffffffffu, h8 ? a2[0] : a2[1], 8);
+    a1 += __shfl_xor_sync(0xffffffffu, a1, 4);
+    a1 += __shfl_xor_sync(0xffffffffu, a1, 2);
+    a1 += __shfl_xor_sync(0xffffffffu, a1, 1);
+    return a1;
+}
+__device__ __forceinline__ int scatter_elem(int lane) { return (lane >> 3) & 3; }
+__device__ __forceinline__ bool scatter_writer(int lane) { return (lane & 7) == 0; }
+
+// The stopping rule of one ACA step, kept in double: ||S_r||_F^2 += 2 cross +
+// |u_r|^2 |v_r|^2, then the rule |u_r|^2 |v_r|^2 <= thr^2 S2 and the
+// reference-row limit rmax^2 <= tol^2 S2 / m, with S2 floored at floor2. In
+// the float kernels the step's terms are formed in float and widened once, so
+// a step costs nine double-pipe instructions, which matters on this GPU
+// where the double pipe runs at a small fraction of the float rate.
+struct StopState {
+    double S2 = 0.0, floor2 = 0.0, rtol2_m = 0.0, thr2 = 0.0, rlim2 = 0.0;
+    bool fixed_rank = false;
+};
+
+__device__ __forceinline__ void stop_step(StopState& st, const TSum<double>& nu2,
+                                          const TSum<double>& nv2, double cross, double rmax,
+                                          bool& resolved, bool& stop_ok)
+{
+    const double p = nu2.value() * nv2.value();
+    st.S2 += 2.0 * cross + p;
+    const double S2f = fmax(st.S2, st.floor2);
+    st.rlim2 = st.rtol2_m * S2f;
+    resolved = !(rmax * rmax > st.rlim2);
+    stop_ok = !st.fixed_rank && p <= st.thr2 * S2f;
+}
+
+__device__ __forceinline__ void stop_step(StopState& st, const TSum<float>& nu2,
+                                          const TSum<float>& nv2, float cross, float rmax,
+                                          bool& resolved, bool& stop_ok)
+{
+    const float p = nu2.rvalue() * nv2.rvalue();
+    st.S2 += (double)fmaf(2.f, cross, p);
+    const double S2f = fmax(st.S2, st.floor2);
+    st.rlim2 = st.rtol2_m * S2f;
+    resolved = !((double)(rmax * rmax) > st.rlim2);
+    stop_ok = !st.fixed_rank && (double)p <= st.thr2 * S2f;
+}
+
+// The reference-row limit alone (after the reference row moved).
+__device__ __forceinline__ bool ref_resolved(const StopState& st, double rmax)
+{
+    return !(rmax * rmax > st.rlim2);
+}
+__device__ __forceinline__ bool ref_resolved(const StopState& st, float rmax)
+{
+    return !((double)(rmax * rmax) > st.rlim2);
+}
 
 // --------------------------------------------------------------------------
 // One warp per block (m, n <= 32 MAXR). Lane l owns rows and columns
@@ -51,7 +122,7 @@ constexpr int UNR = 4;         // rows (columns) per thread whose loads are issu
 // bit masks per lane.
 // --------------------------------------------------------------------------
 template <class R, int KERN, int MAXR>
-__global__ void __launch_bounds__(WARP_NT)
+__global__ void __launch_bounds__(WARP_NT, MAXR <= 2 ? 8 : (MAXR <= 4 ? 6 : 4))
 k_aca_warp(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restrict__ order,
            int64_t nblocks, double thr)
 {
@@ -69,15 +140,19 @@ k_aca_warp(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restric
     const R eps0 = (R)a.eps0;
     const double rtol = a.eps > 0.0 ? a.eps : a.eps0;
     const double floor2 = a.bset ? (double)m * (double)n / (double)a.set_n[a.bset[b]] : 0.0;
-    // both tests in squared form (no division or square root per step)
-    const double rtol2_m = rtol * rtol / (double)m, thr2 = thr * thr;
 
+    // ranks whose loads are issued together
+    constexpr int WB = MAXR <= 4 ? 4 : (MAXR <= 8 ? 2 : 1);
     R acc[MAXR], vv[MAXR];
     Resid<R> res[MAXR], rr[MAXR];   // rr: reference-row residual
     unsigned used = 0, seen = (lane == 0) ? 1u : 0u;
     int r = 0, j = 0, rej = 0, run = 0, iref = 0;
     bool converged = false;
-    double S2 = 0.0;
+    StopState st;
+    st.floor2 = floor2;
+    st.rtol2_m = rtol * rtol / (double)m;
+    st.thr2 = thr * thr;
+    st.fixed_rank = !(thr >= 0.0);
     const int limit = kmax + n + 1;
 
     // reference row 0
@@ -112,14 +187,22 @@ k_aca_warp(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restric
         for (int l0 = 0; l0 < r; l0 += 32) {
             const R vjc = (l0 + lane < r) ? V[(int64_t)(l0 + lane) * n + j] : R(0);
             const int lend = min(r - l0, 32);
-            for (int l = 0; l < lend; ++l) {
-                const R vjl = __shfl_sync(0xffffffffu, vjc, l);
-                const R* Ul = U + (int64_t)(l0 + l) * m;
+            for (int l = 0; l < lend; l += WB) {
+                R sv[WB], uv[WB][MAXR];
 #pragma unroll
-                for (int t = 0; t < MAXR; ++t) {
-                    const int i = lane + 32 * t;
-                    if (i < m) res[t].sub(Ul[i], vjl);
+                for (int e = 0; e < WB; ++e) {
+                    sv[e] = __shfl_sync(0xffffffffu, vjc, (l + e) & 31);
+                    const R* Ul = U + (int64_t)(l0 + l + e) * m;
+#pragma unroll
+                    for (int t = 0; t < MAXR; ++t) {
+                        const int i = lane + 32 * t;
+                        uv[e][t] = (i < m && l + e < lend) ? Ul[i] : R(0);
+                    }
                 }
+#pragma unroll
+                for (int e = 0; e < WB; ++e)
+#pragma unroll
+                    for (int t = 0; t < MAXR; ++t) res[t].sub(uv[e][t], sv[e]);
             }
         }
         R best = -1;
@@ -191,14 +274,22 @@ k_aca_warp(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restric
         for (int l0 = 0; l0 < r; l0 += 32) {
             const R uic = (l0 + lane < r) ? U[(int64_t)(l0 + lane) * m + bi] : R(0);
             const int lend = min(r - l0, 32);
-            for (int l = 0; l < lend; ++l) {
-                const R uil = __shfl_sync(0xffffffffu, uic, l);
-                const R* Vl = V + (int64_t)(l0 + l) * n;
+            for (int l = 0; l < lend; l += WB) {
+                R su[WB], vv[WB][MAXR];
 #pragma unroll
-                for (int t = 0; t < MAXR; ++t) {
-                    const int jj = lane + 32 * t;
-                    if (jj < n) res[t].sub(uil, Vl[jj]);
+                for (int e = 0; e < WB; ++e) {
+                    su[e] = __shfl_sync(0xffffffffu, uic, (l + e) & 31);
+                    const R* Vl = V + (int64_t)(l0 + l + e) * n;
+#pragma unroll
+                    for (int t = 0; t < MAXR; ++t) {
+                        const int jj = lane + 32 * t;
+                        vv[e][t] = (jj < n && l + e < lend) ? Vl[jj] : R(0);
+                    }
                 }
+#pragma unroll
+                for (int e = 0; e < WB; ++e)
+#pragma unroll
+                    for (int t = 0; t < MAXR; ++t) res[t].sub(su[e], vv[e][t]);
             }
         }
         R* __restrict__ Vr = V + (int64_t)r * n;
@@ -223,32 +314,41 @@ k_aca_warp(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restric
             tu.shfl_join(o);
             tv.shfl_join(o);
         }
-        const double nu2 = tu.value(), nv2 = tv.value();
         rmax = warp_max(rmax);
         // cross terms (u_r . u_l)(v_l . v_r), reduced and summed in R
+        // (LC ranks at a time, one reduce-scatter per side; the writer lane
+        // of rank l0 + e keeps its products, the lanes' sums join at the end)
         TSum<R> tc;
         tc.init();
-        for (int l = 0; l < r; ++l) {
-            const R* Ul = U + (int64_t)l * m;
-            const R* Vl = V + (int64_t)l * n;
-            R du = 0, dv = 0;
+        for (int l0 = 0; l0 < r; l0 += LC) {
+            R pu[LC], pv[LC];
 #pragma unroll
-            for (int t = 0; t < MAXR; ++t) {
-                const int i = lane + 32 * t;
-                if (i < m) du += acc[t] * Ul[i];
-                if (i < n) dv += Vl[i] * vv[t];
+            for (int e = 0; e < LC; ++e) {
+                const R* Ul = U + (int64_t)(l0 + e) * m;
+                const R* Vl = V + (int64_t)(l0 + e) * n;
+                R du = 0, dv = 0;
+#pragma unroll
+                for (int t = 0; t < MAXR; ++t) {
+                    const int i = lane + 32 * t;
+                    const R ul = (i < m && l0 + e < r) ? Ul[i] : R(0);
+                    const R vl = (i < n && l0 + e < r) ? Vl[i] : R(0);
+                    du = fma(acc[t], ul, du);
+                    dv = fma(vl, vv[t], dv);
+                }
+                pu[e] = du;
+                pv[e] = dv;
             }
-            const R ddu = warp_sum(du);
-            const R ddv = warp_sum(dv);
-            tc.add(ddu * ddv);
+            const R su = warp_scatter(pu), sv = warp_scatter(pv);
+            if (scatter_writer(lane) && l0 + scatter_elem(lane) < r) tc.add(su * sv);
         }
-        S2 += 2.0 * tc.value() + nu2 * nv2;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) tc.shfl_join(o);
+        bool resolved, stop_ok;
+        stop_step(st, tu, tv, tc.rvalue(), rmax, resolved, stop_ok);
         ++r;
         // a resolved reference row (max |residual| <= tol sqrt(S2 / m)) moves
         // to the lowest row not seen yet
-        const double S2f = fmax(S2, floor2);
-        const double rlim2 = rtol2_m * S2f;
-        if (!((double)rmax * (double)rmax > rlim2)) {
+        if (resolved) {
             int cand = 0x7fffffff;
 #pragma unroll
             for (int t = 0; t < MAXR; ++t) {
@@ -272,14 +372,22 @@ k_aca_warp(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restric
                 for (int l0 = 0; l0 < r; l0 += 32) {
                     const R uic = (l0 + lane < r) ? U[(int64_t)(l0 + lane) * m + iref] : R(0);
                     const int lend = min(r - l0, 32);
-                    for (int l = 0; l < lend; ++l) {
-                        const R uil = __shfl_sync(0xffffffffu, uic, l);
-                        const R* Vl = V + (int64_t)(l0 + l) * n;
+                    for (int l = 0; l < lend; l += WB) {
+                        R su[WB], vv[WB][MAXR];
 #pragma unroll
-                        for (int t = 0; t < MAXR; ++t) {
-                            const int jj = lane + 32 * t;
-                            if (jj < n) res[t].sub(uil, Vl[jj]);
+                        for (int e = 0; e < WB; ++e) {
+                            su[e] = __shfl_sync(0xffffffffu, uic, (l + e) & 31);
+                            const R* Vl = V + (int64_t)(l0 + l + e) * n;
+#pragma unroll
+                            for (int t = 0; t < MAXR; ++t) {
+                                const int jj = lane + 32 * t;
+                                vv[e][t] = (jj < n && l + e < lend) ? Vl[jj] : R(0);
+                            }
                         }
+#pragma unroll
+                        for (int e = 0; e < WB; ++e)
+#pragma unroll
+                            for (int t = 0; t < MAXR; ++t) res[t].sub(su[e], vv[e][t]);
                     }
                 }
                 rmax = 0;
@@ -289,9 +397,10 @@ k_aca_warp(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restric
                     if (lane + 32 * t < n) rmax = max(rmax, fabs(rr[t].value()));
                 }
                 rmax = warp_max(rmax);
+                resolved = ref_resolved(st, rmax);
             }
         }
-        if (thr >= 0.0 && nu2 * nv2 <= thr2 * S2f && !((double)rmax * (double)rmax > rlim2)) {
+        if (stop_ok && resolved) {
             converged = true;
             break;
         }
@@ -831,7 +940,6 @@ k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __rest
 // --------------------------------------------------------------------------
 constexpr int KG = 64;                       // largest rank of k_aca_big
 constexpr int KGP = KG * (KG + 1) / 2;       // packed lower triangle
-constexpr int LC = 8;                        // ranks per batch of loads
 
 __device__ __forceinline__ int pk(int a, int b)   // a >= b
 {
@@ -913,36 +1021,9 @@ struct BigShared {
         BRed<T> q;
         T vec[KG];
     } part[2];                   // per-CTA partials, read by the whole cluster
-    double rlim2;                // decisions of thread 0
-    int resolved, stop_ok;
+    int resolved, stop_ok;       // decisions of thread 0
 };
 
-// Warp sums of eight per-lane values: lanes 4e .. 4e+3 receive the total of
-// value e (a reduce-scatter butterfly, nine shuffles in all).
-template <class T>
-__device__ __forceinline__ T warp_scatter8(const T (&p)[LC])
-{
-    const int lane = threadIdx.x & 31;
-    const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
-    T a4[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        const T send = h16 ? p[e] : p[e + 4];
-        const T keep = h16 ? p[e + 4] : p[e];
-        a4[e] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-    }
-    T a2[2];
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-        const T send = h8 ? a4[e] : a4[e + 2];
-        const T keep = h8 ? a4[e + 2] : a4[e];
-        a2[e] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-    }
-    T a1 = (h4 ? a2[1] : a2[0]) + __shfl_xor_sync(0xffffffffu, h4 ? a2[0] : a2[1], 4);
-    a1 += __shfl_xor_sync(0xffffffffu, a1, 2);
-    a1 += __shfl_xor_sync(0xffffffffu, a1, 1);
-    return a1;
-}
 
 // Cluster-wide reduction of q and of the first nvec entries of the per-warp
 // vectors sh.wvec. Every thread receives the scalar result; lane L of every
@@ -951,8 +1032,8 @@ __device__ __forceinline__ T warp_scatter8(const T (&p)[LC])
 // writes the other buffer, and the one after that only once every CTA has
 // passed the cluster barrier in between.
 template <class T, int NT, class CL>
-__device__ __forceinline__ BRed<T> big_reduce(CL& cl, int CS, BigShared<T, NT / 32>& sh, int& ph,
-                                              BRed<T> q, int nvec, T (&vout)[KG / 32])
+__device__ __noinline__ BRed<T> big_reduce(CL& cl, int CS, BigShared<T, NT / 32>& sh, int& ph,
+                                           BRed<T> q, int nvec, T (&vout)[KG / 32])
 {
     constexpr int NW = NT / 32;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -1025,11 +1106,13 @@ k_aca_big(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restrict
         }
         T* __restrict__ U = reinterpret_cast<T*>(a.Uptr[b]);
         T* __restrict__ V = reinterpret_cast<T*>(a.Vptr[b]);
-        // ||S_r||_F^2, the floor and tol^2 / m: thread 0 of each CTA only
-        double S2 = 0.0, floor2 = 0.0, rtol2_m = 0.0;
+        // ||S_r||_F^2 and the limits of the tests: thread 0 of each CTA only
+        StopState st;
         if (tid == 0) {
-            floor2 = a.bset ? (double)m * (double)n / (double)a.set_n[a.bset[b]] : 0.0;
-            rtol2_m = rtol * rtol / (double)m;
+            st.floor2 = a.bset ? (double)m * (double)n / (double)a.set_n[a.bset[b]] : 0.0;
+            st.rtol2_m = rtol * rtol / (double)m;
+            st.thr2 = thr2;
+            st.fixed_rank = !(thr >= 0.0);
         }
         T uh[R], rr[R];
         unsigned used = 0u, seen = (g == 0) ? 1u : 0u;
@@ -1086,9 +1169,9 @@ k_aca_big(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restrict
 #pragma unroll
                     for (int e = 0; e < LC; ++e) uh[q] = fma(-u[e], sv[e], uh[q]);
                 }
-                const T ps = warp_scatter8(p);
-                const int e = (lane >> 2) & 7;
-                if ((lane & 3) == 0 && l0 + e < r) sh.wvec[w][l0 + e] = ps;
+                const T ps = warp_scatter(p);
+                const int e = scatter_elem(lane);
+                if (scatter_writer(lane) && l0 + e < r) sh.wvec[w][l0 + e] = ps;
             }
             bool have_mn = false;
 #pragma unroll
@@ -1177,9 +1260,9 @@ k_aca_big(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restrict
 #pragma unroll
                     for (int e = 0; e < LC; ++e) uh[q] = fma(-su[e], v[e], uh[q]);
                 }
-                const T ps = warp_scatter8(p);
-                const int e = (lane >> 2) & 7;
-                if ((lane & 3) == 0 && l0 + e < r) sh.wvec[w][l0 + e] = ps;
+                const T ps = warp_scatter(p);
+                const int e = scatter_elem(lane);
+                if (scatter_writer(lane) && l0 + e < r) sh.wvec[w][l0 + e] = ps;
             }
             T* __restrict__ Vr = V + (int64_t)r * n;
             bool have_mn2 = false;
@@ -1217,9 +1300,8 @@ k_aca_big(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restrict
                 dv[s] = x;
                 cr = fma(du[s], x, cr);
             }
-            cr = warp_sum(cr);
-            const double nu2 = orr.s0.value(), nv2 = orr.s1.value();
             if (w == 0) {
+                cr = warp_sum(cr);
 #pragma unroll
                 for (int s = 0; s < KG / 32; ++s) {
                     const int l = lane + 32 * s;
@@ -1229,14 +1311,12 @@ k_aca_big(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restrict
                     }
                 }
                 if (lane == 0) {
-                    sh.Gu[pk(r, r)] = (T)nu2;
-                    sh.Gv[pk(r, r)] = (T)nv2;
-                    S2 += 2.0 * (double)cr + nu2 * nv2;
-                    const double S2f = fmax(S2, floor2);
-                    const double rlim2 = rtol2_m * S2f;
-                    sh.rlim2 = rlim2;
-                    sh.resolved = !((double)orr.x0 * (double)orr.x0 > rlim2);
-                    sh.stop_ok = thr >= 0.0 && nu2 * nv2 <= thr2 * S2f;
+                    sh.Gu[pk(r, r)] = orr.s0.rvalue();
+                    sh.Gv[pk(r, r)] = orr.s1.rvalue();
+                    bool res, stp;
+                    stop_step(st, orr.s0, orr.s1, cr, orr.x0, res, stp);
+                    sh.resolved = res;
+                    sh.stop_ok = stp;
                 }
             }
             __syncthreads();
@@ -1284,7 +1364,7 @@ k_aca_big(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restrict
                 }
                 T dummy[KG / 32];
                 const BRed<T> of = big_reduce<T, NT>(cl, CS, sh, ph, qf, 0, dummy);
-                if (tid == 0) sh.resolved = !((double)of.x0 * (double)of.x0 > sh.rlim2);
+                if (tid == 0) sh.resolved = ref_resolved(st, of.x0);
                 __syncthreads();
                 resolved = sh.resolved;
                 nj = of.ai;

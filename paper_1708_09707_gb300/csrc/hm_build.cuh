@@ -83,6 +83,11 @@ void aca_run(int precision, const KernelParams& kp, const DeviceCoords& X,
 // tile reads are contiguous and in its gather order, each slice column-major
 // with the tile's row count as leading dimension.
 // ---------------------------------------------------------------------------
+// Leading dimension of a tile slice: the tile's rows rounded up to a
+// multiple of four, so every column of a slice starts on a 16-byte boundary
+// for a group of four float (or bfloat16 pair) rows; padding rows hold 0.
+__host__ __device__ __forceinline__ int slice_ld(int rows) { return (rows + 3) & ~3; }
+
 struct LrDesc {        // one (tile, admissible block) pair
     int64_t uoff;      // element offset of the slice in the tile-major U store
     int64_t toff;      // offset of t_b = V_b^T x in the t buffer
@@ -102,8 +107,8 @@ struct DnDesc {        // one (tile, dense block) pair
 // ---------------------------------------------------------------------------
 // Evaluate the dense leaf blocks directly into their tile slices: entry e of
 // the dense gather list is block ent[e].x restricted to the rows of tile
-// etile[e] (offset ent[e].y in the block). BF16X2 slices hold the hi plane
-// followed by the lo plane.
+// etile[e] (offset ent[e].y in the block). In BF16X2 slices every column
+// holds its slice_ld hi entries followed by its slice_ld lo entries.
 void near_assemble(int near_format, const KernelParams& kp, const DeviceCoords& X,
                    const Blk* blk, const int2* ent, const int32_t* etile,
                    const int32_t* tile_m, const DnDesc* desc, int64_t n_ent, void* store,
@@ -137,6 +142,18 @@ struct MvpPlan {
     const void* ustore = nullptr;
     const void* near = nullptr;
     int64_t near_entries = 0;
+    // flat column streams: the U slices of tile q are the ucol_ptr[q + 1] -
+    // ucol_ptr[q] consecutive columns of slice_ld(rows) entries from element
+    // ubase[q] of ustore, column c weighted by t[ucol_t[ucol_ptr[q] + c]];
+    // its near-field slices likewise from entry nbase[q], weighted by
+    // xm[ncol_x[ncol_ptr[q] + c]]
+    const int64_t* ucol_ptr = nullptr;
+    const int64_t* ubase = nullptr;
+    const int32_t* ucol_t = nullptr;
+    const int64_t* ncol_ptr = nullptr;
+    const int64_t* nbase = nullptr;
+    const int32_t* ncol_x = nullptr;
+    int64_t n_ucols = 0, n_ncols = 0;
     // row tiles and their gather lists (CSR over tiles)
     int64_t n_tiles = 0;
     const int64_t* tile_row0 = nullptr;
@@ -187,6 +204,9 @@ struct MvpLists {
     DevBuf<int2> vitems;
     DevBuf<int64_t> tpart_off, toff;
     DevBuf<int32_t> tsum_first, tsum_count, multi;
+    DevBuf<int64_t> ucol_ptr, ubase, ncol_ptr, nbase;   // flat column streams
+    DevBuf<int32_t> ucol_t, ncol_x;
+    int64_t n_ucols = 0, n_ncols = 0;
     int64_t n_tiles = 0, n_vitems = 0, tpart_len = 0, t_len = 0, n_multi = 0;
     int64_t n_lr = 0, n_dn = 0, u_elems = 0, near_elems = 0;
 };

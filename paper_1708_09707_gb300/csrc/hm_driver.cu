@@ -263,15 +263,16 @@ void export_factors(hm_handle_s& h, int64_t b, double* U, double* V, int* rank)
         for (int64_t e = 0; e < L.n_lr; ++e) {
             if (h.h_lr_ent[e].x != b) continue;
             const int rows = h.h_tile_m[h.h_lr_tile[e]];
+            const int ld = slice_ld(rows);
             const int rowoff = h.h_lr_ent[e].y;
-            std::vector<char> raw((size_t)r * rows * esz);
+            std::vector<char> raw((size_t)r * ld * esz);
             HM_CUDA(cudaMemcpy(raw.data(), h.ustore.p + h.h_lr_desc[e].uoff * esz, raw.size(),
                                cudaMemcpyDeviceToHost));
             std::vector<double> sl((size_t)r * rows);
             to_double(raw, sl.size(), sl.data());
             for (int l = 0; l < r; ++l)
                 for (int i = 0; i < rows; ++i)
-                    tmp[(size_t)l * B.m + rowoff + i] = sl[(size_t)l * rows + i];
+                    tmp[(size_t)l * B.m + rowoff + i] = sl[(size_t)l * ld + i];
         }
         copy_out(U, tmp.data(), tmp.size() * sizeof(double), s);
     }

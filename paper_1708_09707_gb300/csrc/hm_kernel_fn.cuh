@@ -139,6 +139,7 @@ struct TSum<double> {
     __device__ __forceinline__ void join(const TSum& o) { s += o.s; }
     __device__ __forceinline__ void shfl_join(int o) { s += __shfl_xor_sync(0xffffffffu, s, o); }
     __device__ __forceinline__ double value() const { return s; }
+    __device__ __forceinline__ double rvalue() const { return s; }
 };
 
 template <>
@@ -173,6 +174,8 @@ struct TSum<float> {
         add2(os, oc);
     }
     __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+    // the pair rounded to float (no double arithmetic)
+    __device__ __forceinline__ float rvalue() const { return s + c; }
 };
 
 // Warp-wide helpers.

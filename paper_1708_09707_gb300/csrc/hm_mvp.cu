@@ -22,7 +22,6 @@ constexpr int NT = 256;
 constexpr int VT_NT = 256;        // threads per CTA of the V^T x kernel
 constexpr int VCH = 256;          // columns per V^T x work item (8 per lane)
 constexpr int TILE_NT = 256;      // threads per CTA of the gather kernel
-constexpr int TILE_WARPS = TILE_NT / 32;
 constexpr int TROWS = 64;         // rows handled per pass of a tile
 
 inline unsigned grid_for(int64_t n, int nt = NT) { return (unsigned)ceil_div(n, nt); }
@@ -126,208 +125,158 @@ struct Acc<float> {
     __device__ double value() const { return (double)s + (double)c; }
 };
 
-// Slices use an even leading dimension (the tile's rows rounded up), so every
-// column starts on an 8-byte boundary for float pairs, 16 for double pairs.
-__host__ __device__ __forceinline__ int slice_ld(int rows) { return rows + (rows & 1); }
-
-// Rows 2i and 2i+1 of column c of a U slice.
-__device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
-__device__ __forceinline__ double2 ld2(const double* p) { return *reinterpret_cast<const double2*>(p); }
-
-template <class R>
-struct V2;
-template <>
-struct V2<float> {
-    using T = float2;
-};
-template <>
-struct V2<double> {
-    using T = double2;
-};
-
-// Rows 2i and 2i+1 of column c of a near-field slice starting at element o
-// (BF16X2 slices are a hi plane followed by a lo plane of `plane` entries).
-template <class R, int FMT>
-__device__ __forceinline__ typename V2<R>::T near2(const void* store, int64_t o, int64_t plane,
-                                                   int64_t e)
+// Four consecutive rows of one slice column, from a 16-byte aligned address
+// (streaming loads: every entry is read once per product).
+__device__ __forceinline__ void ld4(const float* p, float (&o)[4])
 {
-    typename V2<R>::T v;
-    if (FMT == HM_NEAR_FP64) {
-        const double2 a = *reinterpret_cast<const double2*>(static_cast<const double*>(store) + o + e);
-        v.x = (R)a.x;
-        v.y = (R)a.y;
-    } else if (FMT == HM_NEAR_FP32) {
-        const float2 a = *reinterpret_cast<const float2*>(static_cast<const float*>(store) + o + e);
-        v.x = (R)a.x;
-        v.y = (R)a.y;
-    } else if (FMT == HM_NEAR_BF16X2) {
-        const __nv_bfloat16* S = static_cast<const __nv_bfloat16*>(store) + 2 * o;
-        const float2 h = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(S + e));
-        const float2 l = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(S + plane + e));
-        v.x = (R)(h.x + l.x);
-        v.y = (R)(h.y + l.y);
-    } else {
-        const __nv_bfloat16* S = static_cast<const __nv_bfloat16*>(store) + o;
-        const float2 h = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(S + e));
-        v.x = (R)h.x;
-        v.y = (R)h.y;
-    }
-    return v;
+    const float4 a = __ldcs(reinterpret_cast<const float4*>(p));
+    o[0] = a.x;
+    o[1] = a.y;
+    o[2] = a.z;
+    o[3] = a.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&o)[4])
+{
+    const double2 a = __ldcs(reinterpret_cast<const double2*>(p));
+    const double2 b = __ldcs(reinterpret_cast<const double2*>(p) + 1);
+    o[0] = a.x;
+    o[1] = a.y;
+    o[2] = b.x;
+    o[3] = b.y;
 }
 
-constexpr int DESC_CHUNK = 128;   // gather descriptors staged in shared memory
+__device__ __forceinline__ float2 bf2(uint32_t u)
+{
+    __nv_bfloat162 h;
+    memcpy(&h, &u, 4);
+    return __bfloat1622float2(h);
+}
 
-// One CTA per row tile. Lane l owns rows 2l and 2l+1 of the current 64-row
-// pass and reads both with one vector load per column; warps take the tile's
-// gather entries round-robin, four columns at a time, and prefetch the next
-// entry's multipliers (t_b or x) while the current entry streams.
+// Rows ir .. ir+3 of column c of a near-field stream starting at entry nb.
 template <class R, int FMT>
-__global__ void __launch_bounds__(TILE_NT)
+__device__ __forceinline__ void near4(const void* store, int64_t nb, int64_t c, int ld, int ir,
+                                      R (&o)[4])
+{
+    if (FMT == HM_NEAR_FP64) {
+        double v[4];
+        ld4(static_cast<const double*>(store) + nb + c * ld + ir, v);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) o[i] = (R)v[i];
+    } else if (FMT == HM_NEAR_FP32) {
+        float v[4];
+        ld4(static_cast<const float*>(store) + nb + c * ld + ir, v);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) o[i] = (R)v[i];
+    } else if (FMT == HM_NEAR_BF16X2) {
+        const __nv_bfloat16* S = static_cast<const __nv_bfloat16*>(store) + 2 * nb + 2 * c * ld + ir;
+        const uint2 h = __ldcs(reinterpret_cast<const uint2*>(S));
+        const uint2 l = __ldcs(reinterpret_cast<const uint2*>(S + ld));
+        const float2 h0 = bf2(h.x), h1 = bf2(h.y), l0 = bf2(l.x), l1 = bf2(l.y);
+        o[0] = (R)(h0.x + l0.x);
+        o[1] = (R)(h0.y + l0.y);
+        o[2] = (R)(h1.x + l1.x);
+        o[3] = (R)(h1.y + l1.y);
+    } else {
+        const __nv_bfloat16* S = static_cast<const __nv_bfloat16*>(store) + nb + c * ld + ir;
+        const uint2 h = __ldcs(reinterpret_cast<const uint2*>(S));
+        const float2 h0 = bf2(h.x), h1 = bf2(h.y);
+        o[0] = (R)h0.x;
+        o[1] = (R)h0.y;
+        o[2] = (R)h1.x;
+        o[3] = (R)h1.y;
+    }
+}
+
+constexpr int T2_HW = TILE_NT / 16;   // half-warps per CTA
+constexpr int T2_B = 8;               // columns in flight per half-warp
+
+// One CTA per row tile. The tile's U slices and its near-field slices are
+// two streams of consecutive columns (slice_ld rows each); half-warp h takes
+// columns h, h + 16, h + 32, ... of each stream, eight at a time, lane l of
+// the half-warp rows 4l .. 4l+3 of the current 64-row window with one
+// 16-byte load per column (two 8-byte loads for bfloat16 pairs). Lanes 0..7
+// fetch the eight columns' multipliers (t_b entries or Morton-ordered x)
+// and pass them by shuffles. Every half-warp keeps compensated sums for its
+// four rows; the 16 partial sums of a row are added in half-warp order, so
+// the product is deterministic.
+template <class R, int FMT>
+__global__ void __launch_bounds__(TILE_NT, 3)
 k_tile(MvpPlan P, const R* __restrict__ xm, const R* __restrict__ t, const double* __restrict__ x,
        double* __restrict__ y, int accumulate)
 {
-    using R2 = typename V2<R>::T;
-    __shared__ double part[TILE_WARPS][TROWS];
-    __shared__ LrDesc lds[DESC_CHUNK];
-    __shared__ DnDesc dds[DESC_CHUNK];
+    __shared__ double part[T2_HW][TROWS];
     const int64_t tile = blockIdx.x;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int hw = threadIdx.x >> 4, hl = threadIdx.x & 15;
+    const unsigned hmask = 0xffffu << (threadIdx.x & 16);
     const int64_t r0 = P.tile_row0[tile];
     const int mt = P.tile_m[tile];
     const int ld = slice_ld(mt);
-    const int64_t l0 = P.lr_ptr[tile], l1 = P.lr_ptr[tile + 1];
-    const int64_t d0 = P.dn_ptr[tile], d1 = P.dn_ptr[tile + 1];
+    const int64_t uc0 = P.ucol_ptr[tile], nu = P.ucol_ptr[tile + 1] - uc0, ub = P.ubase[tile];
+    const int64_t nc0 = P.ncol_ptr[tile], nn = P.ncol_ptr[tile + 1] - nc0, nb = P.nbase[tile];
     const R* __restrict__ US = static_cast<const R*>(P.ustore);
-    for (int rp = 0; rp < mt; rp += TROWS) {
-        const int rows = min(TROWS, mt - rp);
-        const int ir = rp + 2 * lane;           // first of the lane's two rows
-        const bool act = 2 * lane < rows;
-        Acc<R> acc0, acc1;
-        // low-rank contributions U_b(rows, :) t_b
-        for (int64_t c0 = l0; c0 < l1; c0 += DESC_CHUNK) {
-            const int nc = (l1 - c0) < DESC_CHUNK ? (int)(l1 - c0) : DESC_CHUNK;
-            __syncthreads();
-            for (int q = threadIdx.x; q < nc; q += TILE_NT) lds[q] = P.lr_desc[c0 + q];
-            __syncthreads();
-            int q = w;
-            LrDesc dn;
-            R tn = 0;
-            if (q < nc) {
-                dn = lds[q];
-                tn = (lane < dn.k) ? t[dn.toff + lane] : R(0);
+    for (int rp = 0; rp < ld; rp += TROWS) {
+        const int ir = rp + 4 * hl;
+        const bool act = ir < ld;
+        Acc<R> acc[4];
+        for (int64_t c0 = hw; c0 < nu; c0 += 16 * T2_B) {
+            R mv = R(0);
+            {
+                const int64_t c = c0 + 16 * hl;
+                if (hl < T2_B && c < nu) mv = t[P.ucol_t[uc0 + c]];
             }
-            for (; q < nc; q += TILE_WARPS) {
-                const LrDesc d = dn;
-                R tv = tn;
-                if (q + TILE_WARPS < nc) {
-                    dn = lds[q + TILE_WARPS];
-                    tn = (lane < dn.k) ? t[dn.toff + lane] : R(0);
-                }
-                const R* __restrict__ Us = US + d.uoff + ir;
-                const int k = d.k;
-                R s0 = 0, s1 = 0;
-                for (int lb = 0; lb < k; lb += 32) {
-                    if (lb > 0) tv = (lb + lane < k) ? t[d.toff + lb + lane] : R(0);
-                    const int kn = min(32, k - lb);
-                    int l = 0;
-                    for (; l + 4 <= kn; l += 4) {
-                        const R* Uc = Us + (int64_t)(lb + l) * ld;
-                        R2 a0 = {0, 0}, a1 = {0, 0}, a2 = {0, 0}, a3 = {0, 0};
-                        if (act) {
-                            a0 = ld2(Uc);
-                            a1 = ld2(Uc + ld);
-                            a2 = ld2(Uc + 2 * ld);
-                            a3 = ld2(Uc + 3 * ld);
-                        }
-                        const R t0 = __shfl_sync(0xffffffffu, tv, l);
-                        const R t1 = __shfl_sync(0xffffffffu, tv, l + 1);
-                        const R t2 = __shfl_sync(0xffffffffu, tv, l + 2);
-                        const R t3 = __shfl_sync(0xffffffffu, tv, l + 3);
-                        s0 += a0.x * t0 + a1.x * t1 + a2.x * t2 + a3.x * t3;
-                        s1 += a0.y * t0 + a1.y * t1 + a2.y * t2 + a3.y * t3;
-                    }
-                    for (; l < kn; ++l) {
-                        const R* Uc = Us + (int64_t)(lb + l) * ld;
-                        const R tl = __shfl_sync(0xffffffffu, tv, l);
-                        if (act) {
-                            const R2 a = ld2(Uc);
-                            s0 += a.x * tl;
-                            s1 += a.y * tl;
-                        }
-                    }
-                }
-                acc0.add(s0);
-                acc1.add(s1);
-            }
-        }
-        // dense contributions A_b(rows, :) x|sigma
-        for (int64_t c0 = d0; c0 < d1; c0 += DESC_CHUNK) {
-            const int nc = (d1 - c0) < DESC_CHUNK ? (int)(d1 - c0) : DESC_CHUNK;
-            __syncthreads();
-            for (int q = threadIdx.x; q < nc; q += TILE_NT) dds[q] = P.dn_desc[c0 + q];
-            __syncthreads();
-            int q = w;
-            DnDesc dn;
-            R xn = 0;
-            if (q < nc) {
-                dn = dds[q];
-                xn = (lane < dn.n) ? xm[dn.col0 + lane] : R(0);
-            }
-            for (; q < nc; q += TILE_WARPS) {
-                const DnDesc d = dn;
-                R xv = xn;
-                if (q + TILE_WARPS < nc) {
-                    dn = dds[q + TILE_WARPS];
-                    xn = (lane < dn.n) ? xm[dn.col0 + lane] : R(0);
-                }
-                const int n = d.n;
-                const int64_t plane = (int64_t)ld * n;
-                R s0 = 0, s1 = 0;
-                for (int jb = 0; jb < n; jb += 32) {
-                    if (jb > 0) xv = (jb + lane < n) ? xm[d.col0 + jb + lane] : R(0);
-                    const int jn = min(32, n - jb);
-                    int j = 0;
-                    for (; j + 4 <= jn; j += 4) {
-                        const int64_t c = (int64_t)(jb + j) * ld + ir;
-                        R2 a0 = {0, 0}, a1 = {0, 0}, a2 = {0, 0}, a3 = {0, 0};
-                        if (act) {
-                            a0 = near2<R, FMT>(P.near, d.noff, plane, c);
-                            a1 = near2<R, FMT>(P.near, d.noff, plane, c + ld);
-                            a2 = near2<R, FMT>(P.near, d.noff, plane, c + 2 * ld);
-                            a3 = near2<R, FMT>(P.near, d.noff, plane, c + 3 * ld);
-                        }
-                        const R x0 = __shfl_sync(0xffffffffu, xv, j);
-                        const R x1 = __shfl_sync(0xffffffffu, xv, j + 1);
-                        const R x2 = __shfl_sync(0xffffffffu, xv, j + 2);
-                        const R x3 = __shfl_sync(0xffffffffu, xv, j + 3);
-                        s0 += a0.x * x0 + a1.x * x1 + a2.x * x2 + a3.x * x3;
-                        s1 += a0.y * x0 + a1.y * x1 + a2.y * x2 + a3.y * x3;
-                    }
-                    for (; j < jn; ++j) {
-                        const int64_t c = (int64_t)(jb + j) * ld + ir;
-                        const R xj = __shfl_sync(0xffffffffu, xv, j);
-                        if (act) {
-                            const R2 a = near2<R, FMT>(P.near, d.noff, plane, c);
-                            s0 += a.x * xj;
-                            s1 += a.y * xj;
-                        }
-                    }
-                }
-                acc0.add(s0);
-                acc1.add(s1);
-            }
-        }
-        part[w][2 * lane] = acc0.value();
-        part[w][2 * lane + 1] = acc1.value();
-        __syncthreads();
-        if ((int)threadIdx.x < rows) {
-            double s = 0.0;
+            R a[T2_B][4];
 #pragma unroll
-            for (int q = 0; q < TILE_WARPS; ++q) s += part[q][threadIdx.x];
+            for (int e = 0; e < T2_B; ++e) {
+                const int64_t c = c0 + 16 * e;
+                if (act && c < nu) ld4(US + ub + c * ld + ir, a[e]);
+                else a[e][0] = a[e][1] = a[e][2] = a[e][3] = R(0);
+            }
+            R s[4] = {R(0), R(0), R(0), R(0)};
+#pragma unroll
+            for (int e = 0; e < T2_B; ++e) {
+                const R m = __shfl_sync(hmask, mv, e, 16);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) s[i] = fma(a[e][i], m, s[i]);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[i].add(s[i]);
+        }
+        for (int64_t c0 = hw; c0 < nn; c0 += 16 * T2_B) {
+            R mv = R(0);
+            {
+                const int64_t c = c0 + 16 * hl;
+                if (hl < T2_B && c < nn) mv = xm[P.ncol_x[nc0 + c]];
+            }
+            R a[T2_B][4];
+#pragma unroll
+            for (int e = 0; e < T2_B; ++e) {
+                const int64_t c = c0 + 16 * e;
+                if (act && c < nn) near4<R, FMT>(P.near, nb, c, ld, ir, a[e]);
+                else a[e][0] = a[e][1] = a[e][2] = a[e][3] = R(0);
+            }
+            R s[4] = {R(0), R(0), R(0), R(0)};
+#pragma unroll
+            for (int e = 0; e < T2_B; ++e) {
+                const R m = __shfl_sync(hmask, mv, e, 16);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) s[i] = fma(a[e][i], m, s[i]);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[i].add(s[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (4 * hl + i < TROWS) part[hw][4 * hl + i] = act ? acc[i].value() : 0.0;
+        __syncthreads();
+        const int rows = min(TROWS, mt - rp);
+        if ((int)threadIdx.x < rows) {
+            double sum = 0.0;
+#pragma unroll
+            for (int q = 0; q < T2_HW; ++q) sum += part[q][threadIdx.x];
             const int64_t row = r0 + rp + threadIdx.x;
             const int64_t dst = P.perm[row];
             const double sg = P.sig_row ? P.sig_row[row] : P.sigma2;
-            const double v = s + sg * x[dst];
+            const double v = sum + sg * x[dst];
             y[dst] = accumulate ? y[dst] + v : v;
         }
         __syncthreads();
@@ -554,6 +503,58 @@ __global__ void k_vitems_emit(const Blk* __restrict__ blk, int64_t nb,
     if (c > 1) multi[moff[b]] = (int32_t)b;
 }
 
+// Columns of every gather entry: the rank of its block (low-rank list) or
+// the block's column count (dense list).
+__global__ void k_lr_ncols(const int2* __restrict__ ent, int64_t ne, const int32_t* __restrict__ rank,
+                           int64_t* __restrict__ cnt)
+{
+    int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (e < ne) cnt[e] = rank[ent[e].x];
+}
+
+__global__ void k_dn_ncols(const int2* __restrict__ ent, int64_t ne, const Blk* __restrict__ dblk,
+                           int64_t* __restrict__ cnt)
+{
+    int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (e < ne) cnt[e] = dblk[ent[e].x].n;
+}
+
+// Per tile: first column (colptr) and first element (base) of its stream;
+// colptr[nt] closes the last tile.
+__global__ void k_tile_streams(const int64_t* __restrict__ ptr, int64_t nt, int64_t ne,
+                               const int64_t* __restrict__ ecol, int64_t ncols,
+                               const int64_t* __restrict__ eoff, int64_t nelem,
+                               int64_t* __restrict__ colptr, int64_t* __restrict__ base)
+{
+    int64_t q = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (q > nt) return;
+    const int64_t e = ptr[q];
+    colptr[q] = e < ne ? ecol[e] : ncols;
+    if (q < nt) base[q] = e < ne ? eoff[e] : nelem;
+}
+
+// Multiplier index of every column: t offset of the block (low rank) or its
+// Morton column (dense).
+__global__ void k_fill_ucol(const int2* __restrict__ ent, int64_t ne, const int32_t* __restrict__ rank,
+                            const int64_t* __restrict__ toff, const int64_t* __restrict__ ecol,
+                            int32_t* __restrict__ ucol_t)
+{
+    int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (e >= ne) return;
+    const int b = ent[e].x;
+    const int k = rank[b];
+    for (int c = 0; c < k; ++c) ucol_t[ecol[e] + c] = (int32_t)(toff[b] + c);
+}
+
+__global__ void k_fill_ncol(const int2* __restrict__ ent, int64_t ne, const Blk* __restrict__ dblk,
+                            const int64_t* __restrict__ ecol, int32_t* __restrict__ ncol_x)
+{
+    int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (e >= ne) return;
+    const Blk B = dblk[ent[e].x];
+    for (int c = 0; c < B.n; ++c) ncol_x[ecol[e] + c] = (int32_t)(B.col0 + c);
+}
+
 }  // namespace
 
 void mvp_build_lists(const Blk* ablk, const int32_t* rank, int64_t n_adm, const Blk* dblk,
@@ -585,7 +586,27 @@ void mvp_build_lists(const Blk* ablk, const int32_t* rank, int64_t n_adm, const 
         scan_exclusive_i64(sz.p, off.p, L.n_dn, off.p + L.n_dn, s);
         k_dn_desc<<<grid_for(L.n_dn), NT, 0, s>>>(L.dn_ent.p, L.n_dn, dblk, off.p, L.dn_desc.p); note_launch();
         HM_CUDA(cudaMemcpyAsync(&L.near_elems, off.p + L.n_dn, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        // the near-field column stream of every tile
+        DevBuf<int64_t> cnt(L.n_dn, s), ecol(L.n_dn + 1, s);
+        k_dn_ncols<<<grid_for(L.n_dn), NT, 0, s>>>(L.dn_ent.p, L.n_dn, dblk, cnt.p); note_launch();
+        scan_exclusive_i64(cnt.p, ecol.p, L.n_dn, ecol.p + L.n_dn, s);
+        HM_CUDA(cudaMemcpyAsync(&L.n_ncols, ecol.p + L.n_dn, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         HM_CUDA(cudaStreamSynchronize(s));
+        if (L.n_ncols > INT32_MAX || n_tiles <= 0) fail(HM_EOVERFLOW, "near-field column stream");
+        L.ncol_ptr.alloc(n_tiles + 1, s);
+        L.nbase.alloc(n_tiles, s);
+        L.ncol_x.alloc(std::max<int64_t>(L.n_ncols, 1), s);
+        k_tile_streams<<<grid_for(n_tiles + 1), NT, 0, s>>>(L.dn_ptr.p, n_tiles, L.n_dn, ecol.p,
+                                                             L.n_ncols, off.p, L.near_elems,
+                                                             L.ncol_ptr.p, L.nbase.p); note_launch();
+        k_fill_ncol<<<grid_for(L.n_dn), NT, 0, s>>>(L.dn_ent.p, L.n_dn, dblk, ecol.p, L.ncol_x.p); note_launch();
+        HM_CUDA(cudaStreamSynchronize(s));
+    } else {
+        L.ncol_ptr.alloc(n_tiles + 1, s);
+        L.nbase.alloc(std::max<int64_t>(n_tiles, 1), s);
+        L.ncol_x.alloc(1, s);
+        HM_CUDA(cudaMemsetAsync(L.ncol_ptr.p, 0, (n_tiles + 1) * sizeof(int64_t), s));
+        HM_CUDA(cudaMemsetAsync(L.nbase.p, 0, std::max<int64_t>(n_tiles, 1) * sizeof(int64_t), s));
     }
     // t offsets and V^T x work items
     const int64_t nb = std::max<int64_t>(n_adm, 1);
@@ -628,7 +649,29 @@ void mvp_build_lists(const Blk* ablk, const int32_t* rank, int64_t n_adm, const 
         scan_exclusive_i64(sz.p, off.p, L.n_lr, off.p + L.n_lr, s);
         k_lr_desc<<<grid_for(L.n_lr), NT, 0, s>>>(L.lr_ent.p, L.n_lr, rank, off.p, L.toff.p, L.lr_desc.p); note_launch();
         HM_CUDA(cudaMemcpyAsync(&L.u_elems, off.p + L.n_lr, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        // the U column stream of every tile
+        DevBuf<int64_t> cnt(L.n_lr, s), ecol(L.n_lr + 1, s);
+        k_lr_ncols<<<grid_for(L.n_lr), NT, 0, s>>>(L.lr_ent.p, L.n_lr, rank, cnt.p); note_launch();
+        scan_exclusive_i64(cnt.p, ecol.p, L.n_lr, ecol.p + L.n_lr, s);
+        HM_CUDA(cudaMemcpyAsync(&L.n_ucols, ecol.p + L.n_lr, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         HM_CUDA(cudaStreamSynchronize(s));
+        if (L.n_ucols > INT32_MAX || L.t_len > INT32_MAX || n_tiles <= 0)
+            fail(HM_EOVERFLOW, "low-rank column stream");
+        L.ucol_ptr.alloc(n_tiles + 1, s);
+        L.ubase.alloc(n_tiles, s);
+        L.ucol_t.alloc(std::max<int64_t>(L.n_ucols, 1), s);
+        k_tile_streams<<<grid_for(n_tiles + 1), NT, 0, s>>>(L.lr_ptr.p, n_tiles, L.n_lr, ecol.p,
+                                                             L.n_ucols, off.p, L.u_elems,
+                                                             L.ucol_ptr.p, L.ubase.p); note_launch();
+        k_fill_ucol<<<grid_for(L.n_lr), NT, 0, s>>>(L.lr_ent.p, L.n_lr, rank, L.toff.p, ecol.p,
+                                                   L.ucol_t.p); note_launch();
+        HM_CUDA(cudaStreamSynchronize(s));
+    } else {
+        L.ucol_ptr.alloc(n_tiles + 1, s);
+        L.ubase.alloc(std::max<int64_t>(n_tiles, 1), s);
+        L.ucol_t.alloc(1, s);
+        HM_CUDA(cudaMemsetAsync(L.ucol_ptr.p, 0, (n_tiles + 1) * sizeof(int64_t), s));
+        HM_CUDA(cudaMemsetAsync(L.ubase.p, 0, std::max<int64_t>(n_tiles, 1) * sizeof(int64_t), s));
     }
     HM_LAUNCH("descriptors");
 }

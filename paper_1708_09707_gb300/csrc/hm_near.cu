@@ -3,8 +3,9 @@
 // each slice is stored column-major with the tile's row count as leading
 // dimension, in the product's gather order (tile-major); unlike the paper's
 // stacked layout there is no zero padding to a common column count.
-// Formats: double, float, bfloat16 hi/lo pair (two planes: hi = bf16(a),
-// lo = bf16(a - hi), about 16 significant bits together) or a single bf16.
+// Formats: double, float, bfloat16 hi/lo pair (hi = bf16(a), lo =
+// bf16(a - hi), about 16 significant bits together; each column holds its hi
+// entries, then its lo entries) or a single bf16.
 #include "hm_kernel_fn.cuh"
 
 namespace hm {
@@ -29,10 +30,9 @@ k_near(KernelParams kp, DeviceCoords X, const Blk* __restrict__ blk, const int2*
     const int2 en = ent[e];
     const Blk B = blk[en.x];
     const int rows = tile_m[etile[e]];
-    const int ld = rows + (rows & 1);   // even leading dimension (zero pad row)
+    const int ld = slice_ld(rows);
     const int64_t r0 = B.row0 + en.y;
     const int n = B.n;
-    const int64_t mn = (int64_t)ld * n;
     const int64_t o = desc[e].noff;
     for (int pr0 = 0; pr0 < ld / 2; pr0 += NT) {
         const int npair = min(NT, ld / 2 - pr0);
@@ -41,8 +41,8 @@ k_near(KernelParams kp, DeviceCoords X, const Blk* __restrict__ blk, const int2*
         if (t >= cstep * npair) continue;
         const int i = 2 * (pr0 + t % npair);      // first row of the pair
         const bool v0 = i < rows, v1 = i + 1 < rows;
-        // the pair's points (a padding row repeats the last real row)
-        const int64_t ra = r0 + i, rb = r0 + (v1 ? i + 1 : i);
+        // the pair's points (padding rows load the last real row)
+        const int64_t ra = r0 + min(i, rows - 1), rb = r0 + min(i + 1, rows - 1);
         Pt<double> pa64, pb64;
         Pt<float> pa32, pb32;
         if (FMT == HM_NEAR_FP64) {
@@ -68,12 +68,12 @@ k_near(KernelParams kp, DeviceCoords X, const Blk* __restrict__ blk, const int2*
                 if (FMT == HM_NEAR_FP32) {
                     *reinterpret_cast<float2*>(static_cast<float*>(store) + o + q) = make_float2(a, b);
                 } else if (FMT == HM_NEAR_BF16X2) {
-                    __nv_bfloat16* S = static_cast<__nv_bfloat16*>(store) + 2 * o;
+                    // column j: hi entries at 2 j ld, lo entries at 2 j ld + ld
+                    __nv_bfloat16* S = static_cast<__nv_bfloat16*>(store) + 2 * o + q + (int64_t)j * ld;
                     const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
                     const float2 hf = __bfloat1622float2(h);
-                    *reinterpret_cast<__nv_bfloat162*>(S + q) = h;
-                    *reinterpret_cast<__nv_bfloat162*>(S + mn + q) =
-                        __floats2bfloat162_rn(a - hf.x, b - hf.y);
+                    *reinterpret_cast<__nv_bfloat162*>(S) = h;
+                    *reinterpret_cast<__nv_bfloat162*>(S + ld) = __floats2bfloat162_rn(a - hf.x, b - hf.y);
                 } else {
                     *reinterpret_cast<__nv_bfloat162*>(static_cast<__nv_bfloat16*>(store) + o + q) =
                         __floats2bfloat162_rn(a, b);

@@ -728,6 +728,14 @@ void build_sets(hm_handle_s& h, int nsets, const double* points_all, const int64
     P.n_tiles = h.n_tiles;
     P.tile_row0 = h.tile_row0.p;
     P.tile_m = h.tile_m.p;
+    P.ucol_ptr = h.lists.ucol_ptr.p;
+    P.ubase = h.lists.ubase.p;
+    P.ucol_t = h.lists.ucol_t.p;
+    P.ncol_ptr = h.lists.ncol_ptr.p;
+    P.nbase = h.lists.nbase.p;
+    P.ncol_x = h.lists.ncol_x.p;
+    P.n_ucols = h.lists.n_ucols;
+    P.n_ncols = h.lists.n_ncols;
     P.lr_ptr = h.lists.lr_ptr.p;
     P.lr_desc = h.lists.lr_desc.p;
     P.dn_ptr = h.lists.dn_ptr.p;
@@ -751,20 +759,15 @@ void build_sets(hm_handle_s& h, int nsets, const double* points_all, const int64
     const int64_t fsz = h.precision == HM_PREC_FP64 ? 8 : 4;
     st.factor_bytes = st.factor_entries * fsz;
     st.near_bytes = st.near_entries * (int64_t)near_entry_bytes(h.near_format);
-    int64_t n_ent = 0;
-    {
-        int64_t a = 0, b = 0;
-        HM_CUDA(cudaMemcpy(&a, h.lists.lr_ptr.p + h.n_tiles, sizeof(int64_t), cudaMemcpyDeviceToHost));
-        HM_CUDA(cudaMemcpy(&b, h.lists.dn_ptr.p + h.n_tiles, sizeof(int64_t), cudaMemcpyDeviceToHost));
-        n_ent = a + b;
-    }
     // algorithmic bytes of one product: factors + near field + x (read once
-    // through the permutation) + perm + y written + gather entries
-    st.mvp_bytes = st.factor_bytes + st.near_bytes + Ntot * (8 + 8 + 8) + n_ent * 8;
+    // through the permutation) + perm + y written + the gather's column
+    // multiplier indices (4 bytes per column)
+    const int64_t idx_bytes = (h.lists.n_ucols + h.lists.n_ncols) * 4;
+    st.mvp_bytes = st.factor_bytes + st.near_bytes + Ntot * (8 + 8 + 8) + idx_bytes;
     // per kernel: V^T x reads V and writes t; the gather reads U, the near
-    // field, its entries, perm and x (for sigma^2 x) and writes y
+    // field, its column indices, perm and x (for sigma^2 x) and writes y
     st.mvp_vtx_bytes = (st.factor_entries - h.factor_entries_U) * fsz + h.lists.t_len * fsz;
-    st.mvp_tile_bytes = h.factor_entries_U * fsz + st.near_bytes + Ntot * (8 + 8 + 8) + n_ent * 8;
+    st.mvp_tile_bytes = h.factor_entries_U * fsz + st.near_bytes + Ntot * (8 + 8 + 8) + idx_bytes;
     st.t_total_ms =
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
