@@ -156,6 +156,7 @@ struct MvpPlan {
     int64_t n_ucols = 0, n_ncols = 0;
     // row tiles and their gather lists (CSR over tiles)
     int64_t n_tiles = 0;
+    int max_ld = 0;                       // slice_ld of the largest tile
     const int64_t* tile_row0 = nullptr;
     const int32_t* tile_m = nullptr;
     const int64_t* lr_ptr = nullptr;

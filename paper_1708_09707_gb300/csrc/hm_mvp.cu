@@ -12,6 +12,10 @@
 // U slices and near-field slices a tile reads are contiguous (tile-major
 // stores), and each gather entry carries its own descriptor, so the gather
 // streams its data without dependent metadata loads.
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "hm_kernel_fn.cuh"
 
 namespace hm {
@@ -188,19 +192,58 @@ __device__ __forceinline__ void near4(const void* store, int64_t nb, int64_t c, 
 }
 
 constexpr int T2_HW = TILE_NT / 16;   // half-warps per CTA
-constexpr int T2_B = 8;               // columns in flight per half-warp
+
+// Multiply-accumulate one column stream of a tile: half-warp hw takes
+// columns hw, hw + 16, hw + 32, ..., TB at a time; lane hl < TB of the
+// half-warp fetches the multiplier of the batch's column hl one batch ahead
+// (its index and its value are two dependent loads), and passes it by a
+// shuffle when the batch's data has arrived.
+template <class R, int TB, class LD, class MUL>
+__device__ __forceinline__ void tile_stream(int64_t ncols, int hw, int hl, unsigned hmask, bool act,
+                                            const LD& load_col, const MUL& mult, Acc<R> (&acc)[4])
+{
+    int64_t c0 = hw;
+    R mv = (hl < TB && c0 + 16 * hl < ncols) ? mult(c0 + 16 * hl) : R(0);
+    for (; c0 < ncols; c0 += 16 * TB) {
+        R a[TB][4];
+#pragma unroll
+        for (int e = 0; e < TB; ++e) {
+            const int64_t c = c0 + 16 * e;
+            if (act && c < ncols) load_col(c, a[e]);
+            else a[e][0] = a[e][1] = a[e][2] = a[e][3] = R(0);
+        }
+        const int64_t cn = c0 + 16 * TB + 16 * hl;
+        const R mnext = (hl < TB && cn < ncols) ? mult(cn) : R(0);
+        // plain sums over groups of four columns, each added compensated:
+        // the grouping, hence the result, is the same for every TB
+#pragma unroll
+        for (int e0 = 0; e0 < TB; e0 += 4) {
+            R sg[4] = {R(0), R(0), R(0), R(0)};
+#pragma unroll
+            for (int e = e0; e < e0 + 4; ++e) {
+                const R m = __shfl_sync(hmask, mv, e, 16);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) sg[i] = fma(a[e][i], m, sg[i]);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[i].add(sg[i]);
+        }
+        mv = mnext;
+    }
+}
 
 // One CTA per row tile. The tile's U slices and its near-field slices are
 // two streams of consecutive columns (slice_ld rows each); half-warp h takes
-// columns h, h + 16, h + 32, ... of each stream, eight at a time, lane l of
-// the half-warp rows 4l .. 4l+3 of the current 64-row window with one
-// 16-byte load per column (two 8-byte loads for bfloat16 pairs). Lanes 0..7
-// fetch the eight columns' multipliers (t_b entries or Morton-ordered x)
-// and pass them by shuffles. Every half-warp keeps compensated sums for its
-// four rows; the 16 partial sums of a row are added in half-warp order, so
-// the product is deterministic.
-template <class R, int FMT>
-__global__ void __launch_bounds__(TILE_NT, 3)
+// columns h, h + 16, h + 32, ... of each stream, TB at a time, lane l of the
+// half-warp rows 4l .. 4l+3 of the current 64-row window with one 16-byte
+// load per column (two 8-byte loads for bfloat16 pairs). Every half-warp
+// keeps compensated sums for its four rows, adding the plain sum of every
+// four columns; the 16 partial sums of a row are added in half-warp order,
+// so the product is deterministic and the same for every TB (columns in
+// flight per half-warp, a multiple of four) and MINB (CTAs per SM), the
+// parameters the tuner picks.
+template <class R, int FMT, int TB, int MINB>
+__global__ void __launch_bounds__(TILE_NT, MINB)
 k_tile(MvpPlan P, const R* __restrict__ xm, const R* __restrict__ t, const double* __restrict__ x,
        double* __restrict__ y, int accumulate)
 {
@@ -214,59 +257,23 @@ k_tile(MvpPlan P, const R* __restrict__ xm, const R* __restrict__ t, const doubl
     const int64_t uc0 = P.ucol_ptr[tile], nu = P.ucol_ptr[tile + 1] - uc0, ub = P.ubase[tile];
     const int64_t nc0 = P.ncol_ptr[tile], nn = P.ncol_ptr[tile + 1] - nc0, nb = P.nbase[tile];
     const R* __restrict__ US = static_cast<const R*>(P.ustore);
+    const int32_t* __restrict__ ucol_t = P.ucol_t;
+    const int32_t* __restrict__ ncol_x = P.ncol_x;
+    const void* __restrict__ near = P.near;
     for (int rp = 0; rp < ld; rp += TROWS) {
         const int ir = rp + 4 * hl;
         const bool act = ir < ld;
         Acc<R> acc[4];
-        for (int64_t c0 = hw; c0 < nu; c0 += 16 * T2_B) {
-            R mv = R(0);
-            {
-                const int64_t c = c0 + 16 * hl;
-                if (hl < T2_B && c < nu) mv = t[P.ucol_t[uc0 + c]];
-            }
-            R a[T2_B][4];
+        tile_stream<R, TB>(
+            nu, hw, hl, hmask, act,
+            [&](int64_t c, R(&o)[4]) { ld4(US + ub + c * ld + ir, o); },
+            [&](int64_t c) { return t[ucol_t[uc0 + c]]; }, acc);
+        tile_stream<R, TB>(
+            nn, hw, hl, hmask, act,
+            [&](int64_t c, R(&o)[4]) { near4<R, FMT>(near, nb, c, ld, ir, o); },
+            [&](int64_t c) { return xm[ncol_x[nc0 + c]]; }, acc);
 #pragma unroll
-            for (int e = 0; e < T2_B; ++e) {
-                const int64_t c = c0 + 16 * e;
-                if (act && c < nu) ld4(US + ub + c * ld + ir, a[e]);
-                else a[e][0] = a[e][1] = a[e][2] = a[e][3] = R(0);
-            }
-            R s[4] = {R(0), R(0), R(0), R(0)};
-#pragma unroll
-            for (int e = 0; e < T2_B; ++e) {
-                const R m = __shfl_sync(hmask, mv, e, 16);
-#pragma unroll
-                for (int i = 0; i < 4; ++i) s[i] = fma(a[e][i], m, s[i]);
-            }
-#pragma unroll
-            for (int i = 0; i < 4; ++i) acc[i].add(s[i]);
-        }
-        for (int64_t c0 = hw; c0 < nn; c0 += 16 * T2_B) {
-            R mv = R(0);
-            {
-                const int64_t c = c0 + 16 * hl;
-                if (hl < T2_B && c < nn) mv = xm[P.ncol_x[nc0 + c]];
-            }
-            R a[T2_B][4];
-#pragma unroll
-            for (int e = 0; e < T2_B; ++e) {
-                const int64_t c = c0 + 16 * e;
-                if (act && c < nn) near4<R, FMT>(P.near, nb, c, ld, ir, a[e]);
-                else a[e][0] = a[e][1] = a[e][2] = a[e][3] = R(0);
-            }
-            R s[4] = {R(0), R(0), R(0), R(0)};
-#pragma unroll
-            for (int e = 0; e < T2_B; ++e) {
-                const R m = __shfl_sync(hmask, mv, e, 16);
-#pragma unroll
-                for (int i = 0; i < 4; ++i) s[i] = fma(a[e][i], m, s[i]);
-            }
-#pragma unroll
-            for (int i = 0; i < 4; ++i) acc[i].add(s[i]);
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-            if (4 * hl + i < TROWS) part[hw][4 * hl + i] = act ? acc[i].value() : 0.0;
+        for (int i = 0; i < 4; ++i) part[hw][4 * hl + i] = act ? acc[i].value() : 0.0;
         __syncthreads();
         const int rows = min(TROWS, mt - rp);
         if ((int)threadIdx.x < rows) {
@@ -706,6 +713,92 @@ void mvp_alloc_work(const MvpPlan& P, MvpWork& W, cudaStream_t s)
 
 namespace {
 
+// ---------------------------------------------------------------- tuning
+// Launch shapes of the gather kernel: columns in flight per half-warp and
+// CTAs per SM. The first product of a kind (precision, near-field format,
+// tile leading dimension, log2 of the tile count) on a device times every
+// shape once on the real data and keeps the fastest for the process; all
+// shapes give bit-identical results.
+constexpr int N_TILE_VARIANTS = 3;
+
+template <class R, int FMT>
+void launch_tile(int v, const MvpPlan& P, const R* xm, const R* t, const double* x, double* y,
+                 int accumulate, cudaStream_t s)
+{
+    const unsigned g = (unsigned)P.n_tiles;
+    switch (v) {
+    case 0: k_tile<R, FMT, 8, 3><<<g, TILE_NT, 0, s>>>(P, xm, t, x, y, accumulate); break;
+    case 1: k_tile<R, FMT, 16, 2><<<g, TILE_NT, 0, s>>>(P, xm, t, x, y, accumulate); break;
+    default: k_tile<R, FMT, 4, 4><<<g, TILE_NT, 0, s>>>(P, xm, t, x, y, accumulate); break;
+    }
+    note_launch();
+}
+
+struct TileKey {
+    int dev, precision, fmt, ld, lg_tiles;
+    bool operator<(const TileKey& o) const
+    {
+        return std::tie(dev, precision, fmt, ld, lg_tiles) <
+               std::tie(o.dev, o.precision, o.fmt, o.ld, o.lg_tiles);
+    }
+};
+std::mutex g_tune_mu;
+std::map<TileKey, int> g_tune;
+
+TileKey tile_key(const MvpPlan& P)
+{
+    int dev = 0;
+    HM_CUDA(cudaGetDevice(&dev));
+    int lg = 0;
+    while ((1ll << lg) < P.n_tiles) ++lg;
+    return TileKey{dev, P.precision, P.near_format, P.max_ld, lg};
+}
+
+int tile_variant(const MvpPlan& P)
+{
+    const TileKey k = tile_key(P);
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    auto it = g_tune.find(k);
+    return it == g_tune.end() ? -1 : it->second;
+}
+
+template <class R, int FMT>
+int tune_tile(const MvpPlan& P, const R* xm, const R* t, const double* x, double* y, int accumulate,
+              cudaStream_t s)
+{
+    cudaEvent_t ev[N_TILE_VARIANTS + 1];
+    for (auto& e : ev) HM_CUDA(cudaEventCreate(&e));
+    // a first untimed run settles caches and clocks; every run writes the
+    // same y, and with accumulate = 1 the caller's y must not be touched
+    DevBuf<double> ytmp;
+    double* yt = y;
+    if (accumulate) {
+        ytmp.alloc(P.Ntot, s);
+        yt = ytmp.p;
+    }
+    launch_tile<R, FMT>(0, P, xm, t, x, yt, 0, s);
+    HM_CUDA(cudaEventRecord(ev[0], s));
+    for (int v = 0; v < N_TILE_VARIANTS; ++v) {
+        launch_tile<R, FMT>(v, P, xm, t, x, yt, 0, s);
+        HM_CUDA(cudaEventRecord(ev[v + 1], s));
+    }
+    HM_CUDA(cudaEventSynchronize(ev[N_TILE_VARIANTS]));
+    int best = 0;
+    float tbest = 0.f;
+    for (int v = 0; v < N_TILE_VARIANTS; ++v) {
+        float ms = 0.f;
+        HM_CUDA(cudaEventElapsedTime(&ms, ev[v], ev[v + 1]));
+        if (v == 0 || ms < tbest) {
+            tbest = ms;
+            best = v;
+        }
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tune[tile_key(P)] = best;
+    return best;
+}
+
 template <class R, int FMT>
 void run_typed(const MvpPlan& P, R* xm, R* t, R* tp, const double* x, double* y,
                int accumulate, cudaStream_t s, MvpTimer* timer)
@@ -721,8 +814,11 @@ void run_typed(const MvpPlan& P, R* xm, R* t, R* tp, const double* x, double* y,
         k_tsum<R><<<(unsigned)P.n_multi, 64, 0, s>>>(P.multi, P.n_multi, P.rank, P.tsum_first,
                                                      P.tsum_count, P.tpart_off, P.toff, tp, t); note_launch();
     if (rec) HM_CUDA(cudaEventRecord(rec->e[2], s));
-    if (P.n_tiles > 0)
-        k_tile<R, FMT><<<(unsigned)P.n_tiles, TILE_NT, 0, s>>>(P, xm, t, x, y, accumulate); note_launch();
+    if (P.n_tiles > 0) {
+        int v = tile_variant(P);
+        if (v < 0) v = tune_tile<R, FMT>(P, xm, t, x, y, accumulate, s);
+        launch_tile<R, FMT>(v, P, xm, t, x, y, accumulate, s);
+    }
     if (rec) HM_CUDA(cudaEventRecord(rec->e[3], s));
     HM_LAUNCH("matvec");
 }

@@ -726,6 +726,7 @@ void build_sets(hm_handle_s& h, int nsets, const double* points_all, const int64
     P.near = h.near.p;
     P.near_entries = h.stats.near_entries;
     P.n_tiles = h.n_tiles;
+    P.max_ld = slice_ld(h.leaf);
     P.tile_row0 = h.tile_row0.p;
     P.tile_m = h.tile_m.p;
     P.ucol_ptr = h.lists.ucol_ptr.p;

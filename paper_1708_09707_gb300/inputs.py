@@ -83,6 +83,34 @@ def mixture_points(n: int, d: int, seed: int,
     return np.clip(pts, 0.0, 1.0)
 
 
+_PRIMES = (2, 3, 5)
+
+
+def radical_inverse(idx: np.ndarray, base: int) -> np.ndarray:
+    """van der Corput radical inverse: the base-b digits of idx mirrored
+    about the radix point (digit k of idx becomes the coefficient of
+    b^-(k+1))."""
+    i = np.asarray(idx, dtype=np.int64).copy()
+    assert i.size == 0 or i.max() < (1 << 40)
+    # mirrored digits as an integer over base^digits, one rounding at the end
+    num = np.zeros(i.shape, dtype=np.int64)
+    den = np.ones(i.shape, dtype=np.int64)
+    while np.any(i > 0):
+        live = i > 0
+        num = np.where(live, num * base + i % base, num)
+        den = np.where(live, den * base, den)
+        i //= base
+    return num / den
+
+
+def halton_points(n: int, d: int, start: int = 1) -> np.ndarray:
+    """The first n points of the d-dimensional Halton sequence (Sec. 6.2's
+    point sets): coordinate k of point i is the radical inverse of start + i
+    in the k-th prime base (2, 3, 5); no scrambling, index 0 skipped."""
+    idx = np.arange(start, start + n, dtype=np.int64)
+    return np.stack([radical_inverse(idx, _PRIMES[k]) for k in range(d)], axis=1)
+
+
 def ragged_batch_sizes(count: int, seed: int, lo: float = 1e4,
                        hi: float = 2.0 ** 18):
     """Sizes log-uniform in [lo, hi] and dimensions d in {2,3} with p = 1/2."""
@@ -128,6 +156,12 @@ WORKLOADS = {
     "matern3d_n4m_cg": dict(n=1 << 22, d=3, points="uniform", kernel=1,
                             ell=0.1, leaf=64, eta=1.0, adm="min",
                             eps=1e-6, sigma2=1e-2, seed=POINT_SEED + 5),
+    # the paper's own setting (Sec. 6.5): Halton points in [0,1]^2, the
+    # unscaled Gaussian exp(-r^2), C_leaf = 2048, eta = 1.5 and ACA of fixed
+    # rank k = 16 without a stopping criterion (eps <= 0)
+    "halton2d_n512k_k16": dict(n=1 << 19, d=2, points="halton", kernel=0,
+                               ell=1.0, leaf=2048, eta=1.5, adm="min",
+                               eps=0.0, k_cap=16, seed=0),
 }
 
 
@@ -136,4 +170,6 @@ def workload_points(name: str, n: int | None = None) -> np.ndarray:
     n = w["n"] if n is None else n
     if w["points"] == "uniform":
         return uniform_points(n, w["d"], w["seed"])
+    if w["points"] == "halton":
+        return halton_points(n, w["d"])
     return mixture_points(n, w["d"], w["seed"])

@@ -67,10 +67,15 @@ CASES = [
     (129, 2, "u", 1, 0.3, 64, 2.0, False, 1e-6),
     (1000, 2, "u", 0, 0.2, 8, 0.0, False, 1e-6),     # eta = 0: all dense
     (1500, 3, "u", 0, 0.5, 30, 1.5, False, 0.0),     # fixed-rank mode
+    # the paper's setting scaled down: Halton points, unscaled Gaussian,
+    # eta = 1.5, fixed rank 16 (Sec. 6.5); tiles of 256 rows
+    (16384, 2, "h", 0, 1.0, 256, 1.5, False, 0.0),
 ]
 
 
 def _pts(n, d, kind, seed=11):
+    if kind == "h":
+        return inputs.halton_points(n, d)
     return inputs.uniform_points(n, d, seed) if kind == "u" else inputs.mixture_points(n, d, seed)
 
 
@@ -95,8 +100,11 @@ def test_structure_and_fp64_product(hm, orc, case):
     # blocks of separated intervals are exactly rank 2, so whether a third
     # (rounding-noise) column passes the eps0 test is not unique; there only
     # the product is compared.
+    # With the unscaled Gaussian at fixed rank 16 the residual reaches
+    # rounding level before rank 16, where the eps0 rejections are not
+    # unique either; there too only the product is compared.
     ndiff = int((s["ranks"] != oranks).sum())
-    if d > 1:
+    if d > 1 and kind != "h":
         assert ndiff <= max(1, len(oranks) // 1000), ndiff
     x = inputs.normal_vector(n, inputs.X_SEED)
     y = H.matvec(x)
