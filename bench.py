@@ -408,8 +408,11 @@ def main():
                                "nominal 152 SMs x 128 lanes x 2 x 2070 MHz = %.1f"
                                % (SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12)}
     aca_roof["frac"] = aca_roof["achieved"] / fp32_peak
-    # dominant kernel of the step: ACA phase vs the N_MVP gather launches
-    dominant = aca_roof if st["t_aca_ms"] > N_MVP * mvp_t_tile else mvp_roof
+    # dominant kernel of the step: the gather (N_MVP launches) against the
+    # longest ACA size-class kernel (one launch per class, timed on its stream)
+    aca_cls = list(st["t_aca_class_ms"])
+    aca_roof["class_ms"] = aca_cls
+    dominant = aca_roof if max(aca_cls) > N_MVP * mvp_t_tile else mvp_roof
 
     cpu = None
     if not args.no_cpu and world == 1:

@@ -150,6 +150,10 @@ typedef struct hm_stats {
     int64_t mvp_count;
     double t_mvp_ms, t_mvp_gather_ms, t_mvp_vtx_ms, t_mvp_tile_ms;
     int64_t mvp_vtx_bytes, mvp_tile_bytes;  /* algorithmic bytes per product */
+    /* last build: ACA time per block size class (class c: 2^(c+5) < max(m, n)
+       <= 2^(c+6); class 0 from 1, class 11 unbounded), CUDA events on each
+       class's stream (the classes run concurrently), summed over passes */
+    double t_aca_class_ms[12];
 } hm_stats;
 
 int hm_get_stats(hm_handle h, hm_stats* out);

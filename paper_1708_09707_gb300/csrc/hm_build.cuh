@@ -154,6 +154,12 @@ struct MvpPlan {
     const int64_t* nbase = nullptr;
     const int32_t* ncol_x = nullptr;
     int64_t n_ucols = 0, n_ncols = 0;
+    // work items of the gather: item i covers columns [x, y) of tile z's
+    // U-then-near column stream (items[i] = (z, x, y)); a tile's items are
+    // consecutive from item_ptr[tile] and each writes max_ld partial row sums
+    int64_t n_items = 0;
+    const int3* items = nullptr;
+    const int64_t* item_ptr = nullptr;
     // row tiles and their gather lists (CSR over tiles)
     int64_t n_tiles = 0;
     int max_ld = 0;                       // slice_ld of the largest tile
@@ -185,6 +191,7 @@ struct MvpTimer {
 
 // Work buffers of the product (xm, t, partial sums).
 struct MvpWork {
+    DevBuf<double> part;                  // partial row sums of the gather items
     DevBuf<double> xm64, ym64;
     DevBuf<float> xm32;
     DevBuf<double> t64, tp64;
@@ -208,6 +215,9 @@ struct MvpLists {
     DevBuf<int64_t> ucol_ptr, ubase, ncol_ptr, nbase;   // flat column streams
     DevBuf<int32_t> ucol_t, ncol_x;
     int64_t n_ucols = 0, n_ncols = 0;
+    DevBuf<int3> items;                      // gather work items
+    DevBuf<int64_t> item_ptr;
+    int64_t n_items = 0;
     int64_t n_tiles = 0, n_vitems = 0, tpart_len = 0, t_len = 0, n_multi = 0;
     int64_t n_lr = 0, n_dn = 0, u_elems = 0, near_elems = 0;
 };

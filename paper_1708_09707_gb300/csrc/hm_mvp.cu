@@ -199,10 +199,11 @@ constexpr int T2_HW = TILE_NT / 16;   // half-warps per CTA
 // (its index and its value are two dependent loads), and passes it by a
 // shuffle when the batch's data has arrived.
 template <class R, int TB, class LD, class MUL>
-__device__ __forceinline__ void tile_stream(int64_t ncols, int hw, int hl, unsigned hmask, bool act,
-                                            const LD& load_col, const MUL& mult, Acc<R> (&acc)[4])
+__device__ __forceinline__ void tile_stream(int64_t cb, int64_t ncols, int hw, int hl, unsigned hmask,
+                                            bool act, const LD& load_col, const MUL& mult,
+                                            Acc<R> (&acc)[4])
 {
-    int64_t c0 = hw;
+    int64_t c0 = cb + hw;
     R mv = (hl < TB && c0 + 16 * hl < ncols) ? mult(c0 + 16 * hl) : R(0);
     for (; c0 < ncols; c0 += 16 * TB) {
         R a[TB][4];
@@ -232,61 +233,84 @@ __device__ __forceinline__ void tile_stream(int64_t ncols, int hw, int hl, unsig
     }
 }
 
-// One CTA per row tile. The tile's U slices and its near-field slices are
-// two streams of consecutive columns (slice_ld rows each); half-warp h takes
-// columns h, h + 16, h + 32, ... of each stream, TB at a time, lane l of the
-// half-warp rows 4l .. 4l+3 of the current 64-row window with one 16-byte
-// load per column (two 8-byte loads for bfloat16 pairs). Every half-warp
-// keeps compensated sums for its four rows, adding the plain sum of every
-// four columns; the 16 partial sums of a row are added in half-warp order,
-// so the product is deterministic and the same for every TB (columns in
-// flight per half-warp, a multiple of four) and MINB (CTAs per SM), the
-// parameters the tuner picks.
+// One CTA per work item, a piece of one row tile's column stream: the tile's
+// U slices followed by its near-field slices, slice_ld rows per column.
+// Half-warp h takes the item's columns h, h + 16, h + 32, ... of each part,
+// TB at a time, lane l of the half-warp rows 4l .. 4l+3 of the current
+// 64-row window with one 16-byte load per column (two 8-byte loads for
+// bfloat16 pairs). Every half-warp keeps compensated sums for its four rows,
+// adding the plain sum of every four columns; the 16 partial sums of a row
+// are added in half-warp order into the item's partial row sums. So the
+// product is deterministic and the same for every TB (columns in flight per
+// half-warp, a multiple of four) and MINB (CTAs per SM), the parameters the
+// tuner picks.
 template <class R, int FMT, int TB, int MINB>
 __global__ void __launch_bounds__(TILE_NT, MINB)
-k_tile(MvpPlan P, const R* __restrict__ xm, const R* __restrict__ t, const double* __restrict__ x,
-       double* __restrict__ y, int accumulate)
+k_tile(MvpPlan P, const R* __restrict__ xm, const R* __restrict__ t, double* __restrict__ part)
 {
-    __shared__ double part[T2_HW][TROWS];
-    const int64_t tile = blockIdx.x;
+    __shared__ double ps[T2_HW][TROWS];
+    const int64_t item = blockIdx.x;
+    const int3 it = P.items[item];
+    const int64_t tile = it.x;
     const int hw = threadIdx.x >> 4, hl = threadIdx.x & 15;
     const unsigned hmask = 0xffffu << (threadIdx.x & 16);
-    const int64_t r0 = P.tile_row0[tile];
     const int mt = P.tile_m[tile];
     const int ld = slice_ld(mt);
     const int64_t uc0 = P.ucol_ptr[tile], nu = P.ucol_ptr[tile + 1] - uc0, ub = P.ubase[tile];
     const int64_t nc0 = P.ncol_ptr[tile], nn = P.ncol_ptr[tile + 1] - nc0, nb = P.nbase[tile];
+    // the item's part of each stream
+    const int64_t ucb = it.y < nu ? it.y : nu, uce = it.z < nu ? it.z : nu;
+    const int64_t ncb = it.y > nu ? it.y - nu : 0, nce = it.z > nu ? it.z - nu : 0;
     const R* __restrict__ US = static_cast<const R*>(P.ustore);
     const int32_t* __restrict__ ucol_t = P.ucol_t;
     const int32_t* __restrict__ ncol_x = P.ncol_x;
     const void* __restrict__ near = P.near;
+    double* __restrict__ out = part + item * P.max_ld;
     for (int rp = 0; rp < ld; rp += TROWS) {
         const int ir = rp + 4 * hl;
         const bool act = ir < ld;
         Acc<R> acc[4];
         tile_stream<R, TB>(
-            nu, hw, hl, hmask, act,
+            ucb, uce, hw, hl, hmask, act,
             [&](int64_t c, R(&o)[4]) { ld4(US + ub + c * ld + ir, o); },
             [&](int64_t c) { return t[ucol_t[uc0 + c]]; }, acc);
         tile_stream<R, TB>(
-            nn, hw, hl, hmask, act,
+            ncb, nce, hw, hl, hmask, act,
             [&](int64_t c, R(&o)[4]) { near4<R, FMT>(near, nb, c, ld, ir, o); },
             [&](int64_t c) { return xm[ncol_x[nc0 + c]]; }, acc);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) part[hw][4 * hl + i] = act ? acc[i].value() : 0.0;
+        for (int i = 0; i < 4; ++i) ps[hw][4 * hl + i] = act ? acc[i].value() : 0.0;
         __syncthreads();
         const int rows = min(TROWS, mt - rp);
         if ((int)threadIdx.x < rows) {
             double sum = 0.0;
 #pragma unroll
-            for (int q = 0; q < T2_HW; ++q) sum += part[q][threadIdx.x];
-            const int64_t row = r0 + rp + threadIdx.x;
-            const int64_t dst = P.perm[row];
-            const double sg = P.sig_row ? P.sig_row[row] : P.sigma2;
-            const double v = sum + sg * x[dst];
-            y[dst] = accumulate ? y[dst] + v : v;
+            for (int q = 0; q < T2_HW; ++q) sum += ps[q][threadIdx.x];
+            out[rp + threadIdx.x] = sum;
         }
         __syncthreads();
+    }
+}
+
+// y for every row of every tile: the tile's item sums in item order, plus
+// sigma^2 x, written in the caller's order (one warp per tile).
+__global__ void k_tile_finish(MvpPlan P, const double* __restrict__ part, const double* __restrict__ x,
+                              double* __restrict__ y, int accumulate)
+{
+    const int64_t tile = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (tile >= P.n_tiles) return;
+    const int64_t r0 = P.tile_row0[tile];
+    const int mt = P.tile_m[tile];
+    const int64_t i0 = P.item_ptr[tile], i1 = P.item_ptr[tile + 1];
+    for (int i = lane; i < mt; i += 32) {
+        double sum = 0.0;
+        for (int64_t q = i0; q < i1; ++q) sum += part[q * P.max_ld + i];
+        const int64_t row = r0 + i;
+        const int64_t dst = P.perm[row];
+        const double sg = P.sig_row ? P.sig_row[row] : P.sigma2;
+        const double v = sum + sg * x[dst];
+        y[dst] = accumulate ? y[dst] + v : v;
     }
 }
 
@@ -562,6 +586,33 @@ __global__ void k_fill_ncol(const int2* __restrict__ ent, int64_t ne, const Blk*
     for (int c = 0; c < B.n; ++c) ncol_x[ecol[e] + c] = (int32_t)(B.col0 + c);
 }
 
+// Gather work items: a tile's U-then-near column stream in pieces of at most
+// ITEM_COLS columns, so that the few tiles with very many near-field columns
+// (clusters of coincident points are mutually inadmissible) do not leave one
+// CTA streaming long after the others have finished.
+constexpr int64_t ITEM_COLS = 4096;
+
+__global__ void k_item_count(const int64_t* __restrict__ ucol_ptr, const int64_t* __restrict__ ncol_ptr,
+                             int64_t nt, int64_t* __restrict__ cnt)
+{
+    int64_t q = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (q >= nt) return;
+    const int64_t c = (ucol_ptr[q + 1] - ucol_ptr[q]) + (ncol_ptr[q + 1] - ncol_ptr[q]);
+    cnt[q] = c > 0 ? ceil_div(c, ITEM_COLS) : 1;
+}
+
+__global__ void k_item_emit(const int64_t* __restrict__ ucol_ptr, const int64_t* __restrict__ ncol_ptr,
+                            int64_t nt, const int64_t* __restrict__ off, int3* __restrict__ items)
+{
+    int64_t q = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (q >= nt) return;
+    const int64_t c = (ucol_ptr[q + 1] - ucol_ptr[q]) + (ncol_ptr[q + 1] - ncol_ptr[q]);
+    const int64_t k = c > 0 ? ceil_div(c, ITEM_COLS) : 1;
+    for (int64_t i = 0; i < k; ++i)
+        items[off[q] + i] = make_int3((int)q, (int)(i * ITEM_COLS),
+                                       (int)(c < (i + 1) * ITEM_COLS ? c : (i + 1) * ITEM_COLS));
+}
+
 }  // namespace
 
 void mvp_build_lists(const Blk* ablk, const int32_t* rank, int64_t n_adm, const Blk* dblk,
@@ -680,6 +731,20 @@ void mvp_build_lists(const Blk* ablk, const int32_t* rank, int64_t n_adm, const 
         HM_CUDA(cudaMemsetAsync(L.ucol_ptr.p, 0, (n_tiles + 1) * sizeof(int64_t), s));
         HM_CUDA(cudaMemsetAsync(L.ubase.p, 0, std::max<int64_t>(n_tiles, 1) * sizeof(int64_t), s));
     }
+    // gather work items
+    {
+        const int64_t nt = std::max<int64_t>(n_tiles, 1);
+        DevBuf<int64_t> cnt(nt, s);
+        L.item_ptr.alloc(nt + 1, s);
+        k_item_count<<<grid_for(n_tiles), NT, 0, s>>>(L.ucol_ptr.p, L.ncol_ptr.p, n_tiles, cnt.p); note_launch();
+        scan_exclusive_i64(cnt.p, L.item_ptr.p, n_tiles, L.item_ptr.p + n_tiles, s);
+        HM_CUDA(cudaMemcpyAsync(&L.n_items, L.item_ptr.p + n_tiles, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        HM_CUDA(cudaStreamSynchronize(s));
+        if (L.n_items > INT32_MAX) fail(HM_EOVERFLOW, "too many gather items");
+        L.items.alloc(std::max<int64_t>(L.n_items, 1), s);
+        k_item_emit<<<grid_for(n_tiles), NT, 0, s>>>(L.ucol_ptr.p, L.ncol_ptr.p, n_tiles, L.item_ptr.p,
+                                                     L.items.p); note_launch();
+    }
     HM_LAUNCH("descriptors");
 }
 
@@ -700,6 +765,7 @@ void mvp_relayout_u(int precision, const MvpLists& L, const Blk* ablk, const uin
 
 void mvp_alloc_work(const MvpPlan& P, MvpWork& W, cudaStream_t s)
 {
+    W.part.alloc(std::max<int64_t>(P.n_items, 1) * std::max(P.max_ld, 1), s);
     if (P.precision == HM_PREC_FP64) {
         W.xm64.alloc(std::max<int64_t>(P.Ntot, 1), s);
         W.t64.alloc(std::max<int64_t>(P.t_len, 1), s);
@@ -722,14 +788,13 @@ namespace {
 constexpr int N_TILE_VARIANTS = 3;
 
 template <class R, int FMT>
-void launch_tile(int v, const MvpPlan& P, const R* xm, const R* t, const double* x, double* y,
-                 int accumulate, cudaStream_t s)
+void launch_tile(int v, const MvpPlan& P, const R* xm, const R* t, double* part, cudaStream_t s)
 {
-    const unsigned g = (unsigned)P.n_tiles;
+    const unsigned g = (unsigned)P.n_items;
     switch (v) {
-    case 0: k_tile<R, FMT, 8, 3><<<g, TILE_NT, 0, s>>>(P, xm, t, x, y, accumulate); break;
-    case 1: k_tile<R, FMT, 16, 2><<<g, TILE_NT, 0, s>>>(P, xm, t, x, y, accumulate); break;
-    default: k_tile<R, FMT, 4, 4><<<g, TILE_NT, 0, s>>>(P, xm, t, x, y, accumulate); break;
+    case 0: k_tile<R, FMT, 8, 3><<<g, TILE_NT, 0, s>>>(P, xm, t, part); break;
+    case 1: k_tile<R, FMT, 16, 2><<<g, TILE_NT, 0, s>>>(P, xm, t, part); break;
+    default: k_tile<R, FMT, 4, 4><<<g, TILE_NT, 0, s>>>(P, xm, t, part); break;
     }
     note_launch();
 }
@@ -763,23 +828,16 @@ int tile_variant(const MvpPlan& P)
 }
 
 template <class R, int FMT>
-int tune_tile(const MvpPlan& P, const R* xm, const R* t, const double* x, double* y, int accumulate,
-              cudaStream_t s)
+int tune_tile(const MvpPlan& P, const R* xm, const R* t, double* part, cudaStream_t s)
 {
     cudaEvent_t ev[N_TILE_VARIANTS + 1];
     for (auto& e : ev) HM_CUDA(cudaEventCreate(&e));
     // a first untimed run settles caches and clocks; every run writes the
-    // same y, and with accumulate = 1 the caller's y must not be touched
-    DevBuf<double> ytmp;
-    double* yt = y;
-    if (accumulate) {
-        ytmp.alloc(P.Ntot, s);
-        yt = ytmp.p;
-    }
-    launch_tile<R, FMT>(0, P, xm, t, x, yt, 0, s);
+    // same partial sums
+    launch_tile<R, FMT>(0, P, xm, t, part, s);
     HM_CUDA(cudaEventRecord(ev[0], s));
     for (int v = 0; v < N_TILE_VARIANTS; ++v) {
-        launch_tile<R, FMT>(v, P, xm, t, x, yt, 0, s);
+        launch_tile<R, FMT>(v, P, xm, t, part, s);
         HM_CUDA(cudaEventRecord(ev[v + 1], s));
     }
     HM_CUDA(cudaEventSynchronize(ev[N_TILE_VARIANTS]));
@@ -800,7 +858,7 @@ int tune_tile(const MvpPlan& P, const R* xm, const R* t, const double* x, double
 }
 
 template <class R, int FMT>
-void run_typed(const MvpPlan& P, R* xm, R* t, R* tp, const double* x, double* y,
+void run_typed(const MvpPlan& P, R* xm, R* t, R* tp, double* part, const double* x, double* y,
                int accumulate, cudaStream_t s, MvpTimer* timer)
 {
     MvpTimer::Rec* rec = timer ? timer->begin() : nullptr;
@@ -816,8 +874,9 @@ void run_typed(const MvpPlan& P, R* xm, R* t, R* tp, const double* x, double* y,
     if (rec) HM_CUDA(cudaEventRecord(rec->e[2], s));
     if (P.n_tiles > 0) {
         int v = tile_variant(P);
-        if (v < 0) v = tune_tile<R, FMT>(P, xm, t, x, y, accumulate, s);
-        launch_tile<R, FMT>(v, P, xm, t, x, y, accumulate, s);
+        if (v < 0) v = tune_tile<R, FMT>(P, xm, t, part, s);
+        launch_tile<R, FMT>(v, P, xm, t, part, s);
+        k_tile_finish<<<grid_for(P.n_tiles * 32), NT, 0, s>>>(P, part, x, y, accumulate); note_launch();
     }
     if (rec) HM_CUDA(cudaEventRecord(rec->e[3], s));
     HM_LAUNCH("matvec");
@@ -871,21 +930,21 @@ void mvp_run(const MvpPlan& P, MvpWork& W, const double* x, double* y, int accum
              cudaStream_t s, MvpTimer* timer)
 {
     if (P.precision == HM_PREC_FP64) {
-        run_typed<double, HM_NEAR_FP64>(P, W.xm64.p, W.t64.p, W.tp64.p, x, y, accumulate, s, timer);
+        run_typed<double, HM_NEAR_FP64>(P, W.xm64.p, W.t64.p, W.tp64.p, W.part.p, x, y, accumulate, s, timer);
         return;
     }
     switch (P.near_format) {
     case HM_NEAR_FP64:
-        run_typed<float, HM_NEAR_FP64>(P, W.xm32.p, W.t32.p, W.tp32.p, x, y, accumulate, s, timer);
+        run_typed<float, HM_NEAR_FP64>(P, W.xm32.p, W.t32.p, W.tp32.p, W.part.p, x, y, accumulate, s, timer);
         break;
     case HM_NEAR_FP32:
-        run_typed<float, HM_NEAR_FP32>(P, W.xm32.p, W.t32.p, W.tp32.p, x, y, accumulate, s, timer);
+        run_typed<float, HM_NEAR_FP32>(P, W.xm32.p, W.t32.p, W.tp32.p, W.part.p, x, y, accumulate, s, timer);
         break;
     case HM_NEAR_BF16X2:
-        run_typed<float, HM_NEAR_BF16X2>(P, W.xm32.p, W.t32.p, W.tp32.p, x, y, accumulate, s, timer);
+        run_typed<float, HM_NEAR_BF16X2>(P, W.xm32.p, W.t32.p, W.tp32.p, W.part.p, x, y, accumulate, s, timer);
         break;
     default:
-        run_typed<float, HM_NEAR_BF16>(P, W.xm32.p, W.t32.p, W.tp32.p, x, y, accumulate, s, timer);
+        run_typed<float, HM_NEAR_BF16>(P, W.xm32.p, W.t32.p, W.tp32.p, W.part.p, x, y, accumulate, s, timer);
         break;
     }
 }

@@ -243,18 +243,35 @@ struct Timer {
     }
 };
 
-// Side streams for the ACA size classes, forked from and joined into s.
+// Side streams for the ACA size classes, forked from and joined into s, with
+// a pair of timing events per class.
 struct ClassStreams {
     cudaStream_t main;
     cudaStream_t st[ACA_NCLASS];
     cudaEvent_t ev[ACA_NCLASS + 1];
+    cudaEvent_t t0[ACA_NCLASS], t1[ACA_NCLASS];
+    bool timed[ACA_NCLASS] = {};
     explicit ClassStreams(cudaStream_t s) : main(s)
     {
         for (int c = 0; c < ACA_NCLASS; ++c) {
             HM_CUDA(cudaStreamCreateWithFlags(&st[c], cudaStreamNonBlocking));
             HM_CUDA(cudaEventCreateWithFlags(&ev[c], cudaEventDisableTiming));
+            HM_CUDA(cudaEventCreate(&t0[c]));
+            HM_CUDA(cudaEventCreate(&t1[c]));
         }
         HM_CUDA(cudaEventCreateWithFlags(&ev[ACA_NCLASS], cudaEventDisableTiming));
+    }
+    // add the recorded class times to ms[] (synchronises the events)
+    void collect(double* ms)
+    {
+        for (int c = 0; c < ACA_NCLASS; ++c) {
+            if (!timed[c]) continue;
+            HM_CUDA(cudaEventSynchronize(t1[c]));
+            float x = 0.f;
+            HM_CUDA(cudaEventElapsedTime(&x, t0[c], t1[c]));
+            ms[c] += x;
+            timed[c] = false;
+        }
     }
     void fork()
     {
@@ -274,6 +291,8 @@ struct ClassStreams {
             cudaStreamSynchronize(st[c]);
             cudaStreamDestroy(st[c]);
             cudaEventDestroy(ev[c]);
+            cudaEventDestroy(t0[c]);
+            cudaEventDestroy(t1[c]);
         }
         cudaEventDestroy(ev[ACA_NCLASS]);
     }
@@ -375,11 +394,16 @@ void compress(hm_handle_s& h, const uint32_t* ids, int64_t n, const int32_t* kpr
         cs.fork();
         for (int c = ACA_NCLASS - 1; c >= 0; --c) {
             int64_t lo = std::max(q0, cstart[c]), hi = std::min(q1, cend[c]);
-            if (hi > lo)
+            if (hi > lo) {
+                HM_CUDA(cudaEventRecord(cs.t0[c], cs.st[c]));
                 aca_run(h.precision, h.kp, h.X, a, order.p + lo, hi - lo, c, h.max_set_n,
                         cs.st[c]);
+                HM_CUDA(cudaEventRecord(cs.t1[c], cs.st[c]));
+                cs.timed[c] = true;
+            }
         }
         cs.join();
+        cs.collect(h.stats.t_aca_class_ms);
     };
 
     if (kpred) {
@@ -727,6 +751,9 @@ void build_sets(hm_handle_s& h, int nsets, const double* points_all, const int64
     P.near_entries = h.stats.near_entries;
     P.n_tiles = h.n_tiles;
     P.max_ld = slice_ld(h.leaf);
+    P.n_items = h.lists.n_items;
+    P.items = h.lists.items.p;
+    P.item_ptr = h.lists.item_ptr.p;
     P.tile_row0 = h.tile_row0.p;
     P.tile_m = h.tile_m.p;
     P.ucol_ptr = h.lists.ucol_ptr.p;

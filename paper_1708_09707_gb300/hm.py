@@ -56,10 +56,13 @@ class Stats(C.Structure):
                 ("aca_flops", C.c_double), ("mvp_count", C.c_int64),
                 ("t_mvp_ms", C.c_double), ("t_mvp_gather_ms", C.c_double),
                 ("t_mvp_vtx_ms", C.c_double), ("t_mvp_tile_ms", C.c_double),
-                ("mvp_vtx_bytes", C.c_int64), ("mvp_tile_bytes", C.c_int64)]
+                ("mvp_vtx_bytes", C.c_int64), ("mvp_tile_bytes", C.c_int64),
+                ("t_aca_class_ms", C.c_double * 12)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["t_aca_class_ms"] = list(self.t_aca_class_ms)
+        return d
 
 
 _lib = None
