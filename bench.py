@@ -350,6 +350,18 @@ def main():
         H32.free()
         err = float(np.linalg.norm(y32 - y64) / np.linalg.norm(y64))
 
+    # per-kernel ACA durations: one more (untimed) build with the size classes
+    # run one after another, so each class's time is its own kernels'
+    aca_serial = None
+    if world == 1:
+        mk = dict(kw)
+        if theta is not None:
+            mk["rank_model_theta"] = theta
+        Hs = hm.HMatrix(pts, w["kernel"], w["ell"], w["leaf"], w["eta"], w["eps"],
+                        precision=hm.PREC_MIXED, profile=2, **mk)
+        aca_serial = Hs.stats()["t_aca_class_ms"]
+        Hs.free()
+
     # the same mixed step without the rank model (chunked ACA passes)
     plain = None
     if theta is not None:
@@ -409,10 +421,12 @@ def main():
                                % (SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12)}
     aca_roof["frac"] = aca_roof["achieved"] / fp32_peak
     # dominant kernel of the step: the gather (N_MVP launches) against the
-    # longest ACA size-class kernel (one launch per class, timed on its stream)
-    aca_cls = list(st["t_aca_class_ms"])
-    aca_roof["class_ms"] = aca_cls
-    dominant = aca_roof if max(aca_cls) > N_MVP * mvp_t_tile else mvp_roof
+    # longest ACA size-class kernel, timed alone in the serial-classes build
+    aca_roof["class_ms_concurrent"] = list(st["t_aca_class_ms"])
+    if aca_serial is not None:
+        aca_roof["class_ms_serial"] = list(aca_serial)
+    longest_aca = max(aca_serial) if aca_serial is not None else st["t_aca_ms"]
+    dominant = aca_roof if longest_aca > N_MVP * mvp_t_tile else mvp_roof
 
     cpu = None
     if not args.no_cpu and world == 1:

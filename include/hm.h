@@ -77,7 +77,10 @@ typedef struct hm_options {
     double scratch_gb;    /* bound on ACA scratch per pass, <=0: automatic */
     void* stream;         /* cudaStream_t, NULL = legacy default stream */
     int profile;          /* 1: time every product kernel with CUDA events on
-                             the launching stream (read by hm_get_stats) */
+                             the launching stream (read by hm_get_stats);
+                             2: as 1, and run the ACA size classes one after
+                             another instead of concurrently, so that
+                             t_aca_class_ms holds each class's own duration */
     int structure_only;   /* 1: stop after the cluster tree and the leaf lists
                              (no ACA, no near field; hm_matvec is refused) */
 } hm_options;

@@ -390,15 +390,18 @@ void compress(hm_handle_s& h, const uint32_t* ids, int64_t n, const int32_t* kpr
     // every size class runs on its own stream so that the few largest blocks
     // (clusters of CTAs) overlap the many small ones
     ClassStreams cs(s);
+    // profile = 2 runs the classes one after another on the main stream, so
+    // that each class's time is its kernels' own duration
+    const bool serial = h.opt.profile == 2;
     auto run_range = [&](int64_t q0, int64_t q1) {
         cs.fork();
         for (int c = ACA_NCLASS - 1; c >= 0; --c) {
             int64_t lo = std::max(q0, cstart[c]), hi = std::min(q1, cend[c]);
             if (hi > lo) {
-                HM_CUDA(cudaEventRecord(cs.t0[c], cs.st[c]));
-                aca_run(h.precision, h.kp, h.X, a, order.p + lo, hi - lo, c, h.max_set_n,
-                        cs.st[c]);
-                HM_CUDA(cudaEventRecord(cs.t1[c], cs.st[c]));
+                cudaStream_t sc = serial ? s : cs.st[c];
+                HM_CUDA(cudaEventRecord(cs.t0[c], sc));
+                aca_run(h.precision, h.kp, h.X, a, order.p + lo, hi - lo, c, h.max_set_n, sc);
+                HM_CUDA(cudaEventRecord(cs.t1[c], sc));
                 cs.timed[c] = true;
             }
         }
