@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--workload", default=WORKLOAD)
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-paper", action="store_true",
+                   help="skip the context run in the paper's own setting (N=2^19 Halton, C=2048)")
     p.add_argument("--n", type=int, default=0,
                    help="points of a smaller case of the same workload (profiling only)")
     p.add_argument("--scratch-gb", type=float, default=0.0,
@@ -55,6 +57,64 @@ def parse():
                    help="size the ACA factor arena with the learned rank model "
                         "(trained before the timed region on other point sets)")
     return p.parse_args()
+
+
+# The paper's own GPU numbers for its setting (Sec. 6.5: N = 2^19 Halton
+# points in 2-D, exp(-r^2), C_leaf = 2048, eta = 1.5, fixed ACA rank 16,
+# FP64, factors stored: "P" mode), on one Tesla P100. Context only.
+PAPER_P100 = {"build_s": 1.3, "mvp_s": 1.7, "hardware": "1x Tesla P100 SXM2, CUDA 8.0",
+              "precision": "FP64"}
+
+
+def paper_setting(hm, inputs, n_mvp=3):
+    """Build and multiply in the paper's setting at its size, FP64 and mixed
+    (CUDA events; points and x on the device). Returns a context object."""
+    import torch
+    w = inputs.WORKLOADS["halton2d_n512k_k16"]
+    pts = torch.from_numpy(inputs.workload_points("halton2d_n512k_k16")).cuda()
+    x = torch.from_numpy(inputs.normal_vector(w["n"], inputs.X_SEED)).cuda()
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+    out = {"workload": "halton2d_n512k_k16", "n": w["n"], "d": w["d"], "kernel": "exp(-r^2)",
+           "leaf": w["leaf"], "eta": w["eta"], "aca": "fixed rank %d" % w["k_cap"],
+           "paper_p100": PAPER_P100}
+    for name, prec in (("fp64", hm.PREC_FP64), ("mixed", hm.PREC_MIXED)):
+        res = []
+        for rep in range(2):            # the first build warms up the tuner
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(stream)
+            H = hm.HMatrix(pts, w["kernel"], w["ell"], w["leaf"], w["eta"], w["eps"],
+                           precision=prec, k_cap=w["k_cap"])
+            e[1].record(stream)
+            for _ in range(n_mvp):
+                H.matvec(x, y)
+            e[2].record(stream)
+            torch.cuda.synchronize()
+            st = H.stats()
+            H.free()
+            res.append((e[0].elapsed_time(e[1]) / 1e3, e[1].elapsed_time(e[2]) / n_mvp / 1e3, st))
+        b, m, st = res[-1]
+        out[name] = {"build_s": b, "mvp_s": m,
+                     "mvp_hbm_frac": st["mvp_bytes"] / m / 1e9 / peaks()[0],
+                     "factor_bytes": st["factor_bytes"], "near_bytes": st["near_bytes"]}
+    return out
+
+
+def tile_traffic(mvp_tile_bytes):
+    """DRAM bytes of one gather launch: the ratio of traffic to algorithmic
+    bytes from the committed ncu capture, if the kernel's source is unchanged
+    since it was taken (else None)."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "k_tile_traffic.json")) as f:
+            rec = json.load(f)
+        with open(os.path.join(ROOT, "paper_1708_09707_gb300", "csrc", "hm_mvp.cu"), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+        if rec.get("source_sha256") != sha:
+            return None
+        return rec["traffic_per_algorithmic_byte"] * mvp_tile_bytes
+    except Exception:
+        return None
 
 
 def peaks():
@@ -405,7 +465,8 @@ def main():
     mvp_t = st["t_mvp_ms"] / max(st["mvp_count"], 1)
     mvp_roof = {"bound": "hbm", "kernel": "k_tile (gather: U slices + near field)",
                 "achieved": st["mvp_tile_bytes"] / (mvp_t_tile * 1e-3) / 1e9, "peak": hbm,
-                "unit": "GB/s", "traffic": None,
+                "unit": "GB/s", "traffic": tile_traffic(st["mvp_tile_bytes"]),
+                "algorithmic_bytes": st["mvp_tile_bytes"],
                 "whole_product": {"achieved": st["mvp_bytes"] / (mvp_t * 1e-3) / 1e9,
                                   "ms": mvp_t, "bytes": st["mvp_bytes"]},
                 "vtx": {"achieved": st["mvp_vtx_bytes"] / (mvp_t_vtx * 1e-3) / 1e9,
@@ -427,6 +488,10 @@ def main():
         aca_roof["class_ms_serial"] = list(aca_serial)
     longest_aca = max(aca_serial) if aca_serial is not None else st["t_aca_ms"]
     dominant = aca_roof if longest_aca > N_MVP * mvp_t_tile else mvp_roof
+
+    paper = None
+    if not args.no_paper and world == 1:
+        paper = paper_setting(hm, inputs)
 
     cpu = None
     if not args.no_cpu and world == 1:
@@ -459,6 +524,7 @@ def main():
         "gpu_launches": int(round(launches)),
         "clocks": clocks,
         "cpu_baseline": cpu,
+        "paper_setting": paper,
         "stats": {k: st[k] for k in ("n_adm", "n_dense", "sum_rank", "max_rank",
                                      "rank_cap_hits", "n_rejected", "factor_bytes",
                                      "near_bytes", "mvp_bytes", "t_structure_ms",
