@@ -129,6 +129,17 @@ const char* hm_last_error(void);
 /* Number of CUDA kernels this library has launched in the process so far. */
 uint64_t hm_kernel_launches(void);
 
+/* Launch shape of the product's gather kernel (Sec. 5.4 batched product; a
+ * tuning control, not part of the method). By default (-1) the first product
+ * of a kind on a device times every shape once and keeps the fastest for the
+ * process. shape 0..3 forces one: 0, 1, 2 = load-based streaming with 8, 16
+ * or 4 columns in flight per half-warp (3, 2 or 4 CTAs per SM), 3 = bulk-copy
+ * (TMA) pipeline into shared memory (slices of at most 64 rows; otherwise
+ * shape 0 runs). Every shape gives bit-identical products. Process-wide, not
+ * thread-safe against concurrent products. Returns HM_EINVAL for other
+ * values. */
+int hm_set_gather_shape(int shape);
+
 /* Counts, ranks and bytes of a built handle. */
 typedef struct hm_stats {
     int64_t n_points, n_nodes, n_adm, n_dense, n_tiles;

@@ -146,6 +146,14 @@ const char* hm_last_error(void) { return g_last_error.c_str(); }
 
 uint64_t hm_kernel_launches(void) { return g_launches.load(); }
 
+int hm_set_gather_shape(int shape)
+{
+    set_error("");
+    const int r = hm::mvp_force_shape(shape);
+    if (r != HM_OK) set_error("gather shape must be -1 (tuned) or 0 .. 3");
+    return r;
+}
+
 hm_handle hm_build_ex(const double* points, int64_t N, int d, int kernel, const double* params,
                       int leaf_size, double eta, double aca_eps, const hm_options* opt,
                       int* status)

@@ -160,6 +160,7 @@ struct MvpPlan {
     int64_t n_items = 0;
     const int3* items = nullptr;
     const int64_t* item_ptr = nullptr;
+    int* status = nullptr;                // device status word (bounded waits)
     // row tiles and their gather lists (CSR over tiles)
     int64_t n_tiles = 0;
     int max_ld = 0;                       // slice_ld of the largest tile
@@ -199,6 +200,9 @@ struct MvpWork {
 };
 
 void mvp_alloc_work(const MvpPlan& P, MvpWork& W, cudaStream_t s);
+// Force one launch shape of the product's gather (0 .. 3), or -1 for the
+// per-device tuner; HM_EINVAL for other values.
+int mvp_force_shape(int shape);
 // y = H x (+ sigma^2 x) for device x, y in the caller's order.
 void mvp_run(const MvpPlan& P, MvpWork& W, const double* x, double* y, int accumulate,
              cudaStream_t s, MvpTimer* timer = nullptr);

@@ -12,6 +12,7 @@
 // U slices and near-field slices a tile reads are contiguous (tile-major
 // stores), and each gather entry carries its own descriptor, so the gather
 // streams its data without dependent metadata loads.
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -257,7 +258,7 @@ k_tile(MvpPlan P, const R* __restrict__ xm, const R* __restrict__ t, double* __r
     const int mt = P.tile_m[tile];
     const int ld = slice_ld(mt);
     const int64_t uc0 = P.ucol_ptr[tile], nu = P.ucol_ptr[tile + 1] - uc0, ub = P.ubase[tile];
-    const int64_t nc0 = P.ncol_ptr[tile], nn = P.ncol_ptr[tile + 1] - nc0, nb = P.nbase[tile];
+    const int64_t nc0 = P.ncol_ptr[tile], nb = P.nbase[tile];
     // the item's part of each stream
     const int64_t ucb = it.y < nu ? it.y : nu, uce = it.z < nu ? it.z : nu;
     const int64_t ncb = it.y > nu ? it.y - nu : 0, nce = it.z > nu ? it.z - nu : 0;
@@ -289,6 +290,228 @@ k_tile(MvpPlan P, const R* __restrict__ xm, const R* __restrict__ t, double* __r
             out[rp + threadIdx.x] = sum;
         }
         __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------ bulk-copy gather
+// The same work item as k_tile, with its column streams moved into shared
+// memory by the bulk-copy (TMA) engine: a producer warp issues one
+// cp.async.bulk per chunk of 32 columns (a contiguous run of 32 slice_ld
+// entries per column) into a ring of TS stages and fetches the chunk's 32
+// multipliers; 8 consumer warps wait on the stage's mbarrier, multiply and
+// release the stage. Half-warp h takes the chunk's columns h and h + 16 (the
+// columns h, h + 16, h + 32, ... of the stream, as in k_tile), and the plain
+// sums run over the same groups of four columns, so the result is bit-for-bit
+// that of k_tile. Only for slices of at most 64 rows (one row window).
+constexpr int TS = 4;                  // stages
+constexpr int TCOL = 32;               // columns per stage
+constexpr int T3_CONS = 8;             // consumer warps
+constexpr int T3_NT = (T3_CONS + 1) * 32;
+constexpr long long MBAR_SPIN = 1ll << 24;   // try_wait rounds before giving up
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, int count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* b, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(b)),
+                 "r"(bytes)
+                 : "memory");
+}
+// Wait for the phase of the given parity to complete; false after MBAR_SPIN
+// unsuccessful rounds (each try_wait suspends for a bounded time).
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity)
+{
+    for (long long k = 0; k < MBAR_SPIN; ++k) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(smem_addr(b)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+// Global -> shared bulk copy of bytes (a multiple of 16, both addresses
+// 16-byte aligned), completing on mbarrier b.
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* b)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(b))
+        : "memory");
+}
+
+template <class R, int FMT>
+__host__ __device__ constexpr int col_bytes64()   // bytes of one 64-row column
+{
+    return FMT == HM_NEAR_FP64 ? (sizeof(R) > 8 ? 0 : 512)
+           : (sizeof(R) == 8 ? 512 : 256);
+}
+
+template <class R, int FMT>
+__global__ void __launch_bounds__(T3_NT, 2)
+k_tile_tma(MvpPlan P, const R* __restrict__ xm, const R* __restrict__ t, double* __restrict__ part)
+{
+    extern __shared__ __align__(128) unsigned char tsm[];
+    constexpr int STAGE = TCOL * col_bytes64<R, FMT>();
+    __shared__ uint64_t full[TS], empty[TS];
+    __shared__ R mult[TS][TCOL];
+    __shared__ double ps[T2_HW][TROWS];
+    __shared__ int failed;
+    const int64_t item = blockIdx.x;
+    const int3 it = P.items[item];
+    const int64_t tile = it.x;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int mt = P.tile_m[tile];
+    const int ld = slice_ld(mt);
+    const int64_t uc0 = P.ucol_ptr[tile], nu = P.ucol_ptr[tile + 1] - uc0, ub = P.ubase[tile];
+    const int64_t nc0 = P.ncol_ptr[tile], nb = P.nbase[tile];
+    const int64_t ucb = it.y < nu ? it.y : nu, uce = it.z < nu ? it.z : nu;
+    const int64_t ncb = it.y > nu ? it.y - nu : 0, nce = it.z > nu ? it.z - nu : 0;
+    const int nuch = (int)ceil_div(uce - ucb, TCOL), nnch = (int)ceil_div(nce - ncb, TCOL);
+    const int nch = nuch + nnch;
+    // bytes of one column of the U stream and of the near-field stream
+    const int ucolb = ld * (int)sizeof(R);
+    const int ncolb = FMT == HM_NEAR_FP64 ? ld * 8 : FMT == HM_NEAR_FP32 ? ld * 4
+                    : FMT == HM_NEAR_BF16X2 ? ld * 4 : ld * 2;
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < TS; ++k) {
+            mbar_init(&full[k], 32);        // the producer warp's lanes
+            mbar_init(&empty[k], T3_CONS);  // one arrival per consumer warp
+        }
+        failed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (w == T3_CONS) {
+        // ---------------- producer
+        int k = 0;
+        for (; k < nch; ++k) {
+            const int slot = k % TS;
+            if (k >= TS && !mbar_wait(&empty[slot], ((k / TS) - 1) & 1)) {
+                if (lane == 0) atomicOr(P.status, 4);
+                break;
+            }
+            const bool isu = k < nuch;
+            const int64_t c0 = isu ? ucb + (int64_t)k * TCOL : ncb + (int64_t)(k - nuch) * TCOL;
+            const int64_t cend = isu ? uce : nce;
+            const int cnt = (int)(cend - c0 < TCOL ? cend - c0 : TCOL);
+            R m = R(0);
+            if (lane < cnt) m = isu ? t[P.ucol_t[uc0 + c0 + lane]] : xm[P.ncol_x[nc0 + c0 + lane]];
+            mult[slot][lane] = m;
+            if (lane == 0) {
+                const uint32_t bytes = (uint32_t)(cnt * (isu ? ucolb : ncolb));
+                const char* src = isu
+                    ? reinterpret_cast<const char*>(static_cast<const R*>(P.ustore) + ub + c0 * ld)
+                    : static_cast<const char*>(P.near) + (int64_t)ncolb * (c0) +
+                          (FMT == HM_NEAR_BF16X2 ? 4 * nb : FMT == HM_NEAR_BF16 ? 2 * nb
+                           : FMT == HM_NEAR_FP32 ? 4 * nb : 8 * nb);
+                mbar_arrive_tx(&full[slot], bytes);
+                bulk_copy(tsm + slot * STAGE, src, bytes, &full[slot]);
+            } else {
+                mbar_arrive(&full[slot]);
+            }
+        }
+        if (k < nch) {
+            // gave up: let the copies already issued land before the CTA exits
+            for (int j = (k > TS ? k - TS : 0); j < k; ++j) mbar_wait(&full[j % TS], (j / TS) & 1);
+        }
+    } else {
+        // ---------------- consumers: half-warp h = 2w + (lane >> 4)
+        const int hw = threadIdx.x >> 4, hl = threadIdx.x & 15;
+        const int ir = 4 * hl;
+        const bool act = ir < ld;
+        Acc<R> acc[4];
+        R sg[4] = {R(0), R(0), R(0), R(0)};
+        int ing = 0;   // columns of the current group of four
+        for (int k = 0; k < nch; ++k) {
+            const int slot = k % TS;
+            if (!mbar_wait(&full[slot], (k / TS) & 1)) {
+                if (lane == 0) atomicOr(P.status, 4);
+                failed = 1;
+                break;
+            }
+            const bool isu = k < nuch;
+            const int64_t c0 = isu ? ucb + (int64_t)k * TCOL : ncb + (int64_t)(k - nuch) * TCOL;
+            const int64_t cend = isu ? uce : nce;
+            const int cnt = (int)(cend - c0 < TCOL ? cend - c0 : TCOL);
+            const unsigned char* st = tsm + slot * STAGE;
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int col = hw + 16 * e;
+                R a[4] = {R(0), R(0), R(0), R(0)};
+                if (act && col < cnt) {
+                    if (isu) {
+                        const R* q = reinterpret_cast<const R*>(st + col * ucolb) + ir;
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) a[i] = q[i];
+                    } else if (FMT == HM_NEAR_BF16X2) {
+                        const __nv_bfloat16* q = reinterpret_cast<const __nv_bfloat16*>(st + col * ncolb) + ir;
+                        const uint2 h = *reinterpret_cast<const uint2*>(q);
+                        const uint2 l = *reinterpret_cast<const uint2*>(q + ld);
+                        const float2 h0 = bf2(h.x), h1 = bf2(h.y), l0 = bf2(l.x), l1 = bf2(l.y);
+                        a[0] = (R)(h0.x + l0.x);
+                        a[1] = (R)(h0.y + l0.y);
+                        a[2] = (R)(h1.x + l1.x);
+                        a[3] = (R)(h1.y + l1.y);
+                    } else if (FMT == HM_NEAR_BF16) {
+                        const __nv_bfloat16* q = reinterpret_cast<const __nv_bfloat16*>(st + col * ncolb) + ir;
+                        const uint2 h = *reinterpret_cast<const uint2*>(q);
+                        const float2 h0 = bf2(h.x), h1 = bf2(h.y);
+                        a[0] = (R)h0.x;
+                        a[1] = (R)h0.y;
+                        a[2] = (R)h1.x;
+                        a[3] = (R)h1.y;
+                    } else if (FMT == HM_NEAR_FP32) {
+                        const float* q = reinterpret_cast<const float*>(st + col * ncolb) + ir;
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) a[i] = (R)q[i];
+                    } else {
+                        const double* q = reinterpret_cast<const double*>(st + col * ncolb) + ir;
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) a[i] = (R)q[i];
+                    }
+                }
+                const R m = mult[slot][col];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) sg[i] = fma(a[i], m, sg[i]);
+                // groups of four columns of this half-warp's sequence, as in
+                // k_tile; a stream part starts a new group
+                const bool last = (k == nuch - 1 || k == nch - 1) && e == 1;
+                if (++ing == 4 || last) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        acc[i].add(sg[i]);
+                        sg[i] = R(0);
+                    }
+                    ing = 0;
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[slot]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) ps[hw][4 * hl + i] = act ? acc[i].value() : 0.0;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < mt && !failed) {
+        double sum = 0.0;
+#pragma unroll
+        for (int q = 0; q < T2_HW; ++q) sum += ps[q][threadIdx.x];
+        part[item * P.max_ld + threadIdx.x] = sum;
     }
 }
 
@@ -785,16 +1008,32 @@ namespace {
 // tile leading dimension, log2 of the tile count) on a device times every
 // shape once on the real data and keeps the fastest for the process; all
 // shapes give bit-identical results.
-constexpr int N_TILE_VARIANTS = 3;
+constexpr int N_TILE_VARIANTS = 4;
+
+// The bulk-copy variant needs slices of at most 64 rows and 16-byte column
+// runs (every format but the single bfloat16 one).
+template <class R, int FMT>
+int tile_variants(const MvpPlan& P)
+{
+    return (P.max_ld <= TROWS && FMT != HM_NEAR_BF16) ? 4 : 3;
+}
 
 template <class R, int FMT>
 void launch_tile(int v, const MvpPlan& P, const R* xm, const R* t, double* part, cudaStream_t s)
 {
     const unsigned g = (unsigned)P.n_items;
+    if (v >= tile_variants<R, FMT>(P)) v = 0;
     switch (v) {
     case 0: k_tile<R, FMT, 8, 3><<<g, TILE_NT, 0, s>>>(P, xm, t, part); break;
     case 1: k_tile<R, FMT, 16, 2><<<g, TILE_NT, 0, s>>>(P, xm, t, part); break;
-    default: k_tile<R, FMT, 4, 4><<<g, TILE_NT, 0, s>>>(P, xm, t, part); break;
+    case 2: k_tile<R, FMT, 4, 4><<<g, TILE_NT, 0, s>>>(P, xm, t, part); break;
+    default: {
+        const int bytes = TS * TCOL * col_bytes64<R, FMT>();
+        auto kern = k_tile_tma<R, FMT>;
+        HM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+        kern<<<g, T3_NT, bytes, s>>>(P, xm, t, part);
+        break;
+    }
     }
     note_launch();
 }
@@ -819,8 +1058,12 @@ TileKey tile_key(const MvpPlan& P)
     return TileKey{dev, P.precision, P.near_format, P.max_ld, lg};
 }
 
+std::atomic<int> g_forced_shape{-1};
+
 int tile_variant(const MvpPlan& P)
 {
+    const int f = g_forced_shape.load();
+    if (f >= 0) return f;
     const TileKey k = tile_key(P);
     std::lock_guard<std::mutex> g(g_tune_mu);
     auto it = g_tune.find(k);
@@ -834,16 +1077,17 @@ int tune_tile(const MvpPlan& P, const R* xm, const R* t, double* part, cudaStrea
     for (auto& e : ev) HM_CUDA(cudaEventCreate(&e));
     // a first untimed run settles caches and clocks; every run writes the
     // same partial sums
+    const int nv = tile_variants<R, FMT>(P);
     launch_tile<R, FMT>(0, P, xm, t, part, s);
     HM_CUDA(cudaEventRecord(ev[0], s));
-    for (int v = 0; v < N_TILE_VARIANTS; ++v) {
+    for (int v = 0; v < nv; ++v) {
         launch_tile<R, FMT>(v, P, xm, t, part, s);
         HM_CUDA(cudaEventRecord(ev[v + 1], s));
     }
-    HM_CUDA(cudaEventSynchronize(ev[N_TILE_VARIANTS]));
+    HM_CUDA(cudaEventSynchronize(ev[nv]));
     int best = 0;
     float tbest = 0.f;
-    for (int v = 0; v < N_TILE_VARIANTS; ++v) {
+    for (int v = 0; v < nv; ++v) {
         float ms = 0.f;
         HM_CUDA(cudaEventElapsedTime(&ms, ev[v], ev[v + 1]));
         if (v == 0 || ms < tbest) {
@@ -925,6 +1169,13 @@ MvpTimer::~MvpTimer()
 namespace {
 
 }  // namespace
+
+int mvp_force_shape(int shape)
+{
+    if (shape < -1 || shape >= N_TILE_VARIANTS) return HM_EINVAL;
+    g_forced_shape.store(shape);
+    return HM_OK;
+}
 
 void mvp_run(const MvpPlan& P, MvpWork& W, const double* x, double* y, int accumulate,
              cudaStream_t s, MvpTimer* timer)

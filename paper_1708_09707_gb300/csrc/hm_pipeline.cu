@@ -755,6 +755,7 @@ void build_sets(hm_handle_s& h, int nsets, const double* points_all, const int64
     P.n_tiles = h.n_tiles;
     P.max_ld = slice_ld(h.leaf);
     P.n_items = h.lists.n_items;
+    P.status = h.status.p;
     P.items = h.lists.items.p;
     P.item_ptr = h.lists.item_ptr.p;
     P.tile_row0 = h.tile_row0.p;

@@ -91,6 +91,7 @@ def _declare(L):
     L.hm_options_default.argtypes = [C.POINTER(Options)]
     L.hm_last_error.restype = C.c_char_p
     L.hm_kernel_launches.restype = C.c_uint64
+    L.hm_set_gather_shape.argtypes = [C.c_int]
     L.hm_alu_peak.argtypes = [C.c_int, C.POINTER(C.c_double)]
     L.hm_build_ex.restype = _vp
     L.hm_build_ex.argtypes = [_vp, i64, C.c_int, C.c_int, _vp, C.c_int, C.c_double,
@@ -340,6 +341,11 @@ def mlp_loss_grad(theta, F, target, grad, loss=None, stream=None):
 def mlp_adam(theta, grad, m, v, t: int, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, stream=None):
     _check(lib().hm_mlp_adam(_ptr(theta), _ptr(grad), _ptr(m), _ptr(v), t, lr, b1, b2, eps,
                              _stream_ptr(stream)))
+
+
+def set_gather_shape(shape: int) -> None:
+    """Force the product gather's launch shape (0..3), or -1 to tune."""
+    _check(lib().hm_set_gather_shape(int(shape)))
 
 
 def kernel_launches() -> int:

@@ -205,3 +205,27 @@ def test_scratch_passes_same_result(hm):
     H2 = hm.HMatrix(pts, 0, 0.1, 32, 1.0, 1e-8, scratch_gb=0.002)
     assert H2.stats()["aca_passes"] > 1
     assert np.array_equal(H1.matvec(x), H2.matvec(x))
+
+
+@pytest.mark.parametrize("prec,near", [(1, "bf16x2"), (1, "fp32"), (0, "auto")])
+def test_gather_shapes_bit_identical(hm, orc, prec, near):
+    """Every launch shape of the product's gather (the load-based ones and
+    the bulk-copy pipeline) gives the same bits; all match the oracle."""
+    fmt = {"bf16x2": hm.NEAR_BF16X2, "fp32": hm.NEAR_FP32, "auto": hm.NEAR_AUTO}[near]
+    n = 20000
+    pts = _pts(n, 2, "m", seed=21)
+    x = inputs.normal_vector(n, inputs.X_SEED)
+    H = hm.HMatrix(pts, 0, 0.1, 64, 1.0, 1e-6, sigma2=0.01, precision=prec, near_format=fmt)
+    ys = []
+    try:
+        for shape in range(4):
+            hm.set_gather_shape(shape)
+            ys.append(H.matvec(x))
+    finally:
+        hm.set_gather_shape(-1)
+    for shape in range(1, 4):
+        assert np.array_equal(ys[shape], ys[0]), shape
+    O = orc.HMatrix(pts, 0, 0.1, 64, 1.0, 1e-6, sigma2=0.01)
+    assert rel(ys[0], O.matvec(x)) <= (FP64_TOL if prec == 0 else MIXED_TOL)
+    with pytest.raises(hm.HMError):
+        hm.set_gather_shape(7)
