@@ -132,12 +132,13 @@ uint64_t hm_kernel_launches(void);
 /* Launch shape of the product's gather kernel (Sec. 5.4 batched product; a
  * tuning control, not part of the method). By default (-1) the first product
  * of a kind on a device times every shape once and keeps the fastest for the
- * process. shape 0..3 forces one: 0, 1, 2 = load-based streaming with 8, 16
- * or 4 columns in flight per half-warp (3, 2 or 4 CTAs per SM), 3 = bulk-copy
- * (TMA) pipeline into shared memory (slices of at most 64 rows; otherwise
- * shape 0 runs). Every shape gives bit-identical products. Process-wide, not
- * thread-safe against concurrent products. Returns HM_EINVAL for other
- * values. */
+ * process. shape 0..4 forces one: 0, 1, 2 = load-based streaming with 8, 16
+ * or 4 columns in flight per half-warp (3, 2 or 4 CTAs per SM); 3, 4 =
+ * bulk-copy (TMA) pipeline into shared memory with stages of 32 or 64
+ * columns (slices of at most 64 rows and formats other than the single
+ * bfloat16; otherwise shape 0 runs). Every shape gives bit-identical
+ * products. Process-wide, not thread-safe against concurrent products.
+ * Returns HM_EINVAL for other values. */
 int hm_set_gather_shape(int shape);
 
 /* Counts, ranks and bytes of a built handle. */

@@ -150,7 +150,7 @@ int hm_set_gather_shape(int shape)
 {
     set_error("");
     const int r = hm::mvp_force_shape(shape);
-    if (r != HM_OK) set_error("gather shape must be -1 (tuned) or 0 .. 3");
+    if (r != HM_OK) set_error("gather shape must be -1 (tuned) or 0 .. 4");
     return r;
 }
 

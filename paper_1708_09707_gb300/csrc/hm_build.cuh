@@ -200,7 +200,7 @@ struct MvpWork {
 };
 
 void mvp_alloc_work(const MvpPlan& P, MvpWork& W, cudaStream_t s);
-// Force one launch shape of the product's gather (0 .. 3), or -1 for the
+// Force one launch shape of the product's gather (0 .. 4), or -1 for the
 // per-device tuner; HM_EINVAL for other values.
 int mvp_force_shape(int shape);
 // y = H x (+ sigma^2 x) for device x, y in the caller's order.

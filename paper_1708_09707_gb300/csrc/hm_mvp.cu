@@ -296,18 +296,18 @@ k_tile(MvpPlan P, const R* __restrict__ xm, const R* __restrict__ t, double* __r
 // ------------------------------------------------------------ bulk-copy gather
 // The same work item as k_tile, with its column streams moved into shared
 // memory by the bulk-copy (TMA) engine: a producer warp issues one
-// cp.async.bulk per chunk of 32 columns (a contiguous run of 32 slice_ld
-// entries per column) into a ring of TS stages and fetches the chunk's 32
+// cp.async.bulk per chunk of TCOL columns (a contiguous run of TCOL columns
+// of slice_ld entries) into a ring of TS stages and fetches the chunk's
 // multipliers; 8 consumer warps wait on the stage's mbarrier, multiply and
-// release the stage. Half-warp h takes the chunk's columns h and h + 16 (the
-// columns h, h + 16, h + 32, ... of the stream, as in k_tile), and the plain
-// sums run over the same groups of four columns, so the result is bit-for-bit
-// that of k_tile. Only for slices of at most 64 rows (one row window).
+// release the stage. Half-warp h takes the chunk's columns h, h + 16, ...
+// (the columns h, h + 16, h + 32, ... of the stream, as in k_tile), and the
+// plain sums run over the same groups of four columns, so the result is
+// bit-for-bit that of k_tile. Only for slices of at most 64 rows (one row
+// window).
 constexpr int TS = 4;                  // stages
-constexpr int TCOL = 32;               // columns per stage
 constexpr int T3_CONS = 8;             // consumer warps
 constexpr int T3_NT = (T3_CONS + 1) * 32;
-constexpr long long MBAR_SPIN = 1ll << 24;   // try_wait rounds before giving up
+constexpr uint64_t MBAR_LIMIT_NS = 2000000000ull;   // a wait gives up after 2 s
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p)
 {
@@ -327,11 +327,18 @@ __device__ __forceinline__ void mbar_arrive_tx(uint64_t* b, uint32_t bytes)
                  "r"(bytes)
                  : "memory");
 }
-// Wait for the phase of the given parity to complete; false after MBAR_SPIN
-// unsuccessful rounds (each try_wait suspends for a bounded time).
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for the phase of the given parity to complete; false once the wait
+// has lasted MBAR_LIMIT_NS (each try_wait itself suspends for a bounded time).
 __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity)
 {
-    for (long long k = 0; k < MBAR_SPIN; ++k) {
+    uint64_t t0 = 0;
+    for (int k = 0;; ++k) {
         uint32_t ok;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -340,8 +347,9 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity)
             : "r"(smem_addr(b)), "r"(parity)
             : "memory");
         if (ok) return true;
+        if (k == 0) t0 = global_ns();
+        else if (global_ns() - t0 > MBAR_LIMIT_NS) return false;
     }
-    return false;
 }
 // Global -> shared bulk copy of bytes (a multiple of 16, both addresses
 // 16-byte aligned), completing on mbarrier b.
@@ -361,13 +369,14 @@ __host__ __device__ constexpr int col_bytes64()   // bytes of one 64-row column
            : (sizeof(R) == 8 ? 512 : 256);
 }
 
-template <class R, int FMT>
+template <class R, int FMT, int TCOL>
 __global__ void __launch_bounds__(T3_NT, 2)
 k_tile_tma(MvpPlan P, const R* __restrict__ xm, const R* __restrict__ t, double* __restrict__ part)
 {
     extern __shared__ __align__(128) unsigned char tsm[];
     constexpr int STAGE = TCOL * col_bytes64<R, FMT>();
     __shared__ uint64_t full[TS], empty[TS];
+    static_assert(TCOL == 32 || TCOL == 64, "32 or 64 columns per stage");
     __shared__ R mult[TS][TCOL];
     __shared__ double ps[T2_HW][TROWS];
     __shared__ int failed;
@@ -409,9 +418,12 @@ k_tile_tma(MvpPlan P, const R* __restrict__ xm, const R* __restrict__ t, double*
             const int64_t c0 = isu ? ucb + (int64_t)k * TCOL : ncb + (int64_t)(k - nuch) * TCOL;
             const int64_t cend = isu ? uce : nce;
             const int cnt = (int)(cend - c0 < TCOL ? cend - c0 : TCOL);
-            R m = R(0);
-            if (lane < cnt) m = isu ? t[P.ucol_t[uc0 + c0 + lane]] : xm[P.ncol_x[nc0 + c0 + lane]];
-            mult[slot][lane] = m;
+#pragma unroll
+            for (int cc = lane; cc < TCOL; cc += 32) {
+                R m = R(0);
+                if (cc < cnt) m = isu ? t[P.ucol_t[uc0 + c0 + cc]] : xm[P.ncol_x[nc0 + c0 + cc]];
+                mult[slot][cc] = m;
+            }
             if (lane == 0) {
                 const uint32_t bytes = (uint32_t)(cnt * (isu ? ucolb : ncolb));
                 const char* src = isu
@@ -450,7 +462,7 @@ k_tile_tma(MvpPlan P, const R* __restrict__ xm, const R* __restrict__ t, double*
             const int cnt = (int)(cend - c0 < TCOL ? cend - c0 : TCOL);
             const unsigned char* st = tsm + slot * STAGE;
 #pragma unroll
-            for (int e = 0; e < 2; ++e) {
+            for (int e = 0; e < TCOL / 16; ++e) {
                 const int col = hw + 16 * e;
                 R a[4] = {R(0), R(0), R(0), R(0)};
                 if (act && col < cnt) {
@@ -490,7 +502,7 @@ k_tile_tma(MvpPlan P, const R* __restrict__ xm, const R* __restrict__ t, double*
                 for (int i = 0; i < 4; ++i) sg[i] = fma(a[i], m, sg[i]);
                 // groups of four columns of this half-warp's sequence, as in
                 // k_tile; a stream part starts a new group
-                const bool last = (k == nuch - 1 || k == nch - 1) && e == 1;
+                const bool last = (k == nuch - 1 || k == nch - 1) && e == TCOL / 16 - 1;
                 if (++ing == 4 || last) {
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
@@ -1008,14 +1020,14 @@ namespace {
 // tile leading dimension, log2 of the tile count) on a device times every
 // shape once on the real data and keeps the fastest for the process; all
 // shapes give bit-identical results.
-constexpr int N_TILE_VARIANTS = 4;
+constexpr int N_TILE_VARIANTS = 5;
 
 // The bulk-copy variant needs slices of at most 64 rows and 16-byte column
 // runs (every format but the single bfloat16 one).
 template <class R, int FMT>
 int tile_variants(const MvpPlan& P)
 {
-    return (P.max_ld <= TROWS && FMT != HM_NEAR_BF16) ? 4 : 3;
+    return (P.max_ld <= TROWS && FMT != HM_NEAR_BF16) ? 5 : 3;
 }
 
 template <class R, int FMT>
@@ -1027,9 +1039,16 @@ void launch_tile(int v, const MvpPlan& P, const R* xm, const R* t, double* part,
     case 0: k_tile<R, FMT, 8, 3><<<g, TILE_NT, 0, s>>>(P, xm, t, part); break;
     case 1: k_tile<R, FMT, 16, 2><<<g, TILE_NT, 0, s>>>(P, xm, t, part); break;
     case 2: k_tile<R, FMT, 4, 4><<<g, TILE_NT, 0, s>>>(P, xm, t, part); break;
+    case 3: {
+        const int bytes = TS * 32 * col_bytes64<R, FMT>();
+        auto kern = k_tile_tma<R, FMT, 32>;
+        HM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+        kern<<<g, T3_NT, bytes, s>>>(P, xm, t, part);
+        break;
+    }
     default: {
-        const int bytes = TS * TCOL * col_bytes64<R, FMT>();
-        auto kern = k_tile_tma<R, FMT>;
+        const int bytes = TS * 64 * col_bytes64<R, FMT>();
+        auto kern = k_tile_tma<R, FMT, 64>;
         HM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
         kern<<<g, T3_NT, bytes, s>>>(P, xm, t, part);
         break;

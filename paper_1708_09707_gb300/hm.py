@@ -344,7 +344,7 @@ def mlp_adam(theta, grad, m, v, t: int, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, str
 
 
 def set_gather_shape(shape: int) -> None:
-    """Force the product gather's launch shape (0..3), or -1 to tune."""
+    """Force the product gather's launch shape (0..4), or -1 to tune."""
     _check(lib().hm_set_gather_shape(int(shape)))
 
 

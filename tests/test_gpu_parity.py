@@ -218,12 +218,12 @@ def test_gather_shapes_bit_identical(hm, orc, prec, near):
     H = hm.HMatrix(pts, 0, 0.1, 64, 1.0, 1e-6, sigma2=0.01, precision=prec, near_format=fmt)
     ys = []
     try:
-        for shape in range(4):
+        for shape in range(5):
             hm.set_gather_shape(shape)
             ys.append(H.matvec(x))
     finally:
         hm.set_gather_shape(-1)
-    for shape in range(1, 4):
+    for shape in range(1, 5):
         assert np.array_equal(ys[shape], ys[0]), shape
     O = orc.HMatrix(pts, 0, 0.1, 64, 1.0, 1e-6, sigma2=0.01)
     assert rel(ys[0], O.matvec(x)) <= (FP64_TOL if prec == 0 else MIXED_TOL)
