@@ -295,11 +295,11 @@ k_tile(MvpPlan P, const R* __restrict__ xm, const R* __restrict__ t, double* __r
 
 // ------------------------------------------------------------ bulk-copy gather
 // The same work item as k_tile, with its column streams moved into shared
-// memory by the bulk-copy (TMA) engine: a producer warp issues one
+// memory by the bulk-copy (TMA) engine: one producer thread issues one
 // cp.async.bulk per chunk of TCOL columns (a contiguous run of TCOL columns
-// of slice_ld entries) into a ring of TS stages and fetches the chunk's
-// multipliers; 8 consumer warps wait on the stage's mbarrier, multiply and
-// release the stage. Half-warp h takes the chunk's columns h, h + 16, ...
+// of slice_ld entries) into a ring of TS stages; 8 consumer warps fetch each
+// chunk's multipliers one chunk ahead, wait on the stage's mbarrier,
+// multiply and release the stage. Half-warp h takes the chunk's columns h, h + 16, ...
 // (the columns h, h + 16, h + 32, ... of the stream, as in k_tile), and the
 // plain sums run over the same groups of four columns, so the result is
 // bit-for-bit that of k_tile. Only for slices of at most 64 rows (one row
@@ -377,7 +377,6 @@ k_tile_tma(MvpPlan P, const R* __restrict__ xm, const R* __restrict__ t, double*
     constexpr int STAGE = TCOL * col_bytes64<R, FMT>();
     __shared__ uint64_t full[TS], empty[TS];
     static_assert(TCOL == 32 || TCOL == 64, "32 or 64 columns per stage");
-    __shared__ R mult[TS][TCOL];
     __shared__ double ps[T2_HW][TROWS];
     __shared__ int failed;
     const int64_t item = blockIdx.x;
@@ -398,71 +397,86 @@ k_tile_tma(MvpPlan P, const R* __restrict__ xm, const R* __restrict__ t, double*
                     : FMT == HM_NEAR_BF16X2 ? ld * 4 : ld * 2;
     if (threadIdx.x == 0) {
         for (int k = 0; k < TS; ++k) {
-            mbar_init(&full[k], 32);        // the producer warp's lanes
+            mbar_init(&full[k], 1);         // the producer's arrival with the byte count
             mbar_init(&empty[k], T3_CONS);  // one arrival per consumer warp
         }
         failed = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
+    // chunk k: stream part, first column and column count
+    auto chunk = [&](int k, bool& isu, int64_t& c0, int& cnt) {
+        isu = k < nuch;
+        c0 = isu ? ucb + (int64_t)k * TCOL : ncb + (int64_t)(k - nuch) * TCOL;
+        const int64_t cend = isu ? uce : nce;
+        cnt = (int)(cend - c0 < TCOL ? cend - c0 : TCOL);
+    };
     if (w == T3_CONS) {
-        // ---------------- producer
-        int k = 0;
-        for (; k < nch; ++k) {
-            const int slot = k % TS;
-            if (k >= TS && !mbar_wait(&empty[slot], ((k / TS) - 1) & 1)) {
-                if (lane == 0) atomicOr(P.status, 4);
-                break;
-            }
-            const bool isu = k < nuch;
-            const int64_t c0 = isu ? ucb + (int64_t)k * TCOL : ncb + (int64_t)(k - nuch) * TCOL;
-            const int64_t cend = isu ? uce : nce;
-            const int cnt = (int)(cend - c0 < TCOL ? cend - c0 : TCOL);
-#pragma unroll
-            for (int cc = lane; cc < TCOL; cc += 32) {
-                R m = R(0);
-                if (cc < cnt) m = isu ? t[P.ucol_t[uc0 + c0 + cc]] : xm[P.ncol_x[nc0 + c0 + cc]];
-                mult[slot][cc] = m;
-            }
-            if (lane == 0) {
+        // ---------------- producer: one thread issues the copies
+        if (lane == 0) {
+            int k = 0;
+            for (; k < nch; ++k) {
+                const int slot = k % TS;
+                if (k >= TS && !mbar_wait(&empty[slot], ((k / TS) - 1) & 1)) {
+                    atomicOr(P.status, 4);
+                    break;
+                }
+                bool isu;
+                int64_t c0;
+                int cnt;
+                chunk(k, isu, c0, cnt);
                 const uint32_t bytes = (uint32_t)(cnt * (isu ? ucolb : ncolb));
                 const char* src = isu
                     ? reinterpret_cast<const char*>(static_cast<const R*>(P.ustore) + ub + c0 * ld)
-                    : static_cast<const char*>(P.near) + (int64_t)ncolb * (c0) +
+                    : static_cast<const char*>(P.near) + (int64_t)ncolb * c0 +
                           (FMT == HM_NEAR_BF16X2 ? 4 * nb : FMT == HM_NEAR_BF16 ? 2 * nb
                            : FMT == HM_NEAR_FP32 ? 4 * nb : 8 * nb);
                 mbar_arrive_tx(&full[slot], bytes);
                 bulk_copy(tsm + slot * STAGE, src, bytes, &full[slot]);
-            } else {
-                mbar_arrive(&full[slot]);
+            }
+            if (k < nch) {
+                // gave up: let the copies already issued land before the CTA exits
+                for (int q = (k > TS ? k - TS : 0); q < k; ++q) mbar_wait(&full[q % TS], (q / TS) & 1);
             }
         }
-        if (k < nch) {
-            // gave up: let the copies already issued land before the CTA exits
-            for (int j = (k > TS ? k - TS : 0); j < k; ++j) mbar_wait(&full[j % TS], (j / TS) & 1);
-        }
     } else {
-        // ---------------- consumers: half-warp h = 2w + (lane >> 4)
+        // ---------------- consumers: half-warp hw = 2w + (lane >> 4)
         const int hw = threadIdx.x >> 4, hl = threadIdx.x & 15;
+        const unsigned hmask = 0xffffu << (threadIdx.x & 16);
         const int ir = 4 * hl;
         const bool act = ir < ld;
+        constexpr int E = TCOL / 16;   // columns per half-warp and chunk
+        // lane hl < E of the half-warp fetches the multiplier of the chunk's
+        // column hw + 16 hl, one chunk ahead
+        auto fetch = [&](int k) -> R {
+            if (k >= nch || hl >= E) return R(0);
+            bool isu;
+            int64_t c0;
+            int cnt;
+            chunk(k, isu, c0, cnt);
+            const int col = hw + 16 * hl;
+            if (col >= cnt) return R(0);
+            return isu ? t[P.ucol_t[uc0 + c0 + col]] : xm[P.ncol_x[nc0 + c0 + col]];
+        };
         Acc<R> acc[4];
         R sg[4] = {R(0), R(0), R(0), R(0)};
         int ing = 0;   // columns of the current group of four
+        R mv = fetch(0);
         for (int k = 0; k < nch; ++k) {
             const int slot = k % TS;
+            const R mnext = fetch(k + 1);
             if (!mbar_wait(&full[slot], (k / TS) & 1)) {
                 if (lane == 0) atomicOr(P.status, 4);
                 failed = 1;
                 break;
             }
-            const bool isu = k < nuch;
-            const int64_t c0 = isu ? ucb + (int64_t)k * TCOL : ncb + (int64_t)(k - nuch) * TCOL;
-            const int64_t cend = isu ? uce : nce;
-            const int cnt = (int)(cend - c0 < TCOL ? cend - c0 : TCOL);
+            bool isu;
+            int64_t c0;
+            int cnt;
+            chunk(k, isu, c0, cnt);
             const unsigned char* st = tsm + slot * STAGE;
 #pragma unroll
-            for (int e = 0; e < TCOL / 16; ++e) {
+            for (int e = 0; e < E; ++e) {
                 const int col = hw + 16 * e;
                 R a[4] = {R(0), R(0), R(0), R(0)};
                 if (act && col < cnt) {
@@ -497,12 +511,12 @@ k_tile_tma(MvpPlan P, const R* __restrict__ xm, const R* __restrict__ t, double*
                         for (int i = 0; i < 4; ++i) a[i] = (R)q[i];
                     }
                 }
-                const R m = mult[slot][col];
+                const R m = __shfl_sync(hmask, mv, e, 16);
 #pragma unroll
                 for (int i = 0; i < 4; ++i) sg[i] = fma(a[i], m, sg[i]);
                 // groups of four columns of this half-warp's sequence, as in
                 // k_tile; a stream part starts a new group
-                const bool last = (k == nuch - 1 || k == nch - 1) && e == TCOL / 16 - 1;
+                const bool last = (k == nuch - 1 || k == nch - 1) && e == E - 1;
                 if (++ing == 4 || last) {
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
@@ -514,6 +528,7 @@ k_tile_tma(MvpPlan P, const R* __restrict__ xm, const R* __restrict__ t, double*
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[slot]);
+            mv = mnext;
         }
 #pragma unroll
         for (int i = 0; i < 4; ++i) ps[hw][4 * hl + i] = act ? acc[i].value() : 0.0;
