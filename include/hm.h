@@ -83,6 +83,13 @@ typedef struct hm_options {
                              t_aca_class_ms holds each class's own duration */
     int structure_only;   /* 1: stop after the cluster tree and the leaf lists
                              (no ACA, no near field; hm_matvec is refused) */
+    int symmetric;        /* 1: use phi(y, y') = phi(y', y): compress only the
+                             admissible leaves (tau, sigma) with tau.lo <=
+                             sigma.lo; each mirror leaf (sigma, tau) takes the
+                             same factors with U and V exchanged, so the
+                             H-matrix is symmetric and ACA does half the work.
+                             Not in the paper (its library treats the general
+                             Y1 x Y2 case, Sec. 6.1). Default 0. */
 } hm_options;
 
 typedef struct hm_handle_s* hm_handle;
@@ -134,7 +141,7 @@ uint64_t hm_kernel_launches(void);
  * of a kind on a device times every shape once and keeps the fastest for the
  * process. shape 0..4 forces one: 0, 1, 2 = load-based streaming with 8, 16
  * or 4 columns in flight per half-warp (3, 2 or 4 CTAs per SM); 3, 4 =
- * bulk-copy (TMA) pipeline into shared memory with stages of 32 or 64
+ * bulk-copy (TMA) pipeline into shared memory with 6 or 4 stages of 64
  * columns (slices of at most 64 rows and formats other than the single
  * bfloat16; otherwise shape 0 runs). Every shape gives bit-identical
  * products. Process-wide, not thread-safe against concurrent products.

@@ -84,6 +84,7 @@ def _declare(L):
     L.or_compress_range.argtypes = [C.c_void_p, C.c_int64, C.c_int64,
                                     C.c_double, C.c_int, C.c_double, C.c_double]
     L.or_free.argtypes = [C.c_void_p]
+    L.or_mirror_transposed.argtypes = [C.c_void_p]
     for f in ("or_n_adm", "or_n_dense", "or_n_nodes"):
         getattr(L, f).restype = C.c_int64
         getattr(L, f).argtypes = [C.c_void_p]
@@ -221,7 +222,7 @@ class HMatrix:
     def __init__(self, pts, kernel: int, ell: float, leaf: int, eta: float,
                  aca_eps: float, sigma2: float = 0.0, adm_max: bool = False,
                  k_cap: int = 64, aca_eta: float = 0.0, eps0: float = 0.0,
-                 compress: bool = True):
+                 compress: bool = True, symmetric: bool = False):
         self.pts = _f64(pts)
         self.n, self.d = self.pts.shape
         self.kernel, self.ell, self.leaf, self.eta = kernel, ell, leaf, eta
@@ -232,6 +233,8 @@ class HMatrix:
             self._h = L.or_build(_p(self.pts), self.n, self.d, kernel, _p(prm),
                                  leaf, eta, int(adm_max), aca_eps, k_cap,
                                  aca_eta, eps0)
+            if symmetric:
+                L.or_mirror_transposed(self._h)
         else:
             self._h = L.or_build_structure(_p(self.pts), self.n, self.d, kernel,
                                            _p(prm), leaf, eta, int(adm_max))

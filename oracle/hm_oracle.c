@@ -558,6 +558,40 @@ void or_compress_range(or_hmat* h, int64_t b0, int64_t b1, double aca_eps,
     }
 }
 
+/* Symmetric kernels, phi(y, y') = phi(y', y), give A(sigma, tau) =
+ * A(tau, sigma)^T, and the block tree of Alg. 1 holds both leaves. This
+ * replaces the factors of every admissible leaf with lo[tau] > lo[sigma] by
+ * those of its mirror leaf (sigma, tau) with U and V exchanged, so that the
+ * H-matrix is exactly symmetric. Leaves are in (lo[tau], lo[sigma]) order, so
+ * the mirror of a leaf is found by binary search. */
+void or_mirror_transposed(or_hmat* h)
+{
+    for (int64_t b = 0; b < h->n_adm; ++b) {
+        const int64_t tl = h->lo[h->adm[b].tau], sl = h->lo[h->adm[b].sigma];
+        if (tl <= sl) continue;
+        int64_t a = 0, z = h->n_adm - 1;
+        while (a < z) {
+            const int64_t mid = (a + z) / 2;
+            const int64_t mt = h->lo[h->adm[mid].tau], ms = h->lo[h->adm[mid].sigma];
+            if (mt < sl || (mt == sl && ms < tl)) a = mid + 1;
+            else z = mid;
+        }
+        const int64_t mb = a;
+        if (h->lo[h->adm[mb].tau] != sl || h->lo[h->adm[mb].sigma] != tl) continue;
+        const int64_t m = h->hi[h->adm[b].tau] - tl, n = h->hi[h->adm[b].sigma] - sl;
+        const int r = h->rank[mb];
+        /* U_b (m x r) = V_mb (its n = m rows), V_b (n x r) = U_mb */
+        memcpy(h->Ust + h->offU[b], h->Vst + h->offV[mb], (size_t)m * r * sizeof(double));
+        memcpy(h->Vst + h->offV[b], h->Ust + h->offU[mb], (size_t)n * r * sizeof(double));
+        for (int l = 0; l < r; ++l) {
+            h->pivI[h->offP[b] + l] = h->pivJ[h->offP[mb] + l];
+            h->pivJ[h->offP[b] + l] = h->pivI[h->offP[mb] + l];
+        }
+        h->rank[b] = r;
+        h->rej[b] = 0;
+    }
+}
+
 or_hmat* or_build(const double* pts, int64_t N, int d, int kernel,
                   const double* params, int C, double eta, int adm_max,
                   double aca_eps, int k_cap, double aca_eta, double eps0)

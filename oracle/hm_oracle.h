@@ -91,6 +91,11 @@ void or_free(or_hmat* h);
 or_hmat* or_build_structure(const double* pts, int64_t N, int d, int kernel,
                             const double* params, int C, double eta, int adm_max);
 
+/* Symmetric kernels: every admissible leaf (sigma, tau) with lo[sigma] >
+ * lo[tau] takes the factors of (tau, sigma) with U and V exchanged (call
+ * after compression of all leaves). */
+void or_mirror_transposed(or_hmat* h);
+
 /* ACA of admissible leaves [b0, b1) only (builds the factors of those). */
 void or_compress_range(or_hmat* h, int64_t b0, int64_t b1, double aca_eps,
                        int k_cap, double aca_eta, double eps0);

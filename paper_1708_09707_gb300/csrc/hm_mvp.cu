@@ -304,7 +304,6 @@ k_tile(MvpPlan P, const R* __restrict__ xm, const R* __restrict__ t, double* __r
 // plain sums run over the same groups of four columns, so the result is
 // bit-for-bit that of k_tile. Only for slices of at most 64 rows (one row
 // window).
-constexpr int TS = 4;                  // stages
 constexpr int T3_CONS = 8;             // consumer warps
 constexpr int T3_NT = (T3_CONS + 1) * 32;
 constexpr uint64_t MBAR_LIMIT_NS = 2000000000ull;   // a wait gives up after 2 s
@@ -369,7 +368,7 @@ __host__ __device__ constexpr int col_bytes64()   // bytes of one 64-row column
            : (sizeof(R) == 8 ? 512 : 256);
 }
 
-template <class R, int FMT, int TCOL>
+template <class R, int FMT, int TCOL, int TS>
 __global__ void __launch_bounds__(T3_NT, 2)
 k_tile_tma(MvpPlan P, const R* __restrict__ xm, const R* __restrict__ t, double* __restrict__ part)
 {
@@ -1055,15 +1054,15 @@ void launch_tile(int v, const MvpPlan& P, const R* xm, const R* t, double* part,
     case 1: k_tile<R, FMT, 16, 2><<<g, TILE_NT, 0, s>>>(P, xm, t, part); break;
     case 2: k_tile<R, FMT, 4, 4><<<g, TILE_NT, 0, s>>>(P, xm, t, part); break;
     case 3: {
-        const int bytes = TS * 32 * col_bytes64<R, FMT>();
-        auto kern = k_tile_tma<R, FMT, 32>;
+        const int bytes = 6 * 64 * col_bytes64<R, FMT>();
+        auto kern = k_tile_tma<R, FMT, 64, 6>;
         HM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
         kern<<<g, T3_NT, bytes, s>>>(P, xm, t, part);
         break;
     }
     default: {
-        const int bytes = TS * 64 * col_bytes64<R, FMT>();
-        auto kern = k_tile_tma<R, FMT, 64>;
+        const int bytes = 4 * 64 * col_bytes64<R, FMT>();
+        auto kern = k_tile_tma<R, FMT, 64, 4>;
         HM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
         kern<<<g, T3_NT, bytes, s>>>(P, xm, t, part);
         break;

@@ -108,6 +108,52 @@ __global__ void k_classes(const Blk* __restrict__ blk, const uint32_t* __restric
     atomicAdd((unsigned long long*)&cls_count[c], 1ull);
 }
 
+// Symmetric kernels: leaf b is canonical when its rows start no later than
+// its columns; the others are mirrors of a canonical leaf.
+__global__ void k_canon_flag(const Blk* __restrict__ blk, int64_t n, int64_t* __restrict__ f)
+{
+    int64_t b = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (b < n) f[b] = blk[b].row0 <= blk[b].col0 ? 1 : 0;
+}
+
+__global__ void k_canon_ids(const int64_t* __restrict__ f, const int64_t* __restrict__ off, int64_t n,
+                            uint32_t* __restrict__ ids)
+{
+    int64_t b = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (b < n && f[b]) ids[off[b]] = (uint32_t)b;
+}
+
+// A mirror leaf (sigma, tau) takes the factors of (tau, sigma) with U and V
+// exchanged. The leaves are in (row0, col0) order, so its partner is found by
+// binary search; a missing partner (not possible for a symmetric block tree)
+// sets the status word.
+__global__ void k_mirror(const Blk* __restrict__ blk, int64_t n, uint64_t* __restrict__ Uptr,
+                         uint64_t* __restrict__ Vptr, int32_t* __restrict__ rank,
+                         int32_t* __restrict__ nrej, int32_t* __restrict__ flags, int* status)
+{
+    int64_t b = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (b >= n) return;
+    const Blk B = blk[b];
+    if (B.row0 <= B.col0) return;
+    int64_t lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        const Blk M = blk[mid];
+        if (M.row0 < B.col0 || (M.row0 == B.col0 && M.col0 < B.row0)) lo = mid + 1;
+        else hi = mid;
+    }
+    const Blk M = blk[lo];
+    if (M.row0 != B.col0 || M.col0 != B.row0) {
+        atomicOr(status, 8);
+        return;
+    }
+    Uptr[b] = Vptr[lo];
+    Vptr[b] = Uptr[lo];
+    rank[b] = rank[lo];
+    nrej[b] = 0;
+    flags[b] = flags[lo];
+}
+
 // Reserved entries of block order[q]: total kres (m + n) and the U part kres m.
 __global__ void k_reserve(const Blk* __restrict__ blk, const uint32_t* __restrict__ order,
                           int64_t n, const int32_t* __restrict__ kres, int64_t* __restrict__ res,
@@ -705,8 +751,27 @@ void build_sets(hm_handle_s& h, int nsets, const double* points_all, const int64
             kpred.alloc(std::max<int64_t>(h.n_adm, 1), s);
             predict_ranks(h, kpred.p);
         }
-        compress(h, nullptr, h.n_adm, opt.rank_model ? kpred.p : nullptr);
-        if (opt.rank_model) rerun_mispredicted(h);
+        if (opt.symmetric && h.n_adm > 0) {
+            // compress the canonical leaves only, then mirror
+            const int64_t n = h.n_adm;
+            DevBuf<int64_t> f(n, s), off(n + 1, s);
+            k_canon_flag<<<grid_for(n), NT, 0, s>>>(h.ablk.p, n, f.p); note_launch();
+            scan_exclusive_i64(f.p, off.p, n, off.p + n, s);
+            int64_t nc = 0;
+            HM_CUDA(cudaMemcpyAsync(&nc, off.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            HM_CUDA(cudaStreamSynchronize(s));
+            DevBuf<uint32_t> ids(std::max<int64_t>(nc, 1), s);
+            k_canon_ids<<<grid_for(n), NT, 0, s>>>(f.p, off.p, n, ids.p); note_launch();
+            HM_LAUNCH("canonical leaves");
+            compress(h, ids.p, nc, opt.rank_model ? kpred.p : nullptr);
+            if (opt.rank_model) rerun_mispredicted(h);
+            k_mirror<<<grid_for(n), NT, 0, s>>>(h.ablk.p, n, h.Uptr.p, h.Vptr.p, h.rank.p, h.nrej.p,
+                                                h.flags.p, h.status.p); note_launch();
+            HM_LAUNCH("mirror leaves");
+        } else {
+            compress(h, nullptr, h.n_adm, opt.rank_model ? kpred.p : nullptr);
+            if (opt.rank_model) rerun_mispredicted(h);
+        }
         check_status(h);
         h.stats.t_aca_ms = ta.stop_ms();
     }

@@ -36,7 +36,7 @@ class Options(C.Structure):
                 ("accumulate", C.c_int), ("rank_model", C.c_int),
                 ("rank_model_theta", C.c_void_p), ("scratch_gb", C.c_double),
                 ("stream", C.c_void_p), ("profile", C.c_int),
-                ("structure_only", C.c_int)]
+                ("structure_only", C.c_int), ("symmetric", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -151,7 +151,7 @@ def _stream_ptr(stream):
 
 def options(precision=PREC_FP64, near_format=NEAR_AUTO, adm_max=False, k_cap=64,
             aca_eta=0.0, eps0=0.0, accumulate=False, rank_model_theta=None,
-            scratch_gb=0.0, stream=None, profile=False,
+            scratch_gb=0.0, stream=None, profile=False, symmetric=False,
             structure_only=False) -> Options:
     o = Options()
     lib().hm_options_default(C.byref(o))
@@ -167,6 +167,7 @@ def options(precision=PREC_FP64, near_format=NEAR_AUTO, adm_max=False, k_cap=64,
     o.scratch_gb = scratch_gb
     o.stream = _stream_ptr(stream)
     o.profile = int(profile)
+    o.symmetric = int(symmetric)
     o.structure_only = int(structure_only)
     return o
 

@@ -34,7 +34,7 @@ def test_options_and_stats_layout():
     o = hm.options()
     assert o.k_cap == 64 and o.precision == hm.PREC_FP64
     # struct sizes match the C layout (offsets are natural alignment)
-    assert ctypes.sizeof(hm.Options) == 72
+    assert ctypes.sizeof(hm.Options) == 80
     assert ctypes.sizeof(hm.Stats) == (8 * 5 + 4 * 2 + 8 + 8 + 8 * 9 + 8 * 4 + 4 * 3 + 4
                                        + 8 + 8 + 8 + 8 * 4 + 8 * 2 + 8 * 12)
 

@@ -229,3 +229,32 @@ def test_gather_shapes_bit_identical(hm, orc, prec, near):
     assert rel(ys[0], O.matvec(x)) <= (FP64_TOL if prec == 0 else MIXED_TOL)
     with pytest.raises(hm.HMError):
         hm.set_gather_shape(7)
+
+
+@pytest.mark.parametrize("case", [(6000, 2, "m", 0, 0.1, 64, 1.0, 1e-8),
+                                  (5000, 3, "u", 1, 0.2, 32, 1.0, 1e-6)],
+                         ids=["mix2d", "matern3d"])
+def test_symmetric_mode(hm, orc, case):
+    """Compressing only the leaves with tau.lo <= sigma.lo and mirroring the
+    rest: FP64 equals the oracle's mirrored H-matrix to 1e-10, the operator
+    is symmetric to rounding, and mixed precision stays within 1e-5 of the
+    oracle."""
+    n, d, kind, kern, ell, leaf, eta, eps = case
+    pts = _pts(n, d, kind)
+    x = inputs.normal_vector(n, inputs.X_SEED)
+    z = inputs.normal_vector(n, 91)
+    O = orc.HMatrix(pts, kern, ell, leaf, eta, eps, symmetric=True)
+    H = hm.HMatrix(pts, kern, ell, leaf, eta, eps, symmetric=True)
+    y = H.matvec(x)
+    assert rel(y, O.matvec(x)) <= FP64_TOL
+    assert abs(z @ y - x @ H.matvec(z)) <= 1e-13 * np.linalg.norm(y) * np.linalg.norm(z)
+    s = H.structure()
+    oranks, _ = O.ranks()
+    assert int((s["ranks"] != oranks).sum()) <= max(1, len(oranks) // 1000)
+    Hm = hm.HMatrix(pts, kern, ell, leaf, eta, eps, symmetric=True, precision=hm.PREC_MIXED)
+    On = orc.HMatrix(pts, kern, ell, leaf, eta, eps)
+    assert rel(Hm.matvec(x), On.matvec(x)) <= MIXED_TOL
+    st = Hm.stats()
+    # only the canonical leaves reserve factor storage
+    assert st["reserved_factor_entries"] < 0.6 * hm.HMatrix(
+        pts, kern, ell, leaf, eta, eps, precision=hm.PREC_MIXED).stats()["reserved_factor_entries"]

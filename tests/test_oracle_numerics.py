@@ -167,6 +167,39 @@ def test_matvec_config1_against_brute_force(orc):
     assert abs(z @ y - x @ h.matvec(z)) <= 10 * w["eps"] * np.linalg.norm(yb) * np.linalg.norm(z)
 
 
+def test_symmetric_mirror_is_exactly_symmetric(orc):
+    """Mirroring the transposed leaves (phi symmetric) makes the H-matrix
+    symmetric to rounding, keeps it within the ACA accuracy of the dense
+    product, and gives each mirror leaf the transposed factors of its
+    partner (U and V exchanged, the same rank)."""
+    w = inputs.WORKLOADS["gauss2d_n4096"]
+    pts = inputs.workload_points("gauss2d_n4096")
+    x = inputs.normal_vector(w["n"], inputs.X_SEED)
+    z = inputs.normal_vector(w["n"], 77)
+    h = orc.HMatrix(pts, w["kernel"], w["ell"], w["leaf"], w["eta"], w["eps"],
+                    adm_max=True, symmetric=True)
+    y = h.matvec(x)
+    yb = orc.dense_matvec(pts, w["kernel"], w["ell"], 0.0, x)
+    assert _rel(y, yb) <= 10 * w["eps"]
+    hz = h.matvec(z)
+    assert abs(z @ y - x @ hz) <= 1e-13 * np.linalg.norm(y) * np.linalg.norm(z)
+    lo, hi, _, _ = h.tree()
+    A = h.adm_leaves()
+    r, _ = h.ranks()
+    key = {(int(lo[t]), int(lo[s])): b for b, (t, s) in enumerate(A)}
+    checked = 0
+    for b, (t, s) in enumerate(A):
+        if lo[t] <= lo[s] or checked >= 25:
+            continue
+        mb = key[(int(lo[s]), int(lo[t]))]
+        U, V = h.factors(b)
+        Um, Vm = h.factors(mb)
+        assert r[b] == r[mb]
+        assert np.array_equal(U, Vm) and np.array_equal(V, Um)
+        checked += 1
+    assert checked > 0
+
+
 def test_matvec_fixed_rank_converges_geometrically(orc):
     # Sec. 6.3: e_rel decays exponentially in the fixed ACA rank k
     pts = inputs.uniform_points(2048, 2, 33)
