@@ -53,6 +53,11 @@ def parse():
                    help="points of a smaller case of the same workload (profiling only)")
     p.add_argument("--scratch-gb", type=float, default=0.0,
                    help="cap on the ACA scratch of the plain (no rank model) build")
+    p.add_argument("--gather-shape", type=int, default=-1,
+                   help="launch shape of the product's gather (hm_set_gather_shape); -1 = tuned")
+    p.add_argument("--symmetric", default="on", choices=["on", "off"],
+                   help="mixed-precision builds compress only the leaves with tau <= sigma "
+                        "and mirror the rest (the kernels are symmetric)")
     p.add_argument("--rank-model", default="on", choices=["on", "off"],
                    help="size the ACA factor arena with the learned rank model "
                         "(trained before the timed region on other point sets)")
@@ -307,6 +312,7 @@ def main():
     if not os.path.exists(hbuild.LIB):
         hbuild.build()
     from paper_1708_09707_gb300 import hm, inputs
+    hm.set_gather_shape(args.gather_shape)
     w = dict(inputs.WORKLOADS[args.workload])
     if args.n:
         w["n"] = args.n
@@ -332,10 +338,16 @@ def main():
                       "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1],
                       "train_sets": [dict(s) for s in rank_model.TRAIN_SETS]}
 
-    def step(prec, ev=None, profile=False, model=True):
+    # mixed-precision builds use the kernels' symmetry (compress the leaves
+    # with tau.lo <= sigma.lo, mirror the rest); the FP64 path stays the
+    # paper's plain method
+    use_sym = args.symmetric == "on"
+
+    def step(prec, ev=None, profile=False, model=True, sym=None):
         if ev:
             ev[0].record(stream)
         mk = dict(kw)
+        mk["symmetric"] = (use_sym if sym is None else sym) and prec == hm.PREC_MIXED
         if model and theta is not None:
             mk["rank_model_theta"] = theta
         H = hm.HMatrix(pts, w["kernel"], w["ell"], w["leaf"], w["eta"], w["eps"],
@@ -350,9 +362,9 @@ def main():
         H.free()
         return st
 
-    def timed(prec, steps, warmup, profile, model=True):
+    def timed(prec, steps, warmup, profile, model=True, sym=None):
         for _ in range(warmup):
-            step(prec, model=model)
+            step(prec, model=model, sym=sym)
         torch.cuda.synchronize()
         barrier()
         torch.cuda.synchronize()
@@ -366,7 +378,7 @@ def main():
                                    "compare_%s" % ("mixed_plain" if prec == hm.PREC_MIXED else "fp64"))
         t0.record(stream)
         for k in range(steps):
-            stats.append(step(prec, evs[k], profile, model))
+            stats.append(step(prec, evs[k], profile, model, sym))
         t1.record(stream)
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
@@ -405,7 +417,7 @@ def main():
         if theta is not None:
             mk["rank_model_theta"] = theta
         H32 = hm.HMatrix(pts, w["kernel"], w["ell"], w["leaf"], w["eta"], w["eps"],
-                         precision=hm.PREC_MIXED, **mk)
+                         precision=hm.PREC_MIXED, symmetric=use_sym, **mk)
         y32 = H32.matvec(x).cpu().numpy()
         H32.free()
         err = float(np.linalg.norm(y32 - y64) / np.linalg.norm(y64))
@@ -418,7 +430,7 @@ def main():
         if theta is not None:
             mk["rank_model_theta"] = theta
         Hs = hm.HMatrix(pts, w["kernel"], w["ell"], w["leaf"], w["eta"], w["eps"],
-                        precision=hm.PREC_MIXED, profile=2, **mk)
+                        precision=hm.PREC_MIXED, profile=2, symmetric=use_sym, **mk)
         aca_serial = Hs.stats()["t_aca_class_ms"]
         Hs.free()
 
@@ -429,6 +441,13 @@ def main():
         plain = {"build_s": bp / 1e3, "mvp_ms": mp, "ms_per_step": tp,
                  "aca_ms": sp[-1]["t_aca_ms"], "aca_passes": sp[-1]["aca_passes"],
                  "reserved_factor_entries": sp[-1]["reserved_factor_entries"]}
+
+    # the same mixed step without the symmetry (every admissible leaf compressed)
+    nonsym = None
+    if use_sym:
+        tn, bn, mn, sn, _ = timed(hm.PREC_MIXED, 1, 1, False, sym=False)
+        nonsym = {"build_s": bn / 1e3, "mvp_ms": mn, "ms_per_step": tn,
+                  "aca_ms": sn[-1]["t_aca_ms"]}
 
     # e2e: the same step through the C-ABI with pinned host buffers
     pts_h = torch.from_numpy(pts_np).pin_memory()
@@ -444,7 +463,7 @@ def main():
         mk["rank_model_theta"] = theta
     for _ in range(e2e_steps):
         H = hm.HMatrix(pts_h, w["kernel"], w["ell"], w["leaf"], w["eta"], w["eps"],
-                       precision=hm.PREC_MIXED, **mk)
+                       precision=hm.PREC_MIXED, symmetric=use_sym, **mk)
         for _ in range(N_MVP):
             H.matvec(xs_h, ys_h)
         H.free()
@@ -509,13 +528,14 @@ def main():
                    "points": w["points"], "kernel": "gaussian" if w["kernel"] == 0 else "matern32",
                    "ell": w["ell"], "leaf": w["leaf"], "eta": w["eta"], "aca_eps": w["eps"],
                    "precision": "mixed (FP32 ACA + FP64 stopping test, BF16 hi/lo near field)",
-                   "rank_model": args.rank_model,
+                   "rank_model": args.rank_model, "symmetric": use_sym,
                    "mvp_per_step": N_MVP, "l2": "inputs larger than L2 (product streams "
                    "%.1f GB per call)" % (st["mvp_bytes"] / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
         "build_s": build_ms / 1e3, "mvp_ms": mvp_ms,
         "fp64": fp64, "mixed_vs_fp64_rel_err": err,
-        "mixed_without_rank_model": plain, "rank_model": model_info,
+        "mixed_without_rank_model": plain, "mixed_nonsymmetric": nonsym,
+        "rank_model": model_info,
         "speedup_vs_fp64": (fp64["ms_per_step"] / total) if fp64 else None,
         "e2e": {"value": e2e_ms / 1e3, "unit": "s/step (build + %d H-MVP)" % N_MVP,
                 "h2d_bytes_per_step": N * d * 8 + N_MVP * N * 8,
