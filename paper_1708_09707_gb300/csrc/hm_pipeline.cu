@@ -790,7 +790,9 @@ void build_sets(hm_handle_s& h, int nsets, const double* points_all, const int64
         h.ustore.alloc((size_t)std::max<int64_t>(L.u_elems, 1) * esz, s);
         mvp_relayout_u(h.precision, L, h.ablk.p, h.Uptr.p, h.tile_m.p, h.ustore.p, s);
         HM_CUDA(cudaStreamSynchronize(s));
-        h.usegments.clear();   // the per-block U copies are no longer needed
+        // the per-block U copies are no longer needed, unless mirror leaves
+        // read their V from them (symmetric mode)
+        if (!opt.symmetric) h.usegments.clear();
         h.stats.near_entries = L.near_elems;
         h.stats.t_dense_ms = td.stop_ms();
     }
