@@ -109,7 +109,9 @@ __global__ void k_classes(const Blk* __restrict__ blk, const uint32_t* __restric
 }
 
 // Symmetric kernels: leaf b is canonical when its rows start no later than
-// its columns; the others are mirrors of a canonical leaf.
+// its columns; the others are mirrors of a canonical leaf, marked in flags
+// (no ACA of their own, no reservation; they still count in the product).
+constexpr int MIRROR_FLAG = 4;
 __global__ void k_canon_flag(const Blk* __restrict__ blk, int64_t n, int64_t* __restrict__ f)
 {
     int64_t b = (int64_t)blockIdx.x * NT + threadIdx.x;
@@ -151,7 +153,7 @@ __global__ void k_mirror(const Blk* __restrict__ blk, int64_t n, uint64_t* __res
     Vptr[b] = Uptr[lo];
     rank[b] = rank[lo];
     nrej[b] = 0;
-    flags[b] = flags[lo];
+    flags[b] = MIRROR_FLAG;
 }
 
 // Reserved entries of block order[q]: total kres (m + n) and the U part kres m.
@@ -242,16 +244,17 @@ __global__ void k_rank_stats(const Blk* __restrict__ blk, const int32_t* __restr
     unsigned long long s[NSTAT] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     if (b < n) {
         const unsigned long long r = rank[b], m = blk[b].m, nn = blk[b].n;
+        const bool own = !(flags[b] & MIRROR_FLAG);   // compressed by its own ACA
         s[0] = r;
         s[1] = r;
-        s[2] = (flags[b] & 2) ? 1 : 0;
-        s[3] = (flags[b] & 1) ? 1 : 0;
-        s[4] = nrej[b];
+        s[2] = own && (flags[b] & 2) ? 1 : 0;
+        s[3] = own && (flags[b] & 1) ? 1 : 0;
+        s[4] = own ? nrej[b] : 0;
         s[5] = r * (m + nn);
-        s[6] = (unsigned long long)kres[b] * (m + nn);
+        s[6] = own ? (unsigned long long)kres[b] * (m + nn) : 0ull;
         s[7] = r * m;
-        s[8] = r * (m + nn) + (unsigned long long)nrej[b] * m;
-        s[9] = r ? 2ull * r * (r - 1) * (m + nn) : 0ull;
+        s[8] = own ? r * (m + nn) + (unsigned long long)nrej[b] * m : 0ull;
+        s[9] = own && r ? 2ull * r * (r - 1) * (m + nn) : 0ull;
     }
     for (int o = 16; o > 0; o >>= 1)
         for (int k = 0; k < NSTAT; ++k) {
