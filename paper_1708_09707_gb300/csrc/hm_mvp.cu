@@ -86,66 +86,6 @@ k_vtx(const Blk* __restrict__ blk, const int32_t* __restrict__ rank,
         if (lane == 0) out[l] = s;
     }
 }
-// The same work as k_vtx in persistent warps: warp w takes the items w, w +
-// W, w + 2W, ... (W warps in the grid) and loads the next item's descriptor
-// (its block, rank, V address, output slot) while the current one streams,
-// so the dependent metadata loads are off the critical path.
-template <class R>
-__global__ void __launch_bounds__(VT_NT)
-k_vtx_p(const Blk* __restrict__ blk, const int32_t* __restrict__ rank,
-        const uint64_t* __restrict__ Vptr, const int2* __restrict__ items, int64_t nitems,
-        const int64_t* __restrict__ dst, const R* __restrict__ xm, R* __restrict__ t,
-        R* __restrict__ tp)
-{
-    struct Item {
-        int c0, k, n;
-        int64_t col0, d;
-        const R* V;
-    };
-    const int lane = threadIdx.x & 31;
-    const int64_t w0 = ((int64_t)blockIdx.x * VT_NT + threadIdx.x) >> 5;
-    const int64_t W = ((int64_t)gridDim.x * VT_NT) >> 5;
-    auto load = [&](int64_t w) {
-        Item q;
-        const int2 it = items[w];
-        const Blk B = blk[it.x];
-        q.c0 = it.y;
-        q.k = rank[it.x];
-        q.n = B.n;
-        q.col0 = B.col0;
-        q.V = reinterpret_cast<const R*>(Vptr[it.x]);
-        q.d = dst[w];
-        return q;
-    };
-    if (w0 >= nitems) return;
-    Item cur = load(w0);
-    for (int64_t w = w0; w < nitems; w += W) {
-        const bool more = w + W < nitems;
-        Item nxt = cur;
-        if (more) nxt = load(w + W);
-        const int cn = min(VCH, cur.n - cur.c0);
-        R xs[VCH / 32];
-#pragma unroll
-        for (int q = 0; q < VCH / 32; ++q) {
-            const int jj = lane + 32 * q;
-            xs[q] = (jj < cn) ? xm[cur.col0 + cur.c0 + jj] : R(0);
-        }
-        R* out = cur.d >= 0 ? tp + cur.d : t + (-cur.d - 1);
-        for (int l = 0; l < cur.k; ++l) {
-            const R* Vl = cur.V + (int64_t)l * cur.n + cur.c0;
-            R s = 0;
-#pragma unroll
-            for (int q = 0; q < VCH / 32; ++q) {
-                const int jj = lane + 32 * q;
-                if (jj < cn) s += __ldcs(Vl + jj) * xs[q];
-            }
-            s = warp_sum(s);
-            if (lane == 0) out[l] = s;
-        }
-        cur = nxt;
-    }
-}
-
 // Sum the partials of blocks that span several column chunks (fixed order).
 template <class R>
 __global__ void k_tsum(const int32_t* __restrict__ multi, int64_t nmulti,
@@ -1202,14 +1142,9 @@ void run_typed(const MvpPlan& P, R* xm, R* t, R* tp, double* part, const double*
     if (rec) HM_CUDA(cudaEventRecord(rec->e[0], s));
     k_gather_x<R><<<grid_for(P.Ntot), NT, 0, s>>>(x, P.perm, P.Ntot, xm); note_launch();
     if (rec) HM_CUDA(cudaEventRecord(rec->e[1], s));
-    if (P.n_vitems > 0) {
-        static int occ = 0;
-        if (occ == 0) HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_vtx_p<R>, VT_NT, 0));
-        const int64_t need = ceil_div(P.n_vitems * 32, VT_NT);
-        const unsigned g = (unsigned)std::min<int64_t>(need, (int64_t)std::max(occ, 1) * num_sms());
-        k_vtx_p<R><<<g, VT_NT, 0, s>>>(P.ablk, P.rank, P.Vptr, P.vitems, P.n_vitems, P.tpart_off,
-                                       xm, t, tp); note_launch();
-    }
+    if (P.n_vitems > 0)
+        k_vtx<R><<<grid_for(P.n_vitems * 32, VT_NT), VT_NT, 0, s>>>(
+            P.ablk, P.rank, P.Vptr, P.vitems, P.n_vitems, P.tpart_off, xm, t, tp); note_launch();
     if (P.n_multi > 0)
         k_tsum<R><<<(unsigned)P.n_multi, 64, 0, s>>>(P.multi, P.n_multi, P.rank, P.tsum_first,
                                                      P.tsum_count, P.tpart_off, P.toff, tp, t); note_launch();
