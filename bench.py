@@ -264,6 +264,10 @@ def run_reference(args):
         return
     from paper_1708_09707_gb300 import inputs
     w = inputs.WORKLOADS[args.workload]
+    if "n" not in w:
+        print(json.dumps({"impl": "reference", "unavailable":
+                          "the CPU oracle estimate covers single point-set workloads only"}))
+        return
     vals = []
     sample = ""
     for it in range(args.warmup + args.steps):
@@ -287,26 +291,139 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+# ---------------------------------------------------------------- batch leg
+def run_batch(args):
+    """The ragged batch of 64 independent point sets (sizes log-uniform in
+    [1e4, 2^18], d in {2, 3}): one step builds this rank's sets together
+    (hm_build_batch) and multiplies them N_MVP times. With several ranks the
+    sets are sharded (longest first to the least-loaded rank) and no data
+    crosses ranks, so the total work is fixed: strong scaling."""
+    import torch
+    from paper_1708_09707_gb300 import dist as hdist
+    from paper_1708_09707_gb300 import build as hbuild
+    world, rank, local = hdist.world()
+    torch.cuda.set_device(local)
+    hdist.init("nccl", torch.device("cuda", local))
+    if not os.path.exists(hbuild.LIB):
+        hbuild.build()
+    from paper_1708_09707_gb300 import hm, inputs
+    hm.set_gather_shape(args.gather_shape)
+    w = inputs.WORKLOADS["ragged64"]
+    sizes, dims = inputs.ragged_batch_sizes(w["count"], w["seed"])
+    mine = hdist.shard_sets(sizes, world, rank)
+    sets = [inputs.uniform_points(int(sizes[q]), int(dims[q]), w["seed"] * 10 + q) for q in mine]
+    msz, mdim = sizes[mine], dims[mine]
+    flat_h = np.concatenate([p.ravel() for p in sets])
+    flat = torch.from_numpy(flat_h).cuda()
+    n = int(msz.sum())
+    x_h = inputs.normal_vector(n, inputs.X_SEED)
+    x = torch.from_numpy(x_h).cuda()
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+    opts = dict(precision=hm.PREC_MIXED, symmetric=args.symmetric == "on")
+
+    def step(ev=None, profile=False, host=False):
+        if ev:
+            ev[0].record(stream)
+        B = hm.HBatch(None, w["kernel"], w["ell"], w["leaf"], w["eta"], w["eps"],
+                      flat=flat_hp if host else flat, sizes=msz, dims=mdim, profile=profile, **opts)
+        if ev:
+            ev[1].record(stream)
+        for _ in range(N_MVP):
+            if host:
+                B.matvec(x_hp, y_hp)
+            else:
+                B.matvec(x, y)
+        if ev:
+            ev[2].record(stream)
+        st = B.stats()
+        B.free()
+        return st
+
+    flat_hp = torch.from_numpy(flat_h).pin_memory()
+    x_hp = torch.from_numpy(x_h).pin_memory()
+    y_hp = torch.empty(n, dtype=torch.float64).pin_memory()
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    hdist.barrier()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    l0 = hm.kernel_launches()
+    with ClockSampler(local) as clk:
+        torch.cuda.nvtx.range_push("timed_step")
+        t0.record(stream)
+        stats = [step(evs[k], profile=True) for k in range(args.steps)]
+        t1.record(stream)
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize()
+    clocks = clk.summary()
+    launches = (hm.kernel_launches() - l0) / args.steps
+    total = t0.elapsed_time(t1) / args.steps
+    build_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))
+    mvp_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in evs])) / N_MVP
+    hdist.barrier()
+    total, build_ms, mvp_ms = hdist.max_over_ranks([total, build_ms, mvp_ms], "cuda")
+    # e2e: host points, x and y through the C-ABI
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(max(1, min(args.steps, 3))):
+        step(host=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / max(1, min(args.steps, 3))
+    e2e_ms = hdist.max_over_ranks([e2e_ms], "cuda")[0]
+    if rank != 0:
+        hdist.finalize()
+        return
+    st = stats[-1]
+    hbm, peak_src = peaks()
+    t_tile = st["t_mvp_tile_ms"] / max(st["mvp_count"], 1)
+    roof = {"bound": "hbm", "kernel": "k_tile (gather: U slices + near field)",
+            "achieved": st["mvp_tile_bytes"] / (t_tile * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+            "traffic": tile_traffic(st["mvp_tile_bytes"]), "algorithmic_bytes": st["mvp_tile_bytes"],
+            "peak_source": peak_src + " copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+    roof["frac"] = roof["achieved"] / hbm
+    unit = "s/step (batched build of 64 sets + %d batched H-MVP)" % N_MVP
+    line = {"metric": METRIC, "value": total / 1e3, "unit": unit, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total,
+            "higher_is_better": False, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "ragged64", "sets": int(len(sizes)), "points": int(sizes.sum()),
+                       "sizes": "log-uniform in [1e4, 2^18]", "d": "2 or 3", "kernel": "gaussian",
+                       "ell": w["ell"], "leaf": w["leaf"], "eta": w["eta"], "aca_eps": w["eps"],
+                       "precision": "mixed", "symmetric": args.symmetric == "on",
+                       "mvp_per_step": N_MVP, "parallelism": "sets sharded" if world > 1 else "single"},
+            "build_s": build_ms / 1e3, "mvp_ms": mvp_ms,
+            "e2e": {"value": e2e_ms / 1e3, "unit": unit,
+                    "h2d_bytes_per_step": int(flat_h.nbytes + N_MVP * n * 8),
+                    "d2h_bytes_per_step": int(N_MVP * n * 8)},
+            "roofline": roof, "gpu_launches": int(round(launches)), "clocks": clocks,
+            "cpu_baseline": None,
+            "stats": {k: st[k] for k in ("n_adm", "n_dense", "sum_rank", "factor_bytes",
+                                         "near_bytes", "mvp_bytes", "t_aca_ms", "t_dense_ms")}}
+    print(json.dumps(line))
+    hdist.finalize()
+
+
 # ---------------------------------------------------------------- GPU leg
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
         return
+    if args.workload == "ragged64":
+        run_batch(args)
+        return
     import torch
-    import torch.distributed as dist
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_1708_09707_gb300 import dist as hdist
+    world, rank, local = hdist.world()
     torch.cuda.set_device(local)
-    if world > 1:
-        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
+    hdist.init("nccl", torch.device("cuda", local))
+    barrier = hdist.barrier
 
     from paper_1708_09707_gb300 import build as hbuild
     if not os.path.exists(hbuild.LIB):
@@ -362,7 +479,7 @@ def main():
         H.free()
         return st
 
-    def timed(prec, steps, warmup, profile, model=True, sym=None):
+    def timed(prec, steps, warmup, profile, model=True, sym=None, name="compare"):
         for _ in range(warmup):
             step(prec, model=model, sym=sym)
         torch.cuda.synchronize()
@@ -374,8 +491,7 @@ def main():
         t1 = torch.cuda.Event(enable_timing=True)
         stats = []
         # an NVTX range names the timed launches for a profiler's launch list
-        torch.cuda.nvtx.range_push("timed_step" if (prec == hm.PREC_MIXED and model) else
-                                   "compare_%s" % ("mixed_plain" if prec == hm.PREC_MIXED else "fp64"))
+        torch.cuda.nvtx.range_push(name)
         t0.record(stream)
         for k in range(steps):
             stats.append(step(prec, evs[k], profile, model, sym))
@@ -393,20 +509,17 @@ def main():
     hbm, peak_src = peaks()
     with ClockSampler(local) as clk:
         total, build_ms, mvp_ms, stats, launches = timed(hm.PREC_MIXED, args.steps,
-                                                         args.warmup, True)
+                                                         args.warmup, True, name="timed_step")
     clocks = clk.summary()
     # max over ranks
-    tot_t = torch.tensor([total, build_ms, mvp_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(tot_t, op=dist.ReduceOp.MAX)
-    total, build_ms, mvp_ms = [float(v) for v in tot_t.cpu()]
+    total, build_ms, mvp_ms = hdist.max_over_ranks([total, build_ms, mvp_ms], "cuda")
     st = stats[-1]
 
     # FP64 reference path on the same GPU (same step, fewer repetitions)
     fp64 = None
     err = None
     if not args.no_fp64:
-        t64, b64, m64, s64, _ = timed(hm.PREC_FP64, 1, 1, False, model=False)
+        t64, b64, m64, s64, _ = timed(hm.PREC_FP64, 1, 1, False, model=False, name="compare_fp64")
         fp64 = {"build_s": b64 / 1e3, "mvp_ms": m64, "ms_per_step": t64,
                 "mvp_roofline_frac": s64[-1]["mvp_bytes"] / (m64 * 1e-3) / (hbm * 1e9)}
         H64 = hm.HMatrix(pts, w["kernel"], w["ell"], w["leaf"], w["eta"], w["eps"],
@@ -437,7 +550,8 @@ def main():
     # the same mixed step without the rank model (chunked ACA passes)
     plain = None
     if theta is not None:
-        tp, bp, mp, sp, _ = timed(hm.PREC_MIXED, 1, 1, False, model=False)
+        tp, bp, mp, sp, _ = timed(hm.PREC_MIXED, 1, 1, False, model=False,
+                                  name="compare_no_rank_model")
         plain = {"build_s": bp / 1e3, "mvp_ms": mp, "ms_per_step": tp,
                  "aca_ms": sp[-1]["t_aca_ms"], "aca_passes": sp[-1]["aca_passes"],
                  "reserved_factor_entries": sp[-1]["reserved_factor_entries"]}
@@ -445,7 +559,8 @@ def main():
     # the same mixed step without the symmetry (every admissible leaf compressed)
     nonsym = None
     if use_sym:
-        tn, bn, mn, sn, _ = timed(hm.PREC_MIXED, 1, 1, False, sym=False)
+        tn, bn, mn, sn, _ = timed(hm.PREC_MIXED, 1, 1, False, sym=False,
+                                  name="compare_nonsymmetric")
         nonsym = {"build_s": bn / 1e3, "mvp_ms": mn, "ms_per_step": tn,
                   "aca_ms": sn[-1]["t_aca_ms"]}
 
@@ -474,8 +589,7 @@ def main():
     assert math.isfinite(ysum)
 
     if rank != 0:
-        if world > 1:
-            dist.destroy_process_group()
+        hdist.finalize()
         return
 
     # rooflines from the library's own CUDA events on the launching stream
@@ -552,8 +666,7 @@ def main():
                                      "n_mispredicted", "reserved_factor_entries")},
     }
     print(json.dumps(line))
-    if world > 1:
-        dist.destroy_process_group()
+    hdist.finalize()
 
 
 if __name__ == "__main__":

@@ -364,8 +364,7 @@ int hm_batch_stats(hm_batch b, hm_stats* out)
         set_error("null argument");
         return HM_EINVAL;
     }
-    *out = b->h.stats;
-    return HM_OK;
+    return hm_get_stats(&b->h, out);
 }
 
 void hm_free_batch(hm_batch b)

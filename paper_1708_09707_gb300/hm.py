@@ -273,16 +273,27 @@ class HBatch:
     """Many independent point sets built and multiplied together."""
 
     def __init__(self, point_sets, kernel: int, ell: float, leaf: int, eta: float,
-                 aca_eps: float, sigma2: float = 0.0, **opts):
+                 aca_eps: float, sigma2: float = 0.0, flat=None, sizes=None, dims=None,
+                 **opts):
+        """point_sets: list of (N_s, d_s) arrays; or None with flat (the sets
+        one after another, row-major; numpy or a host / cuda torch tensor),
+        sizes and dims."""
         L = lib()
-        self.sizes = np.array([p.shape[0] for p in point_sets], np.int64)
-        self.dims = np.array([p.shape[1] for p in point_sets], np.int32)
-        allp = np.ascontiguousarray(np.concatenate([np.asarray(p, np.float64).ravel()
-                                                    for p in point_sets]))
+        if point_sets is not None:
+            self.sizes = np.array([p.shape[0] for p in point_sets], np.int64)
+            self.dims = np.array([p.shape[1] for p in point_sets], np.int32)
+            allp = np.ascontiguousarray(np.concatenate([np.asarray(p, np.float64).ravel()
+                                                        for p in point_sets]))
+        else:
+            self.sizes = np.asarray(sizes, np.int64)
+            self.dims = np.asarray(dims, np.int32)
+            allp = flat if _is_torch(flat) else np.ascontiguousarray(flat, dtype=np.float64)
+            npt = int((self.sizes * self.dims).sum())
+            assert allp.numel() == npt if _is_torch(allp) else allp.size == npt
         self.opt = options(**opts)
         prm = np.array([ell, sigma2], dtype=np.float64)
         st = C.c_int(0)
-        self._b = L.hm_build_batch(len(point_sets), _ptr(allp), _ptr(self.sizes),
+        self._b = L.hm_build_batch(len(self.sizes), _ptr(allp), _ptr(self.sizes),
                                    _ptr(self.dims), kernel, prm.ctypes.data, leaf, eta,
                                    aca_eps, C.byref(self.opt), C.byref(st))
         if not self._b:
