@@ -41,7 +41,14 @@ constexpr int WARP_NT = 128;   // threads per CTA of the warp kernel
 constexpr int CTA_NT = 256;
 constexpr int CTA_WARPS = CTA_NT / 32;
 constexpr int KBUF = 128;      // largest supported k_cap
-constexpr int REJ_RUN = 4;     // rejected columns in a row that end a block
+// Rejected columns in a row that end a block: four in double precision (the
+// oracle's rule); two in float, where a rejected column's residual is
+// already at float resolution relative to the column.
+template <class T>
+__host__ __device__ constexpr int rej_run()
+{
+    return sizeof(T) == 4 ? 2 : 4;
+}
 constexpr int UNR = 4;         // rows (columns) per thread whose loads are issued together
 constexpr int LC = 4;          // ranks per batch of loads and dot products
 
@@ -220,9 +227,9 @@ k_aca_warp(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restric
         amax = warp_max(amax);
         if (!(best > eps0 * amax)) {
             // column already represented: take the lowest unused column,
-            // or stop after REJ_RUN rejections in a row
+            // or stop after rej_run rejections in a row
             ++rej;
-            if (++run >= REJ_RUN) {
+            if (++run >= rej_run<R>()) {
                 converged = true;
                 break;
             }
@@ -729,7 +736,7 @@ k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __rest
             const int bi = oc.ai;
             if (!(best > eps0 * amax)) {
                 ++rej;
-                if (++run >= REJ_RUN) {
+                if (++run >= rej_run<R>()) {
                     converged = true;
                     break;
                 }
@@ -1191,9 +1198,9 @@ k_aca_big(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restrict
             const BRed<T> oc = big_reduce<T, NT>(cl, CS, sh, ph, qc, r, Pv);
             if (!(oc.av > eps0 * oc.x0)) {
                 // column already represented: take the lowest unused column,
-                // or stop after REJ_RUN rejections in a row
+                // or stop after rej_run rejections in a row
                 ++rej;
-                if (++run >= REJ_RUN || oc.mn >= n) {
+                if (++run >= rej_run<T>() || oc.mn >= n) {
                     converged = true;
                     break;
                 }
