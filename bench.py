@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--workload", default=WORKLOAD)
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-multi", action="store_true",
+                   help="skip the 16-vector product measured beside the step")
     p.add_argument("--no-paper", action="store_true",
                    help="skip the context run in the paper's own setting (N=2^19 Halton, C=2048)")
     p.add_argument("--n", type=int, default=0,
@@ -569,6 +571,46 @@ def main():
         nonsym = {"build_s": bn / 1e3, "mvp_ms": mn, "ms_per_step": tn,
                   "aca_ms": sn[-1]["t_aca_ms"]}
 
+    # several right-hand sides per call (reported beside the step, not in it):
+    # a group of 16 vectors shares one pass over the stored factors and near
+    # field, against 16 one-vector products on the same handle
+    multi = None
+    if world == 1 and not args.no_multi:
+        mk = dict(kw)
+        if theta is not None:
+            mk["rank_model_theta"] = theta
+        Hm = hm.HMatrix(pts, w["kernel"], w["ell"], w["leaf"], w["eta"], w["eps"],
+                        precision=hm.PREC_MIXED, symmetric=use_sym, **mk)
+        nr = 16
+        Xr = torch.from_numpy(inputs.normal_vector(N, inputs.X_SEED + 1, nrhs=nr)).cuda()
+        Yr = torch.empty_like(Xr)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        reps = 3
+        for _ in range(2):
+            Hm.matvec(Xr, Yr)
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        for _ in range(reps):
+            Hm.matvec(Xr, Yr)
+        ev[1].record(stream)
+        for _ in range(reps):
+            for r in range(nr):
+                Hm.matvec(Xr[r], Yr[r])
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        grp_ms = ev[0].elapsed_time(ev[1]) / reps
+        one_ms = ev[1].elapsed_time(ev[2]) / reps / nr
+        sm = Hm.stats()
+        per_vec = N * 24
+        grp_bytes = sm["mvp_bytes"] - per_vec + nr * per_vec
+        multi = {"nrhs": nr, "ms_per_call": grp_ms, "ms_per_vector": grp_ms / nr,
+                 "one_vector_product_ms": one_ms, "speedup_per_vector": one_ms * nr / grp_ms,
+                 "algorithmic_bytes": grp_bytes,
+                 "achieved_gbs": grp_bytes / (grp_ms * 1e-3) / 1e9,
+                 "note": "bytes: stored factors, near field and column indices once, "
+                         "x, perm and y per vector"}
+        Hm.free()
+
     # e2e: the same step through the C-ABI with pinned host buffers
     pts_h = torch.from_numpy(pts_np).pin_memory()
     xs_h = torch.from_numpy(x_np).pin_memory()
@@ -654,6 +696,7 @@ def main():
         "build_s": build_ms / 1e3, "mvp_ms": mvp_ms,
         "fp64": fp64, "mixed_vs_fp64_rel_err": err,
         "mixed_without_rank_model": plain, "mixed_nonsymmetric": nonsym,
+        "multi_rhs": multi,
         "rank_model": model_info,
         "speedup_vs_fp64": (fp64["ms_per_step"] / total) if fp64 else None,
         "e2e": {"value": e2e_ms / 1e3, "unit": "s/step (build + %d H-MVP)" % N_MVP,

@@ -123,8 +123,15 @@ hm_handle hm_build_ex(const double* points, int64_t N, int d, int kernel,
  * handle was built with accumulate = 1. */
 int hm_matvec(hm_handle h, const double* x, double* y);
 
-/* nrhs right-hand sides stored one after another (x[r*N + i]); stream
- * overrides the handle's stream when not NULL. */
+/* nrhs right-hand sides stored one after another (x[r*N + i]), results
+ * likewise; stream overrides the handle's stream when not NULL.
+ * Mixed-precision handles whose leaf slices have at most 64 rows and whose
+ * near field is FP64, FP32 or BF16X2 multiply groups of up to 16 vectors in
+ * one pass over the stored factors and near field (Alg. 3 applied to the
+ * columns of X): a vector's result does not depend on the vectors it is
+ * grouped with, and it agrees with the one-vector product to rounding (the
+ * two sum in different orders). Other handles run one product per vector.
+ * Host x / y are copied per group of 16 vectors. */
 int hm_matvec_ex(hm_handle h, const double* x, double* y, int nrhs, void* stream);
 
 /* Release everything the handle owns. NULL-safe. */

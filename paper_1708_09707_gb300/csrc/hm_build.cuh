@@ -197,6 +197,9 @@ struct MvpWork {
     DevBuf<float> xm32;
     DevBuf<double> t64, tp64;
     DevBuf<float> t32, tp32;
+    // several right-hand sides (float plans), sized for MVP_NRC_MAX on first use
+    DevBuf<float> xmn, tn, tpn;
+    DevBuf<double> partn;
 };
 
 void mvp_alloc_work(const MvpPlan& P, MvpWork& W, cudaStream_t s);
@@ -206,6 +209,14 @@ int mvp_force_shape(int shape);
 // y = H x (+ sigma^2 x) for device x, y in the caller's order.
 void mvp_run(const MvpPlan& P, MvpWork& W, const double* x, double* y, int accumulate,
              cudaStream_t s, MvpTimer* timer = nullptr);
+// Y = H X (+ sigma^2 X) for nrhs device right-hand sides stored one after
+// another (x[r * Ntot + i]). Float plans whose slices have at most 64 rows and
+// whose near field is not single bfloat16 read every stored entry once per
+// group of up to MVP_NRC_MAX vectors; other plans run one product per vector.
+constexpr int MVP_NRC_MAX = 16;
+bool mvp_multi_fused(const MvpPlan& P);
+void mvp_run_multi(const MvpPlan& P, MvpWork& W, const double* x, double* y, int nrhs,
+                   int accumulate, cudaStream_t s);
 // Build the gather lists of the plan (CSR by tile).
 struct MvpLists {
     DevBuf<int64_t> lr_ptr, dn_ptr;

@@ -139,6 +139,36 @@ void matvec(hm_handle_s& h, const double* x, double* y, int nrhs, cudaStream_t s
         h.ybuf.alloc(N, h.stream);
         HM_CUDA(cudaStreamSynchronize(h.stream));
     }
+    if (nrhs > 1 && mvp_multi_fused(h.plan)) {
+        // groups of up to MVP_NRC_MAX vectors share one pass over the stores
+        constexpr int G = MVP_NRC_MAX;
+        const bool grow_x = !xd && h.xbuf.n < (size_t)(N * G);
+        const bool grow_y = !yd && h.ybuf.n < (size_t)(N * G);
+        if (grow_x || grow_y) {
+            HM_CUDA(cudaStreamSynchronize(s));   // earlier products may still read them
+            if (grow_x) h.xbuf.alloc(N * G, h.stream);
+            if (grow_y) h.ybuf.alloc(N * G, h.stream);
+            HM_CUDA(cudaStreamSynchronize(h.stream));
+        }
+        for (int c = 0; c < nrhs; c += G) {
+            const int nr = std::min(G, nrhs - c);
+            const size_t bytes = (size_t)nr * N * sizeof(double);
+            const double* xin = x + (int64_t)c * N;
+            double* yout = y + (int64_t)c * N;
+            if (!xd) {
+                copy_in(h.xbuf.p, xin, bytes, s);
+                xin = h.xbuf.p;
+            }
+            if (!yd) {
+                if (h.opt.accumulate) copy_in(h.ybuf.p, yout, bytes, s);
+                yout = h.ybuf.p;
+            }
+            mvp_run_multi(h.plan, h.work, xin, yout, nr, h.opt.accumulate, s);
+            if (!yd) copy_out(y + (int64_t)c * N, h.ybuf.p, bytes, s);
+        }
+        if (!yd) HM_CUDA(cudaStreamSynchronize(s));
+        return;
+    }
     for (int r = 0; r < nrhs; ++r) {
         const double* xr = x + (int64_t)r * N;
         double* yr = y + (int64_t)r * N;

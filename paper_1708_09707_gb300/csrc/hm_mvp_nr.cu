@@ -1,0 +1,488 @@
+// hm_mvp_nr.cu -- the H-matrix product for several right-hand sides at once:
+// Alg. 3 (in the batched form of Sec. 5.4) applied to the columns of X. A
+// group of up to 16 vectors shares one pass over the stored factors and near
+// field, so every stored entry is read once per group instead of once per
+// vector; the gather stays bound by HBM while the group is narrow enough for
+// the FP32 pipes.
+//
+// Layout of a group of NRC (8 or 16) vectors, a narrower group padded with
+// zero vectors: the permuted right-hand sides are point-major, xm[i*NRC + r];
+// so is t, t[(toff_b + l)*NRC + r]; the partial row sums of the gather items
+// are part[(item*max_ld + row)*NRC + r] in double.
+//
+// Summation order, the same for every vector whatever the group width and the
+// vector's place in it (the result for one vector does not depend on the
+// vectors multiplied with it):
+//  - t_b: lane j of a warp sums the columns j, j + 32, ... of a 256-column
+//    chunk of V_b in that order with fused multiply-adds; the 32 lane sums
+//    meet in the xor-butterfly tree of masks 16, 8, 4, 2, 1; the chunks of a
+//    block add in chunk order.
+//  - rows of y: column lane j (of four) takes the columns j, j + 4, ... of
+//    every 64-column chunk of the item's U stream and then of its near-field
+//    stream; the plain FP32 sum of its 16 columns of a chunk goes into a
+//    compensated accumulator; the four lane sums add in lane order in double,
+//    the items of a tile in item order, then sigma^2 x.
+#include "hm_kernel_fn.cuh"
+#include "hm_stream.cuh"
+
+namespace hm {
+
+namespace {
+
+constexpr int NT = 256;
+constexpr int VN_W = 4;          // warps per CTA of the V^T X kernel
+constexpr int TN_COL = 64;       // columns per bulk-copy chunk
+constexpr int TN_STAGES = 4;     // chunks in flight per CTA
+constexpr int TN_ROWS = 64;      // slices of at most 64 rows
+constexpr int TN_LANES = 4;      // column lanes
+
+inline unsigned grid_for(int64_t n, int nt = NT) { return (unsigned)ceil_div(n, nt); }
+
+// xm[i*NRC + r] = x[r*N + perm[i]] for r < nr, zero for the padding.
+template <int NRC>
+__global__ void k_gather_xn(const double* __restrict__ x, const int64_t* __restrict__ perm,
+                            int64_t N, int nr, float* __restrict__ xm)
+{
+    const int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (i >= N) return;
+    const int64_t p = perm[i];
+    float v[NRC];
+#pragma unroll
+    for (int r = 0; r < NRC; ++r) v[r] = r < nr ? (float)x[(int64_t)r * N + p] : 0.f;
+    float4* o = reinterpret_cast<float4*>(xm + i * NRC);
+#pragma unroll
+    for (int g = 0; g < NRC / 4; ++g) o[g] = make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
+}
+
+// Warp totals of s[0 .. NRC-1] at once. The first log2(NRC) xor steps swap
+// half of the remaining values (a lane keeps the half its lane bit selects),
+// the remaining xor steps act on one value. Every addition is one of the
+// xor-butterfly tree's, so each total is bit for bit that of a butterfly
+// over one value. The lane holds the total of vector lane >> (5 - log2 NRC).
+template <int NRC>
+__device__ __forceinline__ float warp_sum_scatter(float (&s)[NRC], int lane)
+{
+    constexpr int LG = NRC == 16 ? 4 : NRC == 8 ? 3 : NRC == 4 ? 2 : NRC == 2 ? 1 : 0;
+    static_assert((1 << LG) == NRC, "power of two up to 16");
+#pragma unroll
+    for (int st = 0; st < LG; ++st) {
+        const int m = 16 >> st;
+        const int h = NRC >> (st + 1);
+        const bool up = (lane & m) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const float send = up ? s[i] : s[h + i];
+            const float keep = up ? s[h + i] : s[i];
+            s[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+        }
+    }
+    float v = s[0];
+#pragma unroll
+    for (int m = 16 >> LG; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+    return v;
+}
+
+// t partials for NRC vectors: one warp per (block, 256-column chunk) work
+// item, its chunk of X staged in shared memory (rows padded to NRC + 4 floats
+// so that the 16-byte reads of a quarter warp hit distinct banks); lane j
+// reads the factor entries of columns j, j + 32, ... one factor column ahead.
+template <int NRC>
+__global__ void __launch_bounds__(VN_W * 32)
+k_vtx_n(const Blk* __restrict__ blk, const int32_t* __restrict__ rank,
+        const uint64_t* __restrict__ Vptr, const int2* __restrict__ items, int64_t nitems,
+        const int64_t* __restrict__ dst, const float* __restrict__ xm, float* __restrict__ t,
+        float* __restrict__ tp)
+{
+    constexpr int XS = NRC + 4;
+    constexpr int LG = NRC == 16 ? 4 : 3;
+    extern __shared__ __align__(16) float xsh[];
+    const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t w = (int64_t)blockIdx.x * VN_W + wi;
+    if (w >= nitems) return;   // no CTA-wide barrier follows
+    float* xs = xsh + wi * VCH * XS;
+    const int2 it = items[w];
+    const int b = it.x, c0 = it.y;
+    const Blk B = blk[b];
+    const int k = rank[b];
+    const int n = B.n;
+    const int cn = min(VCH, n - c0);
+    const float4* src = reinterpret_cast<const float4*>(xm + (int64_t)(B.col0 + c0) * NRC);
+    for (int q = lane; q < VCH * (NRC / 4); q += 32) {
+        const int c = q / (NRC / 4), g = q % (NRC / 4);
+        const float4 v = c < cn ? src[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        *reinterpret_cast<float4*>(xs + c * XS + 4 * g) = v;
+    }
+    __syncwarp();
+    const float* __restrict__ V = reinterpret_cast<const float*>(Vptr[b]);
+    const int64_t d = dst[w];
+    float* out = d >= 0 ? tp + d * NRC : t + (-d - 1) * NRC;
+    const int rr = lane >> (5 - LG);
+    const bool writer = (lane & ((1 << (5 - LG)) - 1)) == 0;
+    float vn[8];
+    auto loadv = [&](int l) {
+        const float* Vl = V + (int64_t)l * n + c0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int jj = lane + 32 * q;
+            vn[q] = jj < cn ? __ldcs(Vl + jj) : 0.f;
+        }
+    };
+    if (k > 0) loadv(0);
+    for (int l = 0; l < k; ++l) {
+        float vc[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) vc[q] = vn[q];
+        if (l + 1 < k) loadv(l + 1);
+        float s[NRC];
+#pragma unroll
+        for (int r = 0; r < NRC; ++r) s[r] = 0.f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const float* xr = xs + (lane + 32 * q) * XS;
+#pragma unroll
+            for (int g = 0; g < NRC / 4; ++g) {
+                const float4 xv = *reinterpret_cast<const float4*>(xr + 4 * g);
+                s[4 * g + 0] = fmaf(vc[q], xv.x, s[4 * g + 0]);
+                s[4 * g + 1] = fmaf(vc[q], xv.y, s[4 * g + 1]);
+                s[4 * g + 2] = fmaf(vc[q], xv.z, s[4 * g + 2]);
+                s[4 * g + 3] = fmaf(vc[q], xv.w, s[4 * g + 3]);
+            }
+        }
+        const float tot = warp_sum_scatter<NRC>(s, lane);
+        if (writer) out[(int64_t)l * NRC + rr] = tot;
+    }
+}
+
+// Sum the chunk partials of blocks that span several chunks (chunk order).
+template <int NRC>
+__global__ void k_tsum_n(const int32_t* __restrict__ multi, int64_t nmulti,
+                         const int32_t* __restrict__ rank, const int32_t* __restrict__ first,
+                         const int32_t* __restrict__ count, const int64_t* __restrict__ dst,
+                         const int64_t* __restrict__ toff, const float* __restrict__ tp,
+                         float* __restrict__ t)
+{
+    const int64_t q = blockIdx.x;
+    if (q >= nmulti) return;
+    const int b = multi[q];
+    const int k = rank[b];
+    const int f = first[b], cnt = count[b];
+    for (int e = threadIdx.x; e < k * NRC; e += blockDim.x) {
+        const int l = e / NRC, r = e % NRC;
+        float s = 0.f;
+        for (int c = 0; c < cnt; ++c) s += tp[(dst[f + c] + l) * NRC + r];
+        t[(toff[b] + l) * NRC + r] = s;
+    }
+}
+
+// Bytes of one 64-row column in the near-field store (U columns are float:
+// 256 bytes, never more).
+template <int FMT>
+__host__ __device__ constexpr int ncol_bytes64()
+{
+    return FMT == HM_NEAR_FP64 ? 512 : 256;
+}
+
+__device__ __forceinline__ void consumer_sync(int nthreads)
+{
+    asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+
+// One CTA per gather work item (a piece of one row tile's U-then-near column
+// stream, as in the one-vector product). A producer thread moves 64-column
+// chunks into a ring of shared-memory stages with cp.async.bulk; NRC / 2
+// consumer warps multiply them. Consumer thread (j, g, q) owns rows
+// 4q .. 4q+3, vectors 4g .. 4g+3 and the chunk columns j, j + 4, ..., and
+// fetches one float4 of next chunk's multipliers (column, vector group) into
+// a double-buffered table; a named barrier over the consumers publishes it.
+// Waits are bounded: a wait that gives up sets bit 4 of the status word, the
+// consumers leave together after their barrier, and the item writes nothing.
+template <int FMT, int NRC>
+__global__ void __launch_bounds__((NRC / 2 + 1) * 32, 2)
+k_tile_n(MvpPlan P, const float* __restrict__ xm, const float* __restrict__ t,
+         double* __restrict__ part)
+{
+    constexpr int NCW = NRC / 2;        // consumer warps
+    constexpr int NG = NRC / 4;         // vector groups of four
+    constexpr int STAGE = TN_COL * ncol_bytes64<FMT>();
+    static_assert(16 * NG * TN_LANES == NCW * 32, "one consumer per (rows, group, lane)");
+    static_assert(TN_COL * NG == NCW * 32, "one multiplier float4 per consumer");
+    extern __shared__ __align__(128) unsigned char tsm[];
+    __shared__ uint64_t full[TN_STAGES], empty[TN_STAGES];
+    __shared__ __align__(16) float msm[2][TN_COL * NRC];
+    __shared__ double ps[TN_LANES][TN_ROWS][NRC];
+    __shared__ int failed;
+    const int64_t item = blockIdx.x;
+    const int3 it = P.items[item];
+    const int64_t tile = it.x;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int mt = P.tile_m[tile];
+    const int ld = slice_ld(mt);
+    const int64_t uc0 = P.ucol_ptr[tile], nu = P.ucol_ptr[tile + 1] - uc0, ub = P.ubase[tile];
+    const int64_t nc0 = P.ncol_ptr[tile], nb = P.nbase[tile];
+    const int64_t ucb = it.y < nu ? it.y : nu, uce = it.z < nu ? it.z : nu;
+    const int64_t ncb = it.y > nu ? it.y - nu : 0, nce = it.z > nu ? it.z - nu : 0;
+    const int nuch = (int)ceil_div(uce - ucb, TN_COL), nnch = (int)ceil_div(nce - ncb, TN_COL);
+    const int nch = nuch + nnch;
+    const int ucolb = ld * 4;
+    const int ncolb = FMT == HM_NEAR_FP64 ? ld * 8 : ld * 4;
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < TN_STAGES; ++k) {
+            mbar_init(&full[k], 1);
+            mbar_init(&empty[k], NCW);
+        }
+        failed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    auto chunk = [&](int k, bool& isu, int64_t& c0, int& cnt) {
+        isu = k < nuch;
+        c0 = isu ? ucb + (int64_t)k * TN_COL : ncb + (int64_t)(k - nuch) * TN_COL;
+        const int64_t cend = isu ? uce : nce;
+        cnt = (int)(cend - c0 < TN_COL ? cend - c0 : TN_COL);
+    };
+    if (w == NCW) {
+        // ---------------- producer
+        if (lane == 0) {
+            int k = 0;
+            for (; k < nch; ++k) {
+                const int slot = k % TN_STAGES;
+                if (k >= TN_STAGES && !mbar_wait(&empty[slot], ((k / TN_STAGES) - 1) & 1)) {
+                    atomicOr(P.status, 4);
+                    break;
+                }
+                bool isu;
+                int64_t c0;
+                int cnt;
+                chunk(k, isu, c0, cnt);
+                const uint32_t bytes = (uint32_t)(cnt * (isu ? ucolb : ncolb));
+                const char* src = isu
+                    ? reinterpret_cast<const char*>(static_cast<const float*>(P.ustore) + ub + c0 * ld)
+                    : static_cast<const char*>(P.near) + (int64_t)ncolb * c0 +
+                          (FMT == HM_NEAR_FP64 ? 8 * nb : 4 * nb);
+                mbar_arrive_tx(&full[slot], bytes);
+                bulk_copy(tsm + slot * STAGE, src, bytes, &full[slot]);
+            }
+            if (k < nch) {
+                // gave up: let the copies already issued land before the CTA exits
+                for (int q = (k > TN_STAGES ? k - TN_STAGES : 0); q < k; ++q)
+                    mbar_wait(&full[q % TN_STAGES], (q / TN_STAGES) & 1);
+            }
+        }
+    } else {
+        // ---------------- consumers
+        const int tc = threadIdx.x;
+        const int rq = tc & 15, g = (tc >> 4) % NG, j = tc / (16 * NG);
+        const int ir = 4 * rq;
+        const bool act = ir < ld;
+        const int fc = tc / NG, fg = tc % NG;   // the multiplier float4 this thread fetches
+        const float4* __restrict__ t4 = reinterpret_cast<const float4*>(t);
+        const float4* __restrict__ x4 = reinterpret_cast<const float4*>(xm);
+        auto fetch = [&](int k) -> float4 {
+            float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (k >= nch) return z;
+            bool isu;
+            int64_t c0;
+            int cnt;
+            chunk(k, isu, c0, cnt);
+            if (fc >= cnt) return z;
+            return isu ? t4[(int64_t)P.ucol_t[uc0 + c0 + fc] * NG + fg]
+                       : x4[(int64_t)P.ncol_x[nc0 + c0 + fc] * NG + fg];
+        };
+        Acc<float> acc[4][4];
+        float4 mf = fetch(0);
+        reinterpret_cast<float4*>(msm[0])[tc] = mf;
+        consumer_sync(NCW * 32);
+        for (int k = 0; k < nch; ++k) {
+            const int slot = k % TN_STAGES;
+            mf = fetch(k + 1);
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(&full[slot], (k / TN_STAGES) & 1));
+            if (ok) {
+                bool isu;
+                int64_t c0;
+                int cnt;
+                chunk(k, isu, c0, cnt);
+                const unsigned char* st = tsm + slot * STAGE;
+                const float* ms = msm[k & 1];
+                float sg[4][4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) sg[i][r] = 0.f;
+#pragma unroll 4
+                for (int e = 0; e < TN_COL / TN_LANES; ++e) {
+                    const int col = j + TN_LANES * e;
+                    float a[4] = {0.f, 0.f, 0.f, 0.f};
+                    if (act && col < cnt) {
+                        if (isu) {
+                            const float4 v = *reinterpret_cast<const float4*>(st + col * ucolb + 4 * ir);
+                            a[0] = v.x;
+                            a[1] = v.y;
+                            a[2] = v.z;
+                            a[3] = v.w;
+                        } else if (FMT == HM_NEAR_BF16X2) {
+                            const __nv_bfloat16* q = reinterpret_cast<const __nv_bfloat16*>(st + col * ncolb) + ir;
+                            const uint2 h = *reinterpret_cast<const uint2*>(q);
+                            const uint2 l = *reinterpret_cast<const uint2*>(q + ld);
+                            const float2 h0 = bf2(h.x), h1 = bf2(h.y), l0 = bf2(l.x), l1 = bf2(l.y);
+                            a[0] = h0.x + l0.x;
+                            a[1] = h0.y + l0.y;
+                            a[2] = h1.x + l1.x;
+                            a[3] = h1.y + l1.y;
+                        } else if (FMT == HM_NEAR_FP32) {
+                            const float4 v = *reinterpret_cast<const float4*>(st + col * ncolb + 4 * ir);
+                            a[0] = v.x;
+                            a[1] = v.y;
+                            a[2] = v.z;
+                            a[3] = v.w;
+                        } else {
+                            const double2* q = reinterpret_cast<const double2*>(st + col * ncolb + 8 * ir);
+                            const double2 v0 = q[0], v1 = q[1];
+                            a[0] = (float)v0.x;
+                            a[1] = (float)v0.y;
+                            a[2] = (float)v1.x;
+                            a[3] = (float)v1.y;
+                        }
+                    }
+                    const float4 m = *reinterpret_cast<const float4*>(ms + col * NRC + 4 * g);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        sg[i][0] = fmaf(a[i], m.x, sg[i][0]);
+                        sg[i][1] = fmaf(a[i], m.y, sg[i][1]);
+                        sg[i][2] = fmaf(a[i], m.z, sg[i][2]);
+                        sg[i][3] = fmaf(a[i], m.w, sg[i][3]);
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) acc[i][r].add(sg[i][r]);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[slot]);
+            } else if (lane == 0) {
+                atomicOr(P.status, 4);
+                failed = 1;
+            }
+            reinterpret_cast<float4*>(msm[(k + 1) & 1])[tc] = mf;
+            consumer_sync(NCW * 32);
+            if (*(volatile int*)&failed) break;
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) ps[j][ir + i][4 * g + r] = act ? acc[i][r].value() : 0.0;
+    }
+    __syncthreads();
+    if (*(volatile int*)&failed) return;
+    for (int e = threadIdx.x; e < mt * NRC; e += blockDim.x) {
+        const int row = e / NRC, r = e % NRC;
+        double sum = 0.0;
+#pragma unroll
+        for (int q = 0; q < TN_LANES; ++q) sum += ps[q][row][r];
+        part[(item * P.max_ld + row) * NRC + r] = sum;
+    }
+}
+
+// y for every row of every tile and vector: the tile's item sums in item
+// order plus sigma^2 x, in the caller's order (one warp per tile).
+template <int NRC>
+__global__ void k_finish_n(MvpPlan P, const double* __restrict__ part, const double* __restrict__ x,
+                           double* __restrict__ y, int nr, int accumulate)
+{
+    const int64_t tile = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (tile >= P.n_tiles) return;
+    const int64_t N = P.Ntot;
+    const int64_t r0 = P.tile_row0[tile];
+    const int mt = P.tile_m[tile];
+    const int64_t i0 = P.item_ptr[tile], i1 = P.item_ptr[tile + 1];
+    for (int e = lane; e < mt * NRC; e += 32) {
+        const int i = e / NRC, r = e % NRC;
+        if (r >= nr) continue;
+        double sum = 0.0;
+        for (int64_t q = i0; q < i1; ++q) sum += part[(q * P.max_ld + i) * NRC + r];
+        const int64_t row = r0 + i;
+        const int64_t dst = P.perm[row] + (int64_t)r * N;
+        const double sg = P.sig_row ? P.sig_row[row] : P.sigma2;
+        const double v = sum + sg * x[dst];
+        y[dst] = accumulate ? y[dst] + v : v;
+    }
+}
+
+template <int FMT, int NRC>
+void run_group(const MvpPlan& P, MvpWork& W, const double* x, double* y, int nr, int accumulate,
+               cudaStream_t s)
+{
+    k_gather_xn<NRC><<<grid_for(P.Ntot), NT, 0, s>>>(x, P.perm, P.Ntot, nr, W.xmn.p);
+    note_launch();
+    if (P.n_vitems > 0) {
+        const int smem = VN_W * VCH * (NRC + 4) * (int)sizeof(float);
+        auto kv = k_vtx_n<NRC>;
+        HM_CUDA(cudaFuncSetAttribute(kv, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        kv<<<(unsigned)ceil_div(P.n_vitems, VN_W), VN_W * 32, smem, s>>>(
+            P.ablk, P.rank, P.Vptr, P.vitems, P.n_vitems, P.tpart_off, W.xmn.p, W.tn.p, W.tpn.p);
+        note_launch();
+    }
+    if (P.n_multi > 0) {
+        k_tsum_n<NRC><<<(unsigned)P.n_multi, 128, 0, s>>>(P.multi, P.n_multi, P.rank, P.tsum_first,
+                                                         P.tsum_count, P.tpart_off, P.toff, W.tpn.p,
+                                                         W.tn.p);
+        note_launch();
+    }
+    if (P.n_tiles > 0) {
+        const int smem = TN_STAGES * TN_COL * ncol_bytes64<FMT>();
+        auto kt = k_tile_n<FMT, NRC>;
+        HM_CUDA(cudaFuncSetAttribute(kt, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        kt<<<(unsigned)P.n_items, (NRC / 2 + 1) * 32, smem, s>>>(P, W.xmn.p, W.tn.p, W.partn.p);
+        note_launch();
+        k_finish_n<NRC><<<grid_for(P.n_tiles * 32), NT, 0, s>>>(P, W.partn.p, x, y, nr, accumulate);
+        note_launch();
+    }
+    HM_LAUNCH("matvec (several vectors)");
+}
+
+template <int NRC>
+void run_group_fmt(const MvpPlan& P, MvpWork& W, const double* x, double* y, int nr,
+                   int accumulate, cudaStream_t s)
+{
+    switch (P.near_format) {
+    case HM_NEAR_FP64: run_group<HM_NEAR_FP64, NRC>(P, W, x, y, nr, accumulate, s); break;
+    case HM_NEAR_FP32: run_group<HM_NEAR_FP32, NRC>(P, W, x, y, nr, accumulate, s); break;
+    default: run_group<HM_NEAR_BF16X2, NRC>(P, W, x, y, nr, accumulate, s); break;
+    }
+}
+
+}  // namespace
+
+bool mvp_multi_fused(const MvpPlan& P)
+{
+    return P.precision != HM_PREC_FP64 && P.max_ld <= TN_ROWS &&
+           (P.near_format == HM_NEAR_FP64 || P.near_format == HM_NEAR_FP32 ||
+            P.near_format == HM_NEAR_BF16X2);
+}
+
+void mvp_run_multi(const MvpPlan& P, MvpWork& W, const double* x, double* y, int nrhs,
+                   int accumulate, cudaStream_t s)
+{
+    const int64_t N = P.Ntot;
+    if (!mvp_multi_fused(P)) {
+        for (int r = 0; r < nrhs; ++r)
+            mvp_run(P, W, x + (int64_t)r * N, y + (int64_t)r * N, accumulate, s, nullptr);
+        return;
+    }
+    constexpr int G = MVP_NRC_MAX;
+    if (!W.xmn.p) {
+        W.xmn.alloc(std::max<int64_t>(N, 1) * G, s);
+        W.tn.alloc(std::max<int64_t>(P.t_len, 1) * G, s);
+        W.tpn.alloc(std::max<int64_t>(P.tpart_len, 1) * G, s);
+        W.partn.alloc(std::max<int64_t>(P.n_items, 1) * std::max(P.max_ld, 1) * G, s);
+    }
+    for (int c = 0; c < nrhs; c += G) {
+        const int nr = std::min(G, nrhs - c);
+        const double* xc = x + (int64_t)c * N;
+        double* yc = y + (int64_t)c * N;
+        if (nr <= 8) run_group_fmt<8>(P, W, xc, yc, nr, accumulate, s);
+        else run_group_fmt<16>(P, W, xc, yc, nr, accumulate, s);
+    }
+}
+
+}  // namespace hm
