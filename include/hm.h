@@ -90,6 +90,16 @@ typedef struct hm_options {
                              H-matrix is symmetric and ACA does half the work.
                              Not in the paper (its library treats the general
                              Y1 x Y2 case, Sec. 6.1). Default 0. */
+    int on_the_fly;       /* 1: store no factors and no near field: every
+                             hm_matvec recomputes the ACA factors of the
+                             admissible leaves in passes of consecutive leaves
+                             (bounded by scratch_gb) and applies them at once,
+                             and evaluates the dense leaves inside the product
+                             (the paper's non-precomputed mode, Sec. 5.4).
+                             For point sets whose stored H-matrix does not fit
+                             the GPU. Not with symmetric, rank_model or
+                             hm_build_batch; several right-hand sides run one
+                             product each. Default 0. */
 } hm_options;
 
 typedef struct hm_handle_s* hm_handle;

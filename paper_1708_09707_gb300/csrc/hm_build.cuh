@@ -217,6 +217,22 @@ constexpr int MVP_NRC_MAX = 16;
 bool mvp_multi_fused(const MvpPlan& P);
 void mvp_run_multi(const MvpPlan& P, MvpWork& W, const double* x, double* y, int nrhs,
                    int accumulate, cudaStream_t s);
+// Kernels of the on-the-fly product (no stored factors or near field).
+void np_gather_x(int precision, const double* x, const int64_t* perm, int64_t N, void* xm,
+                 cudaStream_t s);
+// t_b = V_b^T x|sigma, then y_m += U_b t_b for the admissible leaves
+// b0 <= b < b1 (factors as left by ACA), in block order per row tile.
+void np_lowrank(int precision, const Blk* ablk, const int32_t* rank, const uint64_t* Uptr,
+                const uint64_t* Vptr, int64_t b0, int64_t b1, const int64_t* lr_ptr,
+                const int2* lr_ent, const int64_t* tile_row0, const int32_t* tile_m,
+                int64_t n_tiles, const void* xm, void* t, int kcap, double* yacc, cudaStream_t s);
+// y_m += A_b x|sigma for every dense leaf, entries evaluated on the fly.
+void np_near(int precision, const KernelParams& kp, const DeviceCoords& X, const Blk* dblk,
+             const int64_t* dn_ptr, const int2* dn_ent, const int64_t* tile_row0,
+             const int32_t* tile_m, int64_t n_tiles, const void* xm, double* yacc, cudaStream_t s);
+// y[perm[i]] = y_m[i] + sigma^2 x[perm[i]] (or +=).
+void np_finish(const int64_t* perm, const double* sig_row, double sigma2, int64_t N,
+               const double* yacc, const double* x, double* y, int accumulate, cudaStream_t s);
 // Build the gather lists of the plan (CSR by tile).
 struct MvpLists {
     DevBuf<int64_t> lr_ptr, dn_ptr;

@@ -139,7 +139,7 @@ void matvec(hm_handle_s& h, const double* x, double* y, int nrhs, cudaStream_t s
         h.ybuf.alloc(N, h.stream);
         HM_CUDA(cudaStreamSynchronize(h.stream));
     }
-    if (nrhs > 1 && mvp_multi_fused(h.plan)) {
+    if (nrhs > 1 && !h.opt.on_the_fly && mvp_multi_fused(h.plan)) {
         // groups of up to MVP_NRC_MAX vectors share one pass over the stores
         constexpr int G = MVP_NRC_MAX;
         const bool grow_x = !xd && h.xbuf.n < (size_t)(N * G);
@@ -182,7 +182,8 @@ void matvec(hm_handle_s& h, const double* x, double* y, int nrhs, cudaStream_t s
             if (h.opt.accumulate) copy_in(h.ybuf.p, yr, N * sizeof(double), s);
             yout = h.ybuf.p;
         }
-        mvp_run(h.plan, h.work, xin, yout, h.opt.accumulate, s, h.opt.profile ? &h.timer : nullptr);
+        if (h.opt.on_the_fly) np_matvec(h, xin, yout, s);
+        else mvp_run(h.plan, h.work, xin, yout, h.opt.accumulate, s, h.opt.profile ? &h.timer : nullptr);
         if (!yd) copy_out(yr, h.ybuf.p, N * sizeof(double), s);
     }
     if (!yd) HM_CUDA(cudaStreamSynchronize(s));

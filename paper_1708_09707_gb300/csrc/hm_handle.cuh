@@ -55,6 +55,14 @@ struct hm_handle_s {
     hm::MvpWork work;
     hm::MvpTimer timer;
     hm::DevBuf<double> xbuf, ybuf;
+    // on-the-fly product: passes of consecutive admissible leaves
+    // [np_pass[q], np_pass[q + 1]), their ids, the factor scratch, t of a
+    // pass (np_kcap entries per leaf), the permuted x and the row sums
+    std::vector<int64_t> np_pass;
+    hm::DevBuf<uint32_t> np_ids;
+    hm::DevBuf<char> np_scratch, np_t, np_xm;
+    hm::DevBuf<double> np_yacc;
+    int np_kcap = 0;
     hm::DevBuf<int> status;
     hm_stats stats{};
     ~hm_handle_s();
@@ -75,6 +83,8 @@ void build_sets(hm_handle_s& h, int nsets, const double* points_all, const int64
                 const int* d, int kernel, const double* params, int leaf, double eta,
                 double aca_eps, const hm_options& opt);
 void matvec(hm_handle_s& h, const double* x, double* y, int nrhs, cudaStream_t s);
+// The product of an on-the-fly handle (device x, y; one vector).
+void np_matvec(hm_handle_s& h, const double* x, double* y, cudaStream_t s);
 void export_structure(hm_handle_s& h, uint64_t* codes, int64_t* perm, int64_t* adm,
                       int64_t* dense, int32_t* ranks);
 void export_tree(hm_handle_s& h, int64_t* lo, int64_t* hi, double* bbmin, double* bbmax);

@@ -54,47 +54,48 @@ __global__ void k_gather_xn(const double* __restrict__ x, const int64_t* __restr
     for (int g = 0; g < NRC / 4; ++g) o[g] = make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
 }
 
-// Warp totals of s[0 .. NRC-1] at once. The first log2(NRC) xor steps swap
-// half of the remaining values (a lane keeps the half its lane bit selects),
-// the remaining xor steps act on one value. Every addition is one of the
+// Warp totals of v[0 .. NV-1] at once (NV a power of two, at least 32): each
+// xor step m = 16, 8, 4, 2, 1 swaps half of the remaining values (a lane
+// keeps the half its lane bit m selects). Every addition is one of the
 // xor-butterfly tree's, so each total is bit for bit that of a butterfly
-// over one value. The lane holds the total of vector lane >> (5 - log2 NRC).
-template <int NRC>
-__device__ __forceinline__ float warp_sum_scatter(float (&s)[NRC], int lane)
+// over one value. Afterwards lane q holds in v[0 .. NV/32 - 1] the totals of
+// entries (NV/32) q, (NV/32) q + 1, ...
+template <int NV>
+__device__ __forceinline__ void warp_scatter_sum(float (&v)[NV], int lane)
 {
-    constexpr int LG = NRC == 16 ? 4 : NRC == 8 ? 3 : NRC == 4 ? 2 : NRC == 2 ? 1 : 0;
-    static_assert((1 << LG) == NRC, "power of two up to 16");
+    static_assert(NV >= 32 && (NV & (NV - 1)) == 0, "power of two, at least 32");
 #pragma unroll
-    for (int st = 0; st < LG; ++st) {
+    for (int st = 0; st < 5; ++st) {
         const int m = 16 >> st;
-        const int h = NRC >> (st + 1);
+        const int h = NV >> (st + 1);
         const bool up = (lane & m) != 0;
 #pragma unroll
         for (int i = 0; i < h; ++i) {
-            const float send = up ? s[i] : s[h + i];
-            const float keep = up ? s[h + i] : s[i];
-            s[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+            const float send = up ? v[i] : v[h + i];
+            const float keep = up ? v[h + i] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
         }
     }
-    float v = s[0];
-#pragma unroll
-    for (int m = 16 >> LG; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
-    return v;
 }
+
+constexpr int VN_LB = 4;   // factor columns l per pass of the V^T X kernel
 
 // t partials for NRC vectors: one warp per (block, 256-column chunk) work
 // item, its chunk of X staged in shared memory (rows padded to NRC + 4 floats
-// so that the 16-byte reads of a quarter warp hit distinct banks); lane j
-// reads the factor entries of columns j, j + 32, ... one factor column ahead.
+// so that the 16-byte reads of a quarter warp hit distinct banks). A pass
+// takes VN_LB factor columns l at once, so every staged x is read once per
+// pass; lane j holds the factor entries of columns j, j + 32, ... of those
+// l and loads the next pass's while it multiplies (packed FP32 pairs).
 template <int NRC>
-__global__ void __launch_bounds__(VN_W * 32)
+__global__ void __launch_bounds__(VN_W * 32, 2)
 k_vtx_n(const Blk* __restrict__ blk, const int32_t* __restrict__ rank,
         const uint64_t* __restrict__ Vptr, const int2* __restrict__ items, int64_t nitems,
         const int64_t* __restrict__ dst, const float* __restrict__ xm, float* __restrict__ t,
         float* __restrict__ tp)
 {
     constexpr int XS = NRC + 4;
-    constexpr int LG = NRC == 16 ? 4 : 3;
+    constexpr int NV = VN_LB * NRC;        // sums per pass
+    constexpr int PER = NV / 32;           // totals a lane writes per pass
     extern __shared__ __align__(16) float xsh[];
     const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t w = (int64_t)blockIdx.x * VN_W + wi;
@@ -116,40 +117,60 @@ k_vtx_n(const Blk* __restrict__ blk, const int32_t* __restrict__ rank,
     const float* __restrict__ V = reinterpret_cast<const float*>(Vptr[b]);
     const int64_t d = dst[w];
     float* out = d >= 0 ? tp + d * NRC : t + (-d - 1) * NRC;
-    const int rr = lane >> (5 - LG);
-    const bool writer = (lane & ((1 << (5 - LG)) - 1)) == 0;
-    float vn[8];
-    auto loadv = [&](int l) {
-        const float* Vl = V + (int64_t)l * n + c0;
+    float vn[VN_LB][8];
+    auto loadv = [&](int l0) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int jj = lane + 32 * q;
-            vn[q] = jj < cn ? __ldcs(Vl + jj) : 0.f;
+        for (int l = 0; l < VN_LB; ++l) {
+            const float* Vl = V + (int64_t)(l0 + l) * n + c0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int jj = lane + 32 * q;
+                vn[l][q] = (l0 + l < k && jj < cn) ? __ldcs(Vl + jj) : 0.f;
+            }
         }
     };
     if (k > 0) loadv(0);
-    for (int l = 0; l < k; ++l) {
-        float vc[8];
+    for (int l0 = 0; l0 < k; l0 += VN_LB) {
+        float vc[VN_LB][8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) vc[q] = vn[q];
-        if (l + 1 < k) loadv(l + 1);
-        float s[NRC];
+        for (int l = 0; l < VN_LB; ++l)
 #pragma unroll
-        for (int r = 0; r < NRC; ++r) s[r] = 0.f;
+            for (int q = 0; q < 8; ++q) vc[l][q] = vn[l][q];
+        if (l0 + VN_LB < k) loadv(l0 + VN_LB);
+        float2 s2[VN_LB][NRC / 2];
+#pragma unroll
+        for (int l = 0; l < VN_LB; ++l)
+#pragma unroll
+            for (int r = 0; r < NRC / 2; ++r) s2[l][r] = make_float2(0.f, 0.f);
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const float* xr = xs + (lane + 32 * q) * XS;
 #pragma unroll
             for (int g = 0; g < NRC / 4; ++g) {
                 const float4 xv = *reinterpret_cast<const float4*>(xr + 4 * g);
-                s[4 * g + 0] = fmaf(vc[q], xv.x, s[4 * g + 0]);
-                s[4 * g + 1] = fmaf(vc[q], xv.y, s[4 * g + 1]);
-                s[4 * g + 2] = fmaf(vc[q], xv.z, s[4 * g + 2]);
-                s[4 * g + 3] = fmaf(vc[q], xv.w, s[4 * g + 3]);
+                const float2 x01 = make_float2(xv.x, xv.y), x23 = make_float2(xv.z, xv.w);
+#pragma unroll
+                for (int l = 0; l < VN_LB; ++l) {
+                    const float2 vv = make_float2(vc[l][q], vc[l][q]);
+                    s2[l][2 * g] = __ffma2_rn(vv, x01, s2[l][2 * g]);
+                    s2[l][2 * g + 1] = __ffma2_rn(vv, x23, s2[l][2 * g + 1]);
+                }
             }
         }
-        const float tot = warp_sum_scatter<NRC>(s, lane);
-        if (writer) out[(int64_t)l * NRC + rr] = tot;
+        float val[NV];
+#pragma unroll
+        for (int l = 0; l < VN_LB; ++l)
+#pragma unroll
+            for (int r = 0; r < NRC / 2; ++r) {
+                val[l * NRC + 2 * r] = s2[l][r].x;
+                val[l * NRC + 2 * r + 1] = s2[l][r].y;
+            }
+        warp_scatter_sum<NV>(val, lane);
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const int idx = PER * lane + i;
+            if (l0 + idx / NRC < k) out[(int64_t)l0 * NRC + idx] = val[i];
+        }
     }
 }
 
@@ -187,13 +208,77 @@ __device__ __forceinline__ void consumer_sync(int nthreads)
     asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
 }
 
+// Exact rounding error of s + v added to the correction (Knuth's TwoSum,
+// branch-free, on packed FP32 pairs; a - b is written fma(b, -1, a), which
+// rounds once like the subtraction). s + c is the compensated sum.
+__device__ __forceinline__ void two_sum_add(float2& s, float2& c, float2 v)
+{
+    const float2 m1 = make_float2(-1.f, -1.f);
+    const float2 t = __fadd2_rn(s, v);
+    const float2 bp = __ffma2_rn(s, m1, t);    // t - s
+    const float2 ap = __ffma2_rn(bp, m1, t);   // t - bp
+    const float2 da = __ffma2_rn(ap, m1, s);   // s - ap
+    const float2 db = __ffma2_rn(bp, m1, v);   // v - bp
+    c = __fadd2_rn(c, __fadd2_rn(da, db));
+    s = t;
+}
+
+// Rows ir .. ir+3 of chunk column col as two packed row pairs.
+template <int FMT, bool ISU>
+__device__ __forceinline__ void stage_rows(const unsigned char* st, int col, int colb, int ir, int ld,
+                                           float2& a01, float2& a23)
+{
+    if (ISU || FMT == HM_NEAR_FP32) {
+        const float4 v = *reinterpret_cast<const float4*>(st + col * colb + 4 * ir);
+        a01 = make_float2(v.x, v.y);
+        a23 = make_float2(v.z, v.w);
+    } else if (FMT == HM_NEAR_BF16X2) {
+        const __nv_bfloat16* q = reinterpret_cast<const __nv_bfloat16*>(st + col * colb) + ir;
+        const uint2 h = *reinterpret_cast<const uint2*>(q);
+        const uint2 l = *reinterpret_cast<const uint2*>(q + ld);
+        a01 = __fadd2_rn(bf2(h.x), bf2(l.x));
+        a23 = __fadd2_rn(bf2(h.y), bf2(l.y));
+    } else {
+        const double2* q = reinterpret_cast<const double2*>(st + col * colb + 8 * ir);
+        const double2 v0 = q[0], v1 = q[1];
+        a01 = make_float2((float)v0.x, (float)v0.y);
+        a23 = make_float2((float)v1.x, (float)v1.y);
+    }
+}
+
+// Plain sums over one thread's columns j, j + 4, ... of a chunk (ascending),
+// rows ir .. ir+3 against vectors 4g .. 4g+3; the multiplier table holds
+// every multiplier twice ({m0, m0, m1, m1, m2, m2, m3, m3} per column and group).
+template <int FMT, bool ISU, bool TAIL, int NRC>
+__device__ __forceinline__ void chunk_sums(const unsigned char* st, const float* ms, int j, int ir,
+                                           int g, int ld, int colb, int cnt, float2 (&sg)[2][4])
+{
+#pragma unroll 4
+    for (int e = 0; e < TN_COL / TN_LANES; ++e) {
+        const int col = j + TN_LANES * e;
+        if (TAIL && col >= cnt) break;
+        float2 a01, a23;
+        stage_rows<FMT, ISU>(st, col, colb, ir, ld, a01, a23);
+        const float4* mp = reinterpret_cast<const float4*>(ms + 2 * (col * NRC + 4 * g));
+        const float4 mA = mp[0], mB = mp[1];
+        const float2 m[4] = {make_float2(mA.x, mA.y), make_float2(mA.z, mA.w),
+                             make_float2(mB.x, mB.y), make_float2(mB.z, mB.w)};
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            sg[0][r] = __ffma2_rn(a01, m[r], sg[0][r]);
+            sg[1][r] = __ffma2_rn(a23, m[r], sg[1][r]);
+        }
+    }
+}
+
 // One CTA per gather work item (a piece of one row tile's U-then-near column
 // stream, as in the one-vector product). A producer thread moves 64-column
 // chunks into a ring of shared-memory stages with cp.async.bulk; NRC / 2
 // consumer warps multiply them. Consumer thread (j, g, q) owns rows
 // 4q .. 4q+3, vectors 4g .. 4g+3 and the chunk columns j, j + 4, ..., and
-// fetches one float4 of next chunk's multipliers (column, vector group) into
-// a double-buffered table; a named barrier over the consumers publishes it.
+// fetches one float4 of the next chunk's multipliers (column, vector group)
+// into a double-buffered table; a named barrier over the consumers publishes
+// it. Sums run on packed FP32 pairs (two rows of one vector).
 // Waits are bounded: a wait that gives up sets bit 4 of the status word, the
 // consumers leave together after their barrier, and the item writes nothing.
 template <int FMT, int NRC>
@@ -206,10 +291,10 @@ k_tile_n(MvpPlan P, const float* __restrict__ xm, const float* __restrict__ t,
     constexpr int STAGE = TN_COL * ncol_bytes64<FMT>();
     static_assert(16 * NG * TN_LANES == NCW * 32, "one consumer per (rows, group, lane)");
     static_assert(TN_COL * NG == NCW * 32, "one multiplier float4 per consumer");
+    static_assert(TN_LANES * TN_ROWS * NRC * 8 <= TN_STAGES * STAGE, "row sums fit the stages");
     extern __shared__ __align__(128) unsigned char tsm[];
     __shared__ uint64_t full[TN_STAGES], empty[TN_STAGES];
-    __shared__ __align__(16) float msm[2][TN_COL * NRC];
-    __shared__ double ps[TN_LANES][TN_ROWS][NRC];
+    __shared__ __align__(16) float msm[2][2 * TN_COL * NRC];
     __shared__ int failed;
     const int64_t item = blockIdx.x;
     const int3 it = P.items[item];
@@ -240,6 +325,8 @@ k_tile_n(MvpPlan P, const float* __restrict__ xm, const float* __restrict__ t,
         const int64_t cend = isu ? uce : nce;
         cnt = (int)(cend - c0 < TN_COL ? cend - c0 : TN_COL);
     };
+    // the four column lanes' row sums, once the stages are no longer read
+    double (*ps)[TN_ROWS][NRC] = reinterpret_cast<double (*)[TN_ROWS][NRC]>(tsm);
     if (w == NCW) {
         // ---------------- producer
         if (lane == 0) {
@@ -288,88 +375,71 @@ k_tile_n(MvpPlan P, const float* __restrict__ xm, const float* __restrict__ t,
             return isu ? t4[(int64_t)P.ucol_t[uc0 + c0 + fc] * NG + fg]
                        : x4[(int64_t)P.ncol_x[nc0 + c0 + fc] * NG + fg];
         };
-        Acc<float> acc[4][4];
+        auto publish = [&](int buf, float4 m) {
+            float4* d = reinterpret_cast<float4*>(msm[buf]) + 2 * tc;
+            d[0] = make_float4(m.x, m.x, m.y, m.y);
+            d[1] = make_float4(m.z, m.z, m.w, m.w);
+        };
+        float2 as[2][4], ac[2][4];   // compensated sums and corrections [row pair][vector]
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) as[p][r] = ac[p][r] = make_float2(0.f, 0.f);
         float4 mf = fetch(0);
-        reinterpret_cast<float4*>(msm[0])[tc] = mf;
+        publish(0, mf);
         consumer_sync(NCW * 32);
         for (int k = 0; k < nch; ++k) {
             const int slot = k % TN_STAGES;
             mf = fetch(k + 1);
             const bool ok = __all_sync(0xffffffffu, mbar_wait(&full[slot], (k / TN_STAGES) & 1));
             if (ok) {
-                bool isu;
-                int64_t c0;
-                int cnt;
-                chunk(k, isu, c0, cnt);
-                const unsigned char* st = tsm + slot * STAGE;
-                const float* ms = msm[k & 1];
-                float sg[4][4];
+                if (act) {
+                    bool isu;
+                    int64_t c0;
+                    int cnt;
+                    chunk(k, isu, c0, cnt);
+                    const unsigned char* st = tsm + slot * STAGE;
+                    const float* ms = msm[k & 1];
+                    float2 sg[2][4];
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
+                    for (int p = 0; p < 2; ++p)
 #pragma unroll
-                    for (int r = 0; r < 4; ++r) sg[i][r] = 0.f;
-#pragma unroll 4
-                for (int e = 0; e < TN_COL / TN_LANES; ++e) {
-                    const int col = j + TN_LANES * e;
-                    float a[4] = {0.f, 0.f, 0.f, 0.f};
-                    if (act && col < cnt) {
-                        if (isu) {
-                            const float4 v = *reinterpret_cast<const float4*>(st + col * ucolb + 4 * ir);
-                            a[0] = v.x;
-                            a[1] = v.y;
-                            a[2] = v.z;
-                            a[3] = v.w;
-                        } else if (FMT == HM_NEAR_BF16X2) {
-                            const __nv_bfloat16* q = reinterpret_cast<const __nv_bfloat16*>(st + col * ncolb) + ir;
-                            const uint2 h = *reinterpret_cast<const uint2*>(q);
-                            const uint2 l = *reinterpret_cast<const uint2*>(q + ld);
-                            const float2 h0 = bf2(h.x), h1 = bf2(h.y), l0 = bf2(l.x), l1 = bf2(l.y);
-                            a[0] = h0.x + l0.x;
-                            a[1] = h0.y + l0.y;
-                            a[2] = h1.x + l1.x;
-                            a[3] = h1.y + l1.y;
-                        } else if (FMT == HM_NEAR_FP32) {
-                            const float4 v = *reinterpret_cast<const float4*>(st + col * ncolb + 4 * ir);
-                            a[0] = v.x;
-                            a[1] = v.y;
-                            a[2] = v.z;
-                            a[3] = v.w;
-                        } else {
-                            const double2* q = reinterpret_cast<const double2*>(st + col * ncolb + 8 * ir);
-                            const double2 v0 = q[0], v1 = q[1];
-                            a[0] = (float)v0.x;
-                            a[1] = (float)v0.y;
-                            a[2] = (float)v1.x;
-                            a[3] = (float)v1.y;
-                        }
+                        for (int r = 0; r < 4; ++r) sg[p][r] = make_float2(0.f, 0.f);
+                    if (isu) {
+                        if (cnt == TN_COL) chunk_sums<FMT, true, false, NRC>(st, ms, j, ir, g, ld, ucolb, cnt, sg);
+                        else chunk_sums<FMT, true, true, NRC>(st, ms, j, ir, g, ld, ucolb, cnt, sg);
+                    } else {
+                        if (cnt == TN_COL) chunk_sums<FMT, false, false, NRC>(st, ms, j, ir, g, ld, ncolb, cnt, sg);
+                        else chunk_sums<FMT, false, true, NRC>(st, ms, j, ir, g, ld, ncolb, cnt, sg);
                     }
-                    const float4 m = *reinterpret_cast<const float4*>(ms + col * NRC + 4 * g);
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        sg[i][0] = fmaf(a[i], m.x, sg[i][0]);
-                        sg[i][1] = fmaf(a[i], m.y, sg[i][1]);
-                        sg[i][2] = fmaf(a[i], m.z, sg[i][2]);
-                        sg[i][3] = fmaf(a[i], m.w, sg[i][3]);
-                    }
+                    for (int p = 0; p < 2; ++p)
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) two_sum_add(as[p][r], ac[p][r], sg[p][r]);
                 }
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int r = 0; r < 4; ++r) acc[i][r].add(sg[i][r]);
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[slot]);
             } else if (lane == 0) {
                 atomicOr(P.status, 4);
                 failed = 1;
             }
-            reinterpret_cast<float4*>(msm[(k + 1) & 1])[tc] = mf;
+            publish((k + 1) & 1, mf);
             consumer_sync(NCW * 32);
             if (*(volatile int*)&failed) break;
         }
+        // every consumer has passed its last barrier, so no stage is read
+        // any more (the stages are only reused when nothing failed)
+        if (!*(volatile int*)&failed) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+            for (int p = 0; p < 2; ++p)
 #pragma unroll
-            for (int r = 0; r < 4; ++r) ps[j][ir + i][4 * g + r] = act ? acc[i][r].value() : 0.0;
+                for (int r = 0; r < 4; ++r) {
+                    ps[j][ir + 2 * p][4 * g + r] =
+                        act ? (double)as[p][r].x + (double)ac[p][r].x : 0.0;
+                    ps[j][ir + 2 * p + 1][4 * g + r] =
+                        act ? (double)as[p][r].y + (double)ac[p][r].y : 0.0;
+                }
+        }
     }
     __syncthreads();
     if (*(volatile int*)&failed) return;

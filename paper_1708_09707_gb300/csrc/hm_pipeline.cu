@@ -375,42 +375,56 @@ void alloc_factor_meta(hm_handle_s& h)
 // ACA of the admissible blocks ids[0..n) (all blocks when ids is null); see
 // the file comment for the two storage modes (kpred != null: learned sizing,
 // one arena; else bounded scratch passes with exact final segments).
-void compress(hm_handle_s& h, const uint32_t* ids, int64_t n, const int32_t* kpred)
+// Blocks ids[0..n) in size-class order (the largest class first) with their
+// reservations: kres (m + n) entries in all, kres m of them for U.
+struct AcaOrder {
+    int64_t n = 0;
+    DevBuf<uint32_t> order;
+    DevBuf<int64_t> pre, preu;
+    std::vector<int64_t> hpre, hpreu;
+    int64_t cstart[ACA_NCLASS], cend[ACA_NCLASS];
+};
+
+void aca_order(hm_handle_s& h, const uint32_t* ids, int64_t n, const int32_t* kpred, AcaOrder& O)
 {
     cudaStream_t s = h.stream;
-    const int esz = h.precision == HM_PREC_FP64 ? 8 : 4;
-    if (n == 0) return;
-
+    O.n = n;
     DevBuf<uint64_t> key(n, s);
-    DevBuf<uint32_t> order(n, s);
+    O.order.alloc(n, s);
     DevBuf<int64_t> ccount(ACA_NCLASS, s);
     HM_CUDA(cudaMemsetAsync(ccount.p, 0, ACA_NCLASS * sizeof(int64_t), s));
-    k_classes<<<grid_for(n), NT, 0, s>>>(h.ablk.p, ids, n, h.opt.k_cap, kpred, key.p, order.p,
+    k_classes<<<grid_for(n), NT, 0, s>>>(h.ablk.p, ids, n, h.opt.k_cap, kpred, key.p, O.order.p,
                                          h.kres.p, ccount.p); note_launch();
     HM_LAUNCH("classes");
-    radix_sort_u64_u32(key.p, order.p, n, bits_for(ACA_NCLASS), s);
+    radix_sort_u64_u32(key.p, O.order.p, n, bits_for(ACA_NCLASS), s);
     int64_t cc[ACA_NCLASS];
     HM_CUDA(cudaMemcpyAsync(cc, ccount.p, sizeof(cc), cudaMemcpyDeviceToHost, s));
-    DevBuf<int64_t> res(n, s), pre(n + 1, s), resu(n, s), preu(n + 1, s);
-    k_reserve<<<grid_for(n), NT, 0, s>>>(h.ablk.p, order.p, n, h.kres.p, res.p, resu.p); note_launch();
-    scan_exclusive_i64(res.p, pre.p, n, pre.p + n, s);
-    scan_exclusive_i64(resu.p, preu.p, n, preu.p + n, s);
-    std::vector<int64_t> hpre(n + 1), hpreu(n + 1);
-    HM_CUDA(cudaMemcpyAsync(hpre.data(), pre.p, (n + 1) * sizeof(int64_t),
+    DevBuf<int64_t> res(n, s), resu(n, s);
+    O.pre.alloc(n + 1, s);
+    O.preu.alloc(n + 1, s);
+    k_reserve<<<grid_for(n), NT, 0, s>>>(h.ablk.p, O.order.p, n, h.kres.p, res.p, resu.p); note_launch();
+    scan_exclusive_i64(res.p, O.pre.p, n, O.pre.p + n, s);
+    scan_exclusive_i64(resu.p, O.preu.p, n, O.preu.p + n, s);
+    O.hpre.resize(n + 1);
+    O.hpreu.resize(n + 1);
+    HM_CUDA(cudaMemcpyAsync(O.hpre.data(), O.pre.p, (n + 1) * sizeof(int64_t),
                             cudaMemcpyDeviceToHost, s));
-    HM_CUDA(cudaMemcpyAsync(hpreu.data(), preu.p, (n + 1) * sizeof(int64_t),
+    HM_CUDA(cudaMemcpyAsync(O.hpreu.data(), O.preu.p, (n + 1) * sizeof(int64_t),
                             cudaMemcpyDeviceToHost, s));
     HM_CUDA(cudaStreamSynchronize(s));
-    // class ranges in the sorted order: the largest class first
-    int64_t cstart[ACA_NCLASS], cend[ACA_NCLASS];
-    {
-        int64_t q = 0;
-        for (int c = ACA_NCLASS - 1; c >= 0; --c) {
-            cstart[c] = q;
-            q += cc[c];
-            cend[c] = q;
-        }
+    int64_t q = 0;
+    for (int c = ACA_NCLASS - 1; c >= 0; --c) {
+        O.cstart[c] = q;
+        q += cc[c];
+        O.cend[c] = q;
     }
+}
+
+// Arguments of the ACA kernels for this handle (setn keeps the per-set point
+// counts of the mixed stopping floor alive).
+AcaArgs aca_args(hm_handle_s& h, DevBuf<int64_t>& setn)
+{
+    cudaStream_t s = h.stream;
     AcaArgs a;
     a.blk = h.ablk.p;
     a.kres = h.kres.p;
@@ -426,7 +440,6 @@ void compress(hm_handle_s& h, const uint32_t* ids, int64_t n, const int32_t* kpr
     a.k_cap = h.opt.k_cap;
     a.bset = nullptr;
     a.set_n = nullptr;
-    DevBuf<int64_t> setn;
     if (h.precision == HM_PREC_MIXED) {
         std::vector<int64_t> sn(h.sets.size());
         for (size_t q = 0; q < h.sets.size(); ++q) sn[q] = h.sets[q].N;
@@ -435,28 +448,57 @@ void compress(hm_handle_s& h, const uint32_t* ids, int64_t n, const int32_t* kpr
         a.bset = h.adm_set.p;
         a.set_n = setn.p;
     }
+    return a;
+}
 
-    // every size class runs on its own stream so that the few largest blocks
-    // (clusters of CTAs) overlap the many small ones
+// ACA of the blocks O.order[q0..q1): every size class on its own stream so
+// that the few largest blocks (clusters of CTAs) overlap the many small ones;
+// profile = 2 runs the classes one after another on the main stream, so that
+// each class's time is its kernels' own duration.
+void aca_range(hm_handle_s& h, const AcaOrder& O, const AcaArgs& a, int64_t q0, int64_t q1)
+{
+    cudaStream_t s = h.stream;
     ClassStreams cs(s);
-    // profile = 2 runs the classes one after another on the main stream, so
-    // that each class's time is its kernels' own duration
     const bool serial = h.opt.profile == 2;
-    auto run_range = [&](int64_t q0, int64_t q1) {
-        cs.fork();
-        for (int c = ACA_NCLASS - 1; c >= 0; --c) {
-            int64_t lo = std::max(q0, cstart[c]), hi = std::min(q1, cend[c]);
-            if (hi > lo) {
-                cudaStream_t sc = serial ? s : cs.st[c];
-                HM_CUDA(cudaEventRecord(cs.t0[c], sc));
-                aca_run(h.precision, h.kp, h.X, a, order.p + lo, hi - lo, c, h.max_set_n, sc);
-                HM_CUDA(cudaEventRecord(cs.t1[c], sc));
-                cs.timed[c] = true;
-            }
+    cs.fork();
+    for (int c = ACA_NCLASS - 1; c >= 0; --c) {
+        int64_t lo = std::max(q0, O.cstart[c]), hi = std::min(q1, O.cend[c]);
+        if (hi > lo) {
+            cudaStream_t sc = serial ? s : cs.st[c];
+            HM_CUDA(cudaEventRecord(cs.t0[c], sc));
+            aca_run(h.precision, h.kp, h.X, a, O.order.p + lo, hi - lo, c, h.max_set_n, sc);
+            HM_CUDA(cudaEventRecord(cs.t1[c], sc));
+            cs.timed[c] = true;
         }
-        cs.join();
-        cs.collect(h.stats.t_aca_class_ms);
-    };
+    }
+    cs.join();
+    cs.collect(h.stats.t_aca_class_ms);
+}
+
+// Entries of the automatic ACA scratch: 30 % of the free device memory.
+int64_t scratch_entries(hm_handle_s& h, int esz)
+{
+    size_t freeb = 0, totb = 0;
+    HM_CUDA(cudaMemGetInfo(&freeb, &totb));
+    const int64_t cap = h.opt.scratch_gb > 0 ? (int64_t)(h.opt.scratch_gb * 1e9 / esz)
+                                             : (int64_t)(0.30 * (double)freeb / esz);
+    return std::max<int64_t>(cap, 1);
+}
+
+// ACA of the admissible blocks ids[0..n) (all blocks when ids is null); see
+// the file comment for the two storage modes (kpred != null: learned sizing,
+// one arena; else bounded scratch passes with exact final segments).
+void compress(hm_handle_s& h, const uint32_t* ids, int64_t n, const int32_t* kpred)
+{
+    cudaStream_t s = h.stream;
+    const int esz = h.precision == HM_PREC_FP64 ? 8 : 4;
+    if (n == 0) return;
+    AcaOrder O;
+    aca_order(h, ids, n, kpred, O);
+    const std::vector<int64_t>& hpre = O.hpre;
+    const std::vector<int64_t>& hpreu = O.hpreu;
+    DevBuf<int64_t> setn;
+    const AcaArgs a = aca_args(h, setn);
 
     if (kpred) {
         // learned sizing: reserve the predicted ranks directly (no copy)
@@ -464,21 +506,17 @@ void compress(hm_handle_s& h, const uint32_t* ids, int64_t n, const int32_t* kpr
         auto vseg = std::make_unique<FactorSegment>();
         useg->mem.alloc((size_t)std::max<int64_t>(hpreu[n], 1) * esz, s);
         vseg->mem.alloc((size_t)std::max<int64_t>(hpre[n] - hpreu[n], 1) * esz, s);
-        k_set_ptrs<<<grid_for(n), NT, 0, s>>>(order.p, 0, n, pre.p, preu.p, useg->mem.p,
+        k_set_ptrs<<<grid_for(n), NT, 0, s>>>(O.order.p, 0, n, O.pre.p, O.preu.p, useg->mem.p,
                                                vseg->mem.p, esz, h.Uptr.p, h.Vptr.p); note_launch();
         HM_LAUNCH("set ptrs");
         h.usegments.push_back(std::move(useg));
         h.vsegments.push_back(std::move(vseg));
-        run_range(0, n);
+        aca_range(h, O, a, 0, n);
         h.stats.aca_passes += 1;
         return;
     }
 
-    size_t freeb = 0, totb = 0;
-    HM_CUDA(cudaMemGetInfo(&freeb, &totb));
-    int64_t cap = h.opt.scratch_gb > 0 ? (int64_t)(h.opt.scratch_gb * 1e9 / esz)
-                                       : (int64_t)(0.30 * (double)freeb / esz);
-    cap = std::max<int64_t>(cap, 1);
+    int64_t cap = scratch_entries(h, esz);
     int64_t maxres = 0;
     for (int64_t q = 0; q < n; ++q) maxres = std::max(maxres, hpre[q + 1] - hpre[q]);
     cap = std::max(cap, maxres);
@@ -492,13 +530,13 @@ void compress(hm_handle_s& h, const uint32_t* ids, int64_t n, const int32_t* kpr
         q1 = std::max(q1, q0 + 1);
         // the chunk's U reservations first, then its V reservations
         char* vbase = scratch.p + (hpreu[q1] - hpreu[q0]) * esz;
-        k_set_ptrs<<<grid_for(q1 - q0), NT, 0, s>>>(order.p, q0, q1, pre.p, preu.p, scratch.p,
-                                                     vbase, esz, h.Uptr.p, h.Vptr.p); note_launch();
+        k_set_ptrs<<<grid_for(q1 - q0), NT, 0, s>>>(O.order.p, q0, q1, O.pre.p, O.preu.p,
+                                                     scratch.p, vbase, esz, h.Uptr.p, h.Vptr.p); note_launch();
         HM_LAUNCH("set ptrs");
-        run_range(q0, q1);
+        aca_range(h, O, a, q0, q1);
         const int64_t nq = q1 - q0;
         DevBuf<int64_t> fsu(nq, s), fsv(nq, s), foffu(nq + 1, s), foffv(nq + 1, s);
-        k_final_size<<<grid_for(nq), NT, 0, s>>>(h.ablk.p, order.p, q0, q1, h.rank.p, fsu.p, fsv.p); note_launch();
+        k_final_size<<<grid_for(nq), NT, 0, s>>>(h.ablk.p, O.order.p, q0, q1, h.rank.p, fsu.p, fsv.p); note_launch();
         scan_exclusive_i64(fsu.p, foffu.p, nq, foffu.p + nq, s);
         scan_exclusive_i64(fsv.p, foffv.p, nq, foffv.p + nq, s);
         int64_t tot[2] = {0, 0};
@@ -509,7 +547,7 @@ void compress(hm_handle_s& h, const uint32_t* ids, int64_t n, const int32_t* kpr
         auto vseg = std::make_unique<FactorSegment>();
         useg->mem.alloc((size_t)std::max<int64_t>(tot[0], 1) * esz, s);
         vseg->mem.alloc((size_t)std::max<int64_t>(tot[1], 1) * esz, s);
-        k_copy_factors<<<(unsigned)nq, NT, 0, s>>>(h.ablk.p, order.p, q0, q1, h.rank.p, foffu.p,
+        k_copy_factors<<<(unsigned)nq, NT, 0, s>>>(h.ablk.p, O.order.p, q0, q1, h.rank.p, foffu.p,
                                                    foffv.p, useg->mem.p, vseg->mem.p, esz,
                                                    h.Uptr.p, h.Vptr.p); note_launch();
         HM_LAUNCH("copy factors");
@@ -519,6 +557,110 @@ void compress(hm_handle_s& h, const uint32_t* ids, int64_t n, const int32_t* kpr
         q0 = q1;
     }
     h.stats.aca_passes += passes;
+}
+
+__global__ void k_iota_u32(uint32_t* __restrict__ ids, int64_t n)
+{
+    const int64_t q = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (q < n) ids[q] = (uint32_t)q;
+}
+
+__global__ void k_full_reserve(const Blk* __restrict__ blk, int64_t n, int kcap,
+                               int64_t* __restrict__ res)
+{
+    const int64_t b = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (b >= n) return;
+    const Blk B = blk[b];
+    res[b] = (int64_t)min(kcap, min(B.m, B.n)) * (B.m + B.n);
+}
+
+// On-the-fly mode, at build time: passes of consecutive admissible leaves
+// (block order) whose full reservations min(k_cap, m, n) (m + n) fit the
+// scratch bound, and the buffers every product reuses.
+void np_prepare(hm_handle_s& h)
+{
+    cudaStream_t s = h.stream;
+    const int64_t n = h.n_adm;
+    const int esz = h.precision == HM_PREC_FP64 ? 8 : 4;
+    h.np_pass.assign(1, 0);
+    h.np_ids.alloc(std::max<int64_t>(n, 1), s);
+    int64_t cap = 1, most = 1;
+    if (n > 0) {
+        k_iota_u32<<<grid_for(n), NT, 0, s>>>(h.np_ids.p, n); note_launch();
+        DevBuf<int64_t> res(n, s);
+        k_full_reserve<<<grid_for(n), NT, 0, s>>>(h.ablk.p, n, h.opt.k_cap, res.p); note_launch();
+        HM_LAUNCH("np reservations");
+        std::vector<int64_t> hr(n);
+        HM_CUDA(cudaMemcpyAsync(hr.data(), res.p, n * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        HM_CUDA(cudaStreamSynchronize(s));
+        int64_t total = 0, maxres = 0;
+        for (int64_t b = 0; b < n; ++b) {
+            total += hr[b];
+            maxres = std::max(maxres, hr[b]);
+        }
+        cap = std::min(std::max(scratch_entries(h, esz), maxres), std::max<int64_t>(total, 1));
+        int64_t acc = 0, first = 0;
+        for (int64_t b = 0; b < n; ++b) {
+            if (acc + hr[b] > cap && b > first) {
+                h.np_pass.push_back(b);
+                most = std::max(most, b - first);
+                first = b;
+                acc = 0;
+            }
+            acc += hr[b];
+        }
+        h.np_pass.push_back(n);
+        most = std::max(most, n - first);
+    }
+    h.np_kcap = std::max(h.opt.k_cap, 1);
+    h.np_scratch.alloc((size_t)cap * esz, s);
+    h.np_t.alloc((size_t)most * h.np_kcap * esz, s);
+    h.np_xm.alloc((size_t)std::max<int64_t>(h.Ntot, 1) * esz, s);
+    h.np_yacc.alloc(std::max<int64_t>(h.Ntot, 1), s);
+    HM_CUDA(cudaStreamSynchronize(s));
+}
+
+// y = H x (+ sigma^2 x) for device x, y without stored factors: per pass, ACA
+// of its leaves into the scratch, then t_b = V_b^T x|sigma and y_m += U_b t_b;
+// then the dense leaves evaluated on the fly. Runs on the handle's stream,
+// ordered after and before stream s.
+void np_matvec(hm_handle_s& h, const double* x, double* y, cudaStream_t s)
+{
+    cudaStream_t hs = h.stream;
+    cudaEvent_t ev = nullptr;
+    if (s != hs) {
+        HM_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        HM_CUDA(cudaEventRecord(ev, s));
+        HM_CUDA(cudaStreamWaitEvent(hs, ev, 0));
+    }
+    const int64_t N = h.Ntot;
+    const int esz = h.precision == HM_PREC_FP64 ? 8 : 4;
+    HM_CUDA(cudaMemsetAsync(h.np_yacc.p, 0, N * sizeof(double), hs));
+    np_gather_x(h.precision, x, h.perm.p, N, h.np_xm.p, hs);
+    DevBuf<int64_t> setn;
+    const AcaArgs a = aca_args(h, setn);
+    for (size_t q = 0; q + 1 < h.np_pass.size(); ++q) {
+        const int64_t b0 = h.np_pass[q], b1 = h.np_pass[q + 1], nb = b1 - b0;
+        AcaOrder O;
+        aca_order(h, h.np_ids.p + b0, nb, nullptr, O);
+        char* vbase = h.np_scratch.p + O.hpreu[nb] * esz;
+        k_set_ptrs<<<grid_for(nb), NT, 0, hs>>>(O.order.p, 0, nb, O.pre.p, O.preu.p,
+                                                 h.np_scratch.p, vbase, esz, h.Uptr.p, h.Vptr.p); note_launch();
+        HM_LAUNCH("set ptrs");
+        aca_range(h, O, a, 0, nb);
+        np_lowrank(h.precision, h.ablk.p, h.rank.p, h.Uptr.p, h.Vptr.p, b0, b1, h.lists.lr_ptr.p,
+                   h.lists.lr_ent.p, h.tile_row0.p, h.tile_m.p, h.n_tiles, h.np_xm.p, h.np_t.p,
+                   h.np_kcap, h.np_yacc.p, hs);
+    }
+    check_status(h);
+    np_near(h.precision, h.kp, h.X, h.dblk.p, h.lists.dn_ptr.p, h.lists.dn_ent.p, h.tile_row0.p,
+            h.tile_m.p, h.n_tiles, h.np_xm.p, h.np_yacc.p, hs);
+    np_finish(h.perm.p, nullptr, h.sigma2, N, h.np_yacc.p, x, y, h.opt.accumulate, hs);
+    if (ev) {
+        HM_CUDA(cudaEventRecord(ev, hs));
+        HM_CUDA(cudaStreamWaitEvent(s, ev, 0));
+        cudaEventDestroy(ev);
+    }
 }
 
 namespace {
@@ -574,6 +716,8 @@ void validate(int nsets, const int64_t* N, const int* d, int kernel, const doubl
         tot += N[q];
     }
     if (tot >= (1ll << 31)) fail(HM_EINVAL, "more than 2^31 points");
+    if (o.on_the_fly && (o.symmetric || o.rank_model || nsets > 1))
+        fail(HM_ENOTSUP, "on_the_fly runs without symmetric, rank_model and batches");
 }
 
 }  // namespace
@@ -729,6 +873,28 @@ void build_sets(hm_handle_s& h, int nsets, const double* points_all, const int64
     dense.clear();
     if (pts_dev.p) pts_dev.release();
 
+    if (opt.on_the_fly) {
+        // no factors and no near field: the gather lists by tile and the
+        // passes of the products
+        alloc_factor_meta(h);
+        mvp_build_lists(h.ablk.p, h.rank.p, h.n_adm, h.dblk.p, h.n_dense, h.tile_row0.p,
+                        h.tile_m.p, h.n_tiles, h.lists, s);
+        np_prepare(h);
+        hm_stats& st = h.stats;
+        st.n_points = Ntot;
+        st.n_nodes = nn;
+        st.n_adm = h.n_adm;
+        st.n_dense = h.n_dense;
+        st.n_tiles = h.n_tiles;
+        st.depth = h.sets[0].depth;
+        st.d = h.sets[0].d;
+        st.precision = h.precision;
+        st.near_format = h.near_format;
+        st.aca_passes = (int)h.np_pass.size() - 1;
+        st.t_total_ms =
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        return;
+    }
     if (opt.structure_only) {
         alloc_factor_meta(h);
         hm_stats& st = h.stats;

@@ -1,0 +1,98 @@
+"""The on-the-fly product (no stored factors or near field; ACA and the dense
+leaves recomputed inside every product): equal to the oracle within the
+FP64 / mixed bounds, equal to the stored product to rounding, and the same
+bits whatever the number of ACA passes."""
+import numpy as np
+import pytest
+
+from paper_1708_09707_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+MIXED_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def hm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1708_09707_gb300 import build, hm as H
+    build.build()
+    H.lib()
+    return H
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _pts(n, d, kind, seed):
+    if kind == "m":
+        return inputs.mixture_points(n, d, seed)
+    return inputs.uniform_points(n, d, seed)
+
+
+@pytest.mark.parametrize("case", [(6000, 2, "m", 0, 0.1, 64, 1.0, 1e-8, False),
+                                  (5000, 3, "u", 1, 0.2, 32, 1.0, 1e-6, False),
+                                  (4096, 2, "u", 0, 0.1, 32, 1.0, 1e-8, True)],
+                         ids=["mix2d", "matern3d", "uniform2d_max"])
+def test_fp64_matches_oracle_and_stored(hm, orc, case):
+    n, d, kind, kern, ell, leaf, eta, eps, adm_max = case
+    pts = _pts(n, d, kind, 11)
+    x = inputs.normal_vector(n, inputs.X_SEED)
+    H = hm.HMatrix(pts, kern, ell, leaf, eta, eps, sigma2=0.01, adm_max=adm_max, on_the_fly=True)
+    y = H.matvec(x)
+    O = orc.HMatrix(pts, kern, ell, leaf, eta, eps, sigma2=0.01, adm_max=adm_max)
+    assert rel(y, O.matvec(x)) <= FP64_TOL
+    S = hm.HMatrix(pts, kern, ell, leaf, eta, eps, sigma2=0.01, adm_max=adm_max)
+    # the same ACA factors; only the order of the row sums differs
+    assert rel(y, S.matvec(x)) <= 1e-13
+    assert np.array_equal(H.matvec(x), y)
+    st = H.stats()
+    assert st["factor_entries"] == 0 and st["near_entries"] == 0
+    assert np.array_equal(H.structure()["adm"], S.structure()["adm"])
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_pass_count_does_not_change_bits(hm, prec):
+    n = 20000
+    pts = _pts(n, 2, "m", 21)
+    x = inputs.normal_vector(n, 3)
+    H1 = hm.HMatrix(pts, 0, 0.1, 64, 1.0, 1e-6, precision=prec, on_the_fly=True)
+    H2 = hm.HMatrix(pts, 0, 0.1, 64, 1.0, 1e-6, precision=prec, on_the_fly=True,
+                    scratch_gb=0.004)
+    assert H1.stats()["aca_passes"] == 1
+    assert H2.stats()["aca_passes"] > 2
+    assert np.array_equal(H1.matvec(x), H2.matvec(x))
+
+
+def test_mixed_matches_oracle_and_options(hm, orc):
+    import torch
+    n = 9000
+    pts = _pts(n, 2, "m", 31)
+    x = inputs.normal_vector(n, 5)
+    H = hm.HMatrix(pts, 0, 0.1, 64, 1.0, 1e-6, sigma2=0.25, precision=hm.PREC_MIXED,
+                   on_the_fly=True)
+    y = H.matvec(x)
+    O = orc.HMatrix(pts, 0, 0.1, 64, 1.0, 1e-6, sigma2=0.25)
+    assert rel(y, O.matvec(x)) <= MIXED_TOL
+    yd = H.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert np.array_equal(y, yd)
+    X = np.stack([x, -2 * x, inputs.normal_vector(n, 6)])
+    Y = H.matvec(X)
+    for r in range(3):
+        assert np.array_equal(Y[r], H.matvec(X[r]))
+    Ha = hm.HMatrix(pts, 0, 0.1, 64, 1.0, 1e-6, sigma2=0.25, precision=hm.PREC_MIXED,
+                    on_the_fly=True, accumulate=True)
+    ya = np.ones(n)
+    Ha.matvec(x, ya)
+    assert np.array_equal(ya, y + 1.0)
+
+
+def test_refused_combinations(hm):
+    pts = _pts(500, 2, "u", 41)
+    for kw in (dict(symmetric=True), dict(rank_model_theta=np.zeros(4801, np.float32))):
+        with pytest.raises(hm.HMError):
+            hm.HMatrix(pts, 0, 0.1, 32, 1.0, 1e-6, precision=hm.PREC_MIXED, on_the_fly=True, **kw)
