@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-multi", action="store_true",
                    help="skip the 16-vector product measured beside the step")
+    p.add_argument("--no-otf", action="store_true",
+                   help="skip the on-the-fly products measured beside the step")
     p.add_argument("--no-paper", action="store_true",
                    help="skip the context run in the paper's own setting (N=2^19 Halton, C=2048)")
     p.add_argument("--n", type=int, default=0,
@@ -611,6 +613,43 @@ def main():
                          "x, perm and y per vector"}
         Hm.free()
 
+    # the on-the-fly product (nothing stored: ACA and the dense leaves are
+    # recomputed inside every product), reported beside the step: on this
+    # workload, and on the 3-D Matern workload at N = 2^20, whose stored
+    # H-matrix does not fit one GPU
+    otf = None
+    if world == 1 and not args.no_otf:
+        otf = []
+        for wname in (args.workload, "matern3d_n1m"):
+            wo = dict(inputs.WORKLOADS[wname])
+            if wname == args.workload and args.n:
+                wo["n"] = args.n
+            po = pts if wname == args.workload else torch.from_numpy(
+                inputs.workload_points(wname, wo["n"])).cuda()
+            xo = x if wname == args.workload else torch.from_numpy(
+                inputs.normal_vector(wo["n"], inputs.X_SEED)).cuda()
+            yo = torch.empty_like(xo)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            reps = 2
+            torch.cuda.synchronize()
+            ev[0].record(stream)
+            Ho = hm.HMatrix(po, wo["kernel"], wo["ell"], wo["leaf"], wo["eta"], wo["eps"],
+                            precision=hm.PREC_MIXED, on_the_fly=True,
+                            adm_max=(wo["adm"] == "max"))
+            ev[1].record(stream)
+            for _ in range(reps):
+                Ho.matvec(xo, yo)
+            ev[2].record(stream)
+            torch.cuda.synchronize()
+            so = Ho.stats()
+            otf.append({"workload": wname, "n": wo["n"], "precision": "mixed",
+                        "build_s": ev[0].elapsed_time(ev[1]) / 1e3,
+                        "mvp_ms": ev[1].elapsed_time(ev[2]) / reps,
+                        "aca_passes_per_product": so["aca_passes"], "n_adm": so["n_adm"],
+                        "n_dense": so["n_dense"]})
+            Ho.free()
+            del po, xo, yo
+
     # e2e: the same step through the C-ABI with pinned host buffers
     pts_h = torch.from_numpy(pts_np).pin_memory()
     xs_h = torch.from_numpy(x_np).pin_memory()
@@ -696,7 +735,7 @@ def main():
         "build_s": build_ms / 1e3, "mvp_ms": mvp_ms,
         "fp64": fp64, "mixed_vs_fp64_rel_err": err,
         "mixed_without_rank_model": plain, "mixed_nonsymmetric": nonsym,
-        "multi_rhs": multi,
+        "multi_rhs": multi, "on_the_fly": otf,
         "rank_model": model_info,
         "speedup_vs_fp64": (fp64["ms_per_step"] / total) if fp64 else None,
         "e2e": {"value": e2e_ms / 1e3, "unit": "s/step (build + %d H-MVP)" % N_MVP,
