@@ -226,10 +226,14 @@ void np_lowrank(int precision, const Blk* ablk, const int32_t* rank, const uint6
                 const uint64_t* Vptr, int64_t b0, int64_t b1, const int64_t* lr_ptr,
                 const int2* lr_ent, const int64_t* tile_row0, const int32_t* tile_m,
                 int64_t n_tiles, const void* xm, void* t, int kcap, double* yacc, cudaStream_t s);
-// y_m += A_b x|sigma for every dense leaf, entries evaluated on the fly.
-void np_near(int precision, const KernelParams& kp, const DeviceCoords& X, const Blk* dblk,
-             const int64_t* dn_ptr, const int2* dn_ent, const int64_t* tile_row0,
-             const int32_t* tile_m, int64_t n_tiles, const void* xm, double* yacc, cudaStream_t s);
+// y_m += A_b x|sigma for every dense leaf, entries evaluated on the fly, over
+// the gather's work items (runs of a tile's near-field column stream); part
+// holds n_items * max_ld partial row sums.
+void np_near(int precision, const KernelParams& kp, const DeviceCoords& X, const int3* items,
+             int64_t n_items, const int64_t* item_ptr, const int64_t* ucol_ptr,
+             const int64_t* ncol_ptr, const int32_t* ncol_x, const int64_t* tile_row0,
+             const int32_t* tile_m, int64_t n_tiles, int max_ld, const void* xm, double* part,
+             double* yacc, cudaStream_t s);
 // y[perm[i]] = y_m[i] + sigma^2 x[perm[i]] (or +=).
 void np_finish(const int64_t* perm, const double* sig_row, double sigma2, int64_t N,
                const double* yacc, const double* x, double* y, int accumulate, cudaStream_t s);

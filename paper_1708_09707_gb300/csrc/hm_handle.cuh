@@ -61,8 +61,8 @@ struct hm_handle_s {
     std::vector<int64_t> np_pass;
     hm::DevBuf<uint32_t> np_ids;
     hm::DevBuf<char> np_scratch, np_t, np_xm;
-    hm::DevBuf<double> np_yacc;
-    int np_kcap = 0;
+    hm::DevBuf<double> np_yacc, np_part;   // row sums; near-field item sums
+    int np_kcap = 0, np_ld = 0;             // t entries per leaf; rows per item sum
     hm::DevBuf<int> status;
     hm_stats stats{};
     ~hm_handle_s();

@@ -6,7 +6,8 @@
 //
 // Determinism: every row of y is one running sum in double, fed in a fixed
 // order: the admissible leaves of the row's tile in block order (the passes
-// take consecutive block ranges), then its dense leaves in block order.
+// take consecutive block ranges), then the near-field item sums of the tile
+// in item order, each summed in a fixed pattern of warps and columns.
 #include "hm_kernel_fn.cuh"
 #include "hm_stream.cuh"
 
@@ -85,36 +86,88 @@ __global__ void k_np_apply(const int64_t* __restrict__ lr_ptr, const int2* __res
     }
 }
 
-// y_m += A_b x|sigma over the dense leaves of every row tile, the entries
-// phi(y_i, y_j) evaluated on the fly (the same kernel functions as the stored
-// near field); one warp per tile, lane i takes rows i, i + 32, ... Each leaf's
-// plain sum goes into a compensated accumulator (float) or a double sum.
+// The dense leaves of the product, entries phi(y_i, y_j) evaluated on the fly
+// (the same kernel functions as the stored near field). One CTA per work item
+// of the gather (a run of at most 4096 columns of one row tile's near-field
+// column stream, column c the point ncol_x[c]): warp w takes the columns w,
+// w + 8, ... of the item, lane i the rows i and i + 32 of each 64-row window;
+// plain sums over 16 of a warp's columns enter a compensated sum (double sum
+// in FP64), the warps' sums add in warp order into the item's partial row
+// sums, and k_np_near_finish adds the items of a tile in item order.
+constexpr int NN_W = 8;
+constexpr int NN_ROWS = 64;
+
 template <class R, int KERN>
-__global__ void k_np_near(KernelParams kp, DeviceCoords X, const Blk* __restrict__ dblk,
-                          const int64_t* __restrict__ dn_ptr, const int2* __restrict__ dn_ent,
-                          const int64_t* __restrict__ tile_row0, const int32_t* __restrict__ tile_m,
-                          int64_t n_tiles, const R* __restrict__ xm, double* __restrict__ yacc)
+__global__ void __launch_bounds__(NN_W * 32)
+k_np_near(KernelParams kp, DeviceCoords X, const int3* __restrict__ items,
+          const int64_t* __restrict__ ucol_ptr, const int64_t* __restrict__ ncol_ptr,
+          const int32_t* __restrict__ ncol_x, const int64_t* __restrict__ tile_row0,
+          const int32_t* __restrict__ tile_m, int max_ld, const R* __restrict__ xm,
+          double* __restrict__ part)
+{
+    __shared__ double ps[NN_W][NN_ROWS];
+    const int64_t item = blockIdx.x;
+    const int3 it = items[item];
+    const int64_t tile = it.x;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t r0 = tile_row0[tile];
+    const int mt = tile_m[tile];
+    const int64_t nu = ucol_ptr[tile + 1] - ucol_ptr[tile];
+    const int64_t nc0 = ncol_ptr[tile];
+    const int64_t cb = it.y > nu ? it.y - nu : 0, ce = it.z > nu ? it.z - nu : 0;
+    const R c = kconst<R>(kp);
+    for (int rw = 0; rw < mt; rw += NN_ROWS) {
+        const int ia = rw + lane, ib = rw + lane + 32;
+        const Pt<R> pa = load_pt<R>(X, r0 + min(ia, mt - 1));
+        const Pt<R> pb = load_pt<R>(X, r0 + min(ib, mt - 1));
+        Acc<R> aa, ab;
+        R sa = R(0), sb = R(0);
+        int cnt = 0;
+        for (int64_t col = cb + w; col < ce; col += NN_W) {
+            const int32_t q = ncol_x[nc0 + col];
+            const Pt<R> pq = load_pt<R>(X, q);
+            const R xq = xm[q];
+            sa = fma(phi<KERN>(dist2(pa, pq), c), xq, sa);
+            sb = fma(phi<KERN>(dist2(pb, pq), c), xq, sb);
+            if (++cnt == 16) {
+                aa.add(sa);
+                ab.add(sb);
+                sa = sb = R(0);
+                cnt = 0;
+            }
+        }
+        aa.add(sa);
+        ab.add(sb);
+        ps[w][lane] = aa.value();
+        ps[w][lane + 32] = ab.value();
+        __syncthreads();
+        const int rows = min(NN_ROWS, mt - rw);
+        if ((int)threadIdx.x < rows) {
+            double sum = 0.0;
+#pragma unroll
+            for (int q = 0; q < NN_W; ++q) sum += ps[q][threadIdx.x];
+            part[item * max_ld + rw + threadIdx.x] = sum;
+        }
+        __syncthreads();
+    }
+}
+
+// y_m += the near-field item sums of every tile, in item order (one warp per tile).
+__global__ void k_np_near_finish(const int64_t* __restrict__ item_ptr,
+                                 const int64_t* __restrict__ tile_row0,
+                                 const int32_t* __restrict__ tile_m, int64_t n_tiles, int max_ld,
+                                 const double* __restrict__ part, double* __restrict__ yacc)
 {
     const int64_t tile = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (tile >= n_tiles) return;
     const int64_t r0 = tile_row0[tile];
     const int mt = tile_m[tile];
-    const int64_t e0 = dn_ptr[tile], e1 = dn_ptr[tile + 1];
-    const R c = kconst<R>(kp);
+    const int64_t i0 = item_ptr[tile], i1 = item_ptr[tile + 1];
     for (int i = lane; i < mt; i += 32) {
-        const Pt<R> p = load_pt<R>(X, r0 + i);
-        Acc<R> acc;
-        for (int64_t e = e0; e < e1; ++e) {
-            const Blk B = dblk[dn_ent[e].x];
-            R s = R(0);
-            for (int j = 0; j < B.n; ++j) {
-                const Pt<R> q = load_pt<R>(X, B.col0 + j);
-                s = fma(phi<KERN>(dist2(p, q), c), xm[B.col0 + j], s);
-            }
-            acc.add(s);
-        }
-        yacc[r0 + i] += acc.value();
+        double sum = 0.0;
+        for (int64_t q = i0; q < i1; ++q) sum += part[q * max_ld + i];
+        yacc[r0 + i] += sum;
     }
 }
 
@@ -174,29 +227,36 @@ void np_lowrank(int precision, const Blk* ablk, const int32_t* rank, const uint6
     HM_LAUNCH("np low-rank part");
 }
 
-void np_near(int precision, const KernelParams& kp, const DeviceCoords& X, const Blk* dblk,
-             const int64_t* dn_ptr, const int2* dn_ent, const int64_t* tile_row0,
-             const int32_t* tile_m, int64_t n_tiles, const void* xm, double* yacc, cudaStream_t s)
+void np_near(int precision, const KernelParams& kp, const DeviceCoords& X, const int3* items,
+             int64_t n_items, const int64_t* item_ptr, const int64_t* ucol_ptr,
+             const int64_t* ncol_ptr, const int32_t* ncol_x, const int64_t* tile_row0,
+             const int32_t* tile_m, int64_t n_tiles, int max_ld, const void* xm, double* part,
+             double* yacc, cudaStream_t s)
 {
-    if (n_tiles <= 0) return;
-    const unsigned g = grid_for(n_tiles * 32);
+    if (n_tiles <= 0 || n_items <= 0) return;
+    if (n_items > 0x7fffffffll) fail(HM_EOVERFLOW, "too many near-field items for one launch");
+    const unsigned g = (unsigned)n_items;
+    const int bs = NN_W * 32;
     if (precision == HM_PREC_FP64) {
         const double* xd = static_cast<const double*>(xm);
         if (kp.kernel == HM_GAUSSIAN)
-            k_np_near<double, HM_GAUSSIAN><<<g, NT, 0, s>>>(kp, X, dblk, dn_ptr, dn_ent, tile_row0,
-                                                            tile_m, n_tiles, xd, yacc);
+            k_np_near<double, HM_GAUSSIAN><<<g, bs, 0, s>>>(kp, X, items, ucol_ptr, ncol_ptr, ncol_x,
+                                                            tile_row0, tile_m, max_ld, xd, part);
         else
-            k_np_near<double, HM_MATERN32><<<g, NT, 0, s>>>(kp, X, dblk, dn_ptr, dn_ent, tile_row0,
-                                                            tile_m, n_tiles, xd, yacc);
+            k_np_near<double, HM_MATERN32><<<g, bs, 0, s>>>(kp, X, items, ucol_ptr, ncol_ptr, ncol_x,
+                                                            tile_row0, tile_m, max_ld, xd, part);
     } else {
         const float* xf = static_cast<const float*>(xm);
         if (kp.kernel == HM_GAUSSIAN)
-            k_np_near<float, HM_GAUSSIAN><<<g, NT, 0, s>>>(kp, X, dblk, dn_ptr, dn_ent, tile_row0,
-                                                           tile_m, n_tiles, xf, yacc);
+            k_np_near<float, HM_GAUSSIAN><<<g, bs, 0, s>>>(kp, X, items, ucol_ptr, ncol_ptr, ncol_x,
+                                                           tile_row0, tile_m, max_ld, xf, part);
         else
-            k_np_near<float, HM_MATERN32><<<g, NT, 0, s>>>(kp, X, dblk, dn_ptr, dn_ent, tile_row0,
-                                                           tile_m, n_tiles, xf, yacc);
+            k_np_near<float, HM_MATERN32><<<g, bs, 0, s>>>(kp, X, items, ucol_ptr, ncol_ptr, ncol_x,
+                                                           tile_row0, tile_m, max_ld, xf, part);
     }
+    note_launch();
+    k_np_near_finish<<<grid_for(n_tiles * 32), NT, 0, s>>>(item_ptr, tile_row0, tile_m, n_tiles,
+                                                           max_ld, part, yacc);
     note_launch();
     HM_LAUNCH("np near field");
 }

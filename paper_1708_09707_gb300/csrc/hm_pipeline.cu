@@ -617,6 +617,8 @@ void np_prepare(hm_handle_s& h)
     h.np_t.alloc((size_t)most * h.np_kcap * esz, s);
     h.np_xm.alloc((size_t)std::max<int64_t>(h.Ntot, 1) * esz, s);
     h.np_yacc.alloc(std::max<int64_t>(h.Ntot, 1), s);
+    h.np_ld = h.leaf;
+    h.np_part.alloc((size_t)std::max<int64_t>(h.lists.n_items, 1) * std::max(h.np_ld, 1), s);
     HM_CUDA(cudaStreamSynchronize(s));
 }
 
@@ -653,8 +655,9 @@ void np_matvec(hm_handle_s& h, const double* x, double* y, cudaStream_t s)
                    h.np_kcap, h.np_yacc.p, hs);
     }
     check_status(h);
-    np_near(h.precision, h.kp, h.X, h.dblk.p, h.lists.dn_ptr.p, h.lists.dn_ent.p, h.tile_row0.p,
-            h.tile_m.p, h.n_tiles, h.np_xm.p, h.np_yacc.p, hs);
+    np_near(h.precision, h.kp, h.X, h.lists.items.p, h.lists.n_items, h.lists.item_ptr.p,
+            h.lists.ucol_ptr.p, h.lists.ncol_ptr.p, h.lists.ncol_x.p, h.tile_row0.p, h.tile_m.p,
+            h.n_tiles, h.np_ld, h.np_xm.p, h.np_part.p, h.np_yacc.p, hs);
     np_finish(h.perm.p, nullptr, h.sigma2, N, h.np_yacc.p, x, y, h.opt.accumulate, hs);
     if (ev) {
         HM_CUDA(cudaEventRecord(ev, hs));
