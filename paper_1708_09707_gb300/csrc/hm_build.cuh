@@ -220,12 +220,24 @@ void mvp_run_multi(const MvpPlan& P, MvpWork& W, const double* x, double* y, int
 // Kernels of the on-the-fly product (no stored factors or near field).
 void np_gather_x(int precision, const double* x, const int64_t* perm, int64_t N, void* xm,
                  cudaStream_t s);
-// t_b = V_b^T x|sigma, then y_m += U_b t_b for the admissible leaves
-// b0 <= b < b1 (factors as left by ACA), in block order per row tile.
+// Work lists of the on-the-fly low-rank part: V^T x items (block, first
+// column) of 256 columns, consecutive per block from vptr[b] (h_vptr: host
+// copy); apply items (tile, first entry, end entry) of at most 16 entries of
+// the tile's admissible-leaf list, consecutive per tile from aptr[tile].
+void np_lists(const Blk* ablk, int64_t n_adm, const int64_t* lr_ptr, int64_t n_tiles,
+              DevBuf<int64_t>& vptr, DevBuf<int2>& vitems, DevBuf<int64_t>& aptr,
+              DevBuf<int3>& aitems, std::vector<int64_t>& h_vptr, int64_t& n_aitems, cudaStream_t s);
+// For the admissible leaves b0 <= b < b1 (factors as left by ACA):
+// t_b = V_b^T x|sigma (items vi0 .. vi1 - 1, partials in tp, sums in t), then
+// every apply item's running row sums += U_b t_b in block order.
 void np_lowrank(int precision, const Blk* ablk, const int32_t* rank, const uint64_t* Uptr,
-                const uint64_t* Vptr, int64_t b0, int64_t b1, const int64_t* lr_ptr,
-                const int2* lr_ent, const int64_t* tile_row0, const int32_t* tile_m,
-                int64_t n_tiles, const void* xm, void* t, int kcap, double* yacc, cudaStream_t s);
+                const uint64_t* Vptr, int64_t b0, int64_t b1, const int64_t* vptr,
+                const int2* vitems, int64_t vi0, int64_t vi1, const int3* aitems,
+                int64_t n_aitems, const int2* lr_ent, const int32_t* tile_m, const void* xm,
+                void* tp, void* t, int kcap, int ld, double* item_acc, cudaStream_t s);
+// y_m += the apply items' row sums of every tile, in item order.
+void np_apply_finish(const int64_t* aptr, const int64_t* tile_row0, const int32_t* tile_m,
+                     int64_t n_tiles, int ld, const double* item_acc, double* yacc, cudaStream_t s);
 // y_m += A_b x|sigma for every dense leaf, entries evaluated on the fly, over
 // the gather's work items (runs of a tile's near-field column stream); part
 // holds n_items * max_ld partial row sums.

@@ -63,6 +63,15 @@ struct hm_handle_s {
     hm::DevBuf<char> np_scratch, np_t, np_xm;
     hm::DevBuf<double> np_yacc, np_part;   // row sums; near-field item sums
     int np_kcap = 0, np_ld = 0;             // t entries per leaf; rows per item sum
+    // V^T x items and apply items of the low-rank part, the t partials of a
+    // pass and the apply items' running row sums
+    hm::DevBuf<int64_t> np_vptr, np_aptr;
+    hm::DevBuf<int2> np_vitems;
+    hm::DevBuf<int3> np_aitems;
+    std::vector<int64_t> np_hvptr;
+    int64_t np_naitems = 0;
+    hm::DevBuf<char> np_tp;
+    hm::DevBuf<double> np_acc;
     hm::DevBuf<int> status;
     hm_stats stats{};
     ~hm_handle_s();

@@ -11,6 +11,8 @@
 #include "hm_kernel_fn.cuh"
 #include "hm_stream.cuh"
 
+#include <vector>
+
 namespace hm {
 
 namespace {
@@ -26,63 +28,156 @@ __global__ void k_np_gather_x(const double* __restrict__ x, const int64_t* __res
     if (i < N) xm[i] = (R)x[perm[i]];
 }
 
-// t_b = V_b^T x|sigma for the blocks b0 .. b0 + nb - 1: one warp per block,
-// lane j sums the columns j, j + 32, ... of every factor row l, the lane sums
-// meet in the xor butterfly. t_b starts at t + (b - b0) kcap.
+// Work lists, built once: V^T x items (block, first column) of VCH columns,
+// every block's items consecutive from vptr[b]; apply items (tile, first
+// entry, end entry) of at most NP_AE entries of the tile's list of
+// admissible leaves, every tile's items consecutive from aptr[tile].
+constexpr int NP_AE = 16;
+
+__global__ void k_np_vcount(const Blk* __restrict__ blk, int64_t n, int64_t* __restrict__ cnt)
+{
+    const int64_t b = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (b < n) cnt[b] = ceil_div((int64_t)blk[b].n, (int64_t)VCH);
+}
+
+__global__ void k_np_vemit(const Blk* __restrict__ blk, int64_t n, const int64_t* __restrict__ vptr,
+                           int2* __restrict__ items)
+{
+    const int64_t b = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (b >= n) return;
+    const int64_t c = vptr[b + 1] - vptr[b];
+    for (int64_t q = 0; q < c; ++q) items[vptr[b] + q] = make_int2((int)b, (int)(q * VCH));
+}
+
+__global__ void k_np_acount(const int64_t* __restrict__ lr_ptr, int64_t nt, int64_t* __restrict__ cnt)
+{
+    const int64_t q = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (q < nt) cnt[q] = ceil_div(lr_ptr[q + 1] - lr_ptr[q], (int64_t)NP_AE);
+}
+
+__global__ void k_np_aemit(const int64_t* __restrict__ lr_ptr, int64_t nt,
+                           const int64_t* __restrict__ aptr, int3* __restrict__ items)
+{
+    const int64_t q = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (q >= nt) return;
+    const int64_t e0 = lr_ptr[q], e1 = lr_ptr[q + 1];
+    for (int64_t a = aptr[q]; a < aptr[q + 1]; ++a) {
+        const int64_t f = e0 + (a - aptr[q]) * NP_AE;
+        items[a] = make_int3((int)q, (int)f, (int)min(e1, f + NP_AE));
+    }
+}
+
+// t partials of the V^T x items vi0 .. vi0 + ni - 1: one warp per item, lane
+// j sums the columns j, j + 32, ... of the item's chunk for every factor row
+// l, the lane sums meet in the xor butterfly; partial (item, l) goes to
+// tp[(item - vi0) kcap + l].
 template <class R>
 __global__ void k_np_vtx(const Blk* __restrict__ blk, const int32_t* __restrict__ rank,
-                         const uint64_t* __restrict__ Vptr, int64_t b0, int64_t nb,
-                         const R* __restrict__ xm, R* __restrict__ t, int kcap)
+                         const uint64_t* __restrict__ Vptr, const int2* __restrict__ items,
+                         int64_t vi0, int64_t ni, const R* __restrict__ xm, R* __restrict__ tp,
+                         int kcap)
 {
     const int64_t w = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (w >= nb) return;
-    const int64_t b = b0 + w;
-    const Blk B = blk[b];
-    const int k = rank[b];
-    const int n = B.n;
-    const R* __restrict__ V = reinterpret_cast<const R*>(Vptr[b]);
-    const R* __restrict__ xs = xm + B.col0;
-    R* out = t + w * kcap;
+    if (w >= ni) return;
+    const int2 it = items[vi0 + w];
+    const Blk B = blk[it.x];
+    const int k = rank[it.x];
+    const int n = B.n, c0 = it.y;
+    const int cn = min(VCH, n - c0);
+    const R* __restrict__ V = reinterpret_cast<const R*>(Vptr[it.x]) + c0;
+    R xs[VCH / 32];
+#pragma unroll
+    for (int q = 0; q < VCH / 32; ++q) {
+        const int jj = lane + 32 * q;
+        xs[q] = jj < cn ? xm[B.col0 + c0 + jj] : R(0);
+    }
+    R* out = tp + w * kcap;
     for (int l = 0; l < k; ++l) {
         const R* Vl = V + (int64_t)l * n;
         R s = R(0);
-        for (int j = lane; j < n; j += 32) s = fma(__ldcs(Vl + j), xs[j], s);
+#pragma unroll
+        for (int q = 0; q < VCH / 32; ++q) {
+            const int jj = lane + 32 * q;
+            if (jj < cn) s = fma(__ldcs(Vl + jj), xs[q], s);
+        }
         s = warp_sum(s);
         if (lane == 0) out[l] = s;
     }
 }
 
-// y_m += U_b t_b over the admissible leaves b0 <= b < b1 of every row tile,
-// in block order; one warp per tile, lane i takes rows i, i + 32, ...
+// t_b = sum of its items' partials in item order, for the blocks b0 .. b0 +
+// nb - 1 (one warp per block); t_b starts at t + (b - b0) kcap.
 template <class R>
-__global__ void k_np_apply(const int64_t* __restrict__ lr_ptr, const int2* __restrict__ lr_ent,
-                           const Blk* __restrict__ blk, const int32_t* __restrict__ rank,
-                           const uint64_t* __restrict__ Uptr, const int64_t* __restrict__ tile_row0,
-                           const int32_t* __restrict__ tile_m, int64_t n_tiles, int64_t b0,
-                           int64_t b1, const R* __restrict__ t, int kcap, double* __restrict__ yacc)
+__global__ void k_np_tsum(const int64_t* __restrict__ vptr, int64_t b0, int64_t nb,
+                          const int32_t* __restrict__ rank, int64_t vi0, const R* __restrict__ tp,
+                          R* __restrict__ t, int kcap)
 {
-    const int64_t tile = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
+    const int64_t w = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (tile >= n_tiles) return;
-    const int64_t r0 = tile_row0[tile];
-    const int mt = tile_m[tile];
-    const int64_t e0 = lr_ptr[tile], e1 = lr_ptr[tile + 1];
+    if (w >= nb) return;
+    const int64_t b = b0 + w;
+    const int k = rank[b];
+    const int64_t f = vptr[b] - vi0, c = vptr[b + 1] - vptr[b];
+    for (int l = lane; l < k; l += 32) {
+        R s = R(0);
+        for (int64_t q = 0; q < c; ++q) s += tp[(f + q) * kcap + l];
+        t[w * kcap + l] = s;
+    }
+}
+
+// U_b t_b over the admissible leaves b0 <= b < b1 of every apply item, added
+// to the item's running row sums in entry (= block) order; one warp per item,
+// lane i takes rows i, i + 32, ... (item_acc holds ld sums per item).
+template <class R>
+__global__ void k_np_apply(const int3* __restrict__ items, int64_t n_items,
+                           const int2* __restrict__ lr_ent, const Blk* __restrict__ blk,
+                           const int32_t* __restrict__ rank, const uint64_t* __restrict__ Uptr,
+                           const int32_t* __restrict__ tile_m, int64_t b0, int64_t b1,
+                           const R* __restrict__ t, int kcap, int ld, double* __restrict__ item_acc)
+{
+    const int64_t w = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= n_items) return;
+    const int3 it = items[w];
+    int e0 = it.y, e1 = it.z;
+    // the item's entries in this pass (entries ascend by block)
+    while (e0 < e1 && lr_ent[e0].x < b0) ++e0;
+    if (e0 >= e1 || lr_ent[e0].x >= b1) return;
+    const int mt = tile_m[it.x];
     for (int i = lane; i < mt; i += 32) {
-        double yv = yacc[r0 + i];
-        for (int64_t e = e0; e < e1; ++e) {
+        double v = item_acc[w * ld + i];
+        for (int e = e0; e < e1; ++e) {
             const int2 en = lr_ent[e];
-            if (en.x < b0) continue;
-            if (en.x >= b1) break;   // entries ascend by block
+            if (en.x >= b1) break;
             const int k = rank[en.x];
             const int m = blk[en.x].m;
             const R* __restrict__ U = reinterpret_cast<const R*>(Uptr[en.x]) + en.y + i;
             const R* __restrict__ tb = t + (int64_t)(en.x - b0) * kcap;
             R c = R(0);
             for (int l = 0; l < k; ++l) c = fma(U[(int64_t)l * m], tb[l], c);
-            yv += (double)c;
+            v += (double)c;
         }
-        yacc[r0 + i] = yv;
+        item_acc[w * ld + i] = v;
+    }
+}
+
+// y_m += the apply items' row sums of every tile, in item order (one warp per tile).
+__global__ void k_np_apply_finish(const int64_t* __restrict__ aptr,
+                                  const int64_t* __restrict__ tile_row0,
+                                  const int32_t* __restrict__ tile_m, int64_t n_tiles, int ld,
+                                  const double* __restrict__ item_acc, double* __restrict__ yacc)
+{
+    const int64_t tile = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (tile >= n_tiles) return;
+    const int64_t r0 = tile_row0[tile];
+    const int mt = tile_m[tile];
+    const int64_t a0 = aptr[tile], a1 = aptr[tile + 1];
+    for (int i = lane; i < mt; i += 32) {
+        double sum = 0.0;
+        for (int64_t q = a0; q < a1; ++q) sum += item_acc[q * ld + i];
+        yacc[r0 + i] += sum;
     }
 }
 
@@ -197,34 +292,95 @@ void np_gather_x(int precision, const double* x, const int64_t* perm, int64_t N,
     HM_LAUNCH("np gather x");
 }
 
-void np_lowrank(int precision, const Blk* ablk, const int32_t* rank, const uint64_t* Uptr,
-                const uint64_t* Vptr, int64_t b0, int64_t b1, const int64_t* lr_ptr,
-                const int2* lr_ent, const int64_t* tile_row0, const int32_t* tile_m,
-                int64_t n_tiles, const void* xm, void* t, int kcap, double* yacc, cudaStream_t s)
+void np_lists(const Blk* ablk, int64_t n_adm, const int64_t* lr_ptr, int64_t n_tiles,
+              DevBuf<int64_t>& vptr, DevBuf<int2>& vitems, DevBuf<int64_t>& aptr,
+              DevBuf<int3>& aitems, std::vector<int64_t>& h_vptr, int64_t& n_aitems, cudaStream_t s)
 {
-    const int64_t nb = b1 - b0;
+    const int64_t nb = std::max<int64_t>(n_adm, 1);
+    vptr.alloc(nb + 1, s);
+    HM_CUDA(cudaMemsetAsync(vptr.p, 0, (nb + 1) * sizeof(int64_t), s));
+    h_vptr.assign(n_adm + 1, 0);
+    if (n_adm > 0) {
+        DevBuf<int64_t> cnt(n_adm, s);
+        k_np_vcount<<<grid_for(n_adm), NT, 0, s>>>(ablk, n_adm, cnt.p); note_launch();
+        scan_exclusive_i64(cnt.p, vptr.p, n_adm, vptr.p + n_adm, s);
+        HM_CUDA(cudaMemcpyAsync(h_vptr.data(), vptr.p, (n_adm + 1) * sizeof(int64_t),
+                                cudaMemcpyDeviceToHost, s));
+        HM_CUDA(cudaStreamSynchronize(s));
+    }
+    vitems.alloc(std::max<int64_t>(h_vptr[n_adm], 1), s);
+    if (n_adm > 0) {
+        k_np_vemit<<<grid_for(n_adm), NT, 0, s>>>(ablk, n_adm, vptr.p, vitems.p); note_launch();
+    }
+    aptr.alloc(n_tiles + 1, s);
+    HM_CUDA(cudaMemsetAsync(aptr.p, 0, (n_tiles + 1) * sizeof(int64_t), s));
+    n_aitems = 0;
+    if (n_tiles > 0) {
+        DevBuf<int64_t> cnt(n_tiles, s);
+        k_np_acount<<<grid_for(n_tiles), NT, 0, s>>>(lr_ptr, n_tiles, cnt.p); note_launch();
+        scan_exclusive_i64(cnt.p, aptr.p, n_tiles, aptr.p + n_tiles, s);
+        HM_CUDA(cudaMemcpyAsync(&n_aitems, aptr.p + n_tiles, sizeof(int64_t),
+                                cudaMemcpyDeviceToHost, s));
+        HM_CUDA(cudaStreamSynchronize(s));
+    }
+    aitems.alloc(std::max<int64_t>(n_aitems, 1), s);
+    if (n_tiles > 0) {
+        k_np_aemit<<<grid_for(n_tiles), NT, 0, s>>>(lr_ptr, n_tiles, aptr.p, aitems.p); note_launch();
+    }
+    HM_LAUNCH("np lists");
+    HM_CUDA(cudaStreamSynchronize(s));
+}
+
+void np_lowrank(int precision, const Blk* ablk, const int32_t* rank, const uint64_t* Uptr,
+                const uint64_t* Vptr, int64_t b0, int64_t b1, const int64_t* vptr,
+                const int2* vitems, int64_t vi0, int64_t vi1, const int3* aitems,
+                int64_t n_aitems, const int2* lr_ent, const int32_t* tile_m, const void* xm,
+                void* tp, void* t, int kcap, int ld, double* item_acc, cudaStream_t s)
+{
+    const int64_t nb = b1 - b0, ni = vi1 - vi0;
     if (nb <= 0) return;
     if (precision == HM_PREC_FP64) {
-        k_np_vtx<double><<<grid_for(nb * 32), NT, 0, s>>>(ablk, rank, Vptr, b0, nb,
-                                                          static_cast<const double*>(xm),
-                                                          static_cast<double*>(t), kcap);
+        const double* x = static_cast<const double*>(xm);
+        double* p = static_cast<double*>(tp);
+        double* tt = static_cast<double*>(t);
+        if (ni > 0) {
+            k_np_vtx<double><<<grid_for(ni * 32), NT, 0, s>>>(ablk, rank, Vptr, vitems, vi0, ni, x, p, kcap);
+            note_launch();
+        }
+        k_np_tsum<double><<<grid_for(nb * 32), NT, 0, s>>>(vptr, b0, nb, rank, vi0, p, tt, kcap);
         note_launch();
-        if (n_tiles > 0)
-            k_np_apply<double><<<grid_for(n_tiles * 32), NT, 0, s>>>(
-                lr_ptr, lr_ent, ablk, rank, Uptr, tile_row0, tile_m, n_tiles, b0, b1,
-                static_cast<const double*>(t), kcap, yacc);
+        if (n_aitems > 0) {
+            k_np_apply<double><<<grid_for(n_aitems * 32), NT, 0, s>>>(
+                aitems, n_aitems, lr_ent, ablk, rank, Uptr, tile_m, b0, b1, tt, kcap, ld, item_acc);
+            note_launch();
+        }
     } else {
-        k_np_vtx<float><<<grid_for(nb * 32), NT, 0, s>>>(ablk, rank, Vptr, b0, nb,
-                                                         static_cast<const float*>(xm),
-                                                         static_cast<float*>(t), kcap);
+        const float* x = static_cast<const float*>(xm);
+        float* p = static_cast<float*>(tp);
+        float* tt = static_cast<float*>(t);
+        if (ni > 0) {
+            k_np_vtx<float><<<grid_for(ni * 32), NT, 0, s>>>(ablk, rank, Vptr, vitems, vi0, ni, x, p, kcap);
+            note_launch();
+        }
+        k_np_tsum<float><<<grid_for(nb * 32), NT, 0, s>>>(vptr, b0, nb, rank, vi0, p, tt, kcap);
         note_launch();
-        if (n_tiles > 0)
-            k_np_apply<float><<<grid_for(n_tiles * 32), NT, 0, s>>>(
-                lr_ptr, lr_ent, ablk, rank, Uptr, tile_row0, tile_m, n_tiles, b0, b1,
-                static_cast<const float*>(t), kcap, yacc);
+        if (n_aitems > 0) {
+            k_np_apply<float><<<grid_for(n_aitems * 32), NT, 0, s>>>(
+                aitems, n_aitems, lr_ent, ablk, rank, Uptr, tile_m, b0, b1, tt, kcap, ld, item_acc);
+            note_launch();
+        }
     }
-    if (n_tiles > 0) note_launch();
     HM_LAUNCH("np low-rank part");
+}
+
+void np_apply_finish(const int64_t* aptr, const int64_t* tile_row0, const int32_t* tile_m,
+                     int64_t n_tiles, int ld, const double* item_acc, double* yacc, cudaStream_t s)
+{
+    if (n_tiles <= 0) return;
+    k_np_apply_finish<<<grid_for(n_tiles * 32), NT, 0, s>>>(aptr, tile_row0, tile_m, n_tiles, ld,
+                                                            item_acc, yacc);
+    note_launch();
+    HM_LAUNCH("np low-rank sums");
 }
 
 void np_near(int precision, const KernelParams& kp, const DeviceCoords& X, const int3* items,

@@ -617,8 +617,15 @@ void np_prepare(hm_handle_s& h)
     h.np_t.alloc((size_t)most * h.np_kcap * esz, s);
     h.np_xm.alloc((size_t)std::max<int64_t>(h.Ntot, 1) * esz, s);
     h.np_yacc.alloc(std::max<int64_t>(h.Ntot, 1), s);
-    h.np_ld = h.leaf;
-    h.np_part.alloc((size_t)std::max<int64_t>(h.lists.n_items, 1) * std::max(h.np_ld, 1), s);
+    h.np_ld = std::max(h.leaf, 1);
+    h.np_part.alloc((size_t)std::max<int64_t>(h.lists.n_items, 1) * h.np_ld, s);
+    np_lists(h.ablk.p, n, h.lists.lr_ptr.p, h.n_tiles, h.np_vptr, h.np_vitems, h.np_aptr,
+             h.np_aitems, h.np_hvptr, h.np_naitems, s);
+    int64_t most_items = 1;
+    for (size_t q = 0; q + 1 < h.np_pass.size(); ++q)
+        most_items = std::max(most_items, h.np_hvptr[h.np_pass[q + 1]] - h.np_hvptr[h.np_pass[q]]);
+    h.np_tp.alloc((size_t)most_items * h.np_kcap * esz, s);
+    h.np_acc.alloc((size_t)std::max<int64_t>(h.np_naitems, 1) * h.np_ld, s);
     HM_CUDA(cudaStreamSynchronize(s));
 }
 
@@ -638,6 +645,7 @@ void np_matvec(hm_handle_s& h, const double* x, double* y, cudaStream_t s)
     const int64_t N = h.Ntot;
     const int esz = h.precision == HM_PREC_FP64 ? 8 : 4;
     HM_CUDA(cudaMemsetAsync(h.np_yacc.p, 0, N * sizeof(double), hs));
+    HM_CUDA(cudaMemsetAsync(h.np_acc.p, 0, h.np_acc.bytes(), hs));
     np_gather_x(h.precision, x, h.perm.p, N, h.np_xm.p, hs);
     DevBuf<int64_t> setn;
     const AcaArgs a = aca_args(h, setn);
@@ -650,11 +658,14 @@ void np_matvec(hm_handle_s& h, const double* x, double* y, cudaStream_t s)
                                                  h.np_scratch.p, vbase, esz, h.Uptr.p, h.Vptr.p); note_launch();
         HM_LAUNCH("set ptrs");
         aca_range(h, O, a, 0, nb);
-        np_lowrank(h.precision, h.ablk.p, h.rank.p, h.Uptr.p, h.Vptr.p, b0, b1, h.lists.lr_ptr.p,
-                   h.lists.lr_ent.p, h.tile_row0.p, h.tile_m.p, h.n_tiles, h.np_xm.p, h.np_t.p,
-                   h.np_kcap, h.np_yacc.p, hs);
+        np_lowrank(h.precision, h.ablk.p, h.rank.p, h.Uptr.p, h.Vptr.p, b0, b1, h.np_vptr.p,
+                   h.np_vitems.p, h.np_hvptr[b0], h.np_hvptr[b1], h.np_aitems.p, h.np_naitems,
+                   h.lists.lr_ent.p, h.tile_m.p, h.np_xm.p, h.np_tp.p, h.np_t.p, h.np_kcap,
+                   h.np_ld, h.np_acc.p, hs);
     }
     check_status(h);
+    np_apply_finish(h.np_aptr.p, h.tile_row0.p, h.tile_m.p, h.n_tiles, h.np_ld, h.np_acc.p,
+                    h.np_yacc.p, hs);
     np_near(h.precision, h.kp, h.X, h.lists.items.p, h.lists.n_items, h.lists.item_ptr.p,
             h.lists.ucol_ptr.p, h.lists.ncol_ptr.p, h.lists.ncol_x.p, h.tile_row0.p, h.tile_m.p,
             h.n_tiles, h.np_ld, h.np_xm.p, h.np_part.p, h.np_yacc.p, hs);

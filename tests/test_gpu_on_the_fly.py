@@ -96,3 +96,18 @@ def test_refused_combinations(hm):
     for kw in (dict(symmetric=True), dict(rank_model_theta=np.zeros(4801, np.float32))):
         with pytest.raises(hm.HMError):
             hm.HMatrix(pts, 0, 0.1, 32, 1.0, 1e-6, precision=hm.PREC_MIXED, on_the_fly=True, **kw)
+
+
+def test_no_admissible_leaf_and_eta_zero(hm, orc):
+    """C >= N leaves one dense block and eta = 0 admits no block of positive
+    diameter: both products are the dense matrix-vector product."""
+    pts = _pts(300, 2, "u", 51)
+    x = inputs.normal_vector(300, 8)
+    truth = orc.dense_matvec(pts, 0, 0.1, 0.0, x)
+    H = hm.HMatrix(pts, 0, 0.1, 512, 1.0, 1e-8, on_the_fly=True)
+    assert H.stats()["n_adm"] == 0
+    assert rel(H.matvec(x), truth) <= 1e-13
+    pts = _pts(2000, 2, "u", 52)
+    x = inputs.normal_vector(2000, 9)
+    H = hm.HMatrix(pts, 0, 0.1, 16, 0.0, 1e-8, on_the_fly=True)
+    assert rel(H.matvec(x), orc.dense_matvec(pts, 0, 0.1, 0.0, x)) <= 1e-13
