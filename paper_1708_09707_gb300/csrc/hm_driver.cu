@@ -182,7 +182,7 @@ void matvec(hm_handle_s& h, const double* x, double* y, int nrhs, cudaStream_t s
             if (h.opt.accumulate) copy_in(h.ybuf.p, yr, N * sizeof(double), s);
             yout = h.ybuf.p;
         }
-        if (h.opt.on_the_fly) np_matvec(h, xin, yout, s);
+        if (h.opt.on_the_fly) np_matvec(h, xin, yout, h.opt.accumulate, s);
         else mvp_run(h.plan, h.work, xin, yout, h.opt.accumulate, s, h.opt.profile ? &h.timer : nullptr);
         if (!yd) copy_out(yr, h.ybuf.p, N * sizeof(double), s);
     }
@@ -254,6 +254,7 @@ void export_factors(hm_handle_s& h, int64_t b, double* U, double* V, int* rank)
 {
     if (b < 0 || b >= h.n_adm) fail(HM_EINVAL, "block index out of range");
     if (h.opt.structure_only) fail(HM_EINVAL, "the handle was built with structure_only");
+    if (h.opt.on_the_fly) fail(HM_ENOTSUP, "an on-the-fly handle stores no factors");
     cudaStream_t s = h.stream;
     Blk B;
     int r = 0;
@@ -310,6 +311,13 @@ void export_factors(hm_handle_s& h, int64_t b, double* U, double* V, int* rank)
     HM_CUDA(cudaStreamSynchronize(s));
 }
 
+// q = (H + sigma^2 I) p on device vectors, whatever the storage mode.
+void apply_operator(hm_handle_s& h, const double* p, double* q, cudaStream_t s)
+{
+    if (h.opt.on_the_fly) np_matvec(h, p, q, 0, s);
+    else mvp_run(h.plan, h.work, p, q, 0, s);
+}
+
 void cg_solve(hm_handle_s& h, const double* b, double* x, double rtol, int maxit, int* iters,
               double* relres)
 {
@@ -319,7 +327,7 @@ void cg_solve(hm_handle_s& h, const double* b, double* x, double rtol, int maxit
     copy_in(bd.p, b, n * sizeof(double), s);
     copy_in(xd.p, x, n * sizeof(double), s);
     // sc[0] = rr, sc[1] = pq, sc[2] = rr_new, sc[3] = bb
-    mvp_run(h.plan, h.work, xd.p, q.p, 0, s);
+    apply_operator(h, xd.p, q.p, s);
     k_cg_init<<<grid_for(n), NT, 0, s>>>(bd.p, q.p, n, r.p, p.p); note_launch();
     dot(bd.p, bd.p, n, sc.p + 3, part.p, s);
     dot(r.p, r.p, n, sc.p, part.p, s);
@@ -331,7 +339,7 @@ void cg_solve(hm_handle_s& h, const double* b, double* x, double rtol, int maxit
     double rr = hs[0];
     int it = 0;
     while (it < maxit && std::sqrt(rr) / bn > rtol) {
-        mvp_run(h.plan, h.work, p.p, q.p, 0, s);
+        apply_operator(h, p.p, q.p, s);
         dot(p.p, q.p, n, sc.p + 1, part.p, s);
         k_cg_xr<<<grid_for(n), NT, 0, s>>>(sc.p, p.p, q.p, n, xd.p, r.p); note_launch();
         dot(r.p, r.p, n, sc.p + 2, part.p, s);

@@ -93,7 +93,7 @@ void build_sets(hm_handle_s& h, int nsets, const double* points_all, const int64
                 double aca_eps, const hm_options& opt);
 void matvec(hm_handle_s& h, const double* x, double* y, int nrhs, cudaStream_t s);
 // The product of an on-the-fly handle (device x, y; one vector).
-void np_matvec(hm_handle_s& h, const double* x, double* y, cudaStream_t s);
+void np_matvec(hm_handle_s& h, const double* x, double* y, int accumulate, cudaStream_t s);
 void export_structure(hm_handle_s& h, uint64_t* codes, int64_t* perm, int64_t* adm,
                       int64_t* dense, int32_t* ranks);
 void export_tree(hm_handle_s& h, int64_t* lo, int64_t* hi, double* bbmin, double* bbmax);

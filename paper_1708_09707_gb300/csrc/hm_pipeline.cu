@@ -633,7 +633,7 @@ void np_prepare(hm_handle_s& h)
 // of its leaves into the scratch, then t_b = V_b^T x|sigma and y_m += U_b t_b;
 // then the dense leaves evaluated on the fly. Runs on the handle's stream,
 // ordered after and before stream s.
-void np_matvec(hm_handle_s& h, const double* x, double* y, cudaStream_t s)
+void np_matvec(hm_handle_s& h, const double* x, double* y, int accumulate, cudaStream_t s)
 {
     cudaStream_t hs = h.stream;
     cudaEvent_t ev = nullptr;
@@ -669,7 +669,7 @@ void np_matvec(hm_handle_s& h, const double* x, double* y, cudaStream_t s)
     np_near(h.precision, h.kp, h.X, h.lists.items.p, h.lists.n_items, h.lists.item_ptr.p,
             h.lists.ucol_ptr.p, h.lists.ncol_ptr.p, h.lists.ncol_x.p, h.tile_row0.p, h.tile_m.p,
             h.n_tiles, h.np_ld, h.np_xm.p, h.np_part.p, h.np_yacc.p, hs);
-    np_finish(h.perm.p, nullptr, h.sigma2, N, h.np_yacc.p, x, y, h.opt.accumulate, hs);
+    np_finish(h.perm.p, nullptr, h.sigma2, N, h.np_yacc.p, x, y, accumulate, hs);
     if (ev) {
         HM_CUDA(cudaEventRecord(ev, hs));
         HM_CUDA(cudaStreamWaitEvent(s, ev, 0));

@@ -111,3 +111,20 @@ def test_no_admissible_leaf_and_eta_zero(hm, orc):
     x = inputs.normal_vector(2000, 9)
     H = hm.HMatrix(pts, 0, 0.1, 16, 0.0, 1e-8, on_the_fly=True)
     assert rel(H.matvec(x), orc.dense_matvec(pts, 0, 0.1, 0.0, x)) <= 1e-13
+
+
+def test_cg_with_on_the_fly_products(hm, orc):
+    """CG on (A + sigma^2 I) with an on-the-fly handle: every iteration
+    recomputes the H-matrix; the solution matches the oracle's CG."""
+    n = 3000
+    pts = inputs.uniform_points(n, 2, 41)
+    b = inputs.normal_vector(n, inputs.CG_SEED)
+    H = hm.HMatrix(pts, 1, 0.1, 32, 1.0, 1e-8, sigma2=0.1, on_the_fly=True)
+    O = orc.HMatrix(pts, 1, 0.1, 32, 1.0, 1e-8, sigma2=0.1)
+    x, it, rr = H.cg(b, rtol=1e-8, maxit=3000)
+    xo, ito, rro = O.cg(b, rtol=1e-8, maxit=3000)
+    assert rr <= 1e-8 and abs(it - ito) <= max(2, 0.02 * ito), (it, ito)
+    assert rel(x, xo) <= 1e-6
+    assert rel(H.matvec(x), b) <= 2e-8
+    with pytest.raises(hm.HMError):
+        H.factors(0, 32, 32)
