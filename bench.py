@@ -51,6 +51,9 @@ def parse():
                    help="skip the 16-vector product measured beside the step")
     p.add_argument("--no-otf", action="store_true",
                    help="skip the on-the-fly products measured beside the step")
+    p.add_argument("--otf-workloads", default="self,matern3d_n1m",
+                   help="comma-separated workloads of the on-the-fly measurement "
+                        "(self = the bench workload at its size)")
     p.add_argument("--no-paper", action="store_true",
                    help="skip the context run in the paper's own setting (N=2^19 Halton, C=2048)")
     p.add_argument("--n", type=int, default=0,
@@ -592,8 +595,10 @@ def main():
             Hm.matvec(Xr, Yr)
         torch.cuda.synchronize()
         ev[0].record(stream)
+        torch.cuda.nvtx.range_push("multi_rhs")
         for _ in range(reps):
             Hm.matvec(Xr, Yr)
+        torch.cuda.nvtx.range_pop()
         ev[1].record(stream)
         for _ in range(reps):
             for r in range(nr):
@@ -620,7 +625,8 @@ def main():
     otf = None
     if world == 1 and not args.no_otf:
         otf = []
-        for wname in (args.workload, "matern3d_n1m"):
+        names = [args.workload if q == "self" else q for q in args.otf_workloads.split(",")]
+        for wname in names:
             wo = dict(inputs.WORKLOADS[wname])
             if wname == args.workload and args.n:
                 wo["n"] = args.n
@@ -637,8 +643,10 @@ def main():
                             precision=hm.PREC_MIXED, on_the_fly=True,
                             adm_max=(wo["adm"] == "max"))
             ev[1].record(stream)
+            torch.cuda.nvtx.range_push("on_the_fly_" + wname)
             for _ in range(reps):
                 Ho.matvec(xo, yo)
+            torch.cuda.nvtx.range_pop()
             ev[2].record(stream)
             torch.cuda.synchronize()
             so = Ho.stats()
