@@ -20,8 +20,58 @@
 /* Matern order 3/2 are the workloads' parameters).                          */
 /*   Gaussian:    phi = exp(-(D2 * (1/(l*l))))                               */
 /*   Matern-3/2:  s = sqrt(D2) * (sqrt(3)/l),  phi = (1 + s) * exp(-s)       */
+/*   Matern K_1:  s = sqrt(D2) / l,  phi = s * K_1(s), phi(0) = 1: Sec. 6.2's */
+/*                Matern kernel with beta - d/2 = 1 without its constant      */
+/*                factor 1/(2^(beta-1) Gamma(beta)) (reading: a constant      */
+/*                factor of the whole matrix changes no block, rank or        */
+/*                relative error).                                            */
 /* D2 = sum_i (a_i - b_i)^2 accumulated over i = 0..d-1.                     */
 /* ------------------------------------------------------------------------ */
+
+/* K_1(x), x > 0, the modified Bessel function of the second kind of order 1.
+ * x <= 2: the ascending series (Abramowitz and Stegun 9.6.11 with n = 1)
+ *   K_1(x) = 1/x + ln(x/2) I_1(x)
+ *            - (x/4) sum_k (psi(k+1) + psi(k+2)) (x^2/4)^k / (k! (k+1)!),
+ *   I_1(x) = (x/2) sum_k (x^2/4)^k / (k! (k+1)!), psi(k+1) = -gamma + H_k,
+ *   summed over 20 terms (the 20th is below 1e-37 of the first).
+ * x > 2: the integral K_1(x) = int_0^inf exp(-x cosh u) cosh u du (A&S
+ *   9.6.24) by the trapezoidal rule with the step h = 0.2 / sqrt(x), up to
+ *   where x (cosh u - 1) exceeds 60 (the integrand is then below e^-60 of
+ *   its value at 0). The integrand is entire, so the rule's relative error is
+ *   about exp(x (1 - cos a) - 2 pi a / h) for a strip half-width a < pi/2:
+ *   below e^-60 with a = min(1.5, 10 / sqrt(x)), far below rounding. */
+static double or_bessel_k1(double x)
+{
+    if (x <= 2.0) {
+        const double euler_gamma = 0.57721566490153286061;
+        double q = 0.25 * x * x;
+        double term = 1.0;                 /* (x^2/4)^k / (k! (k+1)!) */
+        double Hk = 0.0;                   /* H_k */
+        double sum_i = 0.0, sum_psi = 0.0;
+        for (int k = 0; k < 20; ++k) {
+            double Hk1 = Hk + 1.0 / (double)(k + 1);
+            double psi_sum = (-euler_gamma + Hk) + (-euler_gamma + Hk1);
+            sum_i = sum_i + term;
+            sum_psi = sum_psi + psi_sum * term;
+            term = term * q / ((double)(k + 1) * (double)(k + 2));
+            Hk = Hk1;
+        }
+        double I1 = 0.5 * x * sum_i;
+        return 1.0 / x + log(0.5 * x) * I1 - 0.25 * x * sum_psi;
+    } else {
+        double h = 0.2 / sqrt(x);
+        double sum = 0.5 * exp(-x);        /* half weight at u = 0 */
+        for (int64_t j = 1;; ++j) {
+            double u = (double)j * h;
+            double sh = sinh(0.5 * u);
+            double cm1 = 2.0 * sh * sh;    /* cosh(u) - 1 without cancellation */
+            if (x * cm1 > 60.0) break;
+            sum = sum + exp(-x * (1.0 + cm1)) * (1.0 + cm1);
+        }
+        return h * sum;
+    }
+}
+
 double or_kernel_eval(int kernel, double ell, const double* a, const double* b, int d)
 {
     double D2 = 0.0;
@@ -32,10 +82,14 @@ double or_kernel_eval(int kernel, double ell, const double* a, const double* b, 
     if (kernel == 0) {
         double c = 1.0 / (ell * ell);
         return exp(-(D2 * c));
-    } else {
+    } else if (kernel == 1) {
         double c = sqrt(3.0) / ell;
         double s = sqrt(D2) * c;
         return (1.0 + s) * exp(-s);
+    } else {
+        if (D2 == 0.0) return 1.0;         /* lim_{s -> 0} s K_1(s) = 1 */
+        double s = sqrt(D2) / ell;
+        return s * or_bessel_k1(s);
     }
 }
 

@@ -34,7 +34,8 @@
 extern "C" {
 #endif
 
-/* Kernel ids: 0 = Gaussian exp(-r^2/l^2), 1 = Matern-3/2 (1+sqrt3 r/l)e^{-sqrt3 r/l}. */
+/* Kernel ids: 0 = Gaussian exp(-r^2/l^2), 1 = Matern-3/2 (1+sqrt3 r/l)e^{-sqrt3 r/l},
+ * 2 = Matern of order 1, (r/l) K_1(r/l) (phi(0) = 1). */
 double or_kernel_eval(int kernel, double ell, const double* a, const double* b, int d);
 
 /* Sec. 4.4, Alg. 6: Morton codes. pts row-major (N,d). Writes codes[N] and the
