@@ -79,39 +79,52 @@ def parse():
 # FP64, factors stored: "P" mode), on one Tesla P100. Context only.
 PAPER_P100 = {"build_s": 1.3, "mvp_s": 1.7, "hardware": "1x Tesla P100 SXM2, CUDA 8.0",
               "precision": "FP64"}
+# The same setting without precomputed factors (the paper's NP mode, its
+# default): build 0.8 s, product 2.7 s on the P100.
+PAPER_P100_NP = {"build_s": 0.8, "mvp_s": 2.7, "hardware": "1x Tesla P100 SXM2, CUDA 8.0",
+                 "precision": "FP64"}
+PAPER_KERNELS = {0: "exp(-r^2)", 2: "r K_1(r) (Matern, beta - d/2 = 1, phi(0) = 1)"}
 
 
-def paper_setting(hm, inputs, n_mvp=3):
-    """Build and multiply in the paper's setting at its size, FP64 and mixed
-    (CUDA events; points and x on the device). Returns a context object."""
+def paper_setting(hm, inputs, name="halton2d_n512k_k16", n_mvp=3):
+    """Build and multiply in the paper's setting at its size, FP64 and mixed,
+    with stored factors (P mode) and recomputed per product (NP mode), CUDA
+    events, points and x on the device. Returns a context object."""
     import torch
-    w = inputs.WORKLOADS["halton2d_n512k_k16"]
-    pts = torch.from_numpy(inputs.workload_points("halton2d_n512k_k16")).cuda()
+    w = inputs.WORKLOADS[name]
+    pts = torch.from_numpy(inputs.workload_points(name)).cuda()
     x = torch.from_numpy(inputs.normal_vector(w["n"], inputs.X_SEED)).cuda()
     y = torch.empty_like(x)
     stream = torch.cuda.current_stream()
-    out = {"workload": "halton2d_n512k_k16", "n": w["n"], "d": w["d"], "kernel": "exp(-r^2)",
+    out = {"workload": name, "n": w["n"], "d": w["d"], "kernel": PAPER_KERNELS[w["kernel"]],
            "leaf": w["leaf"], "eta": w["eta"], "aca": "fixed rank %d" % w["k_cap"],
-           "paper_p100": PAPER_P100}
-    for name, prec in (("fp64", hm.PREC_FP64), ("mixed", hm.PREC_MIXED)):
+           "paper_p100": PAPER_P100, "paper_p100_np": PAPER_P100_NP}
+
+    def run(prec, otf, reps, nm):
         res = []
-        for rep in range(2):            # the first build warms up the tuner
+        for rep in range(reps):         # the first build warms up the tuner
             e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
             e[0].record(stream)
             H = hm.HMatrix(pts, w["kernel"], w["ell"], w["leaf"], w["eta"], w["eps"],
-                           precision=prec, k_cap=w["k_cap"])
+                           precision=prec, k_cap=w["k_cap"], on_the_fly=otf)
             e[1].record(stream)
-            for _ in range(n_mvp):
+            for _ in range(nm):
                 H.matvec(x, y)
             e[2].record(stream)
             torch.cuda.synchronize()
             st = H.stats()
             H.free()
-            res.append((e[0].elapsed_time(e[1]) / 1e3, e[1].elapsed_time(e[2]) / n_mvp / 1e3, st))
-        b, m, st = res[-1]
-        out[name] = {"build_s": b, "mvp_s": m,
-                     "mvp_hbm_frac": st["mvp_bytes"] / m / 1e9 / peaks()[0],
-                     "factor_bytes": st["factor_bytes"], "near_bytes": st["near_bytes"]}
+            res.append((e[0].elapsed_time(e[1]) / 1e3, e[1].elapsed_time(e[2]) / nm / 1e3, st))
+        return res[-1]
+
+    for key, prec in (("fp64", hm.PREC_FP64), ("mixed", hm.PREC_MIXED)):
+        b, m, st = run(prec, False, 2, n_mvp)
+        out[key] = {"build_s": b, "mvp_s": m,
+                    "mvp_hbm_frac": st["mvp_bytes"] / m / 1e9 / peaks()[0],
+                    "factor_bytes": st["factor_bytes"], "near_bytes": st["near_bytes"]}
+        b, m, st = run(prec, True, 1, 2)
+        out[key + "_on_the_fly"] = {"build_s": b, "mvp_s": m,
+                                    "aca_passes_per_product": st["aca_passes"]}
     return out
 
 
@@ -716,9 +729,10 @@ def main():
     longest_aca = max(aca_serial) if aca_serial is not None else st["t_aca_ms"]
     dominant = aca_roof if longest_aca > N_MVP * mvp_t_tile else mvp_roof
 
-    paper = None
+    paper = paper_matern = None
     if not args.no_paper and world == 1:
         paper = paper_setting(hm, inputs)
+        paper_matern = paper_setting(hm, inputs, "halton2d_n512k_k16_matern")
 
     cpu = None
     if not args.no_cpu and world == 1:
@@ -753,7 +767,7 @@ def main():
         "gpu_launches": int(round(launches)),
         "clocks": clocks,
         "cpu_baseline": cpu,
-        "paper_setting": paper,
+        "paper_setting": paper, "paper_setting_matern": paper_matern,
         "stats": {k: st[k] for k in ("n_adm", "n_dense", "sum_rank", "max_rank",
                                      "rank_cap_hits", "n_rejected", "factor_bytes",
                                      "near_bytes", "mvp_bytes", "t_structure_ms",

@@ -33,9 +33,16 @@ extern "C" {
 /* Kernel functions phi(y, y') of r = |y - y'|, params[0] = length scale l > 0:
  *   HM_GAUSSIAN:  exp(-r^2 / l^2)           (Sec. 6.2 uses l = 1)
  *   HM_MATERN32:  (1 + sqrt3 r / l) exp(-sqrt3 r / l)
+ *   HM_MATERN_K1: s K_1(s), s = r / l: the Matern kernel of Sec. 6.2 with
+ *                 beta - d/2 = 1 (K_1 the modified Bessel function of the
+ *                 second kind of order 1), normalised to phi(0) = 1; the
+ *                 paper's form is this times 1 / (2^(beta-1) Gamma(beta)),
+ *                 1/2 for d = 2 and 0.26596 for d = 3, a constant factor of
+ *                 the whole matrix that leaves blocks, ranks and relative
+ *                 errors unchanged.
  * params[1] = sigma^2 >= 0 is added on the diagonal by the product (Sec. 1,
  * the GPR / kernel ridge regression system A + sigma^2 I). */
-enum { HM_GAUSSIAN = 0, HM_MATERN32 = 1 };
+enum { HM_GAUSSIAN = 0, HM_MATERN32 = 1, HM_MATERN_K1 = 2 };
 
 enum {
     HM_OK = 0,
@@ -113,7 +120,7 @@ void hm_options_default(hm_options* opt);
  * evaluation of the dense leaves (Sec. 5.4.2)).
  *   points    (N, d) row-major doubles, host or device; copied, may be freed
  *             on return
- *   N >= 1, d in {1, 2, 3}, kernel HM_GAUSSIAN | HM_MATERN32
+ *   N >= 1, d in {1, 2, 3}, kernel HM_GAUSSIAN | HM_MATERN32 | HM_MATERN_K1
  *   params    [l, sigma^2] (host)
  *   leaf_size C_leaf >= 1; eta >= 0 admissibility parameter
  *   aca_eps   relative Frobenius accuracy of each ACA block; <= 0 selects the

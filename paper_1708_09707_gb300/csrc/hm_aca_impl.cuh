@@ -1,4 +1,7 @@
-// hm_aca.cu -- batched adaptive cross approximation (Alg. 2, Sec. 5.4.1).
+// hm_aca_impl.cuh -- batched adaptive cross approximation (Alg. 2, Sec. 5.4.1):
+// the kernel templates and their launchers. hm_aca.cu instantiates them for
+// the Gaussian and Matern-3/2 kernels, hm_aca_k1.cu for the Matern kernel of
+// order 1 (two translation units, compiled in parallel).
 //
 // Every admissible leaf is compressed independently; instead of the paper's
 // batch-wide vote (all blocks iterate until the slowest one stops), each
@@ -29,6 +32,8 @@
 // threads; inside a thread the float kernels keep their partials in float
 // (compensated sums, exact maxima), since this GPU's double pipe runs at a
 // small fraction of its float rate.
+#pragma once
+
 #include <cooperative_groups.h>
 
 #include "hm_kernel_fn.cuh"
@@ -1495,21 +1500,5 @@ void launch_all(const KernelParams& kp, const DeviceCoords& X, const AcaArgs& a,
 }
 
 }  // namespace
-
-void aca_run(int precision, const KernelParams& kp, const DeviceCoords& X, const AcaArgs& a,
-             const uint32_t* order, int64_t n, int cls, int64_t max_n, cudaStream_t s)
-{
-    if (n <= 0) return;
-    if (a.k_cap > KBUF) fail(HM_ENOTSUP, "k_cap above 128 is not supported");
-    const bool f64 = precision == HM_PREC_FP64;
-    if (kp.kernel == HM_GAUSSIAN) {
-        if (f64) launch_all<double, HM_GAUSSIAN>(kp, X, a, order, n, cls, max_n, s);
-        else launch_all<float, HM_GAUSSIAN>(kp, X, a, order, n, cls, max_n, s);
-    } else {
-        if (f64) launch_all<double, HM_MATERN32>(kp, X, a, order, n, cls, max_n, s);
-        else launch_all<float, HM_MATERN32>(kp, X, a, order, n, cls, max_n, s);
-    }
-}
-
 
 }  // namespace hm

@@ -113,7 +113,9 @@ KernelParams make_kernel_params(int kernel, double ell)
 {
     KernelParams k;
     k.kernel = kernel;
-    k.c64 = (kernel == HM_GAUSSIAN) ? 1.0 / (ell * ell) : std::sqrt(3.0) / ell;
+    k.c64 = kernel == HM_GAUSSIAN ? 1.0 / (ell * ell)
+          : kernel == HM_MATERN32 ? std::sqrt(3.0) / ell
+                                  : 0.25 / (ell * ell);
     k.c32 = (float)k.c64;
     return k;
 }

@@ -75,6 +75,9 @@ __host__ __device__ __forceinline__ int aca_class_of(int m, int n)
 void aca_run(int precision, const KernelParams& kp, const DeviceCoords& X,
              const AcaArgs& a, const uint32_t* order, int64_t n, int cls, int64_t max_n,
              cudaStream_t s);
+// The same for the Matern kernel of order 1 (instantiated in its own unit).
+void aca_run_k1(bool f64, const KernelParams& kp, const DeviceCoords& X, const AcaArgs& a,
+                const uint32_t* order, int64_t n, int cls, int64_t max_n, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Product layout. The product gathers, for every row tile (a leaf of the

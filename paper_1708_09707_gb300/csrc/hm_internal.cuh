@@ -107,8 +107,8 @@ void radix_sort_noalloc(uint64_t* keys, uint32_t* vals, int64_t n, int key_bits,
 // Kernel function parameters
 // ---------------------------------------------------------------------------
 struct KernelParams {
-    int kernel;    // HM_GAUSSIAN | HM_MATERN32
-    double c64;    // 1/l^2 (Gaussian) or sqrt(3)/l (Matern-3/2)
+    int kernel;    // HM_GAUSSIAN | HM_MATERN32 | HM_MATERN_K1
+    double c64;    // 1/l^2 (Gaussian), sqrt(3)/l (Matern-3/2) or 1/(4 l^2) (Matern K_1)
     float c32;
 };
 

@@ -116,7 +116,8 @@ void near_assemble(int fmt, const KernelParams& kp, const DeviceCoords& X, const
     if (n <= 0) return;
     if (n > 0x7fffffffll) fail(HM_EOVERFLOW, "too many dense slices for one launch");
     if (kp.kernel == HM_GAUSSIAN) launch<HM_GAUSSIAN>(fmt, kp, X, blk, ent, etile, tile_m, desc, n, store, s);
-    else launch<HM_MATERN32>(fmt, kp, X, blk, ent, etile, tile_m, desc, n, store, s);
+    else if (kp.kernel == HM_MATERN32) launch<HM_MATERN32>(fmt, kp, X, blk, ent, etile, tile_m, desc, n, store, s);
+    else launch<HM_MATERN_K1>(fmt, kp, X, blk, ent, etile, tile_m, desc, n, store, s);
     HM_LAUNCH("near field");
 }
 

@@ -278,6 +278,24 @@ __global__ void k_np_finish(const int64_t* __restrict__ perm, const double* __re
     y[dst] = accumulate ? y[dst] + v : v;
 }
 
+template <class R>
+void launch_np_near(const KernelParams& kp, const DeviceCoords& X, unsigned g, const int3* items,
+                    const int64_t* ucol_ptr, const int64_t* ncol_ptr, const int32_t* ncol_x,
+                    const int64_t* tile_row0, const int32_t* tile_m, int max_ld, const R* xm,
+                    double* part, cudaStream_t s)
+{
+    const int bs = NN_W * 32;
+    if (kp.kernel == HM_GAUSSIAN)
+        k_np_near<R, HM_GAUSSIAN><<<g, bs, 0, s>>>(kp, X, items, ucol_ptr, ncol_ptr, ncol_x,
+                                                   tile_row0, tile_m, max_ld, xm, part);
+    else if (kp.kernel == HM_MATERN32)
+        k_np_near<R, HM_MATERN32><<<g, bs, 0, s>>>(kp, X, items, ucol_ptr, ncol_ptr, ncol_x,
+                                                   tile_row0, tile_m, max_ld, xm, part);
+    else
+        k_np_near<R, HM_MATERN_K1><<<g, bs, 0, s>>>(kp, X, items, ucol_ptr, ncol_ptr, ncol_x,
+                                                    tile_row0, tile_m, max_ld, xm, part);
+}
+
 }  // namespace
 
 void np_gather_x(int precision, const double* x, const int64_t* perm, int64_t N, void* xm,
@@ -392,24 +410,12 @@ void np_near(int precision, const KernelParams& kp, const DeviceCoords& X, const
     if (n_tiles <= 0 || n_items <= 0) return;
     if (n_items > 0x7fffffffll) fail(HM_EOVERFLOW, "too many near-field items for one launch");
     const unsigned g = (unsigned)n_items;
-    const int bs = NN_W * 32;
-    if (precision == HM_PREC_FP64) {
-        const double* xd = static_cast<const double*>(xm);
-        if (kp.kernel == HM_GAUSSIAN)
-            k_np_near<double, HM_GAUSSIAN><<<g, bs, 0, s>>>(kp, X, items, ucol_ptr, ncol_ptr, ncol_x,
-                                                            tile_row0, tile_m, max_ld, xd, part);
-        else
-            k_np_near<double, HM_MATERN32><<<g, bs, 0, s>>>(kp, X, items, ucol_ptr, ncol_ptr, ncol_x,
-                                                            tile_row0, tile_m, max_ld, xd, part);
-    } else {
-        const float* xf = static_cast<const float*>(xm);
-        if (kp.kernel == HM_GAUSSIAN)
-            k_np_near<float, HM_GAUSSIAN><<<g, bs, 0, s>>>(kp, X, items, ucol_ptr, ncol_ptr, ncol_x,
-                                                           tile_row0, tile_m, max_ld, xf, part);
-        else
-            k_np_near<float, HM_MATERN32><<<g, bs, 0, s>>>(kp, X, items, ucol_ptr, ncol_ptr, ncol_x,
-                                                           tile_row0, tile_m, max_ld, xf, part);
-    }
+    if (precision == HM_PREC_FP64)
+        launch_np_near<double>(kp, X, g, items, ucol_ptr, ncol_ptr, ncol_x, tile_row0, tile_m,
+                               max_ld, static_cast<const double*>(xm), part, s);
+    else
+        launch_np_near<float>(kp, X, g, items, ucol_ptr, ncol_ptr, ncol_x, tile_row0, tile_m,
+                              max_ld, static_cast<const float*>(xm), part, s);
     note_launch();
     k_np_near_finish<<<grid_for(n_tiles * 32), NT, 0, s>>>(item_ptr, tile_row0, tile_m, n_tiles,
                                                            max_ld, part, yacc);

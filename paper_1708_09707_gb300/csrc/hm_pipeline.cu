@@ -701,8 +701,10 @@ void rank_stats(hm_handle_s& h)
     // algorithmic flops of one kernel evaluation: squared distance in three
     // coordinates (3 subtractions, 1 multiply, 2 fused multiply-adds = 8)
     // plus the kernel (Gaussian: scale + exp = 2; Matern-3/2: sqrt, scale,
-    // exp, add, multiply = 5)
-    const double fe = h.kernel == HM_GAUSSIAN ? 10.0 : 13.0;
+    // exp, add, multiply = 5; Matern K_1 within twice the length scale: its
+    // two 13-term series (26 fused multiply-adds, 13 multiplies), log, add,
+    // multiply = 68; farther entries take a quadrature of 12 to 20 terms)
+    const double fe = h.kernel == HM_GAUSSIAN ? 10.0 : h.kernel == HM_MATERN32 ? 13.0 : 76.0;
     h.stats.aca_flops = fe * (double)o[8] + (double)o[9];
 }
 
@@ -711,7 +713,8 @@ void validate(int nsets, const int64_t* N, const int* d, int kernel, const doubl
 {
     if (nsets < 1) fail(HM_EINVAL, "no point sets");
     if (!params) fail(HM_EINVAL, "params is NULL");
-    if (kernel != HM_GAUSSIAN && kernel != HM_MATERN32) fail(HM_EINVAL, "unknown kernel");
+    if (kernel != HM_GAUSSIAN && kernel != HM_MATERN32 && kernel != HM_MATERN_K1)
+        fail(HM_EINVAL, "unknown kernel");
     if (!(params[0] > 0.0) || !std::isfinite(params[0])) fail(HM_EINVAL, "length scale must be > 0");
     if (!(params[1] >= 0.0) || !std::isfinite(params[1])) fail(HM_EINVAL, "sigma^2 must be >= 0");
     if (leaf < 1) fail(HM_EINVAL, "leaf_size must be >= 1");

@@ -14,7 +14,7 @@ import numpy as np
 
 from . import build as _build
 
-GAUSSIAN, MATERN32 = 0, 1
+GAUSSIAN, MATERN32, MATERN_K1 = 0, 1, 2
 PREC_FP64, PREC_MIXED = 0, 1
 NEAR_AUTO, NEAR_FP64, NEAR_FP32, NEAR_BF16X2, NEAR_BF16 = range(5)
 MLP_NPARAM = 4801

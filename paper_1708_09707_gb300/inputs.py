@@ -140,7 +140,7 @@ POINT_SEED = 1000
 X_SEED = 2000
 CG_SEED = 3000
 
-# The five workloads the tests and the bench use (sizes, kernel, parameters).
+# The workloads the tests and the bench use (sizes, kernel, parameters).
 WORKLOADS = {
     "gauss2d_n4096": dict(n=4096, d=2, points="uniform", kernel=0,
                           ell=0.1, leaf=32, eta=1.0, adm="max",
@@ -162,6 +162,11 @@ WORKLOADS = {
     "halton2d_n512k_k16": dict(n=1 << 19, d=2, points="halton", kernel=0,
                                ell=1.0, leaf=2048, eta=1.5, adm="min",
                                eps=0.0, k_cap=16, seed=0),
+    # the same setting with the paper's Matern kernel of order 1 (Sec. 6.2,
+    # beta - d/2 = 1), unscaled: phi = r K_1(r), normalised to phi(0) = 1
+    "halton2d_n512k_k16_matern": dict(n=1 << 19, d=2, points="halton", kernel=2,
+                                      ell=1.0, leaf=2048, eta=1.5, adm="min",
+                                      eps=0.0, k_cap=16, seed=0),
 }
 
 
