@@ -78,6 +78,20 @@ def _declare(L):
     L.or_build.argtypes = [_d, C.c_int64, C.c_int, C.c_int, _d, C.c_int,
                            C.c_double, C.c_int, C.c_double, C.c_int,
                            C.c_double, C.c_double]
+    L.or_build_rect.restype = C.c_void_p
+    L.or_build_rect.argtypes = [_d, C.c_int64, _d, C.c_int64, C.c_int, C.c_int, _d, C.c_int,
+                                C.c_double, C.c_int, C.c_double, C.c_int,
+                                C.c_double, C.c_double]
+    L.or_build_structure_rect.restype = C.c_void_p
+    L.or_build_structure_rect.argtypes = [_d, C.c_int64, _d, C.c_int64, C.c_int, C.c_int, _d,
+                                          C.c_int, C.c_double, C.c_int]
+    for f in ("or_n_cols", "or_n_nodes_cols"):
+        getattr(L, f).restype = C.c_int64
+        getattr(L, f).argtypes = [C.c_void_p]
+    L.or_get_col_perm.argtypes = [C.c_void_p, _i64]
+    L.or_get_col_tree.argtypes = [C.c_void_p, _i64, _i64, _d, _d]
+    L.or_dense_matvec_rect.argtypes = [_d, C.c_int64, _d, C.c_int64, C.c_int, C.c_int, _d,
+                                       _d, _d]
     L.or_build_structure.restype = C.c_void_p
     L.or_build_structure.argtypes = [_d, C.c_int64, C.c_int, C.c_int, _d,
                                      C.c_int, C.c_double, C.c_int]
@@ -200,6 +214,18 @@ def dense_matvec(pts, kernel: int, ell: float, sigma2: float, x):
     return y
 
 
+def dense_matvec_rect(rows, cols, kernel: int, ell: float, x):
+    """Brute force y = A_{phi, Y1 x Y2} x, rows = Y1 (N1, d), cols = Y2 (N2, d)."""
+    rows = _f64(rows)
+    cols = _f64(cols)
+    x = _f64(x)
+    y = np.zeros(rows.shape[0])
+    prm = np.array([ell, 0.0])
+    lib().or_dense_matvec_rect(_p(rows), rows.shape[0], _p(cols), cols.shape[0], rows.shape[1],
+                               kernel, _p(prm), _p(x), _p(y))
+    return y
+
+
 def dense_rows(pts, kernel: int, ell: float, sigma2: float, rows, x):
     pts = _f64(pts)
     x = _f64(x)
@@ -222,14 +248,27 @@ class HMatrix:
     def __init__(self, pts, kernel: int, ell: float, leaf: int, eta: float,
                  aca_eps: float, sigma2: float = 0.0, adm_max: bool = False,
                  k_cap: int = 64, aca_eta: float = 0.0, eps0: float = 0.0,
-                 compress: bool = True, symmetric: bool = False):
+                 compress: bool = True, symmetric: bool = False, cols=None):
+        """cols: a second point set Y2 for A_{phi, Y1 x Y2} (pts = Y1); the
+        product then maps x of length len(cols) to y of length len(pts)."""
         self.pts = _f64(pts)
         self.n, self.d = self.pts.shape
+        self.cols = None if cols is None else _f64(cols)
         self.kernel, self.ell, self.leaf, self.eta = kernel, ell, leaf, eta
         self.aca_eps, self.sigma2, self.k_cap = aca_eps, sigma2, k_cap
         prm = np.array([ell, sigma2])
         L = lib()
-        if compress:
+        if self.cols is not None:
+            n2 = self.cols.shape[0]
+            if compress:
+                self._h = L.or_build_rect(_p(self.pts), self.n, _p(self.cols), n2, self.d,
+                                          kernel, _p(prm), leaf, eta, int(adm_max), aca_eps,
+                                          k_cap, aca_eta, eps0)
+            else:
+                self._h = L.or_build_structure_rect(_p(self.pts), self.n, _p(self.cols), n2,
+                                                    self.d, kernel, _p(prm), leaf, eta,
+                                                    int(adm_max))
+        elif compress:
             self._h = L.or_build(_p(self.pts), self.n, self.d, kernel, _p(prm),
                                  leaf, eta, int(adm_max), aca_eps, k_cap,
                                  aca_eta, eps0)
@@ -241,6 +280,8 @@ class HMatrix:
         self.n_adm = L.or_n_adm(self._h)
         self.n_dense = L.or_n_dense(self._h)
         self.n_nodes = L.or_n_nodes(self._h)
+        self.n_cols = L.or_n_cols(self._h)
+        self.n_nodes_cols = L.or_n_nodes_cols(self._h)
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -270,6 +311,20 @@ class HMatrix:
         lib().or_get_coords(self._h, _p(c))
         return c
 
+    def col_perm(self):
+        p = np.zeros(self.n_cols, np.int64)
+        lib().or_get_col_perm(self._h, _p(p, _i64))
+        return p
+
+    def col_tree(self):
+        k = self.n_nodes_cols
+        lo = np.zeros(k, np.int64)
+        hi = np.zeros(k, np.int64)
+        bmin = np.zeros((k, self.d))
+        bmax = np.zeros((k, self.d))
+        lib().or_get_col_tree(self._h, _p(lo, _i64), _p(hi, _i64), _p(bmin), _p(bmax))
+        return lo, hi, bmin, bmax
+
     def tree(self):
         lo = np.zeros(self.n_nodes, np.int64)
         hi = np.zeros(self.n_nodes, np.int64)
@@ -296,8 +351,9 @@ class HMatrix:
 
     def factors(self, b: int):
         lo, hi, _, _ = self.tree()
+        lo2, hi2, _, _ = self.col_tree()
         t, s = self.adm_leaves()[b]
-        m, n = hi[t] - lo[t], hi[s] - lo[s]
+        m, n = hi[t] - lo[t], hi2[s] - lo2[s]
         r = int(self.ranks()[0][b])
         U = np.zeros((r, m))
         V = np.zeros((r, n))

@@ -458,6 +458,17 @@ struct or_hmat {
     double *Ust, *Vst;
     int64_t *pivI, *pivJ; /* per adm leaf, rank entries at offP */
     int64_t* offP;
+    /* Column side: the set Y2 of A_{phi, Y1 x Y2} (Sec. 6.1 treats two point
+     * sets) with its own Morton order and cluster tree. For A_{phi, Y x Y}
+     * these point at the row side's arrays (rect = 0). */
+    int rect;
+    int64_t N2;
+    uint64_t* codes2;
+    int64_t* perm2;
+    double* coords2;     /* Morton order, (N2, d) */
+    int64_t n_nodes2;
+    int64_t *lo2, *hi2;
+    double *bbmin2, *bbmax2;
 };
 
 typedef struct { or_leaf* v; int64_t n, cap; } or_leafvec;
@@ -477,13 +488,15 @@ static void or_push(or_leafvec* a, int64_t t, int64_t s, int adm)
 /* Alg. 1 build_block_cluster_tree: split (tau, sigma) into the four child   */
 /* pairs iff it is not admissible and both clusters hold more than C_leaf    */
 /* indices; otherwise it is a leaf (admissible -> low rank, else dense).     */
+/* tau is a node of the row tree, sigma of the column tree (the same tree    */
+/* for A_{phi, Y x Y}).                                                      */
 static void or_block_tree(const or_hmat* h, int64_t t, int64_t s, double eta2,
                           or_leafvec* adm, or_leafvec* dense)
 {
     int d = h->d;
-    int a = or_admissible(h->bbmin + t * d, h->bbmax + t * d, h->bbmin + s * d,
-                          h->bbmax + s * d, d, eta2, h->adm_max);
-    int64_t nt = h->hi[t] - h->lo[t], ns = h->hi[s] - h->lo[s];
+    int a = or_admissible(h->bbmin + t * d, h->bbmax + t * d, h->bbmin2 + s * d,
+                          h->bbmax2 + s * d, d, eta2, h->adm_max);
+    int64_t nt = h->hi[t] - h->lo[t], ns = h->hi2[s] - h->lo2[s];
     if (!a && nt > h->C && ns > h->C) {
         or_block_tree(h, 2 * t + 1, 2 * s + 1, eta2, adm, dense);
         or_block_tree(h, 2 * t + 1, 2 * s + 2, eta2, adm, dense);
@@ -504,13 +517,39 @@ static int or_leaf_cmp(const void* a, const void* b)
     const or_leaf* y = (const or_leaf*)b;
     int64_t xt = or_sort_ctx->lo[x->tau], yt = or_sort_ctx->lo[y->tau];
     if (xt != yt) return xt < yt ? -1 : 1;
-    int64_t xs = or_sort_ctx->lo[x->sigma], ys = or_sort_ctx->lo[y->sigma];
+    int64_t xs = or_sort_ctx->lo2[x->sigma], ys = or_sort_ctx->lo2[y->sigma];
     if (xs != ys) return xs < ys ? -1 : 1;
     return 0;
 }
 
-or_hmat* or_build_structure(const double* pts, int64_t N, int d, int kernel,
-                            const double* params, int C, double eta, int adm_max)
+/* One point set's Morton codes, stable order, Morton-ordered coordinates,   */
+/* cluster tree and bounding boxes (Sec. 4.4, 5.1, 2.1, 2.2).               */
+static void or_cluster_side(const double* pts, int64_t N, int d, int C, uint64_t** codes,
+                            int64_t** perm, double** coords, int64_t* n_nodes, int64_t** lo,
+                            int64_t** hi, double** bbmin, double** bbmax)
+{
+    double blo[3], bhi[3], sc[3];
+    *codes = (uint64_t*)malloc((size_t)N * sizeof(uint64_t));
+    *perm = (int64_t*)malloc((size_t)N * sizeof(int64_t));
+    or_morton(pts, N, d, *codes, blo, bhi, sc);
+    or_sort(*codes, N, *perm);
+    *coords = (double*)malloc((size_t)N * d * sizeof(double));
+    for (int64_t j = 0; j < N; ++j)
+        for (int i = 0; i < d; ++i) (*coords)[j * d + i] = pts[(*perm)[j] * d + i];
+    *n_nodes = or_tree_nodes(N, C);
+    *lo = (int64_t*)malloc((size_t)*n_nodes * sizeof(int64_t));
+    *hi = (int64_t*)malloc((size_t)*n_nodes * sizeof(int64_t));
+    or_tree_ranges(N, C, *lo, *hi);
+    *bbmin = (double*)malloc((size_t)*n_nodes * d * sizeof(double));
+    *bbmax = (double*)malloc((size_t)*n_nodes * d * sizeof(double));
+    or_bbox(*coords, N, d, C, *lo, *hi, *bbmin, *bbmax);
+}
+
+/* Structure of A_{phi, Y1 x Y2}: both sets clustered on their own, then    */
+/* Alg. 1 from the pair of roots. pts2 == NULL gives A_{phi, Y x Y}.        */
+static or_hmat* or_structure_pair(const double* pts, int64_t N, const double* pts2,
+                                  int64_t N2, int d, int kernel, const double* params,
+                                  int C, double eta, int adm_max)
 {
     or_hmat* h = (or_hmat*)calloc(1, sizeof(or_hmat));
     h->N = N;
@@ -521,21 +560,24 @@ or_hmat* or_build_structure(const double* pts, int64_t N, int d, int kernel,
     h->ell = params[0];
     h->sigma2 = params[1];
     h->eta = eta;
-    double lo[3], hi[3], sc[3];
-    h->codes = (uint64_t*)malloc((size_t)N * sizeof(uint64_t));
-    h->perm = (int64_t*)malloc((size_t)N * sizeof(int64_t));
-    or_morton(pts, N, d, h->codes, lo, hi, sc);
-    or_sort(h->codes, N, h->perm);
-    h->coords = (double*)malloc((size_t)N * d * sizeof(double));
-    for (int64_t j = 0; j < N; ++j)
-        for (int i = 0; i < d; ++i) h->coords[j * d + i] = pts[h->perm[j] * d + i];
-    h->n_nodes = or_tree_nodes(N, C);
-    h->lo = (int64_t*)malloc((size_t)h->n_nodes * sizeof(int64_t));
-    h->hi = (int64_t*)malloc((size_t)h->n_nodes * sizeof(int64_t));
-    or_tree_ranges(N, C, h->lo, h->hi);
-    h->bbmin = (double*)malloc((size_t)h->n_nodes * d * sizeof(double));
-    h->bbmax = (double*)malloc((size_t)h->n_nodes * d * sizeof(double));
-    or_bbox(h->coords, N, d, C, h->lo, h->hi, h->bbmin, h->bbmax);
+    or_cluster_side(pts, N, d, C, &h->codes, &h->perm, &h->coords, &h->n_nodes, &h->lo,
+                    &h->hi, &h->bbmin, &h->bbmax);
+    if (pts2) {
+        h->rect = 1;
+        h->N2 = N2;
+        or_cluster_side(pts2, N2, d, C, &h->codes2, &h->perm2, &h->coords2, &h->n_nodes2,
+                        &h->lo2, &h->hi2, &h->bbmin2, &h->bbmax2);
+    } else {
+        h->N2 = N;
+        h->codes2 = h->codes;
+        h->perm2 = h->perm;
+        h->coords2 = h->coords;
+        h->n_nodes2 = h->n_nodes;
+        h->lo2 = h->lo;
+        h->hi2 = h->hi;
+        h->bbmin2 = h->bbmin;
+        h->bbmax2 = h->bbmax;
+    }
 
     or_leafvec adm = {0}, dense = {0};
     or_block_tree(h, 0, 0, eta * eta, &adm, &dense);
@@ -557,6 +599,19 @@ or_hmat* or_build_structure(const double* pts, int64_t N, int d, int kernel,
     return h;
 }
 
+or_hmat* or_build_structure(const double* pts, int64_t N, int d, int kernel,
+                            const double* params, int C, double eta, int adm_max)
+{
+    return or_structure_pair(pts, N, NULL, 0, d, kernel, params, C, eta, adm_max);
+}
+
+or_hmat* or_build_structure_rect(const double* pts1, int64_t N1, const double* pts2,
+                                 int64_t N2, int d, int kernel, const double* params, int C,
+                                 double eta, int adm_max)
+{
+    return or_structure_pair(pts1, N1, pts2, N2, d, kernel, params, C, eta, adm_max);
+}
+
 typedef struct { const or_hmat* h; int64_t t0, s0; } or_block_ctx;
 
 static double or_block_entry(const void* ctx, int64_t i, int64_t j)
@@ -564,7 +619,7 @@ static double or_block_entry(const void* ctx, int64_t i, int64_t j)
     const or_block_ctx* c = (const or_block_ctx*)ctx;
     const or_hmat* h = c->h;
     return or_kernel_eval(h->kernel, h->ell, h->coords + (c->t0 + i) * h->d,
-                          h->coords + (c->s0 + j) * h->d, h->d);
+                          h->coords2 + (c->s0 + j) * h->d, h->d);
 }
 
 void or_compress_range(or_hmat* h, int64_t b0, int64_t b1, double aca_eps,
@@ -574,7 +629,7 @@ void or_compress_range(or_hmat* h, int64_t b0, int64_t b1, double aca_eps,
     int64_t totU = 0, totV = 0, totP = 0;
     for (int64_t b = b0; b < b1; ++b) {
         int64_t m = h->hi[h->adm[b].tau] - h->lo[h->adm[b].tau];
-        int64_t n = h->hi[h->adm[b].sigma] - h->lo[h->adm[b].sigma];
+        int64_t n = h->hi2[h->adm[b].sigma] - h->lo2[h->adm[b].sigma];
         int64_t k = k_cap;
         if (k > m) k = m;
         if (k > n) k = n;
@@ -594,8 +649,8 @@ void or_compress_range(or_hmat* h, int64_t b0, int64_t b1, double aca_eps,
     int64_t oU = 0, oV = 0, oP = 0;
     for (int64_t b = b0; b < b1; ++b) {
         int64_t m = h->hi[h->adm[b].tau] - h->lo[h->adm[b].tau];
-        int64_t n = h->hi[h->adm[b].sigma] - h->lo[h->adm[b].sigma];
-        or_block_ctx c = {h, h->lo[h->adm[b].tau], h->lo[h->adm[b].sigma]};
+        int64_t n = h->hi2[h->adm[b].sigma] - h->lo2[h->adm[b].sigma];
+        or_block_ctx c = {h, h->lo[h->adm[b].tau], h->lo2[h->adm[b].sigma]};
         h->offU[b] = oU;
         h->offV[b] = oV;
         h->offP[b] = oP;
@@ -620,6 +675,7 @@ void or_compress_range(or_hmat* h, int64_t b0, int64_t b1, double aca_eps,
  * the mirror of a leaf is found by binary search. */
 void or_mirror_transposed(or_hmat* h)
 {
+    if (h->rect) return;   /* A_{phi, Y1 x Y2} has no mirror leaves */
     for (int64_t b = 0; b < h->n_adm; ++b) {
         const int64_t tl = h->lo[h->adm[b].tau], sl = h->lo[h->adm[b].sigma];
         if (tl <= sl) continue;
@@ -655,9 +711,22 @@ or_hmat* or_build(const double* pts, int64_t N, int d, int kernel,
     return h;
 }
 
+or_hmat* or_build_rect(const double* pts1, int64_t N1, const double* pts2, int64_t N2,
+                       int d, int kernel, const double* params, int C, double eta,
+                       int adm_max, double aca_eps, int k_cap, double aca_eta, double eps0)
+{
+    or_hmat* h = or_build_structure_rect(pts1, N1, pts2, N2, d, kernel, params, C, eta, adm_max);
+    or_compress_range(h, 0, h->n_adm, aca_eps, k_cap, aca_eta, eps0);
+    return h;
+}
+
 void or_free(or_hmat* h)
 {
     if (!h) return;
+    if (h->rect) {
+        free(h->codes2); free(h->perm2); free(h->coords2);
+        free(h->lo2); free(h->hi2); free(h->bbmin2); free(h->bbmax2);
+    }
     free(h->codes); free(h->perm); free(h->coords);
     free(h->lo); free(h->hi); free(h->bbmin); free(h->bbmax);
     free(h->adm); free(h->dense); free(h->rank); free(h->rej);
@@ -693,6 +762,22 @@ void or_get_tree(const or_hmat* h, int64_t* lo, int64_t* hi, double* bbmin, doub
     memcpy(bbmax, h->bbmax, (size_t)h->n_nodes * h->d * sizeof(double));
 }
 
+int64_t or_n_cols(const or_hmat* h) { return h->N2; }
+int64_t or_n_nodes_cols(const or_hmat* h) { return h->n_nodes2; }
+
+void or_get_col_perm(const or_hmat* h, int64_t* perm)
+{
+    memcpy(perm, h->perm2, (size_t)h->N2 * sizeof(int64_t));
+}
+
+void or_get_col_tree(const or_hmat* h, int64_t* lo, int64_t* hi, double* bbmin, double* bbmax)
+{
+    memcpy(lo, h->lo2, (size_t)h->n_nodes2 * sizeof(int64_t));
+    memcpy(hi, h->hi2, (size_t)h->n_nodes2 * sizeof(int64_t));
+    memcpy(bbmin, h->bbmin2, (size_t)h->n_nodes2 * h->d * sizeof(double));
+    memcpy(bbmax, h->bbmax2, (size_t)h->n_nodes2 * h->d * sizeof(double));
+}
+
 void or_get_adm(const or_hmat* h, int64_t* leaves)
 {
     for (int64_t b = 0; b < h->n_adm; ++b) {
@@ -720,7 +805,7 @@ void or_get_ranks(const or_hmat* h, int32_t* ranks, int64_t* n_rej)
 void or_get_factors(const or_hmat* h, int64_t b, double* U, double* V)
 {
     int64_t m = h->hi[h->adm[b].tau] - h->lo[h->adm[b].tau];
-    int64_t n = h->hi[h->adm[b].sigma] - h->lo[h->adm[b].sigma];
+    int64_t n = h->hi2[h->adm[b].sigma] - h->lo2[h->adm[b].sigma];
     int r = h->rank[b];
     if (r <= 0) return;
     memcpy(U, h->Ust + h->offU[b], (size_t)(m * r) * sizeof(double));
@@ -745,16 +830,16 @@ void or_get_pivots(const or_hmat* h, int64_t b, int64_t* piv_i, int64_t* piv_j)
 /* ------------------------------------------------------------------------ */
 void or_matvec(const or_hmat* h, const double* x, double* y)
 {
-    int64_t N = h->N;
+    int64_t N = h->N, N2 = h->N2;
     int d = h->d;
-    double* xm = (double*)malloc((size_t)N * sizeof(double));
-    double* ym = (double*)calloc((size_t)N, sizeof(double));
-    for (int64_t i = 0; i < N; ++i) xm[i] = x[h->perm[i]];
+    double* xm = (double*)malloc((size_t)(N2 > 0 ? N2 : 1) * sizeof(double));
+    double* ym = (double*)calloc((size_t)(N > 0 ? N : 1), sizeof(double));
+    for (int64_t j = 0; j < N2; ++j) xm[j] = x[h->perm2[j]];
     double* t = (double*)malloc(64 * sizeof(double));
     int tcap = 64;
     for (int64_t b = 0; b < h->n_adm; ++b) {
         int64_t t0 = h->lo[h->adm[b].tau], m = h->hi[h->adm[b].tau] - t0;
-        int64_t s0 = h->lo[h->adm[b].sigma], n = h->hi[h->adm[b].sigma] - s0;
+        int64_t s0 = h->lo2[h->adm[b].sigma], n = h->hi2[h->adm[b].sigma] - s0;
         int r = h->rank[b];
         if (r <= 0) continue;
         if (r > tcap) {
@@ -776,16 +861,18 @@ void or_matvec(const or_hmat* h, const double* x, double* y)
     }
     for (int64_t b = 0; b < h->n_dense; ++b) {
         int64_t t0 = h->lo[h->dense[b].tau], m = h->hi[h->dense[b].tau] - t0;
-        int64_t s0 = h->lo[h->dense[b].sigma], n = h->hi[h->dense[b].sigma] - s0;
+        int64_t s0 = h->lo2[h->dense[b].sigma], n = h->hi2[h->dense[b].sigma] - s0;
         for (int64_t i = 0; i < m; ++i) {
             double s = 0.0;
             for (int64_t j = 0; j < n; ++j)
                 s = s + or_kernel_eval(h->kernel, h->ell, h->coords + (t0 + i) * d,
-                                       h->coords + (s0 + j) * d, d) * xm[s0 + j];
+                                       h->coords2 + (s0 + j) * d, d) * xm[s0 + j];
             ym[t0 + i] = ym[t0 + i] + s;
         }
     }
-    for (int64_t i = 0; i < N; ++i) y[h->perm[i]] = ym[i] + h->sigma2 * x[h->perm[i]];
+    /* sigma^2 x on the diagonal only exists for A_{phi, Y x Y} */
+    for (int64_t i = 0; i < N; ++i)
+        y[h->perm[i]] = h->rect ? ym[i] : ym[i] + h->sigma2 * x[h->perm[i]];
     free(t);
     free(xm);
     free(ym);
@@ -826,6 +913,25 @@ void or_dense_rows(const double* pts, int64_t N, int d, int kernel,
     }
 }
 
+/* Brute force of A_{phi, Y1 x Y2} x: y_i = sum_j phi(y1_i, y2_j) x_j over  */
+/* the N2 points of Y2 (Neumaier-compensated), for the N1 points of Y1.     */
+void or_dense_matvec_rect(const double* pts1, int64_t N1, const double* pts2, int64_t N2,
+                          int d, int kernel, const double* params, const double* x,
+                          double* y)
+{
+    for (int64_t i = 0; i < N1; ++i) {
+        double s = 0.0, c = 0.0;
+        for (int64_t j = 0; j < N2; ++j) {
+            double v = or_kernel_eval(kernel, params[0], pts1 + i * d, pts2 + j * d, d) * x[j];
+            double t = s + v;
+            if (fabs(s) >= fabs(v)) c = c + ((s - t) + v);
+            else c = c + ((v - t) + s);
+            s = t;
+        }
+        y[i] = s + c;
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Conjugate gradients (Hestenes-Stiefel) on (A_H + sigma^2 I) x = b, the   */
 /* system of Sec. 1 solved with the fast H-MVP as the operator.             */
@@ -840,6 +946,7 @@ static double or_dot(const double* a, const double* b, int64_t n)
 int or_cg(const or_hmat* h, const double* b, double* x, double rtol, int maxit,
           double* relres)
 {
+    if (h->rect) return -1;   /* CG needs the square system A + sigma^2 I */
     int64_t N = h->N;
     double* r = (double*)malloc((size_t)N * sizeof(double));
     double* p = (double*)malloc((size_t)N * sizeof(double));
@@ -888,11 +995,11 @@ void or_block_features(const or_hmat* h, double aca_eps, double* feats)
         double Dt = 0.0, Ds = 0.0, G2 = 0.0;
         for (int i = 0; i < d; ++i) {
             double et = h->bbmax[t * d + i] - h->bbmin[t * d + i];
-            double es = h->bbmax[s * d + i] - h->bbmin[s * d + i];
+            double es = h->bbmax2[s * d + i] - h->bbmin2[s * d + i];
             Dt = Dt + et * et;
             Ds = Ds + es * es;
-            double g1 = h->bbmin[t * d + i] - h->bbmax[s * d + i];
-            double g2 = h->bbmin[s * d + i] - h->bbmax[t * d + i];
+            double g1 = h->bbmin[t * d + i] - h->bbmax2[s * d + i];
+            double g2 = h->bbmin2[s * d + i] - h->bbmax[t * d + i];
             if (g1 < 0.0) g1 = 0.0;
             if (g2 < 0.0) g2 = 0.0;
             G2 = G2 + (g1 * g1 + g2 * g2);
@@ -900,7 +1007,7 @@ void or_block_features(const or_hmat* h, double aca_eps, double* feats)
         double* f = feats + b * 8;
         f[0] = d / 3.0;
         f[1] = log2((double)(h->hi[t] - h->lo[t])) / 16.0;
-        f[2] = log2((double)(h->hi[s] - h->lo[s])) / 16.0;
+        f[2] = log2((double)(h->hi2[s] - h->lo2[s])) / 16.0;
         f[3] = log2(1.0 + sqrt(Dt) / h->ell);
         f[4] = log2(1.0 + sqrt(Ds) / h->ell);
         f[5] = log2(1.0 + sqrt(G2) / h->ell);

@@ -22,6 +22,11 @@
  *   or_matvec        eta = 0 and C >= N reduce to the dense product; error
  *                    against brute force within O(eps); symmetry; sigma^2 x
  *   or_dense_matvec  numpy dense matrix product
+ *   or_build_rect    Y2 = Y1 gives the square build bit for bit; leaves tile
+ *                    I1 x I2 once; eta = 0 and C >= max(N1, N2) reduce to
+ *                    the dense product; error against or_dense_matvec_rect
+ *                    within O(eps); A(Y1,Y2) and A(Y2,Y1) are transposes
+ *   or_dense_matvec_rect  numpy dense matrix product
  *   or_cg            numpy.linalg.solve on the same dense system
  *   or_mlp_*         central finite differences; closed-form first Adam step
  */
@@ -88,6 +93,23 @@ or_hmat* or_build(const double* pts, int64_t N, int d, int kernel,
                   double aca_eps, int k_cap, double aca_eta, double eps0);
 void or_free(or_hmat* h);
 
+/* A_{phi, Y1 x Y2} for two point sets (Sec. 6.1: the paper's library builds
+ * A for sets Y1 and Y2): each set is ordered and clustered on its own, Alg. 1
+ * runs from the pair of roots with tau in Y1's tree and sigma in Y2's, ACA
+ * entries are phi(y1_i, y2_j). params[1] (sigma^2) is ignored: there is no
+ * diagonal. The product maps x of length N2 to y of length N1. */
+or_hmat* or_build_rect(const double* pts1, int64_t N1, const double* pts2, int64_t N2,
+                       int d, int kernel, const double* params, int C, double eta,
+                       int adm_max, double aca_eps, int k_cap, double aca_eta, double eps0);
+or_hmat* or_build_structure_rect(const double* pts1, int64_t N1, const double* pts2,
+                                 int64_t N2, int d, int kernel, const double* params, int C,
+                                 double eta, int adm_max);
+/* Column side (Y2) of a rectangular handle; the row side for a square one. */
+int64_t or_n_cols(const or_hmat* h);
+int64_t or_n_nodes_cols(const or_hmat* h);
+void or_get_col_perm(const or_hmat* h, int64_t* perm);
+void or_get_col_tree(const or_hmat* h, int64_t* lo, int64_t* hi, double* bbmin, double* bbmax);
+
 /* Structure only (no ACA): for the large-N parity of integer structure. */
 or_hmat* or_build_structure(const double* pts, int64_t N, int d, int kernel,
                             const double* params, int C, double eta, int adm_max);
@@ -123,6 +145,10 @@ void or_matvec(const or_hmat* h, const double* x, double* y);
 /* Brute force y_i = sum_j phi(y_i, y_j) x_j + sigma^2 x_i (Neumaier sums). */
 void or_dense_matvec(const double* pts, int64_t N, int d, int kernel,
                      const double* params, const double* x, double* y);
+/* Brute force of A_{phi, Y1 x Y2} x (Neumaier sums over the N2 columns). */
+void or_dense_matvec_rect(const double* pts1, int64_t N1, const double* pts2, int64_t N2,
+                          int d, int kernel, const double* params, const double* x,
+                          double* y);
 /* The same for a subset of rows: y_rows[r] for row index rows[r]. */
 void or_dense_rows(const double* pts, int64_t N, int d, int kernel,
                    const double* params, const int64_t* rows, int64_t nrows,
