@@ -135,6 +135,28 @@ hm_handle hm_build_ex(const double* points, int64_t N, int d, int kernel,
                       const double* params, int leaf_size, double eta,
                       double aca_eps, const hm_options* opt, int* status);
 
+/* Build the H-matrix of A_{phi, Y1 x Y2} for two point sets (Sec. 6.1: the
+ * library is for a kernel matrix on sets Y1 and Y2). Each set gets its own
+ * Morton order and cluster tree (Sec. 4.4); Alg. 1 runs from the pair of
+ * roots, tau a cluster of Y1 and sigma a cluster of Y2; ACA and the dense
+ * leaves evaluate phi(y1_i, y2_j).
+ *   rows  (N1, d) row-major doubles (Y1), cols (N2, d) (Y2), host or device;
+ *         both copied, may be freed on return
+ *   params[1] (sigma^2) must be 0: there is no diagonal
+ *   the other arguments as hm_build_ex. symmetric and rank_model are
+ *   refused (HM_ENOTSUP); on_the_fly is supported. In mixed precision every
+ *   block keeps the blockwise ACA test (the global floor rests on the unit
+ *   diagonal of a square kernel matrix).
+ * hm_matvec / hm_matvec_ex then take x of N2 entries (per vector, in Y2's
+ * order) and write y of N1 entries (Y1's order), one product per vector;
+ * hm_cg refuses the handle. hm_export_structure writes Y1's permutation
+ * followed by Y2's (set-local), leaf pairs (tau in Y1's tree, sigma in Y2's)
+ * and hm_export_tree Y1's nodes followed by Y2's.
+ * Returns NULL on failure; *status (may be NULL) receives the HM_* code. */
+hm_handle hm_build_rect(const double* rows, int64_t N1, const double* cols, int64_t N2, int d,
+                        int kernel, const double* params, int leaf_size, double eta,
+                        double aca_eps, const hm_options* opt, int* status);
+
 /* y = H x + sigma^2 x (Alg. 3, batched: Sec. 5.4), x and y of length N in the
  * caller's point order, host or device doubles. y is overwritten unless the
  * handle was built with accumulate = 1. */

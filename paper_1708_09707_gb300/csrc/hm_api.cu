@@ -178,6 +178,38 @@ hm_handle hm_build_ex(const double* points, int64_t N, int d, int kernel, const 
     }
 }
 
+hm_handle hm_build_rect(const double* rows, int64_t N1, const double* cols, int64_t N2, int d,
+                        int kernel, const double* params, int leaf_size, double eta,
+                        double aca_eps, const hm_options* opt, int* status)
+{
+    set_error("");
+    try {
+        hm_options o;
+        hm_options_default(&o);
+        if (opt) o = *opt;
+        if (!rows || !cols) fail(HM_EINVAL, "points is NULL");
+        if (N1 < 1 || N2 < 1) fail(HM_EINVAL, "N must be >= 1");
+        if (d < 1 || d > 3) fail(HM_EINVAL, "d must be 1, 2 or 3");
+        if (N1 + N2 >= (1ll << 31)) fail(HM_EINVAL, "more than 2^31 points");
+        std::unique_ptr<hm_handle_s> h(new hm_handle_s());
+        // both sets in one device array, rows first (the build reads them there)
+        cudaStream_t s = (cudaStream_t)o.stream;
+        DevBuf<double> both((N1 + N2) * d, s);
+        copy_in(both.p, rows, N1 * d * sizeof(double), s);
+        copy_in(both.p + N1 * d, cols, N2 * d * sizeof(double), s);
+        int64_t Ns[2] = {N1, N2};
+        int ds[2] = {d, d};
+        build_sets(*h, 2, both.p, Ns, ds, kernel, params, leaf_size, eta, aca_eps, o, true);
+        HM_CUDA(cudaStreamSynchronize(s));
+        if (status) *status = HM_OK;
+        return h.release();
+    } catch (const std::exception& e) {
+        int st = to_status(e);
+        if (status) *status = st;
+        return nullptr;
+    }
+}
+
 hm_handle hm_build(const double* points, int64_t N, int d, int kernel, const double* params,
                    int leaf_size, double eta, double aca_eps)
 {

@@ -248,9 +248,13 @@ __device__ __forceinline__ bool admissible(const double* tmn, const double* tmx,
 // is packed into one int64 per pair so that a single exclusive scan yields
 // the adm offset (low 32 bits) and the dense offset (high 32 bits); the split
 // offset is p - adm - dense.
+// tau is a node of the row tree (lo, hi, bmin, bmax), sigma of the column
+// tree (lo2, ...); the same tree for A_{phi, Y x Y}.
 __global__ void k_classify(const int2* __restrict__ pairs, int64_t P, int C,
                            const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
                            const double* __restrict__ bmin, const double* __restrict__ bmax,
+                           const int32_t* __restrict__ lo2, const int32_t* __restrict__ hi2,
+                           const double* __restrict__ bmin2, const double* __restrict__ bmax2,
                            double eta2, int adm_max, int64_t* __restrict__ flag)
 {
     int64_t p = (int64_t)blockIdx.x * NT + threadIdx.x;
@@ -262,11 +266,11 @@ __global__ void k_classify(const int2* __restrict__ pairs, int64_t P, int C,
     for (int i = 0; i < 3; ++i) {
         tmn[i] = bmin[(int64_t)t * 3 + i];
         tmx[i] = bmax[(int64_t)t * 3 + i];
-        smn[i] = bmin[(int64_t)s * 3 + i];
-        smx[i] = bmax[(int64_t)s * 3 + i];
+        smn[i] = bmin2[(int64_t)s * 3 + i];
+        smx[i] = bmax2[(int64_t)s * 3 + i];
     }
     bool a = admissible(tmn, tmx, smn, smx, eta2, adm_max);
-    int nt = hi[t] - lo[t], ns = hi[s] - lo[s];
+    int nt = hi[t] - lo[t], ns = hi2[s] - lo2[s];
     int64_t f;
     if (a) f = 1;                          // admissible leaf
     else if (nt > C && ns > C) f = 0;      // split
@@ -298,15 +302,16 @@ __global__ void k_emit(const int2* __restrict__ pairs, int64_t P,
     }
 }
 
-// Canonical leaf order key: tau.lo * N + sigma.lo.
+// Canonical leaf order key: tau.lo * N2 + sigma.lo (tau.lo in the row tree,
+// sigma.lo in the column tree, N2 the column set's size).
 __global__ void k_leaf_keys(const int2* __restrict__ leaves, int64_t n,
-                            const int32_t* __restrict__ lo, int64_t N,
-                            uint64_t* __restrict__ keys, uint32_t* __restrict__ idx)
+                            const int32_t* __restrict__ lo, const int32_t* __restrict__ lo2,
+                            int64_t N2, uint64_t* __restrict__ keys, uint32_t* __restrict__ idx)
 {
     int64_t b = (int64_t)blockIdx.x * NT + threadIdx.x;
     if (b >= n) return;
     int2 ts = leaves[b];
-    keys[b] = (uint64_t)lo[ts.x] * (uint64_t)N + (uint64_t)lo[ts.y];
+    keys[b] = (uint64_t)lo[ts.x] * (uint64_t)N2 + (uint64_t)lo2[ts.y];
     idx[b] = (uint32_t)b;
 }
 
@@ -328,14 +333,14 @@ int bits_for(int64_t n)
 
 // Sort a leaf list into canonical (tau.lo, sigma.lo) order.
 void canonical_sort(DevBuf<int2>& leaves, int64_t n, const int32_t* lo, int64_t N,
-                    cudaStream_t s)
+                    const int32_t* lo2, int64_t N2, cudaStream_t s)
 {
     if (n <= 1) return;
     DevBuf<uint64_t> keys(n, s);
     DevBuf<uint32_t> idx(n, s);
-    k_leaf_keys<<<grid_for(n), NT, 0, s>>>(leaves.p, n, lo, N, keys.p, idx.p); note_launch();
+    k_leaf_keys<<<grid_for(n), NT, 0, s>>>(leaves.p, n, lo, lo2, N2, keys.p, idx.p); note_launch();
     HM_LAUNCH("leaf keys");
-    radix_sort_u64_u32(keys.p, idx.p, n, 2 * bits_for(N + 1), s);
+    radix_sort_u64_u32(keys.p, idx.p, n, bits_for(N + 1) + bits_for(N2 + 1), s);
     DevBuf<int2> out(n, s);
     k_gather_pairs<<<grid_for(n), NT, 0, s>>>(leaves.p, idx.p, n, out.p); note_launch();
     HM_LAUNCH("leaf gather");
@@ -384,10 +389,9 @@ void morton_codes(const double* pts, int64_t N, int d, uint64_t* codes, uint32_t
     if (hbad) fail(HM_EINVAL, "non-finite point coordinate");
 }
 
-void build_structure(const double* pts, SetStructure& S, double eta, int adm_max,
-                     const DeviceCoords& X, int64_t* perm_out, uint64_t* codes_out,
-                     int32_t* node_lo, int32_t* node_hi, double* bmin, double* bmax,
-                     DevBuf<int2>& adm, DevBuf<int2>& dense, cudaStream_t s)
+void build_tree(const double* pts, SetStructure& S, const DeviceCoords& X, int64_t* perm_out,
+                uint64_t* codes_out, int32_t* node_lo, int32_t* node_hi, double* bmin,
+                double* bmax, cudaStream_t s)
 {
     const int64_t N = S.N;
     const int d = S.d, C = S.C;
@@ -425,20 +429,38 @@ void build_structure(const double* pts, SetStructure& S, double eta, int adm_max
                                                          X.x64[2] + r0, bn, bx); note_launch();
     }
     HM_LAUNCH("bbox");
+}
 
-    // level-synchronous traversal (Alg. 1 via Alg. 4)
+void traverse(SetStructure& R, const SetStructure& Cs, double eta, int adm_max,
+              const int32_t* node_lo, const int32_t* node_hi, const double* bmin,
+              const double* bmax, DevBuf<int2>& adm, DevBuf<int2>& dense, cudaStream_t s)
+{
+    const int C = R.C;
+    const int32_t* lo = node_lo + R.node0;
+    const int32_t* hi = node_hi + R.node0;
+    const double* bn = bmin + R.node0 * 3;
+    const double* bx = bmax + R.node0 * 3;
+    const int32_t* lo2 = node_lo + Cs.node0;
+    const int32_t* hi2 = node_hi + Cs.node0;
+    const double* bn2 = bmin + Cs.node0 * 3;
+    const double* bx2 = bmax + Cs.node0 * 3;
+    const int depth = std::max(R.depth, Cs.depth);
+
+    // level-synchronous traversal (Alg. 1 via Alg. 4) from the pair of roots
     const double eta2 = eta * eta;
     DevBuf<int2> cur(1, s), nxt;
     int2 root = make_int2(0, 0);
     HM_CUDA(cudaMemcpyAsync(cur.p, &root, sizeof(int2), cudaMemcpyHostToDevice, s));
     int64_t P = 1, n_adm = 0, n_dense = 0;
     DevBuf<int64_t> tot(1, s);
-    adm.alloc(std::max<int64_t>(1024, N), s);
-    dense.alloc(std::max<int64_t>(1024, N), s);
+    const int64_t guess = std::max<int64_t>(1024, std::max(R.N, Cs.N));
+    adm.alloc(guess, s);
+    dense.alloc(guess, s);
     for (int l = 0; P > 0; ++l) {
-        if (l > S.depth) fail(HM_EOVERFLOW, "block tree deeper than the cluster tree");
+        if (l > depth) fail(HM_EOVERFLOW, "block tree deeper than the cluster trees");
         DevBuf<int64_t> flag(P, s), off(P, s);
-        k_classify<<<grid_for(P), NT, 0, s>>>(cur.p, P, C, lo, hi, bn, bx, eta2, adm_max, flag.p); note_launch();
+        k_classify<<<grid_for(P), NT, 0, s>>>(cur.p, P, C, lo, hi, bn, bx, lo2, hi2, bn2, bx2,
+                                              eta2, adm_max, flag.p); note_launch();
         HM_LAUNCH("classify");
         scan_exclusive_i64(flag.p, off.p, P, tot.p, s);
         int64_t h_tot = 0;
@@ -456,10 +478,19 @@ void build_structure(const double* pts, SetStructure& S, double eta, int adm_max
         P = 4 * ns;
         std::swap(cur, nxt);
     }
-    S.n_adm = n_adm;
-    S.n_dense = n_dense;
-    canonical_sort(adm, n_adm, lo, N, s);
-    canonical_sort(dense, n_dense, lo, N, s);
+    R.n_adm = n_adm;
+    R.n_dense = n_dense;
+    canonical_sort(adm, n_adm, lo, R.N, lo2, Cs.N, s);
+    canonical_sort(dense, n_dense, lo, R.N, lo2, Cs.N, s);
+}
+
+void build_structure(const double* pts, SetStructure& S, double eta, int adm_max,
+                     const DeviceCoords& X, int64_t* perm_out, uint64_t* codes_out,
+                     int32_t* node_lo, int32_t* node_hi, double* bmin, double* bmax,
+                     DevBuf<int2>& adm, DevBuf<int2>& dense, cudaStream_t s)
+{
+    build_tree(pts, S, X, perm_out, codes_out, node_lo, node_hi, bmin, bmax, s);
+    traverse(S, S, eta, adm_max, node_lo, node_hi, bmin, bmax, adm, dense, s);
 }
 
 }  // namespace hm

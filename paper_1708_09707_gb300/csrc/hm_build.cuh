@@ -26,6 +26,18 @@ void morton_codes(const double* pts, int64_t N, int d, uint64_t* codes, uint32_t
 // Morton sort, coordinates, cluster tree, boxes, traversal and canonical leaf
 // lists of one point set. pts: device (N, d) row-major. adm / dense receive
 // (tau, sigma) node ids local to the set.
+// One set's Morton codes, order, coordinates, cluster tree and boxes.
+void build_tree(const double* pts, SetStructure& S, const DeviceCoords& X, int64_t* perm_out,
+                uint64_t* codes_out, int32_t* node_lo, int32_t* node_hi, double* bmin,
+                double* bmax, cudaStream_t s);
+// Alg. 1 from the pair of roots of the row set R's tree and the column set
+// Cs's tree (R and Cs the same set for A_{phi, Y x Y}); leaf pairs hold
+// set-local node ids (tau in R's tree, sigma in Cs's), in canonical order.
+// Writes R.n_adm and R.n_dense.
+void traverse(SetStructure& R, const SetStructure& Cs, double eta, int adm_max,
+              const int32_t* node_lo, const int32_t* node_hi, const double* bmin,
+              const double* bmax, DevBuf<int2>& adm, DevBuf<int2>& dense, cudaStream_t s);
+// build_tree and traverse of one set with itself.
 void build_structure(const double* pts, SetStructure& S, double eta, int adm_max,
                      const DeviceCoords& X, int64_t* perm_out, uint64_t* codes_out,
                      int32_t* node_lo, int32_t* node_hi, double* bmin, double* bmax,

@@ -129,9 +129,42 @@ void add_perm_offsets(hm_handle_s& h)
     HM_LAUNCH("perm offsets");
 }
 
+namespace {
+
+// y (N1 entries per vector) = A_{phi, Y1 x Y2} x (N2 entries per vector):
+// each x goes into set 1's part of a staging vector whose set 0 part stays
+// zero, the square product runs on it (its blocks read columns of set 1 and
+// its tiles are the rows of set 0 only), and set 0's part of the result is y.
+void rect_matvec(hm_handle_s& h, const double* x, double* y, int nrhs, cudaStream_t s)
+{
+    const int64_t N = h.Ntot, N1 = h.n_rows, N2 = h.n_cols;
+    if (!h.rxbuf.p) {
+        h.rxbuf.alloc(N, h.stream);
+        h.rybuf.alloc(N, h.stream);
+        HM_CUDA(cudaMemsetAsync(h.rxbuf.p, 0, N * sizeof(double), h.stream));
+        HM_CUDA(cudaMemsetAsync(h.rybuf.p, 0, N * sizeof(double), h.stream));
+        HM_CUDA(cudaStreamSynchronize(h.stream));
+    }
+    for (int r = 0; r < nrhs; ++r) {
+        copy_in(h.rxbuf.p + N1, x + (int64_t)r * N2, N2 * sizeof(double), s);
+        if (h.opt.accumulate) copy_in(h.rybuf.p, y + (int64_t)r * N1, N1 * sizeof(double), s);
+        if (h.opt.on_the_fly) np_matvec(h, h.rxbuf.p, h.rybuf.p, h.opt.accumulate, s);
+        else mvp_run(h.plan, h.work, h.rxbuf.p, h.rybuf.p, h.opt.accumulate, s,
+                     h.opt.profile ? &h.timer : nullptr);
+        copy_out(y + (int64_t)r * N1, h.rybuf.p, N1 * sizeof(double), s);
+    }
+    if (!is_device_ptr(y)) HM_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace
+
 void matvec(hm_handle_s& h, const double* x, double* y, int nrhs, cudaStream_t s)
 {
     if (h.opt.structure_only) fail(HM_EINVAL, "the handle was built with structure_only");
+    if (h.rect) {
+        rect_matvec(h, x, y, nrhs, s);
+        return;
+    }
     const int64_t N = h.Ntot;
     const bool xd = is_device_ptr(x), yd = is_device_ptr(y);
     if ((!xd || !yd) && !h.xbuf.p) {
@@ -321,6 +354,7 @@ void apply_operator(hm_handle_s& h, const double* p, double* q, cudaStream_t s)
 void cg_solve(hm_handle_s& h, const double* b, double* x, double rtol, int maxit, int* iters,
               double* relres)
 {
+    if (h.rect) fail(HM_EINVAL, "CG needs a square matrix (one set for rows and columns)");
     cudaStream_t s = h.stream;
     const int64_t n = h.Ntot;
     DevBuf<double> bd(n, s), xd(n, s), r(n, s), p(n, s), q(n, s), part(DOT_BLOCKS, s), sc(4, s);

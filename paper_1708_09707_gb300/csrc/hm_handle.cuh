@@ -25,6 +25,12 @@ struct hm_handle_s {
     int64_t Ntot = 0, n_nodes_tot = 0, n_adm = 0, n_dense = 0, n_tiles = 0;
     int64_t max_set_n = 0;
     int64_t factor_entries_U = 0;   // sum_b k_b m_b
+    // A_{phi, Y1 x Y2}: set 0 gives the rows, set 1 the columns; the product
+    // runs on staging vectors of Ntot entries (x in set 1's part, zeros in
+    // set 0's; y in set 0's part)
+    bool rect = false;
+    int64_t n_rows = 0, n_cols = 0;
+    hm::DevBuf<double> rxbuf, rybuf;
     // points and structure
     hm::DevBuf<double> X64;
     hm::DevBuf<float> X32;
@@ -90,7 +96,7 @@ int to_status(const std::exception& e);
 
 void build_sets(hm_handle_s& h, int nsets, const double* points_all, const int64_t* N,
                 const int* d, int kernel, const double* params, int leaf, double eta,
-                double aca_eps, const hm_options& opt);
+                double aca_eps, const hm_options& opt, bool rect = false);
 void matvec(hm_handle_s& h, const double* x, double* y, int nrhs, cudaStream_t s);
 // The product of an on-the-fly handle (device x, y; one vector).
 void np_matvec(hm_handle_s& h, const double* x, double* y, int accumulate, cudaStream_t s);

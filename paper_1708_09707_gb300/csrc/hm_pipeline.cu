@@ -43,18 +43,21 @@ int bits_for(int64_t n)
     return b;
 }
 
+// Block descriptors of leaf pairs: tau in the row tree (lo, hi; its set's
+// first row row0), sigma in the column tree (lo2, hi2; col0).
 __global__ void k_make_blk(const int2* __restrict__ pairs, int64_t n,
                            const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
-                           int64_t row0, Blk* __restrict__ out)
+                           int64_t row0, const int32_t* __restrict__ lo2,
+                           const int32_t* __restrict__ hi2, int64_t col0, Blk* __restrict__ out)
 {
     int64_t b = (int64_t)blockIdx.x * NT + threadIdx.x;
     if (b >= n) return;
     int2 p = pairs[b];
     Blk B;
     B.row0 = row0 + lo[p.x];
-    B.col0 = row0 + lo[p.y];
+    B.col0 = col0 + lo2[p.y];
     B.m = hi[p.x] - lo[p.x];
-    B.n = hi[p.y] - lo[p.y];
+    B.n = hi2[p.y] - lo2[p.y];
     out[b] = B;
 }
 
@@ -440,7 +443,10 @@ AcaArgs aca_args(hm_handle_s& h, DevBuf<int64_t>& setn)
     a.k_cap = h.opt.k_cap;
     a.bset = nullptr;
     a.set_n = nullptr;
-    if (h.precision == HM_PREC_MIXED) {
+    // The mixed-precision floor m n / N rests on ||A||_F >= sqrt(N) phi(0),
+    // which holds for A_{phi, Y x Y} (its diagonal) but not for two sets:
+    // there every block keeps the blockwise test.
+    if (h.precision == HM_PREC_MIXED && !h.rect) {
         std::vector<int64_t> sn(h.sets.size());
         for (size_t q = 0; q < h.sets.size(); ++q) sn[q] = h.sets[q].N;
         setn.alloc(sn.size(), s);
@@ -709,7 +715,7 @@ void rank_stats(hm_handle_s& h)
 }
 
 void validate(int nsets, const int64_t* N, const int* d, int kernel, const double* params,
-              int leaf, double eta, const hm_options& o)
+              int leaf, double eta, const hm_options& o, bool rect)
 {
     if (nsets < 1) fail(HM_EINVAL, "no point sets");
     if (!params) fail(HM_EINVAL, "params is NULL");
@@ -733,17 +739,25 @@ void validate(int nsets, const int64_t* N, const int* d, int kernel, const doubl
         tot += N[q];
     }
     if (tot >= (1ll << 31)) fail(HM_EINVAL, "more than 2^31 points");
-    if (o.on_the_fly && (o.symmetric || o.rank_model || nsets > 1))
+    if (o.on_the_fly && (o.symmetric || o.rank_model || (nsets > 1 && !rect)))
         fail(HM_ENOTSUP, "on_the_fly runs without symmetric, rank_model and batches");
+    if (rect) {
+        if (nsets != 2) fail(HM_EINVAL, "a rectangular matrix takes two point sets");
+        if (d[0] != d[1]) fail(HM_EINVAL, "both point sets need the same dimension");
+        if (params[1] != 0.0)
+            fail(HM_EINVAL, "sigma^2 needs a square matrix (one set for rows and columns)");
+        if (o.symmetric || o.rank_model)
+            fail(HM_ENOTSUP, "symmetric mode and the rank model need a square matrix");
+    }
 }
 
 }  // namespace
 
 void build_sets(hm_handle_s& h, int nsets, const double* points_all, const int64_t* N,
                 const int* d, int kernel, const double* params, int leaf, double eta,
-                double aca_eps, const hm_options& opt)
+                double aca_eps, const hm_options& opt, bool rect)
 {
-    validate(nsets, N, d, kernel, params, leaf, eta, opt);
+    validate(nsets, N, d, kernel, params, leaf, eta, opt, rect);
     if (!points_all) fail(HM_EINVAL, "points is NULL");
     auto t0 = std::chrono::steady_clock::now();
     h.opt = opt;
@@ -782,6 +796,9 @@ void build_sets(hm_handle_s& h, int nsets, const double* points_all, const int64
     }
     h.Ntot = Ntot;
     h.n_nodes_tot = nn;
+    h.rect = rect;
+    h.n_rows = rect ? N[0] : Ntot;
+    h.n_cols = rect ? N[1] : Ntot;
 
     Timer tstruct(s);
     // points on the device
@@ -810,13 +827,28 @@ void build_sets(hm_handle_s& h, int nsets, const double* points_all, const int64
 
     std::vector<DevBuf<int2>> adm(nsets), dense(nsets);
     const double* p = pts;
-    for (int q = 0; q < nsets; ++q) {
-        SetStructure& S = h.sets[q];
-        build_structure(p, S, eta, opt.adm_max, h.X, h.perm.p, h.codes.p + S.row0, h.node_lo.p,
-                        h.node_hi.p, h.bmin.p, h.bmax.p, adm[q], dense[q], s);
-        p += S.N * S.d;
-        h.n_adm += S.n_adm;
-        h.n_dense += S.n_dense;
+    if (rect) {
+        // both sets clustered on their own, Alg. 1 from (root of Y1, root of Y2)
+        for (int q = 0; q < 2; ++q) {
+            SetStructure& S = h.sets[q];
+            build_tree(p, S, h.X, h.perm.p, h.codes.p + S.row0, h.node_lo.p, h.node_hi.p,
+                       h.bmin.p, h.bmax.p, s);
+            p += S.N * S.d;
+        }
+        traverse(h.sets[0], h.sets[1], eta, opt.adm_max, h.node_lo.p, h.node_hi.p, h.bmin.p,
+                 h.bmax.p, adm[0], dense[0], s);
+        h.sets[1].n_adm = h.sets[1].n_dense = 0;
+        h.n_adm = h.sets[0].n_adm;
+        h.n_dense = h.sets[0].n_dense;
+    } else {
+        for (int q = 0; q < nsets; ++q) {
+            SetStructure& S = h.sets[q];
+            build_structure(p, S, eta, opt.adm_max, h.X, h.perm.p, h.codes.p + S.row0,
+                            h.node_lo.p, h.node_hi.p, h.bmin.p, h.bmax.p, adm[q], dense[q], s);
+            p += S.N * S.d;
+            h.n_adm += S.n_adm;
+            h.n_dense += S.n_dense;
+        }
     }
     // perm holds set-local indices; make them absolute for the product
     // (the offsets are applied below by a small kernel per set)
@@ -833,21 +865,28 @@ void build_sets(hm_handle_s& h, int nsets, const double* points_all, const int64
             SetStructure& S = h.sets[q];
             const int32_t* lo = h.node_lo.p + S.node0;
             const int32_t* hi = h.node_hi.p + S.node0;
+            // the column tree: set 1's for a rectangular matrix, else the same
+            const SetStructure& Sc = rect ? h.sets[1] : S;
+            const int32_t* lo2 = h.node_lo.p + Sc.node0;
+            const int32_t* hi2 = h.node_hi.p + Sc.node0;
             if (S.n_adm) {
                 HM_CUDA(cudaMemcpyAsync(h.adm_pairs.p + ao, adm[q].p, S.n_adm * sizeof(int2),
                                         cudaMemcpyDeviceToDevice, s));
                 k_make_blk<<<grid_for(S.n_adm), NT, 0, s>>>(adm[q].p, S.n_adm, lo, hi, S.row0,
-                                                            h.ablk.p + ao); note_launch();
+                                                            lo2, hi2, Sc.row0, h.ablk.p + ao); note_launch();
             }
             if (S.n_dense) {
                 HM_CUDA(cudaMemcpyAsync(h.dense_pairs.p + dof, dense[q].p,
                                         S.n_dense * sizeof(int2), cudaMemcpyDeviceToDevice, s));
                 k_make_blk<<<grid_for(S.n_dense), NT, 0, s>>>(dense[q].p, S.n_dense, lo, hi,
-                                                              S.row0, h.dblk.p + dof); note_launch();
+                                                              S.row0, lo2, hi2, Sc.row0,
+                                                              h.dblk.p + dof); note_launch();
             }
             HM_LAUNCH("blocks");
             ao += S.n_adm;
             dof += S.n_dense;
+            ntile[q] = 0;
+            if (rect && q > 0) continue;   // the column set gives no rows
             // leaf tiles of this set, in row order
             DevBuf<int64_t> flag(S.n_nodes, s), off(S.n_nodes + 1, s);
             k_leaf_flags<<<grid_for(S.n_nodes), NT, 0, s>>>(lo, hi, S.n_nodes, leaf, flag.p); note_launch();
@@ -876,6 +915,7 @@ void build_sets(hm_handle_s& h, int nsets, const double* points_all, const int64
     {
         int64_t o = 0;
         for (int q = 0; q < nsets; ++q) {
+            if (!ntile[q]) continue;
             HM_CUDA(cudaMemcpyAsync(h.tile_row0.p + o, trow[q].p, ntile[q] * sizeof(int64_t),
                                     cudaMemcpyDeviceToDevice, s));
             HM_CUDA(cudaMemcpyAsync(h.tile_m.p + o, tm[q].p, ntile[q] * sizeof(int32_t),

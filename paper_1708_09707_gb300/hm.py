@@ -97,6 +97,9 @@ def _declare(L):
     L.hm_build_ex.restype = _vp
     L.hm_build_ex.argtypes = [_vp, i64, C.c_int, C.c_int, _vp, C.c_int, C.c_double,
                               C.c_double, C.POINTER(Options), pi]
+    L.hm_build_rect.restype = _vp
+    L.hm_build_rect.argtypes = [_vp, i64, _vp, i64, C.c_int, C.c_int, _vp, C.c_int, C.c_double,
+                                C.c_double, C.POINTER(Options), pi]
     L.hm_build.restype = _vp
     L.hm_build.argtypes = [_vp, i64, C.c_int, C.c_int, _vp, C.c_int, C.c_double, C.c_double]
     L.hm_matvec.argtypes = [_vp, _vp, _vp]
@@ -175,23 +178,35 @@ def options(precision=PREC_FP64, near_format=NEAR_AUTO, adm_max=False, k_cap=64,
 
 
 class HMatrix:
-    """H-matrix of A_{phi, Y x Y} (+ sigma^2 I) built on the GPU (hm_build_ex).
+    """H-matrix of A_{phi, Y x Y} (+ sigma^2 I) built on the GPU (hm_build_ex),
+    or of A_{phi, Y1 x Y2} with cols = Y2 (hm_build_rect; points = Y1).
 
     points: (N, d) float64 numpy array (host) or torch tensor (host or cuda).
     """
 
     def __init__(self, points, kernel: int, ell: float, leaf: int, eta: float,
-                 aca_eps: float, sigma2: float = 0.0, **opts):
+                 aca_eps: float, sigma2: float = 0.0, cols=None, **opts):
         L = lib()
         if isinstance(points, np.ndarray):
             points = np.ascontiguousarray(points, dtype=np.float64)
+        if isinstance(cols, np.ndarray):
+            cols = np.ascontiguousarray(cols, dtype=np.float64)
         self.n, self.d = int(points.shape[0]), int(points.shape[1])
+        self.rect = cols is not None
+        self.n_cols = int(cols.shape[0]) if self.rect else self.n
         self._theta = opts.get("rank_model_theta")
         self.opt = options(**opts)
         prm = np.array([ell, sigma2], dtype=np.float64)
         st = C.c_int(0)
-        self._h = L.hm_build_ex(_ptr(points), self.n, self.d, kernel, prm.ctypes.data, leaf,
-                                eta, aca_eps, C.byref(self.opt), C.byref(st))
+        if self.rect:
+            if int(cols.shape[1]) != self.d:
+                raise HMError(-1, "both point sets need the same dimension")
+            self._h = L.hm_build_rect(_ptr(points), self.n, _ptr(cols), self.n_cols, self.d,
+                                      kernel, prm.ctypes.data, leaf, eta, aca_eps,
+                                      C.byref(self.opt), C.byref(st))
+        else:
+            self._h = L.hm_build_ex(_ptr(points), self.n, self.d, kernel, prm.ctypes.data, leaf,
+                                    eta, aca_eps, C.byref(self.opt), C.byref(st))
         if not self._h:
             raise HMError(st.value, L.hm_last_error().decode())
         self.kernel, self.ell, self.leaf, self.eta = kernel, ell, leaf, eta
@@ -205,17 +220,19 @@ class HMatrix:
     __del__ = free
 
     def matvec(self, x, y=None, stream=None):
-        """y = H x + sigma^2 x; numpy in -> numpy out, torch in -> torch out."""
+        """y = H x + sigma^2 x; numpy in -> numpy out, torch in -> torch out.
+        For two point sets x has n_cols entries per vector and y n."""
         if _is_torch(x):
             import torch
             nrhs = 1 if x.dim() == 1 else x.shape[0]
             if y is None:
-                y = torch.empty_like(x)
+                shape = (self.n,) if x.dim() == 1 else (nrhs, self.n)
+                y = torch.empty(shape, dtype=x.dtype, device=x.device)
         else:
             x = np.ascontiguousarray(x, dtype=np.float64)
             nrhs = 1 if x.ndim == 1 else x.shape[0]
             if y is None:
-                y = np.empty_like(x)
+                y = np.empty((self.n,) if x.ndim == 1 else (nrhs, self.n))
         _check(lib().hm_matvec_ex(self._h, _ptr(x), _ptr(y), nrhs, _stream_ptr(stream)))
         return y
 
@@ -226,8 +243,9 @@ class HMatrix:
 
     def structure(self):
         st = self.stats()
-        codes = np.zeros(self.n, np.uint64)
-        perm = np.zeros(self.n, np.int64)
+        ntot = self.n + self.n_cols if self.rect else self.n
+        codes = np.zeros(ntot, np.uint64)
+        perm = np.zeros(ntot, np.int64)
         adm = np.zeros((max(st["n_adm"], 1), 2), np.int64)
         dense = np.zeros((max(st["n_dense"], 1), 2), np.int64)
         ranks = np.zeros(max(st["n_adm"], 1), np.int32)
