@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--otf-workloads", default="self,matern3d_n1m",
                    help="comma-separated workloads of the on-the-fly measurement "
                         "(self = the bench workload at its size)")
+    p.add_argument("--no-rect", action="store_true",
+                   help="skip the context run of A(Y1 x Y2) for two point sets")
     p.add_argument("--no-paper", action="store_true",
                    help="skip the context run in the paper's own setting (N=2^19 Halton, C=2048)")
     p.add_argument("--n", type=int, default=0,
@@ -126,6 +128,38 @@ def paper_setting(hm, inputs, name="halton2d_n512k_k16", n_mvp=3):
         out[key + "_on_the_fly"] = {"build_s": b, "mvp_s": m,
                                     "aca_passes_per_product": st["aca_passes"]}
     return out
+
+
+def rect_context(hm, inputs, w, rows, n_cols=1 << 19, n_mvp=3):
+    """A(Y1 x Y2) for two point sets (hm_build_rect): Y1 the step's points,
+    Y2 n_cols Halton points in the same unit cube, the step's kernel and
+    parameters, mixed precision; build and product time (CUDA events, points
+    and x on the device)."""
+    import torch
+    d = rows.shape[1]
+    cols = torch.from_numpy(inputs.halton_points(n_cols, d)).cuda()
+    x = torch.from_numpy(inputs.normal_vector(n_cols, inputs.X_SEED)).cuda()
+    y = torch.empty(rows.shape[0], dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    res = []
+    for rep in range(2):                # the first build warms up the tuner
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        H = hm.HMatrix(rows, w["kernel"], w["ell"], w["leaf"], w["eta"], w["eps"], cols=cols,
+                       precision=hm.PREC_MIXED)
+        e[1].record(stream)
+        for _ in range(n_mvp):
+            H.matvec(x, y)
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        st = H.stats()
+        H.free()
+        res.append((e[0].elapsed_time(e[1]) / 1e3, e[1].elapsed_time(e[2]) / n_mvp, st))
+    b, m, st = res[-1]
+    return {"rows": int(rows.shape[0]), "cols": n_cols, "cols_points": "halton", "d": d,
+            "precision": "mixed", "build_s": b, "mvp_ms": m,
+            "mvp_hbm_frac": st["mvp_bytes"] / (m / 1e3) / 1e9 / peaks()[0],
+            "n_adm": st["n_adm"], "n_dense": st["n_dense"], "max_rank": st["max_rank"]}
 
 
 def tile_traffic(mvp_tile_bytes):
@@ -671,6 +705,11 @@ def main():
             Ho.free()
             del po, xo, yo
 
+    # A(Y1 x Y2): the step's points against 2^19 Halton points
+    rect = None
+    if world == 1 and not args.no_rect:
+        rect = rect_context(hm, inputs, w, pts)
+
     # e2e: the same step through the C-ABI with pinned host buffers
     pts_h = torch.from_numpy(pts_np).pin_memory()
     xs_h = torch.from_numpy(x_np).pin_memory()
@@ -757,7 +796,7 @@ def main():
         "build_s": build_ms / 1e3, "mvp_ms": mvp_ms,
         "fp64": fp64, "mixed_vs_fp64_rel_err": err,
         "mixed_without_rank_model": plain, "mixed_nonsymmetric": nonsym,
-        "multi_rhs": multi, "on_the_fly": otf,
+        "multi_rhs": multi, "on_the_fly": otf, "rectangular": rect,
         "rank_model": model_info,
         "speedup_vs_fp64": (fp64["ms_per_step"] / total) if fp64 else None,
         "e2e": {"value": e2e_ms / 1e3, "unit": "s/step (build + %d H-MVP)" % N_MVP,
