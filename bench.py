@@ -54,6 +54,9 @@ def parse():
     p.add_argument("--otf-workloads", default="self,matern3d_n1m",
                    help="comma-separated workloads of the on-the-fly measurement "
                         "(self = the bench workload at its size)")
+    p.add_argument("--sweeps", action="store_true",
+                   help="instead of the step: the paper's experiments as curves (Sec. 6.3 "
+                        "convergence in k, Sec. 6.4 runtime against N), one JSON line")
     p.add_argument("--no-rect", action="store_true",
                    help="skip the context run of A(Y1 x Y2) for two point sets")
     p.add_argument("--no-paper", action="store_true",
@@ -467,6 +470,122 @@ def run_batch(args):
     hdist.finalize()
 
 
+# ------------------------------------------------------------- sweeps
+def _elapsed(fn, stream):
+    """CUDA-event time (ms) of fn() on the stream, with a synchronize on both sides."""
+    import torch
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    e[0].record(stream)
+    out = fn()
+    e[1].record(stream)
+    torch.cuda.synchronize()
+    return e[0].elapsed_time(e[1]), out
+
+
+def run_sweeps(args):
+    """The paper's experiments on this GPU, FP64 as in the paper, Halton
+    points in [0,1]^d, the unscaled kernels, C_leaf, eta and the fixed rank
+    of Sec. 6.3 to 6.4; points and x on the device, CUDA events.
+      convergence  Sec. 6.3: N = 32768, C_leaf 256, eta 1.5, e_rel of the
+                   fixed-rank-k product against the exact product (an eta = 0
+                   build: every leaf dense), mean over three x
+      structure    Sec. 6.4, first figure: Morton codes + sort (the spatial
+                   data structure) and the whole structure (codes, sort, tree,
+                   boxes, Alg. 1 traversal) for N up to 2^26, C_leaf 2048;
+                   uniform points here (the host makes 2^26 Halton points ten
+                   times slower)
+      mvp          Sec. 6.4, second figure: product time with stored factors
+                   (P) and with factors recomputed per product (NP), C_leaf
+                   2048, eta 1.5, k = 16"""
+    import torch
+    from paper_1708_09707_gb300 import build, hm, inputs
+    build.build()
+    hm.lib()
+    stream = torch.cuda.current_stream()
+    out = {"precision": "fp64", "points": "halton", "kernels": {"gaussian": "exp(-r^2)",
+           "matern_k1": "r K_1(r), phi(0) = 1"}}
+    kernels = (("gaussian", hm.GAUSSIAN), ("matern_k1", hm.MATERN_K1))
+
+    conv = []
+    n = 32768
+    for d in (2, 3):
+        pts = torch.from_numpy(inputs.halton_points(n, d)).cuda()
+        xs = [torch.from_numpy(inputs.normal_vector(n, inputs.X_SEED + t)).cuda() for t in range(3)]
+        for kname, kern in kernels:
+            E = hm.HMatrix(pts, kern, 1.0, 256, 0.0, 1e-6)
+            ys = [E.matvec(x) for x in xs]
+            E.free()
+            errs = []
+            for k in (1, 2, 3, 4, 6, 8, 10, 12, 14, 16):
+                H = hm.HMatrix(pts, kern, 1.0, 256, 1.5, 0.0, k_cap=k)
+                e = [float(torch.linalg.norm(H.matvec(x) - y) / torch.linalg.norm(y))
+                     for x, y in zip(xs, ys)]
+                H.free()
+                errs.append([k, sum(e) / len(e)])
+            conv.append({"d": d, "kernel": kname, "n": n, "leaf": 256, "eta": 1.5,
+                         "e_rel_by_k": errs})
+        del pts, xs
+    out["convergence"] = conv
+
+    struct = []
+    for d in (2, 3):
+        for lg in range(16, 27, 2):
+            n = 1 << lg
+            pts = torch.from_numpy(inputs.uniform_points(n, d, inputs.POINT_SEED + 20 + d)).cuda()
+            codes = torch.empty(n, dtype=torch.int64, device="cuda")
+            vals = torch.arange(n, dtype=torch.int32, device="cuda")
+            bits = d * min(32, 64 // d)
+
+            def spatial():
+                hm.morton_codes(pts, codes)
+                hm.radix_sort_pairs(codes, vals, bits)
+            spatial()
+            t_sp, _ = _elapsed(spatial, stream)
+            hm.HMatrix(pts, hm.GAUSSIAN, 1.0, 2048, 1.5, 0.0, k_cap=16, structure_only=True).free()
+            t_all, H = _elapsed(lambda: hm.HMatrix(pts, hm.GAUSSIAN, 1.0, 2048, 1.5, 0.0,
+                                                   k_cap=16, structure_only=True), stream)
+            st = H.stats()
+            H.free()
+            struct.append({"d": d, "n": n, "morton_sort_ms": t_sp, "structure_ms": t_all,
+                           "n_adm": st["n_adm"], "n_dense": st["n_dense"]})
+            del pts, codes, vals
+    out["structure"] = struct
+    out["structure_points"] = "uniform"
+    out["structure_paper_p100"] = {"morton_sort_s_at_2^26": "below 0.5",
+                                   "tree_and_traversal_s_at_2^26": "below 3"}
+
+    mvp = []
+    for d in (2, 3):
+        for lg in range(15, 23):
+            n = 1 << lg
+            pts = torch.from_numpy(inputs.halton_points(n, d)).cuda()
+            x = torch.from_numpy(inputs.normal_vector(n, inputs.X_SEED)).cuda()
+            y = torch.empty_like(x)
+            row = {"d": d, "n": n}
+            # stored: the FP64 near field of C_leaf 2048 is 116 GB at 2^19 in 2-D
+            stored_max = 19 if d == 2 else 17
+            for mode, otf, top in (("P", False, stored_max), ("NP", True, 21 if d == 2 else 20)):
+                if lg > top:
+                    continue
+                try:
+                    tb, H = _elapsed(lambda: hm.HMatrix(pts, hm.GAUSSIAN, 1.0, 2048, 1.5, 0.0,
+                                                        k_cap=16, on_the_fly=otf), stream)
+                    if not otf:
+                        H.matvec(x, y)           # the first product tunes the gather
+                    reps = 3 if n <= (1 << 18) else 1
+                    tm, _ = _elapsed(lambda: [H.matvec(x, y) for _ in range(reps)], stream)
+                    H.free()
+                    row[mode] = {"build_ms": tb, "mvp_ms": tm / reps}
+                except hm.HMError as e:
+                    row[mode] = {"error": str(e)}
+            mvp.append(row)
+            del pts, x, y
+    out["mvp"] = mvp
+    out["mvp_paper_p100"] = {"np_mvp_at_2^25_d2": "about 6 minutes"}
+    print(json.dumps({"sweeps": out}))
+
+
 # ---------------------------------------------------------------- GPU leg
 def main():
     args = parse()
@@ -475,6 +594,9 @@ def main():
         return
     if args.workload == "ragged64":
         run_batch(args)
+        return
+    if args.sweeps:
+        run_sweeps(args)
         return
     import torch
 
