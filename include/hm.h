@@ -144,9 +144,9 @@ hm_handle hm_build_ex(const double* points, int64_t N, int d, int kernel,
  *         both copied, may be freed on return
  *   params[1] (sigma^2) must be 0: there is no diagonal
  *   the other arguments as hm_build_ex. symmetric and rank_model are
- *   refused (HM_ENOTSUP); on_the_fly is supported. In mixed precision every
- *   block keeps the blockwise ACA test (the global floor rests on the unit
- *   diagonal of a square kernel matrix).
+ *   refused (HM_ENOTSUP); on_the_fly is supported. In mixed precision the
+ *   global floor of the ACA tests takes the dense leaves' sum of squares as
+ *   its lower bound of ||A||_F^2 (a square matrix uses its unit diagonal).
  * hm_matvec / hm_matvec_ex then take x of N2 entries (per vector, in Y2's
  * order) and write y of N1 entries (Y1's order), one product per vector;
  * hm_cg refuses the handle. hm_export_structure writes Y1's permutation

@@ -129,6 +129,10 @@ void near_assemble(int near_format, const KernelParams& kp, const DeviceCoords& 
                    const int32_t* tile_m, const DnDesc* desc, int64_t n_ent, void* store,
                    cudaStream_t s);
 size_t near_entry_bytes(int near_format);
+// Sum over the dense leaves blk[0..n) of ||A_b||_F^2, entries in float (the
+// mixed path's X.x32 coordinates); a lower bound of ||A||_F^2.
+double dense_fro2(const KernelParams& kp, const DeviceCoords& X, const Blk* blk, int64_t n,
+                  cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Product (hm_mvp.cu)

@@ -30,6 +30,7 @@ struct hm_handle_s {
     // set 0's; y in set 0's part)
     bool rect = false;
     int64_t n_rows = 0, n_cols = 0;
+    double rect_fro2 = 0.0;   // mixed precision: sum of ||A_b||_F^2 over the dense leaves
     hm::DevBuf<double> rxbuf, rybuf;
     // points and structure
     hm::DevBuf<double> X64;

@@ -8,6 +8,8 @@
 // entries, then its lo entries) or a single bf16.
 #include "hm_kernel_fn.cuh"
 
+#include <vector>
+
 namespace hm {
 
 namespace {
@@ -97,7 +99,54 @@ void launch(int fmt, const KernelParams& kp, const DeviceCoords& X, const Blk* b
     }
 }
 
+// Sum of phi^2 over the entries of each dense leaf (one warp per leaf, the
+// float kernel functions of the mixed path); out[b] in double.
+template <int KERN>
+__global__ void k_dense_fro2(KernelParams kp, DeviceCoords X, const Blk* __restrict__ blk,
+                             int64_t n, double* __restrict__ out)
+{
+    const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (b >= n) return;
+    const Blk B = blk[b];
+    const float c = kconst<float>(kp);
+    double s = 0.0;
+    for (int i = 0; i < B.m; ++i) {
+        const Pt<float> pi = load_pt<float>(X, B.row0 + i);
+        float si = 0.f;
+        for (int j = lane; j < B.n; j += 32) {
+            const float v = phi<KERN>(dist2(pi, load_pt<float>(X, B.col0 + j)), c);
+            si = fmaf(v, v, si);
+        }
+        s += (double)si;
+    }
+    s = warp_sum(s);
+    if (lane == 0) out[b] = s;
+}
+
 }  // namespace
+
+double dense_fro2(const KernelParams& kp, const DeviceCoords& X, const Blk* blk, int64_t n,
+                  cudaStream_t s)
+{
+    if (n <= 0) return 0.0;
+    DevBuf<double> part(n, s);
+    const unsigned g = (unsigned)ceil_div(n * 32, (int64_t)256);
+    if (kp.kernel == HM_GAUSSIAN)
+        k_dense_fro2<HM_GAUSSIAN><<<g, 256, 0, s>>>(kp, X, blk, n, part.p);
+    else if (kp.kernel == HM_MATERN32)
+        k_dense_fro2<HM_MATERN32><<<g, 256, 0, s>>>(kp, X, blk, n, part.p);
+    else
+        k_dense_fro2<HM_MATERN_K1><<<g, 256, 0, s>>>(kp, X, blk, n, part.p);
+    note_launch();
+    HM_LAUNCH("dense leaf norms");
+    std::vector<double> h(n);
+    HM_CUDA(cudaMemcpyAsync(h.data(), part.p, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    HM_CUDA(cudaStreamSynchronize(s));
+    double sum = 0.0;          // in leaf order: the same value on every run
+    for (int64_t b = 0; b < n; ++b) sum += h[b];
+    return sum;
+}
 
 size_t near_entry_bytes(int fmt)
 {

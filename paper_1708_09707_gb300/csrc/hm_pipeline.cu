@@ -443,12 +443,19 @@ AcaArgs aca_args(hm_handle_s& h, DevBuf<int64_t>& setn)
     a.k_cap = h.opt.k_cap;
     a.bset = nullptr;
     a.set_n = nullptr;
-    // The mixed-precision floor m n / N rests on ||A||_F >= sqrt(N) phi(0),
-    // which holds for A_{phi, Y x Y} (its diagonal) but not for two sets:
-    // there every block keeps the blockwise test.
-    if (h.precision == HM_PREC_MIXED && !h.rect) {
+    // The mixed-precision floor m n / N rests on ||A||_F^2 >= N phi(0)^2 (the
+    // diagonal of A_{phi, Y x Y}), so the floors of all blocks add up to at
+    // most ||A||_F^2. Two sets have no diagonal; there F^2 = the dense leaves'
+    // sum of squares, also a lower bound of ||A||_F^2, takes its place with
+    // N1 N2 entries: floor m n F^2 / (N1 N2), i.e. N replaced by
+    // ceil(N1 N2 / F^2). Without dense leaves (F^2 = 0) no floor is used.
+    const bool floor = h.precision == HM_PREC_MIXED && (!h.rect || h.rect_fro2 > 0.0);
+    if (floor) {
         std::vector<int64_t> sn(h.sets.size());
         for (size_t q = 0; q < h.sets.size(); ++q) sn[q] = h.sets[q].N;
+        if (h.rect)
+            sn[0] = std::max<int64_t>(
+                1, (int64_t)std::ceil((double)h.n_rows * (double)h.n_cols / h.rect_fro2));
         setn.alloc(sn.size(), s);
         copy_in(setn.p, sn.data(), sn.size() * sizeof(int64_t), s);
         a.bset = h.adm_set.p;
@@ -925,6 +932,8 @@ void build_sets(hm_handle_s& h, int nsets, const double* points_all, const int64
     }
     fill_block_sets(h);
     add_perm_offsets(h);
+    if (rect && h.precision == HM_PREC_MIXED)
+        h.rect_fro2 = dense_fro2(h.kp, h.X, h.dblk.p, h.n_dense, s);
     h.stats.t_structure_ms = tstruct.stop_ms();
     adm.clear();
     dense.clear();

@@ -142,3 +142,20 @@ def test_rectangular_refusals(hm, orc):
     with pytest.raises(hm.HMError) as e:
         H.cg(np.ones(500))
     assert e.value.code == -1
+
+
+def test_mixed_floor_keeps_ranks_below_the_cap(hm, orc):
+    """Mixed precision for two sets: the floor of the ACA tests (with the
+    dense leaves' sum of squares as its bound of ||A||_F^2) stops blocks whose
+    entries lie near float underflow before they fit rounding noise up to the
+    rank cap, and the product stays within 1e-5 of the oracle."""
+    P = inputs.mixture_points(1 << 15, 2, 51)
+    Q = inputs.halton_points(1 << 14, 2)
+    x = inputs.normal_vector(1 << 14, 52)
+    O = orc.HMatrix(P, 0, 0.1, 64, 1.0, 1e-6, cols=Q)
+    H = hm.HMatrix(P, 0, 0.1, 64, 1.0, 1e-6, cols=Q, precision=hm.PREC_MIXED)
+    st = H.stats()
+    assert st["rank_cap_hits"] == 0, st["rank_cap_hits"]
+    assert st["max_rank"] <= int(O.ranks()[0].max()) + 8
+    e = rel(H.matvec(x), O.matvec(x))
+    assert e <= MIXED_TOL, e
