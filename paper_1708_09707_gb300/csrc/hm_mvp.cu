@@ -47,28 +47,8 @@ __global__ void k_gather_x(const double* __restrict__ x, const int64_t* __restri
     if (i < N) xm[i] = (R)x[perm[i]];
 }
 
-// Four lane values s[0..3] summed over the warp as a reduce-scatter: after
-// it the lanes 8e .. 8e + 7 hold the total of s[e] (xor partners 16 and 8
-// split the values, 4, 2, 1 add the rest; 6 shuffles for 4 sums).
-template <class R>
-__device__ __forceinline__ R warp_sum4(const R (&s)[4], int lane)
-{
-    const bool hi = lane & 16, mid = lane & 8;
-    R a = hi ? s[2] : s[0], b = hi ? s[3] : s[1];
-    a += __shfl_xor_sync(0xffffffffu, hi ? s[0] : s[2], 16);
-    b += __shfl_xor_sync(0xffffffffu, hi ? s[1] : s[3], 16);
-    R v = mid ? b : a;
-    v += __shfl_xor_sync(0xffffffffu, mid ? a : b, 8);
-    v += __shfl_xor_sync(0xffffffffu, v, 4);
-    v += __shfl_xor_sync(0xffffffffu, v, 2);
-    v += __shfl_xor_sync(0xffffffffu, v, 1);
-    return v;
-}
-
-// t partials: one warp per (block, 256-column chunk); lane j holds x of the
-// chunk's columns j, j + 32, ... Four factor columns per pass: their loads
-// are issued together (a pass past the rank re-reads column k - 1, an L1
-// hit, and writes nothing) and their lane sums meet in one reduce-scatter.
+// t partials: one warp per (block, 256-column chunk); lane j holds x of 8
+// columns and each factor column is reduced with shuffles.
 template <class R>
 __global__ void __launch_bounds__(VT_NT)
 k_vtx(const Blk* __restrict__ blk, const int32_t* __restrict__ rank,
@@ -94,21 +74,16 @@ k_vtx(const Blk* __restrict__ blk, const int32_t* __restrict__ rank,
     }
     const int64_t d = dst[w];
     R* out = d >= 0 ? tp + d : t + (-d - 1);
-    for (int l0 = 0; l0 < k; l0 += 4) {
-        R s[4];
+    for (int l = 0; l < k; ++l) {
+        const R* Vl = V + (int64_t)l * n + c0;
+        R s = 0;
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const R* Vl = V + (int64_t)min(l0 + e, k - 1) * n + c0;
-            s[e] = 0;
-#pragma unroll
-            for (int q = 0; q < VCH / 32; ++q) {
-                const int jj = lane + 32 * q;
-                if (jj < cn) s[e] += Vl[jj] * xs[q];
-            }
+        for (int q = 0; q < VCH / 32; ++q) {
+            const int jj = lane + 32 * q;
+            if (jj < cn) s += Vl[jj] * xs[q];
         }
-        const R v = warp_sum4(s, lane);
-        const int e = lane >> 3;
-        if ((lane & 7) == 0 && l0 + e < k) out[l0 + e] = v;
+        s = warp_sum(s);
+        if (lane == 0) out[l] = s;
     }
 }
 // Sum the partials of blocks that span several column chunks (fixed order).
