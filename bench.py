@@ -133,6 +133,34 @@ def paper_setting(hm, inputs, name="halton2d_n512k_k16", n_mvp=3):
     return out
 
 
+# Algorithmic flops of one kernel evaluation (squared distance in three
+# coordinates plus the kernel, as the library counts them for ACA) and the
+# multiply-add that takes an evaluated entry into a row sum.
+EVAL_FLOPS = {0: 10.0, 1: 13.0, 2: 76.0}
+
+
+def otf_roofline(so, kernel, peak):
+    """ALU rooflines of an on-the-fly product (profiled handle): the ACA
+    passes (the library's count of ACA flops for one product) and the dense
+    leaves evaluated inside the product (near entries x (evaluation + the
+    multiply-add)), each per product against the measured FP32 FMA peak."""
+    cnt = max(so["mvp_count"], 1)
+    t_aca = so["t_np_aca_ms"] / cnt
+    t_low = so["t_np_lowrank_ms"] / cnt
+    t_near = so["t_np_near_ms"] / cnt
+    near_flops = so["near_entries"] * (EVAL_FLOPS[kernel] + 2.0)
+    out = {"bound": "alu", "peak": peak, "unit": "TFLOP/s",
+           "peak_source": "measured FP32 FMA peak (hm_alu_peak)",
+           "aca": {"ms": t_aca, "flops": so["aca_flops"]},
+           "near": {"ms": t_near, "flops": near_flops, "entries": so["near_entries"]},
+           "lowrank_ms": t_low}
+    for k in ("aca", "near"):
+        ms = out[k]["ms"]
+        out[k]["achieved"] = out[k]["flops"] / (ms * 1e-3) / 1e12 if ms > 0 else None
+        out[k]["frac"] = out[k]["achieved"] / peak if out[k]["achieved"] else None
+    return out
+
+
 def rect_context(hm, inputs, w, rows, n_cols=1 << 19, n_mvp=3):
     """A(Y1 x Y2) for two point sets (hm_build_rect): Y1 the step's points,
     Y2 n_cols Halton points in the same unit cube, the step's kernel and
@@ -792,6 +820,7 @@ def main():
     # workload, and on the 3-D Matern workload at N = 2^20, whose stored
     # H-matrix does not fit one GPU
     otf = None
+    fp32_peak = hm.alu_peak(hm.PREC_MIXED) / 1e12
     if world == 1 and not args.no_otf:
         otf = []
         names = [args.workload if q == "self" else q for q in args.otf_workloads.split(",")]
@@ -809,7 +838,7 @@ def main():
             torch.cuda.synchronize()
             ev[0].record(stream)
             Ho = hm.HMatrix(po, wo["kernel"], wo["ell"], wo["leaf"], wo["eta"], wo["eps"],
-                            precision=hm.PREC_MIXED, on_the_fly=True,
+                            precision=hm.PREC_MIXED, on_the_fly=True, profile=True,
                             adm_max=(wo["adm"] == "max"))
             ev[1].record(stream)
             torch.cuda.nvtx.range_push("on_the_fly_" + wname)
@@ -823,7 +852,8 @@ def main():
                         "build_s": ev[0].elapsed_time(ev[1]) / 1e3,
                         "mvp_ms": ev[1].elapsed_time(ev[2]) / reps,
                         "aca_passes_per_product": so["aca_passes"], "n_adm": so["n_adm"],
-                        "n_dense": so["n_dense"]})
+                        "n_dense": so["n_dense"],
+                        "roofline": otf_roofline(so, wo["kernel"], fp32_peak)})
             Ho.free()
             del po, xo, yo
 
@@ -874,7 +904,6 @@ def main():
                         "ms": mvp_t_vtx}}
     mvp_roof["frac"] = mvp_roof["achieved"] / hbm
     mvp_roof["peak_source"] = peak_src + " copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
-    fp32_peak = hm.alu_peak(hm.PREC_MIXED) / 1e12
     aca_roof = {"bound": "alu", "kernel": "batched ACA (all size classes, concurrent)",
                 "achieved": st["aca_flops"] / (st["t_aca_ms"] * 1e-3) / 1e12,
                 "peak": fp32_peak, "unit": "TFLOP/s", "traffic": None,

@@ -222,6 +222,12 @@ typedef struct hm_stats {
        <= 2^(c+6); class 0 from 1, class 11 unbounded), CUDA events on each
        class's stream (the classes run concurrently), summed over passes */
     double t_aca_class_ms[12];
+    /* profile = 1 on an on-the-fly handle: sums over the products since the
+       last hm_get_stats of the time in the ACA passes, in the low-rank apply
+       (t = V^T x and U t of each pass) and in the dense leaves; aca_evals and
+       aca_flops then count the ACA work of one product, near_entries the
+       dense entries evaluated per product */
+    double t_np_aca_ms, t_np_lowrank_ms, t_np_near_ms;
 } hm_stats;
 
 int hm_get_stats(hm_handle h, hm_stats* out);

@@ -253,6 +253,14 @@ int hm_get_stats(hm_handle h, hm_stats* out)
         return HM_EINVAL;
     }
     try {
+        if (h->opt.profile && h->opt.on_the_fly) {
+            // the on-the-fly product keeps its sums in the stats themselves
+            *out = h->stats;
+            h->stats.mvp_count = 0;
+            h->stats.t_mvp_ms = h->stats.t_np_aca_ms = h->stats.t_np_lowrank_ms = 0.0;
+            h->stats.t_np_near_ms = 0.0;
+            return HM_OK;
+        }
         if (h->opt.profile) {
             h->timer.collect();
             h->stats.mvp_count = h->timer.count;

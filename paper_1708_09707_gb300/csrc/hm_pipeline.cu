@@ -642,6 +642,10 @@ void np_prepare(hm_handle_s& h)
     HM_CUDA(cudaStreamSynchronize(s));
 }
 
+namespace {
+void rank_stats(hm_handle_s& h);
+}
+
 // y = H x (+ sigma^2 x) for device x, y without stored factors: per pass, ACA
 // of its leaves into the scratch, then t_b = V_b^T x|sigma and y_m += U_b t_b;
 // then the dense leaves evaluated on the fly. Runs on the handle's stream,
@@ -662,7 +666,20 @@ void np_matvec(hm_handle_s& h, const double* x, double* y, int accumulate, cudaS
     np_gather_x(h.precision, x, h.perm.p, N, h.np_xm.p, hs);
     DevBuf<int64_t> setn;
     const AcaArgs a = aca_args(h, setn);
-    for (size_t q = 0; q + 1 < h.np_pass.size(); ++q) {
+    // profile = 1: events on the handle's stream around every phase (ACA and
+    // low-rank apply of each pass, then the dense leaves)
+    const bool prof = h.opt.profile != 0;
+    const size_t npass = h.np_pass.size() - 1;
+    std::vector<cudaEvent_t> pe;
+    auto mark = [&]() {
+        if (!prof) return;
+        cudaEvent_t e;
+        HM_CUDA(cudaEventCreate(&e));
+        HM_CUDA(cudaEventRecord(e, hs));
+        pe.push_back(e);
+    };
+    mark();
+    for (size_t q = 0; q < npass; ++q) {
         const int64_t b0 = h.np_pass[q], b1 = h.np_pass[q + 1], nb = b1 - b0;
         AcaOrder O;
         aca_order(h, h.np_ids.p + b0, nb, nullptr, O);
@@ -671,18 +688,43 @@ void np_matvec(hm_handle_s& h, const double* x, double* y, int accumulate, cudaS
                                                  h.np_scratch.p, vbase, esz, h.Uptr.p, h.Vptr.p); note_launch();
         HM_LAUNCH("set ptrs");
         aca_range(h, O, a, 0, nb);
+        mark();
         np_lowrank(h.precision, h.ablk.p, h.rank.p, h.Uptr.p, h.Vptr.p, b0, b1, h.np_vptr.p,
                    h.np_vitems.p, h.np_hvptr[b0], h.np_hvptr[b1], h.np_aitems.p, h.np_naitems,
                    h.lists.lr_ent.p, h.tile_m.p, h.np_xm.p, h.np_tp.p, h.np_t.p, h.np_kcap,
                    h.np_ld, h.np_acc.p, hs);
+        mark();
     }
     check_status(h);
     np_apply_finish(h.np_aptr.p, h.tile_row0.p, h.tile_m.p, h.n_tiles, h.np_ld, h.np_acc.p,
                     h.np_yacc.p, hs);
+    mark();
     np_near(h.precision, h.kp, h.X, h.lists.items.p, h.lists.n_items, h.lists.item_ptr.p,
             h.lists.ucol_ptr.p, h.lists.ncol_ptr.p, h.lists.ncol_x.p, h.tile_row0.p, h.tile_m.p,
             h.n_tiles, h.np_ld, h.np_xm.p, h.np_part.p, h.np_yacc.p, hs);
+    mark();
     np_finish(h.perm.p, nullptr, h.sigma2, N, h.np_yacc.p, x, y, accumulate, hs);
+    mark();
+    if (prof) {
+        // pe: start, then (after ACA, after low-rank) per pass, before and
+        // after the dense leaves, end
+        HM_CUDA(cudaEventSynchronize(pe.back()));
+        auto ms = [&](size_t i, size_t j) {
+            float t = 0.f;
+            HM_CUDA(cudaEventElapsedTime(&t, pe[i], pe[j]));
+            return (double)t;
+        };
+        for (size_t q = 0; q < npass; ++q) {
+            h.stats.t_np_aca_ms += ms(q == 0 ? 0 : 2 * q, 2 * q + 1);
+            h.stats.t_np_lowrank_ms += ms(2 * q + 1, 2 * q + 2);
+        }
+        const size_t k0 = 2 * npass + 1;
+        h.stats.t_np_near_ms += ms(k0, k0 + 1);
+        h.stats.t_mvp_ms += ms(0, pe.size() - 1);
+        h.stats.mvp_count += 1;
+        for (cudaEvent_t e : pe) cudaEventDestroy(e);
+        rank_stats(h);      // the ACA work of this product (ranks, evaluations, flops)
+    }
     if (ev) {
         HM_CUDA(cudaEventRecord(ev, hs));
         HM_CUDA(cudaStreamWaitEvent(s, ev, 0));
@@ -957,6 +999,7 @@ void build_sets(hm_handle_s& h, int nsets, const double* points_all, const int64
         st.precision = h.precision;
         st.near_format = h.near_format;
         st.aca_passes = (int)h.np_pass.size() - 1;
+        st.near_entries = h.lists.near_elems;   // evaluated in every product
         st.t_total_ms =
             std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         return;

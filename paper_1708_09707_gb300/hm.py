@@ -58,7 +58,9 @@ class Stats(C.Structure):
                 ("t_mvp_ms", C.c_double), ("t_mvp_gather_ms", C.c_double),
                 ("t_mvp_vtx_ms", C.c_double), ("t_mvp_tile_ms", C.c_double),
                 ("mvp_vtx_bytes", C.c_int64), ("mvp_tile_bytes", C.c_int64),
-                ("t_aca_class_ms", C.c_double * 12)]
+                ("t_aca_class_ms", C.c_double * 12),
+                ("t_np_aca_ms", C.c_double), ("t_np_lowrank_ms", C.c_double),
+                ("t_np_near_ms", C.c_double)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

@@ -36,7 +36,7 @@ def test_options_and_stats_layout():
     # struct sizes match the C layout (offsets are natural alignment)
     assert ctypes.sizeof(hm.Options) == 80
     assert ctypes.sizeof(hm.Stats) == (8 * 5 + 4 * 2 + 8 + 8 + 8 * 9 + 8 * 4 + 4 * 3 + 4
-                                       + 8 + 8 + 8 + 8 * 4 + 8 * 2 + 8 * 12)
+                                       + 8 + 8 + 8 + 8 * 4 + 8 * 2 + 8 * 12 + 8 * 3)
 
 
 def test_library_is_not_a_cpu_fallback():

@@ -51,7 +51,9 @@ def test_fp64_matches_oracle_and_stored(hm, orc, case):
     assert rel(y, S.matvec(x)) <= 1e-13
     assert np.array_equal(H.matvec(x), y)
     st = H.stats()
-    assert st["factor_entries"] == 0 and st["near_entries"] == 0
+    # nothing stored; the dense entries are evaluated in every product
+    assert st["factor_entries"] == 0 and st["factor_bytes"] == 0 and st["near_bytes"] == 0
+    assert st["near_entries"] == S.stats()["near_entries"]
     assert np.array_equal(H.structure()["adm"], S.structure()["adm"])
 
 
@@ -128,3 +130,28 @@ def test_cg_with_on_the_fly_products(hm, orc):
     assert rel(H.matvec(x), b) <= 2e-8
     with pytest.raises(hm.HMError):
         H.factors(0, 32, 32)
+
+
+def test_profiled_phases(hm):
+    """profile = 1 on an on-the-fly handle: per-phase CUDA-event times summed
+    over the products since the last hm_get_stats, the ACA work of one product
+    counted, and the product unchanged by the profiling."""
+    pts = _pts(8000, 2, "m", 21)
+    x = inputs.normal_vector(8000, 22)
+    P = hm.HMatrix(pts, 0, 0.1, 64, 1.0, 1e-6, precision=hm.PREC_MIXED, on_the_fly=True,
+                   profile=True, scratch_gb=0.01)
+    Q = hm.HMatrix(pts, 0, 0.1, 64, 1.0, 1e-6, precision=hm.PREC_MIXED, on_the_fly=True,
+                   scratch_gb=0.01)
+    y = P.matvec(x)
+    P.matvec(x)
+    assert np.array_equal(y, Q.matvec(x))
+    st = P.stats()
+    assert st["mvp_count"] == 2 and st["aca_passes"] > 1
+    parts = st["t_np_aca_ms"] + st["t_np_lowrank_ms"] + st["t_np_near_ms"]
+    assert min(st["t_np_aca_ms"], st["t_np_lowrank_ms"], st["t_np_near_ms"]) > 0
+    # disjoint intervals inside the product (event times have about 0.5 us resolution)
+    assert parts <= st["t_mvp_ms"] * 1.01 + 0.1
+    assert st["aca_evals"] > 0 and st["aca_flops"] > 0 and st["sum_rank"] > 0
+    assert st["near_entries"] > 0
+    # the sums restart after hm_get_stats
+    assert P.stats()["mvp_count"] == 0
