@@ -1086,12 +1086,6 @@ __device__ __noinline__ BRed<T> big_reduce(CL& cl, int CS, BigShared<T, NT / 32>
     return t;
 }
 
-// Loads: a thread reads the entries (u_l)_i of the rows it owns and (v_l)_j of
-// the columns it owns, which it wrote itself, through L1 (__ldca: a thread's
-// own stores are visible to its later loads on the same SM, and no other
-// thread writes those entries); entries written by other threads or other
-// CTAs of the cluster (the pivot row's u, the pivot column's v) bypass L1
-// (__ldcg), since L1 is not coherent across SMs.
 template <class T, int KERN, int R, int NT>
 __global__ void __launch_bounds__(NT, 512 / NT)
 k_aca_big(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restrict__ order,
@@ -1181,7 +1175,7 @@ k_aca_big(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restrict
                     T u[LC];
 #pragma unroll
                     for (int e = 0; e < LC; ++e)
-                        u[e] = (i < m && l0 + e < r) ? __ldca(U + (int64_t)(l0 + e) * m + i) : T(0);
+                        u[e] = (i < m && l0 + e < r) ? __ldcg(U + (int64_t)(l0 + e) * m + i) : T(0);
 #pragma unroll
                     for (int e = 0; e < LC; ++e) p[e] = fma(uh[q], u[e], p[e]);
 #pragma unroll
@@ -1272,7 +1266,7 @@ k_aca_big(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restrict
                     T v[LC];
 #pragma unroll
                     for (int e = 0; e < LC; ++e)
-                        v[e] = (jj < n && l0 + e < r) ? __ldca(V + (int64_t)(l0 + e) * n + jj) : T(0);
+                        v[e] = (jj < n && l0 + e < r) ? __ldcg(V + (int64_t)(l0 + e) * n + jj) : T(0);
 #pragma unroll
                     for (int e = 0; e < LC; ++e) p[e] = fma(uh[q], v[e], p[e]);
 #pragma unroll
@@ -1363,7 +1357,7 @@ k_aca_big(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restrict
                         T v[LC];
 #pragma unroll
                         for (int e = 0; e < LC; ++e)
-                            v[e] = (jj < n && l0 + e < r) ? __ldca(V + (int64_t)(l0 + e) * n + jj) : T(0);
+                            v[e] = (jj < n && l0 + e < r) ? __ldcg(V + (int64_t)(l0 + e) * n + jj) : T(0);
 #pragma unroll
                         for (int e = 0; e < LC; ++e) uh[q] = fma(-su[e], v[e], uh[q]);
                     }
