@@ -839,7 +839,7 @@ def main():
             ev[0].record(stream)
             Ho = hm.HMatrix(po, wo["kernel"], wo["ell"], wo["leaf"], wo["eta"], wo["eps"],
                             precision=hm.PREC_MIXED, on_the_fly=True, profile=True,
-                            adm_max=(wo["adm"] == "max"))
+                            symmetric=(args.symmetric == "on"), adm_max=(wo["adm"] == "max"))
             ev[1].record(stream)
             torch.cuda.nvtx.range_push("on_the_fly_" + wname)
             for _ in range(reps):
@@ -849,6 +849,7 @@ def main():
             torch.cuda.synchronize()
             so = Ho.stats()
             otf.append({"workload": wname, "n": wo["n"], "precision": "mixed",
+                        "symmetric": args.symmetric == "on",
                         "build_s": ev[0].elapsed_time(ev[1]) / 1e3,
                         "mvp_ms": ev[1].elapsed_time(ev[2]) / reps,
                         "aca_passes_per_product": so["aca_passes"], "n_adm": so["n_adm"],

@@ -104,9 +104,12 @@ typedef struct hm_options {
                              and evaluates the dense leaves inside the product
                              (the paper's non-precomputed mode, Sec. 5.4).
                              For point sets whose stored H-matrix does not fit
-                             the GPU. Not with symmetric, rank_model or
-                             hm_build_batch; several right-hand sides run one
-                             product each. Default 0. */
+                             the GPU. With symmetric, a pass compresses the
+                             canonical leaves of its range and applies them
+                             and their mirror leaves (its row sums then depend
+                             on the pass count to rounding). Not with
+                             rank_model or hm_build_batch; several right-hand
+                             sides run one product each. Default 0. */
 } hm_options;
 
 typedef struct hm_handle_s* hm_handle;

@@ -246,14 +246,28 @@ void np_gather_x(int precision, const double* x, const int64_t* perm, int64_t N,
 void np_lists(const Blk* ablk, int64_t n_adm, const int64_t* lr_ptr, int64_t n_tiles,
               DevBuf<int64_t>& vptr, DevBuf<int2>& vitems, DevBuf<int64_t>& aptr,
               DevBuf<int3>& aitems, std::vector<int64_t>& h_vptr, int64_t& n_aitems, cudaStream_t s);
+// The lists of one pass q of a symmetric on-the-fly handle: its blocks are
+// pblk[b0 .. b1), their V^T x items pitems[vi0 .. vi1) (block b's first at
+// pfirst[b] within the pass), passid / tidx every leaf's pass and place.
+struct NpSymPass {
+    const int64_t* pitems = nullptr;
+    const int64_t* pblk = nullptr;
+    const int64_t* pfirst = nullptr;
+    const int32_t* passid = nullptr;
+    const int32_t* tidx = nullptr;
+    int q = 0;
+};
 // For the admissible leaves b0 <= b < b1 (factors as left by ACA):
 // t_b = V_b^T x|sigma (items vi0 .. vi1 - 1, partials in tp, sums in t), then
-// every apply item's running row sums += U_b t_b in block order.
+// every apply item's running row sums += U_b t_b in block order. With sym the
+// blocks and items are those of the pass's lists (see NpSymPass) and the
+// apply takes the entries of the pass's leaves in entry order.
 void np_lowrank(int precision, const Blk* ablk, const int32_t* rank, const uint64_t* Uptr,
                 const uint64_t* Vptr, int64_t b0, int64_t b1, const int64_t* vptr,
                 const int2* vitems, int64_t vi0, int64_t vi1, const int3* aitems,
                 int64_t n_aitems, const int2* lr_ent, const int32_t* tile_m, const void* xm,
-                void* tp, void* t, int kcap, int ld, double* item_acc, cudaStream_t s);
+                void* tp, void* t, int kcap, int ld, double* item_acc, cudaStream_t s,
+                const NpSymPass* sym = nullptr);
 // y_m += the apply items' row sums of every tile, in item order.
 void np_apply_finish(const int64_t* aptr, const int64_t* tile_row0, const int32_t* tile_m,
                      int64_t n_tiles, int ld, const double* item_acc, double* yacc, cudaStream_t s);

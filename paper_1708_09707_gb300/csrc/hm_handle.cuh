@@ -79,6 +79,14 @@ struct hm_handle_s {
     int64_t np_naitems = 0;
     hm::DevBuf<char> np_tp;
     hm::DevBuf<double> np_acc;
+    // symmetric on-the-fly handles: pass q compresses the canonical leaves of
+    // its block range (np_ids[np_cptr[q] ..)) and applies them and their
+    // mirror leaves; np_passid / np_tidx give every leaf its pass and its
+    // place in the pass's block list np_pblk[np_pbptr[q] ..), whose V^T x
+    // items are np_pitems[np_piptr[q] ..) (leaf b's first at np_pfirst[b])
+    std::vector<int64_t> np_cptr, np_pbptr, np_piptr;
+    hm::DevBuf<int32_t> np_passid, np_tidx;
+    hm::DevBuf<int64_t> np_pblk, np_pfirst, np_pitems;
     hm::DevBuf<int> status;
     hm_stats stats{};
     ~hm_handle_s();

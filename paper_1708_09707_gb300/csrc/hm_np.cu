@@ -71,16 +71,17 @@ __global__ void k_np_aemit(const int64_t* __restrict__ lr_ptr, int64_t nt,
 // j sums the columns j, j + 32, ... of the item's chunk for every factor row
 // l, the lane sums meet in the xor butterfly; partial (item, l) goes to
 // tp[(item - vi0) kcap + l].
+// With pidx (symmetric handles) the pass's items are items[pidx[vi0 + w]].
 template <class R>
 __global__ void k_np_vtx(const Blk* __restrict__ blk, const int32_t* __restrict__ rank,
                          const uint64_t* __restrict__ Vptr, const int2* __restrict__ items,
-                         int64_t vi0, int64_t ni, const R* __restrict__ xm, R* __restrict__ tp,
-                         int kcap)
+                         const int64_t* __restrict__ pidx, int64_t vi0, int64_t ni,
+                         const R* __restrict__ xm, R* __restrict__ tp, int kcap)
 {
     const int64_t w = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (w >= ni) return;
-    const int2 it = items[vi0 + w];
+    const int2 it = items[pidx ? pidx[vi0 + w] : vi0 + w];
     const Blk B = blk[it.x];
     const int k = rank[it.x];
     const int n = B.n, c0 = it.y;
@@ -107,18 +108,21 @@ __global__ void k_np_vtx(const Blk* __restrict__ blk, const int32_t* __restrict_
 }
 
 // t_b = sum of its items' partials in item order, for the blocks b0 .. b0 +
-// nb - 1 (one warp per block); t_b starts at t + (b - b0) kcap.
+// nb - 1 (one warp per block); t_b starts at t + (b - b0) kcap. With pblk
+// (symmetric handles) the blocks are pblk[b0 + w] and the first partial of
+// block b is pfirst[b].
 template <class R>
-__global__ void k_np_tsum(const int64_t* __restrict__ vptr, int64_t b0, int64_t nb,
+__global__ void k_np_tsum(const int64_t* __restrict__ vptr, const int64_t* __restrict__ pblk,
+                          const int64_t* __restrict__ pfirst, int64_t b0, int64_t nb,
                           const int32_t* __restrict__ rank, int64_t vi0, const R* __restrict__ tp,
                           R* __restrict__ t, int kcap)
 {
     const int64_t w = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (w >= nb) return;
-    const int64_t b = b0 + w;
+    const int64_t b = pblk ? pblk[b0 + w] : b0 + w;
     const int k = rank[b];
-    const int64_t f = vptr[b] - vi0, c = vptr[b + 1] - vptr[b];
+    const int64_t f = pblk ? pfirst[b] : vptr[b] - vi0, c = vptr[b + 1] - vptr[b];
     for (int l = lane; l < k; l += 32) {
         R s = R(0);
         for (int64_t q = 0; q < c; ++q) s += tp[(f + q) * kcap + l];
@@ -154,6 +158,42 @@ __global__ void k_np_apply(const int3* __restrict__ items, int64_t n_items,
             const int m = blk[en.x].m;
             const R* __restrict__ U = reinterpret_cast<const R*>(Uptr[en.x]) + en.y + i;
             const R* __restrict__ tb = t + (int64_t)(en.x - b0) * kcap;
+            R c = R(0);
+            for (int l = 0; l < k; ++l) c = fma(U[(int64_t)l * m], tb[l], c);
+            v += (double)c;
+        }
+        item_acc[w * ld + i] = v;
+    }
+}
+
+// Symmetric handles: U_b t_b over the entries of every apply item whose leaf
+// is in pass q (canonical leaves of the pass and their mirror leaves, whose
+// U is the partner's V), in entry order; t_b at t + tidx[b] kcap.
+template <class R>
+__global__ void k_np_apply_sym(const int3* __restrict__ items, int64_t n_items,
+                               const int2* __restrict__ lr_ent, const Blk* __restrict__ blk,
+                               const int32_t* __restrict__ rank, const uint64_t* __restrict__ Uptr,
+                               const int32_t* __restrict__ tile_m, const int32_t* __restrict__ passid,
+                               const int32_t* __restrict__ tidx, int q, const R* __restrict__ t,
+                               int kcap, int ld, double* __restrict__ item_acc)
+{
+    const int64_t w = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= n_items) return;
+    const int3 it = items[w];
+    bool any = false;
+    for (int e = it.y; e < it.z; ++e) any |= passid[lr_ent[e].x] == q;
+    if (!any) return;
+    const int mt = tile_m[it.x];
+    for (int i = lane; i < mt; i += 32) {
+        double v = item_acc[w * ld + i];
+        for (int e = it.y; e < it.z; ++e) {
+            const int2 en = lr_ent[e];
+            if (passid[en.x] != q) continue;
+            const int k = rank[en.x];
+            const int m = blk[en.x].m;
+            const R* __restrict__ U = reinterpret_cast<const R*>(Uptr[en.x]) + en.y + i;
+            const R* __restrict__ tb = t + (int64_t)tidx[en.x] * kcap;
             R c = R(0);
             for (int l = 0; l < k; ++l) c = fma(U[(int64_t)l * m], tb[l], c);
             v += (double)c;
@@ -349,45 +389,60 @@ void np_lists(const Blk* ablk, int64_t n_adm, const int64_t* lr_ptr, int64_t n_t
     HM_CUDA(cudaStreamSynchronize(s));
 }
 
+namespace {
+
+template <class R>
+void lowrank_typed(const Blk* ablk, const int32_t* rank, const uint64_t* Uptr,
+                   const uint64_t* Vptr, int64_t b0, int64_t b1, const int64_t* vptr,
+                   const int2* vitems, int64_t vi0, int64_t vi1, const int3* aitems,
+                   int64_t n_aitems, const int2* lr_ent, const int32_t* tile_m, const R* x,
+                   R* p, R* tt, int kcap, int ld, double* item_acc, const NpSymPass* sym,
+                   cudaStream_t s)
+{
+    const int64_t nb = b1 - b0, ni = vi1 - vi0;
+    if (ni > 0) {
+        k_np_vtx<R><<<grid_for(ni * 32), NT, 0, s>>>(ablk, rank, Vptr, vitems,
+                                                    sym ? sym->pitems : nullptr, vi0, ni, x, p,
+                                                    kcap);
+        note_launch();
+    }
+    k_np_tsum<R><<<grid_for(nb * 32), NT, 0, s>>>(vptr, sym ? sym->pblk : nullptr,
+                                                  sym ? sym->pfirst : nullptr, b0, nb, rank, vi0,
+                                                  p, tt, kcap);
+    note_launch();
+    if (n_aitems > 0) {
+        if (sym)
+            k_np_apply_sym<R><<<grid_for(n_aitems * 32), NT, 0, s>>>(
+                aitems, n_aitems, lr_ent, ablk, rank, Uptr, tile_m, sym->passid, sym->tidx,
+                sym->q, tt, kcap, ld, item_acc);
+        else
+            k_np_apply<R><<<grid_for(n_aitems * 32), NT, 0, s>>>(
+                aitems, n_aitems, lr_ent, ablk, rank, Uptr, tile_m, b0, b1, tt, kcap, ld,
+                item_acc);
+        note_launch();
+    }
+}
+
+}  // namespace
+
 void np_lowrank(int precision, const Blk* ablk, const int32_t* rank, const uint64_t* Uptr,
                 const uint64_t* Vptr, int64_t b0, int64_t b1, const int64_t* vptr,
                 const int2* vitems, int64_t vi0, int64_t vi1, const int3* aitems,
                 int64_t n_aitems, const int2* lr_ent, const int32_t* tile_m, const void* xm,
-                void* tp, void* t, int kcap, int ld, double* item_acc, cudaStream_t s)
+                void* tp, void* t, int kcap, int ld, double* item_acc, cudaStream_t s,
+                const NpSymPass* sym)
 {
-    const int64_t nb = b1 - b0, ni = vi1 - vi0;
-    if (nb <= 0) return;
-    if (precision == HM_PREC_FP64) {
-        const double* x = static_cast<const double*>(xm);
-        double* p = static_cast<double*>(tp);
-        double* tt = static_cast<double*>(t);
-        if (ni > 0) {
-            k_np_vtx<double><<<grid_for(ni * 32), NT, 0, s>>>(ablk, rank, Vptr, vitems, vi0, ni, x, p, kcap);
-            note_launch();
-        }
-        k_np_tsum<double><<<grid_for(nb * 32), NT, 0, s>>>(vptr, b0, nb, rank, vi0, p, tt, kcap);
-        note_launch();
-        if (n_aitems > 0) {
-            k_np_apply<double><<<grid_for(n_aitems * 32), NT, 0, s>>>(
-                aitems, n_aitems, lr_ent, ablk, rank, Uptr, tile_m, b0, b1, tt, kcap, ld, item_acc);
-            note_launch();
-        }
-    } else {
-        const float* x = static_cast<const float*>(xm);
-        float* p = static_cast<float*>(tp);
-        float* tt = static_cast<float*>(t);
-        if (ni > 0) {
-            k_np_vtx<float><<<grid_for(ni * 32), NT, 0, s>>>(ablk, rank, Vptr, vitems, vi0, ni, x, p, kcap);
-            note_launch();
-        }
-        k_np_tsum<float><<<grid_for(nb * 32), NT, 0, s>>>(vptr, b0, nb, rank, vi0, p, tt, kcap);
-        note_launch();
-        if (n_aitems > 0) {
-            k_np_apply<float><<<grid_for(n_aitems * 32), NT, 0, s>>>(
-                aitems, n_aitems, lr_ent, ablk, rank, Uptr, tile_m, b0, b1, tt, kcap, ld, item_acc);
-            note_launch();
-        }
-    }
+    if (b1 - b0 <= 0) return;
+    if (precision == HM_PREC_FP64)
+        lowrank_typed<double>(ablk, rank, Uptr, Vptr, b0, b1, vptr, vitems, vi0, vi1, aitems,
+                              n_aitems, lr_ent, tile_m, static_cast<const double*>(xm),
+                              static_cast<double*>(tp), static_cast<double*>(t), kcap, ld,
+                              item_acc, sym, s);
+    else
+        lowrank_typed<float>(ablk, rank, Uptr, Vptr, b0, b1, vptr, vitems, vi0, vi1, aitems,
+                             n_aitems, lr_ent, tile_m, static_cast<const float*>(xm),
+                             static_cast<float*>(tp), static_cast<float*>(t), kcap, ld,
+                             item_acc, sym, s);
     HM_LAUNCH("np low-rank part");
 }
 

@@ -159,6 +159,35 @@ __global__ void k_mirror(const Blk* __restrict__ blk, int64_t n, uint64_t* __res
     flags[b] = MIRROR_FLAG;
 }
 
+// The canonical partner of every admissible leaf: itself when row0 <= col0,
+// else the leaf (tau, sigma) of the mirror leaf (sigma, tau), found by binary
+// search as in k_mirror; -1 (and the status word) if missing.
+__global__ void k_np_partner(const Blk* __restrict__ blk, int64_t n, int64_t* __restrict__ partner,
+                             int* status)
+{
+    int64_t b = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (b >= n) return;
+    const Blk B = blk[b];
+    if (B.row0 <= B.col0) {
+        partner[b] = b;
+        return;
+    }
+    int64_t lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        const Blk M = blk[mid];
+        if (M.row0 < B.col0 || (M.row0 == B.col0 && M.col0 < B.row0)) lo = mid + 1;
+        else hi = mid;
+    }
+    const Blk M = blk[lo];
+    if (M.row0 != B.col0 || M.col0 != B.row0) {
+        atomicOr(status, 8);
+        partner[b] = -1;
+        return;
+    }
+    partner[b] = lo;
+}
+
 // Reserved entries of block order[q]: total kres (m + n) and the U part kres m.
 __global__ void k_reserve(const Blk* __restrict__ blk, const uint32_t* __restrict__ order,
                           int64_t n, const int32_t* __restrict__ kres, int64_t* __restrict__ res,
@@ -598,6 +627,7 @@ void np_prepare(hm_handle_s& h)
     h.np_pass.assign(1, 0);
     h.np_ids.alloc(std::max<int64_t>(n, 1), s);
     int64_t cap = 1, most = 1;
+    std::vector<int64_t> partner;   // symmetric: canonical partner of every leaf
     if (n > 0) {
         k_iota_u32<<<grid_for(n), NT, 0, s>>>(h.np_ids.p, n); note_launch();
         DevBuf<int64_t> res(n, s);
@@ -606,6 +636,19 @@ void np_prepare(hm_handle_s& h)
         std::vector<int64_t> hr(n);
         HM_CUDA(cudaMemcpyAsync(hr.data(), res.p, n * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         HM_CUDA(cudaStreamSynchronize(s));
+        if (h.opt.symmetric) {
+            // mirror leaves reserve nothing: they take their partner's factors
+            DevBuf<int64_t> dp(n, s);
+            k_np_partner<<<grid_for(n), NT, 0, s>>>(h.ablk.p, n, dp.p, h.status.p); note_launch();
+            HM_LAUNCH("np partners");
+            partner.resize(n);
+            HM_CUDA(cudaMemcpyAsync(partner.data(), dp.p, n * sizeof(int64_t),
+                                    cudaMemcpyDeviceToHost, s));
+            HM_CUDA(cudaStreamSynchronize(s));
+            check_status(h);
+            for (int64_t b = 0; b < n; ++b)
+                if (partner[b] != b) hr[b] = 0;
+        }
         int64_t total = 0, maxres = 0;
         for (int64_t b = 0; b < n; ++b) {
             total += hr[b];
@@ -627,7 +670,6 @@ void np_prepare(hm_handle_s& h)
     }
     h.np_kcap = std::max(h.opt.k_cap, 1);
     h.np_scratch.alloc((size_t)cap * esz, s);
-    h.np_t.alloc((size_t)most * h.np_kcap * esz, s);
     h.np_xm.alloc((size_t)std::max<int64_t>(h.Ntot, 1) * esz, s);
     h.np_yacc.alloc(std::max<int64_t>(h.Ntot, 1), s);
     h.np_ld = std::max(h.leaf, 1);
@@ -635,8 +677,64 @@ void np_prepare(hm_handle_s& h)
     np_lists(h.ablk.p, n, h.lists.lr_ptr.p, h.n_tiles, h.np_vptr, h.np_vitems, h.np_aptr,
              h.np_aitems, h.np_hvptr, h.np_naitems, s);
     int64_t most_items = 1;
-    for (size_t q = 0; q + 1 < h.np_pass.size(); ++q)
-        most_items = std::max(most_items, h.np_hvptr[h.np_pass[q + 1]] - h.np_hvptr[h.np_pass[q]]);
+    if (h.opt.symmetric && n > 0) {
+        // pass q: the canonical leaves of its block range and their mirrors
+        const int64_t P = (int64_t)h.np_pass.size() - 1;
+        std::vector<int32_t> pid(n), tix(n);
+        for (int64_t q = 0; q < P; ++q)
+            for (int64_t b = h.np_pass[q]; b < h.np_pass[q + 1]; ++b)
+                if (partner[b] == b) pid[b] = (int32_t)q;
+        std::vector<uint32_t> cids;
+        h.np_cptr.assign(P + 1, 0);
+        for (int64_t q = 0; q < P; ++q) {
+            h.np_cptr[q] = (int64_t)cids.size();
+            for (int64_t b = h.np_pass[q]; b < h.np_pass[q + 1]; ++b)
+                if (partner[b] == b) cids.push_back((uint32_t)b);
+        }
+        h.np_cptr[P] = (int64_t)cids.size();
+        for (int64_t b = 0; b < n; ++b)
+            if (partner[b] != b) pid[b] = pid[partner[b]];
+        h.np_pbptr.assign(P + 1, 0);
+        for (int64_t b = 0; b < n; ++b) ++h.np_pbptr[pid[b] + 1];
+        for (int64_t q = 0; q < P; ++q) h.np_pbptr[q + 1] += h.np_pbptr[q];
+        std::vector<int64_t> pblk(n), fill(h.np_pbptr.begin(), h.np_pbptr.end() - 1);
+        for (int64_t b = 0; b < n; ++b) {
+            const int64_t at = fill[pid[b]]++;
+            pblk[at] = b;
+            tix[b] = (int32_t)(at - h.np_pbptr[pid[b]]);
+        }
+        std::vector<int64_t> pitems, pfirst(n, 0);
+        pitems.reserve(h.np_hvptr[n]);
+        h.np_piptr.assign(P + 1, 0);
+        most = 1;
+        for (int64_t q = 0; q < P; ++q) {
+            h.np_piptr[q] = (int64_t)pitems.size();
+            for (int64_t at = h.np_pbptr[q]; at < h.np_pbptr[q + 1]; ++at) {
+                const int64_t b = pblk[at];
+                pfirst[b] = (int64_t)pitems.size() - h.np_piptr[q];
+                for (int64_t it = h.np_hvptr[b]; it < h.np_hvptr[b + 1]; ++it) pitems.push_back(it);
+            }
+            most = std::max(most, h.np_pbptr[q + 1] - h.np_pbptr[q]);
+            most_items = std::max(most_items, (int64_t)pitems.size() - h.np_piptr[q]);
+        }
+        h.np_piptr[P] = (int64_t)pitems.size();
+        copy_in(h.np_ids.p, cids.data(), cids.size() * sizeof(uint32_t), s);
+        h.np_passid.alloc(n, s);
+        h.np_tidx.alloc(n, s);
+        h.np_pblk.alloc(n, s);
+        h.np_pfirst.alloc(n, s);
+        h.np_pitems.alloc(std::max<size_t>(pitems.size(), 1), s);
+        copy_in(h.np_passid.p, pid.data(), n * sizeof(int32_t), s);
+        copy_in(h.np_tidx.p, tix.data(), n * sizeof(int32_t), s);
+        copy_in(h.np_pblk.p, pblk.data(), n * sizeof(int64_t), s);
+        copy_in(h.np_pfirst.p, pfirst.data(), n * sizeof(int64_t), s);
+        copy_in(h.np_pitems.p, pitems.data(), pitems.size() * sizeof(int64_t), s);
+        HM_CUDA(cudaStreamSynchronize(s));
+    } else {
+        for (size_t q = 0; q + 1 < h.np_pass.size(); ++q)
+            most_items = std::max(most_items, h.np_hvptr[h.np_pass[q + 1]] - h.np_hvptr[h.np_pass[q]]);
+    }
+    h.np_t.alloc((size_t)most * h.np_kcap * esz, s);
     h.np_tp.alloc((size_t)most_items * h.np_kcap * esz, s);
     h.np_acc.alloc((size_t)std::max<int64_t>(h.np_naitems, 1) * h.np_ld, s);
     HM_CUDA(cudaStreamSynchronize(s));
@@ -679,20 +777,50 @@ void np_matvec(hm_handle_s& h, const double* x, double* y, int accumulate, cudaS
         pe.push_back(e);
     };
     mark();
+    const bool sym = h.opt.symmetric;
     for (size_t q = 0; q < npass; ++q) {
-        const int64_t b0 = h.np_pass[q], b1 = h.np_pass[q + 1], nb = b1 - b0;
-        AcaOrder O;
-        aca_order(h, h.np_ids.p + b0, nb, nullptr, O);
-        char* vbase = h.np_scratch.p + O.hpreu[nb] * esz;
-        k_set_ptrs<<<grid_for(nb), NT, 0, hs>>>(O.order.p, 0, nb, O.pre.p, O.preu.p,
-                                                 h.np_scratch.p, vbase, esz, h.Uptr.p, h.Vptr.p); note_launch();
-        HM_LAUNCH("set ptrs");
-        aca_range(h, O, a, 0, nb);
+        // the leaves compressed in this pass: its block range, or only the
+        // canonical ones of it (symmetric)
+        const int64_t c0 = sym ? h.np_cptr[q] : h.np_pass[q];
+        const int64_t nb = (sym ? h.np_cptr[q + 1] : h.np_pass[q + 1]) - c0;
+        if (nb > 0) {
+            AcaOrder O;
+            aca_order(h, h.np_ids.p + c0, nb, nullptr, O);
+            char* vbase = h.np_scratch.p + O.hpreu[nb] * esz;
+            k_set_ptrs<<<grid_for(nb), NT, 0, hs>>>(O.order.p, 0, nb, O.pre.p, O.preu.p,
+                                                     h.np_scratch.p, vbase, esz, h.Uptr.p, h.Vptr.p); note_launch();
+            HM_LAUNCH("set ptrs");
+            aca_range(h, O, a, 0, nb);
+        }
+        if (sym) {
+            // mirror leaves take their partners' factors (those of this pass
+            // are applied now; the others are reset in their partners' pass)
+            k_mirror<<<grid_for(h.n_adm), NT, 0, hs>>>(h.ablk.p, h.n_adm, h.Uptr.p, h.Vptr.p,
+                                                       h.rank.p, h.nrej.p, h.flags.p,
+                                                       h.status.p); note_launch();
+            HM_LAUNCH("np mirror leaves");
+        }
         mark();
-        np_lowrank(h.precision, h.ablk.p, h.rank.p, h.Uptr.p, h.Vptr.p, b0, b1, h.np_vptr.p,
-                   h.np_vitems.p, h.np_hvptr[b0], h.np_hvptr[b1], h.np_aitems.p, h.np_naitems,
-                   h.lists.lr_ent.p, h.tile_m.p, h.np_xm.p, h.np_tp.p, h.np_t.p, h.np_kcap,
-                   h.np_ld, h.np_acc.p, hs);
+        if (sym) {
+            NpSymPass sp;
+            sp.pitems = h.np_pitems.p;
+            sp.pblk = h.np_pblk.p;
+            sp.pfirst = h.np_pfirst.p;
+            sp.passid = h.np_passid.p;
+            sp.tidx = h.np_tidx.p;
+            sp.q = (int)q;
+            np_lowrank(h.precision, h.ablk.p, h.rank.p, h.Uptr.p, h.Vptr.p, h.np_pbptr[q],
+                       h.np_pbptr[q + 1], h.np_vptr.p, h.np_vitems.p, h.np_piptr[q],
+                       h.np_piptr[q + 1], h.np_aitems.p, h.np_naitems, h.lists.lr_ent.p,
+                       h.tile_m.p, h.np_xm.p, h.np_tp.p, h.np_t.p, h.np_kcap, h.np_ld,
+                       h.np_acc.p, hs, &sp);
+        } else {
+            const int64_t b0 = h.np_pass[q], b1 = h.np_pass[q + 1];
+            np_lowrank(h.precision, h.ablk.p, h.rank.p, h.Uptr.p, h.Vptr.p, b0, b1, h.np_vptr.p,
+                       h.np_vitems.p, h.np_hvptr[b0], h.np_hvptr[b1], h.np_aitems.p,
+                       h.np_naitems, h.lists.lr_ent.p, h.tile_m.p, h.np_xm.p, h.np_tp.p,
+                       h.np_t.p, h.np_kcap, h.np_ld, h.np_acc.p, hs);
+        }
         mark();
     }
     check_status(h);
@@ -788,8 +916,8 @@ void validate(int nsets, const int64_t* N, const int* d, int kernel, const doubl
         tot += N[q];
     }
     if (tot >= (1ll << 31)) fail(HM_EINVAL, "more than 2^31 points");
-    if (o.on_the_fly && (o.symmetric || o.rank_model || (nsets > 1 && !rect)))
-        fail(HM_ENOTSUP, "on_the_fly runs without symmetric, rank_model and batches");
+    if (o.on_the_fly && (o.rank_model || (nsets > 1 && !rect)))
+        fail(HM_ENOTSUP, "on_the_fly runs without rank_model and batches");
     if (rect) {
         if (nsets != 2) fail(HM_EINVAL, "a rectangular matrix takes two point sets");
         if (d[0] != d[1]) fail(HM_EINVAL, "both point sets need the same dimension");

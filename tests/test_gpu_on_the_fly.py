@@ -95,7 +95,7 @@ def test_mixed_matches_oracle_and_options(hm, orc):
 
 def test_refused_combinations(hm):
     pts = _pts(500, 2, "u", 41)
-    for kw in (dict(symmetric=True), dict(rank_model_theta=np.zeros(4801, np.float32))):
+    for kw in (dict(rank_model_theta=np.zeros(4801, np.float32)),):
         with pytest.raises(hm.HMError):
             hm.HMatrix(pts, 0, 0.1, 32, 1.0, 1e-6, precision=hm.PREC_MIXED, on_the_fly=True, **kw)
 
@@ -155,3 +155,41 @@ def test_profiled_phases(hm):
     assert st["near_entries"] > 0
     # the sums restart after hm_get_stats
     assert P.stats()["mvp_count"] == 0
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("case", [(6000, 2, "m", 0, 0.1, 64, 1.0), (5000, 3, "u", 1, 0.2, 32, 1.0)],
+                         ids=["mix2d", "matern3d"])
+def test_symmetric_on_the_fly(hm, orc, case, prec):
+    """Symmetric mode on the fly: each pass compresses the canonical leaves
+    (tau.lo <= sigma.lo) of its block range and applies them and their mirror
+    leaves (U and V exchanged); the product equals the stored symmetric one
+    and the oracle's mirrored H-matrix, with about half the ACA work of the
+    non-symmetric product."""
+    n, d, kind, kern, ell, leaf, eta = case
+    eps = 1e-8 if prec == 0 else 1e-6
+    pts = _pts(n, d, kind, 11)
+    x = inputs.normal_vector(n, inputs.X_SEED)
+    kw = dict(precision=prec, symmetric=True)
+    F = hm.HMatrix(pts, kern, ell, leaf, eta, eps, on_the_fly=True, profile=True,
+                   scratch_gb=0.004, **kw)
+    y = F.matvec(x)
+    sf = F.stats()
+    assert sf["aca_passes"] > 1
+    O = orc.HMatrix(pts, kern, ell, leaf, eta, eps, symmetric=True)
+    yo = O.matvec(x)
+    if prec == 0:
+        S = hm.HMatrix(pts, kern, ell, leaf, eta, eps, **kw)
+        assert rel(y, S.matvec(x)) <= 1e-13
+        assert rel(y, yo) <= FP64_TOL
+        # a different pass count changes the order of the row sums only
+        G = hm.HMatrix(pts, kern, ell, leaf, eta, eps, on_the_fly=True, scratch_gb=0.02, **kw)
+        assert rel(G.matvec(x), y) <= 1e-14
+    else:
+        assert rel(y, yo) <= MIXED_TOL
+    assert np.array_equal(F.matvec(x), y)
+    N = hm.HMatrix(pts, kern, ell, leaf, eta, eps, on_the_fly=True, profile=True,
+                   scratch_gb=0.004, precision=prec)
+    N.matvec(x)
+    sn = N.stats()
+    assert sf["aca_evals"] < 0.65 * sn["aca_evals"], (sf["aca_evals"], sn["aca_evals"])
