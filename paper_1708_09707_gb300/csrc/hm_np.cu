@@ -232,6 +232,26 @@ __global__ void k_np_apply_finish(const int64_t* __restrict__ aptr,
 constexpr int NN_W = 8;
 constexpr int NN_ROWS = 64;
 
+// A point held by lane src, to every lane of the warp.
+__device__ __forceinline__ Pt<double> shfl_pt(const Pt<double>& p, int src)
+{
+    Pt<double> o;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) o.x[i] = __shfl_sync(0xffffffffu, p.x[i], src);
+    return o;
+}
+
+__device__ __forceinline__ Pt<float> shfl_pt(const Pt<float>& p, int src)
+{
+    Pt<float> o;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        o.h[i] = __shfl_sync(0xffffffffu, p.h[i], src);
+        o.l[i] = __shfl_sync(0xffffffffu, p.l[i], src);
+    }
+    return o;
+}
+
 template <class R, int KERN>
 __global__ void __launch_bounds__(NN_W * 32)
 k_np_near(KernelParams kp, DeviceCoords X, const int3* __restrict__ items,
@@ -258,17 +278,31 @@ k_np_near(KernelParams kp, DeviceCoords X, const int3* __restrict__ items,
         Acc<R> aa, ab;
         R sa = R(0), sb = R(0);
         int cnt = 0;
-        for (int64_t col = cb + w; col < ce; col += NN_W) {
-            const int32_t q = ncol_x[nc0 + col];
-            const Pt<R> pq = load_pt<R>(X, q);
-            const R xq = xm[q];
-            sa = fma(phi<KERN>(dist2(pa, pq), c), xq, sa);
-            sb = fma(phi<KERN>(dist2(pb, pq), c), xq, sb);
-            if (++cnt == 16) {
-                aa.add(sa);
-                ab.add(sb);
-                sa = sb = R(0);
-                cnt = 0;
+        // the warp's columns w, w + NN_W, ... in batches of 32: lane L fetches
+        // column base + NN_W L (index, point, x) for the whole batch at once,
+        // then the batch is walked in column order with the column's point
+        // and x taken from its lane
+        for (int64_t base = cb + w; base < ce; base += (int64_t)NN_W * 32) {
+            const int64_t mycol = base + (int64_t)NN_W * lane;
+            Pt<R> pl = load_pt<R>(X, r0);          // any valid point for idle lanes
+            R xl = R(0);
+            if (mycol < ce) {
+                const int32_t q = ncol_x[nc0 + mycol];
+                pl = load_pt<R>(X, q);
+                xl = xm[q];
+            }
+            const int nt = (int)min((int64_t)32, (ce - base + NN_W - 1) / NN_W);
+            for (int t = 0; t < nt; ++t) {
+                const Pt<R> pq = shfl_pt(pl, t);
+                const R xq = __shfl_sync(0xffffffffu, xl, t);
+                sa = fma(phi<KERN>(dist2(pa, pq), c), xq, sa);
+                sb = fma(phi<KERN>(dist2(pb, pq), c), xq, sb);
+                if (++cnt == 16) {
+                    aa.add(sa);
+                    ab.add(sb);
+                    sa = sb = R(0);
+                    cnt = 0;
+                }
             }
         }
         aa.add(sa);
