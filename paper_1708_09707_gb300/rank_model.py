@@ -10,6 +10,7 @@ columns per block and re-runs the blocks whose prediction was too small.
 """
 from __future__ import annotations
 
+import json
 import time
 
 import numpy as np
@@ -116,3 +117,29 @@ def predict(theta, F):
 def reserved_rank(yhat):
     """Columns the build reserves for a prediction (before clamping)."""
     return np.maximum(np.ceil(1.25 * (np.exp2(np.minimum(yhat, 8.0)) - 1.0) + 2.0), 1.0)
+
+
+LAYOUT = "W1 (64 x 8), b1 (64), W2 (64 x 64), b2 (64), W3 (1 x 64), b3 (1); row-major, float32"
+
+
+def save(path, theta, meta=None) -> None:
+    """Write trained weights (the library's flat order, NPARAM float32 values)
+    and a JSON description (features, training sets, losses, ...) to an .npz
+    file, so that later builds reuse a model without training it again."""
+    theta = np.asarray(theta, np.float32).ravel()
+    if theta.size != NPARAM:
+        raise ValueError("theta has %d values, the model has %d" % (theta.size, NPARAM))
+    m = dict(meta or {})
+    m["nparam"] = NPARAM
+    m["layout"] = LAYOUT
+    np.savez(path, theta=theta, meta=np.frombuffer(json.dumps(m).encode(), np.uint8))
+
+
+def load(path):
+    """(theta, meta) written by save(); raises ValueError for another layout."""
+    with np.load(path) as z:
+        theta = np.array(z["theta"], np.float32)
+        meta = json.loads(bytes(z["meta"]).decode())
+    if theta.size != NPARAM or meta.get("nparam") != NPARAM or meta.get("layout") != LAYOUT:
+        raise ValueError("not a weight file of this model")
+    return theta, meta
