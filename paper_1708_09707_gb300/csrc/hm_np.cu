@@ -7,7 +7,10 @@
 // Determinism: every row of y is one running sum in double, fed in a fixed
 // order: the admissible leaves of the row's tile in block order (the passes
 // take consecutive block ranges), then the near-field item sums of the tile
-// in item order, each summed in a fixed pattern of warps and columns.
+// in item order, each summed in a fixed pattern of warps and columns. In
+// symmetric mode a pass applies its canonical leaves and their mirror leaves,
+// which lie later in block order, so a row's leaves enter in (pass, block)
+// order: fixed for a given scratch size, equal to rounding across sizes.
 #include "hm_kernel_fn.cuh"
 #include "hm_stream.cuh"
 
