@@ -55,8 +55,8 @@ def parse():
                    help="comma-separated workloads of the on-the-fly measurement "
                         "(self = the bench workload at its size)")
     p.add_argument("--sweeps", action="store_true",
-                   help="instead of the step: the paper's experiments as curves (Sec. 6.3 "
-                        "convergence in k, Sec. 6.4 runtime against N), one JSON line")
+                   help="instead of the step: the paper's experiments as curves (Sec. 6.4 "
+                        "convergence in k, Sec. 6.5 runtime against N), one JSON line")
     p.add_argument("--no-rect", action="store_true",
                    help="skip the context run of A(Y1 x Y2) for two point sets")
     p.add_argument("--no-paper", action="store_true",
@@ -79,7 +79,7 @@ def parse():
     return p.parse_args()
 
 
-# The paper's own GPU numbers for its setting (Sec. 6.5: N = 2^19 Halton
+# The paper's own GPU numbers for its setting (Sec. 6.7: N = 2^19 Halton
 # points in 2-D, exp(-r^2), C_leaf = 2048, eta = 1.5, fixed ACA rank 16,
 # FP64, factors stored: "P" mode), on one Tesla P100. Context only.
 PAPER_P100 = {"build_s": 1.3, "mvp_s": 1.7, "hardware": "1x Tesla P100 SXM2, CUDA 8.0",
@@ -514,16 +514,16 @@ def _elapsed(fn, stream):
 def run_sweeps(args):
     """The paper's experiments on this GPU, FP64 as in the paper, Halton
     points in [0,1]^d, the unscaled kernels, C_leaf, eta and the fixed rank
-    of Sec. 6.3 to 6.4; points and x on the device, CUDA events.
-      convergence  Sec. 6.3: N = 32768, C_leaf 256, eta 1.5, e_rel of the
+    of Sec. 6.4 to 6.5; points and x on the device, CUDA events.
+      convergence  Sec. 6.4: N = 32768, C_leaf 256, eta 1.5, e_rel of the
                    fixed-rank-k product against the exact product (an eta = 0
                    build: every leaf dense), mean over three x
-      structure    Sec. 6.4, first figure: Morton codes + sort (the spatial
+      structure    Sec. 6.5, first figure: Morton codes + sort (the spatial
                    data structure) and the whole structure (codes, sort, tree,
                    boxes, Alg. 1 traversal) for N up to 2^26, C_leaf 2048;
                    uniform points here (the host makes 2^26 Halton points ten
                    times slower)
-      mvp          Sec. 6.4, second figure: product time with stored factors
+      mvp          Sec. 6.5, second figure: product time with stored factors
                    (P) and with factors recomputed per product (NP), C_leaf
                    2048, eta 1.5, k = 16"""
     import torch

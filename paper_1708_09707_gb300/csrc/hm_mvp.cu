@@ -349,10 +349,11 @@ k_tile_tma(MvpPlan P, const R* __restrict__ xm, const R* __restrict__ t, double*
                 mbar_arrive_tx(&full[slot], bytes);
                 bulk_copy(tsm + slot * STAGE, src, bytes, &full[slot]);
             }
-            if (k < nch) {
-                // gave up: let the copies already issued land before the CTA exits
-                for (int q = (k > TS ? k - TS : 0); q < k; ++q) mbar_wait(&full[q % TS], (q / TS) & 1);
-            }
+            // every copy issued lands before the CTA exits: only the last TS
+            // chunks issued can still be in flight, and a wait on a phase
+            // that has completed returns at once
+            for (int q = (k > TS ? k - TS : 0); q < k; ++q)
+                if (!mbar_wait(&full[q % TS], (q / TS) & 1)) atomicOr(P.status, 4);
         }
     } else {
         // ---------------- consumers: half-warp hw = 2w + (lane >> 4)
@@ -380,7 +381,9 @@ k_tile_tma(MvpPlan P, const R* __restrict__ xm, const R* __restrict__ t, double*
         for (int k = 0; k < nch; ++k) {
             const int slot = k % TS;
             const R mnext = fetch(k + 1);
-            if (!mbar_wait(&full[slot], (k / TS) & 1)) {
+            // the whole warp gives up together, so the shuffles below never
+            // name a lane that has left
+            if (!__all_sync(0xffffffffu, mbar_wait(&full[slot], (k / TS) & 1))) {
                 if (lane == 0) atomicOr(P.status, 4);
                 failed = 1;
                 break;

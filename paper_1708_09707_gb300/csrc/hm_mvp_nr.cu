@@ -349,11 +349,9 @@ k_tile_n(MvpPlan P, const float* __restrict__ xm, const float* __restrict__ t,
                 mbar_arrive_tx(&full[slot], bytes);
                 bulk_copy(tsm + slot * STAGE, src, bytes, &full[slot]);
             }
-            if (k < nch) {
-                // gave up: let the copies already issued land before the CTA exits
-                for (int q = (k > TN_STAGES ? k - TN_STAGES : 0); q < k; ++q)
-                    mbar_wait(&full[q % TN_STAGES], (q / TN_STAGES) & 1);
-            }
+            // every copy issued lands before the CTA exits (see k_tile_tma)
+            for (int q = (k > TN_STAGES ? k - TN_STAGES : 0); q < k; ++q)
+                if (!mbar_wait(&full[q % TN_STAGES], (q / TN_STAGES) & 1)) atomicOr(P.status, 4);
         }
     } else {
         // ---------------- consumers

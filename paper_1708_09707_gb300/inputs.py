@@ -156,7 +156,7 @@ WORKLOADS = {
     "matern3d_n4m_cg": dict(n=1 << 22, d=3, points="uniform", kernel=1,
                             ell=0.1, leaf=64, eta=1.0, adm="min",
                             eps=1e-6, sigma2=1e-2, seed=POINT_SEED + 5),
-    # the paper's own setting (Sec. 6.5): Halton points in [0,1]^2, the
+    # the paper's own setting (Sec. 6.7): Halton points in [0,1]^2, the
     # unscaled Gaussian exp(-r^2), C_leaf = 2048, eta = 1.5 and ACA of fixed
     # rank k = 16 without a stopping criterion (eps <= 0)
     "halton2d_n512k_k16": dict(n=1 << 19, d=2, points="halton", kernel=0,

@@ -20,7 +20,7 @@ CASES = {
     "u3d": (3000, 3, "u", 0.3, 32, 1.0, False, 1e-6),
     "mix2d": (3000, 2, "m", 0.1, 64, 1.0, False, 1e-6),  # clipped mixture: duplicates
     # the paper's setting scaled down: Halton points, unscaled kernel,
-    # eta = 1.5, fixed rank 16 (Sec. 6.5)
+    # eta = 1.5, fixed rank 16 (Sec. 6.7)
     "paper": (8192, 2, "h", 1.0, 128, 1.5, False, 0.0),
     "eta0": (1000, 2, "u", 0.2, 8, 0.0, False, 1e-6),    # every block dense
 }

@@ -68,7 +68,7 @@ CASES = [
     (1000, 2, "u", 0, 0.2, 8, 0.0, False, 1e-6),     # eta = 0: all dense
     (1500, 3, "u", 0, 0.5, 30, 1.5, False, 0.0),     # fixed-rank mode
     # the paper's setting scaled down: Halton points, unscaled Gaussian,
-    # eta = 1.5, fixed rank 16 (Sec. 6.5); tiles of 256 rows
+    # eta = 1.5, fixed rank 16 (Sec. 6.7); tiles of 256 rows
     (16384, 2, "h", 0, 1.0, 256, 1.5, False, 0.0),
 ]
 

@@ -85,7 +85,7 @@ def test_k1_hmatrix_eta0_is_exact(orc, d):
 
 @pytest.mark.parametrize("d,ell", [(2, 1.0), (3, 0.2)])
 def test_k1_hmatrix_error_within_eps(orc, d, ell):
-    # Sec. 6.3's setting (eta = 1.5) with the eps-adaptive ACA: the product's
+    # Sec. 6.4's setting (eta = 1.5) with the eps-adaptive ACA: the product's
     # error against brute force is of the order of eps
     n = 2048
     pts = inputs.halton_points(n, d) if d == 2 else inputs.uniform_points(n, d, 31)
@@ -97,7 +97,7 @@ def test_k1_hmatrix_error_within_eps(orc, d, ell):
 
 
 def test_k1_fixed_rank_converges_geometrically(orc):
-    # Sec. 6.3: e_rel of the product decays exponentially in the fixed ACA
+    # Sec. 6.4: e_rel of the product decays exponentially in the fixed ACA
     # rank k, for the Matern kernel as for the Gaussian (Halton points,
     # unscaled kernel, eta = 1.5)
     pts = inputs.halton_points(2048, 2)

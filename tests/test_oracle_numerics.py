@@ -201,7 +201,7 @@ def test_symmetric_mirror_is_exactly_symmetric(orc):
 
 
 def test_matvec_fixed_rank_converges_geometrically(orc):
-    # Sec. 6.3: e_rel decays exponentially in the fixed ACA rank k
+    # Sec. 6.4: e_rel decays exponentially in the fixed ACA rank k
     pts = inputs.uniform_points(2048, 2, 33)
     x = inputs.normal_vector(2048, 5)
     yb = orc.dense_matvec(pts, 0, 0.3, 0.0, x)
@@ -270,3 +270,80 @@ def test_adam_first_step_closed_form(orc):
     orc.adam_step(th, g, m, v, 1, lr=0.01)
     exp = np.array([1.0, -2.0, 0.5]) - 0.01 * g / (np.abs(g) + 1e-8)
     assert np.allclose(th, exp, rtol=1e-12, atol=1e-15)
+
+
+def _golden_features():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "block_features.txt")
+    pts = prm = None
+    leaves = []
+    for line in open(path):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        tag, body = [s.strip() for s in line.split("|", 1)]
+        if tag == "points":
+            pts = np.array([[float(v) for v in p.split()] for p in body.split(";")])
+        elif tag == "params":
+            prm = body.split()
+        elif tag == "leaf":
+            leaves.append([float(v) for v in body.split()])
+    return pts, prm, np.array(leaves)
+
+
+def test_block_features_hand_worked(orc):
+    # two hand-placed clusters: diameters, distance and sizes worked out by
+    # hand in tests/golden/block_features.txt
+    pts, prm, exp = _golden_features()
+    leaf, eta, ell, eps, kern = int(prm[0]), float(prm[1]), float(prm[2]), float(prm[3]), int(prm[4])
+    O = orc.HMatrix(pts, kern, ell, leaf, eta, eps)
+    assert O.n_adm == 2 and O.n_dense == 2
+    f = O.features()
+    assert f.shape == exp.shape
+    assert np.allclose(f, exp, rtol=1e-14, atol=1e-15), (f, exp)
+
+
+def test_block_features_respond_to_each_input(orc):
+    # moving B away by dl in x changes only the distance feature, by
+    # log2(1 + (3.375 + dl)/l); a Matern kernel id changes only f7; eps
+    # changes only f6
+    pts, prm, exp = _golden_features()
+    leaf, eta, ell = int(prm[0]), float(prm[1]), float(prm[2])
+    p2 = pts.copy()
+    p2[2:, 0] += 1.25
+    f = orc.HMatrix(p2, 1, ell, leaf, eta, 1e-8).features()
+    want = exp.copy()
+    want[:, 5] = np.log2(1.0 + (3.375 + 1.25) / ell)
+    want[:, 6] = 1.0
+    want[:, 7] = 1.0
+    assert np.allclose(f, want, rtol=1e-14, atol=1e-15), (f, want)
+
+
+@pytest.mark.parametrize("steps", [2, 3, 5])
+def test_adam_constant_gradient_closed_form(orc, steps):
+    # with a constant gradient g from m = v = 0, the bias-corrected moments
+    # are exactly m_hat = g and v_hat = g^2 at every step t (the corrections
+    # 1 - b^t cancel the geometric sums), so each step moves theta by
+    # lr * g / (|g| + eps): a wrong correction exponent at t >= 2 fails here
+    th0 = np.array([1.0, -2.0, 0.5, 3.0])
+    g = np.array([0.3, -4.0, 1e-3, -0.02])
+    th, m, v = th0.copy(), np.zeros(4), np.zeros(4)
+    for t in range(1, steps + 1):
+        orc.adam_step(th, g, m, v, t, lr=0.01)
+    exp = th0 - steps * 0.01 * g / (np.abs(g) + 1e-8)
+    assert np.allclose(th, exp, rtol=1e-12, atol=1e-15)
+    assert np.allclose(m, (1 - 0.9 ** steps) * g, rtol=1e-13)
+    assert np.allclose(v, (1 - 0.999 ** steps) * g * g, rtol=1e-12)
+
+
+def test_adam_sign_flip_second_step(orc):
+    # g then -g: m_2 = (0.09 - 0.1) g = -0.01 g, v_2 = (0.000999 + 0.001) g^2;
+    # the second step moves against the first by a factor 0.01/0.19 over
+    # sqrt(0.001999/0.001999) = 1 relative to |g|, i.e. by lr (1/19) g/|g|
+    th0 = np.array([0.7, -1.5])
+    g = np.array([2.0, -0.5])
+    th, m, v = th0.copy(), np.zeros(2), np.zeros(2)
+    orc.adam_step(th, g, m, v, 1, lr=0.1, eps=0.0)
+    orc.adam_step(th, -g, m, v, 2, lr=0.1, eps=0.0)
+    exp = th0 - 0.1 * np.sign(g) + 0.1 * np.sign(g) / 19.0
+    assert np.allclose(th, exp, rtol=1e-13)

@@ -11,10 +11,13 @@ for one set and for two sets:
 import numpy as np
 import pytest
 
-hyp = pytest.importorskip("hypothesis")
-from hypothesis import given, settings, strategies as st  # noqa: E402
+from paper_1708_09707_gb300 import inputs
 
-from paper_1708_09707_gb300 import inputs  # noqa: E402
+try:
+    from hypothesis import given, settings, strategies as st
+    HAVE_HYPOTHESIS = True
+except ImportError:   # a machine without hypothesis draws the cases with numpy
+    HAVE_HYPOTHESIS = False
 
 
 def _points(n, d, seed, dup):
@@ -46,22 +49,45 @@ def _check(H, n1, n2, leaf, eta, adm_max, rect):
     assert (cover == 1).all()
 
 
-@settings(max_examples=40, deadline=None)
-@given(n=st.integers(1, 400), d=st.integers(1, 3), leaf=st.integers(1, 48),
-       eta=st.sampled_from([0.0, 0.5, 1.0, 1.5, 2.0]), adm_max=st.booleans(),
-       dup=st.booleans(), seed=st.integers(0, 10_000))
-def test_block_structure_one_set(orc, n, d, leaf, eta, adm_max, dup, seed):
+def _one_set(orc, n, d, leaf, eta, adm_max, dup, seed):
     pts = _points(n, d, seed, dup)
     H = orc.HMatrix(pts, 0, 0.2, leaf, eta, 1e-6, adm_max=adm_max, compress=False)
     _check(H, n, n, leaf, eta, adm_max, False)
 
 
-@settings(max_examples=30, deadline=None)
-@given(n1=st.integers(1, 300), n2=st.integers(1, 300), d=st.integers(1, 3),
-       leaf=st.integers(1, 40), eta=st.sampled_from([0.0, 1.0, 1.5]), dup=st.booleans(),
-       seed=st.integers(0, 10_000))
-def test_block_structure_two_sets(orc, n1, n2, d, leaf, eta, dup, seed):
+def _two_sets(orc, n1, n2, d, leaf, eta, dup, seed):
     P = _points(n1, d, seed, dup)
     Q = _points(n2, d, seed + 1, dup)
     H = orc.HMatrix(P, 0, 0.2, leaf, eta, 1e-6, compress=False, cols=Q)
     _check(H, n1, n2, leaf, eta, False, True)
+
+
+if HAVE_HYPOTHESIS:
+    @settings(max_examples=40, deadline=None)
+    @given(n=st.integers(1, 400), d=st.integers(1, 3), leaf=st.integers(1, 48),
+           eta=st.sampled_from([0.0, 0.5, 1.0, 1.5, 2.0]), adm_max=st.booleans(),
+           dup=st.booleans(), seed=st.integers(0, 10_000))
+    def test_block_structure_one_set(orc, n, d, leaf, eta, adm_max, dup, seed):
+        _one_set(orc, n, d, leaf, eta, adm_max, dup, seed)
+
+    @settings(max_examples=30, deadline=None)
+    @given(n1=st.integers(1, 300), n2=st.integers(1, 300), d=st.integers(1, 3),
+           leaf=st.integers(1, 40), eta=st.sampled_from([0.0, 1.0, 1.5]), dup=st.booleans(),
+           seed=st.integers(0, 10_000))
+    def test_block_structure_two_sets(orc, n1, n2, d, leaf, eta, dup, seed):
+        _two_sets(orc, n1, n2, d, leaf, eta, dup, seed)
+else:
+    def test_block_structure_one_set(orc):
+        rng = np.random.default_rng(20260)
+        for _ in range(40):
+            _one_set(orc, int(rng.integers(1, 401)), int(rng.integers(1, 4)),
+                     int(rng.integers(1, 49)), float(rng.choice([0.0, 0.5, 1.0, 1.5, 2.0])),
+                     bool(rng.integers(2)), bool(rng.integers(2)), int(rng.integers(10_001)))
+
+    def test_block_structure_two_sets(orc):
+        rng = np.random.default_rng(20261)
+        for _ in range(30):
+            _two_sets(orc, int(rng.integers(1, 301)), int(rng.integers(1, 301)),
+                      int(rng.integers(1, 4)), int(rng.integers(1, 41)),
+                      float(rng.choice([0.0, 1.0, 1.5])), bool(rng.integers(2)),
+                      int(rng.integers(10_001)))

@@ -45,15 +45,21 @@ def test_noalloc_sort_matches_allocating_sort_twice(lib):
     L = lib
     nmax = 262144
     rng = np.random.default_rng(13)
-    # two calls in a row: the first fills the shared scratch, the second must
-    # not see anything of it (different size, ties, different key width)
-    cases = [(nmax, 64, False), (100003, 40, True)]
-    for n, bits, ties in cases:
-        keys = rng.integers(0, 2 ** 62, size=n, dtype=np.int64).astype(np.uint64)
+    # calls in a row: each one fills the shared scratch, the next must not
+    # see anything of it (different size, ties, different key width)
+    # keys are drawn over the full 64 bits, so the last radix pass sorts on
+    # the top bits; one case sets the top bit of every other key, one is a
+    # single pair
+    cases = [(nmax, 64, False, False), (100003, 40, True, False), (77777, 64, False, True),
+             (1, 64, False, True)]
+    for n, bits, ties, high in cases:
+        keys = rng.integers(0, 2 ** 64, size=n, dtype=np.uint64)
         if bits < 64:
             keys &= np.uint64((1 << bits) - 1)
         if ties:
             keys %= np.uint64(997)
+        if high:
+            keys[::2] |= np.uint64(1 << 63)
         vals = np.arange(n, dtype=np.uint32)
         ka, va, kb, vb = _sorted_both(L, keys, vals, bits)
         assert np.array_equal(ka, kb) and np.array_equal(va, vb)
