@@ -197,6 +197,34 @@ uint64_t hm_kernel_launches(void);
  * Returns HM_EINVAL for other values. */
 int hm_set_gather_shape(int shape);
 
+/* Launch shape of the batched ACA of one block size class (Sec. 5.4.1
+ * batching; a tuning control, not part of the method). Size class c holds
+ * the admissible blocks with 2^(c+5) < max(m, n) <= 2^(c+6) (class 0 from 1,
+ * class 11 unbounded); cls = -1 sets every class. shape -1 (default): the
+ * team kernels for classes 0 .. 8 (a team of 1 to 32 warps per block, the
+ * residuals in registers, the reductions inside the team), the cluster
+ * kernels above; 0: the cluster kernels of the first design for the class
+ * (one warp per block up to 512 rows, then a CTA or a thread-block cluster
+ * per block); 1: the class's default team shape; 2: another team shape
+ * (compiled for float Gaussian builds of classes 2 .. 8; elsewhere the
+ * default team shape runs). All compute the
+ * same approximation with the same readings of Alg. 2; their sums run in
+ * different orders, so results agree to rounding. Blocks whose reservation
+ * exceeds 64 ranks always run the cluster kernels. Process-wide; applies to
+ * builds started afterwards. Returns HM_EINVAL for other values. */
+int hm_set_aca_shape(int cls, int shape);
+
+/* Test hooks of the failure paths (not part of the method; process-wide,
+ * applying to builds and products started afterwards; 0 restores the
+ * default):
+ *   HM_HOOK_ACA_STEP_LIMIT  value > 0 caps the iterations of every block's
+ *                           ACA loop at value (default k + n + 1, which no
+ *                           block reaches); a block that hits the cap stops
+ *                           and the build returns HM_ETIMEOUT.
+ * Returns HM_EINVAL for an unknown hook or a value out of range. */
+enum { HM_HOOK_ACA_STEP_LIMIT = 0 };
+int hm_set_test_hook(int hook, int64_t value);
+
 /* Counts, ranks and bytes of a built handle. */
 typedef struct hm_stats {
     int64_t n_points, n_nodes, n_adm, n_dense, n_tiles;

@@ -165,7 +165,7 @@ k_aca_warp(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restric
     st.rtol2_m = rtol * rtol / (double)m;
     st.thr2 = thr * thr;
     st.fixed_rank = !(thr >= 0.0);
-    const int limit = kmax + n + 1;
+    const int limit = a.step_limit > 0 ? a.step_limit : kmax + n + 1;
 
     // reference row 0
     {
@@ -686,7 +686,7 @@ k_aca_cluster(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __rest
         }
         int r = 0, j = 0, rej = 0, run = 0, iref = 0;
         bool converged = false;
-        const int limit = kmax + n + 1;
+        const int limit = a.step_limit > 0 ? a.step_limit : kmax + n + 1;
         for (int it = 0; r < kmax; ++it) {
             if (it > limit) {
                 if (gt == 0) atomicOr(a.status, 1);
@@ -1138,7 +1138,7 @@ k_aca_big(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restrict
         }
         int r = 0, j = 0, rej = 0, run = 0, iref = 0;
         bool converged = false;
-        const int limit = kmax + n + 1;
+        const int limit = a.step_limit > 0 ? a.step_limit : kmax + n + 1;
         T du[KG / 32];
         for (int it = 0; r < kmax; ++it) {
             if (it > limit) {

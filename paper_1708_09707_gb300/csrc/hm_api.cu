@@ -156,6 +156,33 @@ int hm_set_gather_shape(int shape)
     return r;
 }
 
+int hm_set_aca_shape(int cls, int shape)
+{
+    set_error("");
+    if (cls < -1 || cls >= hm::ACA_NCLASS || shape < -1 || shape > 2) {
+        set_error("ACA shape: class -1 or 0 .. 11, shape -1 .. 2");
+        return HM_EINVAL;
+    }
+    for (int c = (cls < 0 ? 0 : cls); c < (cls < 0 ? hm::ACA_NCLASS : cls + 1); ++c)
+        hm::set_aca_shape(c, shape);
+    return HM_OK;
+}
+
+int hm_set_test_hook(int hook, int64_t value)
+{
+    set_error("");
+    switch (hook) {
+    case HM_HOOK_ACA_STEP_LIMIT:
+        if (value < 0 || value > INT32_MAX) break;
+        hm::set_aca_step_limit((int)value);
+        return HM_OK;
+    default:
+        break;
+    }
+    set_error("unknown test hook or value out of range");
+    return HM_EINVAL;
+}
+
 hm_handle hm_build_ex(const double* points, int64_t N, int d, int kernel, const double* params,
                       int leaf_size, double eta, double aca_eps, const hm_options* opt,
                       int* status)

@@ -64,6 +64,9 @@ struct AcaArgs {
     // the block's point set; null = the paper's blockwise relative test.
     const int32_t* bset;     // per block: its point set
     const int64_t* set_n;    // per set: number of points
+    // Iteration limit of a block's loop; 0: k_max + n + 1 (no block needs
+    // more). A smaller value is a test hook of the HM_ETIMEOUT path.
+    int step_limit;
 };
 
 // Size classes of admissible blocks by d = max(m, n): class c holds the
@@ -73,6 +76,17 @@ struct AcaArgs {
 // residuals in registers, class 11 a cluster of 8 CTAs with its residuals in
 // global scratch.
 constexpr int ACA_NCLASS = 12;
+// Rank buckets of the reservations inside a size class: bucket k holds the
+// blocks with 2^(k+3) < kres <= 2^(k+4) (bucket 0 from 1, the last bucket
+// unbounded); a launch of the team kernels sizes its Gram matrices for the
+// bucket's largest rank (16, 32 or 64), the last bucket runs the cluster
+// kernels. With the learned rank model the buckets follow the predicted
+// ranks (Sec. 5.4.1's batching of similar tasks, by size and rank).
+constexpr int ACA_NKB = 4;
+__host__ __device__ __forceinline__ int aca_kbucket(int kres)
+{
+    return kres <= 16 ? 0 : kres <= 32 ? 1 : kres <= 64 ? 2 : 3;
+}
 __host__ __device__ __forceinline__ int aca_class_dim(int c) { return 64 << c; }
 __host__ __device__ __forceinline__ int aca_class_of(int m, int n)
 {
@@ -84,12 +98,29 @@ __host__ __device__ __forceinline__ int aca_class_of(int m, int n)
 
 // Run ACA on the blocks listed in order[0..n) (indices into the block arrays),
 // all of size class cls; max_n bounds the column count of any block.
+// kb is the blocks' rank bucket (aca_kbucket of every block's reservation).
 void aca_run(int precision, const KernelParams& kp, const DeviceCoords& X,
-             const AcaArgs& a, const uint32_t* order, int64_t n, int cls, int64_t max_n,
+             const AcaArgs& a, const uint32_t* order, int64_t n, int cls, int kb, int64_t max_n,
              cudaStream_t s);
 // The same for the Matern kernel of order 1 (instantiated in its own unit).
 void aca_run_k1(bool f64, const KernelParams& kp, const DeviceCoords& X, const AcaArgs& a,
-                const uint32_t* order, int64_t n, int cls, int64_t max_n, cudaStream_t s);
+                const uint32_t* order, int64_t n, int cls, int kb, int64_t max_n, cudaStream_t s);
+// Team kernels (hm_aca_team.cuh) of size class cls with Gram matrices for
+// ranks up to KT; false when the class has no team shape or the shape
+// control selects the cluster kernels (hm_set_aca_shape).
+bool aca_team_gm(bool f64, const KernelParams& kp, const DeviceCoords& X, const AcaArgs& a,
+                 const uint32_t* order, int64_t n, int cls, int shape, int KT, cudaStream_t s);
+bool aca_team_k1(bool f64, const KernelParams& kp, const DeviceCoords& X, const AcaArgs& a,
+                 const uint32_t* order, int64_t n, int cls, int shape, int KT, cudaStream_t s);
+// Launch shape of the ACA of size class cls: -1 default, 0 the cluster
+// kernels of hm_aca_impl.cuh, 1 .. 3 team kernel shapes (process-wide).
+int aca_shape(int cls);
+// The default shape of each class (the measured best).
+int aca_default_shape(int cls);
+// Iteration limit handed to the ACA kernels (0: none beyond k + n + 1).
+int aca_step_limit();
+void set_aca_shape(int cls, int shape);
+void set_aca_step_limit(int v);
 
 // ---------------------------------------------------------------------------
 // Product layout. The product gathers, for every row tile (a leaf of the

@@ -104,11 +104,14 @@ __global__ void k_classes(const Blk* __restrict__ blk, const uint32_t* __restric
     const uint32_t b = ids ? ids[q] : (uint32_t)q;
     Blk B = blk[b];
     int c = aca_class_of(B.m, B.n);
-    key[q] = (uint64_t)(ACA_NCLASS - 1 - c);   // largest class first
-    val[q] = b;
     int full = min(kcap, min(B.m, B.n));
-    kres[b] = kpred ? max(1, min(kpred[b], full)) : full;
-    atomicAdd((unsigned long long*)&cls_count[c], 1ull);
+    const int k = kpred ? max(1, min(kpred[b], full)) : full;
+    kres[b] = k;
+    const int kb = aca_kbucket(k);
+    // largest class first, then the rank buckets in increasing order
+    key[q] = (uint64_t)((ACA_NCLASS - 1 - c) * ACA_NKB + kb);
+    val[q] = b;
+    atomicAdd((unsigned long long*)&cls_count[c * ACA_NKB + kb], 1ull);
 }
 
 // Symmetric kernels: leaf b is canonical when its rows start no later than
@@ -414,7 +417,7 @@ struct AcaOrder {
     DevBuf<uint32_t> order;
     DevBuf<int64_t> pre, preu;
     std::vector<int64_t> hpre, hpreu;
-    int64_t cstart[ACA_NCLASS], cend[ACA_NCLASS];
+    int64_t cstart[ACA_NCLASS][ACA_NKB], cend[ACA_NCLASS][ACA_NKB];
 };
 
 void aca_order(hm_handle_s& h, const uint32_t* ids, int64_t n, const int32_t* kpred, AcaOrder& O)
@@ -423,13 +426,13 @@ void aca_order(hm_handle_s& h, const uint32_t* ids, int64_t n, const int32_t* kp
     O.n = n;
     DevBuf<uint64_t> key(n, s);
     O.order.alloc(n, s);
-    DevBuf<int64_t> ccount(ACA_NCLASS, s);
-    HM_CUDA(cudaMemsetAsync(ccount.p, 0, ACA_NCLASS * sizeof(int64_t), s));
+    DevBuf<int64_t> ccount(ACA_NCLASS * ACA_NKB, s);
+    HM_CUDA(cudaMemsetAsync(ccount.p, 0, ACA_NCLASS * ACA_NKB * sizeof(int64_t), s));
     k_classes<<<grid_for(n), NT, 0, s>>>(h.ablk.p, ids, n, h.opt.k_cap, kpred, key.p, O.order.p,
                                          h.kres.p, ccount.p); note_launch();
     HM_LAUNCH("classes");
-    radix_sort_u64_u32(key.p, O.order.p, n, bits_for(ACA_NCLASS), s);
-    int64_t cc[ACA_NCLASS];
+    radix_sort_u64_u32(key.p, O.order.p, n, bits_for(ACA_NCLASS * ACA_NKB), s);
+    int64_t cc[ACA_NCLASS * ACA_NKB];
     HM_CUDA(cudaMemcpyAsync(cc, ccount.p, sizeof(cc), cudaMemcpyDeviceToHost, s));
     DevBuf<int64_t> res(n, s), resu(n, s);
     O.pre.alloc(n + 1, s);
@@ -445,11 +448,12 @@ void aca_order(hm_handle_s& h, const uint32_t* ids, int64_t n, const int32_t* kp
                             cudaMemcpyDeviceToHost, s));
     HM_CUDA(cudaStreamSynchronize(s));
     int64_t q = 0;
-    for (int c = ACA_NCLASS - 1; c >= 0; --c) {
-        O.cstart[c] = q;
-        q += cc[c];
-        O.cend[c] = q;
-    }
+    for (int c = ACA_NCLASS - 1; c >= 0; --c)
+        for (int kb = 0; kb < ACA_NKB; ++kb) {
+            O.cstart[c][kb] = q;
+            q += cc[c * ACA_NKB + kb];
+            O.cend[c][kb] = q;
+        }
 }
 
 // Arguments of the ACA kernels for this handle (setn keeps the per-set point
@@ -471,6 +475,7 @@ AcaArgs aca_args(hm_handle_s& h, DevBuf<int64_t>& setn)
     a.eps0 = h.opt.eps0 > 0 ? h.opt.eps0 : (h.precision == HM_PREC_FP64 ? 1e-14 : 1e-6);
     a.k_cap = h.opt.k_cap;
     a.bset = nullptr;
+    a.step_limit = aca_step_limit();
     a.set_n = nullptr;
     // The mixed-precision floor m n / N rests on ||A||_F^2 >= N phi(0)^2 (the
     // diagonal of A_{phi, Y x Y}), so the floors of all blocks add up to at
@@ -504,11 +509,16 @@ void aca_range(hm_handle_s& h, const AcaOrder& O, const AcaArgs& a, int64_t q0, 
     const bool serial = h.opt.profile == 2;
     cs.fork();
     for (int c = ACA_NCLASS - 1; c >= 0; --c) {
-        int64_t lo = std::max(q0, O.cstart[c]), hi = std::min(q1, O.cend[c]);
-        if (hi > lo) {
-            cudaStream_t sc = serial ? s : cs.st[c];
-            HM_CUDA(cudaEventRecord(cs.t0[c], sc));
-            aca_run(h.precision, h.kp, h.X, a, O.order.p + lo, hi - lo, c, h.max_set_n, sc);
+        cudaStream_t sc = serial ? s : cs.st[c];
+        bool any = false;
+        for (int kb = 0; kb < ACA_NKB; ++kb) {
+            int64_t lo = std::max(q0, O.cstart[c][kb]), hi = std::min(q1, O.cend[c][kb]);
+            if (hi <= lo) continue;
+            if (!any) HM_CUDA(cudaEventRecord(cs.t0[c], sc));
+            any = true;
+            aca_run(h.precision, h.kp, h.X, a, O.order.p + lo, hi - lo, c, kb, h.max_set_n, sc);
+        }
+        if (any) {
             HM_CUDA(cudaEventRecord(cs.t1[c], sc));
             cs.timed[c] = true;
         }

@@ -18,6 +18,7 @@ GAUSSIAN, MATERN32, MATERN_K1 = 0, 1, 2
 PREC_FP64, PREC_MIXED = 0, 1
 NEAR_AUTO, NEAR_FP64, NEAR_FP32, NEAR_BF16X2, NEAR_BF16 = range(5)
 MLP_NPARAM = 4801
+OK, EINVAL, ENOMEM, EOVERFLOW, ECUDA, ETIMEOUT, ENOTSUP = 0, -1, -2, -3, -4, -5, -6
 
 _STATUS = {0: "HM_OK", -1: "HM_EINVAL", -2: "HM_ENOMEM", -3: "HM_EOVERFLOW",
            -4: "HM_ECUDA", -5: "HM_ETIMEOUT", -6: "HM_ENOTSUP"}
@@ -95,6 +96,8 @@ def _declare(L):
     L.hm_last_error.restype = C.c_char_p
     L.hm_kernel_launches.restype = C.c_uint64
     L.hm_set_gather_shape.argtypes = [C.c_int]
+    L.hm_set_aca_shape.argtypes = [C.c_int, C.c_int]
+    L.hm_set_test_hook.argtypes = [C.c_int, C.c_int64]
     L.hm_alu_peak.argtypes = [C.c_int, C.POINTER(C.c_double)]
     L.hm_build_ex.restype = _vp
     L.hm_build_ex.argtypes = [_vp, i64, C.c_int, C.c_int, _vp, C.c_int, C.c_double,
@@ -380,6 +383,21 @@ def mlp_adam(theta, grad, m, v, t: int, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, str
 def set_gather_shape(shape: int) -> None:
     """Force the product gather's launch shape (0..4), or -1 to tune."""
     _check(lib().hm_set_gather_shape(int(shape)))
+
+
+def set_aca_shape(cls: int, shape: int) -> None:
+    """hm_set_aca_shape: launch shape of the batched ACA of one size class
+    (-1 every class); shape -1 default, 0 the cluster kernels, 1 the default team
+    shape, 2 another team shape."""
+    _check(lib().hm_set_aca_shape(int(cls), int(shape)))
+
+
+HOOK_ACA_STEP_LIMIT = 0
+
+
+def set_test_hook(hook: int, value: int) -> None:
+    """hm_set_test_hook: a test hook of the failure paths (0 restores the default)."""
+    _check(lib().hm_set_test_hook(int(hook), int(value)))
 
 
 def kernel_launches() -> int:
