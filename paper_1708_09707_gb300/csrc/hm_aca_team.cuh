@@ -427,9 +427,11 @@ k_aca_team(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restric
         }
         run = 0;
         const T piv = oc.aval;
-        // u_r = u^ / piv as products with 1 / piv, unless 1 / piv would
-        // overflow (far blocks whose entries are near the underflow limit)
-        const bool small_piv = !(fabs(piv) >= T(1e-30));
+        // in float u_r = u^ / piv as products with 1 / piv, unless 1 / piv
+        // would overflow (far blocks whose entries are near the underflow
+        // limit); in double the quotients of Alg. 2 themselves, as the CPU
+        // oracle forms them
+        const bool small_piv = sizeof(T) == 8 || !(fabs(piv) >= T(1e-30));
         const T rpiv = small_piv ? T(0) : T(1) / piv;
         const int bi = oc.ai;
         const T uiref = small_piv ? oc.pick / piv : oc.pick * rpiv;
