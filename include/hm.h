@@ -221,9 +221,43 @@ int hm_set_aca_shape(int cls, int shape);
  *                           ACA loop at value (default k + n + 1, which no
  *                           block reaches); a block that hits the cap stops
  *                           and the build returns HM_ETIMEOUT.
+ *   HM_HOOK_WAIT_LIMIT_NS   value > 0 bounds every mbarrier wait of the
+ *                           product's bulk-copy kernels at value ns
+ *                           (default 2 s); the producer's final waits for
+ *                           copies it issued keep at least 2 s, so no CTA
+ *                           exits with a copy into its shared memory in
+ *                           flight.
+ *   HM_HOOK_GATHER_WITHHOLD value k + 1 > 0: the bulk-copy producer of every
+ *                           work item leaves out its chunk k, so that the
+ *                           consumers' wait for it runs out; the product
+ *                           gives up, sets the status word and returns no
+ *                           valid result (see hm_check_status).
+ *   HM_HOOK_FAIL_ALLOC      value n > 0: the n-th device allocation of the
+ *                           library from now fails as if the device were out
+ *                           of memory (HM_ENOMEM); the failing call releases
+ *                           what it had allocated.
  * Returns HM_EINVAL for an unknown hook or a value out of range. */
-enum { HM_HOOK_ACA_STEP_LIMIT = 0 };
+enum {
+    HM_HOOK_ACA_STEP_LIMIT = 0,
+    HM_HOOK_WAIT_LIMIT_NS = 1,
+    HM_HOOK_GATHER_WITHHOLD = 2,
+    HM_HOOK_FAIL_ALLOC = 3
+};
 int hm_set_test_hook(int hook, int64_t value);
+
+/* Device status of a handle's earlier calls: synchronises the handle's
+ * stream and returns HM_ETIMEOUT if a bounded device loop or wait gave up
+ * since the last check (the status word is then cleared), else HM_OK. A
+ * product whose y is in host memory does this check itself before it
+ * returns; a product on device buffers (and one captured in a CUDA graph)
+ * leaves it to this call. */
+int hm_check_status(hm_handle h);
+
+/* Device bytes the library holds at this moment, over every handle, batch
+ * and call in flight (the allocations it made and has not yet released; the
+ * fixed array of the allocation-free sort is not counted). For checks that a
+ * failed call released what it had allocated. */
+uint64_t hm_device_bytes(void);
 
 /* Counts, ranks and bytes of a built handle. */
 typedef struct hm_stats {

@@ -182,6 +182,56 @@ __device__ __forceinline__ void warp_red(TRed<double>& q, int pick_lane)
     if (F & RD_PICK) q.pick = __shfl_sync(FULL, q.pick, pick_lane);
 }
 
+// Combination of up to 32 warp results held one per lane (lanes past the
+// team's warps hold the identity): every lane receives the total. Used for
+// teams of 8 or more warps in place of a join loop over the slots.
+template <int F>
+__device__ __forceinline__ void lane_join(TRed<float>& q)
+{
+    constexpr unsigned FULL = 0xffffffffu;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        if (F & RD_SUMS) {
+            q.s0.shfl_join(o);
+            q.s1.shfl_join(o);
+        }
+        if (F & RD_PICK) q.pick += __shfl_xor_sync(FULL, q.pick, o);
+    }
+    q.x0 = __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(q.x0)));
+    if (F & RD_ARG) {
+        const unsigned vb = __reduce_max_sync(FULL, __float_as_uint(q.av));
+        const bool cand = __float_as_uint(q.av) == vb;
+        const int w = __reduce_min_sync(FULL, cand ? q.ai : 0x7fffffff);
+        const unsigned who = __ballot_sync(FULL, cand && q.ai == w);
+        q.aval = __shfl_sync(FULL, q.aval, who ? __ffs(who) - 1 : 0);
+        q.av = __uint_as_float(vb);
+        q.ai = w;
+    }
+    if (F & RD_MN) q.mn = __reduce_min_sync(FULL, q.mn);
+}
+
+template <int F>
+__device__ __forceinline__ void lane_join(TRed<double>& q)
+{
+    constexpr unsigned FULL = 0xffffffffu;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        if (F & RD_SUMS) {
+            q.s0.shfl_join(o);
+            q.s1.shfl_join(o);
+        }
+        if (F & RD_PICK) q.pick += __shfl_xor_sync(FULL, q.pick, o);
+        q.x0 = max(q.x0, __shfl_xor_sync(FULL, q.x0, o));
+        if (F & RD_ARG) {
+            const double oav = __shfl_xor_sync(FULL, q.av, o);
+            const double oaval = __shfl_xor_sync(FULL, q.aval, o);
+            const int oai = __shfl_xor_sync(FULL, q.ai, o);
+            q.take(oav, oaval, oai);
+        }
+        if (F & RD_MN) q.mn = min(q.mn, __shfl_xor_sync(FULL, q.mn, o));
+    }
+}
+
 // Per-team shared memory (dynamic, KT chosen at launch).
 template <class T>
 struct TeamSmem {
@@ -189,7 +239,7 @@ struct TeamSmem {
     T* Gv;      // packed Gram matrix of the v's
     T* sgv;     // (v_l)_j of the current step, KT
     T* sgu;     // (u_l)_{i*} (or (u_l)_{iref}), KT
-    T* dotw;    // per-warp partial dots, W x KT
+    T* dotw;    // per-warp partial dots, 2 x W x KT (column, row side)
     TRed<T>* slot;   // reduction slots, 2 x W
     StopState* st;   // the stopping test's state (thread 0 of the team)
     int* ctl;   // decisions of the step: resolved, stop_ok
@@ -202,7 +252,7 @@ __host__ __device__ inline size_t team_smem_bytes(int W, int KT)
 {
     const size_t ktp = (size_t)KT * (KT + 1) / 2;
     return team_align(2 * ktp * sizeof(T)) + team_align(2 * KT * sizeof(T)) +
-           team_align((size_t)W * KT * sizeof(T)) + team_align(2 * W * sizeof(TRed<T>)) +
+           team_align((size_t)2 * W * KT * sizeof(T)) + team_align(2 * W * sizeof(TRed<T>)) +
            team_align(sizeof(StopState)) + 16;
 }
 
@@ -219,7 +269,7 @@ __device__ __forceinline__ TeamSmem<T> team_carve(unsigned char* base, int W, in
     s.sgu = s.sgv + KT;
     p += team_align(2 * KT * sizeof(T));
     s.dotw = reinterpret_cast<T*>(p);
-    p += team_align((size_t)W * KT * sizeof(T));
+    p += team_align((size_t)2 * W * KT * sizeof(T));
     s.slot = reinterpret_cast<TRed<T>*>(p);
     p += team_align(2 * W * sizeof(TRed<T>));
     s.st = reinterpret_cast<StopState*>(p);
@@ -244,9 +294,16 @@ __device__ __forceinline__ TRed<T> team_reduce(TRed<T> q, const TeamSmem<T>& S, 
     TRed<T>* sl = S.slot + ph * W;
     if (lane == 0) sl[wt] = q;
     team_sync<W>(bar);
-    TRed<T> t = sl[0];
-#pragma unroll 1
-    for (int k = 1; k < W; ++k) t.join(sl[k]);
+    TRed<T> t;
+    if (W >= 8) {
+        if (lane < W) t = sl[lane];
+        else t.init();
+        lane_join<F>(t);
+    } else {
+        t = sl[0];
+#pragma unroll
+        for (int k = 1; k < W; ++k) t.join(sl[k]);
+    }
     ph ^= 1;
     return t;
 }
@@ -269,7 +326,7 @@ __host__ __device__ constexpr int team_cta_threads()
 
 // Residual pass of one side: entries uh[q] (index g + q G < len, zero
 // elsewhere) minus sum_l s_l F_l (F_l the l-th factor column, length len,
-// s_l = coef[l]), in batches of LC ranks with the dots uh . F_l taken before
+// s_l held by lane l mod 32 of every warp in coef[l / 32]), in batches of LC ranks with the dots uh . F_l taken before
 // each batch is subtracted (the partial residuals of the Gram correction);
 // the warp's dot partials of rank l go to dotw[l]. Every load reads a valid
 // entry (indices past len are clamped to len - 1) so that the loads of a
@@ -277,15 +334,16 @@ __host__ __device__ constexpr int team_cta_threads()
 // batch.
 template <class T, int W, int R, bool DOTS>
 __device__ __forceinline__ void team_resid(T (&uh)[R], const T* __restrict__ F, int len, int r,
-                                           const T* coef, T* dotw, int g, int lane)
+                                           const T (&coef)[2], T* dotw, int g, int lane)
 {
     constexpr int G = 32 * W;
     for (int l0 = 0; l0 < r; l0 += LC) {
         T sv[LC], p[LC];
         const T* Fb[LC];
+        const T cw = l0 < 32 ? coef[0] : coef[1];   // lane l holds s_l, s_{l+32}
 #pragma unroll
         for (int e = 0; e < LC; ++e) {
-            sv[e] = coef[l0 + e];
+            sv[e] = __shfl_sync(0xffffffffu, cw, (l0 + e) & 31);
             p[e] = T(0);
             Fb[e] = F + (l0 + e < r ? (l0 + e) : l0) * len;
         }
@@ -385,18 +443,23 @@ k_aca_team(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restric
             break;
         }
         if (j % G == g) used |= 1u << (j / G);
-        const int rpad = ((r + LC - 1) / LC) * LC;
-        // (v_l)_j of the earlier ranks, for every warp of the team
-        if (wt == 0)
-            for (int l = lane; l < rpad; l += 32) S.sgv[l] = l < r ? V[l * n + j] : T(0);
-        team_sync<W>(bar);
+        // (v_l)_j of the earlier ranks: every warp loads them for itself
+        // (lane l: ranks l and l + 32), warp 0 also keeps them for its Gram
+        // correction
+        T sreg[2];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const int l = lane + 32 * s;
+            sreg[s] = l < r ? V[l * n + j] : T(0);
+            if (wt == 0 && l < KT) S.sgv[l] = sreg[s];
+        }
         // ---- column pass: u^ = A(:, j) - sum_l u_l (v_l)_j, with w . u_l
         team_eval<T, KERN, W, R>(uh, X, load_pt<T>(X, B.col0 + j), B.row0, m, g, c, c2);
         TRed<T> qc;
         qc.init();
 #pragma unroll
         for (int q = 0; q < R; ++q) qc.x0 = max(qc.x0, fabs(uh[q]));
-        team_resid<T, W, R, true>(uh, U, m, r, S.sgv, dotw, g, lane);
+        team_resid<T, W, R, true>(uh, U, m, r, sreg, dotw, g, lane);
         {
             bool have_mn = false;
 #pragma unroll
@@ -452,7 +515,13 @@ k_aca_team(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restric
                 }
                 du[s] = x;
             }
-            for (int l = lane; l < rpad; l += 32) S.sgu[l] = l < r ? U[l * m + bi] : T(0);
+        }
+        // (u_l)_{i*} of the earlier ranks, per warp as above
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const int l = lane + 32 * s;
+            sreg[s] = l < r ? U[l * m + bi] : T(0);
+            if (wt == 0 && l < KT) S.sgu[l] = sreg[s];
         }
         // u_r = u^ / piv
         TRed<T> qr;
@@ -475,10 +544,11 @@ k_aca_team(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restric
                 }
             }
         }
-        team_sync<W>(bar);
         // ---- row pass: v = A(i*, :) - sum_l (u_l)_{i*} v_l, with w . v_l
+        // (its dot partials go to the second buffer: warp 0 may still read
+        // the column pass's)
         team_eval<T, KERN, W, R>(uh, X, load_pt<T>(X, B.row0 + bi), B.col0, n, g, c, c2);
-        team_resid<T, W, R, true>(uh, V, n, r, S.sgu, dotw, g, lane);
+        team_resid<T, W, R, true>(uh, V, n, r, sreg, dotw + W * KT, g, lane);
         {
             T* __restrict__ Vr = V + r * n + g;
             bool have_mn = false;
@@ -511,7 +581,7 @@ k_aca_team(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restric
                 T x = T(0);
                 if (l < r) {
 #pragma unroll
-                    for (int k = 0; k < W; ++k) x += S.dotw[k * KT + l];
+                    for (int k = 0; k < W; ++k) x += S.dotw[(W + k) * KT + l];
                     for (int l2 = l - l % LC; l2 < r; ++l2)
                         x = fma(-S.Gv[l >= l2 ? pk(l, l2) : pk(l2, l)], S.sgu[l2], x);
                 }
@@ -545,13 +615,14 @@ k_aca_team(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restric
         if (resolved && orr.mn < m) {
             iref = orr.mn;
             if (iref % G == g) seen |= 1u << (iref / G);
-            // every thread has read ctl and sgu before this barrier
-            const int rp2 = ((r + LC - 1) / LC) * LC;
-            if (wt == 0)
-                for (int l = lane; l < rp2; l += 32) S.sgu[l] = l < r ? U[l * m + iref] : T(0);
-            team_sync<W>(bar);
+            T sref[2];
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const int l = lane + 32 * s;
+                sref[s] = l < r ? U[l * m + iref] : T(0);
+            }
             team_eval<T, KERN, W, R>(uh, X, load_pt<T>(X, B.row0 + iref), B.col0, n, g, c, c2);
-            team_resid<T, W, R, false>(uh, V, n, r, S.sgu, dotw, g, lane);
+            team_resid<T, W, R, false>(uh, V, n, r, sref, dotw, g, lane);
             TRed<T> qf;
             qf.init();
 #pragma unroll
@@ -632,7 +703,7 @@ bool launch_team_class(const KernelParams& kp, const DeviceCoords& X, const AcaA
     case 4 * 4 + 1: HM_TEAM(4, 8); break;
     case 5 * 4 + 1: HM_TEAM(8, 8); break;
     case 6 * 4 + 1: HM_TEAM(16, 8); break;
-    case 7 * 4 + 1: HM_TEAM(32, 8); break;
+    case 7 * 4 + 1: HM_TEAM(16, 16); break;
     case 8 * 4 + 1: HM_TEAM(32, 16); break;
     default:
         if constexpr (alts) {
@@ -642,7 +713,7 @@ bool launch_team_class(const KernelParams& kp, const DeviceCoords& X, const AcaA
             case 4 * 4 + 2: HM_TEAM(8, 4); break;
             case 5 * 4 + 2: HM_TEAM(16, 4); break;
             case 6 * 4 + 2: HM_TEAM(8, 16); break;
-            case 7 * 4 + 2: HM_TEAM(16, 16); break;
+            case 7 * 4 + 2: HM_TEAM(32, 8); break;
             case 8 * 4 + 2: HM_TEAM(16, 32); break;
             default: return false;
             }

@@ -4,6 +4,8 @@
 
 #include <algorithm>
 #include <atomic>
+#include <unordered_map>
+#include <mutex>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -47,9 +49,18 @@ int to_status(const std::exception& e)
 
 // ------------------------------------------------------------------ memory
 static bool g_pool_ready = false;
+// test hook: the n-th device allocation from now fails (0: none)
+static std::atomic<int64_t> g_fail_alloc{0};
+// device bytes the library holds (hm_device_bytes)
+static std::mutex g_live_mu;
+static std::unordered_map<void*, size_t> g_live;
+static uint64_t g_live_bytes = 0;
 
 void* dev_alloc(size_t bytes, cudaStream_t s)
 {
+    if (g_fail_alloc.load() > 0 && g_fail_alloc.fetch_sub(1) == 1)
+        fail(HM_ENOMEM, "device allocation of " + std::to_string(bytes) +
+                            " bytes failed (injected by the test hook)");
     if (!g_pool_ready) {
         int dev = 0;
         HM_CUDA(cudaGetDevice(&dev));
@@ -66,12 +77,26 @@ void* dev_alloc(size_t bytes, cudaStream_t s)
         fail(HM_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed: " +
                             cudaGetErrorString(e));
     }
+    if (p) {
+        std::lock_guard<std::mutex> lk(g_live_mu);
+        g_live[p] = bytes;
+        g_live_bytes += bytes;
+    }
     return p;
 }
 
 void dev_free(void* p, cudaStream_t s)
 {
-    if (p) cudaFreeAsync(p, s);
+    if (!p) return;
+    {
+        std::lock_guard<std::mutex> lk(g_live_mu);
+        auto it = g_live.find(p);
+        if (it != g_live.end()) {
+            g_live_bytes -= it->second;
+            g_live.erase(it);
+        }
+    }
+    cudaFreeAsync(p, s);
 }
 
 bool is_device_ptr(const void* p)
@@ -176,6 +201,18 @@ int hm_set_test_hook(int hook, int64_t value)
         if (value < 0 || value > INT32_MAX) break;
         hm::set_aca_step_limit((int)value);
         return HM_OK;
+    case HM_HOOK_WAIT_LIMIT_NS:
+        if (value < 0) break;
+        hm::set_mvp_wait_ns((uint64_t)value);
+        return HM_OK;
+    case HM_HOOK_GATHER_WITHHOLD:
+        if (value < 0 || value > INT32_MAX) break;
+        hm::set_mvp_withhold((int)value - 1);
+        return HM_OK;
+    case HM_HOOK_FAIL_ALLOC:
+        if (value < 0) break;
+        g_fail_alloc = value;
+        return HM_OK;
     default:
         break;
     }
@@ -259,6 +296,32 @@ int hm_matvec_ex(hm_handle h, const double* x, double* y, int nrhs, void* stream
 int hm_matvec(hm_handle h, const double* x, double* y)
 {
     return hm_matvec_ex(h, x, y, 1, nullptr);
+}
+
+uint64_t hm_device_bytes(void)
+{
+    std::lock_guard<std::mutex> lk(g_live_mu);
+    return g_live_bytes;
+}
+
+int hm_check_status(hm_handle h)
+{
+    set_error("");
+    try {
+        if (!h) fail(HM_EINVAL, "null handle");
+        int st = 0;
+        HM_CUDA(cudaMemcpyAsync(&st, h->status.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        HM_CUDA(cudaStreamSynchronize(h->stream));
+        if (st) {
+            HM_CUDA(cudaMemsetAsync(h->status.p, 0, sizeof(int), h->stream));
+            HM_CUDA(cudaStreamSynchronize(h->stream));
+            fail(HM_ETIMEOUT, std::string("a device loop or wait gave up (status ") +
+                                  std::to_string(st) + ")");
+        }
+        return HM_OK;
+    } catch (const std::exception& e) {
+        return to_status(e);
+    }
 }
 
 void hm_free(hm_handle h)

@@ -119,6 +119,12 @@ int aca_shape(int cls);
 int aca_default_shape(int cls);
 // Iteration limit handed to the ACA kernels (0: none beyond k + n + 1).
 int aca_step_limit();
+// Test hooks of the product's bulk-copy kernels: the wait bound in ns and the
+// withheld chunk (-1: none); applied to a plan by mvp_hooks.
+uint64_t mvp_wait_ns();
+int mvp_withhold();
+void set_mvp_wait_ns(uint64_t ns);
+void set_mvp_withhold(int k);
 void set_aca_shape(int cls, int shape);
 void set_aca_step_limit(int v);
 
@@ -211,6 +217,11 @@ struct MvpPlan {
     const int3* items = nullptr;
     const int64_t* item_ptr = nullptr;
     int* status = nullptr;                // device status word (bounded waits)
+    // bound of every mbarrier wait of the bulk-copy kernels, and a chunk that
+    // their producer leaves out (-1: none); test hooks of the timeout path,
+    // set per product from hm_set_test_hook
+    uint64_t wait_ns = 2000000000ull;
+    int withhold = -1;
     // row tiles and their gather lists (CSR over tiles)
     int64_t n_tiles = 0;
     int max_ld = 0;                       // slice_ld of the largest tile

@@ -158,6 +158,21 @@ void rect_matvec(hm_handle_s& h, const double* x, double* y, int nrhs, cudaStrea
 
 }  // namespace
 
+// A product whose results go to host memory waits for them anyway; it then
+// also reads the handle's status word (a bounded wait of the product that
+// gave up) and reports it as HM_ETIMEOUT.
+static void sync_and_check(hm_handle_s& h, cudaStream_t s)
+{
+    int st = 0;
+    HM_CUDA(cudaMemcpyAsync(&st, h.status.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HM_CUDA(cudaStreamSynchronize(s));
+    if (st) {
+        HM_CUDA(cudaMemsetAsync(h.status.p, 0, sizeof(int), s));
+        HM_CUDA(cudaStreamSynchronize(s));
+        fail(HM_ETIMEOUT, "a bounded wait of the product gave up (status " + std::to_string(st) + ")");
+    }
+}
+
 void matvec(hm_handle_s& h, const double* x, double* y, int nrhs, cudaStream_t s)
 {
     if (h.opt.structure_only) fail(HM_EINVAL, "the handle was built with structure_only");
@@ -199,7 +214,7 @@ void matvec(hm_handle_s& h, const double* x, double* y, int nrhs, cudaStream_t s
             mvp_run_multi(h.plan, h.work, xin, yout, nr, h.opt.accumulate, s);
             if (!yd) copy_out(y + (int64_t)c * N, h.ybuf.p, bytes, s);
         }
-        if (!yd) HM_CUDA(cudaStreamSynchronize(s));
+        if (!yd) sync_and_check(h, s);
         return;
     }
     for (int r = 0; r < nrhs; ++r) {
@@ -219,7 +234,7 @@ void matvec(hm_handle_s& h, const double* x, double* y, int nrhs, cudaStream_t s
         else mvp_run(h.plan, h.work, xin, yout, h.opt.accumulate, s, h.opt.profile ? &h.timer : nullptr);
         if (!yd) copy_out(yr, h.ybuf.p, N * sizeof(double), s);
     }
-    if (!yd) HM_CUDA(cudaStreamSynchronize(s));
+    if (!yd) sync_and_check(h, s);
 }
 
 void export_structure(hm_handle_s& h, uint64_t* codes, int64_t* perm, int64_t* adm,

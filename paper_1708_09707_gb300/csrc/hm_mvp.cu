@@ -332,13 +332,14 @@ k_tile_tma(MvpPlan P, const R* __restrict__ xm, const R* __restrict__ t, double*
             int k = 0;
             for (; k < nch; ++k) {
                 const int slot = k % TS;
-                if (k >= TS && !mbar_wait(&empty[slot], ((k / TS) - 1) & 1)) {
+                if (k >= TS && !mbar_wait(&empty[slot], ((k / TS) - 1) & 1, P.wait_ns)) {
                     atomicOr(P.status, 4);
                     break;
                 }
                 bool isu;
                 int64_t c0;
                 int cnt;
+                if (k == P.withhold) continue;   // test hook: this chunk never arrives
                 chunk(k, isu, c0, cnt);
                 const uint32_t bytes = (uint32_t)(cnt * (isu ? ucolb : ncolb));
                 const char* src = isu
@@ -353,7 +354,9 @@ k_tile_tma(MvpPlan P, const R* __restrict__ xm, const R* __restrict__ t, double*
             // chunks issued can still be in flight, and a wait on a phase
             // that has completed returns at once
             for (int q = (k > TS ? k - TS : 0); q < k; ++q)
-                if (!mbar_wait(&full[q % TS], (q / TS) & 1)) atomicOr(P.status, 4);
+                if (q != P.withhold &&
+                    !mbar_wait(&full[q % TS], (q / TS) & 1, P.wait_ns > MBAR_DRAIN_NS ? P.wait_ns : MBAR_DRAIN_NS))
+                    atomicOr(P.status, 4);
         }
     } else {
         // ---------------- consumers: half-warp hw = 2w + (lane >> 4)
@@ -383,7 +386,7 @@ k_tile_tma(MvpPlan P, const R* __restrict__ xm, const R* __restrict__ t, double*
             const R mnext = fetch(k + 1);
             // the whole warp gives up together, so the shuffles below never
             // name a lane that has left
-            if (!__all_sync(0xffffffffu, mbar_wait(&full[slot], (k / TS) & 1))) {
+            if (!__all_sync(0xffffffffu, mbar_wait(&full[slot], (k / TS) & 1, P.wait_ns))) {
                 if (lane == 0) atomicOr(P.status, 4);
                 failed = 1;
                 break;
@@ -1129,9 +1132,22 @@ int mvp_force_shape(int shape)
     return HM_OK;
 }
 
-void mvp_run(const MvpPlan& P, MvpWork& W, const double* x, double* y, int accumulate,
+namespace {
+std::atomic<uint64_t> g_wait_ns{2000000000ull};
+std::atomic<int> g_withhold{-1};
+}  // namespace
+
+uint64_t mvp_wait_ns() { return g_wait_ns.load(); }
+int mvp_withhold() { return g_withhold.load(); }
+void set_mvp_wait_ns(uint64_t ns) { g_wait_ns = ns ? ns : 2000000000ull; }
+void set_mvp_withhold(int k) { g_withhold = k; }
+
+void mvp_run(const MvpPlan& P0, MvpWork& W, const double* x, double* y, int accumulate,
              cudaStream_t s, MvpTimer* timer)
 {
+    MvpPlan P = P0;
+    P.wait_ns = mvp_wait_ns();
+    P.withhold = mvp_withhold();
     if (P.precision == HM_PREC_FP64) {
         run_typed<double, HM_NEAR_FP64>(P, W.xm64.p, W.t64.p, W.tp64.p, W.part.p, x, y, accumulate, s, timer);
         return;

@@ -333,13 +333,14 @@ k_tile_n(MvpPlan P, const float* __restrict__ xm, const float* __restrict__ t,
             int k = 0;
             for (; k < nch; ++k) {
                 const int slot = k % TN_STAGES;
-                if (k >= TN_STAGES && !mbar_wait(&empty[slot], ((k / TN_STAGES) - 1) & 1)) {
+                if (k >= TN_STAGES && !mbar_wait(&empty[slot], ((k / TN_STAGES) - 1) & 1, P.wait_ns)) {
                     atomicOr(P.status, 4);
                     break;
                 }
                 bool isu;
                 int64_t c0;
                 int cnt;
+                if (k == P.withhold) continue;   // test hook: this chunk never arrives
                 chunk(k, isu, c0, cnt);
                 const uint32_t bytes = (uint32_t)(cnt * (isu ? ucolb : ncolb));
                 const char* src = isu
@@ -351,7 +352,9 @@ k_tile_n(MvpPlan P, const float* __restrict__ xm, const float* __restrict__ t,
             }
             // every copy issued lands before the CTA exits (see k_tile_tma)
             for (int q = (k > TN_STAGES ? k - TN_STAGES : 0); q < k; ++q)
-                if (!mbar_wait(&full[q % TN_STAGES], (q / TN_STAGES) & 1)) atomicOr(P.status, 4);
+                if (q != P.withhold &&
+                    !mbar_wait(&full[q % TN_STAGES], (q / TN_STAGES) & 1, P.wait_ns > MBAR_DRAIN_NS ? P.wait_ns : MBAR_DRAIN_NS))
+                    atomicOr(P.status, 4);
         }
     } else {
         // ---------------- consumers
@@ -389,7 +392,7 @@ k_tile_n(MvpPlan P, const float* __restrict__ xm, const float* __restrict__ t,
         for (int k = 0; k < nch; ++k) {
             const int slot = k % TN_STAGES;
             mf = fetch(k + 1);
-            const bool ok = __all_sync(0xffffffffu, mbar_wait(&full[slot], (k / TN_STAGES) & 1));
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(&full[slot], (k / TN_STAGES) & 1, P.wait_ns));
             if (ok) {
                 if (act) {
                     bool isu;
@@ -528,9 +531,12 @@ bool mvp_multi_fused(const MvpPlan& P)
             P.near_format == HM_NEAR_BF16X2);
 }
 
-void mvp_run_multi(const MvpPlan& P, MvpWork& W, const double* x, double* y, int nrhs,
+void mvp_run_multi(const MvpPlan& P0, MvpWork& W, const double* x, double* y, int nrhs,
                    int accumulate, cudaStream_t s)
 {
+    MvpPlan P = P0;
+    P.wait_ns = mvp_wait_ns();
+    P.withhold = mvp_withhold();
     const int64_t N = P.Ntot;
     if (!mvp_multi_fused(P)) {
         for (int r = 0; r < nrhs; ++r)

@@ -45,7 +45,11 @@ __device__ __forceinline__ float2 bf2(uint32_t u)
     return __bfloat1622float2(h);
 }
 
-constexpr uint64_t MBAR_LIMIT_NS = 2000000000ull;   // a wait gives up after 2 s
+
+// The producer's last waits, for copies it has issued, use at least this
+// bound whatever the bound of the other waits: a CTA never exits while a
+// bulk copy into its shared memory may be in flight.
+constexpr uint64_t MBAR_DRAIN_NS = 2000000000ull;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p)
 {
@@ -72,8 +76,8 @@ __device__ __forceinline__ uint64_t global_ns()
     return t;
 }
 // Wait for the phase of the given parity to complete; false once the wait
-// has lasted MBAR_LIMIT_NS (each try_wait itself suspends for a bounded time).
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity)
+// has lasted limit_ns (each try_wait itself suspends for a bounded time).
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, uint64_t limit_ns)
 {
     uint64_t t0 = 0;
     for (int k = 0;; ++k) {
@@ -86,7 +90,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity)
             : "memory");
         if (ok) return true;
         if (k == 0) t0 = global_ns();
-        else if (global_ns() - t0 > MBAR_LIMIT_NS) return false;
+        else if (global_ns() - t0 > limit_ns) return false;
     }
 }
 // Global -> shared bulk copy of bytes (a multiple of 16, both addresses

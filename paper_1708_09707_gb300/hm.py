@@ -98,6 +98,9 @@ def _declare(L):
     L.hm_set_gather_shape.argtypes = [C.c_int]
     L.hm_set_aca_shape.argtypes = [C.c_int, C.c_int]
     L.hm_set_test_hook.argtypes = [C.c_int, C.c_int64]
+    L.hm_check_status.argtypes = [_vp]
+    L.hm_device_bytes.restype = C.c_uint64
+    L.hm_device_bytes.argtypes = []
     L.hm_alu_peak.argtypes = [C.c_int, C.POINTER(C.c_double)]
     L.hm_build_ex.restype = _vp
     L.hm_build_ex.argtypes = [_vp, i64, C.c_int, C.c_int, _vp, C.c_int, C.c_double,
@@ -240,6 +243,11 @@ class HMatrix:
                 y = np.empty((self.n,) if x.ndim == 1 else (nrhs, self.n))
         _check(lib().hm_matvec_ex(self._h, _ptr(x), _ptr(y), nrhs, _stream_ptr(stream)))
         return y
+
+    def check_status(self) -> None:
+        """hm_check_status: raise HMError(HM_ETIMEOUT) if a bounded device
+        loop or wait of an earlier call gave up."""
+        _check(lib().hm_check_status(self._h))
 
     def stats(self) -> dict:
         s = Stats()
@@ -392,12 +400,17 @@ def set_aca_shape(cls: int, shape: int) -> None:
     _check(lib().hm_set_aca_shape(int(cls), int(shape)))
 
 
-HOOK_ACA_STEP_LIMIT = 0
+HOOK_ACA_STEP_LIMIT, HOOK_WAIT_LIMIT_NS, HOOK_GATHER_WITHHOLD, HOOK_FAIL_ALLOC = 0, 1, 2, 3
 
 
 def set_test_hook(hook: int, value: int) -> None:
     """hm_set_test_hook: a test hook of the failure paths (0 restores the default)."""
     _check(lib().hm_set_test_hook(int(hook), int(value)))
+
+
+def device_bytes() -> int:
+    """hm_device_bytes: device bytes the library holds right now."""
+    return int(lib().hm_device_bytes())
 
 
 def kernel_launches() -> int:

@@ -88,3 +88,37 @@ def test_fullsize_sampled_rows(hm, orc):
         e = np.linalg.norm(y[rows] - yb) / np.linalg.norm(yb)
         assert e <= 10 * w["eps"], (prec, e)
         H.free()
+
+
+def test_timed_configuration_parity(hm, orc):
+    # exactly the configuration bench.py times: the clipped mixture at
+    # N = 2^20, mixed precision, symmetric mode, the learned rank model
+    # trained as the bench trains it; 256 sampled rows against the exact sums
+    # (Neumaier-compensated FP64 brute force), and the whole product against
+    # the FP64 GPU build, whose parity with the oracle the smaller cases pin
+    from paper_1708_09707_gb300 import rank_model
+    name = "mix2d_n1m"
+    w = inputs.WORKLOADS[name]
+    pts = inputs.workload_points(name)
+    x = inputs.normal_vector(w["n"], inputs.X_SEED)
+    F, T = rank_model.training_data()
+    theta, _ = rank_model.train(F, T)
+    H = hm.HMatrix(pts, w["kernel"], w["ell"], w["leaf"], w["eta"], w["eps"],
+                   precision=hm.PREC_MIXED, symmetric=True, rank_model_theta=theta)
+    y = H.matvec(x)
+    st = H.stats()
+    H.free()
+    assert st["n_mispredicted"] < 0.01 * st["n_adm"]
+    rows = np.sort(np.random.default_rng(1).choice(w["n"], 256, replace=False))
+    yb = orc.dense_rows(pts, w["kernel"], w["ell"], 0.0, rows, x)
+    e_rows = np.linalg.norm(y[rows] - yb) / np.linalg.norm(yb)
+    assert e_rows <= 1e-5, e_rows
+    H64 = hm.HMatrix(pts, w["kernel"], w["ell"], w["leaf"], w["eta"], w["eps"],
+                     precision=hm.PREC_FP64)
+    y64 = H64.matvec(x)
+    H64.free()
+    e64 = np.linalg.norm(y - y64) / np.linalg.norm(y64)
+    assert e64 <= 1e-5, e64
+    # the FP64 build itself against the exact rows, at the accuracy eps asks
+    e64_rows = np.linalg.norm(y64[rows] - yb) / np.linalg.norm(yb)
+    assert e64_rows <= 10 * w["eps"], e64_rows
