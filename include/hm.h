@@ -110,6 +110,20 @@ typedef struct hm_options {
                              on the pass count to rounding). Not with
                              rank_model or hm_build_batch; several right-hand
                              sides run one product each. Default 0. */
+    int64_t row_lo, row_hi; /* block-row share of one H-matrix (distributed
+                             H-matrices, the outlook of Sec. 7), Morton-order
+                             rows [row_lo, row_hi): keep only the leaves whose
+                             row cluster meets the range (in symmetric mode
+                             also the canonical partners of kept mirror
+                             leaves), so that the build compresses and stores
+                             only those and the product computes every row of
+                             the range exactly as the whole H-matrix does, bit
+                             for bit. Rows outside the range then hold
+                             incomplete sums: the caller keeps the rows of its
+                             range (hm_export_structure's permutation maps
+                             Morton rows to points). row_hi <= 0: all rows
+                             (default). One point set only (not with
+                             hm_build_rect or hm_build_batch). */
 } hm_options;
 
 typedef struct hm_handle_s* hm_handle;

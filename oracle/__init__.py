@@ -112,6 +112,7 @@ def _declare(L):
     L.or_get_factors.argtypes = [C.c_void_p, C.c_int64, _d, _d]
     L.or_get_pivots.argtypes = [C.c_void_p, C.c_int64, _i64, _i64]
     L.or_matvec.argtypes = [C.c_void_p, _d, _d]
+    L.or_matvec_rows.argtypes = [C.c_void_p, _d, C.c_int64, C.c_int64, _d]
     L.or_dense_matvec.argtypes = [_d, C.c_int64, C.c_int, C.c_int, _d, _d, _d]
     L.or_dense_rows.argtypes = [_d, C.c_int64, C.c_int, C.c_int, _d, _i64,
                                 C.c_int64, _d, _d]
@@ -371,6 +372,14 @@ class HMatrix:
         x = _f64(x)
         y = np.zeros(self.n)
         lib().or_matvec(self._h, _p(x), _p(y))
+        return y
+
+    def matvec_rows(self, xm, r0: int, r1: int):
+        """Rows [r0, r1) of the Morton-ordered product from the Morton-ordered
+        x_m, from the leaves that touch them (a block-row share)."""
+        xm = _f64(xm)
+        y = np.zeros(max(r1 - r0, 0))
+        lib().or_matvec_rows(self._h, _p(xm), r0, r1, _p(y))
         return y
 
     def cg(self, b, rtol: float = 1e-6, maxit: int = 1000, x0=None):

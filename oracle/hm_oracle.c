@@ -878,6 +878,65 @@ void or_matvec(const or_hmat* h, const double* x, double* y)
     free(ym);
 }
 
+/* Block-row share of the product (distributed H-matrices, the outlook of   */
+/* Sec. 7): the Morton-ordered rows [r0, r1) of y_m = H x_m (+ sigma^2 x_m), */
+/* from the Morton-ordered x_m, using only the leaves whose row cluster tau  */
+/* meets [r0, r1), in the canonical order of or_matvec. Every leaf that      */
+/* touches a row in the range is among them, and each row receives the same  */
+/* sums in the same order as in or_matvec, so the rows are bit for bit those */
+/* of the whole product.                                                      */
+void or_matvec_rows(const or_hmat* h, const double* xm, int64_t r0, int64_t r1, double* yr)
+{
+    int64_t N = h->N;
+    int d = h->d;
+    if (r0 < 0) r0 = 0;
+    if (r1 > N) r1 = N;
+    if (r1 <= r0) return;
+    double* ym = (double*)calloc((size_t)(r1 - r0), sizeof(double));
+    double* t = (double*)malloc(64 * sizeof(double));
+    int tcap = 64;
+    for (int64_t b = 0; b < h->n_adm; ++b) {
+        int64_t t0 = h->lo[h->adm[b].tau], m = h->hi[h->adm[b].tau] - t0;
+        int64_t s0 = h->lo2[h->adm[b].sigma], n = h->hi2[h->adm[b].sigma] - s0;
+        int r = h->rank[b];
+        if (r <= 0 || t0 + m <= r0 || t0 >= r1) continue;
+        if (r > tcap) {
+            tcap = r;
+            t = (double*)realloc(t, (size_t)tcap * sizeof(double));
+        }
+        const double* U = h->Ust + h->offU[b];
+        const double* V = h->Vst + h->offV[b];
+        for (int l = 0; l < r; ++l) {
+            double s = 0.0;
+            for (int64_t j = 0; j < n; ++j) s = s + V[l * n + j] * xm[s0 + j];
+            t[l] = s;
+        }
+        for (int64_t i = 0; i < m; ++i) {
+            if (t0 + i < r0 || t0 + i >= r1) continue;
+            double s = 0.0;
+            for (int l = 0; l < r; ++l) s = s + U[l * m + i] * t[l];
+            ym[t0 + i - r0] = ym[t0 + i - r0] + s;
+        }
+    }
+    for (int64_t b = 0; b < h->n_dense; ++b) {
+        int64_t t0 = h->lo[h->dense[b].tau], m = h->hi[h->dense[b].tau] - t0;
+        int64_t s0 = h->lo2[h->dense[b].sigma], n = h->hi2[h->dense[b].sigma] - s0;
+        if (t0 + m <= r0 || t0 >= r1) continue;
+        for (int64_t i = 0; i < m; ++i) {
+            if (t0 + i < r0 || t0 + i >= r1) continue;
+            double s = 0.0;
+            for (int64_t j = 0; j < n; ++j)
+                s = s + or_kernel_eval(h->kernel, h->ell, h->coords + (t0 + i) * d,
+                                       h->coords2 + (s0 + j) * d, d) * xm[s0 + j];
+            ym[t0 + i - r0] = ym[t0 + i - r0] + s;
+        }
+    }
+    for (int64_t i = r0; i < r1; ++i)
+        yr[i - r0] = h->rect ? ym[i - r0] : ym[i - r0] + h->sigma2 * xm[i];
+    free(t);
+    free(ym);
+}
+
 /* Brute-force truth: y_i = sum_j phi(y_i, y_j) x_j + sigma^2 x_i with       */
 /* Neumaier-compensated summation over j.                                    */
 static double or_neumaier_row(const double* pts, int64_t N, int d, int kernel,

@@ -141,6 +141,10 @@ void or_get_pivots(const or_hmat* h, int64_t b, int64_t* piv_i, int64_t* piv_j);
 
 /* Alg. 3: y = H x (+ sigma^2 x), x and y in the caller's point order. */
 void or_matvec(const or_hmat* h, const double* x, double* y);
+/* Rows [r0, r1) of the Morton-ordered product from the Morton-ordered x_m,
+ * from the leaves that touch them (block-row share; bit for bit or_matvec's
+ * rows). */
+void or_matvec_rows(const or_hmat* h, const double* xm, int64_t r0, int64_t r1, double* yr);
 
 /* Brute force y_i = sum_j phi(y_i, y_j) x_j + sigma^2 x_i (Neumaier sums). */
 void or_dense_matvec(const double* pts, int64_t N, int d, int kernel,

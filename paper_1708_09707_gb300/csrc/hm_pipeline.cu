@@ -114,6 +114,48 @@ __global__ void k_classes(const Blk* __restrict__ blk, const uint32_t* __restric
     atomicAdd((unsigned long long*)&cls_count[c * ACA_NKB + kb], 1ull);
 }
 
+// Block-row share (hm_options.row_lo / row_hi): leaf (tau, sigma) stays when
+// tau meets the rows [r0, r1), or, in symmetric mode, when it is canonical
+// (tau.lo <= sigma.lo) and sigma meets them (the partner of a kept mirror
+// leaf).
+__global__ void k_row_keep(const int2* __restrict__ pairs, int64_t n,
+                           const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
+                           int64_t r0, int64_t r1, int sym, int64_t* __restrict__ keep)
+{
+    int64_t b = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (b >= n) return;
+    const int2 p = pairs[b];
+    const bool rows = lo[p.x] < r1 && hi[p.x] > r0;
+    const bool partner = sym && lo[p.x] <= lo[p.y] && lo[p.y] < r1 && hi[p.y] > r0;
+    keep[b] = (rows || partner) ? 1 : 0;
+}
+
+__global__ void k_row_compact(const int2* __restrict__ in, int64_t n,
+                              const int64_t* __restrict__ keep, const int64_t* __restrict__ off,
+                              int2* __restrict__ out)
+{
+    int64_t b = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (b < n && keep[b]) out[off[b]] = in[b];
+}
+
+// Keep the leaves of a block-row share, in their canonical order.
+int64_t row_filter(DevBuf<int2>& pairs, int64_t n, const int32_t* lo, const int32_t* hi,
+                   int64_t r0, int64_t r1, int sym, cudaStream_t s)
+{
+    if (n == 0) return 0;
+    DevBuf<int64_t> keep(n, s), off(n + 1, s);
+    k_row_keep<<<grid_for(n), NT, 0, s>>>(pairs.p, n, lo, hi, r0, r1, sym, keep.p); note_launch();
+    scan_exclusive_i64(keep.p, off.p, n, off.p + n, s);
+    int64_t cnt = 0;
+    HM_CUDA(cudaMemcpyAsync(&cnt, off.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    HM_CUDA(cudaStreamSynchronize(s));
+    DevBuf<int2> out(std::max<int64_t>(cnt, 1), s);
+    k_row_compact<<<grid_for(n), NT, 0, s>>>(pairs.p, n, keep.p, off.p, out.p); note_launch();
+    HM_LAUNCH("row share");
+    pairs = std::move(out);
+    return cnt;
+}
+
 // Symmetric kernels: leaf b is canonical when its rows start no later than
 // its columns; the others are mirrors of a canonical leaf, marked in flags
 // (no ACA of their own, no reservation; they still count in the product).
@@ -926,6 +968,12 @@ void validate(int nsets, const int64_t* N, const int* d, int kernel, const doubl
         tot += N[q];
     }
     if (tot >= (1ll << 31)) fail(HM_EINVAL, "more than 2^31 points");
+    if (o.row_hi > 0) {
+        if (rect || nsets != 1)
+            fail(HM_ENOTSUP, "a block-row share (row_lo, row_hi) is for one point set");
+        if (o.row_lo < 0 || o.row_lo >= o.row_hi || o.row_hi > N[0])
+            fail(HM_EINVAL, "row range must satisfy 0 <= row_lo < row_hi <= N");
+    }
     if (o.on_the_fly && (o.rank_model || (nsets > 1 && !rect)))
         fail(HM_ENOTSUP, "on_the_fly runs without rank_model and batches");
     if (rect) {
@@ -1033,6 +1081,15 @@ void build_sets(hm_handle_s& h, int nsets, const double* points_all, const int64
             build_structure(p, S, eta, opt.adm_max, h.X, h.perm.p, h.codes.p + S.row0,
                             h.node_lo.p, h.node_hi.p, h.bmin.p, h.bmax.p, adm[q], dense[q], s);
             p += S.N * S.d;
+            if (opt.row_hi > 0) {
+                // block-row share: the leaves whose rows meet [row_lo, row_hi)
+                const int32_t* lo = h.node_lo.p + S.node0;
+                const int32_t* hi = h.node_hi.p + S.node0;
+                S.n_adm = row_filter(adm[q], S.n_adm, lo, hi, opt.row_lo, opt.row_hi,
+                                     opt.symmetric, s);
+                S.n_dense = row_filter(dense[q], S.n_dense, lo, hi, opt.row_lo, opt.row_hi,
+                                       opt.symmetric, s);
+            }
             h.n_adm += S.n_adm;
             h.n_dense += S.n_dense;
         }

@@ -38,7 +38,7 @@ class Options(C.Structure):
                 ("rank_model_theta", C.c_void_p), ("scratch_gb", C.c_double),
                 ("stream", C.c_void_p), ("profile", C.c_int),
                 ("structure_only", C.c_int), ("symmetric", C.c_int),
-                ("on_the_fly", C.c_int)]
+                ("on_the_fly", C.c_int), ("row_lo", C.c_int64), ("row_hi", C.c_int64)]
 
 
 class Stats(C.Structure):
@@ -164,7 +164,7 @@ def _stream_ptr(stream):
 def options(precision=PREC_FP64, near_format=NEAR_AUTO, adm_max=False, k_cap=64,
             aca_eta=0.0, eps0=0.0, accumulate=False, rank_model_theta=None,
             scratch_gb=0.0, stream=None, profile=False, symmetric=False,
-            structure_only=False, on_the_fly=False) -> Options:
+            structure_only=False, on_the_fly=False, row_range=None) -> Options:
     o = Options()
     lib().hm_options_default(C.byref(o))
     o.precision = precision
@@ -182,6 +182,8 @@ def options(precision=PREC_FP64, near_format=NEAR_AUTO, adm_max=False, k_cap=64,
     o.symmetric = int(symmetric)
     o.structure_only = int(structure_only)
     o.on_the_fly = int(on_the_fly)
+    if row_range is not None:
+        o.row_lo, o.row_hi = int(row_range[0]), int(row_range[1])
     return o
 
 

@@ -29,12 +29,42 @@ def test_library_exports_every_declared_symbol():
     assert not missing, missing
 
 
+def _c_layout():
+    import os
+    import subprocess
+    import tempfile
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = r"""
+#include <stddef.h>
+#include <stdio.h>
+#include "hm.h"
+int main(void) {
+    printf("sizeof_options %zu\n", sizeof(hm_options));
+    printf("off_stream %zu\n", offsetof(hm_options, stream));
+    printf("off_on_the_fly %zu\n", offsetof(hm_options, on_the_fly));
+    printf("off_row_lo %zu\n", offsetof(hm_options, row_lo));
+    printf("off_row_hi %zu\n", offsetof(hm_options, row_hi));
+    return 0;
+}
+"""
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "layout.c")
+        exe = os.path.join(d, "layout")
+        open(c, "w").write(src)
+        subprocess.run(["gcc", "-I", os.path.join(root, "include"), c, "-o", exe], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout
+    return {k: int(v) for k, v in (line.split() for line in out.splitlines())}
+
+
 def test_options_and_stats_layout():
     from paper_1708_09707_gb300 import hm
     o = hm.options()
     assert o.k_cap == 64 and o.precision == hm.PREC_FP64
-    # struct sizes match the C layout (offsets are natural alignment)
-    assert ctypes.sizeof(hm.Options) == 80
+    # struct sizes and offsets match the C layout, as the C compiler lays it out
+    c = _c_layout()
+    assert ctypes.sizeof(hm.Options) == c["sizeof_options"] == 96
+    for f in ("stream", "on_the_fly", "row_lo", "row_hi"):
+        assert getattr(hm.Options, f).offset == c["off_" + f], f
     assert ctypes.sizeof(hm.Stats) == (8 * 5 + 4 * 2 + 8 + 8 + 8 * 9 + 8 * 4 + 4 * 3 + 4
                                        + 8 + 8 + 8 + 8 * 4 + 8 * 2 + 8 * 12 + 8 * 3)
 
