@@ -57,6 +57,8 @@ def parse():
     p.add_argument("--sweeps", action="store_true",
                    help="instead of the step: the paper's experiments as curves (Sec. 6.4 "
                         "convergence in k, Sec. 6.5 runtime against N), one JSON line")
+    p.add_argument("--no-large", action="store_true",
+                   help="skip the 2^22-point CG workload and the FP64 on-the-fly 3-D workload")
     p.add_argument("--no-rect", action="store_true",
                    help="skip the context run of A(Y1 x Y2) for two point sets")
     p.add_argument("--no-paper", action="store_true",
@@ -159,6 +161,97 @@ def otf_roofline(so, kernel, peak):
         out[k]["achieved"] = out[k]["flops"] / (ms * 1e-3) / 1e12 if ms > 0 else None
         out[k]["frac"] = out[k]["achieved"] / peak if out[k]["achieved"] else None
     return out
+
+
+def cg_workload(hm, inputs, theta, cg_iters=4, small_logs=(15,)):
+    """The 2^22-point solve: 3-D uniform points, Matern-3/2 l = 0.1, CG on
+    (A + 1e-2 I) x = b to 1e-6 with the product on the fly (stored, it needs
+    more memory than one GPU has), mixed precision, symmetric, the learned
+    rank model sizing the ACA passes. At 2^22 the build, one product and a few
+    CG iterations are timed (s per iteration); the whole solve is timed at
+    smaller N of the same workload, in FP64 (stored) and mixed (on the fly),
+    with the true residual of the mixed solution in the FP64 system."""
+    import torch
+    name = "matern3d_n4m_cg"
+    w = inputs.WORKLOADS[name]
+    n = w["n"]
+    pts = torch.from_numpy(inputs.workload_points(name)).cuda()
+    b = inputs.normal_vector(n, inputs.CG_SEED)
+    kw = dict(precision=hm.PREC_MIXED, on_the_fly=True, symmetric=True, sigma2=w["sigma2"],
+              rank_model_theta=theta)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    H = hm.HMatrix(pts, w["kernel"], w["ell"], w["leaf"], w["eta"], w["eps"], **kw)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    bd = torch.from_numpy(b).cuda()
+    t0 = time.perf_counter()
+    H.matvec(bd)
+    torch.cuda.synchronize()
+    product_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    _, it, rr = H.cg(b, rtol=w.get("rtol", 1e-6), maxit=cg_iters)
+    cg_s = time.perf_counter() - t0
+    st = H.stats()
+    H.free()
+    del pts, bd
+    out = {"workload": name, "n": n, "precision": "mixed, on the fly, symmetric, rank model",
+           "build_s": build_s, "product_s": product_s, "aca_passes": st["aca_passes"],
+           "n_adm": st["n_adm"], "n_dense": st["n_dense"],
+           "mispredicted_per_product": st["n_mispredicted"] / (2.0 + it),
+           "cg_iterations_timed": it, "cg_relres_after": rr,
+           "cg_s_per_iteration": cg_s / max(it, 1), "solves": []}
+    for lg in small_logs:
+        ns = 1 << lg
+        ps = torch.from_numpy(inputs.workload_points(name, ns)).cuda()
+        bs = inputs.normal_vector(ns, inputs.CG_SEED)
+        H64 = hm.HMatrix(ps, w["kernel"], w["ell"], w["leaf"], w["eta"], w["eps"],
+                         precision=hm.PREC_FP64, sigma2=w["sigma2"])
+        rec = {"n": ns}
+        for nm, H in (("fp64_stored", H64),
+                      ("mixed_on_the_fly", hm.HMatrix(ps, w["kernel"], w["ell"], w["leaf"], w["eta"],
+                                                      w["eps"], **kw))):
+            t0 = time.perf_counter()
+            x, it, rr = H.cg(bs, rtol=1e-6, maxit=50000)
+            dt = time.perf_counter() - t0
+            res = bs - H64.matvec(x)
+            rec[nm] = {"iterations": it, "relres": rr, "s": dt,
+                       "true_relres_fp64_system": float(np.linalg.norm(res) / np.linalg.norm(bs))}
+            if H is not H64:
+                H.free()
+        H64.free()
+        out["solves"].append(rec)
+    return out
+
+
+def fp64_on_the_fly(hm, inputs, n_mvp=2):
+    """The plain FP64 method on the 3-D Matern-3/2 workload at N = 2^20
+    (l = 0.2): its stored form does not fit one GPU (about 525 GB), so every
+    product recomputes ACA and the dense leaves; build and n_mvp products."""
+    import torch
+    name = "matern3d_n1m"
+    w = inputs.WORKLOADS[name]
+    pts = torch.from_numpy(inputs.workload_points(name)).cuda()
+    x = torch.from_numpy(inputs.normal_vector(w["n"], inputs.X_SEED)).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    H = hm.HMatrix(pts, w["kernel"], w["ell"], w["leaf"], w["eta"], w["eps"],
+                   precision=hm.PREC_FP64, on_the_fly=True, profile=True)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for _ in range(n_mvp):
+        H.matvec(x)
+    torch.cuda.synchronize()
+    mvp_s = (time.perf_counter() - t0) / n_mvp
+    st = H.stats()
+    H.free()
+    return {"workload": name, "n": w["n"], "precision": "fp64, on the fly (plain method)",
+            "build_s": build_s, "mvp_s": mvp_s, "products_timed": n_mvp,
+            "aca_passes": st["aca_passes"], "n_adm": st["n_adm"], "n_dense": st["n_dense"],
+            "aca_s_per_product": st["t_np_aca_ms"] / 1e3 / n_mvp,
+            "near_s_per_product": st["t_np_near_ms"] / 1e3 / n_mvp,
+            "lowrank_s_per_product": st["t_np_lowrank_ms"] / 1e3 / n_mvp}
 
 
 def rect_context(hm, inputs, w, rows, n_cols=1 << 19, n_mvp=3):
@@ -858,6 +951,14 @@ def main():
             Ho.free()
             del po, xo, yo
 
+    # the 2^22-point CG workload and the FP64 3-D Matern workload at 2^20,
+    # both on the fly (their stored forms do not fit one GPU)
+    cg5 = fp64_otf = None
+    if world == 1 and not args.no_large and theta is not None:
+        cg5 = cg_workload(hm, inputs, theta)
+    if world == 1 and not args.no_large:
+        fp64_otf = fp64_on_the_fly(hm, inputs)
+
     # A(Y1 x Y2): the step's points against 2^19 Halton points
     rect = None
     if world == 1 and not args.no_rect:
@@ -949,6 +1050,7 @@ def main():
         "fp64": fp64, "mixed_vs_fp64_rel_err": err,
         "mixed_without_rank_model": plain, "mixed_nonsymmetric": nonsym,
         "multi_rhs": multi, "on_the_fly": otf, "rectangular": rect,
+        "cg_matern3d_n4m": cg5, "fp64_on_the_fly_matern3d_n1m": fp64_otf,
         "rank_model": model_info,
         "speedup_vs_fp64": (fp64["ms_per_step"] / total) if fp64 else None,
         "e2e": {"value": e2e_ms / 1e3, "unit": "s/step (build + %d H-MVP)" % N_MVP,

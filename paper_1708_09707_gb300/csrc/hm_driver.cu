@@ -393,10 +393,21 @@ void cg_solve(hm_handle_s& h, const double* b, double* x, double rtol, int maxit
         k_cg_xr<<<grid_for(n), NT, 0, s>>>(sc.p, p.p, q.p, n, xd.p, r.p); note_launch();
         dot(r.p, r.p, n, sc.p + 2, part.p, s);
         k_cg_p<<<grid_for(n), NT, 0, s>>>(sc.p, r.p, n, p.p); note_launch();
+        double got[3];
         HM_CUDA(cudaMemcpyAsync(sc.p, sc.p + 2, sizeof(double), cudaMemcpyDeviceToDevice, s));
-        HM_CUDA(cudaMemcpyAsync(&rr, sc.p + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
+        HM_CUDA(cudaMemcpyAsync(got, sc.p, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
         HM_CUDA(cudaStreamSynchronize(s));
+        rr = got[2];
         ++it;
+        // p^T (H + sigma^2 I) p <= 0: the operator is not positive definite
+        // along p (its approximation error exceeds the diagonal shift), and
+        // the iteration has no meaning beyond this point
+        if (!(got[1] > 0.0)) {
+            if (iters) *iters = it;
+            if (relres) *relres = std::sqrt(rr) / bn;
+            fail(HM_EINVAL, "CG: p^T (H + sigma^2 I) p <= 0 at iteration " + std::to_string(it) +
+                                ": the H-matrix plus sigma^2 I is not positive definite");
+        }
     }
     copy_out(x, xd.p, n * sizeof(double), s);
     HM_CUDA(cudaStreamSynchronize(s));

@@ -70,6 +70,8 @@ struct hm_handle_s {
     hm::DevBuf<char> np_scratch, np_t, np_xm;
     hm::DevBuf<double> np_yacc, np_part;   // row sums; near-field item sums
     int np_kcap = 0, np_ld = 0;             // t entries per leaf; rows per item sum
+    hm::DevBuf<int32_t> np_kpred;           // rank model: predicted ranks per leaf
+    int64_t np_mispredicted = 0;            // re-run blocks, summed over products
     // V^T x items and apply items of the low-rank part, the t partials of a
     // pass and the apply items' running row sums
     hm::DevBuf<int64_t> np_vptr, np_aptr;

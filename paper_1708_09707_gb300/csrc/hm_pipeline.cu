@@ -668,6 +668,32 @@ __global__ void k_full_reserve(const Blk* __restrict__ blk, int64_t n, int kcap,
     res[b] = (int64_t)min(kcap, min(B.m, B.n)) * (B.m + B.n);
 }
 
+__global__ void k_pred_reserve(const Blk* __restrict__ blk, int64_t n, int kcap,
+                               const int32_t* __restrict__ kpred, int64_t* __restrict__ res)
+{
+    const int64_t b = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (b >= n) return;
+    const Blk B = blk[b];
+    const int full = min(kcap, min(B.m, B.n));
+    res[b] = (int64_t)max(1, min(kpred[b], full)) * (B.m + B.n);
+}
+
+// Blocks of ids[0..n) whose reservation was too small (flag bit 0).
+__global__ void k_np_mispred(const uint32_t* __restrict__ ids, int64_t n,
+                             const int32_t* __restrict__ flags, int64_t* __restrict__ f)
+{
+    const int64_t q = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (q < n) f[q] = (flags[ids[q]] & 1) ? 1 : 0;
+}
+
+__global__ void k_np_mispred_ids(const uint32_t* __restrict__ ids, int64_t n,
+                                 const int64_t* __restrict__ f, const int64_t* __restrict__ off,
+                                 uint32_t* __restrict__ out)
+{
+    const int64_t q = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (q < n && f[q]) out[off[q]] = ids[q];
+}
+
 // On-the-fly mode, at build time: passes of consecutive admissible leaves
 // (block order) whose full reservations min(k_cap, m, n) (m + n) fit the
 // scratch bound, and the buffers every product reuses.
@@ -683,7 +709,17 @@ void np_prepare(hm_handle_s& h)
     if (n > 0) {
         k_iota_u32<<<grid_for(n), NT, 0, s>>>(h.np_ids.p, n); note_launch();
         DevBuf<int64_t> res(n, s);
-        k_full_reserve<<<grid_for(n), NT, 0, s>>>(h.ablk.p, n, h.opt.k_cap, res.p); note_launch();
+        if (h.opt.rank_model) {
+            // the learned model sizes every leaf's reservation (the passes
+            // then hold more leaves); a block whose prediction is too small
+            // is re-run inside its pass with the full reservation
+            h.np_kpred.alloc(n, s);
+            predict_ranks(h, h.np_kpred.p);
+            k_pred_reserve<<<grid_for(n), NT, 0, s>>>(h.ablk.p, n, h.opt.k_cap, h.np_kpred.p,
+                                                      res.p); note_launch();
+        } else {
+            k_full_reserve<<<grid_for(n), NT, 0, s>>>(h.ablk.p, n, h.opt.k_cap, res.p); note_launch();
+        }
         HM_LAUNCH("np reservations");
         std::vector<int64_t> hr(n);
         HM_CUDA(cudaMemcpyAsync(hr.data(), res.p, n * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -800,6 +836,35 @@ void rank_stats(hm_handle_s& h);
 // of its leaves into the scratch, then t_b = V_b^T x|sigma and y_m += U_b t_b;
 // then the dense leaves evaluated on the fly. Runs on the handle's stream,
 // ordered after and before stream s.
+// Rank model in the on-the-fly mode: the blocks of one pass (ids[0..n)) whose
+// predicted reservation was too small run again with the full one, in memory
+// of their own that lives until the product ends.
+void np_rerun(hm_handle_s& h, const uint32_t* ids, int64_t n, const AcaArgs& a, int esz,
+              std::vector<DevBuf<char>>& keep)
+{
+    cudaStream_t s = h.stream;
+    DevBuf<int64_t> f(n, s), off(n + 1, s);
+    k_np_mispred<<<grid_for(n), NT, 0, s>>>(ids, n, h.flags.p, f.p); note_launch();
+    scan_exclusive_i64(f.p, off.p, n, off.p + n, s);
+    int64_t cnt = 0;
+    HM_CUDA(cudaMemcpyAsync(&cnt, off.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    HM_CUDA(cudaStreamSynchronize(s));
+    if (cnt == 0) return;
+    h.np_mispredicted += cnt;
+    DevBuf<uint32_t> mis(cnt, s);
+    k_np_mispred_ids<<<grid_for(n), NT, 0, s>>>(ids, n, f.p, off.p, mis.p); note_launch();
+    HM_LAUNCH("np mispredicted ids");
+    AcaOrder O;
+    aca_order(h, mis.p, cnt, nullptr, O);
+    DevBuf<char> mem((size_t)std::max<int64_t>(O.hpre[cnt], 1) * esz, s);
+    char* vbase = mem.p + O.hpreu[cnt] * esz;
+    k_set_ptrs<<<grid_for(cnt), NT, 0, s>>>(O.order.p, 0, cnt, O.pre.p, O.preu.p, mem.p, vbase,
+                                            esz, h.Uptr.p, h.Vptr.p); note_launch();
+    HM_LAUNCH("set ptrs");
+    aca_range(h, O, a, 0, cnt);
+    keep.push_back(std::move(mem));
+}
+
 void np_matvec(hm_handle_s& h, const double* x, double* y, int accumulate, cudaStream_t s)
 {
     cudaStream_t hs = h.stream;
@@ -830,19 +895,22 @@ void np_matvec(hm_handle_s& h, const double* x, double* y, int accumulate, cudaS
     };
     mark();
     const bool sym = h.opt.symmetric;
+    std::vector<DevBuf<char>> rerun_mem;   // factors of re-run blocks, kept to the end
     for (size_t q = 0; q < npass; ++q) {
         // the leaves compressed in this pass: its block range, or only the
         // canonical ones of it (symmetric)
         const int64_t c0 = sym ? h.np_cptr[q] : h.np_pass[q];
         const int64_t nb = (sym ? h.np_cptr[q + 1] : h.np_pass[q + 1]) - c0;
         if (nb > 0) {
+            const int32_t* kp = h.opt.rank_model ? h.np_kpred.p : nullptr;
             AcaOrder O;
-            aca_order(h, h.np_ids.p + c0, nb, nullptr, O);
+            aca_order(h, h.np_ids.p + c0, nb, kp, O);
             char* vbase = h.np_scratch.p + O.hpreu[nb] * esz;
             k_set_ptrs<<<grid_for(nb), NT, 0, hs>>>(O.order.p, 0, nb, O.pre.p, O.preu.p,
                                                      h.np_scratch.p, vbase, esz, h.Uptr.p, h.Vptr.p); note_launch();
             HM_LAUNCH("set ptrs");
             aca_range(h, O, a, 0, nb);
+            if (kp) np_rerun(h, h.np_ids.p + c0, nb, a, esz, rerun_mem);
         }
         if (sym) {
             // mirror leaves take their partners' factors (those of this pass
@@ -876,6 +944,7 @@ void np_matvec(hm_handle_s& h, const double* x, double* y, int accumulate, cudaS
         mark();
     }
     check_status(h);
+    h.stats.n_mispredicted = h.np_mispredicted;
     np_apply_finish(h.np_aptr.p, h.tile_row0.p, h.tile_m.p, h.n_tiles, h.np_ld, h.np_acc.p,
                     h.np_yacc.p, hs);
     mark();
@@ -974,8 +1043,9 @@ void validate(int nsets, const int64_t* N, const int* d, int kernel, const doubl
         if (o.row_lo < 0 || o.row_lo >= o.row_hi || o.row_hi > N[0])
             fail(HM_EINVAL, "row range must satisfy 0 <= row_lo < row_hi <= N");
     }
-    if (o.on_the_fly && (o.rank_model || (nsets > 1 && !rect)))
-        fail(HM_ENOTSUP, "on_the_fly runs without rank_model and batches");
+    if (o.on_the_fly && nsets > 1 && !rect) fail(HM_ENOTSUP, "on_the_fly runs without batches");
+    if (o.on_the_fly && o.rank_model && rect)
+        fail(HM_ENOTSUP, "the rank model needs one square point set");
     if (rect) {
         if (nsets != 2) fail(HM_EINVAL, "a rectangular matrix takes two point sets");
         if (d[0] != d[1]) fail(HM_EINVAL, "both point sets need the same dimension");

@@ -95,9 +95,64 @@ def test_mixed_matches_oracle_and_options(hm, orc):
 
 def test_refused_combinations(hm):
     pts = _pts(500, 2, "u", 41)
-    for kw in (dict(rank_model_theta=np.zeros(4801, np.float32)),):
-        with pytest.raises(hm.HMError):
-            hm.HMatrix(pts, 0, 0.1, 32, 1.0, 1e-6, precision=hm.PREC_MIXED, on_the_fly=True, **kw)
+    with pytest.raises(hm.HMError):
+        hm.HBatch([pts, pts], 0, 0.1, 32, 1.0, 1e-6, precision=hm.PREC_MIXED, on_the_fly=True)
+    with pytest.raises(hm.HMError):
+        hm.HMatrix(pts, 0, 0.1, 32, 1.0, 1e-6, cols=pts, precision=hm.PREC_MIXED,
+                   on_the_fly=True, rank_model_theta=np.zeros(4801, np.float32))
+
+
+@pytest.fixture(scope="module")
+def theta(hm):
+    from paper_1708_09707_gb300 import rank_model
+    F, T = rank_model.training_data()
+    th, _ = rank_model.train(F, T)
+    return th
+
+
+@pytest.mark.parametrize("sym", [False, True])
+def test_rank_model_on_the_fly(hm, orc, theta, sym):
+    # the learned model sizes each pass's reservations; blocks predicted too
+    # small run again inside their pass: the product is that of the stored
+    # build with the model, to the mixed bound against the oracle
+    n = 1 << 15
+    w = inputs.WORKLOADS["matern3d_n1m"]
+    pts = inputs.workload_points("matern3d_n1m", n)
+    x = inputs.normal_vector(n, inputs.X_SEED)
+    O = orc.HMatrix(pts, w["kernel"], w["ell"], w["leaf"], w["eta"], w["eps"], symmetric=sym)
+    yo = O.matvec(x)
+    kw = dict(precision=hm.PREC_MIXED, symmetric=sym, rank_model_theta=theta)
+    Hp = hm.HMatrix(pts, w["kernel"], w["ell"], w["leaf"], w["eta"], w["eps"], on_the_fly=True,
+                    scratch_gb=0.05, **kw)
+    Hf = hm.HMatrix(pts, w["kernel"], w["ell"], w["leaf"], w["eta"], w["eps"], on_the_fly=True,
+                    scratch_gb=0.05, symmetric=sym, precision=hm.PREC_MIXED)
+    assert Hp.stats()["aca_passes"] < Hf.stats()["aca_passes"]
+    y = Hp.matvec(x)
+    st = Hp.stats()
+    assert rel(y, yo) <= MIXED_TOL, rel(y, yo)
+    assert st["n_mispredicted"] <= 0.05 * st["n_adm"]
+    Hs = hm.HMatrix(pts, w["kernel"], w["ell"], w["leaf"], w["eta"], w["eps"],
+                    near_format=hm.NEAR_FP32, **kw)
+    assert rel(y, Hs.matvec(x)) <= 1e-6
+    for H in (Hp, Hf, Hs):
+        H.free()
+
+
+def test_rank_model_on_the_fly_forced_reruns(hm, orc):
+    # a model that predicts rank 1 for every block: nearly every block runs
+    # twice, and the product still meets the FP64 bound
+    n = 6000
+    pts = _pts(n, 2, "m", 43)
+    x = inputs.normal_vector(n, inputs.X_SEED)
+    th = np.zeros(4801, np.float32)
+    th[4800] = -4.0                      # yhat = -4: the smallest reservation
+    O = orc.HMatrix(pts, 0, 0.1, 64, 1.0, 1e-8)
+    H = hm.HMatrix(pts, 0, 0.1, 64, 1.0, 1e-8, on_the_fly=True, rank_model_theta=th)
+    y = H.matvec(x)
+    st = H.stats()
+    H.free()
+    assert rel(y, O.matvec(x)) <= FP64_TOL
+    assert st["n_mispredicted"] > 0.5 * st["n_adm"]
 
 
 def test_no_admissible_leaf_and_eta_zero(hm, orc):
