@@ -200,7 +200,8 @@ def cg_workload(hm, inputs, theta, cg_iters=4, small_logs=(15,)):
            "n_adm": st["n_adm"], "n_dense": st["n_dense"],
            "mispredicted_per_product": st["n_mispredicted"] / (2.0 + it),
            "cg_iterations_timed": it, "cg_relres_after": rr,
-           "cg_s_per_iteration": cg_s / max(it, 1), "solves": []}
+           "cg_s_per_iteration": cg_s / (it + 1),   # it iterations + the initial residual
+           "solves": []}
     for lg in small_logs:
         ns = 1 << lg
         ps = torch.from_numpy(inputs.workload_points(name, ns)).cuda()

@@ -223,6 +223,86 @@ __device__ __forceinline__ void two_sum_add(float2& s, float2& c, float2 v)
     s = t;
 }
 
+// ---------------------------------------------------------------- tensor cores
+// Near-field chunks in bfloat16 pairs run on the tensor cores (mma.sync
+// m16n8k16, bfloat16 operands, FP32 accumulation): the chunk's tile rows x 64
+// columns, each entry hi + lo, times the chunk's multipliers (64 columns x
+// NRC vectors), each split into three bfloat16 terms x = x1 + x2 + x3 (x1 the
+// rounding of x, x2 that of x - x1, x3 that of the rest: 24 bits of x). Five
+// products hi x1 + hi x2 + hi x3 + lo x1 + lo x2 carry every term above 2^-24
+// of the entry times the multiplier; each product of two bfloat16 numbers is
+// exact in FP32. Warp w takes the rows 16 (w mod 4) .. + 15 of every vector
+// of the group. Only for slices whose row count is a multiple of 8 (a column's
+// hi and lo halves then start on 16-byte boundaries, as ldmatrix needs).
+constexpr int XT_LD = TN_COL + 8;   // bf16 per row of a multiplier table (144 bytes)
+
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t addr, uint32_t (&r)[4])
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ void ldsm_x2(uint32_t addr, uint32_t (&r)[2])
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0, %1}, [%2];"
+                 : "=r"(r[0]), "=r"(r[1])
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2])
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, "
+        "{%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// Three bfloat16 terms of x (round to nearest each time).
+__device__ __forceinline__ void split3(float x, __nv_bfloat16& h1, __nv_bfloat16& h2,
+                                       __nv_bfloat16& h3)
+{
+    h1 = __float2bfloat16_rn(x);
+    const float r1 = x - __bfloat162float(h1);
+    h2 = __float2bfloat16_rn(r1);
+    h3 = __float2bfloat16_rn(r1 - __bfloat162float(h2));
+}
+
+// One near-field chunk on the tensor cores: rows 16 mi .. 16 mi + 15 of
+// NRC vectors (NT8 = NRC / 8 tiles of 8), accumulated into c[NT8][4].
+template <int NRC>
+__device__ __forceinline__ void chunk_mma(const unsigned char* st, int colb, int ld, int cnt,
+                                          const __nv_bfloat16 (*xt)[NRC][XT_LD], int mi, int lane,
+                                          float (&c)[NRC / 8][4])
+{
+    constexpr int NT8 = NRC / 8;
+    const int mat = lane >> 3, rr = lane & 7;
+    const int arow = 16 * mi + 8 * (mat & 1);           // this lane's 8-row block
+    const uint32_t abase = smem_addr(st) + (uint32_t)(arow * 2);
+    const int bn = lane & 7, bk = 8 * ((lane >> 3) & 1);   // lanes 0..15 address B
+#pragma unroll
+    for (int ks = 0; ks < TN_COL / 16; ++ks) {
+        if (16 * ks >= cnt) break;
+        const int acol = 16 * ks + rr + 8 * (mat >> 1);
+        uint32_t ahi[4], alo[4];
+        ldsm_x4_trans(abase + (uint32_t)(acol * colb), ahi);
+        ldsm_x4_trans(abase + (uint32_t)(acol * colb + 2 * ld), alo);
+#pragma unroll
+        for (int nt = 0; nt < NT8; ++nt) {
+            uint32_t b[3][2];
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+                ldsm_x2(smem_addr(&xt[q][8 * nt + bn][16 * ks + bk]), b[q]);
+            mma_bf16(c[nt], ahi, b[0]);
+            mma_bf16(c[nt], ahi, b[1]);
+            mma_bf16(c[nt], ahi, b[2]);
+            mma_bf16(c[nt], alo, b[0]);
+            mma_bf16(c[nt], alo, b[1]);
+        }
+    }
+}
+
 // Rows ir .. ir+3 of chunk column col as two packed row pairs.
 template <int FMT, bool ISU>
 __device__ __forceinline__ void stage_rows(const unsigned char* st, int col, int colb, int ir, int ld,
@@ -291,10 +371,13 @@ k_tile_n(MvpPlan P, const float* __restrict__ xm, const float* __restrict__ t,
     constexpr int STAGE = TN_COL * ncol_bytes64<FMT>();
     static_assert(16 * NG * TN_LANES == NCW * 32, "one consumer per (rows, group, lane)");
     static_assert(TN_COL * NG == NCW * 32, "one multiplier float4 per consumer");
-    static_assert(TN_LANES * TN_ROWS * NRC * 8 <= TN_STAGES * STAGE, "row sums fit the stages");
+    static_assert((TN_LANES + 1) * TN_ROWS * NRC * 8 <= TN_STAGES * STAGE, "row sums fit the stages");
+    constexpr int NT8 = NRC / 8;
     extern __shared__ __align__(128) unsigned char tsm[];
     __shared__ uint64_t full[TN_STAGES], empty[TN_STAGES];
     __shared__ __align__(16) float msm[2][2 * TN_COL * NRC];
+    // the tensor cores' multiplier tables (three bfloat16 terms per value)
+    __shared__ __align__(16) __nv_bfloat16 xt[FMT == HM_NEAR_BF16X2 ? 2 : 1][3][NRC][XT_LD];
     __shared__ int failed;
     const int64_t item = blockIdx.x;
     const int3 it = P.items[item];
@@ -310,6 +393,20 @@ k_tile_n(MvpPlan P, const float* __restrict__ xm, const float* __restrict__ t,
     const int nch = nuch + nnch;
     const int ucolb = ld * 4;
     const int ncolb = FMT == HM_NEAR_FP64 ? ld * 8 : ld * 4;
+    // near-field chunks on the tensor cores (bfloat16 pairs, slices of a
+    // multiple of 8 rows)
+    const bool tc = FMT == HM_NEAR_BF16X2 && (ld & 7) == 0;
+    if (tc) {
+        // a tensor-core chunk of fewer than 64 columns reads whole 16-column
+        // steps, and its columns past the chunk multiply zero multipliers:
+        // start from zeroed stages so that they hold finite values (later
+        // only earlier chunks' entries); the fence orders these writes before
+        // the bulk copies into the same memory
+        uint4* z = reinterpret_cast<uint4*>(tsm);
+        for (int e = threadIdx.x; e < TN_STAGES * STAGE / 16; e += blockDim.x)
+            z[e] = make_uint4(0u, 0u, 0u, 0u);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
     if (threadIdx.x == 0) {
         for (int k = 0; k < TN_STAGES; ++k) {
             mbar_init(&full[k], 1);
@@ -358,11 +455,11 @@ k_tile_n(MvpPlan P, const float* __restrict__ xm, const float* __restrict__ t,
         }
     } else {
         // ---------------- consumers
-        const int tc = threadIdx.x;
-        const int rq = tc & 15, g = (tc >> 4) % NG, j = tc / (16 * NG);
+        const int tc_id = threadIdx.x;
+        const int rq = tc_id & 15, g = (tc_id >> 4) % NG, j = tc_id / (16 * NG);
         const int ir = 4 * rq;
         const bool act = ir < ld;
-        const int fc = tc / NG, fg = tc % NG;   // the multiplier float4 this thread fetches
+        const int fc = tc_id / NG, fg = tc_id % NG;   // the multiplier float4 this thread fetches
         const float4* __restrict__ t4 = reinterpret_cast<const float4*>(t);
         const float4* __restrict__ x4 = reinterpret_cast<const float4*>(xm);
         auto fetch = [&](int k) -> float4 {
@@ -376,25 +473,77 @@ k_tile_n(MvpPlan P, const float* __restrict__ xm, const float* __restrict__ t,
             return isu ? t4[(int64_t)P.ucol_t[uc0 + c0 + fc] * NG + fg]
                        : x4[(int64_t)P.ncol_x[nc0 + c0 + fc] * NG + fg];
         };
-        auto publish = [&](int buf, float4 m) {
-            float4* d = reinterpret_cast<float4*>(msm[buf]) + 2 * tc;
+        // the next chunk's multipliers: a near chunk on the tensor cores
+        // takes them split into bfloat16 terms, any other chunk duplicated
+        // for the packed FP32 pairs
+        auto publish = [&](int buf, float4 m, int kn) {
+            if (FMT == HM_NEAR_BF16X2 && tc && kn >= nuch) {
+                const float v[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    __nv_bfloat16 h1, h2, h3;
+                    split3(v[e], h1, h2, h3);
+                    xt[buf & (FMT == HM_NEAR_BF16X2 ? 1 : 0)][0][4 * fg + e][fc] = h1;
+                    xt[buf & (FMT == HM_NEAR_BF16X2 ? 1 : 0)][1][4 * fg + e][fc] = h2;
+                    xt[buf & (FMT == HM_NEAR_BF16X2 ? 1 : 0)][2][4 * fg + e][fc] = h3;
+                }
+                return;
+            }
+            float4* d = reinterpret_cast<float4*>(msm[buf]) + 2 * tc_id;
             d[0] = make_float4(m.x, m.x, m.y, m.y);
             d[1] = make_float4(m.z, m.z, m.w, m.w);
         };
+        float tsum[NT8][4], tcmp[NT8][4];   // tensor-core rows: compensated sums
+#pragma unroll
+        for (int nt = 0; nt < NT8; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) tsum[nt][e] = tcmp[nt][e] = 0.f;
         float2 as[2][4], ac[2][4];   // compensated sums and corrections [row pair][vector]
 #pragma unroll
         for (int p = 0; p < 2; ++p)
 #pragma unroll
             for (int r = 0; r < 4; ++r) as[p][r] = ac[p][r] = make_float2(0.f, 0.f);
         float4 mf = fetch(0);
-        publish(0, mf);
+        publish(0, mf, 0);
         consumer_sync(NCW * 32);
         for (int k = 0; k < nch; ++k) {
             const int slot = k % TN_STAGES;
             mf = fetch(k + 1);
             const bool ok = __all_sync(0xffffffffu, mbar_wait(&full[slot], (k / TN_STAGES) & 1, P.wait_ns));
+            bool isu_k;
+            {
+                int64_t c0k;
+                int cntk;
+                chunk(k, isu_k, c0k, cntk);
+                if (ok && tc && !isu_k) {
+                    // a near chunk on the tensor cores: warp w < 4 takes rows
+                    // 16 w .. 16 w + 15 of every vector
+                    if (w < 4 && 16 * w < ld) {
+                        float cz[NT8][4];
+#pragma unroll
+                        for (int nt = 0; nt < NT8; ++nt)
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) cz[nt][e] = 0.f;
+                        chunk_mma<NRC>(tsm + slot * STAGE, ncolb, ld, cntk,
+                                       xt[k & (FMT == HM_NEAR_BF16X2 ? 1 : 0)], w, lane, cz);
+#pragma unroll
+                        for (int nt = 0; nt < NT8; ++nt) {
+                            float2 s01 = make_float2(tsum[nt][0], tsum[nt][1]);
+                            float2 c01 = make_float2(tcmp[nt][0], tcmp[nt][1]);
+                            float2 s23 = make_float2(tsum[nt][2], tsum[nt][3]);
+                            float2 c23 = make_float2(tcmp[nt][2], tcmp[nt][3]);
+                            two_sum_add(s01, c01, make_float2(cz[nt][0], cz[nt][1]));
+                            two_sum_add(s23, c23, make_float2(cz[nt][2], cz[nt][3]));
+                            tsum[nt][0] = s01.x; tsum[nt][1] = s01.y;
+                            tsum[nt][2] = s23.x; tsum[nt][3] = s23.y;
+                            tcmp[nt][0] = c01.x; tcmp[nt][1] = c01.y;
+                            tcmp[nt][2] = c23.x; tcmp[nt][3] = c23.y;
+                        }
+                    }
+                }
+            }
             if (ok) {
-                if (act) {
+                if (act && !(tc && !isu_k)) {
                     bool isu;
                     int64_t c0;
                     int cnt;
@@ -424,7 +573,7 @@ k_tile_n(MvpPlan P, const float* __restrict__ xm, const float* __restrict__ t,
                 atomicOr(P.status, 4);
                 failed = 1;
             }
-            publish((k + 1) & 1, mf);
+            publish((k + 1) & 1, mf, k + 1);
             consumer_sync(NCW * 32);
             if (*(volatile int*)&failed) break;
         }
@@ -440,6 +589,17 @@ k_tile_n(MvpPlan P, const float* __restrict__ xm, const float* __restrict__ t,
                     ps[j][ir + 2 * p + 1][4 * g + r] =
                         act ? (double)as[p][r].y + (double)ac[p][r].y : 0.0;
                 }
+            // the tensor cores' rows in a fifth slot (zero without them):
+            // fragment element e of tile nt is row 16 w + lane / 4 (+ 8 for
+            // e >= 2), vector 8 nt + 2 (lane mod 4) (+ 1 for odd e)
+            if (w < 4) {
+#pragma unroll
+                for (int nt = 0; nt < NT8; ++nt)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        ps[TN_LANES][16 * w + (lane >> 2) + 8 * (e >> 1)][8 * nt + 2 * (lane & 3) + (e & 1)] =
+                            (double)tsum[nt][e] + (double)tcmp[nt][e];
+            }
         }
     }
     __syncthreads();
@@ -448,7 +608,7 @@ k_tile_n(MvpPlan P, const float* __restrict__ xm, const float* __restrict__ t,
         const int row = e / NRC, r = e % NRC;
         double sum = 0.0;
 #pragma unroll
-        for (int q = 0; q < TN_LANES; ++q) sum += ps[q][row][r];
+        for (int q = 0; q <= TN_LANES; ++q) sum += ps[q][row][r];
         part[(item * P.max_ld + row) * NRC + r] = sum;
     }
 }
@@ -500,7 +660,9 @@ void run_group(const MvpPlan& P, MvpWork& W, const double* x, double* y, int nr,
         note_launch();
     }
     if (P.n_tiles > 0) {
-        const int smem = TN_STAGES * TN_COL * ncol_bytes64<FMT>();
+        // (+256 bytes: a tensor-core fragment of the last stage may read up
+        // to 16 bytes past it, into this padding)
+        const int smem = TN_STAGES * TN_COL * ncol_bytes64<FMT>() + 256;
         auto kt = k_tile_n<FMT, NRC>;
         HM_CUDA(cudaFuncSetAttribute(kt, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         kt<<<(unsigned)P.n_items, (NRC / 2 + 1) * 32, smem, s>>>(P, W.xmn.p, W.tn.p, W.partn.p);
