@@ -372,17 +372,19 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- oracle leg
-def oracle_sample(name: str, budget_s: float = 12.0, seed: int = 0):
+def oracle_sample(name: str, budget_s: float = 12.0, seed: int = 0, threads: int = 1):
     """The CPU oracle, as it stands, on a bounded sample of the workload.
 
     Full-size structure (Morton sort, cluster tree, Alg. 1 traversal) is timed
     as is; ACA is timed on blocks sampled per size class and scaled by the
     class counts; the product is timed on the same workload at N = 2^14 and
-    scaled by the number of stored entries. Returns seconds per step (build +
-    N_MVP products) and a description of the sample.
+    scaled by the number of stored entries. threads > 1 spreads the oracle's
+    block loops (ACA, product) over that many host threads (OpenMP). Returns
+    seconds per step (build + N_MVP products) and a description of the sample.
     """
     import oracle
     from paper_1708_09707_gb300 import inputs
+    oracle.set_threads(threads)
     w = inputs.WORKLOADS[name]
     pts = inputs.workload_points(name)
     t0 = time.perf_counter()
@@ -399,31 +401,35 @@ def oracle_sample(name: str, budget_s: float = 12.0, seed: int = 0):
     spent = 0.0
     nsampled = 0
     classes = np.unique(size)
-    per = max(1.0, budget_s / max(len(classes), 1))
+    per = max(0.5, budget_s / max(len(classes), 1))
     for c in classes:
         idx = np.nonzero(size == c)[0]
         rng.shuffle(idx)
-        t_cls = 0.0
-        k = 0
-        for b in idx:
+        # grow the sample fourfold until it takes a quarter of the class's time
+        k = min(len(idx), max(2 * threads, 4))
+        while True:
             ts = time.perf_counter()
-            O.compress_range(int(b), int(b) + 1)
-            t_cls += time.perf_counter() - ts
-            k += 1
-            if t_cls > per or k >= len(idx):
+            O.compress_ids(idx[:k])
+            dt = time.perf_counter() - ts
+            spent += dt
+            if dt > per / 4 or k >= len(idx):
                 break
-        spent += t_cls
+            k = min(len(idx), 4 * k)
         nsampled += k
-        t_aca += t_cls / k * len(idx)
+        t_aca += dt / k * len(idx)
     # product: full oracle H-matrix at N = 2^14, scaled by stored entries
     ns = 1 << 14
     ps = inputs.workload_points(name, ns)
     Os = oracle.HMatrix(ps, w["kernel"], w["ell"], w["leaf"], w["eta"], w["eps"],
                         adm_max=(w["adm"] == "max"))
     xs = inputs.normal_vector(ns, 1)
-    ts = time.perf_counter()
     Os.matvec(xs)
-    t_mv_small = time.perf_counter() - ts
+    ts = time.perf_counter()
+    reps = 3
+    for _ in range(reps):
+        Os.matvec(xs)
+    t_mv_small = (time.perf_counter() - ts) / reps
+    oracle.set_threads(1)
 
     def entries(H):
         l, h, _, _ = H.tree()
@@ -433,11 +439,20 @@ def oracle_sample(name: str, budget_s: float = 12.0, seed: int = 0):
 
     t_mv = t_mv_small * entries(O) / max(entries(Os), 1)
     step = t_struct + t_aca + N_MVP * t_mv
-    sample = ("full-size structure (%.1f s); ACA on %d of %d admissible blocks sampled per "
-              "size class (%.1f s), scaled by class counts; product timed at N=2^14 "
-              "(%.2f s) scaled by stored entries; single thread" %
-              (t_struct, nsampled, len(A), spent, t_mv_small))
+    sample = ("full-size structure (%.1f s, one thread); ACA on %d of %d admissible blocks "
+              "sampled per size class (%.1f s), scaled by class counts; product timed at "
+              "N=2^14 (%.3f s) scaled by stored entries; %d thread%s for ACA and the product" %
+              (t_struct, nsampled, len(A), spent, t_mv_small, threads,
+               "" if threads == 1 else "s (OpenMP over blocks)"))
     return step, t_struct + t_aca, t_mv, sample
+
+
+def host_threads() -> int:
+    """Host cores this process may use."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
 
 
 def run_reference(args):
@@ -452,8 +467,9 @@ def run_reference(args):
         return
     vals = []
     sample = ""
+    cores = host_threads()
     for it in range(args.warmup + args.steps):
-        step, tb, tm, sample = oracle_sample(args.workload, budget_s=6.0, seed=it)
+        step, tb, tm, sample = oracle_sample(args.workload, budget_s=6.0, seed=it, threads=cores)
         if it >= args.warmup:
             vals.append(step)
     v = float(np.mean(vals))
@@ -466,7 +482,7 @@ def run_reference(args):
                        "kernel": "gaussian" if w["kernel"] == 0 else "matern32",
                        "ell": w["ell"], "leaf": w["leaf"], "eta": w["eta"],
                        "aca_eps": w["eps"], "mvp_per_step": N_MVP},
-            "cpu_baseline": {"value": v, "unit": unit, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": unit, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -1029,9 +1045,14 @@ def main():
 
     cpu = None
     if not args.no_cpu and world == 1:
-        cstep, cbuild, cmv, sample = oracle_sample(args.workload, budget_s=12.0)
-        cpu = {"value": cstep, "unit": "s/step (build + %d H-MVP)" % N_MVP, "cores": 1,
-               "kind": "oracle", "sample": sample, "build_s": cbuild, "mvp_ms": cmv * 1e3}
+        # the oracle on all host cores (OpenMP over blocks), and on one core
+        cores = host_threads()
+        cstep, cbuild, cmv, sample = oracle_sample(args.workload, budget_s=8.0, threads=cores)
+        sstep, sbuild, smv, ssample = oracle_sample(args.workload, budget_s=8.0, threads=1)
+        cpu = {"value": cstep, "unit": "s/step (build + %d H-MVP)" % N_MVP, "cores": cores,
+               "kind": "oracle", "sample": sample, "build_s": cbuild, "mvp_ms": cmv * 1e3,
+               "single_core": {"value": sstep, "build_s": sbuild, "mvp_ms": smv * 1e3,
+                               "sample": ssample}}
 
     value = total / 1e3
     line = {

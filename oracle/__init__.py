@@ -33,9 +33,12 @@ def build(force: bool = False) -> str:
             or os.path.getmtime(_SO) < max(os.path.getmtime(_SRC),
                                            os.path.getmtime(_SRC[:-1] + "h"))):
         tmp = _SO + ".%d.tmp" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off",
-                               "-fno-fast-math", "-fPIC", "-shared", _SRC,
-                               "-o", tmp, "-lm"])
+        base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+                "-shared", _SRC, "-o", tmp, "-lm"]
+        # OpenMP only spreads the block loops over threads when asked
+        # (set_threads); without it the same code runs on one thread
+        if subprocess.run(base + ["-fopenmp"], capture_output=True).returncode != 0:
+            subprocess.check_call(base)
         os.replace(tmp, _SO)
     return _SO
 
@@ -97,6 +100,9 @@ def _declare(L):
                                      C.c_int, C.c_double, C.c_int]
     L.or_compress_range.argtypes = [C.c_void_p, C.c_int64, C.c_int64,
                                     C.c_double, C.c_int, C.c_double, C.c_double]
+    L.or_compress_ids.argtypes = [C.c_void_p, _i64, C.c_int64,
+                                  C.c_double, C.c_int, C.c_double, C.c_double]
+    L.or_set_threads.argtypes = [C.c_int]
     L.or_free.argtypes = [C.c_void_p]
     L.or_mirror_transposed.argtypes = [C.c_void_p]
     for f in ("or_n_adm", "or_n_dense", "or_n_nodes"):
@@ -297,6 +303,15 @@ class HMatrix:
                                 self.k_cap if k_cap is None else k_cap,
                                 aca_eta, eps0)
 
+    def compress_ids(self, ids, aca_eps=None, k_cap=None, aca_eta: float = 0.0,
+                     eps0: float = 0.0):
+        """ACA of the listed admissible leaves (the factors of earlier calls
+        are dropped), on the threads set by set_threads."""
+        ids = np.ascontiguousarray(ids, dtype=np.int64)
+        lib().or_compress_ids(self._h, _p(ids, _i64), ids.size,
+                              self.aca_eps if aca_eps is None else aca_eps,
+                              self.k_cap if k_cap is None else k_cap, aca_eta, eps0)
+
     def codes(self):
         c = np.zeros(self.n, np.uint64)
         lib().or_get_codes(self._h, _p(c, _u64))
@@ -398,6 +413,12 @@ class HMatrix:
 # ---------------------------------------------------------------------------
 # Rank-model MLP
 # ---------------------------------------------------------------------------
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's block loops (ACA and the product); 1 = the
+    plain loops. Used to time the oracle on all host cores."""
+    lib().or_set_threads(int(n))
+
 
 def mlp_forward(theta, F):
     theta = _f64(theta)

@@ -13,6 +13,9 @@
 
 #include <math.h>
 #include <stdlib.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <string.h>
 
 /* ------------------------------------------------------------------------ */
@@ -622,17 +625,28 @@ static double or_block_entry(const void* ctx, int64_t i, int64_t j)
                           h->coords2 + (c->s0 + j) * h->d, h->d);
 }
 
-void or_compress_range(or_hmat* h, int64_t b0, int64_t b1, double aca_eps,
-                       int k_cap, double aca_eta, double eps0)
+/* Threads of the block loops (ACA and the product); 1 = the plain loops.  */
+/* The blocks are independent, so ACA gives the same factors on any count; */
+/* the product then sums per-thread partial vectors (rounding order only).  */
+static int or_threads = 1;
+void or_set_threads(int t) { or_threads = t > 1 ? t : 1; }
+
+/* ACA of the admissible leaves ids[0..n) (Alg. 2 per leaf); the factors of  */
+/* all listed leaves are kept in one store, appended in list order.          */
+void or_compress_ids(or_hmat* h, const int64_t* ids, int64_t n_ids, double aca_eps,
+                     int k_cap, double aca_eta, double eps0)
 {
-    /* factors of all blocks are kept in one store, appended in block order */
     int64_t totU = 0, totV = 0, totP = 0;
-    for (int64_t b = b0; b < b1; ++b) {
+    for (int64_t q = 0; q < n_ids; ++q) {
+        int64_t b = ids[q];
         int64_t m = h->hi[h->adm[b].tau] - h->lo[h->adm[b].tau];
         int64_t n = h->hi2[h->adm[b].sigma] - h->lo2[h->adm[b].sigma];
         int64_t k = k_cap;
         if (k > m) k = m;
         if (k > n) k = n;
+        h->offU[b] = totU;
+        h->offV[b] = totV;
+        h->offP[b] = totP;
         totU += m * k;
         totV += n * k;
         totP += k;
@@ -646,25 +660,27 @@ void or_compress_range(or_hmat* h, int64_t b0, int64_t b1, double aca_eps,
     h->pivI = (int64_t*)malloc((size_t)(totP ? totP : 1) * sizeof(int64_t));
     h->pivJ = (int64_t*)malloc((size_t)(totP ? totP : 1) * sizeof(int64_t));
     for (int64_t b = 0; b < h->n_adm; ++b) h->rank[b] = -1;
-    int64_t oU = 0, oV = 0, oP = 0;
-    for (int64_t b = b0; b < b1; ++b) {
+#pragma omp parallel for schedule(dynamic, 4) num_threads(or_threads) if (or_threads > 1)
+    for (int64_t q = 0; q < n_ids; ++q) {
+        int64_t b = ids[q];
         int64_t m = h->hi[h->adm[b].tau] - h->lo[h->adm[b].tau];
         int64_t n = h->hi2[h->adm[b].sigma] - h->lo2[h->adm[b].sigma];
         or_block_ctx c = {h, h->lo[h->adm[b].tau], h->lo2[h->adm[b].sigma]};
-        h->offU[b] = oU;
-        h->offV[b] = oV;
-        h->offP[b] = oP;
         int r = or_aca(or_block_entry, &c, m, n, aca_eps, k_cap, aca_eta, eps0,
-                       h->Ust + oU, h->Vst + oV, h->pivI + oP, h->pivJ + oP,
-                       &h->rej[b]);
+                       h->Ust + h->offU[b], h->Vst + h->offV[b], h->pivI + h->offP[b],
+                       h->pivJ + h->offP[b], &h->rej[b]);
         h->rank[b] = r;
-        int64_t k = k_cap;
-        if (k > m) k = m;
-        if (k > n) k = n;
-        oU += m * k;
-        oV += n * k;
-        oP += k;
     }
+}
+
+void or_compress_range(or_hmat* h, int64_t b0, int64_t b1, double aca_eps,
+                       int k_cap, double aca_eta, double eps0)
+{
+    int64_t n = b1 > b0 ? b1 - b0 : 0;
+    int64_t* ids = (int64_t*)malloc((size_t)(n ? n : 1) * sizeof(int64_t));
+    for (int64_t q = 0; q < n; ++q) ids[q] = b0 + q;
+    or_compress_ids(h, ids, n, aca_eps, k_cap, aca_eta, eps0);
+    free(ids);
 }
 
 /* Symmetric kernels, phi(y, y') = phi(y', y), give A(sigma, tau) =
@@ -828,6 +844,8 @@ void or_get_pivots(const or_hmat* h, int64_t b, int64_t* piv_i, int64_t* piv_j)
 /* order; x is permuted into Morton order first (Sec. 5.1) and the result   */
 /* permuted back, with sigma^2 x added (Sec. 1, the GPR/KRR variant).        */
 /* ------------------------------------------------------------------------ */
+static void or_matvec_threads(const or_hmat* h, const double* xm, double* ym);
+
 void or_matvec(const or_hmat* h, const double* x, double* y)
 {
     int64_t N = h->N, N2 = h->N2;
@@ -835,6 +853,14 @@ void or_matvec(const or_hmat* h, const double* x, double* y)
     double* xm = (double*)malloc((size_t)(N2 > 0 ? N2 : 1) * sizeof(double));
     double* ym = (double*)calloc((size_t)(N > 0 ? N : 1), sizeof(double));
     for (int64_t j = 0; j < N2; ++j) xm[j] = x[h->perm2[j]];
+    if (or_threads > 1) {
+        or_matvec_threads(h, xm, ym);
+        for (int64_t i = 0; i < N; ++i)
+            y[h->perm[i]] = h->rect ? ym[i] : ym[i] + h->sigma2 * x[h->perm[i]];
+        free(xm);
+        free(ym);
+        return;
+    }
     double* t = (double*)malloc(64 * sizeof(double));
     int tcap = 64;
     for (int64_t b = 0; b < h->n_adm; ++b) {
@@ -876,6 +902,67 @@ void or_matvec(const or_hmat* h, const double* x, double* y)
     free(t);
     free(xm);
     free(ym);
+}
+
+/* The product's leaf loops on or_threads threads, for timing the oracle on  */
+/* all host cores: each thread adds its leaves into a vector of its own and  */
+/* the vectors add in thread order (the same leaf terms as or_matvec, summed */
+/* in another order).                                                        */
+static void or_matvec_threads(const or_hmat* h, const double* xm, double* ym)
+{
+    int64_t N = h->N;
+    int d = h->d;
+    int T = or_threads;
+    double* part = (double*)calloc((size_t)T * (size_t)(N > 0 ? N : 1), sizeof(double));
+#pragma omp parallel num_threads(T)
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        double* yt = part + (size_t)tid * (size_t)(N > 0 ? N : 1);
+        int tcap = 64;
+        double* t = (double*)malloc((size_t)tcap * sizeof(double));
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t b = 0; b < h->n_adm; ++b) {
+            int64_t t0 = h->lo[h->adm[b].tau], m = h->hi[h->adm[b].tau] - t0;
+            int64_t s0 = h->lo2[h->adm[b].sigma], n = h->hi2[h->adm[b].sigma] - s0;
+            int r = h->rank[b];
+            if (r <= 0) continue;
+            if (r > tcap) {
+                tcap = r;
+                t = (double*)realloc(t, (size_t)tcap * sizeof(double));
+            }
+            const double* U = h->Ust + h->offU[b];
+            const double* V = h->Vst + h->offV[b];
+            for (int l = 0; l < r; ++l) {
+                double sm = 0.0;
+                for (int64_t j = 0; j < n; ++j) sm = sm + V[l * n + j] * xm[s0 + j];
+                t[l] = sm;
+            }
+            for (int64_t i = 0; i < m; ++i) {
+                double sm = 0.0;
+                for (int l = 0; l < r; ++l) sm = sm + U[l * m + i] * t[l];
+                yt[t0 + i] = yt[t0 + i] + sm;
+            }
+        }
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t b = 0; b < h->n_dense; ++b) {
+            int64_t t0 = h->lo[h->dense[b].tau], m = h->hi[h->dense[b].tau] - t0;
+            int64_t s0 = h->lo2[h->dense[b].sigma], n = h->hi2[h->dense[b].sigma] - s0;
+            for (int64_t i = 0; i < m; ++i) {
+                double sm = 0.0;
+                for (int64_t j = 0; j < n; ++j)
+                    sm = sm + or_kernel_eval(h->kernel, h->ell, h->coords + (t0 + i) * d,
+                                             h->coords2 + (s0 + j) * d, d) * xm[s0 + j];
+                yt[t0 + i] = yt[t0 + i] + sm;
+            }
+        }
+        free(t);
+    }
+    for (int tq = 0; tq < T; ++tq)
+        for (int64_t i = 0; i < N; ++i) ym[i] = ym[i] + part[(size_t)tq * (size_t)N + i];
+    free(part);
 }
 
 /* Block-row share of the product (distributed H-matrices, the outlook of   */

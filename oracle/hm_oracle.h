@@ -120,6 +120,11 @@ or_hmat* or_build_structure(const double* pts, int64_t N, int d, int kernel,
 void or_mirror_transposed(or_hmat* h);
 
 /* ACA of admissible leaves [b0, b1) only (builds the factors of those). */
+/* Threads of the block loops of ACA and the product (1: plain loops). */
+void or_set_threads(int t);
+/* ACA of the listed admissible leaves (factors stored in list order). */
+void or_compress_ids(or_hmat* h, const int64_t* ids, int64_t n_ids, double aca_eps,
+                     int k_cap, double aca_eta, double eps0);
 void or_compress_range(or_hmat* h, int64_t b0, int64_t b1, double aca_eps,
                        int k_cap, double aca_eta, double eps0);
 
