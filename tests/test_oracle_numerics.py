@@ -347,3 +347,24 @@ def test_adam_sign_flip_second_step(orc):
     orc.adam_step(th, -g, m, v, 2, lr=0.1, eps=0.0)
     exp = th0 - 0.1 * np.sign(g) + 0.1 * np.sign(g) / 19.0
     assert np.allclose(th, exp, rtol=1e-13)
+
+
+def test_oracle_threads_same_factors(orc):
+    # the block loops on several threads (used to time the oracle on all
+    # host cores): the same ranks and factors, the product to rounding
+    pts = inputs.mixture_points(6000, 2, 77)
+    x = inputs.normal_vector(6000, 1)
+    O = orc.HMatrix(pts, 0, 0.1, 32, 1.0, 1e-7)
+    y1 = O.matvec(x)
+    r1 = O.ranks()[0].copy()
+    U1, V1 = O.factors(len(r1) // 2)
+    try:
+        orc.set_threads(4)
+        O.compress_range(0, O.n_adm)
+        y4 = O.matvec(x)
+        U4, V4 = O.factors(len(r1) // 2)
+    finally:
+        orc.set_threads(1)
+    assert np.array_equal(O.ranks()[0], r1)
+    assert np.array_equal(U1, U4) and np.array_equal(V1, V4)
+    assert np.linalg.norm(y4 - y1) <= 1e-14 * np.linalg.norm(y1)
