@@ -374,18 +374,119 @@ __device__ __forceinline__ void team_resid(T (&uh)[R], const T* __restrict__ F, 
     }
 }
 
-// Entries A(i, col0 + jj) of one row (or column: pass the other side's
-// points) at the thread's indices g + q G < len, zero elsewhere.
-template <class T, int KERN, int W, int R>
-__device__ __forceinline__ void team_eval(T (&uh)[R], const DeviceCoords& X, const Pt<T>& p0,
-                                          int64_t base, int len, int g, T c, T c2)
+// Squared distance from p0 to the point in Morton row `row`, over the first
+// D coordinate planes only (the planes above the sets' dimension hold zeros;
+// their terms would add exact zeros, so the result is bit for bit that of
+// dist2 over three planes).
+template <int D>
+__device__ __forceinline__ float dist2_planes(const Pt<float>& a, const DeviceCoords& X, int64_t row)
+{
+    const float* F = X.x32;
+    const int64_t st = X.stride32;
+    float t[3];
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+        t[i] = (a.h[i] - F[(2 * i) * st + row]) + (a.l[i] - F[(2 * i + 1) * st + row]);
+    float r = t[0] * t[0];
+#pragma unroll
+    for (int i = 1; i < D; ++i) r = fmaf(t[i], t[i], r);
+    return r;
+}
+
+template <int D>
+__device__ __forceinline__ double dist2_planes(const Pt<double>& a, const DeviceCoords& X, int64_t row)
+{
+    double t[3];
+#pragma unroll
+    for (int i = 0; i < D; ++i) t[i] = a.x[i] - X.x64[i][row];
+    double r = t[0] * t[0];
+#pragma unroll
+    for (int i = 1; i < D; ++i) r = fma(t[i], t[i], r);
+    return r;
+}
+
+// The same pass in float on packed pairs of entries (q, q + 1): each
+// residual entry takes the same fused multiply-adds in the same order
+// (fma(u, -s, w) rounds like fma(-u, s, w)); the dots keep two partial sums,
+// joined before the warp's reduce-scatter.
+template <int W, int R, bool DOTS>
+__device__ __forceinline__ void team_resid_f2(float (&uh)[R], const float* __restrict__ F, int len,
+                                           int r, const float (&coef)[2], float* dotw, int g,
+                                           int lane)
 {
     constexpr int G = 32 * W;
+    static_assert(R % 2 == 0, "entries in pairs");
+    for (int l0 = 0; l0 < r; l0 += LC) {
+        float2 ns[LC], p2[LC];
+        const float* Fb[LC];
+        const float cw = l0 < 32 ? coef[0] : coef[1];
 #pragma unroll
-    for (int q = 0; q < R; ++q) {
-        const bool ok = g + q * G < len;
-        const T v = phi_team<KERN>(dist2(p0, load_pt<T>(X, base + (ok ? g + q * G : 0))), c, c2);
-        uh[q] = ok ? v : T(0);
+        for (int e = 0; e < LC; ++e) {
+            const float sv = __shfl_sync(0xffffffffu, cw, (l0 + e) & 31);
+            ns[e] = make_float2(-sv, -sv);
+            p2[e] = make_float2(0.f, 0.f);
+            Fb[e] = F + (l0 + e < r ? (l0 + e) : l0) * len;
+        }
+#pragma unroll
+        for (int q = 0; q < R; q += 2) {
+            const bool ok0 = g + q * G < len, ok1 = g + (q + 1) * G < len;
+            const int i0 = ok0 ? g + q * G : len - 1, i1 = ok1 ? g + (q + 1) * G : len - 1;
+            float2 w = make_float2(uh[q], uh[q + 1]);
+            float2 u[LC];
+#pragma unroll
+            for (int e = 0; e < LC; ++e) u[e] = make_float2(Fb[e][i0], Fb[e][i1]);
+            if (DOTS) {
+#pragma unroll
+                for (int e = 0; e < LC; ++e) p2[e] = __ffma2_rn(w, u[e], p2[e]);
+            }
+#pragma unroll
+            for (int e = 0; e < LC; ++e) w = __ffma2_rn(u[e], ns[e], w);
+            uh[q] = ok0 ? w.x : 0.f;
+            uh[q + 1] = ok1 ? w.y : 0.f;
+        }
+        if (DOTS) {
+            float p[LC];
+#pragma unroll
+            for (int e = 0; e < LC; ++e) p[e] = p2[e].x + p2[e].y;
+            const float ps = warp_scatter(p);
+            const int e = scatter_elem(lane);
+            if (scatter_writer(lane) && l0 + e < r) dotw[l0 + e] = ps;
+        }
+    }
+}
+
+template <class T, int W, int R, bool DOTS>
+__device__ __forceinline__ void team_pass(T (&uh)[R], const T* __restrict__ F, int len, int r,
+                                          const T (&coef)[2], T* dotw, int g, int lane)
+{
+    if constexpr (std::is_same<T, float>::value)
+        team_resid_f2<W, R, DOTS>(uh, F, len, r, coef, dotw, g, lane);
+    else
+        team_resid<T, W, R, DOTS>(uh, F, len, r, coef, dotw, g, lane);
+}
+
+// Entries A(i, col0 + jj) of one row (or column: pass the other side's
+// points) at the thread's indices g + q G < len, zero elsewhere; d2 selects
+// the two-plane distance (sets of dimension 1 or 2).
+template <class T, int KERN, int W, int R>
+__device__ __forceinline__ void team_eval(T (&uh)[R], const DeviceCoords& X, const Pt<T>& p0,
+                                          int64_t base, int len, int g, T c, T c2, bool d2)
+{
+    constexpr int G = 32 * W;
+    if (d2) {
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const bool ok = g + q * G < len;
+            const T v = phi_team<KERN>(dist2_planes<2>(p0, X, base + (ok ? g + q * G : 0)), c, c2);
+            uh[q] = ok ? v : T(0);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const bool ok = g + q * G < len;
+            const T v = phi_team<KERN>(dist2_planes<3>(p0, X, base + (ok ? g + q * G : 0)), c, c2);
+            uh[q] = ok ? v : T(0);
+        }
     }
 }
 
@@ -415,6 +516,7 @@ k_aca_team(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restric
     T* __restrict__ V = reinterpret_cast<T*>(a.Vptr[b]);
     const T c = kconst<T>(kp);
     const T eps0 = (T)a.eps0;
+    const bool d2 = kp.dmax <= 2;
     if (max(m, n) > R * G || kmax > KT) {   // the host routes no such block here
         if (g == 0) atomicOr(a.status, 2);
         return;
@@ -431,7 +533,7 @@ k_aca_team(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restric
     int ph = 0;
     T uh[R], rr[R];
     unsigned used = 0u, seen = (g == 0) ? 1u : 0u;
-    team_eval<T, KERN, W, R>(rr, X, load_pt<T>(X, B.row0), B.col0, n, g, c, c2);   // reference row 0
+    team_eval<T, KERN, W, R>(rr, X, load_pt<T>(X, B.row0), B.col0, n, g, c, c2, d2);   // reference row 0
     int r = 0, j = 0, rej = 0, run = 0, iref = 0;
     bool converged = false;
     const int limit = a.step_limit > 0 ? a.step_limit : kmax + n + 1;
@@ -454,12 +556,12 @@ k_aca_team(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restric
             if (wt == 0 && l < KT) S.sgv[l] = sreg[s];
         }
         // ---- column pass: u^ = A(:, j) - sum_l u_l (v_l)_j, with w . u_l
-        team_eval<T, KERN, W, R>(uh, X, load_pt<T>(X, B.col0 + j), B.row0, m, g, c, c2);
+        team_eval<T, KERN, W, R>(uh, X, load_pt<T>(X, B.col0 + j), B.row0, m, g, c, c2, d2);
         TRed<T> qc;
         qc.init();
 #pragma unroll
         for (int q = 0; q < R; ++q) qc.x0 = max(qc.x0, fabs(uh[q]));
-        team_resid<T, W, R, true>(uh, U, m, r, sreg, dotw, g, lane);
+        team_pass<T, W, R, true>(uh, U, m, r, sreg, dotw, g, lane);
         {
             bool have_mn = false;
 #pragma unroll
@@ -547,8 +649,8 @@ k_aca_team(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restric
         // ---- row pass: v = A(i*, :) - sum_l (u_l)_{i*} v_l, with w . v_l
         // (its dot partials go to the second buffer: warp 0 may still read
         // the column pass's)
-        team_eval<T, KERN, W, R>(uh, X, load_pt<T>(X, B.row0 + bi), B.col0, n, g, c, c2);
-        team_resid<T, W, R, true>(uh, V, n, r, sreg, dotw + W * KT, g, lane);
+        team_eval<T, KERN, W, R>(uh, X, load_pt<T>(X, B.row0 + bi), B.col0, n, g, c, c2, d2);
+        team_pass<T, W, R, true>(uh, V, n, r, sreg, dotw + W * KT, g, lane);
         {
             T* __restrict__ Vr = V + r * n + g;
             bool have_mn = false;
@@ -621,8 +723,8 @@ k_aca_team(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restric
                 const int l = lane + 32 * s;
                 sref[s] = l < r ? U[l * m + iref] : T(0);
             }
-            team_eval<T, KERN, W, R>(uh, X, load_pt<T>(X, B.row0 + iref), B.col0, n, g, c, c2);
-            team_resid<T, W, R, false>(uh, V, n, r, sref, dotw, g, lane);
+            team_eval<T, KERN, W, R>(uh, X, load_pt<T>(X, B.row0 + iref), B.col0, n, g, c, c2, d2);
+            team_pass<T, W, R, false>(uh, V, n, r, sref, dotw, g, lane);
             TRed<T> qf;
             qf.init();
 #pragma unroll

@@ -110,6 +110,8 @@ struct KernelParams {
     int kernel;    // HM_GAUSSIAN | HM_MATERN32 | HM_MATERN_K1
     double c64;    // 1/l^2 (Gaussian), sqrt(3)/l (Matern-3/2) or 1/(4 l^2) (Matern K_1)
     float c32;
+    int dmax = 3;  // largest dimension of the handle's point sets (the planes
+                   // above it hold zeros, so kernels may skip them)
 };
 
 KernelParams make_kernel_params(int kernel, double ell);

@@ -1078,6 +1078,8 @@ void build_sets(hm_handle_s& h, int nsets, const double* points_all, const int64
                         : opt.near_format;
     h.stream = (cudaStream_t)opt.stream;
     h.kp = make_kernel_params(kernel, h.ell);
+    h.kp.dmax = 1;
+    for (int q = 0; q < nsets; ++q) h.kp.dmax = std::max(h.kp.dmax, d[q]);
     cudaStream_t s = h.stream;
     h.status.alloc(1, s);
     HM_CUDA(cudaMemsetAsync(h.status.p, 0, sizeof(int), s));
