@@ -250,12 +250,25 @@ int hm_set_aca_shape(int cls, int shape);
  *                           library from now fails as if the device were out
  *                           of memory (HM_ENOMEM); the failing call releases
  *                           what it had allocated.
+ *   HM_HOOK_TRAVERSAL_KAPPA value > 0 sets the first level bound of the
+ *                           block-tree traversal: level l may hold
+ *                           min(4^l, value * 2^l) pairs (default 16, 256 or
+ *                           1024 for d = 1, 2, 3, times ceil(1/eta)^d for
+ *                           eta < 1). A level that does not fit ends the
+ *                           traversal on the device; the host then runs it
+ *                           again with the bounds doubled (hm_stats
+ *                           traversal_reruns counts these runs).
+ *   HM_HOOK_TRAVERSAL_TRIES value n > 0: at most n traversals (default 16);
+ *                           if the n-th still does not fit the build
+ *                           returns HM_EOVERFLOW.
  * Returns HM_EINVAL for an unknown hook or a value out of range. */
 enum {
     HM_HOOK_ACA_STEP_LIMIT = 0,
     HM_HOOK_WAIT_LIMIT_NS = 1,
     HM_HOOK_GATHER_WITHHOLD = 2,
-    HM_HOOK_FAIL_ALLOC = 3
+    HM_HOOK_FAIL_ALLOC = 3,
+    HM_HOOK_TRAVERSAL_KAPPA = 4,
+    HM_HOOK_TRAVERSAL_TRIES = 5
 };
 int hm_set_test_hook(int hook, int64_t value);
 
@@ -307,6 +320,9 @@ typedef struct hm_stats {
        aca_flops then count the ACA work of one product, near_entries the
        dense entries evaluated per product */
     double t_np_aca_ms, t_np_lowrank_ms, t_np_near_ms;
+    /* last build: traversals run again because a level of the block tree
+       did not fit its bound (summed over the point sets) */
+    int traversal_reruns;
 } hm_stats;
 
 int hm_get_stats(hm_handle h, hm_stats* out);

@@ -213,6 +213,14 @@ int hm_set_test_hook(int hook, int64_t value)
         if (value < 0) break;
         g_fail_alloc = value;
         return HM_OK;
+    case HM_HOOK_TRAVERSAL_KAPPA:
+        if (value < 0 || value > (1 << 20)) break;
+        hm::set_traversal_kappa(value);
+        return HM_OK;
+    case HM_HOOK_TRAVERSAL_TRIES:
+        if (value < 0 || value > 64) break;
+        hm::set_traversal_attempts((int)value);
+        return HM_OK;
     default:
         break;
     }

@@ -10,6 +10,9 @@
 // round-to-nearest intrinsics so that the compiler cannot contract them into
 // fused multiply-adds: the sequence of IEEE operations is the one stated in
 // the comments.
+#include <atomic>
+#include <cmath>
+
 #include "hm_build.cuh"
 
 namespace hm {
@@ -243,62 +246,100 @@ __device__ __forceinline__ bool admissible(const double* tmn, const double* tmx,
     return D <= __dmul_rn(eta2, G2);
 }
 
-// Alg. 1 on one level: classify every pair (tau, sigma) as admissible leaf,
-// split (four children on the next level) or dense leaf. The classification
-// is packed into one int64 per pair so that a single exclusive scan yields
-// the adm offset (low 32 bits) and the dense offset (high 32 bits); the split
-// offset is p - adm - dense.
+// Alg. 1 on one level (Alg. 4's level-synchronous form): classify every
+// pair (tau, sigma) as admissible leaf, split (four children on the next
+// level) or dense leaf. The classification is packed into one int64 per pair
+// so that a single exclusive scan yields the adm offset (low 32 bits) and the
+// dense offset (high 32 bits); the split offset is p - adm - dense.
 // tau is a node of the row tree (lo, hi, bmin, bmax), sigma of the column
 // tree (lo2, ...); the same tree for A_{phi, Y x Y}.
-__global__ void k_classify(const int2* __restrict__ pairs, int64_t P, int C,
-                           const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
-                           const double* __restrict__ bmin, const double* __restrict__ bmax,
-                           const int32_t* __restrict__ lo2, const int32_t* __restrict__ hi2,
-                           const double* __restrict__ bmin2, const double* __restrict__ bmax2,
-                           double eta2, int adm_max, int64_t* __restrict__ flag)
+//
+// The level's pair count stays on the device: cnt = {P, admissible leaves so
+// far, dense leaves so far}. The grids are sized for the level's bound and
+// stride over the P pairs, so no launch waits for the host to learn P.
+__global__ void k_classify(const int2* __restrict__ pairs, const int64_t* __restrict__ cnt,
+                           int64_t B, int C, const int32_t* __restrict__ lo,
+                           const int32_t* __restrict__ hi, const double* __restrict__ bmin,
+                           const double* __restrict__ bmax, const int32_t* __restrict__ lo2,
+                           const int32_t* __restrict__ hi2, const double* __restrict__ bmin2,
+                           const double* __restrict__ bmax2, double eta2, int adm_max,
+                           int64_t* __restrict__ flag)
 {
-    int64_t p = (int64_t)blockIdx.x * NT + threadIdx.x;
-    if (p >= P) return;
-    int2 ts = pairs[p];
-    int t = ts.x, s = ts.y;
-    double tmn[3], tmx[3], smn[3], smx[3];
+    const int64_t P = cnt[0] < B ? cnt[0] : B;
+    for (int64_t p = (int64_t)blockIdx.x * NT + threadIdx.x; p < P;
+         p += (int64_t)gridDim.x * NT) {
+        const int2 ts = pairs[p];
+        const int t = ts.x, s = ts.y;
+        double tmn[3], tmx[3], smn[3], smx[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        tmn[i] = bmin[(int64_t)t * 3 + i];
-        tmx[i] = bmax[(int64_t)t * 3 + i];
-        smn[i] = bmin2[(int64_t)s * 3 + i];
-        smx[i] = bmax2[(int64_t)s * 3 + i];
+        for (int i = 0; i < 3; ++i) {
+            tmn[i] = bmin[(int64_t)t * 3 + i];
+            tmx[i] = bmax[(int64_t)t * 3 + i];
+            smn[i] = bmin2[(int64_t)s * 3 + i];
+            smx[i] = bmax2[(int64_t)s * 3 + i];
+        }
+        const bool a = admissible(tmn, tmx, smn, smx, eta2, adm_max);
+        const int nt = hi[t] - lo[t], ns = hi2[s] - lo2[s];
+        int64_t f;
+        if (a) f = 1;                          // admissible leaf
+        else if (nt > C && ns > C) f = 0;      // split
+        else f = 1ll << 32;                    // dense leaf
+        flag[p] = f;
     }
-    bool a = admissible(tmn, tmx, smn, smx, eta2, adm_max);
-    int nt = hi[t] - lo[t], ns = hi2[s] - lo2[s];
-    int64_t f;
-    if (a) f = 1;                          // admissible leaf
-    else if (nt > C && ns > C) f = 0;      // split
-    else f = 1ll << 32;                    // dense leaf
-    flag[p] = f;
 }
 
-__global__ void k_emit(const int2* __restrict__ pairs, int64_t P,
-                       const int64_t* __restrict__ flag, const int64_t* __restrict__ off,
-                       int2* __restrict__ next, int2* __restrict__ adm, int64_t adm_base,
-                       int2* __restrict__ dense, int64_t dense_base)
+// Writes the level's leaves into one arena of BL pairs, admissible leaves
+// from the front and dense leaves from the back, and its splits' children
+// into next (at most Bnext pairs). Children that would pass Bnext are not
+// written; k_level_advance then stops the traversal and raises the overflow
+// word.
+__global__ void k_emit(const int2* __restrict__ pairs, int64_t B, const int64_t* __restrict__ flag,
+                       const int64_t* __restrict__ off, const int64_t* __restrict__ cnt,
+                       int2* __restrict__ next, int64_t Bnext, int2* __restrict__ leaves,
+                       int64_t BL)
 {
-    int64_t p = (int64_t)blockIdx.x * NT + threadIdx.x;
-    if (p >= P) return;
-    int64_t f = flag[p], o = off[p];
-    int64_t a = o & 0xFFFFFFFFll, dn = o >> 32;
-    int2 ts = pairs[p];
-    if (f == 1) {
-        adm[adm_base + a] = ts;
-    } else if (f != 0) {
-        dense[dense_base + dn] = ts;
+    const int64_t P = cnt[0] < B ? cnt[0] : B;
+    const int64_t adm0 = cnt[1], dense0 = cnt[2];
+    for (int64_t p = (int64_t)blockIdx.x * NT + threadIdx.x; p < P;
+         p += (int64_t)gridDim.x * NT) {
+        const int64_t f = flag[p], o = off[p];
+        const int64_t a = o & 0xFFFFFFFFll, dn = o >> 32;
+        const int2 ts = pairs[p];
+        if (f == 1) {
+            const int64_t at = adm0 + a;
+            if (at < BL) leaves[at] = ts;
+        } else if (f != 0) {
+            const int64_t at = BL - 1 - (dense0 + dn);
+            if (at >= 0) leaves[at] = ts;
+        } else {
+            const int64_t sp = p - a - dn;
+            if (4 * sp + 3 >= Bnext) continue;
+            const int t1 = 2 * ts.x + 1, s1 = 2 * ts.y + 1;
+            next[4 * sp + 0] = make_int2(t1, s1);
+            next[4 * sp + 1] = make_int2(t1, s1 + 1);
+            next[4 * sp + 2] = make_int2(t1 + 1, s1);
+            next[4 * sp + 3] = make_int2(t1 + 1, s1 + 1);
+        }
+    }
+}
+
+// After a level: the leaf counts and the next level's pair count; a next
+// level above its bound (or leaves above the arena) sets *ovf and ends the
+// traversal (P = 0), so that no later launch reads a pair never written.
+__global__ void k_level_advance(const int64_t* __restrict__ tot, int64_t* __restrict__ cnt,
+                                int64_t Bnext, int64_t BL, int* __restrict__ ovf)
+{
+    const int64_t t = *tot;
+    const int64_t P = cnt[0];
+    const int64_t na = t & 0xFFFFFFFFll, nd = t >> 32;
+    const int64_t ns = P - na - nd;
+    cnt[1] += na;
+    cnt[2] += nd;
+    if (4 * ns > Bnext || cnt[1] + cnt[2] > BL) {
+        *ovf = 1;
+        cnt[0] = 0;
     } else {
-        int64_t sp = p - a - dn;
-        int t1 = 2 * ts.x + 1, s1 = 2 * ts.y + 1;
-        next[4 * sp + 0] = make_int2(t1, s1);
-        next[4 * sp + 1] = make_int2(t1, s1 + 1);
-        next[4 * sp + 2] = make_int2(t1 + 1, s1);
-        next[4 * sp + 3] = make_int2(t1 + 1, s1 + 1);
+        cnt[0] = 4 * ns;
     }
 }
 
@@ -331,29 +372,42 @@ int bits_for(int64_t n)
     return b;
 }
 
-// Sort a leaf list into canonical (tau.lo, sigma.lo) order.
-void canonical_sort(DevBuf<int2>& leaves, int64_t n, const int32_t* lo, int64_t N,
+// Sort n leaf pairs (device, in) into canonical (tau.lo, sigma.lo) order in
+// out (allocated here, n pairs).
+void canonical_sort(const int2* in, int64_t n, DevBuf<int2>& out, const int32_t* lo, int64_t N,
                     const int32_t* lo2, int64_t N2, cudaStream_t s)
 {
-    if (n <= 1) return;
+    out.alloc(std::max<int64_t>(n, 1), s);
+    if (n == 0) return;
+    if (n == 1) {
+        HM_CUDA(cudaMemcpyAsync(out.p, in, sizeof(int2), cudaMemcpyDeviceToDevice, s));
+        return;
+    }
     DevBuf<uint64_t> keys(n, s);
     DevBuf<uint32_t> idx(n, s);
-    k_leaf_keys<<<grid_for(n), NT, 0, s>>>(leaves.p, n, lo, lo2, N2, keys.p, idx.p); note_launch();
+    k_leaf_keys<<<grid_for(n), NT, 0, s>>>(in, n, lo, lo2, N2, keys.p, idx.p); note_launch();
     HM_LAUNCH("leaf keys");
     radix_sort_u64_u32(keys.p, idx.p, n, bits_for(N + 1) + bits_for(N2 + 1), s);
-    DevBuf<int2> out(n, s);
-    k_gather_pairs<<<grid_for(n), NT, 0, s>>>(leaves.p, idx.p, n, out.p); note_launch();
+    k_gather_pairs<<<grid_for(n), NT, 0, s>>>(in, idx.p, n, out.p); note_launch();
     HM_LAUNCH("leaf gather");
-    leaves = std::move(out);
 }
 
-void grow(DevBuf<int2>& buf, int64_t used, int64_t need, cudaStream_t s)
+// Level bounds of the traversal: level l of the block tree holds at most
+// min(4^l, kappa 2^l) pairs. A cluster of level l meets a bounded number of
+// clusters of its level that it is not yet separated from (Sec. 2.2: the
+// admissibility condition compares diameter and distance), about 2^l of
+// them per unit of kappa; kappa grows with the dimension and with 1 / eta.
+std::atomic<int64_t> g_trav_kappa{0};
+std::atomic<int> g_trav_attempts{0};
+
+int64_t default_kappa(int d, double eta)
 {
-    if ((int64_t)buf.n >= need) return;
-    int64_t cap = std::max<int64_t>(need, 2 * (int64_t)buf.n);
-    DevBuf<int2> nb(cap, s);
-    if (used) HM_CUDA(cudaMemcpyAsync(nb.p, buf.p, used * sizeof(int2), cudaMemcpyDeviceToDevice, s));
-    buf = std::move(nb);
+    int64_t k = d <= 1 ? 16 : d == 2 ? 256 : 1024;
+    if (eta < 1.0) {
+        const double f = std::ceil(1.0 / eta);
+        k = (int64_t)std::min(std::pow(f, (double)std::max(d, 1)) * (double)k, 1048576.0);
+    }
+    return k;
 }
 
 }  // namespace
@@ -446,43 +500,75 @@ void traverse(SetStructure& R, const SetStructure& Cs, double eta, int adm_max,
     const double* bx2 = bmax + Cs.node0 * 3;
     const int depth = std::max(R.depth, Cs.depth);
 
-    // level-synchronous traversal (Alg. 1 via Alg. 4) from the pair of roots
+    // level-synchronous traversal (Alg. 1 via Alg. 4) from the pair of roots,
+    // every count kept on the device: the host reads the leaf counts once,
+    // after the last level, and runs the traversal again with twice the
+    // level bounds if a level did not fit
     const double eta2 = eta * eta;
-    DevBuf<int2> cur(1, s), nxt;
-    int2 root = make_int2(0, 0);
-    HM_CUDA(cudaMemcpyAsync(cur.p, &root, sizeof(int2), cudaMemcpyHostToDevice, s));
-    int64_t P = 1, n_adm = 0, n_dense = 0;
-    DevBuf<int64_t> tot(1, s);
-    const int64_t guess = std::max<int64_t>(1024, std::max(R.N, Cs.N));
-    adm.alloc(guess, s);
-    dense.alloc(guess, s);
-    for (int l = 0; P > 0; ++l) {
-        if (l > depth) fail(HM_EOVERFLOW, "block tree deeper than the cluster trees");
-        DevBuf<int64_t> flag(P, s), off(P, s);
-        k_classify<<<grid_for(P), NT, 0, s>>>(cur.p, P, C, lo, hi, bn, bx, lo2, hi2, bn2, bx2,
-                                              eta2, adm_max, flag.p); note_launch();
-        HM_LAUNCH("classify");
-        scan_exclusive_i64(flag.p, off.p, P, tot.p, s);
-        int64_t h_tot = 0;
-        HM_CUDA(cudaMemcpyAsync(&h_tot, tot.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    const int L = depth + 1;
+    const int d = std::max(R.d, Cs.d);
+    int64_t kappa = g_trav_kappa.load() > 0 ? g_trav_kappa.load() : default_kappa(d, eta);
+    const int attempts = g_trav_attempts.load() > 0 ? g_trav_attempts.load() : 16;
+    const int gmax = 8 * num_sms();
+    for (int attempt = 0;; ++attempt) {
+        if (attempt >= attempts)
+            fail(HM_EOVERFLOW, "block-tree level bounds still too small after " +
+                                   std::to_string(attempts) + " traversals");
+        std::vector<int64_t> bound(L + 1);
+        int64_t bmax_l = 1, bsum = 0;
+        for (int l = 0; l <= L; ++l) {
+            const int64_t full = l < 31 ? (1ll << (2 * l)) : (1ll << 62);
+            const int64_t geo = (l < 40 && kappa < (1ll << 20)) ? kappa << l : (1ll << 62);
+            bound[l] = std::max<int64_t>(1, std::min(full, geo));
+            if (l < L) {
+                bmax_l = std::max(bmax_l, bound[l]);
+                bsum += bound[l];
+            }
+        }
+        bmax_l = std::max(bmax_l, bound[L]);
+        DevBuf<int2> cur(bmax_l, s), nxt(bmax_l, s), leaves(bsum, s);
+        DevBuf<int64_t> flag(bmax_l, s), off(bmax_l, s), tot(1, s), cnt(3, s);
+        DevBuf<int> ovf(1, s);
+        const int2 root = make_int2(0, 0);
+        const int64_t c0[3] = {1, 0, 0};
+        HM_CUDA(cudaMemcpyAsync(cur.p, &root, sizeof(int2), cudaMemcpyHostToDevice, s));
+        HM_CUDA(cudaMemcpyAsync(cnt.p, c0, sizeof(c0), cudaMemcpyHostToDevice, s));
+        HM_CUDA(cudaMemsetAsync(ovf.p, 0, sizeof(int), s));
+        for (int l = 0; l < L; ++l) {
+            const int64_t B = bound[l];
+            const unsigned g = (unsigned)std::min<int64_t>(grid_for(B), gmax);
+            k_classify<<<g, NT, 0, s>>>(cur.p, cnt.p, B, C, lo, hi, bn, bx, lo2, hi2, bn2, bx2,
+                                        eta2, adm_max, flag.p); note_launch();
+            HM_LAUNCH("classify");
+            scan_exclusive_i64_dev(flag.p, off.p, cnt.p, B, tot.p, s);
+            k_emit<<<g, NT, 0, s>>>(cur.p, B, flag.p, off.p, cnt.p, nxt.p, bound[l + 1],
+                                    leaves.p, bsum); note_launch();
+            k_level_advance<<<1, 1, 0, s>>>(tot.p, cnt.p, bound[l + 1], bsum, ovf.p); note_launch();
+            HM_LAUNCH("emit");
+            std::swap(cur, nxt);
+        }
+        int64_t hc[3] = {0, 0, 0};
+        int hovf = 0;
+        HM_CUDA(cudaMemcpyAsync(hc, cnt.p, sizeof(hc), cudaMemcpyDeviceToHost, s));
+        HM_CUDA(cudaMemcpyAsync(&hovf, ovf.p, sizeof(int), cudaMemcpyDeviceToHost, s));
         HM_CUDA(cudaStreamSynchronize(s));
-        int64_t na = h_tot & 0xFFFFFFFFll, nd = h_tot >> 32, ns = P - na - nd;
-        grow(adm, n_adm, n_adm + na, s);
-        grow(dense, n_dense, n_dense + nd, s);
-        nxt.alloc(std::max<int64_t>(4 * ns, 1), s);
-        k_emit<<<grid_for(P), NT, 0, s>>>(cur.p, P, flag.p, off.p, nxt.p, adm.p, n_adm,
-                                         dense.p, n_dense); note_launch();
-        HM_LAUNCH("emit");
-        n_adm += na;
-        n_dense += nd;
-        P = 4 * ns;
-        std::swap(cur, nxt);
+        if (hovf) {
+            kappa *= 2;
+            continue;
+        }
+        if (hc[0] != 0) fail(HM_EOVERFLOW, "block tree deeper than the cluster trees");
+        R.n_adm = hc[1];
+        R.n_dense = hc[2];
+        R.traversal_reruns = attempt;
+        // admissible leaves at the front of the arena, dense leaves at its back
+        canonical_sort(leaves.p, R.n_adm, adm, lo, R.N, lo2, Cs.N, s);
+        canonical_sort(leaves.p + (bsum - R.n_dense), R.n_dense, dense, lo, R.N, lo2, Cs.N, s);
+        return;                            // the arena's free is stream-ordered
     }
-    R.n_adm = n_adm;
-    R.n_dense = n_dense;
-    canonical_sort(adm, n_adm, lo, R.N, lo2, Cs.N, s);
-    canonical_sort(dense, n_dense, lo, R.N, lo2, Cs.N, s);
 }
+
+void set_traversal_kappa(int64_t k) { g_trav_kappa = k; }
+void set_traversal_attempts(int n) { g_trav_attempts = n; }
 
 void build_structure(const double* pts, SetStructure& S, double eta, int adm_max,
                      const DeviceCoords& X, int64_t* perm_out, uint64_t* codes_out,

@@ -127,6 +127,11 @@ void set_mvp_wait_ns(uint64_t ns);
 void set_mvp_withhold(int k);
 void set_aca_shape(int cls, int shape);
 void set_aca_step_limit(int v);
+// Test hooks of the traversal (process-wide): the first level-bound factor
+// kappa (0: the default for the dimension and eta) and the number of
+// traversals tried before HM_EOVERFLOW (0: 16).
+void set_traversal_kappa(int64_t k);
+void set_traversal_attempts(int n);
 
 // ---------------------------------------------------------------------------
 // Product layout. The product gathers, for every row tile (a leaf of the

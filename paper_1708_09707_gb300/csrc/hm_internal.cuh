@@ -96,6 +96,10 @@ void scan_exclusive_i64(const int64_t* in, int64_t* out, int64_t n,
                         int64_t* total, cudaStream_t s);
 void scan_exclusive_i32(const int32_t* in, int32_t* out, int64_t n,
                         int32_t* total, cudaStream_t s);
+// The same over n = min(*ndev, nmax) entries, n read on the device (ndev a
+// device pointer); no host synchronisation.
+void scan_exclusive_i64_dev(const int64_t* in, int64_t* out, const int64_t* ndev, int64_t nmax,
+                            int64_t* total, cudaStream_t s);
 // Stable LSD radix sort of (key, value) on the low key_bits bits.
 void radix_sort_u64_u32(uint64_t* keys, uint32_t* vals, int64_t n, int key_bits,
                         cudaStream_t s);
@@ -132,6 +136,7 @@ struct SetStructure {
     int64_t row0 = 0;      // first Morton row of this set in the concatenation
     int64_t node0 = 0;     // first node of this set in the node arrays
     int64_t n_adm = 0, n_dense = 0;
+    int traversal_reruns = 0;  // traversals run again with larger level bounds
 };
 
 }  // namespace hm

@@ -1166,6 +1166,7 @@ void build_sets(hm_handle_s& h, int nsets, const double* points_all, const int64
             h.n_dense += S.n_dense;
         }
     }
+    for (const SetStructure& S : h.sets) h.stats.traversal_reruns += S.traversal_reruns;
     // perm holds set-local indices; make them absolute for the product
     // (the offsets are applied below by a small kernel per set)
     h.adm_pairs.alloc(std::max<int64_t>(h.n_adm, 1), s);

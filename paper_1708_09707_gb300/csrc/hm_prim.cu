@@ -5,6 +5,7 @@
 // inter-block spin waits: the scan is reduce -> scan partials -> downsweep and
 // each radix pass is histogram -> scan -> scatter, so no launch can hang on
 // another block's progress.
+#include <algorithm>
 #include <mutex>
 #include <string>
 
@@ -114,6 +115,73 @@ void scan_exclusive(const T* in, T* out, int64_t n, T* total, cudaStream_t s)
     k_scan_partials<T><<<1, SCAN_THREADS, 0, s>>>(part.p, tiles, total); note_launch();
     k_scan_down<T><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, out, n, part.p); note_launch();
     HM_LAUNCH("scan");
+}
+
+// Device-count variant: the scan covers n = min(*ndev, nmax) entries, n read
+// on the device, so that a caller can chain launches whose sizes are known
+// only on the device. The grids are sized for nmax but stride over the tiles
+// of n, so the work follows n.
+template <class T>
+__global__ void k_scan_reduce_dev(const T* __restrict__ in, const int64_t* __restrict__ ndev,
+                                  int64_t nmax, T* __restrict__ part)
+{
+    __shared__ T tot;
+    const int64_t n = *ndev < nmax ? *ndev : nmax;
+    const int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const int64_t base = t * SCAN_TILE;
+        T s = 0;
+#pragma unroll
+        for (int k = 0; k < SCAN_ITEMS; ++k) {
+            const int64_t i = base + (int64_t)threadIdx.x * SCAN_ITEMS + k;
+            if (i < n) s += in[i];
+        }
+        block_exclusive_scan<T, SCAN_THREADS>(s, &tot);
+        if (threadIdx.x == 0) part[t] = tot;
+    }
+}
+
+template <class T>
+__global__ void k_scan_partials_dev(T* part, const int64_t* __restrict__ ndev, int64_t nmax,
+                                    T* total)
+{
+    __shared__ T tot;
+    const int64_t n = *ndev < nmax ? *ndev : nmax;
+    const int64_t np = (n + SCAN_TILE - 1) / SCAN_TILE;
+    T carry = 0;
+    for (int64_t c = 0; c < np; c += SCAN_THREADS) {
+        const int64_t i = c + threadIdx.x;
+        const T v = (i < np) ? part[i] : T(0);
+        const T ex = block_exclusive_scan<T, SCAN_THREADS>(v, &tot);
+        if (i < np) part[i] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0 && total) *total = carry;
+}
+
+template <class T>
+__global__ void k_scan_down_dev(const T* in, T* out, const int64_t* __restrict__ ndev,
+                                int64_t nmax, const T* __restrict__ part)
+{
+    __shared__ T tot;
+    const int64_t n = *ndev < nmax ? *ndev : nmax;
+    const int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const int64_t base = t * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+        T v[SCAN_ITEMS];
+        T s = 0;
+#pragma unroll
+        for (int k = 0; k < SCAN_ITEMS; ++k) {
+            v[k] = (base + k < n) ? in[base + k] : T(0);
+            s += v[k];
+        }
+        T ex = block_exclusive_scan<T, SCAN_THREADS>(s, &tot) + part[t];
+#pragma unroll
+        for (int k = 0; k < SCAN_ITEMS; ++k) {
+            if (base + k < n) out[base + k] = ex;
+            ex += v[k];
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -227,6 +295,18 @@ void scan_exclusive_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* tot
                         cudaStream_t s)
 {
     scan_exclusive<int64_t>(in, out, n, total, s);
+}
+
+void scan_exclusive_i64_dev(const int64_t* in, int64_t* out, const int64_t* ndev, int64_t nmax,
+                            int64_t* total, cudaStream_t s)
+{
+    const int64_t tiles = std::max<int64_t>(1, ceil_div(nmax, SCAN_TILE));
+    const unsigned grid = (unsigned)std::min<int64_t>(tiles, 4 * (int64_t)num_sms());
+    DevBuf<int64_t> part(tiles, s);
+    k_scan_reduce_dev<int64_t><<<grid, SCAN_THREADS, 0, s>>>(in, ndev, nmax, part.p); note_launch();
+    k_scan_partials_dev<int64_t><<<1, SCAN_THREADS, 0, s>>>(part.p, ndev, nmax, total); note_launch();
+    k_scan_down_dev<int64_t><<<grid, SCAN_THREADS, 0, s>>>(in, out, ndev, nmax, part.p); note_launch();
+    HM_LAUNCH("scan");
 }
 
 void scan_exclusive_i32(const int32_t* in, int32_t* out, int64_t n, int32_t* total,

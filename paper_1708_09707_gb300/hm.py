@@ -61,7 +61,7 @@ class Stats(C.Structure):
                 ("mvp_vtx_bytes", C.c_int64), ("mvp_tile_bytes", C.c_int64),
                 ("t_aca_class_ms", C.c_double * 12),
                 ("t_np_aca_ms", C.c_double), ("t_np_lowrank_ms", C.c_double),
-                ("t_np_near_ms", C.c_double)]
+                ("t_np_near_ms", C.c_double), ("traversal_reruns", C.c_int)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -403,6 +403,7 @@ def set_aca_shape(cls: int, shape: int) -> None:
 
 
 HOOK_ACA_STEP_LIMIT, HOOK_WAIT_LIMIT_NS, HOOK_GATHER_WITHHOLD, HOOK_FAIL_ALLOC = 0, 1, 2, 3
+HOOK_TRAVERSAL_KAPPA, HOOK_TRAVERSAL_TRIES = 4, 5
 
 
 def set_test_hook(hook: int, value: int) -> None:

@@ -44,6 +44,10 @@ int main(void) {
     printf("off_on_the_fly %zu\n", offsetof(hm_options, on_the_fly));
     printf("off_row_lo %zu\n", offsetof(hm_options, row_lo));
     printf("off_row_hi %zu\n", offsetof(hm_options, row_hi));
+    printf("sizeof_stats %zu\n", sizeof(hm_stats));
+    printf("soff_t_aca_class_ms %zu\n", offsetof(hm_stats, t_aca_class_ms));
+    printf("soff_t_np_near_ms %zu\n", offsetof(hm_stats, t_np_near_ms));
+    printf("soff_traversal_reruns %zu\n", offsetof(hm_stats, traversal_reruns));
     return 0;
 }
 """
@@ -65,8 +69,11 @@ def test_options_and_stats_layout():
     assert ctypes.sizeof(hm.Options) == c["sizeof_options"] == 96
     for f in ("stream", "on_the_fly", "row_lo", "row_hi"):
         assert getattr(hm.Options, f).offset == c["off_" + f], f
-    assert ctypes.sizeof(hm.Stats) == (8 * 5 + 4 * 2 + 8 + 8 + 8 * 9 + 8 * 4 + 4 * 3 + 4
-                                       + 8 + 8 + 8 + 8 * 4 + 8 * 2 + 8 * 12 + 8 * 3)
+    assert ctypes.sizeof(hm.Stats) == c["sizeof_stats"] == (
+        8 * 5 + 4 * 2 + 8 + 8 + 8 * 9 + 8 * 4 + 4 * 3 + 4 + 8 + 8 + 8 + 8 * 4 + 8 * 2 + 8 * 12
+        + 8 * 3 + 8)
+    for f in ("t_aca_class_ms", "t_np_near_ms", "traversal_reruns"):
+        assert getattr(hm.Stats, f).offset == c["soff_" + f], f
 
 
 def test_library_is_not_a_cpu_fallback():
@@ -75,3 +82,17 @@ def test_library_is_not_a_cpu_fallback():
     from paper_1708_09707_gb300 import hm
     src = open(hm.__file__).read()
     assert "oracle" not in src
+
+
+def test_test_hook_ranges_without_a_gpu():
+    # hm_set_test_hook only records process-wide settings: no device call
+    from paper_1708_09707_gb300 import build, hm
+    build.build()
+    L = hm.lib()
+    assert L.hm_set_test_hook(hm.HOOK_TRAVERSAL_KAPPA, -1) == hm.EINVAL
+    assert L.hm_set_test_hook(hm.HOOK_TRAVERSAL_KAPPA, (1 << 20) + 1) == hm.EINVAL
+    assert L.hm_set_test_hook(hm.HOOK_TRAVERSAL_TRIES, 65) == hm.EINVAL
+    assert L.hm_set_test_hook(99, 1) == hm.EINVAL
+    for hook in (hm.HOOK_TRAVERSAL_KAPPA, hm.HOOK_TRAVERSAL_TRIES):
+        assert L.hm_set_test_hook(hook, 3) == hm.OK
+        assert L.hm_set_test_hook(hook, 0) == hm.OK

@@ -8,6 +8,11 @@
 - An allocation fails: the n-th device allocation from now is made to fail;
   the build returns HM_ENOMEM with no handle, and the library holds no more
   device memory afterwards than before.
+- A level of the block-tree traversal does not fit its bound: with the
+  first bound forced down to min(4^l, 2^l) pairs the traversal overflows on
+  the device, the host runs it again with doubled bounds, and the leaf lists
+  are those of a traversal that fitted at once; allowed a single traversal,
+  the build returns HM_EOVERFLOW instead and holds no device memory after.
 The ACA iteration-limit hook is covered in test_gpu_aca_shapes.py.
 """
 import numpy as np
@@ -27,7 +32,8 @@ def hm():
     build.build()
     H.lib()
     yield H
-    for hook in (H.HOOK_WAIT_LIMIT_NS, H.HOOK_GATHER_WITHHOLD, H.HOOK_FAIL_ALLOC):
+    for hook in (H.HOOK_WAIT_LIMIT_NS, H.HOOK_GATHER_WITHHOLD, H.HOOK_FAIL_ALLOC,
+                 H.HOOK_TRAVERSAL_KAPPA, H.HOOK_TRAVERSAL_TRIES):
         H.set_test_hook(hook, 0)
     H.set_gather_shape(-1)
 
@@ -113,3 +119,53 @@ def test_injected_allocation_failure(hm, prec):
     H.free()
     assert np.isfinite(y).all()
     assert hm.device_bytes() == base
+
+
+def _structure(hm, pts, cols=None, **kw):
+    if cols is None:
+        H = hm.HMatrix(pts, 0, 0.1, 32, 1.0, 1e-6, structure_only=True, **kw)
+    else:
+        H = hm.HMatrix(pts, 0, 0.1, 32, 1.0, 1e-6, structure_only=True, cols=cols, **kw)
+    st, reruns = H.structure(), H.stats()["traversal_reruns"]
+    H.free()
+    return st, reruns
+
+
+@pytest.mark.parametrize("case", ["uniform1d", "mixture2d", "uniform3d", "rect3d"])
+def test_traversal_overflow_reruns_transparently(hm, case):
+    d = {"uniform1d": 1, "mixture2d": 2, "uniform3d": 3, "rect3d": 3}[case]
+    n = 1 << 14
+    pts = (inputs.mixture_points(n, d, 31) if case == "mixture2d"
+           else inputs.uniform_points(n, d, 31))
+    cols = inputs.uniform_points(n // 2 + 77, d, 32) if case == "rect3d" else None
+    ref, r0 = _structure(hm, pts, cols)
+    assert r0 == 0                          # the default bounds fit
+    hm.set_test_hook(hm.HOOK_TRAVERSAL_KAPPA, 1)
+    try:
+        got, r1 = _structure(hm, pts, cols)
+    finally:
+        hm.set_test_hook(hm.HOOK_TRAVERSAL_KAPPA, 0)
+    assert r1 >= 2, r1                      # the forced bound overflowed
+    for k in ("adm", "dense", "perm"):
+        assert np.array_equal(got[k], ref[k]), k
+
+
+def test_traversal_overflow_reports_eoverflow(hm):
+    import torch
+    pts = inputs.mixture_points(1 << 14, 2, 33)
+    torch.cuda.synchronize()
+    base = hm.device_bytes()
+    hm.set_test_hook(hm.HOOK_TRAVERSAL_KAPPA, 1)
+    hm.set_test_hook(hm.HOOK_TRAVERSAL_TRIES, 1)
+    try:
+        with pytest.raises(hm.HMError) as ei:
+            hm.HMatrix(pts, 0, 0.1, 32, 1.0, 1e-6)
+        assert ei.value.code == hm.EOVERFLOW
+    finally:
+        hm.set_test_hook(hm.HOOK_TRAVERSAL_TRIES, 0)
+        hm.set_test_hook(hm.HOOK_TRAVERSAL_KAPPA, 0)
+    torch.cuda.synchronize()
+    assert hm.device_bytes() == base
+    H = hm.HMatrix(pts, 0, 0.1, 32, 1.0, 1e-6)
+    assert H.stats()["traversal_reruns"] == 0
+    H.free()
