@@ -57,6 +57,9 @@ def parse():
     p.add_argument("--sweeps", action="store_true",
                    help="instead of the step: the paper's experiments as curves (Sec. 6.4 "
                         "convergence in k, Sec. 6.5 runtime against N), one JSON line")
+    p.add_argument("--batching-study", action="store_true",
+                   help="instead of the step: the batching study of Sec. 6.4 (ACA and "
+                        "gather time against the batch size), one JSON line")
     p.add_argument("--no-large", action="store_true",
                    help="skip the 2^22-point CG workload and the FP64 on-the-fly 3-D workload")
     p.add_argument("--no-rect", action="store_true",
@@ -724,6 +727,66 @@ def run_sweeps(args):
     print(json.dumps({"sweeps": out}))
 
 
+def run_batching(args):
+    """The batching study of Sec. 6.4 on this GPU: the paper's setting
+    (Halton points in [0,1]^2, exp(-r^2), eta 1.5, fixed rank 16, FP64) with
+    C_leaf 1024 and 2048, at N = 2^19 (the stored FP64 near field of
+    C_leaf 2048 at 2^20 is 232 GB, more than one GPU holds). Batch sizes:
+      ACA     reserved factor entries per launch (bs_ACA; 1 = one launch per
+              block, 0 = one launch per size class); the build's ACA time
+      gather  work items per launch of the product's gather (an item is a
+              row tile's near-field blocks and U slices; 1 = one launch per
+              item, 0 = one launch); the product's time, mean of 3
+    Every batch size gives the same ranks and bit-identical products (checked
+    here)."""
+    import torch
+    from paper_1708_09707_gb300 import build, hm, inputs
+    build.build()
+    hm.lib()
+    stream = torch.cuda.current_stream()
+    n = 1 << 19
+    pts = torch.from_numpy(inputs.halton_points(n, 2)).cuda()
+    x = torch.from_numpy(inputs.normal_vector(n, inputs.X_SEED)).cuda()
+    y = torch.empty_like(x)
+    out = {"n": n, "d": 2, "kernel": "exp(-r^2)", "eta": 1.5, "aca": "fixed rank 16",
+           "precision": "fp64", "points": "halton", "leaves": []}
+    hm.set_gather_shape(0)     # one launch shape for every batch size
+    try:
+        for leaf in (1024, 2048):
+            row = {"leaf": leaf, "aca": [], "gather": []}
+            ref_y = ref_rank = None
+            for bs in (0, 1 << 27, 1 << 25, 1 << 23, 1 << 21, 1 << 19, 1):
+                hm.set_batch_limits(bs, 0)
+                H = hm.HMatrix(pts, hm.GAUSSIAN, 1.0, leaf, 1.5, 0.0, k_cap=16)
+                st = H.stats()
+                yv = H.matvec(x)
+                rk = H.structure()["ranks"]
+                H.free()
+                if ref_y is None:
+                    ref_y, ref_rank = yv, rk
+                    row["n_adm"], row["n_dense"] = st["n_adm"], st["n_dense"]
+                row["aca"].append({"bs_aca": bs, "aca_ms": st["t_aca_ms"],
+                                   "same": bool(torch.equal(yv, ref_y)
+                                                and (rk == ref_rank).all())})
+            hm.set_batch_limits(0, 0)
+            H = hm.HMatrix(pts, hm.GAUSSIAN, 1.0, leaf, 1.5, 0.0, k_cap=16)
+            H.matvec(x, y)
+            ref = y.clone()
+            for items in (0, 1024, 256, 64, 16, 4, 1):
+                hm.set_batch_limits(0, items)
+                H.matvec(x, y)
+                same = bool(torch.equal(y, ref))
+                t, _ = _elapsed(lambda: [H.matvec(x, y) for _ in range(3)], stream)
+                row["gather"].append({"items_per_launch": items, "mvp_ms": t / 3, "same": same})
+            row["n_items"] = H.stats()["n_tiles"]
+            H.free()
+            out["leaves"].append(row)
+    finally:
+        hm.set_batch_limits(0, 0)
+        hm.set_gather_shape(-1)
+    print(json.dumps({"batching": out}))
+
+
 # ---------------------------------------------------------------- GPU leg
 def main():
     args = parse()
@@ -735,6 +798,9 @@ def main():
         return
     if args.sweeps:
         run_sweeps(args)
+        return
+    if args.batching_study:
+        run_batching(args)
         return
     import torch
 

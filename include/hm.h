@@ -211,6 +211,22 @@ uint64_t hm_kernel_launches(void);
  * Returns HM_EINVAL for other values. */
 int hm_set_gather_shape(int shape);
 
+/* Batching sizes (Sec. 5.4.1, bs_ACA; Sec. 5.4.2, bs_dense; a measurement
+ * control for the batching study of Sec. 6.4, not part of the method).
+ *   aca_entries  > 0: one ACA launch takes consecutive blocks of one size
+ *                class and rank bucket while their reserved factor entries
+ *                sum_b k_res,b (m_b + n_b) stay <= aca_entries (at least one
+ *                block per launch; 1 gives one launch per block);
+ *                0 (default): one launch per class and bucket.
+ *   gather_items > 0: the one-vector product's gather runs as launches of at
+ *                most this many work items (an item is a row tile's U slices and
+ *                near-field blocks, up to 4096 columns; 1 gives one launch
+ *                per item); 0 (default): one launch.
+ * Results do not depend on either: every block and item computes the same
+ * values whatever launch it runs in. Process-wide; applies to builds and
+ * products started afterwards. Returns HM_EINVAL for negative values. */
+int hm_set_batch_limits(int64_t aca_entries, int64_t gather_items);
+
 /* Launch shape of the batched ACA of one block size class (Sec. 5.4.1
  * batching; a tuning control, not part of the method). Size class c holds
  * the admissible blocks with 2^(c+5) < max(m, n) <= 2^(c+6) (class 0 from 1,

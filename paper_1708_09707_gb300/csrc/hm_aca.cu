@@ -23,6 +23,18 @@ struct ShapeInit {
 int aca_shape(int cls) { return g_aca_shape[cls].load(); }
 int aca_default_shape(int cls) { return cls <= 8 ? 1 : 0; }
 int aca_step_limit() { return g_aca_step_limit.load(); }
+
+namespace {
+std::atomic<int64_t> g_aca_batch{0}, g_mvp_batch{0};
+}  // namespace
+
+int64_t aca_batch_entries() { return g_aca_batch.load(); }
+int64_t mvp_batch_items() { return g_mvp_batch.load(); }
+void set_batch_limits(int64_t aca_entries, int64_t gather_items)
+{
+    g_aca_batch = aca_entries;
+    g_mvp_batch = gather_items;
+}
 void set_aca_shape(int cls, int shape) { g_aca_shape[cls] = shape; }
 void set_aca_step_limit(int v) { g_aca_step_limit = v; }
 

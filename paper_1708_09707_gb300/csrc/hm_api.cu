@@ -193,6 +193,17 @@ int hm_set_aca_shape(int cls, int shape)
     return HM_OK;
 }
 
+int hm_set_batch_limits(int64_t aca_entries, int64_t gather_items)
+{
+    set_error("");
+    if (aca_entries < 0 || gather_items < 0) {
+        set_error("batch limits must be >= 0");
+        return HM_EINVAL;
+    }
+    hm::set_batch_limits(aca_entries, gather_items);
+    return HM_OK;
+}
+
 int hm_set_test_hook(int hook, int64_t value)
 {
     set_error("");

@@ -132,6 +132,11 @@ void set_aca_step_limit(int v);
 // traversals tried before HM_EOVERFLOW (0: 16).
 void set_traversal_kappa(int64_t k);
 void set_traversal_attempts(int n);
+// Batching sizes (hm_set_batch_limits; 0: unlimited): reserved factor entries
+// per ACA launch and work items per gather launch.
+int64_t aca_batch_entries();
+int64_t mvp_batch_items();
+void set_batch_limits(int64_t aca_entries, int64_t gather_items);
 
 // ---------------------------------------------------------------------------
 // Product layout. The product gathers, for every row tile (a leaf of the

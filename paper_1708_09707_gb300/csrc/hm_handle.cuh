@@ -118,7 +118,8 @@ void export_factors(hm_handle_s& h, int64_t b, double* U, double* V, int* rank);
 void add_perm_offsets(hm_handle_s& h);
 void fill_block_sets(hm_handle_s& h);
 void alloc_factor_meta(hm_handle_s& h);
-void compress(hm_handle_s& h, const uint32_t* ids, int64_t n, const int32_t* kpred);
+void compress(hm_handle_s& h, const uint32_t* ids, int64_t n, const int32_t* kpred,
+              bool keep_reserved = false);
 // learned rank model (hm_mlp.cu)
 void predict_ranks(hm_handle_s& h, int32_t* kpred);
 void rerun_mispredicted(hm_handle_s& h);

@@ -324,7 +324,7 @@ void rerun_mispredicted(hm_handle_s& h)
     DevBuf<uint32_t> ids(cnt, s);
     k_emit_ids<<<grid_for(n), NT, 0, s>>>(f.p, off.p, n, ids.p); note_launch();
     HM_LAUNCH("mispredicted ids");
-    compress(h, ids.p, cnt, nullptr);
+    compress(h, ids.p, cnt, nullptr, true);
 }
 
 }  // namespace hm

@@ -1074,7 +1074,19 @@ void run_typed(const MvpPlan& P, R* xm, R* t, R* tp, double* part, const double*
     if (P.n_tiles > 0) {
         int v = tile_variant(P);
         if (v < 0) v = tune_tile<R, FMT>(P, xm, t, part, s);
-        launch_tile<R, FMT>(v, P, xm, t, part, s);
+        const int64_t bs = mvp_batch_items();
+        if (bs > 0 && bs < P.n_items) {
+            // launches of at most bs work items; each item keeps its partial
+            // slot, so the sums are those of one launch
+            for (int64_t i0 = 0; i0 < P.n_items; i0 += bs) {
+                MvpPlan Q = P;
+                Q.items = P.items + i0;
+                Q.n_items = std::min(bs, P.n_items - i0);
+                launch_tile<R, FMT>(v, Q, xm, t, part + i0 * P.max_ld, s);
+            }
+        } else {
+            launch_tile<R, FMT>(v, P, xm, t, part, s);
+        }
         k_tile_finish<<<grid_for(P.n_tiles * 32), NT, 0, s>>>(P, part, x, y, accumulate); note_launch();
     }
     if (rec) HM_CUDA(cudaEventRecord(rec->e[3], s));

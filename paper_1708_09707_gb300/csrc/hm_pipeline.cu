@@ -558,7 +558,19 @@ void aca_range(hm_handle_s& h, const AcaOrder& O, const AcaArgs& a, int64_t q0, 
             if (hi <= lo) continue;
             if (!any) HM_CUDA(cudaEventRecord(cs.t0[c], sc));
             any = true;
-            aca_run(h.precision, h.kp, h.X, a, O.order.p + lo, hi - lo, c, kb, h.max_set_n, sc);
+            const int64_t bs = aca_batch_entries();
+            if (bs <= 0) {
+                aca_run(h.precision, h.kp, h.X, a, O.order.p + lo, hi - lo, c, kb, h.max_set_n, sc);
+                continue;
+            }
+            // batches of consecutive blocks with at most bs reserved entries
+            for (int64_t b0 = lo; b0 < hi;) {
+                int64_t b1 = std::upper_bound(O.hpre.begin() + b0 + 1, O.hpre.begin() + hi + 1,
+                                              O.hpre[b0] + bs) - O.hpre.begin() - 1;
+                b1 = std::max(b1, b0 + 1);
+                aca_run(h.precision, h.kp, h.X, a, O.order.p + b0, b1 - b0, c, kb, h.max_set_n, sc);
+                b0 = b1;
+            }
         }
         if (any) {
             HM_CUDA(cudaEventRecord(cs.t1[c], sc));
@@ -582,7 +594,12 @@ int64_t scratch_entries(hm_handle_s& h, int esz)
 // ACA of the admissible blocks ids[0..n) (all blocks when ids is null); see
 // the file comment for the two storage modes (kpred != null: learned sizing,
 // one arena; else bounded scratch passes with exact final segments).
-void compress(hm_handle_s& h, const uint32_t* ids, int64_t n, const int32_t* kpred)
+// keep_reserved: when one scratch pass holds every block, the scratch itself
+// becomes the blocks' storage (their rank-k columns are the prefixes of their
+// reservations), with no copy into exact segments; used for the few blocks a
+// rank model under-predicted.
+void compress(hm_handle_s& h, const uint32_t* ids, int64_t n, const int32_t* kpred,
+              bool keep_reserved)
 {
     cudaStream_t s = h.stream;
     const int esz = h.precision == HM_PREC_FP64 ? 8 : 4;
@@ -628,6 +645,14 @@ void compress(hm_handle_s& h, const uint32_t* ids, int64_t n, const int32_t* kpr
                                                      scratch.p, vbase, esz, h.Uptr.p, h.Vptr.p); note_launch();
         HM_LAUNCH("set ptrs");
         aca_range(h, O, a, q0, q1);
+        if (keep_reserved && q0 == 0 && q1 == n) {
+            // kept in the V segments, which live as long as the handle
+            auto seg = std::make_unique<FactorSegment>();
+            seg->mem = std::move(scratch);
+            h.vsegments.push_back(std::move(seg));
+            ++passes;
+            break;
+        }
         const int64_t nq = q1 - q0;
         DevBuf<int64_t> fsu(nq, s), fsv(nq, s), foffu(nq + 1, s), foffv(nq + 1, s);
         k_final_size<<<grid_for(nq), NT, 0, s>>>(h.ablk.p, O.order.p, q0, q1, h.rank.p, fsu.p, fsv.p); note_launch();

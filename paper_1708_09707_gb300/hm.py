@@ -98,6 +98,7 @@ def _declare(L):
     L.hm_set_gather_shape.argtypes = [C.c_int]
     L.hm_set_aca_shape.argtypes = [C.c_int, C.c_int]
     L.hm_set_test_hook.argtypes = [C.c_int, C.c_int64]
+    L.hm_set_batch_limits.argtypes = [C.c_int64, C.c_int64]
     L.hm_check_status.argtypes = [_vp]
     L.hm_device_bytes.restype = C.c_uint64
     L.hm_device_bytes.argtypes = []
@@ -400,6 +401,13 @@ def set_aca_shape(cls: int, shape: int) -> None:
     (-1 every class); shape -1 default, 0 the cluster kernels, 1 the default team
     shape, 2 another team shape."""
     _check(lib().hm_set_aca_shape(int(cls), int(shape)))
+
+
+def set_batch_limits(aca_entries: int = 0, gather_items: int = 0) -> None:
+    """hm_set_batch_limits: reserved factor entries per ACA launch and work
+    items per gather launch (0: one launch per size class / one gather
+    launch); a control for the batching study, not part of the method."""
+    _check(lib().hm_set_batch_limits(int(aca_entries), int(gather_items)))
 
 
 HOOK_ACA_STEP_LIMIT, HOOK_WAIT_LIMIT_NS, HOOK_GATHER_WITHHOLD, HOOK_FAIL_ALLOC = 0, 1, 2, 3

@@ -96,3 +96,13 @@ def test_test_hook_ranges_without_a_gpu():
     for hook in (hm.HOOK_TRAVERSAL_KAPPA, hm.HOOK_TRAVERSAL_TRIES):
         assert L.hm_set_test_hook(hook, 3) == hm.OK
         assert L.hm_set_test_hook(hook, 0) == hm.OK
+
+
+def test_batch_limits_without_a_gpu():
+    from paper_1708_09707_gb300 import build, hm
+    build.build()
+    L = hm.lib()
+    assert L.hm_set_batch_limits(-1, 0) == hm.EINVAL
+    assert L.hm_set_batch_limits(0, -5) == hm.EINVAL
+    assert L.hm_set_batch_limits(1 << 20, 16) == hm.OK
+    assert L.hm_set_batch_limits(0, 0) == hm.OK
