@@ -907,6 +907,15 @@ def main():
         t64, b64, m64, s64, _ = timed(hm.PREC_FP64, 1, 1, False, model=False, name="compare_fp64")
         fp64 = {"build_s": b64 / 1e3, "mvp_ms": m64, "ms_per_step": t64,
                 "mvp_roofline_frac": s64[-1]["mvp_bytes"] / (m64 * 1e-3) / (hbm * 1e9)}
+        # the FP64 product is bound by the FP64 pipe before HBM: one
+        # multiply-add (2 flops) per 8-byte entry streamed, so at most
+        # 4 B per flop x the measured FP64 FMA throughput
+        p64 = hm.alu_peak(hm.PREC_FP64)
+        fp64["fp64_pipe_bound"] = {
+            "peak_tflops": p64 / 1e12, "bound_gbs": 4.0 * p64 / 1e9,
+            "achieved_gbs": s64[-1]["mvp_bytes"] / (m64 * 1e-3) / 1e9,
+            "frac": s64[-1]["mvp_bytes"] / (m64 * 1e-3) / (4.0 * p64),
+            "peak_source": "measured: FP64 FMA chains on every SM (hm_alu_peak)"}
         H64 = hm.HMatrix(pts, w["kernel"], w["ell"], w["leaf"], w["eta"], w["eps"],
                          precision=hm.PREC_FP64, **kw)
         y64 = H64.matvec(x).cpu().numpy()
