@@ -57,6 +57,8 @@ def parse():
     p.add_argument("--sweeps", action="store_true",
                    help="instead of the step: the paper's experiments as curves (Sec. 6.4 "
                         "convergence in k, Sec. 6.5 runtime against N), one JSON line")
+    p.add_argument("--aca-tune", default="on", choices=["on", "off"],
+                   help="time the ACA launch shapes per size class before the timed steps")
     p.add_argument("--batching-study", action="store_true",
                    help="instead of the step: the batching study of Sec. 6.4 (ACA and "
                         "gather time against the batch size), one JSON line")
@@ -891,6 +893,20 @@ def main():
         mvp = np.mean([e[1].elapsed_time(e[2]) for e in evs]) / N_MVP
         return total, build, mvp, stats, launches
 
+    # ACA launch shapes tuned on this problem before anything is timed (the
+    # gather's shape is tuned by its first product the same way)
+    aca_shapes = None
+    if args.aca_tune == "on":
+        tk = dict(kw)
+        tk["symmetric"] = use_sym
+        if theta is not None:
+            tk["rank_model_theta"] = theta
+        t_t = time.time()
+        aca_shapes = {"shapes_by_class": hm.tune_aca_shapes(
+            pts, w["kernel"], w["ell"], w["leaf"], w["eta"], w["eps"], reps=2,
+            precision=hm.PREC_MIXED, **tk)}
+        aca_shapes["tune_s"] = time.time() - t_t
+
     hbm, peak_src = peaks()
     with ClockSampler(local) as clk:
         total, build_ms, mvp_ms, stats, launches = timed(hm.PREC_MIXED, args.steps,
@@ -1154,6 +1170,7 @@ def main():
                 "h2d_bytes_per_step": N * d * 8 + N_MVP * N * 8,
                 "d2h_bytes_per_step": N_MVP * N * 8},
         "roofline": dominant, "mvp_roofline": mvp_roof, "aca_roofline": aca_roof,
+        "aca_shapes": aca_shapes,
         "gpu_launches": int(round(launches)),
         "clocks": clocks,
         "cpu_baseline": cpu,

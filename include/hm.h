@@ -211,6 +211,21 @@ uint64_t hm_kernel_launches(void);
  * Returns HM_EINVAL for other values. */
 int hm_set_gather_shape(int shape);
 
+/* ACA launch-shape autotuner (Sec. 6.4 tunes the batching parameters by
+ * hand; a tuning control, not part of the method). Builds the given problem
+ * (arguments as hm_build_ex; on_the_fly must be 0) reps times with each of
+ * the shapes 0, 1, 2 of hm_set_aca_shape for every size class, the classes
+ * run one after another (profile 2) so that each has its own CUDA-event
+ * time, keeps per class the shape of the least time (min over reps), and
+ * sets it as by hm_set_aca_shape(class, shape) for later builds. shapes
+ * (may be NULL) receives the 12 chosen shapes (-1: class empty, default
+ * kept). Shapes give the same approximation up to the order of their sums.
+ * On failure the earlier shapes are restored and the build's status is
+ * returned. */
+int hm_tune_aca_shapes(const double* points, int64_t N, int d, int kernel, const double* params,
+                       int leaf_size, double eta, double aca_eps, const hm_options* opt,
+                       int reps, int* shapes);
+
 /* Batching sizes (Sec. 5.4.1, bs_ACA; Sec. 5.4.2, bs_dense; a measurement
  * control for the batching study of Sec. 6.4, not part of the method).
  *   aca_entries  > 0: one ACA launch takes consecutive blocks of one size

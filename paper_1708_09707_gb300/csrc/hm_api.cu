@@ -193,6 +193,52 @@ int hm_set_aca_shape(int cls, int shape)
     return HM_OK;
 }
 
+int hm_tune_aca_shapes(const double* points, int64_t N, int d, int kernel, const double* params,
+                       int leaf_size, double eta, double aca_eps, const hm_options* opt,
+                       int reps, int* shapes)
+{
+    set_error("");
+    int saved[hm::ACA_NCLASS];
+    for (int c = 0; c < hm::ACA_NCLASS; ++c) saved[c] = hm::aca_shape(c);
+    try {
+        hm_options o;
+        hm_options_default(&o);
+        if (opt) o = *opt;
+        if (o.on_the_fly) fail(HM_EINVAL, "ACA shape tuning builds stored factors (on_the_fly = 0)");
+        if (reps < 1) reps = 1;
+        o.profile = 2;   // size classes one after another: one time per class
+        constexpr int NS = 3;
+        double t[NS][hm::ACA_NCLASS];
+        for (int sh = 0; sh < NS; ++sh) {
+            for (int c = 0; c < hm::ACA_NCLASS; ++c) {
+                t[sh][c] = -1.0;
+                hm::set_aca_shape(c, sh);
+            }
+            for (int r = 0; r < reps; ++r) {
+                std::unique_ptr<hm_handle_s> h(new hm_handle_s());
+                int64_t Ns[1] = {N};
+                int ds[1] = {d};
+                build_sets(*h, 1, points, Ns, ds, kernel, params, leaf_size, eta, aca_eps, o);
+                for (int c = 0; c < hm::ACA_NCLASS; ++c) {
+                    const double v = h->stats.t_aca_class_ms[c];
+                    if (v > 0.0 && (t[sh][c] < 0.0 || v < t[sh][c])) t[sh][c] = v;
+                }
+            }
+        }
+        for (int c = 0; c < hm::ACA_NCLASS; ++c) {
+            int best = -1;
+            for (int sh = 0; sh < NS; ++sh)
+                if (t[sh][c] > 0.0 && (best < 0 || t[sh][c] < t[best][c])) best = sh;
+            hm::set_aca_shape(c, best);    // -1 (the default) for an empty class
+            if (shapes) shapes[c] = best;
+        }
+        return HM_OK;
+    } catch (const std::exception& e) {
+        for (int c = 0; c < hm::ACA_NCLASS; ++c) hm::set_aca_shape(c, saved[c]);
+        return to_status(e);
+    }
+}
+
 int hm_set_batch_limits(int64_t aca_entries, int64_t gather_items)
 {
     set_error("");

@@ -99,6 +99,8 @@ def _declare(L):
     L.hm_set_aca_shape.argtypes = [C.c_int, C.c_int]
     L.hm_set_test_hook.argtypes = [C.c_int, C.c_int64]
     L.hm_set_batch_limits.argtypes = [C.c_int64, C.c_int64]
+    L.hm_tune_aca_shapes.argtypes = [_vp, i64, C.c_int, C.c_int, _vp, C.c_int, C.c_double,
+                                     C.c_double, C.POINTER(Options), C.c_int, _vp]
     L.hm_check_status.argtypes = [_vp]
     L.hm_device_bytes.restype = C.c_uint64
     L.hm_device_bytes.argtypes = []
@@ -401,6 +403,23 @@ def set_aca_shape(cls: int, shape: int) -> None:
     (-1 every class); shape -1 default, 0 the cluster kernels, 1 the default team
     shape, 2 another team shape."""
     _check(lib().hm_set_aca_shape(int(cls), int(shape)))
+
+
+def tune_aca_shapes(points, kernel: int, ell: float, leaf: int, eta: float, aca_eps: float,
+                    sigma2: float = 0.0, reps: int = 2, **opts) -> list:
+    """hm_tune_aca_shapes: time the ACA shapes 0, 1, 2 per size class on this
+    problem (stored build, classes serial) and keep the fastest for later
+    builds; returns the 12 chosen shapes (-1: empty class)."""
+    import numpy as _np
+    o = options(**opts)
+    n, d = int(points.shape[0]), int(points.shape[1])
+    if isinstance(points, _np.ndarray):
+        points = _np.ascontiguousarray(points, dtype=_np.float64)
+    prm = _np.array([ell, sigma2], _np.float64)
+    out = (C.c_int * 12)()
+    _check(lib().hm_tune_aca_shapes(_ptr(points), n, d, int(kernel), _ptr(prm), int(leaf),
+                                    float(eta), float(aca_eps), C.byref(o), int(reps), out))
+    return list(out)
 
 
 def set_batch_limits(aca_entries: int = 0, gather_items: int = 0) -> None:

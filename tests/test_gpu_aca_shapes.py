@@ -127,3 +127,25 @@ def test_aca_step_limit_gives_timeout(hm, shape):
     assert np.isfinite(y).all()
     with pytest.raises(hm.HMError):
         hm.set_test_hook(99, 1)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_shape_tuner_picks_a_shape_per_class(hm, orc, prec):
+    n = 1 << 15
+    pts = inputs.mixture_points(n, 2, 33)
+    x = inputs.normal_vector(n, inputs.X_SEED)
+    p = hm.PREC_FP64 if prec == "fp64" else hm.PREC_MIXED
+    try:
+        shapes = hm.tune_aca_shapes(pts, 0, 0.1, 64, 1.0, 1e-6, reps=1, precision=p)
+        assert len(shapes) == 12 and set(shapes) <= {-1, 0, 1, 2}
+        # the classes that hold blocks at N = 2^15 (rows up to 2^13) got a shape
+        assert all(s >= 0 for s in shapes[:6]), shapes
+        H = hm.HMatrix(pts, 0, 0.1, 64, 1.0, 1e-6, precision=p)
+        y = H.matvec(x)
+        H.free()
+    finally:
+        hm.set_aca_shape(-1, -1)
+    yo = orc.HMatrix(pts, 0, 0.1, 64, 1.0, 1e-6).matvec(x)
+    assert rel(y, yo) <= (FP64_TOL if prec == "fp64" else MIXED_TOL)
+    with pytest.raises(hm.HMError):
+        hm.tune_aca_shapes(pts, 0, 0.1, 64, 1.0, 1e-6, on_the_fly=True)
