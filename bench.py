@@ -77,9 +77,10 @@ def parse():
                         "(all 64 in stored mode need more than one GPU's memory)")
     p.add_argument("--gather-shape", type=int, default=-1,
                    help="launch shape of the product's gather (hm_set_gather_shape); -1 = tuned")
-    p.add_argument("--symmetric", default="on", choices=["on", "off"],
+    p.add_argument("--symmetric", default="near", choices=["near", "on", "off"],
                    help="mixed-precision builds compress only the leaves with tau <= sigma "
-                        "and mirror the rest (the kernels are symmetric)")
+                        "and mirror the rest (the kernels are symmetric); near: also store "
+                        "each off-diagonal dense leaf once and apply it both ways")
     p.add_argument("--rank-model", default="on", choices=["on", "off"],
                    help="size the ACA factor arena with the learned rank model "
                         "(trained before the timed region on other point sets)")
@@ -845,13 +846,13 @@ def main():
     # mixed-precision builds use the kernels' symmetry (compress the leaves
     # with tau.lo <= sigma.lo, mirror the rest); the FP64 path stays the
     # paper's plain method
-    use_sym = args.symmetric == "on"
+    use_sym = {"near": 2, "on": 1, "off": 0}[args.symmetric]
 
     def step(prec, ev=None, profile=False, model=True, sym=None):
         if ev:
             ev[0].record(stream)
         mk = dict(kw)
-        mk["symmetric"] = (use_sym if sym is None else sym) and prec == hm.PREC_MIXED
+        mk["symmetric"] = (use_sym if sym is None else int(sym)) if prec == hm.PREC_MIXED else 0
         if model and theta is not None:
             mk["rank_model_theta"] = theta
         H = hm.HMatrix(pts, w["kernel"], w["ell"], w["leaf"], w["eta"], w["eps"],
@@ -982,8 +983,10 @@ def main():
         mk = dict(kw)
         if theta is not None:
             mk["rank_model_theta"] = theta
+        # (the symmetric near field runs several vectors one at a time, so
+        # this leg keeps the mirrored factors only)
         Hm = hm.HMatrix(pts, w["kernel"], w["ell"], w["leaf"], w["eta"], w["eps"],
-                        precision=hm.PREC_MIXED, symmetric=use_sym, **mk)
+                        precision=hm.PREC_MIXED, symmetric=min(use_sym, 1), **mk)
         nr = 16
         Xr = torch.from_numpy(inputs.normal_vector(N, inputs.X_SEED + 1, nrhs=nr)).cuda()
         Yr = torch.empty_like(Xr)

@@ -95,8 +95,20 @@ typedef struct hm_options {
                              sigma.lo; each mirror leaf (sigma, tau) takes the
                              same factors with U and V exchanged, so the
                              H-matrix is symmetric and ACA does half the work.
+                             2: as 1, and store the dense leaves with tau.lo <=
+                             sigma.lo only: the product applies each
+                             off-diagonal one to both its rows (A x|sigma) and
+                             its mirror's rows (A^T x|tau, through a buffer of
+                             one value per stored column added in a fixed
+                             order), so the near field's bytes about halve.
+                             Mixed precision with the paired-bfloat16 or FP32
+                             near field, leaf_size <= 64 and stored mode only;
+                             elsewhere 2 acts as 1. Its products with several
+                             right-hand sides run one vector at a time, and
+                             every gather shape runs the bulk-copy kernel.
                              Not in the paper (its library treats the general
-                             Y1 x Y2 case, Sec. 6.1). Default 0. */
+                             Y1 x Y2 case, Sec. 6.1). Default 0; other values
+                             HM_EINVAL. */
     int on_the_fly;       /* 1: store no factors and no near field: every
                              hm_matvec recomputes the ACA factors of the
                              admissible leaves in passes of consecutive leaves

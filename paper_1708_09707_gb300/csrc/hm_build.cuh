@@ -241,6 +241,17 @@ struct MvpPlan {
     const LrDesc* lr_desc = nullptr;
     const int64_t* dn_ptr = nullptr;
     const DnDesc* dn_desc = nullptr;
+    // symmetric near field: only the dense leaves with tau.lo <= sigma.lo
+    // are stored; the gather also forms, for every near column of an
+    // off-diagonal leaf, the transposed product (A^T x|tau)_c and writes it
+    // at the column's index of the near stream into zbuf (n_ncols floats);
+    // the finish adds, for tile q, records [zptr[q], zptr[q + 1]): rows
+    // 0 .. zlen[r] - 1 of the tile take zbuf[zbase[r] + row]
+    int sym_near = 0;
+    float* zbuf = nullptr;
+    const int64_t* zptr = nullptr;
+    const int64_t* zbase = nullptr;
+    const int32_t* zlen = nullptr;
     // permutation and diagonal shift
     const int64_t* perm = nullptr;      // Morton row -> caller index (absolute)
     double sigma2 = 0.0;
@@ -271,6 +282,7 @@ struct MvpWork {
     // several right-hand sides (float plans), sized for MVP_NRC_MAX on first use
     DevBuf<float> xmn, tn, tpn;
     DevBuf<double> partn;
+    DevBuf<float> zbuf;                   // transposed near-field products (symmetric near field)
 };
 
 void mvp_alloc_work(const MvpPlan& P, MvpWork& W, cudaStream_t s);
@@ -352,10 +364,17 @@ struct MvpLists {
     int64_t n_items = 0;
     int64_t n_tiles = 0, n_vitems = 0, tpart_len = 0, t_len = 0, n_multi = 0;
     int64_t n_lr = 0, n_dn = 0, u_elems = 0, near_elems = 0;
+    // symmetric near field (sym_near): transposed-product records per tile
+    int sym_near = 0;
+    DevBuf<int64_t> zptr, zbase;
+    DevBuf<int32_t> zlen;
+    int64_t n_zrec = 0, n_zcols = 0;
 };
+// dblk: the dense leaves to store; with sym_near they are the canonical ones
+// (row0 <= col0) and the lists also get the transposed-product records.
 void mvp_build_lists(const Blk* ablk, const int32_t* rank, int64_t n_adm, const Blk* dblk,
                      int64_t n_dense, const int64_t* leaf_row0, const int32_t* leaf_m,
-                     int64_t n_tiles, MvpLists& L, cudaStream_t s);
+                     int64_t n_tiles, MvpLists& L, cudaStream_t s, int sym_near = 0);
 // Copy every block's U rows of every tile it covers into the tile-major store.
 void mvp_relayout_u(int precision, const MvpLists& L, const Blk* ablk, const uint64_t* Uptr,
                     const int32_t* tile_m, void* ustore, cudaStream_t s);

@@ -16,6 +16,7 @@ struct FactorSegment {
 }  // namespace hm
 
 struct hm_handle_s {
+    int sym_near = 0;                 // symmetric near field (hm_options.symmetric = 2)
     hm_options opt{};
     int kernel = 0, leaf = 0, precision = 0, near_format = 0;
     double ell = 1.0, sigma2 = 0.0, eta = 0.0, aca_eps = 0.0;

@@ -334,8 +334,31 @@ __host__ __device__ constexpr int col_bytes64()   // bytes of one 64-row column
            : (sizeof(R) == 8 ? 512 : 256);
 }
 
-template <class R, int FMT, int TCOL, int TS>
-__global__ void __launch_bounds__(T3_NT, 2)
+// Reduce-scatter of four per-lane values over a half-warp: every lane
+// returns the half-warp total of value (hl >> 2) & 3 (hl the lane's index in
+// its half-warp). Both half-warps run it together.
+template <class R>
+__device__ __forceinline__ R halfwarp_sum4(const R (&v)[4], int hl)
+{
+    const bool b3 = (hl & 8) != 0, b2 = (hl & 4) != 0;
+    R a0 = b3 ? v[2] : v[0], a1 = b3 ? v[3] : v[1];
+    const R s0 = b3 ? v[0] : v[2], s1 = b3 ? v[1] : v[3];
+    a0 += __shfl_xor_sync(0xffffffffu, s0, 8);
+    a1 += __shfl_xor_sync(0xffffffffu, s1, 8);
+    R c = b2 ? a1 : a0;
+    const R e = b2 ? a0 : a1;
+    c += __shfl_xor_sync(0xffffffffu, e, 4);
+    c += __shfl_xor_sync(0xffffffffu, c, 2);
+    c += __shfl_xor_sync(0xffffffffu, c, 1);
+    return c;
+}
+
+// ZT (symmetric near field): a near column c of the tile's stream also
+// gives (A^T x|tile)_c = sum over the tile's rows of A(row, c) x(row), the
+// row-c entry of the mirror leaf's product, written to P.zbuf at the
+// column's index in the near stream.
+template <class R, int FMT, int TCOL, int TS, bool ZT = false>
+__global__ void __launch_bounds__(T3_NT, ZT ? 3 : 2)
 k_tile_tma(MvpPlan P, const R* __restrict__ xm, const R* __restrict__ t, double* __restrict__ part)
 {
     extern __shared__ __align__(128) unsigned char tsm[];
@@ -430,6 +453,13 @@ k_tile_tma(MvpPlan P, const R* __restrict__ xm, const R* __restrict__ t, double*
         Acc<R> acc[4];
         R sg[4] = {R(0), R(0), R(0), R(0)};
         int ing = 0;   // columns of the current group of four
+        R xr[4] = {R(0), R(0), R(0), R(0)};   // x of this lane's rows (ZT)
+        if constexpr (ZT) {
+            static_assert(TCOL / 16 == 4, "four columns per half-warp and chunk");
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (ir + i < mt) xr[i] = xm[P.tile_row0[tile] + ir + i];
+        }
         R mv = fetch(0);
         for (int k = 0; k < nch; ++k) {
             const int slot = k % TS;
@@ -446,6 +476,7 @@ k_tile_tma(MvpPlan P, const R* __restrict__ xm, const R* __restrict__ t, double*
             int cnt;
             chunk(k, isu, c0, cnt);
             const unsigned char* st = tsm + slot * STAGE;
+            R za[4] = {R(0), R(0), R(0), R(0)};
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int col = hw + 16 * e;
@@ -485,6 +516,12 @@ k_tile_tma(MvpPlan P, const R* __restrict__ xm, const R* __restrict__ t, double*
                 const R m = __shfl_sync(hmask, mv, e, 16);
 #pragma unroll
                 for (int i = 0; i < 4; ++i) sg[i] = fma(a[i], m, sg[i]);
+                if constexpr (ZT) {
+                    if (e < 4 && !isu) {
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) za[e] = fma(a[i], xr[i], za[e]);
+                    }
+                }
                 // groups of four columns of this half-warp's sequence, as in
                 // k_tile; a stream part starts a new group
                 const bool last = (k == nuch - 1 || k == nch - 1) && e == E - 1;
@@ -495,6 +532,14 @@ k_tile_tma(MvpPlan P, const R* __restrict__ xm, const R* __restrict__ t, double*
                         sg[i] = R(0);
                     }
                     ing = 0;
+                }
+            }
+            if constexpr (ZT) {
+                if (!isu) {
+                    // one transposed product per column of the chunk
+                    const R z = halfwarp_sum4(za, hl);
+                    const int col = hw + 16 * ((hl >> 2) & 3);
+                    if ((hl & 3) == 0 && col < cnt) P.zbuf[nc0 + c0 + col] = (float)z;
                 }
             }
             __syncwarp();
@@ -533,6 +578,40 @@ __global__ void k_tile_finish(MvpPlan P, const double* __restrict__ part, const 
         const double v = sum + sg * x[dst];
         y[dst] = accumulate ? y[dst] + v : v;
     }
+}
+
+// The finish of a symmetric near field (tiles of at most 64 rows): one CTA
+// per tile, four groups of 64 threads (thread = row). Group g sums the
+// mirror leaves' transposed products of records g, g + 4, ... in record
+// order; row i then takes its item sums in item order and the four group
+// sums in group order, plus sigma^2 x.
+__global__ void __launch_bounds__(256)
+k_tile_finish_sym(MvpPlan P, const double* __restrict__ part, const double* __restrict__ x,
+                  double* __restrict__ y, int accumulate)
+{
+    __shared__ double zs[4][64];
+    const int64_t tile = blockIdx.x;
+    const int i = threadIdx.x & 63, g = threadIdx.x >> 6;
+    const int mt = P.tile_m[tile];
+    const int64_t z0 = P.zptr[tile], z1 = P.zptr[tile + 1];
+    double s = 0.0;
+    for (int64_t r = z0 + g; r < z1; r += 4)
+        if (i < P.zlen[r]) s += (double)P.zbuf[P.zbase[r] + i];
+    zs[g][i] = s;
+    __syncthreads();
+    if (g != 0 || i >= mt) return;
+    const int64_t i0 = P.item_ptr[tile], i1 = P.item_ptr[tile + 1];
+    double sum = 0.0;
+    for (int64_t q = i0; q < i1; ++q) sum += part[q * P.max_ld + i];
+    sum += zs[0][i];
+    sum += zs[1][i];
+    sum += zs[2][i];
+    sum += zs[3][i];
+    const int64_t row = P.tile_row0[tile] + i;
+    const int64_t dst = P.perm[row];
+    const double sg = P.sig_row ? P.sig_row[row] : P.sigma2;
+    const double v = sum + sg * x[dst];
+    y[dst] = accumulate ? y[dst] + v : v;
 }
 
 // ------------------------------------------------------------------ lists
@@ -807,6 +886,52 @@ __global__ void k_fill_ncol(const int2* __restrict__ ent, int64_t ne, const Blk*
     for (int c = 0; c < B.n; ++c) ncol_x[ecol[e] + c] = (int32_t)(B.col0 + c);
 }
 
+// Symmetric near field: the near entries of off-diagonal leaves (row0 !=
+// col0; the list holds only leaves with row0 <= col0) give transposed
+// products over their columns, which are rows of the mirror leaf. zblk[j]
+// describes entry j's transposed range as a block whose rows are the
+// entry's columns, so that build_csr cuts it into tiles; zcol[j] is the
+// near-stream index of the entry's first column.
+__global__ void k_z_flag(const int2* __restrict__ ent, int64_t ne, const Blk* __restrict__ dblk,
+                         int64_t* __restrict__ f)
+{
+    const int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (e >= ne) return;
+    const Blk B = dblk[ent[e].x];
+    f[e] = B.row0 != B.col0 ? 1 : 0;
+}
+
+__global__ void k_z_blocks(const int2* __restrict__ ent, int64_t ne, const Blk* __restrict__ dblk,
+                           const int64_t* __restrict__ f, const int64_t* __restrict__ off,
+                           const int64_t* __restrict__ ecol, Blk* __restrict__ zblk,
+                           int64_t* __restrict__ zcol)
+{
+    const int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (e >= ne || !f[e]) return;
+    const Blk B = dblk[ent[e].x];
+    Blk Z;
+    Z.row0 = B.col0;
+    Z.col0 = B.row0;
+    Z.m = B.n;
+    Z.n = 0;
+    zblk[off[e]] = Z;
+    zcol[off[e]] = ecol[e];
+}
+
+// Per record r (transposed range j met by tile q at row offset o of the
+// range): the zbuf entry of the tile's first row and the rows it covers.
+__global__ void k_z_records(const int2* __restrict__ zent, const int32_t* __restrict__ zt,
+                            int64_t nr, const Blk* __restrict__ zblk,
+                            const int64_t* __restrict__ zcol, const int32_t* __restrict__ tile_m,
+                            int64_t* __restrict__ zbase, int32_t* __restrict__ zlen)
+{
+    const int64_t r = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (r >= nr) return;
+    const int j = zent[r].x, o = zent[r].y;
+    zbase[r] = zcol[j] + o;
+    zlen[r] = min(tile_m[zt[r]], zblk[j].m - o);
+}
+
 // Gather work items: a tile's U-then-near column stream in pieces of at most
 // ITEM_COLS columns, so that the few tiles with very many near-field columns
 // (clusters of coincident points are mutually inadmissible) do not leave one
@@ -838,9 +963,10 @@ __global__ void k_item_emit(const int64_t* __restrict__ ucol_ptr, const int64_t*
 
 void mvp_build_lists(const Blk* ablk, const int32_t* rank, int64_t n_adm, const Blk* dblk,
                      int64_t n_dense, const int64_t* leaf_row0, const int32_t* leaf_m,
-                     int64_t n_tiles, MvpLists& L, cudaStream_t s)
+                     int64_t n_tiles, MvpLists& L, cudaStream_t s, int sym_near)
 {
     L.n_tiles = n_tiles;
+    L.sym_near = sym_near;
     build_csr(ablk, n_adm, leaf_row0, n_tiles, L.lr_ptr, L.lr_ent, s);
     build_csr(dblk, n_dense, leaf_row0, n_tiles, L.dn_ptr, L.dn_ent, s);
     {
@@ -880,12 +1006,45 @@ void mvp_build_lists(const Blk* ablk, const int32_t* rank, int64_t n_adm, const 
                                                              L.ncol_ptr.p, L.nbase.p); note_launch();
         k_fill_ncol<<<grid_for(L.n_dn), NT, 0, s>>>(L.dn_ent.p, L.n_dn, dblk, ecol.p, L.ncol_x.p); note_launch();
         HM_CUDA(cudaStreamSynchronize(s));
+        if (sym_near) {
+            // transposed-product records of the off-diagonal near entries
+            DevBuf<int64_t> f(L.n_dn, s), zo(L.n_dn + 1, s);
+            k_z_flag<<<grid_for(L.n_dn), NT, 0, s>>>(L.dn_ent.p, L.n_dn, dblk, f.p); note_launch();
+            scan_exclusive_i64(f.p, zo.p, L.n_dn, zo.p + L.n_dn, s);
+            int64_t nz = 0;
+            HM_CUDA(cudaMemcpyAsync(&nz, zo.p + L.n_dn, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            HM_CUDA(cudaStreamSynchronize(s));
+            DevBuf<Blk> zblk(std::max<int64_t>(nz, 1), s);
+            DevBuf<int64_t> zcol(std::max<int64_t>(nz, 1), s);
+            k_z_blocks<<<grid_for(L.n_dn), NT, 0, s>>>(L.dn_ent.p, L.n_dn, dblk, f.p, zo.p, ecol.p,
+                                                       zblk.p, zcol.p); note_launch();
+            DevBuf<int2> zent;
+            build_csr(zblk.p, nz, leaf_row0, n_tiles, L.zptr, zent, s);
+            HM_CUDA(cudaMemcpyAsync(&L.n_zrec, L.zptr.p + n_tiles, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            HM_CUDA(cudaStreamSynchronize(s));
+            DevBuf<int32_t> zt(std::max<int64_t>(L.n_zrec, 1), s);
+            L.zbase.alloc(std::max<int64_t>(L.n_zrec, 1), s);
+            L.zlen.alloc(std::max<int64_t>(L.n_zrec, 1), s);
+            if (L.n_zrec > 0) {
+                k_entry_tiles<<<(unsigned)n_tiles, 64, 0, s>>>(L.zptr.p, n_tiles, zt.p); note_launch();
+                k_z_records<<<grid_for(L.n_zrec), NT, 0, s>>>(zent.p, zt.p, L.n_zrec, zblk.p, zcol.p,
+                                                              leaf_m, L.zbase.p, L.zlen.p); note_launch();
+            }
+            L.n_zcols = L.n_ncols;
+            HM_CUDA(cudaStreamSynchronize(s));
+        }
     } else {
         L.ncol_ptr.alloc(n_tiles + 1, s);
         L.nbase.alloc(std::max<int64_t>(n_tiles, 1), s);
         L.ncol_x.alloc(1, s);
         HM_CUDA(cudaMemsetAsync(L.ncol_ptr.p, 0, (n_tiles + 1) * sizeof(int64_t), s));
         HM_CUDA(cudaMemsetAsync(L.nbase.p, 0, std::max<int64_t>(n_tiles, 1) * sizeof(int64_t), s));
+    }
+    if (sym_near && !L.zptr.p) {
+        L.zptr.alloc(std::max<int64_t>(n_tiles, 0) + 1, s);
+        HM_CUDA(cudaMemsetAsync(L.zptr.p, 0, (std::max<int64_t>(n_tiles, 0) + 1) * sizeof(int64_t), s));
+        L.zbase.alloc(1, s);
+        L.zlen.alloc(1, s);
     }
     // t offsets and V^T x work items
     const int64_t nb = std::max<int64_t>(n_adm, 1);
@@ -987,6 +1146,7 @@ void mvp_relayout_u(int precision, const MvpLists& L, const Blk* ablk, const uin
 void mvp_alloc_work(const MvpPlan& P, MvpWork& W, cudaStream_t s)
 {
     W.part.alloc(std::max<int64_t>(P.n_items, 1) * std::max(P.max_ld, 1), s);
+    if (P.sym_near) W.zbuf.alloc(std::max<int64_t>(P.n_ncols, 1), s);
     if (P.precision == HM_PREC_FP64) {
         W.xm64.alloc(std::max<int64_t>(P.Ntot, 1), s);
         W.t64.alloc(std::max<int64_t>(P.t_len, 1), s);
@@ -1020,6 +1180,22 @@ template <class R, int FMT>
 void launch_tile(int v, const MvpPlan& P, const R* xm, const R* t, double* part, cudaStream_t s)
 {
     const unsigned g = (unsigned)P.n_items;
+    if (P.sym_near) {
+        // the symmetric near field runs on the bulk-copy kernels only
+        // (shape 3: six stages, every other shape: four)
+        if constexpr (sizeof(R) == 4 && FMT != HM_NEAR_BF16) {
+            if (P.max_ld > TROWS) fail(HM_ENOTSUP, "symmetric near field: slices above 64 rows");
+            const int nst = v == 3 ? 6 : 4;
+            const int bytes = nst * 64 * col_bytes64<R, FMT>();
+            auto kern = nst == 6 ? k_tile_tma<R, FMT, 64, 6, true> : k_tile_tma<R, FMT, 64, 4, true>;
+            HM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+            kern<<<g, T3_NT, bytes, s>>>(P, xm, t, part);
+            note_launch();
+            return;
+        } else {
+            fail(HM_ENOTSUP, "symmetric near field: mixed precision and a paired or FP32 near field");
+        }
+    }
     if (v >= tile_variants<R, FMT>(P)) v = 0;
     switch (v) {
     case 0: k_tile<R, FMT, 8, 3><<<g, TILE_NT, 0, s>>>(P, xm, t, part); break;
@@ -1044,11 +1220,11 @@ void launch_tile(int v, const MvpPlan& P, const R* xm, const R* t, double* part,
 }
 
 struct TileKey {
-    int dev, precision, fmt, ld, lg_tiles;
+    int dev, precision, fmt, ld, lg_tiles, sym;
     bool operator<(const TileKey& o) const
     {
-        return std::tie(dev, precision, fmt, ld, lg_tiles) <
-               std::tie(o.dev, o.precision, o.fmt, o.ld, o.lg_tiles);
+        return std::tie(dev, precision, fmt, ld, lg_tiles, sym) <
+               std::tie(o.dev, o.precision, o.fmt, o.ld, o.lg_tiles, o.sym);
     }
 };
 std::mutex g_tune_mu;
@@ -1060,7 +1236,7 @@ TileKey tile_key(const MvpPlan& P)
     HM_CUDA(cudaGetDevice(&dev));
     int lg = 0;
     while ((1ll << lg) < P.n_tiles) ++lg;
-    return TileKey{dev, P.precision, P.near_format, P.max_ld, lg};
+    return TileKey{dev, P.precision, P.near_format, P.max_ld, lg, P.sym_near};
 }
 
 std::atomic<int> g_forced_shape{-1};
@@ -1137,7 +1313,11 @@ void run_typed(const MvpPlan& P, R* xm, R* t, R* tp, double* part, const double*
         } else {
             launch_tile<R, FMT>(v, P, xm, t, part, s);
         }
-        k_tile_finish<<<grid_for(P.n_tiles * 32), NT, 0, s>>>(P, part, x, y, accumulate); note_launch();
+        if (P.sym_near)
+            k_tile_finish_sym<<<(unsigned)P.n_tiles, 256, 0, s>>>(P, part, x, y, accumulate);
+        else
+            k_tile_finish<<<grid_for(P.n_tiles * 32), NT, 0, s>>>(P, part, x, y, accumulate);
+        note_launch();
     }
     if (rec) HM_CUDA(cudaEventRecord(rec->e[3], s));
     HM_LAUNCH("matvec");
@@ -1210,6 +1390,7 @@ void mvp_run(const MvpPlan& P0, MvpWork& W, const double* x, double* y, int accu
     MvpPlan P = P0;
     P.wait_ns = mvp_wait_ns();
     P.withhold = mvp_withhold();
+    P.zbuf = W.zbuf.p;
     if (P.precision == HM_PREC_FP64) {
         run_typed<double, HM_NEAR_FP64>(P, W.xm64.p, W.t64.p, W.tp64.p, W.part.p, x, y, accumulate, s, timer);
         return;

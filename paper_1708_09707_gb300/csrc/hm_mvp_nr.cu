@@ -688,7 +688,7 @@ void run_group_fmt(const MvpPlan& P, MvpWork& W, const double* x, double* y, int
 
 bool mvp_multi_fused(const MvpPlan& P)
 {
-    return P.precision != HM_PREC_FP64 && P.max_ld <= TN_ROWS &&
+    return P.precision != HM_PREC_FP64 && P.max_ld <= TN_ROWS && !P.sym_near &&
            (P.near_format == HM_NEAR_FP64 || P.near_format == HM_NEAR_FP32 ||
             P.near_format == HM_NEAR_BF16X2);
 }

@@ -173,6 +173,13 @@ __global__ void k_canon_ids(const int64_t* __restrict__ f, const int64_t* __rest
     if (b < n && f[b]) ids[off[b]] = (uint32_t)b;
 }
 
+__global__ void k_canon_blocks(const Blk* __restrict__ blk, const int64_t* __restrict__ f,
+                               const int64_t* __restrict__ off, int64_t n, Blk* __restrict__ out)
+{
+    int64_t b = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (b < n && f[b]) out[off[b]] = blk[b];
+}
+
 // A mirror leaf (sigma, tau) takes the factors of (tau, sigma) with U and V
 // exchanged. The leaves are in (row0, col0) order, so its partner is found by
 // binary search; a missing partner (not possible for a symmetric block tree)
@@ -1055,6 +1062,7 @@ void validate(int nsets, const int64_t* N, const int* d, int kernel, const doubl
     if (o.precision == HM_PREC_FP64 && o.near_format != HM_NEAR_AUTO &&
         o.near_format != HM_NEAR_FP64)
         fail(HM_ENOTSUP, "the FP64 path stores the near field in FP64");
+    if (o.symmetric < 0 || o.symmetric > 2) fail(HM_EINVAL, "symmetric must be 0, 1 or 2");
     int64_t tot = 0;
     for (int q = 0; q < nsets; ++q) {
         if (N[q] < 1) fail(HM_EINVAL, "N must be >= 1");
@@ -1101,6 +1109,12 @@ void build_sets(hm_handle_s& h, int nsets, const double* points_all, const int64
     h.near_format = opt.near_format == HM_NEAR_AUTO
                         ? (opt.precision == HM_PREC_FP64 ? HM_NEAR_FP64 : HM_NEAR_BF16X2)
                         : opt.near_format;
+    // symmetric = 2: also store each off-diagonal dense leaf once (mixed
+    // precision, a paired or FP32 near field, slices of at most 64 rows,
+    // stored mode); otherwise it acts as symmetric = 1
+    h.sym_near = opt.symmetric == 2 && opt.precision == HM_PREC_MIXED && !opt.on_the_fly &&
+                 !rect && slice_ld(leaf) <= 64 && h.near_format != HM_NEAR_BF16 &&
+                 h.near_format != HM_NEAR_FP64 ? 1 : 0;
     h.stream = (cudaStream_t)opt.stream;
     h.kp = make_kernel_params(kernel, h.ell);
     h.kp.dmax = 1;
@@ -1351,11 +1365,28 @@ void build_sets(hm_handle_s& h, int nsets, const double* points_all, const int64
     // product lists, near field in tile slices, U in tile slices
     {
         Timer td(s);
-        mvp_build_lists(h.ablk.p, h.rank.p, h.n_adm, h.dblk.p, h.n_dense, h.tile_row0.p,
-                        h.tile_m.p, h.n_tiles, h.lists, s);
+        // symmetric near field: store the dense leaves with tau.lo <= sigma.lo
+        // only; the product applies each off-diagonal one both ways
+        const Blk* dl = h.dblk.p;
+        int64_t nd = h.n_dense;
+        DevBuf<Blk> dcan;
+        if (h.sym_near && h.n_dense > 0) {
+            DevBuf<int64_t> f(h.n_dense, s), off(h.n_dense + 1, s);
+            k_canon_flag<<<grid_for(h.n_dense), NT, 0, s>>>(h.dblk.p, h.n_dense, f.p); note_launch();
+            scan_exclusive_i64(f.p, off.p, h.n_dense, off.p + h.n_dense, s);
+            HM_CUDA(cudaMemcpyAsync(&nd, off.p + h.n_dense, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            HM_CUDA(cudaStreamSynchronize(s));
+            dcan.alloc(std::max<int64_t>(nd, 1), s);
+            k_canon_blocks<<<grid_for(h.n_dense), NT, 0, s>>>(h.dblk.p, f.p, off.p, h.n_dense,
+                                                              dcan.p); note_launch();
+            HM_LAUNCH("canonical dense leaves");
+            dl = dcan.p;
+        }
+        mvp_build_lists(h.ablk.p, h.rank.p, h.n_adm, dl, nd, h.tile_row0.p,
+                        h.tile_m.p, h.n_tiles, h.lists, s, h.sym_near);
         const MvpLists& L = h.lists;
         h.near.alloc((size_t)std::max<int64_t>(L.near_elems, 1) * near_entry_bytes(h.near_format), s);
-        near_assemble(h.near_format, h.kp, h.X, h.dblk.p, L.dn_ent.p,
+        near_assemble(h.near_format, h.kp, h.X, dl, L.dn_ent.p,
                       L.dn_tile.p, h.tile_m.p, L.dn_desc.p, L.n_dn, h.near.p, s);
         const int esz = h.precision == HM_PREC_FP64 ? 8 : 4;
         h.ustore.alloc((size_t)std::max<int64_t>(L.u_elems, 1) * esz, s);
@@ -1412,6 +1443,10 @@ void build_sets(hm_handle_s& h, int nsets, const double* points_all, const int64
     P.dn_desc = h.lists.dn_desc.p;
     P.perm = h.perm.p;
     P.sigma2 = h.sigma2;
+    P.sym_near = h.sym_near;
+    P.zptr = h.lists.zptr.p;
+    P.zbase = h.lists.zbase.p;
+    P.zlen = h.lists.zlen.p;
     mvp_alloc_work(P, h.work, s);
     HM_CUDA(cudaStreamSynchronize(s));
 
@@ -1432,7 +1467,10 @@ void build_sets(hm_handle_s& h, int nsets, const double* points_all, const int64
     // algorithmic bytes of one product: factors + near field + x (read once
     // through the permutation) + perm + y written + the gather's column
     // multiplier indices (4 bytes per column)
-    const int64_t idx_bytes = (h.lists.n_ucols + h.lists.n_ncols) * 4;
+    // (symmetric near field: the transposed products are written and read
+    // once, 4 + 4 bytes per near column)
+    const int64_t idx_bytes = (h.lists.n_ucols + h.lists.n_ncols) * 4 +
+                              (h.sym_near ? 8 * h.lists.n_ncols : 0);
     st.mvp_bytes = st.factor_bytes + st.near_bytes + Ntot * (8 + 8 + 8) + idx_bytes;
     // per kernel: V^T x reads V and writes t; the gather reads U, the near
     // field, its column indices, perm and x (for sigma^2 x) and writes y
