@@ -525,7 +525,8 @@ def run_batch(args):
     x = torch.from_numpy(x_h).cuda()
     y = torch.empty_like(x)
     stream = torch.cuda.current_stream()
-    opts = dict(precision=hm.PREC_MIXED, symmetric=args.symmetric == "on")
+    opts = dict(precision=hm.PREC_MIXED,
+                symmetric={"near": 2, "on": 1, "off": 0}[args.symmetric])
 
     def step(ev=None, profile=False, host=False):
         if ev:
@@ -600,7 +601,7 @@ def run_batch(args):
                        "points": int(sizes.sum()),
                        "sizes": "log-uniform in [1e4, 2^18]", "d": "2 or 3", "kernel": "gaussian",
                        "ell": w["ell"], "leaf": w["leaf"], "eta": w["eta"], "aca_eps": w["eps"],
-                       "precision": "mixed", "symmetric": args.symmetric == "on",
+                       "precision": "mixed", "symmetric": args.symmetric,
                        "mvp_per_step": N_MVP, "parallelism": "sets sharded" if world > 1 else "single"},
             "build_s": build_ms / 1e3, "mvp_ms": mvp_ms,
             "e2e": {"value": e2e_ms / 1e3, "unit": unit,
@@ -1043,7 +1044,7 @@ def main():
             ev[0].record(stream)
             Ho = hm.HMatrix(po, wo["kernel"], wo["ell"], wo["leaf"], wo["eta"], wo["eps"],
                             precision=hm.PREC_MIXED, on_the_fly=True, profile=True,
-                            symmetric=(args.symmetric == "on"), adm_max=(wo["adm"] == "max"))
+                            symmetric=min(use_sym, 1), adm_max=(wo["adm"] == "max"))
             ev[1].record(stream)
             torch.cuda.nvtx.range_push("on_the_fly_" + wname)
             for _ in range(reps):
@@ -1053,7 +1054,7 @@ def main():
             torch.cuda.synchronize()
             so = Ho.stats()
             otf.append({"workload": wname, "n": wo["n"], "precision": "mixed",
-                        "symmetric": args.symmetric == "on",
+                        "symmetric": use_sym > 0,
                         "build_s": ev[0].elapsed_time(ev[1]) / 1e3,
                         "mvp_ms": ev[1].elapsed_time(ev[2]) / reps,
                         "aca_passes_per_product": so["aca_passes"], "n_adm": so["n_adm"],

@@ -92,7 +92,8 @@ def test_fullsize_sampled_rows(hm, orc):
 
 def test_timed_configuration_parity(hm, orc):
     # exactly the configuration bench.py times: the clipped mixture at
-    # N = 2^20, mixed precision, symmetric mode, the learned rank model
+    # N = 2^20, mixed precision, symmetric mode with the symmetric near field
+    # (symmetric = 2), the learned rank model
     # trained as the bench trains it; 256 sampled rows against the exact sums
     # (Neumaier-compensated FP64 brute force), and the whole product against
     # the FP64 GPU build, whose parity with the oracle the smaller cases pin
@@ -104,10 +105,17 @@ def test_timed_configuration_parity(hm, orc):
     F, T = rank_model.training_data()
     theta, _ = rank_model.train(F, T)
     H = hm.HMatrix(pts, w["kernel"], w["ell"], w["leaf"], w["eta"], w["eps"],
-                   precision=hm.PREC_MIXED, symmetric=True, rank_model_theta=theta)
+                   precision=hm.PREC_MIXED, symmetric=2, rank_model_theta=theta)
     y = H.matvec(x)
     st = H.stats()
     H.free()
+    # the symmetric near field really is on: the stored near field about halves
+    H1 = hm.HMatrix(pts, w["kernel"], w["ell"], w["leaf"], w["eta"], w["eps"],
+                    precision=hm.PREC_MIXED, symmetric=1, rank_model_theta=theta)
+    y1 = H1.matvec(x)
+    assert st["near_bytes"] <= 0.6 * H1.stats()["near_bytes"]
+    H1.free()
+    assert np.linalg.norm(y - y1) / np.linalg.norm(y1) <= 1e-6
     assert st["n_mispredicted"] < 0.01 * st["n_adm"]
     rows = np.sort(np.random.default_rng(1).choice(w["n"], 256, replace=False))
     yb = orc.dense_rows(pts, w["kernel"], w["ell"], 0.0, rows, x)
