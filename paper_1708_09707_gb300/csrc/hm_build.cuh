@@ -252,6 +252,25 @@ struct MvpPlan {
     const int64_t* zptr = nullptr;
     const int64_t* zbase = nullptr;
     const int32_t* zlen = nullptr;
+    // symmetric low-rank part (with the symmetric near field): a tile's U
+    // stream holds its canonical slices (tau.lo < sigma.lo) before its
+    // mirror slices, which start at column umid[tile]. Pass A (uview 1)
+    // streams the canonical slices and the near field and writes, for every
+    // U column, (U^T x|tile)_c into zubuf (n_ucols floats); the mirror
+    // blocks' t = U_b^T x|tau is summed from it (k_tmirror); pass B (uview
+    // 2) streams the mirror slices, as items items_b / item_ptr_b whose
+    // partial sums follow pass A's n_items slots.
+    const int64_t* umid = nullptr;
+    int uview = 0;
+    float* zubuf = nullptr;
+    int64_t n_items_b = 0;
+    const int3* items_b = nullptr;
+    const int64_t* item_ptr_b = nullptr;
+    const int32_t* mirror_of = nullptr;   // per admissible block: its mirror (canonical blocks), else -1
+    const int64_t* lr_boff = nullptr;     // per block: first block-major low-rank entry
+    const int64_t* lr_pos = nullptr;      // block-major entry -> CSR position
+    const int64_t* lr_ecol = nullptr;     // block-major entry -> its first U column
+    int64_t n_lr = 0;
     // permutation and diagonal shift
     const int64_t* perm = nullptr;      // Morton row -> caller index (absolute)
     double sigma2 = 0.0;
@@ -283,6 +302,7 @@ struct MvpWork {
     DevBuf<float> xmn, tn, tpn;
     DevBuf<double> partn;
     DevBuf<float> zbuf;                   // transposed near-field products (symmetric near field)
+    DevBuf<float> zubuf;                  // transposed U-slice products (symmetric low-rank part)
 };
 
 void mvp_alloc_work(const MvpPlan& P, MvpWork& W, cudaStream_t s);
@@ -369,6 +389,12 @@ struct MvpLists {
     DevBuf<int64_t> zptr, zbase;
     DevBuf<int32_t> zlen;
     int64_t n_zrec = 0, n_zcols = 0;
+    // symmetric low-rank part (with sym_near): see MvpPlan
+    DevBuf<int64_t> umid, item_ptr_b, lr_boff, lr_pos, lr_ecol;
+    DevBuf<int3> items_b;
+    DevBuf<int32_t> mirror_of;
+    int64_t n_items_b = 0;
+    int64_t u_elems_canon = 0;   // elements of the canonical slices
 };
 // dblk: the dense leaves to store; with sym_near they are the canonical ones
 // (row0 <= col0) and the lists also get the transposed-product records.

@@ -26,6 +26,7 @@ struct hm_handle_s {
     int64_t Ntot = 0, n_nodes_tot = 0, n_adm = 0, n_dense = 0, n_tiles = 0;
     int64_t max_set_n = 0;
     int64_t factor_entries_U = 0;   // sum_b k_b m_b
+    int64_t factor_entries_Vc = 0;  // sum over canonical blocks (row0 < col0) of k_b n_b
     // A_{phi, Y1 x Y2}: set 0 gives the rows, set 1 the columns; the product
     // runs on staging vectors of Ntot entries (x in set 1's part, zeros in
     // set 0's; y in set 0's part)

@@ -356,7 +356,9 @@ __device__ __forceinline__ R halfwarp_sum4(const R (&v)[4], int hl)
 // ZT (symmetric near field): a near column c of the tile's stream also
 // gives (A^T x|tile)_c = sum over the tile's rows of A(row, c) x(row), the
 // row-c entry of the mirror leaf's product, written to P.zbuf at the
-// column's index in the near stream.
+// column's index in the near stream; with P.zubuf (pass A of the symmetric
+// low-rank part) every U column likewise gives (U_b^T x|tile)_l, written at
+// its index in the U stream.
 template <class R, int FMT, int TCOL, int TS, bool ZT = false>
 __global__ void __launch_bounds__(T3_NT, ZT ? 3 : 2)
 k_tile_tma(MvpPlan P, const R* __restrict__ xm, const R* __restrict__ t, double* __restrict__ part)
@@ -373,7 +375,19 @@ k_tile_tma(MvpPlan P, const R* __restrict__ xm, const R* __restrict__ t, double*
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int mt = P.tile_m[tile];
     const int ld = slice_ld(mt);
-    const int64_t uc0 = P.ucol_ptr[tile], nu = P.ucol_ptr[tile + 1] - uc0, ub = P.ubase[tile];
+    int64_t uc0 = P.ucol_ptr[tile], nu = P.ucol_ptr[tile + 1] - uc0, ub = P.ubase[tile];
+    if (P.umid) {
+        // symmetric low-rank part: pass A streams the canonical slices (and
+        // the near field), pass B the mirror slices
+        const int64_t um = P.umid[tile];
+        if (P.uview == 2) {
+            ub += (um - uc0) * ld;
+            nu -= um - uc0;
+            uc0 = um;
+        } else {
+            nu = um - uc0;
+        }
+    }
     const int64_t nc0 = P.ncol_ptr[tile], nb = P.nbase[tile];
     const int64_t ucb = it.y < nu ? it.y : nu, uce = it.z < nu ? it.z : nu;
     const int64_t ncb = it.y > nu ? it.y - nu : 0, nce = it.z > nu ? it.z - nu : 0;
@@ -517,7 +531,7 @@ k_tile_tma(MvpPlan P, const R* __restrict__ xm, const R* __restrict__ t, double*
 #pragma unroll
                 for (int i = 0; i < 4; ++i) sg[i] = fma(a[i], m, sg[i]);
                 if constexpr (ZT) {
-                    if (e < 4 && !isu) {
+                    if (e < 4 && (!isu || P.zubuf)) {
 #pragma unroll
                         for (int i = 0; i < 4; ++i) za[e] = fma(a[i], xr[i], za[e]);
                     }
@@ -535,11 +549,16 @@ k_tile_tma(MvpPlan P, const R* __restrict__ xm, const R* __restrict__ t, double*
                 }
             }
             if constexpr (ZT) {
-                if (!isu) {
-                    // one transposed product per column of the chunk
+                if (!isu || P.zubuf) {
+                    // one transposed product per column of the chunk (near
+                    // columns: the mirror leaf's rows; U columns of pass A:
+                    // the mirror block's t)
                     const R z = halfwarp_sum4(za, hl);
                     const int col = hw + 16 * ((hl >> 2) & 3);
-                    if ((hl & 3) == 0 && col < cnt) P.zbuf[nc0 + c0 + col] = (float)z;
+                    if ((hl & 3) == 0 && col < cnt) {
+                        if (isu) P.zubuf[uc0 + c0 + col] = (float)z;
+                        else P.zbuf[nc0 + c0 + col] = (float)z;
+                    }
                 }
             }
             __syncwarp();
@@ -580,6 +599,50 @@ __global__ void k_tile_finish(MvpPlan P, const double* __restrict__ part, const 
     }
 }
 
+// Symmetric low-rank part: t of every mirror block (sigma, tau) is U_b^T x|tau
+// of its canonical partner b, the sum over b's slices of the transposed
+// products pass A wrote per U column. One warp per canonical block: with at
+// most 8 slices lane l sums column l over them in tile order; else lane j
+// sums the slices j, j + 32, ... of column l, then a warp sum. bmcol[e] is
+// the first U column of b's block-major entry e.
+__global__ void k_tmirror(const int32_t* __restrict__ rank, const int32_t* __restrict__ mirror_of,
+                          const int64_t* __restrict__ boff, const int64_t* __restrict__ bmcol,
+                          int64_t nlr, int64_t nb, const int64_t* __restrict__ toff,
+                          const float* __restrict__ zu, float* __restrict__ t)
+{
+    const int64_t b = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (b >= nb) return;
+    const int32_t m = mirror_of[b];
+    if (m < 0) return;
+    const int k = rank[b];
+    const int64_t e0 = boff[b], e1 = b + 1 < nb ? boff[b + 1] : nlr;
+    if (e1 - e0 <= 8) {
+        // few slices (most blocks): lane l sums column l over them in order
+        for (int l = lane; l < k; l += 32) {
+            float sum = 0.f;
+            for (int64_t e = e0; e < e1; ++e) sum += zu[bmcol[e] + l];
+            t[toff[m] + l] = sum;
+        }
+        return;
+    }
+    for (int l = 0; l < k; ++l) {
+        float sum = 0.f;
+        for (int64_t e = e0 + lane; e < e1; e += 32) sum += zu[bmcol[e] + l];
+        sum = warp_sum(sum);
+        if (lane == 0) t[toff[m] + l] = sum;
+    }
+}
+
+// First U column of every block-major low-rank entry (through the CSR
+// position of the entry).
+__global__ void k_bm_ecol(const int64_t* __restrict__ pos, const int64_t* __restrict__ ecol,
+                          int64_t n, int64_t* __restrict__ out)
+{
+    const int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (e < n) out[e] = ecol[pos[e]];
+}
+
 // The finish of a symmetric near field (tiles of at most 64 rows): one CTA
 // per tile, four groups of 64 threads (thread = row). Group g sums the
 // mirror leaves' transposed products of records g, g + 4, ... in record
@@ -603,6 +666,11 @@ k_tile_finish_sym(MvpPlan P, const double* __restrict__ part, const double* __re
     const int64_t i0 = P.item_ptr[tile], i1 = P.item_ptr[tile + 1];
     double sum = 0.0;
     for (int64_t q = i0; q < i1; ++q) sum += part[q * P.max_ld + i];
+    if (P.item_ptr_b) {
+        // pass B's items (mirror slices), stored after pass A's
+        const int64_t j0 = P.item_ptr_b[tile], j1 = P.item_ptr_b[tile + 1];
+        for (int64_t q = j0; q < j1; ++q) sum += part[(P.n_items + q) * P.max_ld + i];
+    }
     sum += zs[0][i];
     sum += zs[1][i];
     sum += zs[2][i];
@@ -646,14 +714,14 @@ __global__ void k_emit_entries(const Blk* __restrict__ blk, int64_t nb,
                                const int64_t* __restrict__ cnt, const int64_t* __restrict__ off,
                                const int64_t* __restrict__ tr0, uint64_t* __restrict__ key,
                                uint32_t* __restrict__ val, int2* __restrict__ ent,
-                               int32_t* __restrict__ tcount)
+                               int32_t* __restrict__ tcount, const int32_t* __restrict__ cls)
 {
     int64_t b = (int64_t)blockIdx.x * NT + threadIdx.x;
     if (b >= nb) return;
     const Blk B = blk[b];
     for (int64_t q = 0; q < cnt[b]; ++q) {
         int64_t e = off[b] + q, tl = first[b] + q;
-        key[e] = (uint64_t)tl;
+        key[e] = cls ? 2 * (uint64_t)tl + (uint64_t)cls[b] : (uint64_t)tl;
         val[e] = (uint32_t)e;
         ent[e] = make_int2((int)b, (int)(tr0[tl] - B.row0));
         atomicAdd(&tcount[tl], 1);
@@ -673,9 +741,21 @@ __global__ void k_i32_to_i64(const int32_t* __restrict__ in, int64_t n, int64_t*
     if (e < n) out[e] = in[e];
 }
 
-// Build one CSR over tiles for a list of blocks.
+__global__ void k_inverse_perm(const uint32_t* __restrict__ val, int64_t n, int64_t* __restrict__ pos)
+{
+    int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (i < n) pos[val[i]] = i;
+}
+
+// Build one CSR over tiles for a list of blocks. Within a tile the entries
+// keep block order; with cls (0 or 1 per block) the class-0 entries of a
+// tile come first. boff/pos (optional): the first block-major entry of every
+// block (its entries over its tiles are boff[b] .. boff[b] + count - 1, in
+// tile order) and the CSR position of every block-major entry.
 void build_csr(const Blk* blk, int64_t nb, const int64_t* tr0, int64_t nt,
-               DevBuf<int64_t>& ptr, DevBuf<int2>& ent, cudaStream_t s)
+               DevBuf<int64_t>& ptr, DevBuf<int2>& ent, cudaStream_t s,
+               const int32_t* cls = nullptr, DevBuf<int64_t>* boff = nullptr,
+               DevBuf<int64_t>* pos = nullptr)
 {
     ptr.alloc(nt + 1, s);
     DevBuf<int32_t> tcount(nt + 1, s);
@@ -696,11 +776,16 @@ void build_csr(const Blk* blk, int64_t nb, const int64_t* tr0, int64_t nt,
     DevBuf<uint32_t> val(E, s);
     DevBuf<int2> tmp(E, s);
     k_emit_entries<<<grid_for(nb), NT, 0, s>>>(blk, nb, first.p, cnt.p, off.p, tr0, key.p,
-                                               val.p, tmp.p, tcount.p); note_launch();
+                                               val.p, tmp.p, tcount.p, cls); note_launch();
     HM_LAUNCH("emit entries");
-    radix_sort_u64_u32(key.p, val.p, E, bits_for(nt + 1), s);
+    radix_sort_u64_u32(key.p, val.p, E, bits_for(nt + 1) + (cls ? 1 : 0), s);
     ent.alloc(E, s);
     k_gather_ent<<<grid_for(E), NT, 0, s>>>(tmp.p, val.p, E, ent.p); note_launch();
+    if (pos) {
+        pos->alloc(E, s);
+        k_inverse_perm<<<grid_for(E), NT, 0, s>>>(val.p, E, pos->p); note_launch();
+    }
+    if (boff) *boff = std::move(off);
     DevBuf<int64_t> c64(nt + 1, s);
     k_i32_to_i64<<<grid_for(nt + 1), NT, 0, s>>>(tcount.p, nt + 1, c64.p); note_launch();
     scan_exclusive_i64(c64.p, ptr.p, nt + 1, nullptr, s);
@@ -802,12 +887,13 @@ __global__ void k_relayout_u(const int2* __restrict__ ent, const int32_t* __rest
 __global__ void k_vitems_count(const Blk* __restrict__ blk, const int32_t* __restrict__ rank,
                                int64_t nb, int64_t* __restrict__ cnt,
                                int64_t* __restrict__ multi_t, int32_t* __restrict__ ismulti,
-                               int64_t* __restrict__ rk)
+                               int64_t* __restrict__ rk, const int32_t* __restrict__ cls)
 {
     int64_t b = (int64_t)blockIdx.x * NT + threadIdx.x;
     if (b >= nb) return;
     int k = rank[b];
-    int64_t c = k > 0 ? ceil_div(blk[b].n, VCH) : 0;
+    // (the symmetric low-rank part forms a mirror block's t in pass A)
+    int64_t c = (k > 0 && !(cls && cls[b])) ? ceil_div(blk[b].n, VCH) : 0;
     cnt[b] = c;
     multi_t[b] = c > 1 ? c * k : 0;
     ismulti[b] = c > 1 ? 1 : 0;
@@ -886,6 +972,82 @@ __global__ void k_fill_ncol(const int2* __restrict__ ent, int64_t ne, const Blk*
     for (int c = 0; c < B.n; ++c) ncol_x[ecol[e] + c] = (int32_t)(B.col0 + c);
 }
 
+// Gather work items: a tile's U-then-near column stream in pieces of at most
+// ITEM_COLS columns, so that the few tiles with very many near-field columns
+// (clusters of coincident points are mutually inadmissible) do not leave one
+// CTA streaming long after the others have finished.
+constexpr int64_t ITEM_COLS = 4096;
+
+// Symmetric low-rank part: class of every admissible block (1: mirror,
+// row0 > col0) and, for a canonical block, the index of its mirror (col0,
+// row0) in the (row0, col0)-ordered list (-1 when the list lacks it, as in a
+// block-row share).
+__global__ void k_adm_class(const Blk* __restrict__ blk, int64_t n, int32_t* __restrict__ cls,
+                            int32_t* __restrict__ mir)
+{
+    const int64_t b = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (b >= n) return;
+    const Blk B = blk[b];
+    cls[b] = B.row0 > B.col0 ? 1 : 0;
+    int32_t m = -1;
+    if (B.row0 < B.col0) {
+        int64_t lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            const Blk C = blk[mid];
+            if (C.row0 < B.col0 || (C.row0 == B.col0 && C.col0 < B.row0)) lo = mid + 1;
+            else hi = mid;
+        }
+        const Blk C = blk[lo];
+        if (C.row0 == B.col0 && C.col0 == B.row0) m = (int32_t)lo;
+    }
+    mir[b] = m;
+}
+
+// First mirror column of every tile's U stream (class-1 entries follow the
+// class-0 ones within a tile).
+__global__ void k_umid(const int64_t* __restrict__ ptr, const int2* __restrict__ ent,
+                       const int32_t* __restrict__ cls, const int64_t* __restrict__ ecol,
+                       const int64_t* __restrict__ ucol_ptr, int64_t nt, int64_t* __restrict__ umid)
+{
+    const int64_t q = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (q >= nt) return;
+    int64_t e = ptr[q];
+    while (e < ptr[q + 1] && cls[ent[e].x] == 0) ++e;
+    umid[q] = e < ptr[q + 1] ? ecol[e] : ucol_ptr[q + 1];
+}
+
+// Pass A / pass B columns of every tile (A: canonical U + near; B: mirror U).
+__global__ void k_pass_cols(const int64_t* __restrict__ ucol_ptr, const int64_t* __restrict__ umid,
+                            const int64_t* __restrict__ ncol_ptr, int64_t nt,
+                            int64_t* __restrict__ ca, int64_t* __restrict__ cb)
+{
+    const int64_t q = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (q >= nt) return;
+    ca[q] = (umid[q] - ucol_ptr[q]) + (ncol_ptr[q + 1] - ncol_ptr[q]);
+    cb[q] = ucol_ptr[q + 1] - umid[q];
+}
+
+// Items over per-tile column counts c[q]: pieces of at most ITEM_COLS
+// columns; a tile without columns gets one item when keep_empty.
+__global__ void k_items_from_counts(const int64_t* __restrict__ c, int64_t nt, int keep_empty,
+                                    int64_t* __restrict__ cnt)
+{
+    const int64_t q = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (q < nt) cnt[q] = c[q] > 0 ? ceil_div(c[q], ITEM_COLS) : (keep_empty ? 1 : 0);
+}
+
+__global__ void k_items_emit_counts(const int64_t* __restrict__ c, int64_t nt,
+                                    const int64_t* __restrict__ off, int3* __restrict__ items)
+{
+    const int64_t q = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (q >= nt) return;
+    const int64_t n = off[q + 1] - off[q];
+    for (int64_t i = 0; i < n; ++i)
+        items[off[q] + i] = make_int3((int)q, (int)(i * ITEM_COLS),
+                                      (int)(c[q] < (i + 1) * ITEM_COLS ? c[q] : (i + 1) * ITEM_COLS));
+}
+
 // Symmetric near field: the near entries of off-diagonal leaves (row0 !=
 // col0; the list holds only leaves with row0 <= col0) give transposed
 // products over their columns, which are rows of the mirror leaf. zblk[j]
@@ -933,10 +1095,7 @@ __global__ void k_z_records(const int2* __restrict__ zent, const int32_t* __rest
 }
 
 // Gather work items: a tile's U-then-near column stream in pieces of at most
-// ITEM_COLS columns, so that the few tiles with very many near-field columns
-// (clusters of coincident points are mutually inadmissible) do not leave one
-// CTA streaming long after the others have finished.
-constexpr int64_t ITEM_COLS = 4096;
+// ITEM_COLS columns (defined above).
 
 __global__ void k_item_count(const int64_t* __restrict__ ucol_ptr, const int64_t* __restrict__ ncol_ptr,
                              int64_t nt, int64_t* __restrict__ cnt)
@@ -967,7 +1126,20 @@ void mvp_build_lists(const Blk* ablk, const int32_t* rank, int64_t n_adm, const 
 {
     L.n_tiles = n_tiles;
     L.sym_near = sym_near;
-    build_csr(ablk, n_adm, leaf_row0, n_tiles, L.lr_ptr, L.lr_ent, s);
+    // symmetric low-rank part: class 1 = mirror blocks (row0 > col0), whose
+    // slices follow the canonical ones in every tile
+    DevBuf<int32_t> acls;
+    if (sym_near) {
+        acls.alloc(std::max<int64_t>(n_adm, 1), s);
+        L.mirror_of.alloc(std::max<int64_t>(n_adm, 1), s);
+        if (n_adm > 0) {
+            k_adm_class<<<grid_for(n_adm), NT, 0, s>>>(ablk, n_adm, acls.p, L.mirror_of.p); note_launch();
+        }
+        build_csr(ablk, n_adm, leaf_row0, n_tiles, L.lr_ptr, L.lr_ent, s, acls.p, &L.lr_boff,
+                  &L.lr_pos);
+    } else {
+        build_csr(ablk, n_adm, leaf_row0, n_tiles, L.lr_ptr, L.lr_ent, s);
+    }
     build_csr(dblk, n_dense, leaf_row0, n_tiles, L.dn_ptr, L.dn_ent, s);
     {
         int64_t h[2] = {0, 0};
@@ -1056,7 +1228,8 @@ void mvp_build_lists(const Blk* ablk, const int32_t* rank, int64_t n_adm, const 
     int64_t h[3] = {0, 0, 0};
     int32_t hm = 0;
     if (n_adm > 0) {
-        k_vitems_count<<<grid_for(n_adm), NT, 0, s>>>(ablk, rank, n_adm, cnt.p, mt.p, ism.p, rk.p); note_launch();
+        k_vitems_count<<<grid_for(n_adm), NT, 0, s>>>(ablk, rank, n_adm, cnt.p, mt.p, ism.p, rk.p,
+                                                     sym_near ? acls.p : nullptr); note_launch();
         scan_exclusive_i64(cnt.p, ioff.p, n_adm, tot.p, s);
         scan_exclusive_i64(mt.p, poff.p, n_adm, tot.p + 1, s);
         scan_exclusive_i64(rk.p, L.toff.p, n_adm, tot.p + 2, s);
@@ -1103,6 +1276,14 @@ void mvp_build_lists(const Blk* ablk, const int32_t* rank, int64_t n_adm, const 
                                                              L.ucol_ptr.p, L.ubase.p); note_launch();
         k_fill_ucol<<<grid_for(L.n_lr), NT, 0, s>>>(L.lr_ent.p, L.n_lr, rank, L.toff.p, ecol.p,
                                                    L.ucol_t.p); note_launch();
+        if (sym_near) {
+            L.umid.alloc(n_tiles, s);
+            k_umid<<<grid_for(n_tiles), NT, 0, s>>>(L.lr_ptr.p, L.lr_ent.p, acls.p, ecol.p,
+                                                   L.ucol_ptr.p, n_tiles, L.umid.p); note_launch();
+            // lr_ecol: the first U column of every block-major entry
+            L.lr_ecol.alloc(L.n_lr, s);
+            k_bm_ecol<<<grid_for(L.n_lr), NT, 0, s>>>(L.lr_pos.p, ecol.p, L.n_lr, L.lr_ecol.p); note_launch();
+        }
         HM_CUDA(cudaStreamSynchronize(s));
     } else {
         L.ucol_ptr.alloc(n_tiles + 1, s);
@@ -1110,6 +1291,48 @@ void mvp_build_lists(const Blk* ablk, const int32_t* rank, int64_t n_adm, const 
         L.ucol_t.alloc(1, s);
         HM_CUDA(cudaMemsetAsync(L.ucol_ptr.p, 0, (n_tiles + 1) * sizeof(int64_t), s));
         HM_CUDA(cudaMemsetAsync(L.ubase.p, 0, std::max<int64_t>(n_tiles, 1) * sizeof(int64_t), s));
+        if (sym_near) {
+            L.umid.alloc(std::max<int64_t>(n_tiles, 1), s);
+            HM_CUDA(cudaMemsetAsync(L.umid.p, 0, std::max<int64_t>(n_tiles, 1) * sizeof(int64_t), s));
+            L.lr_ecol.alloc(1, s);
+        }
+    }
+    if (sym_near) {
+        if (!L.lr_boff.p) L.lr_boff.alloc(1, s);
+        if (!L.lr_pos.p) L.lr_pos.alloc(1, s);
+        // pass A (canonical U slices, then the near field) and pass B (mirror
+        // U slices) work items
+        const int64_t nt = std::max<int64_t>(n_tiles, 1);
+        DevBuf<int64_t> ca(nt, s), cb(nt, s), cnt(nt, s);
+        k_pass_cols<<<grid_for(n_tiles), NT, 0, s>>>(L.ucol_ptr.p, L.umid.p, L.ncol_ptr.p, n_tiles,
+                                                     ca.p, cb.p); note_launch();
+        L.item_ptr.alloc(nt + 1, s);
+        L.item_ptr_b.alloc(nt + 1, s);
+        k_items_from_counts<<<grid_for(n_tiles), NT, 0, s>>>(ca.p, n_tiles, 1, cnt.p); note_launch();
+        scan_exclusive_i64(cnt.p, L.item_ptr.p, n_tiles, L.item_ptr.p + n_tiles, s);
+        k_items_from_counts<<<grid_for(n_tiles), NT, 0, s>>>(cb.p, n_tiles, 0, cnt.p); note_launch();
+        scan_exclusive_i64(cnt.p, L.item_ptr_b.p, n_tiles, L.item_ptr_b.p + n_tiles, s);
+        HM_CUDA(cudaMemcpyAsync(&L.n_items, L.item_ptr.p + n_tiles, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        HM_CUDA(cudaMemcpyAsync(&L.n_items_b, L.item_ptr_b.p + n_tiles, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        HM_CUDA(cudaStreamSynchronize(s));
+        if (L.n_items + L.n_items_b > INT32_MAX) fail(HM_EOVERFLOW, "too many gather items");
+        L.items.alloc(std::max<int64_t>(L.n_items, 1), s);
+        L.items_b.alloc(std::max<int64_t>(L.n_items_b, 1), s);
+        k_items_emit_counts<<<grid_for(n_tiles), NT, 0, s>>>(ca.p, n_tiles, L.item_ptr.p, L.items.p); note_launch();
+        k_items_emit_counts<<<grid_for(n_tiles), NT, 0, s>>>(cb.p, n_tiles, L.item_ptr_b.p, L.items_b.p); note_launch();
+        // elements of the canonical slices (the bytes pass A streams)
+        std::vector<int64_t> hu(n_tiles + 1), hm(n_tiles);
+        std::vector<int32_t> htm(n_tiles);
+        if (n_tiles > 0) {
+            HM_CUDA(cudaMemcpyAsync(hu.data(), L.ucol_ptr.p, (n_tiles + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            HM_CUDA(cudaMemcpyAsync(hm.data(), L.umid.p, n_tiles * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            HM_CUDA(cudaMemcpyAsync(htm.data(), leaf_m, n_tiles * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            HM_CUDA(cudaStreamSynchronize(s));
+        }
+        L.u_elems_canon = 0;
+        for (int64_t q = 0; q < n_tiles; ++q) L.u_elems_canon += (hm[q] - hu[q]) * slice_ld(htm[q]);
+        HM_LAUNCH("descriptors");
+        return;
     }
     // gather work items
     {
@@ -1145,8 +1368,9 @@ void mvp_relayout_u(int precision, const MvpLists& L, const Blk* ablk, const uin
 
 void mvp_alloc_work(const MvpPlan& P, MvpWork& W, cudaStream_t s)
 {
-    W.part.alloc(std::max<int64_t>(P.n_items, 1) * std::max(P.max_ld, 1), s);
+    W.part.alloc(std::max<int64_t>(P.n_items + P.n_items_b, 1) * std::max(P.max_ld, 1), s);
     if (P.sym_near) W.zbuf.alloc(std::max<int64_t>(P.n_ncols, 1), s);
+    if (P.umid) W.zubuf.alloc(std::max<int64_t>(P.n_ucols, 1), s);
     if (P.precision == HM_PREC_FP64) {
         W.xm64.alloc(std::max<int64_t>(P.Ntot, 1), s);
         W.t64.alloc(std::max<int64_t>(P.t_len, 1), s);
@@ -1297,7 +1521,35 @@ void run_typed(const MvpPlan& P, R* xm, R* t, R* tp, double* part, const double*
         k_tsum<R><<<(unsigned)P.n_multi, 64, 0, s>>>(P.multi, P.n_multi, P.rank, P.tsum_first,
                                                      P.tsum_count, P.tpart_off, P.toff, tp, t); note_launch();
     if (rec) HM_CUDA(cudaEventRecord(rec->e[2], s));
-    if (P.n_tiles > 0) {
+    if (P.n_tiles > 0 && P.umid) {
+        // symmetric low-rank part (float plans with the symmetric near
+        // field): pass A, the mirror blocks' t, pass B, finish
+        if constexpr (sizeof(R) == 4) {
+            MvpPlan A = P;
+            A.uview = 1;
+            int v = tile_variant(A);
+            if (v < 0) v = tune_tile<R, FMT>(A, xm, t, part, s);
+            launch_tile<R, FMT>(v, A, xm, t, part, s);
+            if (P.n_adm > 0) {
+                k_tmirror<<<(unsigned)ceil_div(P.n_adm * 32, NT), NT, 0, s>>>(
+                    P.rank, P.mirror_of, P.lr_boff, P.lr_ecol, P.n_lr, P.n_adm, P.toff,
+                    P.zubuf, t); note_launch();
+            }
+            if (P.n_items_b > 0) {
+                MvpPlan B = P;
+                B.uview = 2;
+                B.sym_near = 0;          // no near field and no transposed products
+                B.zubuf = nullptr;
+                B.items = P.items_b;
+                B.n_items = P.n_items_b;
+                launch_tile<R, FMT>(v == 3 ? 3 : 4, B, xm, t, part + P.n_items * P.max_ld, s);
+            }
+            k_tile_finish_sym<<<(unsigned)P.n_tiles, 256, 0, s>>>(P, part, x, y, accumulate);
+            note_launch();
+        } else {
+            fail(HM_ENOTSUP, "symmetric low-rank part: single precision only");
+        }
+    } else if (P.n_tiles > 0) {
         int v = tile_variant(P);
         if (v < 0) v = tune_tile<R, FMT>(P, xm, t, part, s);
         const int64_t bs = mvp_batch_items();
@@ -1391,6 +1643,7 @@ void mvp_run(const MvpPlan& P0, MvpWork& W, const double* x, double* y, int accu
     P.wait_ns = mvp_wait_ns();
     P.withhold = mvp_withhold();
     P.zbuf = W.zbuf.p;
+    P.zubuf = P.umid ? W.zubuf.p : nullptr;
     if (P.precision == HM_PREC_FP64) {
         run_typed<double, HM_NEAR_FP64>(P, W.xm64.p, W.t64.p, W.tp64.p, W.part.p, x, y, accumulate, s, timer);
         return;

@@ -318,14 +318,14 @@ __global__ void k_copy_factors(const Blk* __restrict__ blk, const uint32_t* __re
 // Statistics of the factors: [sum rank, max rank, cap hits, mispredicted,
 // rejected, factor entries, reserved entries, sum k m, evaluations,
 // sum 2 k (k-1) (m + n)]
-constexpr int NSTAT = 10;
+constexpr int NSTAT = 11;
 __global__ void k_rank_stats(const Blk* __restrict__ blk, const int32_t* __restrict__ rank,
                              const int32_t* __restrict__ nrej, const int32_t* __restrict__ flags,
                              const int32_t* __restrict__ kres, int64_t n,
                              unsigned long long* __restrict__ out)
 {
     int64_t b = (int64_t)blockIdx.x * NT + threadIdx.x;
-    unsigned long long s[NSTAT] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    unsigned long long s[NSTAT] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     if (b < n) {
         const unsigned long long r = rank[b], m = blk[b].m, nn = blk[b].n;
         const bool own = !(flags[b] & MIRROR_FLAG);   // compressed by its own ACA
@@ -339,6 +339,7 @@ __global__ void k_rank_stats(const Blk* __restrict__ blk, const int32_t* __restr
         s[7] = r * m;
         s[8] = own ? r * (m + nn) + (unsigned long long)nrej[b] * m : 0ull;
         s[9] = own && r ? 2ull * r * (r - 1) * (m + nn) : 0ull;
+        s[10] = blk[b].row0 < blk[b].col0 ? r * nn : 0ull;   // V of the canonical blocks
     }
     for (int o = 16; o > 0; o >>= 1)
         for (int k = 0; k < NSTAT; ++k) {
@@ -1033,6 +1034,7 @@ void rank_stats(hm_handle_s& h)
     h.stats.factor_entries = (int64_t)o[5];
     h.stats.reserved_factor_entries = (int64_t)o[6];
     h.factor_entries_U = (int64_t)o[7];
+    h.factor_entries_Vc = (int64_t)o[10];
     h.stats.aca_evals = (int64_t)o[8];
     // algorithmic flops of one kernel evaluation: squared distance in three
     // coordinates (3 subtractions, 1 multiply, 2 fused multiply-adds = 8)
@@ -1447,6 +1449,17 @@ void build_sets(hm_handle_s& h, int nsets, const double* points_all, const int64
     P.zptr = h.lists.zptr.p;
     P.zbase = h.lists.zbase.p;
     P.zlen = h.lists.zlen.p;
+    if (h.sym_near) {
+        P.umid = h.lists.umid.p;
+        P.n_items_b = h.lists.n_items_b;
+        P.items_b = h.lists.items_b.p;
+        P.item_ptr_b = h.lists.item_ptr_b.p;
+        P.mirror_of = h.lists.mirror_of.p;
+        P.lr_boff = h.lists.lr_boff.p;
+        P.lr_pos = h.lists.lr_pos.p;
+        P.lr_ecol = h.lists.lr_ecol.p;
+        P.n_lr = h.lists.n_lr;
+    }
     mvp_alloc_work(P, h.work, s);
     HM_CUDA(cudaStreamSynchronize(s));
 
@@ -1476,6 +1489,19 @@ void build_sets(hm_handle_s& h, int nsets, const double* points_all, const int64
     // field, its column indices, perm and x (for sigma^2 x) and writes y
     st.mvp_vtx_bytes = (st.factor_entries - h.factor_entries_U) * fsz + h.lists.t_len * fsz;
     st.mvp_tile_bytes = h.factor_entries_U * fsz + st.near_bytes + Ntot * (8 + 8 + 8) + idx_bytes;
+    if (h.sym_near && h.lists.umid.p) {
+        // symmetric low-rank part: V^T x reads the canonical blocks' V; the
+        // gather reads the canonical U (pass A, writing one float per U
+        // column read back by k_tmirror) and the canonical V as the mirror
+        // slices (pass B)
+        const int64_t vtx = h.factor_entries_Vc * fsz + h.lists.t_len * fsz;
+        const int64_t zu = 8 * h.lists.n_ucols;
+        st.mvp_tile_bytes = (h.factor_entries_U - h.factor_entries_Vc) * fsz +
+                            h.factor_entries_Vc * fsz + st.near_bytes + Ntot * (8 + 8 + 8) +
+                            idx_bytes + zu;
+        st.mvp_vtx_bytes = vtx;
+        st.mvp_bytes = st.mvp_tile_bytes + vtx;
+    }
     st.t_total_ms =
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
