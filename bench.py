@@ -1111,14 +1111,22 @@ def main():
     mvp_t_tile = st["t_mvp_tile_ms"] / max(st["mvp_count"], 1)
     mvp_t_vtx = st["t_mvp_vtx_ms"] / max(st["mvp_count"], 1)
     mvp_t = st["t_mvp_ms"] / max(st["mvp_count"], 1)
-    mvp_roof = {"bound": "hbm", "kernel": "k_tile (gather: U slices + near field)",
+    mvp_t_tail = st["t_mvp_tail_ms"] / max(st["mvp_count"], 1)
+    gname = ("k_tile_tma pass A (canonical U slices + symmetric near field, transposed "
+             "products)" if use_sym == 2 else "k_tile (gather: U slices + near field)")
+    mvp_roof = {"bound": "hbm", "kernel": gname,
                 "achieved": st["mvp_tile_bytes"] / (mvp_t_tile * 1e-3) / 1e9, "peak": hbm,
                 "unit": "GB/s", "traffic": tile_traffic(st["mvp_tile_bytes"]),
-                "algorithmic_bytes": st["mvp_tile_bytes"],
+                "algorithmic_bytes": st["mvp_tile_bytes"], "ms": mvp_t_tile,
                 "whole_product": {"achieved": st["mvp_bytes"] / (mvp_t * 1e-3) / 1e9,
                                   "ms": mvp_t, "bytes": st["mvp_bytes"]},
                 "vtx": {"achieved": st["mvp_vtx_bytes"] / (mvp_t_vtx * 1e-3) / 1e9,
-                        "ms": mvp_t_vtx}}
+                        "ms": mvp_t_vtx, "bytes": st["mvp_vtx_bytes"]},
+                "tail": {"what": ("mirror t (k_tmirror), pass B (mirror slices), finish"
+                                  if use_sym == 2 else "finish"),
+                         "achieved": st["mvp_tail_bytes"] / (mvp_t_tail * 1e-3) / 1e9
+                         if mvp_t_tail > 0 else None,
+                         "ms": mvp_t_tail, "bytes": st["mvp_tail_bytes"]}}
     mvp_roof["frac"] = mvp_roof["achieved"] / hbm
     mvp_roof["peak_source"] = peak_src + " copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
     aca_roof = {"bound": "alu", "kernel": "batched ACA (all size classes, concurrent)",

@@ -352,7 +352,8 @@ typedef struct hm_stats {
     /* profile = 1: sums over the products since the last hm_get_stats */
     int64_t mvp_count;
     double t_mvp_ms, t_mvp_gather_ms, t_mvp_vtx_ms, t_mvp_tile_ms;
-    int64_t mvp_vtx_bytes, mvp_tile_bytes;  /* algorithmic bytes per product */
+    int64_t mvp_vtx_bytes, mvp_tile_bytes;  /* algorithmic bytes per product of
+                                               V^T x and of the main gather kernel */
     /* last build: ACA time per block size class (class c: 2^(c+5) < max(m, n)
        <= 2^(c+6); class 0 from 1, class 11 unbounded), CUDA events on each
        class's stream (the classes run concurrently), summed over passes */
@@ -366,6 +367,12 @@ typedef struct hm_stats {
     /* last build: traversals run again because a level of the block tree
        did not fit its bound (summed over the point sets) */
     int traversal_reruns;
+    /* profile = 1: the product's time and algorithmic bytes after its main
+       gather kernel (t_mvp_tile_ms, mvp_tile_bytes): the finish that writes
+       y and, with symmetric = 2, the mirror blocks' t and the gather of the
+       mirror slices (sums over the products since the last hm_get_stats) */
+    double t_mvp_tail_ms;
+    int64_t mvp_tail_bytes;
 } hm_stats;
 
 int hm_get_stats(hm_handle h, hm_stats* out);

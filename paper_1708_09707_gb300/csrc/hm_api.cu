@@ -423,8 +423,10 @@ int hm_get_stats(hm_handle h, hm_stats* out)
             h->stats.t_mvp_gather_ms = h->timer.t_gather;
             h->stats.t_mvp_vtx_ms = h->timer.t_vtx;
             h->stats.t_mvp_tile_ms = h->timer.t_tile;
+            h->stats.t_mvp_tail_ms = h->timer.t_tail;
             h->timer.count = 0;
             h->timer.t_total = h->timer.t_gather = h->timer.t_vtx = h->timer.t_tile = 0.0;
+            h->timer.t_tail = 0.0;
         }
     } catch (const std::exception& e) {
         return to_status(e);

@@ -280,11 +280,11 @@ struct MvpPlan {
 // CUDA events around the product's kernels (when profiling), read later.
 struct MvpTimer {
     struct Rec {
-        cudaEvent_t e[4];
+        cudaEvent_t e[5];
     };
     std::vector<Rec> recs;
     std::vector<Rec> pool;
-    double t_total = 0, t_gather = 0, t_vtx = 0, t_tile = 0;
+    double t_total = 0, t_gather = 0, t_vtx = 0, t_tile = 0, t_tail = 0;
     int64_t count = 0;
     Rec* begin();
     void collect();   // synchronises the recorded events and sums the times
@@ -395,6 +395,7 @@ struct MvpLists {
     DevBuf<int32_t> mirror_of;
     int64_t n_items_b = 0;
     int64_t u_elems_canon = 0;   // elements of the canonical slices
+    int64_t n_ucols_canon = 0;   // U columns of the canonical slices
 };
 // dblk: the dense leaves to store; with sym_near they are the canonical ones
 // (row0 <= col0) and the lists also get the transposed-product records.

@@ -1330,7 +1330,11 @@ void mvp_build_lists(const Blk* ablk, const int32_t* rank, int64_t n_adm, const 
             HM_CUDA(cudaStreamSynchronize(s));
         }
         L.u_elems_canon = 0;
-        for (int64_t q = 0; q < n_tiles; ++q) L.u_elems_canon += (hm[q] - hu[q]) * slice_ld(htm[q]);
+        L.n_ucols_canon = 0;
+        for (int64_t q = 0; q < n_tiles; ++q) {
+            L.u_elems_canon += (hm[q] - hu[q]) * slice_ld(htm[q]);
+            L.n_ucols_canon += hm[q] - hu[q];
+        }
         HM_LAUNCH("descriptors");
         return;
     }
@@ -1530,6 +1534,7 @@ void run_typed(const MvpPlan& P, R* xm, R* t, R* tp, double* part, const double*
             int v = tile_variant(A);
             if (v < 0) v = tune_tile<R, FMT>(A, xm, t, part, s);
             launch_tile<R, FMT>(v, A, xm, t, part, s);
+            if (rec) HM_CUDA(cudaEventRecord(rec->e[3], s));
             if (P.n_adm > 0) {
                 k_tmirror<<<(unsigned)ceil_div(P.n_adm * 32, NT), NT, 0, s>>>(
                     P.rank, P.mirror_of, P.lr_boff, P.lr_ecol, P.n_lr, P.n_adm, P.toff,
@@ -1565,13 +1570,15 @@ void run_typed(const MvpPlan& P, R* xm, R* t, R* tp, double* part, const double*
         } else {
             launch_tile<R, FMT>(v, P, xm, t, part, s);
         }
+        if (rec) HM_CUDA(cudaEventRecord(rec->e[3], s));
         if (P.sym_near)
             k_tile_finish_sym<<<(unsigned)P.n_tiles, 256, 0, s>>>(P, part, x, y, accumulate);
         else
             k_tile_finish<<<grid_for(P.n_tiles * 32), NT, 0, s>>>(P, part, x, y, accumulate);
         note_launch();
     }
-    if (rec) HM_CUDA(cudaEventRecord(rec->e[3], s));
+    if (rec && P.n_tiles <= 0) HM_CUDA(cudaEventRecord(rec->e[3], s));
+    if (rec) HM_CUDA(cudaEventRecord(rec->e[4], s));
     HM_LAUNCH("matvec");
 }
 
@@ -1584,7 +1591,7 @@ MvpTimer::Rec* MvpTimer::begin()
         r = pool.back();
         pool.pop_back();
     } else {
-        for (int k = 0; k < 4; ++k) HM_CUDA(cudaEventCreate(&r.e[k]));
+        for (int k = 0; k < 5; ++k) HM_CUDA(cudaEventCreate(&r.e[k]));
     }
     recs.push_back(r);
     return &recs.back();
@@ -1593,15 +1600,17 @@ MvpTimer::Rec* MvpTimer::begin()
 void MvpTimer::collect()
 {
     for (Rec& r : recs) {
-        HM_CUDA(cudaEventSynchronize(r.e[3]));
-        float a = 0, b = 0, c = 0;
+        HM_CUDA(cudaEventSynchronize(r.e[4]));
+        float a = 0, b = 0, c = 0, d = 0;
         HM_CUDA(cudaEventElapsedTime(&a, r.e[0], r.e[1]));
         HM_CUDA(cudaEventElapsedTime(&b, r.e[1], r.e[2]));
         HM_CUDA(cudaEventElapsedTime(&c, r.e[2], r.e[3]));
+        HM_CUDA(cudaEventElapsedTime(&d, r.e[3], r.e[4]));
         t_gather += a;
         t_vtx += b;
         t_tile += c;
-        t_total += a + b + c;
+        t_tail += d;
+        t_total += a + b + c + d;
         ++count;
         pool.push_back(r);
     }
@@ -1612,7 +1621,7 @@ MvpTimer::~MvpTimer()
 {
     for (Rec& r : recs) pool.push_back(r);
     for (Rec& r : pool)
-        for (int k = 0; k < 4; ++k) cudaEventDestroy(r.e[k]);
+        for (int k = 0; k < 5; ++k) cudaEventDestroy(r.e[k]);
 }
 
 namespace {

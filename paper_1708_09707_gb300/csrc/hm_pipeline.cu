@@ -1488,19 +1488,20 @@ void build_sets(hm_handle_s& h, int nsets, const double* points_all, const int64
     // per kernel: V^T x reads V and writes t; the gather reads U, the near
     // field, its column indices, perm and x (for sigma^2 x) and writes y
     st.mvp_vtx_bytes = (st.factor_entries - h.factor_entries_U) * fsz + h.lists.t_len * fsz;
-    st.mvp_tile_bytes = h.factor_entries_U * fsz + st.near_bytes + Ntot * (8 + 8 + 8) + idx_bytes;
+    st.mvp_tile_bytes = h.factor_entries_U * fsz + st.near_bytes + idx_bytes;
+    st.mvp_tail_bytes = Ntot * (8 + 8 + 8);   // the finish: x (sigma^2 x), perm, y
     if (h.sym_near && h.lists.umid.p) {
-        // symmetric low-rank part: V^T x reads the canonical blocks' V; the
-        // gather reads the canonical U (pass A, writing one float per U
-        // column read back by k_tmirror) and the canonical V as the mirror
-        // slices (pass B)
-        const int64_t vtx = h.factor_entries_Vc * fsz + h.lists.t_len * fsz;
-        const int64_t zu = 8 * h.lists.n_ucols;
-        st.mvp_tile_bytes = (h.factor_entries_U - h.factor_entries_Vc) * fsz +
-                            h.factor_entries_Vc * fsz + st.near_bytes + Ntot * (8 + 8 + 8) +
-                            idx_bytes + zu;
-        st.mvp_vtx_bytes = vtx;
-        st.mvp_bytes = st.mvp_tile_bytes + vtx;
+        // symmetric low-rank part: V^T x reads the canonical blocks' V; pass
+        // A reads the canonical U and the near field and writes one float
+        // per column; the tail reads those floats back (k_tmirror, the
+        // finish) and streams the canonical V as the mirror slices (pass B)
+        const int64_t uca = h.lists.n_ucols_canon, ucb = h.lists.n_ucols - uca;
+        const int64_t nnc = h.lists.n_ncols;
+        st.mvp_vtx_bytes = h.factor_entries_Vc * fsz + h.lists.t_len * fsz;
+        st.mvp_tile_bytes = (h.factor_entries_U - h.factor_entries_Vc) * fsz + st.near_bytes +
+                            8 * (uca + nnc);
+        st.mvp_tail_bytes = h.factor_entries_Vc * fsz + 4 * ucb + 4 * (uca + nnc) + Ntot * 24;
+        st.mvp_bytes = st.mvp_vtx_bytes + st.mvp_tile_bytes + st.mvp_tail_bytes;
     }
     st.t_total_ms =
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();

@@ -61,7 +61,8 @@ class Stats(C.Structure):
                 ("mvp_vtx_bytes", C.c_int64), ("mvp_tile_bytes", C.c_int64),
                 ("t_aca_class_ms", C.c_double * 12),
                 ("t_np_aca_ms", C.c_double), ("t_np_lowrank_ms", C.c_double),
-                ("t_np_near_ms", C.c_double), ("traversal_reruns", C.c_int)]
+                ("t_np_near_ms", C.c_double), ("traversal_reruns", C.c_int),
+                ("t_mvp_tail_ms", C.c_double), ("mvp_tail_bytes", C.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

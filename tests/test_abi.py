@@ -48,6 +48,8 @@ int main(void) {
     printf("soff_t_aca_class_ms %zu\n", offsetof(hm_stats, t_aca_class_ms));
     printf("soff_t_np_near_ms %zu\n", offsetof(hm_stats, t_np_near_ms));
     printf("soff_traversal_reruns %zu\n", offsetof(hm_stats, traversal_reruns));
+    printf("soff_t_mvp_tail_ms %zu\n", offsetof(hm_stats, t_mvp_tail_ms));
+    printf("soff_mvp_tail_bytes %zu\n", offsetof(hm_stats, mvp_tail_bytes));
     return 0;
 }
 """
@@ -71,8 +73,9 @@ def test_options_and_stats_layout():
         assert getattr(hm.Options, f).offset == c["off_" + f], f
     assert ctypes.sizeof(hm.Stats) == c["sizeof_stats"] == (
         8 * 5 + 4 * 2 + 8 + 8 + 8 * 9 + 8 * 4 + 4 * 3 + 4 + 8 + 8 + 8 + 8 * 4 + 8 * 2 + 8 * 12
-        + 8 * 3 + 8)
-    for f in ("t_aca_class_ms", "t_np_near_ms", "traversal_reruns"):
+        + 8 * 3 + 8 + 8 + 8)
+    for f in ("t_aca_class_ms", "t_np_near_ms", "traversal_reruns", "t_mvp_tail_ms",
+              "mvp_tail_bytes"):
         assert getattr(hm.Stats, f).offset == c["soff_" + f], f
 
 
