@@ -271,6 +271,8 @@ struct MvpPlan {
     const int64_t* lr_pos = nullptr;      // block-major entry -> CSR position
     const int64_t* lr_ecol = nullptr;     // block-major entry -> its first U column
     int64_t n_lr = 0;
+    const int32_t* big = nullptr;         // canonical blocks with more than 8 slices
+    int64_t n_big = 0;
     // permutation and diagonal shift
     const int64_t* perm = nullptr;      // Morton row -> caller index (absolute)
     double sigma2 = 0.0;
@@ -392,8 +394,8 @@ struct MvpLists {
     // symmetric low-rank part (with sym_near): see MvpPlan
     DevBuf<int64_t> umid, item_ptr_b, lr_boff, lr_pos, lr_ecol;
     DevBuf<int3> items_b;
-    DevBuf<int32_t> mirror_of;
-    int64_t n_items_b = 0;
+    DevBuf<int32_t> mirror_of, big;
+    int64_t n_items_b = 0, n_big = 0;
     int64_t u_elems_canon = 0;   // elements of the canonical slices
     int64_t n_ucols_canon = 0;   // U columns of the canonical slices
 };

@@ -600,38 +600,69 @@ __global__ void k_tile_finish(MvpPlan P, const double* __restrict__ part, const 
 }
 
 // Symmetric low-rank part: t of every mirror block (sigma, tau) is U_b^T x|tau
-// of its canonical partner b, the sum over b's slices of the transposed
-// products pass A wrote per U column. One warp per canonical block: with at
-// most 8 slices lane l sums column l over them in tile order; else lane j
-// sums the slices j, j + 32, ... of column l, then a warp sum. bmcol[e] is
-// the first U column of b's block-major entry e.
-__global__ void k_tmirror(const int32_t* __restrict__ rank, const int32_t* __restrict__ mirror_of,
-                          const int64_t* __restrict__ boff, const int64_t* __restrict__ bmcol,
-                          int64_t nlr, int64_t nb, const int64_t* __restrict__ toff,
-                          const float* __restrict__ zu, float* __restrict__ t)
+// of its canonical partner b, the sum over b's slices (tile order) of the
+// transposed products pass A wrote per U column; bmcol[e] is the first U
+// column of b's block-major entry e. Blocks of at most 8 slices (most): one
+// thread per block, column by column, the slices in order.
+__global__ void k_tmirror_small(const int32_t* __restrict__ rank,
+                                const int32_t* __restrict__ mirror_of,
+                                const int64_t* __restrict__ boff, const int64_t* __restrict__ bmcol,
+                                int64_t nlr, int64_t nb, const int64_t* __restrict__ toff,
+                                const float* __restrict__ zu, float* __restrict__ t)
 {
-    const int64_t b = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+    const int64_t b = (int64_t)blockIdx.x * NT + threadIdx.x;
     if (b >= nb) return;
     const int32_t m = mirror_of[b];
     if (m < 0) return;
+    const int64_t e0 = boff[b], e1 = b + 1 < nb ? boff[b + 1] : nlr;
+    if (e1 - e0 > 8) return;
+    const int k = rank[b];
+    for (int l = 0; l < k; ++l) {
+        float sum = 0.f;
+        for (int64_t e = e0; e < e1; ++e) sum += zu[bmcol[e] + l];
+        t[toff[m] + l] = sum;
+    }
+}
+
+// The canonical blocks of more than 8 slices (big[]): one warp per block;
+// lane j sums the slices j, j + 32, ... of column l, then a warp sum.
+__global__ void k_tmirror_big(const int32_t* __restrict__ big, int64_t nbig,
+                              const int32_t* __restrict__ rank,
+                              const int32_t* __restrict__ mirror_of,
+                              const int64_t* __restrict__ boff, const int64_t* __restrict__ bmcol,
+                              int64_t nlr, int64_t nb, const int64_t* __restrict__ toff,
+                              const float* __restrict__ zu, float* __restrict__ t)
+{
+    const int64_t w = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= nbig) return;
+    const int b = big[w];
+    const int32_t m = mirror_of[b];
     const int k = rank[b];
     const int64_t e0 = boff[b], e1 = b + 1 < nb ? boff[b + 1] : nlr;
-    if (e1 - e0 <= 8) {
-        // few slices (most blocks): lane l sums column l over them in order
-        for (int l = lane; l < k; l += 32) {
-            float sum = 0.f;
-            for (int64_t e = e0; e < e1; ++e) sum += zu[bmcol[e] + l];
-            t[toff[m] + l] = sum;
-        }
-        return;
-    }
     for (int l = 0; l < k; ++l) {
         float sum = 0.f;
         for (int64_t e = e0 + lane; e < e1; e += 32) sum += zu[bmcol[e] + l];
         sum = warp_sum(sum);
         if (lane == 0) t[toff[m] + l] = sum;
     }
+}
+
+// Canonical blocks with a mirror and more than 8 slices.
+__global__ void k_big_flag(const int32_t* __restrict__ mirror_of, const int64_t* __restrict__ boff,
+                           int64_t nlr, int64_t nb, int64_t* __restrict__ f)
+{
+    const int64_t b = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (b >= nb) return;
+    const int64_t e1 = b + 1 < nb ? boff[b + 1] : nlr;
+    f[b] = (mirror_of[b] >= 0 && e1 - boff[b] > 8) ? 1 : 0;
+}
+
+__global__ void k_big_ids(const int64_t* __restrict__ f, const int64_t* __restrict__ off,
+                          int64_t nb, int32_t* __restrict__ ids)
+{
+    const int64_t b = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (b < nb && f[b]) ids[off[b]] = (int32_t)b;
 }
 
 // First U column of every block-major low-rank entry (through the CSR
@@ -1006,15 +1037,23 @@ __global__ void k_adm_class(const Blk* __restrict__ blk, int64_t n, int32_t* __r
 
 // First mirror column of every tile's U stream (class-1 entries follow the
 // class-0 ones within a tile).
-__global__ void k_umid(const int64_t* __restrict__ ptr, const int2* __restrict__ ent,
-                       const int32_t* __restrict__ cls, const int64_t* __restrict__ ecol,
-                       const int64_t* __restrict__ ucol_ptr, int64_t nt, int64_t* __restrict__ umid)
+// (umid starts as the end of the tile's U stream; the first class-1 entry
+// of a tile, the one whose predecessor in the tile is class 0, sets it)
+__global__ void k_umid_init(const int64_t* __restrict__ ucol_ptr, int64_t nt,
+                            int64_t* __restrict__ umid)
 {
     const int64_t q = (int64_t)blockIdx.x * NT + threadIdx.x;
-    if (q >= nt) return;
-    int64_t e = ptr[q];
-    while (e < ptr[q + 1] && cls[ent[e].x] == 0) ++e;
-    umid[q] = e < ptr[q + 1] ? ecol[e] : ucol_ptr[q + 1];
+    if (q < nt) umid[q] = ucol_ptr[q + 1];
+}
+
+__global__ void k_umid(const int64_t* __restrict__ ptr, const int2* __restrict__ ent,
+                       const int32_t* __restrict__ et, const int32_t* __restrict__ cls,
+                       const int64_t* __restrict__ ecol, int64_t ne, int64_t* __restrict__ umid)
+{
+    const int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (e >= ne || cls[ent[e].x] == 0) return;
+    const int32_t q = et[e];
+    if (e == ptr[q] || cls[ent[e - 1].x] == 0) umid[q] = ecol[e];
 }
 
 // Pass A / pass B columns of every tile (A: canonical U + near; B: mirror U).
@@ -1278,11 +1317,21 @@ void mvp_build_lists(const Blk* ablk, const int32_t* rank, int64_t n_adm, const 
                                                    L.ucol_t.p); note_launch();
         if (sym_near) {
             L.umid.alloc(n_tiles, s);
-            k_umid<<<grid_for(n_tiles), NT, 0, s>>>(L.lr_ptr.p, L.lr_ent.p, acls.p, ecol.p,
-                                                   L.ucol_ptr.p, n_tiles, L.umid.p); note_launch();
+            k_umid_init<<<grid_for(n_tiles), NT, 0, s>>>(L.ucol_ptr.p, n_tiles, L.umid.p); note_launch();
+            k_umid<<<grid_for(L.n_lr), NT, 0, s>>>(L.lr_ptr.p, L.lr_ent.p, L.lr_tile.p, acls.p,
+                                                  ecol.p, L.n_lr, L.umid.p); note_launch();
             // lr_ecol: the first U column of every block-major entry
             L.lr_ecol.alloc(L.n_lr, s);
             k_bm_ecol<<<grid_for(L.n_lr), NT, 0, s>>>(L.lr_pos.p, ecol.p, L.n_lr, L.lr_ecol.p); note_launch();
+            // the canonical blocks of more than 8 slices
+            DevBuf<int64_t> bf(n_adm, s), bo(n_adm + 1, s);
+            k_big_flag<<<grid_for(n_adm), NT, 0, s>>>(L.mirror_of.p, L.lr_boff.p, L.n_lr, n_adm,
+                                                     bf.p); note_launch();
+            scan_exclusive_i64(bf.p, bo.p, n_adm, bo.p + n_adm, s);
+            HM_CUDA(cudaMemcpyAsync(&L.n_big, bo.p + n_adm, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            HM_CUDA(cudaStreamSynchronize(s));
+            L.big.alloc(std::max<int64_t>(L.n_big, 1), s);
+            k_big_ids<<<grid_for(n_adm), NT, 0, s>>>(bf.p, bo.p, n_adm, L.big.p); note_launch();
         }
         HM_CUDA(cudaStreamSynchronize(s));
     } else {
@@ -1536,9 +1585,14 @@ void run_typed(const MvpPlan& P, R* xm, R* t, R* tp, double* part, const double*
             launch_tile<R, FMT>(v, A, xm, t, part, s);
             if (rec) HM_CUDA(cudaEventRecord(rec->e[3], s));
             if (P.n_adm > 0) {
-                k_tmirror<<<(unsigned)ceil_div(P.n_adm * 32, NT), NT, 0, s>>>(
+                k_tmirror_small<<<grid_for(P.n_adm), NT, 0, s>>>(
                     P.rank, P.mirror_of, P.lr_boff, P.lr_ecol, P.n_lr, P.n_adm, P.toff,
                     P.zubuf, t); note_launch();
+                if (P.n_big > 0) {
+                    k_tmirror_big<<<(unsigned)ceil_div(P.n_big * 32, NT), NT, 0, s>>>(
+                        P.big, P.n_big, P.rank, P.mirror_of, P.lr_boff, P.lr_ecol, P.n_lr,
+                        P.n_adm, P.toff, P.zubuf, t); note_launch();
+                }
             }
             if (P.n_items_b > 0) {
                 MvpPlan B = P;

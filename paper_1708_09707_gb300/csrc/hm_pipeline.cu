@@ -1459,6 +1459,8 @@ void build_sets(hm_handle_s& h, int nsets, const double* points_all, const int64
         P.lr_pos = h.lists.lr_pos.p;
         P.lr_ecol = h.lists.lr_ecol.p;
         P.n_lr = h.lists.n_lr;
+        P.big = h.lists.big.p;
+        P.n_big = h.lists.n_big;
     }
     mvp_alloc_work(P, h.work, s);
     HM_CUDA(cudaStreamSynchronize(s));
