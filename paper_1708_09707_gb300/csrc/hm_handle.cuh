@@ -123,7 +123,10 @@ void alloc_factor_meta(hm_handle_s& h);
 void compress(hm_handle_s& h, const uint32_t* ids, int64_t n, const int32_t* kpred,
               bool keep_reserved = false);
 // learned rank model (hm_mlp.cu)
-void predict_ranks(hm_handle_s& h, int32_t* kpred);
+// Predicted ranks (the rank model) of the admissible blocks ids[0..nids)
+// into kpred[id] (all blocks when ids is null).
+void predict_ranks(hm_handle_s& h, int32_t* kpred, const uint32_t* ids = nullptr,
+                   int64_t nids = -1);
 void rerun_mispredicted(hm_handle_s& h);
 void cg_solve(hm_handle_s& h, const double* b, double* x, double rtol, int maxit, int* iters,
               double* relres);

@@ -190,10 +190,11 @@ __global__ void k_features(const int2* __restrict__ pairs, const int32_t* __rest
                            const double* __restrict__ bmax, const int32_t* __restrict__ lo,
                            const int32_t* __restrict__ hi, double ell, double aca_eps, int kernel,
                            const int32_t* __restrict__ rank, float* __restrict__ F,
-                           float* __restrict__ target)
+                           float* __restrict__ target, const uint32_t* __restrict__ ids)
 {
-    int64_t b = (int64_t)blockIdx.x * NT + threadIdx.x;
-    if (b >= n) return;
+    int64_t r = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (r >= n) return;
+    const int64_t b = ids ? (int64_t)ids[r] : r;   // the block of feature row r
     const int q = bset[b];
     const int64_t base = set_node0[q];
     const int64_t t = base + pairs[b].x, s = base + pairs[b].y;
@@ -207,7 +208,7 @@ __global__ void k_features(const int2* __restrict__ pairs, const int32_t* __rest
         double g2 = fmax(0.0, bmin[s * 3 + i] - bmax[t * 3 + i]);
         G2 += g1 * g1 + g2 * g2;
     }
-    float* f = F + b * MLP_F;
+    float* f = F + r * MLP_F;
     f[0] = (float)(set_d[q] / 3.0);
     f[1] = (float)(log2((double)(hi[t] - lo[t])) / 16.0);
     f[2] = (float)(log2((double)(hi[s] - lo[s])) / 16.0);
@@ -216,15 +217,16 @@ __global__ void k_features(const int2* __restrict__ pairs, const int32_t* __rest
     f[5] = (float)log2(1.0 + sqrt(G2) / ell);
     f[6] = (float)(-log10(aca_eps) / 8.0);
     f[7] = (float)kernel;
-    if (target && rank) target[b] = (float)log2(1.0 + (double)rank[b]);
+    if (target && rank) target[r] = (float)log2(1.0 + (double)rank[b]);
 }
 
-__global__ void k_pred_to_rank(const float* __restrict__ yhat, int64_t n, int32_t* __restrict__ k)
+__global__ void k_pred_to_rank(const float* __restrict__ yhat, int64_t n,
+                               const uint32_t* __restrict__ ids, int32_t* __restrict__ k)
 {
     int64_t b = (int64_t)blockIdx.x * NT + threadIdx.x;
     if (b >= n) return;
     float r = ceilf(1.25f * (exp2f(fminf(yhat[b], 8.f)) - 1.f) + 2.f);
-    k[b] = (int32_t)fmaxf(r, 1.f);
+    k[ids ? (int64_t)ids[b] : b] = (int32_t)fmaxf(r, 1.f);
 }
 
 __global__ void k_flag_mispred(const int32_t* __restrict__ flags, int64_t n,
@@ -241,10 +243,13 @@ __global__ void k_emit_ids(const int64_t* __restrict__ f, const int64_t* __restr
     if (b < n && f[b]) ids[off[b]] = (uint32_t)b;
 }
 
-void features(hm_handle_s& h, float* F, float* target, cudaStream_t s)
+// Features of the admissible blocks ids[0..n) (all blocks when ids is null),
+// one row per listed block.
+void features(hm_handle_s& h, float* F, float* target, cudaStream_t s,
+              const uint32_t* ids = nullptr, int64_t nids = -1)
 {
-    const int64_t n = h.n_adm;
-    if (n == 0) return;
+    const int64_t n = ids ? nids : h.n_adm;
+    if (n <= 0) return;
     std::vector<int64_t> n0(h.sets.size());
     std::vector<int32_t> dd(h.sets.size());
     for (size_t q = 0; q < h.sets.size(); ++q) {
@@ -257,7 +262,7 @@ void features(hm_handle_s& h, float* F, float* target, cudaStream_t s)
     copy_in(sd.p, dd.data(), dd.size() * sizeof(int32_t), s);
     k_features<<<grid_for(n), NT, 0, s>>>(h.adm_pairs.p, h.adm_set.p, n, sn0.p, sd.p, h.bmin.p,
                                          h.bmax.p, h.node_lo.p, h.node_hi.p, h.ell, h.aca_eps,
-                                         h.kernel, target ? h.rank.p : nullptr, F, target); note_launch();
+                                         h.kernel, target ? h.rank.p : nullptr, F, target, ids); note_launch();
     HM_LAUNCH("features");
     HM_CUDA(cudaStreamSynchronize(s));
 }
@@ -294,17 +299,17 @@ void mlp_adam(float* theta, const float* grad, float* m, float* v, int64_t t, fl
     HM_LAUNCH("adam");
 }
 
-void predict_ranks(hm_handle_s& h, int32_t* kpred)
+void predict_ranks(hm_handle_s& h, int32_t* kpred, const uint32_t* ids, int64_t nids)
 {
     cudaStream_t s = h.stream;
-    const int64_t n = h.n_adm;
-    if (n == 0) return;
+    const int64_t n = ids ? nids : h.n_adm;
+    if (n <= 0) return;
     if (!h.opt.rank_model_theta) fail(HM_EINVAL, "rank_model set without rank_model_theta");
     DevBuf<float> th(MLP_NPARAM, s), F(n * MLP_F, s), y(n, s);
     copy_in(th.p, h.opt.rank_model_theta, MLP_NPARAM * sizeof(float), s);
-    features(h, F.p, nullptr, s);
+    features(h, F.p, nullptr, s, ids, n);
     mlp_forward(th.p, F.p, n, y.p, s);
-    k_pred_to_rank<<<grid_for(n), NT, 0, s>>>(y.p, n, kpred); note_launch();
+    k_pred_to_rank<<<grid_for(n), NT, 0, s>>>(y.p, n, ids, kpred); note_launch();
     HM_LAUNCH("predict ranks");
 }
 

@@ -1334,10 +1334,8 @@ void build_sets(hm_handle_s& h, int nsets, const double* points_all, const int64
         Timer ta(s);
         alloc_factor_meta(h);
         DevBuf<int32_t> kpred;
-        if (opt.rank_model) {
-            kpred.alloc(std::max<int64_t>(h.n_adm, 1), s);
-            predict_ranks(h, kpred.p);
-        }
+        if (opt.rank_model) kpred.alloc(std::max<int64_t>(h.n_adm, 1), s);
+        if (opt.rank_model && !(opt.symmetric && h.n_adm > 0)) predict_ranks(h, kpred.p);
         if (opt.symmetric && h.n_adm > 0) {
             // compress the canonical leaves only, then mirror
             const int64_t n = h.n_adm;
@@ -1350,6 +1348,8 @@ void build_sets(hm_handle_s& h, int nsets, const double* points_all, const int64
             DevBuf<uint32_t> ids(std::max<int64_t>(nc, 1), s);
             k_canon_ids<<<grid_for(n), NT, 0, s>>>(f.p, off.p, n, ids.p); note_launch();
             HM_LAUNCH("canonical leaves");
+            // only the canonical leaves are compressed: predict their ranks only
+            if (opt.rank_model) predict_ranks(h, kpred.p, ids.p, nc);
             compress(h, ids.p, nc, opt.rank_model ? kpred.p : nullptr);
             if (opt.rank_model) rerun_mispredicted(h);
             k_mirror<<<grid_for(n), NT, 0, s>>>(h.ablk.p, n, h.Uptr.p, h.Vptr.p, h.rank.p, h.nrej.p,
