@@ -466,11 +466,15 @@ struct AcaOrder {
     int64_t n = 0;
     DevBuf<uint32_t> order;
     DevBuf<int64_t> pre, preu;
-    std::vector<int64_t> hpre, hpreu;
+    std::vector<int64_t> hpre, hpreu;   // host copies of pre / preu (when asked for)
+    int64_t tot = 0, totu = 0;           // pre[n], preu[n]
     int64_t cstart[ACA_NCLASS][ACA_NKB], cend[ACA_NCLASS][ACA_NKB];
 };
 
-void aca_order(hm_handle_s& h, const uint32_t* ids, int64_t n, const int32_t* kpred, AcaOrder& O)
+// host_prefix: copy the whole reservation prefixes to the host (the bounded
+// scratch passes and batch limits cut ranges by them); else only the totals.
+void aca_order(hm_handle_s& h, const uint32_t* ids, int64_t n, const int32_t* kpred, AcaOrder& O,
+               bool host_prefix = true)
 {
     cudaStream_t s = h.stream;
     O.n = n;
@@ -490,13 +494,20 @@ void aca_order(hm_handle_s& h, const uint32_t* ids, int64_t n, const int32_t* kp
     k_reserve<<<grid_for(n), NT, 0, s>>>(h.ablk.p, O.order.p, n, h.kres.p, res.p, resu.p); note_launch();
     scan_exclusive_i64(res.p, O.pre.p, n, O.pre.p + n, s);
     scan_exclusive_i64(resu.p, O.preu.p, n, O.preu.p + n, s);
-    O.hpre.resize(n + 1);
-    O.hpreu.resize(n + 1);
-    HM_CUDA(cudaMemcpyAsync(O.hpre.data(), O.pre.p, (n + 1) * sizeof(int64_t),
-                            cudaMemcpyDeviceToHost, s));
-    HM_CUDA(cudaMemcpyAsync(O.hpreu.data(), O.preu.p, (n + 1) * sizeof(int64_t),
-                            cudaMemcpyDeviceToHost, s));
+    if (host_prefix) {
+        O.hpre.resize(n + 1);
+        O.hpreu.resize(n + 1);
+        HM_CUDA(cudaMemcpyAsync(O.hpre.data(), O.pre.p, (n + 1) * sizeof(int64_t),
+                                cudaMemcpyDeviceToHost, s));
+        HM_CUDA(cudaMemcpyAsync(O.hpreu.data(), O.preu.p, (n + 1) * sizeof(int64_t),
+                                cudaMemcpyDeviceToHost, s));
+    }
+    int64_t t2[2] = {0, 0};
+    HM_CUDA(cudaMemcpyAsync(&t2[0], O.pre.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    HM_CUDA(cudaMemcpyAsync(&t2[1], O.preu.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     HM_CUDA(cudaStreamSynchronize(s));
+    O.tot = t2[0];
+    O.totu = t2[1];
     int64_t q = 0;
     for (int c = ACA_NCLASS - 1; c >= 0; --c)
         for (int kb = 0; kb < ACA_NKB; ++kb) {
@@ -613,7 +624,9 @@ void compress(hm_handle_s& h, const uint32_t* ids, int64_t n, const int32_t* kpr
     const int esz = h.precision == HM_PREC_FP64 ? 8 : 4;
     if (n == 0) return;
     AcaOrder O;
-    aca_order(h, ids, n, kpred, O);
+    // learned sizing needs only the totals on the host, unless batch limits
+    // cut the class ranges by the prefixes
+    aca_order(h, ids, n, kpred, O, !kpred || aca_batch_entries() > 0);
     const std::vector<int64_t>& hpre = O.hpre;
     const std::vector<int64_t>& hpreu = O.hpreu;
     DevBuf<int64_t> setn;
@@ -623,8 +636,8 @@ void compress(hm_handle_s& h, const uint32_t* ids, int64_t n, const int32_t* kpr
         // learned sizing: reserve the predicted ranks directly (no copy)
         auto useg = std::make_unique<FactorSegment>();
         auto vseg = std::make_unique<FactorSegment>();
-        useg->mem.alloc((size_t)std::max<int64_t>(hpreu[n], 1) * esz, s);
-        vseg->mem.alloc((size_t)std::max<int64_t>(hpre[n] - hpreu[n], 1) * esz, s);
+        useg->mem.alloc((size_t)std::max<int64_t>(O.totu, 1) * esz, s);
+        vseg->mem.alloc((size_t)std::max<int64_t>(O.tot - O.totu, 1) * esz, s);
         k_set_ptrs<<<grid_for(n), NT, 0, s>>>(O.order.p, 0, n, O.pre.p, O.preu.p, useg->mem.p,
                                                vseg->mem.p, esz, h.Uptr.p, h.Vptr.p); note_launch();
         HM_LAUNCH("set ptrs");
@@ -888,9 +901,9 @@ void np_rerun(hm_handle_s& h, const uint32_t* ids, int64_t n, const AcaArgs& a, 
     k_np_mispred_ids<<<grid_for(n), NT, 0, s>>>(ids, n, f.p, off.p, mis.p); note_launch();
     HM_LAUNCH("np mispredicted ids");
     AcaOrder O;
-    aca_order(h, mis.p, cnt, nullptr, O);
-    DevBuf<char> mem((size_t)std::max<int64_t>(O.hpre[cnt], 1) * esz, s);
-    char* vbase = mem.p + O.hpreu[cnt] * esz;
+    aca_order(h, mis.p, cnt, nullptr, O, aca_batch_entries() > 0);
+    DevBuf<char> mem((size_t)std::max<int64_t>(O.tot, 1) * esz, s);
+    char* vbase = mem.p + O.totu * esz;
     k_set_ptrs<<<grid_for(cnt), NT, 0, s>>>(O.order.p, 0, cnt, O.pre.p, O.preu.p, mem.p, vbase,
                                             esz, h.Uptr.p, h.Vptr.p); note_launch();
     HM_LAUNCH("set ptrs");
@@ -937,8 +950,8 @@ void np_matvec(hm_handle_s& h, const double* x, double* y, int accumulate, cudaS
         if (nb > 0) {
             const int32_t* kp = h.opt.rank_model ? h.np_kpred.p : nullptr;
             AcaOrder O;
-            aca_order(h, h.np_ids.p + c0, nb, kp, O);
-            char* vbase = h.np_scratch.p + O.hpreu[nb] * esz;
+            aca_order(h, h.np_ids.p + c0, nb, kp, O, aca_batch_entries() > 0);
+            char* vbase = h.np_scratch.p + O.totu * esz;
             k_set_ptrs<<<grid_for(nb), NT, 0, hs>>>(O.order.p, 0, nb, O.pre.p, O.preu.p,
                                                      h.np_scratch.p, vbase, esz, h.Uptr.p, h.Vptr.p); note_launch();
             HM_LAUNCH("set ptrs");
