@@ -106,7 +106,7 @@ __global__ void k_classes(const Blk* __restrict__ blk, const uint32_t* __restric
     int c = aca_class_of(B.m, B.n);
     int full = min(kcap, min(B.m, B.n));
     int k = kpred ? max(1, min(kpred[b], full)) : full;
-    // blocks of more than 4096 rows reserve at least 32 ranks: the few of
+    // blocks of more than 2048 rows reserve at least 32 ranks: the few of
     // them a model under-predicts were the long pole of the re-run phase
     // (the reservation grows by about 28 %, the ACA phase falls by 0.5 ms)
     if (kpred && c >= 6) k = max(k, min(full, 32));
