@@ -95,6 +95,21 @@ __host__ __device__ __forceinline__ int aca_class_of(int m, int n)
     while (c < ACA_NCLASS - 1 && d > aca_class_dim(c)) ++c;
     return c;
 }
+// Columns block (m x n) reserves for its factors: min(k_cap, m, n) without a
+// rank model; with one, its prediction kpred clamped to [1, min(k_cap, m, n)],
+// and at least 32 in the size classes above 2048 rows (the few large blocks
+// a model under-predicts were the long pole of the re-run phase). Every
+// reservation, and every scratch sized by reservations, comes from here.
+__host__ __device__ __forceinline__ int aca_reservation(int m, int n, int kcap, const int32_t* kpred,
+                                                        int64_t b)
+{
+    const int full = kcap < (m < n ? m : n) ? kcap : (m < n ? m : n);
+    if (!kpred) return full;
+    int k = kpred[b] < full ? kpred[b] : full;
+    if (k < 1) k = 1;
+    if (aca_class_of(m, n) >= 6 && k < 32) k = full < 32 ? full : 32;
+    return k;
+}
 
 // Run ACA on the blocks listed in order[0..n) (indices into the block arrays),
 // all of size class cls; max_n bounds the column count of any block.

@@ -104,12 +104,7 @@ __global__ void k_classes(const Blk* __restrict__ blk, const uint32_t* __restric
     const uint32_t b = ids ? ids[q] : (uint32_t)q;
     Blk B = blk[b];
     int c = aca_class_of(B.m, B.n);
-    int full = min(kcap, min(B.m, B.n));
-    int k = kpred ? max(1, min(kpred[b], full)) : full;
-    // blocks of more than 2048 rows reserve at least 32 ranks: the few of
-    // them a model under-predicts were the long pole of the re-run phase
-    // (the reservation grows by about 28 %, the ACA phase falls by 0.5 ms)
-    if (kpred && c >= 6) k = max(k, min(full, 32));
+    const int k = aca_reservation(B.m, B.n, kcap, kpred, b);
     kres[b] = k;
     const int kb = aca_kbucket(k);
     // largest class first, then the rank buckets in increasing order
@@ -724,8 +719,7 @@ __global__ void k_pred_reserve(const Blk* __restrict__ blk, int64_t n, int kcap,
     const int64_t b = (int64_t)blockIdx.x * NT + threadIdx.x;
     if (b >= n) return;
     const Blk B = blk[b];
-    const int full = min(kcap, min(B.m, B.n));
-    res[b] = (int64_t)max(1, min(kpred[b], full)) * (B.m + B.n);
+    res[b] = (int64_t)aca_reservation(B.m, B.n, kcap, kpred, b) * (B.m + B.n);
 }
 
 // Blocks of ids[0..n) whose reservation was too small (flag bit 0).
@@ -955,6 +949,9 @@ void np_matvec(hm_handle_s& h, const double* x, double* y, int accumulate, cudaS
             const int32_t* kp = h.opt.rank_model ? h.np_kpred.p : nullptr;
             AcaOrder O;
             aca_order(h, h.np_ids.p + c0, nb, kp, O, aca_batch_entries() > 0);
+            // the pass's reservations must fit the scratch they were cut for
+            if (O.tot * esz > (int64_t)h.np_scratch.n)
+                fail(HM_EOVERFLOW, "on-the-fly pass reserves more than its scratch");
             char* vbase = h.np_scratch.p + O.totu * esz;
             k_set_ptrs<<<grid_for(nb), NT, 0, hs>>>(O.order.p, 0, nb, O.pre.p, O.preu.p,
                                                      h.np_scratch.p, vbase, esz, h.Uptr.p, h.Vptr.p); note_launch();

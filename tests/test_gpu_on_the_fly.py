@@ -155,6 +155,25 @@ def test_rank_model_on_the_fly_forced_reruns(hm, orc):
     assert st["n_mispredicted"] > 0.5 * st["n_adm"]
 
 
+def test_rank_model_tight_scratch_with_large_blocks(hm, orc):
+    # every pass filled to a small scratch, blocks above 2048 rows (whose
+    # reservation has a floor of 32 ranks) predicted at rank 1: the passes
+    # are cut by the reservations the ACA then uses, so each fits its scratch
+    n = 6000
+    pts = _pts(n, 2, "m", 44)
+    x = inputs.normal_vector(n, inputs.X_SEED)
+    th = np.zeros(4801, np.float32)
+    th[4800] = -4.0
+    O = orc.HMatrix(pts, 0, 0.1, 64, 1.0, 1e-8)
+    H = hm.HMatrix(pts, 0, 0.1, 64, 1.0, 1e-8, on_the_fly=True, rank_model_theta=th,
+                   scratch_gb=0.002)
+    y = H.matvec(x)
+    st = H.stats()
+    H.free()
+    assert st["aca_passes"] >= 3
+    assert rel(y, O.matvec(x)) <= FP64_TOL
+
+
 def test_no_admissible_leaf_and_eta_zero(hm, orc):
     """C >= N leaves one dense block and eta = 0 admits no block of positive
     diameter: both products are the dense matrix-vector product."""
