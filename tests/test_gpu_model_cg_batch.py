@@ -142,6 +142,14 @@ def test_cg_matches_oracle(hm, orc, sigma2):
     back = np.linalg.norm(b - H.matvec(xm)) / (nrm * np.linalg.norm(xm) + np.linalg.norm(b))
     assert back <= 1e-5, back
     assert _rel(xm, xo) <= 4.0 * back * nrm / sigma2
+    # the same with the symmetric product (symmetric = 2), the benchmark's form
+    Hs = hm.HMatrix(pts, 1, 0.1, 32, 1.0, 1e-8, sigma2=sigma2, precision=hm.PREC_MIXED,
+                    symmetric=2)
+    xs, its, rrs = Hs.cg(b, rtol=1e-6, maxit=3000)
+    assert rrs <= 1e-6
+    backs = np.linalg.norm(b - H.matvec(xs)) / (nrm * np.linalg.norm(xs) + np.linalg.norm(b))
+    assert backs <= 1e-5, backs
+    Hs.free()
 
 
 @pytest.mark.parametrize("prec", [0, 1])
