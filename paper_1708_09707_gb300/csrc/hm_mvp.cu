@@ -236,19 +236,30 @@ __device__ __forceinline__ void tile_stream(int64_t cb, int64_t ncols, int hw, i
         }
         const int64_t cn = c0 + 16 * TB + 16 * hl;
         const R mnext = (hl < TB && cn < ncols) ? mult(cn) : R(0);
-        // plain sums over groups of four columns, each added compensated:
-        // the grouping, hence the result, is the same for every TB
+        if constexpr (sizeof(R) == 8) {
+            // double: one running sum per row, column after column (the
+            // FP64 pipe bounds this kernel, so no extra addition per group)
 #pragma unroll
-        for (int e0 = 0; e0 < TB; e0 += 4) {
-            R sg[4] = {R(0), R(0), R(0), R(0)};
-#pragma unroll
-            for (int e = e0; e < e0 + 4; ++e) {
+            for (int e = 0; e < TB; ++e) {
                 const R m = __shfl_sync(hmask, mv, e, 16);
 #pragma unroll
-                for (int i = 0; i < 4; ++i) sg[i] = fma(a[e][i], m, sg[i]);
+                for (int i = 0; i < 4; ++i) acc[i].s = fma(a[e][i], m, acc[i].s);
             }
+        } else {
+            // plain sums over groups of four columns, each added compensated:
+            // the grouping, hence the result, is the same for every TB
 #pragma unroll
-            for (int i = 0; i < 4; ++i) acc[i].add(sg[i]);
+            for (int e0 = 0; e0 < TB; e0 += 4) {
+                R sg[4] = {R(0), R(0), R(0), R(0)};
+#pragma unroll
+                for (int e = e0; e < e0 + 4; ++e) {
+                    const R m = __shfl_sync(hmask, mv, e, 16);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) sg[i] = fma(a[e][i], m, sg[i]);
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) acc[i].add(sg[i]);
+            }
         }
         mv = mnext;
     }
@@ -528,8 +539,14 @@ k_tile_tma(MvpPlan P, const R* __restrict__ xm, const R* __restrict__ t, double*
                     }
                 }
                 const R m = __shfl_sync(hmask, mv, e, 16);
+                if constexpr (sizeof(R) == 8) {
+                    // double: one running sum per row, as in k_tile
 #pragma unroll
-                for (int i = 0; i < 4; ++i) sg[i] = fma(a[i], m, sg[i]);
+                    for (int i = 0; i < 4; ++i) acc[i].s = fma(a[i], m, acc[i].s);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) sg[i] = fma(a[i], m, sg[i]);
+                }
                 if constexpr (ZT) {
                     if (e < 4 && (!isu || P.zubuf)) {
 #pragma unroll
@@ -539,7 +556,7 @@ k_tile_tma(MvpPlan P, const R* __restrict__ xm, const R* __restrict__ t, double*
                 // groups of four columns of this half-warp's sequence, as in
                 // k_tile; a stream part starts a new group
                 const bool last = (k == nuch - 1 || k == nch - 1) && e == E - 1;
-                if (++ing == 4 || last) {
+                if (sizeof(R) != 8 && (++ing == 4 || last)) {
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                         acc[i].add(sg[i]);
