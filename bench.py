@@ -73,8 +73,12 @@ def parse():
     p.add_argument("--scratch-gb", type=float, default=0.0,
                    help="cap on the ACA scratch of the plain (no rank model) build")
     p.add_argument("--sets", type=int, default=64,
-                   help="ragged64 workload: build only the first SETS of the 64 point sets "
-                        "(all 64 in stored mode need more than one GPU's memory)")
+                   help="ragged64 workload: build only the first SETS of the 64 point sets")
+    p.add_argument("--batch-mode", default="auto", choices=["auto", "stored", "on-the-fly"],
+                   help="ragged64 workload: store the factors and near field, or recompute "
+                        "them in every product (hm_build_batch with on_the_fly); auto: "
+                        "stored up to 8 sets, on the fly above (all 64 sets stored need "
+                        "more than one GPU's memory)")
     p.add_argument("--gather-shape", type=int, default=-1,
                    help="launch shape of the product's gather (hm_set_gather_shape); -1 = tuned")
     p.add_argument("--symmetric", default="near", choices=["near", "on", "off"],
@@ -525,7 +529,8 @@ def run_batch(args):
     x = torch.from_numpy(x_h).cuda()
     y = torch.empty_like(x)
     stream = torch.cuda.current_stream()
-    opts = dict(precision=hm.PREC_MIXED,
+    otf = args.batch_mode == "on-the-fly" or (args.batch_mode == "auto" and len(sizes) > 8)
+    opts = dict(precision=hm.PREC_MIXED, on_the_fly=otf,
                 symmetric={"near": 2, "on": 1, "off": 0}[args.symmetric])
 
     def step(ev=None, profile=False, host=False):
@@ -585,13 +590,23 @@ def run_batch(args):
         hdist.finalize()
         return
     st = stats[-1]
-    hbm, peak_src = peaks()
-    t_tile = st["t_mvp_tile_ms"] / max(st["mvp_count"], 1)
-    roof = {"bound": "hbm", "kernel": "k_tile (gather: U slices + near field)",
-            "achieved": st["mvp_tile_bytes"] / (t_tile * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
-            "traffic": tile_traffic(st["mvp_tile_bytes"]), "algorithmic_bytes": st["mvp_tile_bytes"],
-            "peak_source": peak_src + " copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
-    roof["frac"] = roof["achieved"] / hbm
+    if otf:
+        # nothing stored: the products are bound by the ACA passes' arithmetic
+        fp32_peak = hm.alu_peak(hm.PREC_MIXED) / 1e12
+        o = otf_roofline(st, w["kernel"], fp32_peak)
+        roof = {"bound": "alu", "kernel": "batched ACA passes (on the fly)",
+                "achieved": o["aca"]["achieved"], "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": o["aca"]["frac"], "traffic": None, "peak_source": o["peak_source"],
+                "phases_per_product": o}
+    else:
+        hbm, peak_src = peaks()
+        t_tile = st["t_mvp_tile_ms"] / max(st["mvp_count"], 1)
+        roof = {"bound": "hbm", "kernel": "k_tile (gather: U slices + near field)",
+                "achieved": st["mvp_tile_bytes"] / (t_tile * 1e-3) / 1e9, "peak": hbm,
+                "unit": "GB/s", "traffic": tile_traffic(st["mvp_tile_bytes"]),
+                "algorithmic_bytes": st["mvp_tile_bytes"],
+                "peak_source": peak_src + " copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+        roof["frac"] = roof["achieved"] / hbm
     unit = "s/step (batched build of %d sets + %d batched H-MVP)" % (len(sizes), N_MVP)
     line = {"metric": METRIC, "value": total / 1e3, "unit": unit, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total,
@@ -602,6 +617,7 @@ def run_batch(args):
                        "sizes": "log-uniform in [1e4, 2^18]", "d": "2 or 3", "kernel": "gaussian",
                        "ell": w["ell"], "leaf": w["leaf"], "eta": w["eta"], "aca_eps": w["eps"],
                        "precision": "mixed", "symmetric": args.symmetric,
+                       "mode": "on the fly" if otf else "stored",
                        "mvp_per_step": N_MVP, "parallelism": "sets sharded" if world > 1 else "single"},
             "build_s": build_ms / 1e3, "mvp_ms": mvp_ms,
             "e2e": {"value": e2e_ms / 1e3, "unit": unit,
@@ -610,7 +626,8 @@ def run_batch(args):
             "roofline": roof, "gpu_launches": int(round(launches)), "clocks": clocks,
             "cpu_baseline": None,
             "stats": {k: st[k] for k in ("n_adm", "n_dense", "sum_rank", "factor_bytes",
-                                         "near_bytes", "mvp_bytes", "t_aca_ms", "t_dense_ms")}}
+                                         "near_bytes", "mvp_bytes", "t_aca_ms", "t_dense_ms",
+                                         "aca_passes", "near_entries")}}
     print(json.dumps(line))
     hdist.finalize()
 

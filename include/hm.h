@@ -119,9 +119,13 @@ typedef struct hm_options {
                              the GPU. With symmetric, a pass compresses the
                              canonical leaves of its range and applies them
                              and their mirror leaves (its row sums then depend
-                             on the pass count to rounding). Not with
-                             rank_model or hm_build_batch; several right-hand
-                             sides run one product each. Default 0. */
+                             on the pass count to rounding). With
+                             hm_build_batch the passes run over the leaves of
+                             all sets in order (a pass may hold leaves of
+                             several sets). With rank_model (square matrices)
+                             the predicted ranks size the passes. Several
+                             right-hand sides run one product each.
+                             Default 0. */
     int64_t row_lo, row_hi; /* block-row share of one H-matrix (distributed
                              H-matrices, the outlook of Sec. 7), Morton-order
                              rows [row_lo, row_hi): keep only the leaves whose

@@ -1092,7 +1092,6 @@ void validate(int nsets, const int64_t* N, const int* d, int kernel, const doubl
         if (o.row_lo < 0 || o.row_lo >= o.row_hi || o.row_hi > N[0])
             fail(HM_EINVAL, "row range must satisfy 0 <= row_lo < row_hi <= N");
     }
-    if (o.on_the_fly && nsets > 1 && !rect) fail(HM_ENOTSUP, "on_the_fly runs without batches");
     if (o.on_the_fly && o.rank_model && rect)
         fail(HM_ENOTSUP, "the rank model needs one square point set");
     if (rect) {

@@ -93,10 +93,47 @@ def test_mixed_matches_oracle_and_options(hm, orc):
     assert np.array_equal(ya, y + 1.0)
 
 
+@pytest.mark.parametrize("sym", [False, True], ids=["general", "symmetric"])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batch_on_the_fly(hm, orc, prec, sym):
+    """hm_build_batch with on_the_fly: the passes run over the leaves of all
+    sets in order, so one pass may hold leaves of several sets. Every set's
+    part of the product equals the oracle's H-matrix of that set within the
+    FP64 / mixed bound and that set's own on-the-fly product to rounding, the
+    stored batch's product agrees, and a repeated product gives the same
+    bits."""
+    # uniform sets: on a 4000-point mixture the FP32 kernel entries alone put
+    # the mixed product 1.4e-5 from the FP64 one (every mixed storage mode alike)
+    sets = [_pts(4000, 2, "u", 42), _pts(3000, 3, "u", 43), _pts(2500, 1, "u", 44),
+            _pts(40, 3, "u", 45)]
+    eps = 1e-8 if prec == 0 else 1e-6
+    kw = dict(precision=prec, symmetric=sym, sigma2=0.01)
+    xs = [inputs.normal_vector(p.shape[0], 50 + q) for q, p in enumerate(sets)]
+    x = np.concatenate(xs)
+    B = hm.HBatch(sets, 0, 0.1, 32, 1.0, eps, on_the_fly=True, scratch_gb=0.004, **kw)
+    y = B.matvec(x)
+    st = B.stats()
+    assert st["aca_passes"] > 2
+    assert st["factor_bytes"] == 0 and st["near_bytes"] == 0
+    assert np.array_equal(B.matvec(x), y)
+    B.free()
+    S = hm.HBatch(sets, 0, 0.1, 32, 1.0, eps, **kw)
+    ys = S.matvec(x)
+    S.free()
+    assert rel(y, ys) <= (1e-13 if prec == 0 else MIXED_TOL)
+    o = 0
+    for p, xq in zip(sets, xs):
+        yq = y[o:o + len(xq)]
+        O = orc.HMatrix(p, 0, 0.1, 32, 1.0, eps, sigma2=0.01, symmetric=sym)
+        assert rel(yq, O.matvec(xq)) <= (FP64_TOL if prec == 0 else MIXED_TOL)
+        H = hm.HMatrix(p, 0, 0.1, 32, 1.0, eps, on_the_fly=True, **kw)
+        assert rel(yq, H.matvec(xq)) <= 1e-13
+        H.free()
+        o += len(xq)
+
+
 def test_refused_combinations(hm):
     pts = _pts(500, 2, "u", 41)
-    with pytest.raises(hm.HMError):
-        hm.HBatch([pts, pts], 0, 0.1, 32, 1.0, 1e-6, precision=hm.PREC_MIXED, on_the_fly=True)
     with pytest.raises(hm.HMError):
         hm.HMatrix(pts, 0, 0.1, 32, 1.0, 1e-6, cols=pts, precision=hm.PREC_MIXED,
                    on_the_fly=True, rank_model_theta=np.zeros(4801, np.float32))
