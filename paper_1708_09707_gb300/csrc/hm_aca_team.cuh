@@ -311,11 +311,14 @@ __device__ __forceinline__ TRed<T> team_reduce(TRed<T> q, const TeamSmem<T>& S, 
 // Resident CTAs per SM asked of the register allocator: the small shapes
 // are latency-bound and want many warps; the large ones keep 2 R residual
 // entries and their loads in flight in registers.
-template <int W, int R>
+template <class T, int W, int R>
 __host__ __device__ constexpr int team_min_ctas()
 {
-    // 128-thread CTAs up to W = 4, one team of W warps above
-    return W > 4 ? (W == 8 && R <= 16 ? 2 : 1) : R <= 4 ? 6 : R <= 16 ? 4 : 2;
+    // 128-thread CTAs up to W = 4, one team of W warps above; float teams of
+    // up to 4 warps with 8 entries per thread fit 96 registers (20 warps per
+    // SM in place of 16)
+    return W > 4 ? (W == 8 && R <= 16 ? 2 : 1)
+                 : R <= 4 ? 6 : (R <= 8 && sizeof(T) == 4) ? 5 : R <= 16 ? 4 : 2;
 }
 // Threads of a CTA: 4 warps, or one team of W warps.
 template <int W>
@@ -491,7 +494,7 @@ __device__ __forceinline__ void team_eval(T (&uh)[R], const DeviceCoords& X, con
 }
 
 template <class T, int KERN, int W, int R>
-__global__ void __launch_bounds__(team_cta_threads<W>(), (team_min_ctas<W, R>()))
+__global__ void __launch_bounds__(team_cta_threads<W>(), (team_min_ctas<T, W, R>()))
 k_aca_team(KernelParams kp, DeviceCoords X, AcaArgs a, const uint32_t* __restrict__ order,
            int64_t nblocks, double thr, T c2, int KT)
 {
