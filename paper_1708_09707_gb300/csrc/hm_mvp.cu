@@ -516,10 +516,19 @@ k_tile_tma(MvpPlan P, const R* __restrict__ xm, const R* __restrict__ t, double*
                         const uint2 h = *reinterpret_cast<const uint2*>(q);
                         const uint2 l = *reinterpret_cast<const uint2*>(q + ld);
                         const float2 h0 = bf2(h.x), h1 = bf2(h.y), l0 = bf2(l.x), l1 = bf2(l.y);
-                        a[0] = (R)(h0.x + l0.x);
-                        a[1] = (R)(h0.y + l0.y);
-                        a[2] = (R)(h1.x + l1.x);
-                        a[3] = (R)(h1.y + l1.y);
+                        if constexpr (sizeof(R) == 4) {
+                            // packed pairs: every entry rounds as hi + lo alone
+                            const float2 s01 = __fadd2_rn(h0, l0), s23 = __fadd2_rn(h1, l1);
+                            a[0] = s01.x;
+                            a[1] = s01.y;
+                            a[2] = s23.x;
+                            a[3] = s23.y;
+                        } else {
+                            a[0] = (R)(h0.x + l0.x);
+                            a[1] = (R)(h0.y + l0.y);
+                            a[2] = (R)(h1.x + l1.x);
+                            a[3] = (R)(h1.y + l1.y);
+                        }
                     } else if (FMT == HM_NEAR_BF16) {
                         const __nv_bfloat16* q = reinterpret_cast<const __nv_bfloat16*>(st + col * ncolb) + ir;
                         const uint2 h = *reinterpret_cast<const uint2*>(q);
@@ -544,13 +553,28 @@ k_tile_tma(MvpPlan P, const R* __restrict__ xm, const R* __restrict__ t, double*
 #pragma unroll
                     for (int i = 0; i < 4; ++i) acc[i].s = fma(a[i], m, acc[i].s);
                 } else {
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) sg[i] = fma(a[i], m, sg[i]);
+                    // packed pairs of rows: every row takes the multiply-add
+                    // it takes alone (the sums of k_tile, bit for bit)
+                    const float2 mm = make_float2(m, m);
+                    const float2 s01 = __ffma2_rn(make_float2(a[0], a[1]), mm, make_float2(sg[0], sg[1]));
+                    const float2 s23 = __ffma2_rn(make_float2(a[2], a[3]), mm, make_float2(sg[2], sg[3]));
+                    sg[0] = s01.x;
+                    sg[1] = s01.y;
+                    sg[2] = s23.x;
+                    sg[3] = s23.y;
                 }
                 if constexpr (ZT) {
                     if (e < 4 && (!isu || P.zubuf)) {
+                        if constexpr (sizeof(R) == 4) {
+                            // rows (0, 2) and (1, 3) in two packed running
+                            // sums, joined at the end
+                            float2 zp = __fmul2_rn(make_float2(a[0], a[1]), make_float2(xr[0], xr[1]));
+                            zp = __ffma2_rn(make_float2(a[2], a[3]), make_float2(xr[2], xr[3]), zp);
+                            za[e] = zp.x + zp.y;
+                        } else {
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) za[e] = fma(a[i], xr[i], za[e]);
+                            for (int i = 0; i < 4; ++i) za[e] = fma(a[i], xr[i], za[e]);
+                        }
                     }
                 }
                 // groups of four columns of this half-warp's sequence, as in
