@@ -72,7 +72,8 @@ __device__ __forceinline__ R warp_sum4(const R (&v)[4], int lane)
 
 // t partials: one warp per (block, 256-column chunk); lane j holds x of 8
 // columns. Single precision reduces each factor column with its own warp
-// sum. Double precision takes the columns four at a time, each lane summing
+// sum; a chunk of at most 64 columns (the blocks of one leaf's width) takes
+// two factor columns at once, one per half-warp. Double precision takes the columns four at a time, each lane summing
 // its eight products per column, then one reduce-scatter (warp_sum4) per
 // four columns: the additions share the FP64 pipe with the dot products, and
 // this cuts them from five to 1.5 per column (measured at N = 2^20: 13.3 ms
@@ -95,6 +96,36 @@ k_vtx(const Blk* __restrict__ blk, const int32_t* __restrict__ rank,
     const int n = B.n;
     const int cn = min(VCH, n - c0);
     const R* __restrict__ V = reinterpret_cast<const R*>(Vptr[b]);
+    if (sizeof(R) == 4 && cn <= 64) {
+        // chunks of at most 64 columns in float: half-warp h takes the ranks
+        // l = h, h + 2, ..., lane j of it the columns j, j + 16, j + 32,
+        // j + 48 (one running sum), then a butterfly over the half-warp
+        const int h = lane >> 4, j = lane & 15;
+        R xv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int jj = j + 16 * i;
+            xv[i] = jj < cn ? xm[B.col0 + c0 + jj] : R(0);
+        }
+        const int64_t d = dst[w];
+        R* out = d >= 0 ? tp + d : t + (-d - 1);
+        for (int l0 = 0; l0 < k; l0 += 2) {
+            const int l = l0 + h;
+            R s = 0;
+            if (l < k) {
+                const R* Vl = V + (int64_t)l * n + c0;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int jj = j + 16 * i;
+                    if (jj < cn) s += Vl[jj] * xv[i];
+                }
+            }
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (j == 0 && l < k) out[l] = s;
+        }
+        return;
+    }
     R xs[VCH / 32];
 #pragma unroll
     for (int q = 0; q < VCH / 32; ++q) {
