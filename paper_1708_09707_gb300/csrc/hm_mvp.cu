@@ -402,13 +402,13 @@ __device__ __forceinline__ R halfwarp_sum4(const R (&v)[4], int hl)
 // low-rank part) every U column likewise gives (U_b^T x|tile)_l, written at
 // its index in the U stream.
 template <class R, int FMT, int TCOL, int TS, bool ZT = false>
-__global__ void __launch_bounds__(T3_NT, ZT ? 3 : 2)
+__global__ void __launch_bounds__(T3_NT, (ZT || TCOL == 128) ? 3 : 2)
 k_tile_tma(MvpPlan P, const R* __restrict__ xm, const R* __restrict__ t, double* __restrict__ part)
 {
     extern __shared__ __align__(128) unsigned char tsm[];
     constexpr int STAGE = TCOL * col_bytes64<R, FMT>();
     __shared__ uint64_t full[TS], empty[TS];
-    static_assert(TCOL == 32 || TCOL == 64, "32 or 64 columns per stage");
+    static_assert(TCOL == 32 || TCOL == 64 || TCOL == 128, "32, 64 or 128 columns per stage");
     __shared__ double ps[T2_HW][TROWS];
     __shared__ int failed;
     const int64_t item = blockIdx.x;
@@ -511,7 +511,7 @@ k_tile_tma(MvpPlan P, const R* __restrict__ xm, const R* __restrict__ t, double*
         int ing = 0;   // columns of the current group of four
         R xr[4] = {R(0), R(0), R(0), R(0)};   // x of this lane's rows (ZT)
         if constexpr (ZT) {
-            static_assert(TCOL / 16 == 4, "four columns per half-warp and chunk");
+            static_assert(TCOL / 16 == 4 || TCOL / 16 == 8, "four or eight columns per half-warp and chunk");
 #pragma unroll
             for (int i = 0; i < 4; ++i)
                 if (ir + i < mt) xr[i] = xm[P.tile_row0[tile] + ir + i];
@@ -532,7 +532,9 @@ k_tile_tma(MvpPlan P, const R* __restrict__ xm, const R* __restrict__ t, double*
             int cnt;
             chunk(k, isu, c0, cnt);
             const unsigned char* st = tsm + slot * STAGE;
-            R za[4] = {R(0), R(0), R(0), R(0)};
+            R za[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) za[e] = R(0);
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int col = hw + 16 * e;
@@ -595,7 +597,7 @@ k_tile_tma(MvpPlan P, const R* __restrict__ xm, const R* __restrict__ t, double*
                     sg[3] = s23.y;
                 }
                 if constexpr (ZT) {
-                    if (e < 4 && (!isu || P.zubuf)) {
+                    if (!isu || P.zubuf) {
                         if constexpr (sizeof(R) == 4) {
                             // rows (0, 2) and (1, 3) in two packed running
                             // sums, joined at the end
@@ -625,11 +627,15 @@ k_tile_tma(MvpPlan P, const R* __restrict__ xm, const R* __restrict__ t, double*
                     // one transposed product per column of the chunk (near
                     // columns: the mirror leaf's rows; U columns of pass A:
                     // the mirror block's t)
-                    const R z = halfwarp_sum4(za, hl);
-                    const int col = hw + 16 * ((hl >> 2) & 3);
-                    if ((hl & 3) == 0 && col < cnt) {
-                        if (isu) P.zubuf[uc0 + c0 + col] = (float)z;
-                        else P.zbuf[nc0 + c0 + col] = (float)z;
+#pragma unroll
+                    for (int g4 = 0; g4 < E / 4; ++g4) {
+                        const R zq[4] = {za[4 * g4], za[4 * g4 + 1], za[4 * g4 + 2], za[4 * g4 + 3]};
+                        const R z = halfwarp_sum4(zq, hl);
+                        const int col = hw + 16 * (4 * g4 + ((hl >> 2) & 3));
+                        if ((hl & 3) == 0 && col < cnt) {
+                            if (isu) P.zubuf[uc0 + c0 + col] = (float)z;
+                            else P.zbuf[nc0 + c0 + col] = (float)z;
+                        }
                     }
                 }
             }
@@ -1516,6 +1522,9 @@ namespace {
 // shape once on the real data and keeps the fastest for the process; all
 // shapes give bit-identical results.
 constexpr int N_TILE_VARIANTS = 5;
+// Not a tuned shape of its own: the 128-column bulk-copy kernel for pass B
+// of the symmetric product when pass A runs shape 2.
+constexpr int TILE_WIDE = 100;
 
 // The bulk-copy variant needs slices of at most 64 rows and 16-byte column
 // runs (every format but the single bfloat16 one).
@@ -1531,12 +1540,14 @@ void launch_tile(int v, const MvpPlan& P, const R* xm, const R* t, double* part,
     const unsigned g = (unsigned)P.n_items;
     if (P.sym_near) {
         // the symmetric near field runs on the bulk-copy kernels only
-        // (shape 3: six stages, every other shape: four)
+        // (shape 3: six stages of 64 columns, shape 2: two stages of 128
+        // columns, every other shape: four stages of 64 columns)
         if constexpr (sizeof(R) == 4 && FMT != HM_NEAR_BF16) {
             if (P.max_ld > TROWS) fail(HM_ENOTSUP, "symmetric near field: slices above 64 rows");
-            const int nst = v == 3 ? 6 : 4;
-            const int bytes = nst * 64 * col_bytes64<R, FMT>();
-            auto kern = nst == 6 ? k_tile_tma<R, FMT, 64, 6, true> : k_tile_tma<R, FMT, 64, 4, true>;
+            const int tcol = v == 2 ? 128 : 64, nst = v == 3 ? 6 : v == 2 ? 2 : 4;
+            const int bytes = nst * tcol * col_bytes64<R, FMT>();
+            auto kern = v == 2 ? k_tile_tma<R, FMT, 128, 2, true>
+                      : nst == 6 ? k_tile_tma<R, FMT, 64, 6, true> : k_tile_tma<R, FMT, 64, 4, true>;
             HM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
             kern<<<g, T3_NT, bytes, s>>>(P, xm, t, part);
             note_launch();
@@ -1544,6 +1555,20 @@ void launch_tile(int v, const MvpPlan& P, const R* xm, const R* t, double* part,
         } else {
             fail(HM_ENOTSUP, "symmetric near field: mixed precision and a paired or FP32 near field");
         }
+    }
+    if (v == TILE_WIDE) {
+        // two stages of 128 columns (pass B of the symmetric product)
+        if constexpr (sizeof(R) == 4 && FMT != HM_NEAR_BF16) {
+            if (P.max_ld <= TROWS) {
+                const int bytes = 2 * 128 * col_bytes64<R, FMT>();
+                auto kern = k_tile_tma<R, FMT, 128, 2>;
+                HM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+                kern<<<g, T3_NT, bytes, s>>>(P, xm, t, part);
+                note_launch();
+                return;
+            }
+        }
+        v = 0;
     }
     if (v >= tile_variants<R, FMT>(P)) v = 0;
     switch (v) {
@@ -1673,7 +1698,8 @@ void run_typed(const MvpPlan& P, R* xm, R* t, R* tp, double* part, const double*
                 B.zubuf = nullptr;
                 B.items = P.items_b;
                 B.n_items = P.n_items_b;
-                launch_tile<R, FMT>(v == 3 ? 3 : 4, B, xm, t, part + P.n_items * P.max_ld, s);
+                launch_tile<R, FMT>(v == 3 ? 3 : v == 2 ? TILE_WIDE : 4, B, xm, t,
+                                    part + P.n_items * P.max_ld, s);
             }
             k_tile_finish_sym<<<(unsigned)P.n_tiles, 256, 0, s>>>(P, part, x, y, accumulate);
             note_launch();
