@@ -222,7 +222,10 @@ uint64_t hm_kernel_launches(void);
  * or 4 columns in flight per half-warp (3, 2 or 4 CTAs per SM); 3, 4 =
  * bulk-copy (TMA) pipeline into shared memory with 6 or 4 stages of 64
  * columns (slices of at most 64 rows and formats other than the single
- * bfloat16; otherwise shape 0 runs). Every shape gives bit-identical
+ * bfloat16; otherwise shape 0 runs). A product with the symmetric near
+ * field (symmetric = 2) runs the bulk-copy pipeline for every shape: shape 3
+ * with 6 stages of 64 columns, shape 2 with 2 stages of 128 columns, the
+ * others with 4 stages of 64. Every shape gives bit-identical
  * products. Process-wide, not thread-safe against concurrent products.
  * Returns HM_EINVAL for other values. */
 int hm_set_gather_shape(int shape);
