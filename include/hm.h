@@ -412,6 +412,11 @@ int hm_cg(hm_handle h, const double* b, double* x, double rtol, int maxit,
  * Batched form: many independent point sets built and multiplied together
  * (Sec. 4.2 batching applied across problems). points_all holds the sets one
  * after another ((sum N_s), d_s per set, row-major), x_all / y_all likewise.
+ * All sets share one plan: their blocks go through the same size-class ACA
+ * launches and one gather per product. opt as hm_build_ex; on_the_fly runs
+ * the passes over the leaves of all sets in order (a pass may hold leaves
+ * of several sets); a block-row share (row_lo, row_hi) is refused
+ * (HM_ENOTSUP).
  * ------------------------------------------------------------------------ */
 typedef struct hm_batch_s* hm_batch;
 
