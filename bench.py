@@ -503,7 +503,9 @@ def run_reference(args):
 def run_batch(args):
     """The ragged batch of 64 independent point sets (sizes log-uniform in
     [1e4, 2^18], d in {2, 3}): one step builds this rank's sets together
-    (hm_build_batch) and multiplies them N_MVP times. With several ranks the
+    (hm_build_batch) and multiplies them N_MVP times, with stored factors and
+    near field or on the fly (all 64 sets stored need more memory than one
+    GPU has; the on-the-fly roofline is the ACA passes' arithmetic). With several ranks the
     sets are sharded (longest first to the least-loaded rank) and no data
     crosses ranks, so the total work is fixed: strong scaling."""
     import torch
